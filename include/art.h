@@ -1,0 +1,171 @@
+/*
+ * art.h -- C-ABI of the GB300-native adaptive ray tracer (libart_gb300.so).
+ *
+ * Adaptive ray tracing of Kerr black-hole images after Gelles et al. 2021, "The Role of Adaptive
+ * Ray Tracing in Analyzing Black Hole Structure" (arXiv:2103.07417):
+ *   - Sec. 3.2: a base grid of n0x x n0y rays is traced, then N times the grid is refined by a
+ *     factor 2 to (2 n0 - 1); every new point is traced if BOTH estimated errors exceed their
+ *     tolerances (eps_abs > R_abs and eps_rel > R_rel) and interpolated otherwise.  The final
+ *     image has n = 2^N (n0 - 1) + 1 points per axis.
+ *   - Eqs. (epabs), (eprel), Appendix A: the estimated errors (linear and nearest schemes) from the
+ *     eight neighbours of the previous level, normalised by I_bar_int, the interpolated mean
+ *     intensity after the first pass.
+ *   - Eqs. (interpdef), (fluxdef), (msedef): interpolation fraction, flux error, MSE.
+ * The intensity of one pixel is the covariant radiative transfer integrated along the null
+ * geodesic traced backward from a static pinhole camera through the Kerr metric (the paper leaves
+ * this to ipole; here: outgoing Cartesian Kerr-Schild Hamiltonian, RK4 with h = step_frac * r).
+ *
+ * Conventions for every call:
+ *   - Every pointer named *_dev is a device pointer on the context's device; the caller owns it
+ *     and it must stay valid until the work queued on the context's stream has finished.
+ *     Pointers named *_host are ordinary host memory.  The library owns only its scratch (ray
+ *     queues, counters), allocated on first use and grown when a larger job arrives.
+ *   - Work is queued on the stream given to art_create; calls that return statistics to the host
+ *     synchronise that stream before returning.
+ *   - Images are planes x ny x nx, row-major (pixel p = j*nx + i; i runs along the screen's
+ *     horizontal axis alpha, j along the vertical axis beta, which is the projected spin axis).
+ *     Plane order is Stokes (I[,Q,U,V]) inside subring index: plane = n * stokes + s.
+ *   - Return value: ART_OK (0) or a negative ART_ERR_* code; art_strerror() names it.  No call
+ *     falls back to the CPU: without a CUDA device every compute call returns ART_ERR_CUDA.
+ */
+#ifndef ART_GB300_H
+#define ART_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ART_OK 0
+#define ART_ERR_ARG (-1)         /* invalid argument or job */
+#define ART_ERR_CUDA (-2)        /* CUDA runtime error (no device, launch failure, ...) */
+#define ART_ERR_OOM (-3)         /* device allocation of library scratch failed */
+#define ART_ERR_UNSUPPORTED (-4) /* option combination not built */
+#define ART_ERR_DEVICE (-5)      /* a kernel reported an internal inconsistency */
+
+enum { ART_EMIT_CFG0 = 0, ART_EMIT_SYNCH_DISK = 1 };
+enum { ART_FLOW_KEPLER = 0, ART_FLOW_STATIC = 1 };
+enum { ART_NORM_IBAR_INT = 0, ART_NORM_PEAK = 1 };
+enum { ART_INTERP_LINEAR = 0, ART_INTERP_NEAREST = 1 };
+enum { ART_EDGE_ONESIDED = 0, ART_EDGE_TRACE = 1 };
+enum { ART_FP64 = 0, ART_MIXED = 1, ART_FP32 = 2 };
+enum { ART_MASK_UNSET = 0, ART_MASK_TRACED = 1, ART_MASK_INTERP = 2 };
+enum { ART_RAY_ESCAPED = 0, ART_RAY_CAPTURED = 1, ART_RAY_CAP = 2, ART_RAY_NAN = 3 };
+
+/* One rendering problem: camera, spacetime, emission model and the refinement parameters of
+ * Sec. 3.2 (n0x, n0y, N, R_rel, R_abs, interpolation scheme). */
+typedef struct art_job {
+    double a;            /* dimensionless spin, |a| < 1 (M = 1 units) */
+    double r_obs;        /* camera radius [M] */
+    double incl_deg;     /* camera inclination [deg], 0 < incl < 180 */
+    double fov;          /* horizontal field of view [M]; spacing fov/(nx-1) on both axes */
+    int32_t n0x, n0y;    /* base grid, n0x >= 2, n0y >= 1 */
+    int32_t levels;      /* N >= 0 refinement levels (<= 14) */
+    double R_rel, R_abs; /* tolerances of Sec. 3.2 (strict '>' traces) */
+    int32_t abs_norm;    /* ART_NORM_IBAR_INT (paper) or ART_NORM_PEAK (max of the base image) */
+    int32_t interp;      /* ART_INTERP_LINEAR (paper default) or ART_INTERP_NEAREST */
+    int32_t edge_mode;   /* ART_EDGE_ONESIDED or ART_EDGE_TRACE (trace points lacking a stencil) */
+    int32_t emission;    /* ART_EMIT_* */
+    int32_t flow;        /* ART_FLOW_* */
+    int32_t stokes;      /* 1 (unpolarized) */
+    int32_t subrings;    /* 0, or the number of subring planes n = 0..subrings-1 */
+    int32_t precision;   /* ART_FP64, ART_MIXED (FP32 with FP64 re-trace), ART_FP32 */
+    int32_t max_steps;   /* RK4 step cap per ray */
+    int32_t fp64_nturn;  /* ART_MIXED: re-trace in FP64 rays with >= this many polar turns */
+    double step_frac;    /* RK4 step h = step_frac * r */
+    double h_min;        /* floor of h */
+    double horizon_eps;  /* stop rays at r < (1 + horizon_eps) r_+ */
+    double escape_frac;  /* stop rays at r > escape_frac * r_obs */
+    double disk_w;       /* ART_EMIT_CFG0: vertical Gaussian width as a fraction of r */
+} art_job;
+
+/* Statistics of one render (host struct, filled on return). */
+typedef struct art_stats {
+    int64_t rays_traced;        /* rays whose result is in the image */
+    int64_t rays_fp64;          /* ART_MIXED: rays re-traced in FP64 */
+    int64_t steps;              /* RK4 steps summed over all traced rays (incl. re-traces) */
+    int64_t rays_capped;        /* rays that hit max_steps */
+    int64_t rays_nan;           /* rays stopped by a non-finite state */
+    int64_t rays_per_level[16]; /* rays traced at level 0..N */
+    double norm;                /* I_bar_int (or the peak) used by the criterion */
+} art_stats;
+
+/* Per-ray diagnostics (device arrays, one entry per traced ray; nullable members). */
+typedef struct art_rayaux {
+    int32_t* status; /* ART_RAY_* */
+    int32_t* steps;  /* RK4 steps */
+    int32_t* nturn;  /* polar (theta) turning points = subring index of the last segment */
+    float* min_r;    /* closest Kerr-Schild radius reached */
+} art_rayaux;
+
+typedef struct art_ctx art_ctx;
+
+/* Create a context on CUDA device `device` that queues its work on `stream` (a cudaStream_t, or
+ * NULL for the legacy default stream).  *out receives the context.  Errors: ART_ERR_ARG (null
+ * out), ART_ERR_CUDA (no such device).  Allocates no device memory yet. */
+int art_create(art_ctx** out, int device, void* stream);
+
+/* Synchronise the stream and free the context's scratch.  Null is ignored. */
+void art_destroy(art_ctx* ctx);
+
+/* Static description of an error code. */
+const char* art_strerror(int code);
+
+/* Final image size n = 2^N (n0 - 1) + 1 (Sec. 3.2).  Errors: ART_ERR_ARG. */
+int art_image_size(const art_job* job, int32_t* nx, int32_t* ny);
+
+/* Number of planes of the image: stokes * max(subrings, 1). */
+int art_planes(const art_job* job);
+
+/* Trace the pixels pix_dev[0..n) (linear indices j*nx + i of the job's final grid) and write
+ * their planes to out_dev[q*planes + plane] (ray-major).  aux (nullable, and each member
+ * nullable) receives per-ray diagnostics.  The precision is the job's (ART_MIXED: FP32 trace
+ * then an FP64 re-trace of rays with >= fp64_nturn polar turns).  Errors: ART_ERR_ARG
+ * (bad job, n < 0, pixel index not checked on the host: an index outside [0, nx*ny) is
+ * skipped by the kernel and reported as ART_ERR_DEVICE), ART_ERR_CUDA, ART_ERR_OOM. */
+int art_trace_pixels(art_ctx* ctx, const art_job* job, const int32_t* pix_dev, int64_t n,
+                     double* out_dev, const art_rayaux* aux);
+
+/* I_bar_int (Sec. 3.2): mean of the bilinear interpolant of the sub-lattice of stride `stride`
+ * of the nx x ny plane img_dev, i.e. trapezoid weights; and the maximum of that sub-lattice.
+ * Both are returned to the host (synchronises the stream). */
+int art_ibar_int(art_ctx* ctx, const double* img_dev, int32_t nx, int32_t ny, int32_t stride,
+                 double* ibar_host, double* peak_host);
+
+/* One refinement level (Sec. 3.2, Eqs. epabs/eprel, Appendix A) on the job's final grid:
+ * every new point of `level` (1..N) reads only points of level-1 in img_dev (plane 0 decides),
+ * gets mask ART_MASK_TRACED and its index appended to queue_dev (capacity: the number of new
+ * points of the level), or receives the interpolant in every plane and ART_MASK_INTERP.
+ * `norm` is I_bar_int (or the peak).  *count_host receives the queue length (synchronises).
+ * The queue's order is unspecified.  Errors: ART_ERR_ARG, ART_ERR_CUDA. */
+int art_refine_level(art_ctx* ctx, const art_job* job, double* img_dev, uint8_t* mask_dev,
+                     int32_t level, double norm, int32_t* queue_dev, int64_t* count_host);
+
+/* The whole adaptive render (Sec. 3.2): trace the base grid, compute the normalisation, then
+ * for each level refine and trace the queue on the device (no host round trip inside).
+ * img_dev: planes x ny x nx doubles; mask_dev (nullable): ny x nx bytes (ART_MASK_*).
+ * truth_dev (nullable): if given (planes x ny x nx), "tracing" a pixel copies it from there, so
+ * the refinement logic can be run on any precomputed image.  stats_host (nullable) is filled and
+ * the stream synchronised if it is given.  Errors: ART_ERR_ARG, ART_ERR_CUDA, ART_ERR_OOM,
+ * ART_ERR_DEVICE. */
+int art_render(art_ctx* ctx, const art_job* job, const double* truth_dev, double* img_dev,
+               uint8_t* mask_dev, art_stats* stats_host);
+
+/* art_render into HOST buffers: the image and mask are rendered into context-owned device
+ * buffers and copied to img_host (planes x ny x nx doubles) and mask_host (nullable, ny x nx
+ * bytes).  Synchronises the stream. */
+int art_render_host(art_ctx* ctx, const art_job* job, double* img_host, uint8_t* mask_host,
+                    art_stats* stats_host);
+
+/* Image metrics of plane 0 (Eqs. interpdef, fluxdef, msedef): out_host[0] = interpolation
+ * fraction (mask_dev nullable -> 0), [1] = flux error with the trapezoid flux, [2] = MSE
+ * sum|I - I_hat|^2 / sum|I|^2, [3] = sum|I - I_hat|^2 / (N mean(I)^2).  Synchronises. */
+int art_metrics(art_ctx* ctx, const double* truth_dev, const double* img_dev,
+                const uint8_t* mask_dev, int32_t nx, int32_t ny, double* out_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,243 @@
+"""Thin ctypes binding of libart_gb300.so (include/art.h).
+
+Argument marshalling only: every step of the adaptive render runs in the library's CUDA
+kernels.  Device buffers are torch tensors (PyTorch supplies device memory and the stream).
+There is no CPU fallback: if the library cannot be built or loaded, or no CUDA device exists,
+these functions raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+ART_OK, ART_ERR_ARG, ART_ERR_CUDA, ART_ERR_OOM, ART_ERR_UNSUPPORTED, ART_ERR_DEVICE = (
+    0, -1, -2, -3, -4, -5)
+MASK_UNSET, MASK_TRACED, MASK_INTERP = 0, 1, 2
+RAY_ESCAPED, RAY_CAPTURED, RAY_CAP, RAY_NAN = 0, 1, 2, 3
+
+_NAMES = dict(
+    emission={"cfg0": 0, "synch_disk": 1},
+    flow={"kepler": 0, "static": 1},
+    abs_norm={"ibar_int": 0, "peak": 1},
+    interp={"linear": 0, "nearest": 1},
+    edge_mode={"onesided": 0, "trace": 1},
+    precision={"fp64": 0, "mixed": 1, "fp32": 2},
+)
+
+
+class Job(ctypes.Structure):
+    _fields_ = [
+        ("a", ctypes.c_double), ("r_obs", ctypes.c_double), ("incl_deg", ctypes.c_double),
+        ("fov", ctypes.c_double), ("n0x", ctypes.c_int32), ("n0y", ctypes.c_int32),
+        ("levels", ctypes.c_int32), ("R_rel", ctypes.c_double), ("R_abs", ctypes.c_double),
+        ("abs_norm", ctypes.c_int32), ("interp", ctypes.c_int32), ("edge_mode", ctypes.c_int32),
+        ("emission", ctypes.c_int32), ("flow", ctypes.c_int32), ("stokes", ctypes.c_int32),
+        ("subrings", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("max_steps", ctypes.c_int32), ("fp64_nturn", ctypes.c_int32),
+        ("step_frac", ctypes.c_double), ("h_min", ctypes.c_double),
+        ("horizon_eps", ctypes.c_double), ("escape_frac", ctypes.c_double),
+        ("disk_w", ctypes.c_double),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("rays_traced", ctypes.c_int64), ("rays_fp64", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("rays_capped", ctypes.c_int64),
+                ("rays_nan", ctypes.c_int64), ("rays_per_level", ctypes.c_int64 * 16),
+                ("norm", ctypes.c_double)]
+
+
+class RayAux(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_void_p), ("steps", ctypes.c_void_p),
+                ("nturn", ctypes.c_void_p), ("min_r", ctypes.c_void_p)]
+
+
+_JOB_DEFAULTS = dict(fp64_nturn=2)
+
+
+def make_job(**params) -> Job:
+    """The library's job from a parameter dict (option names are mapped to the C enums)."""
+    d = dict(_JOB_DEFAULTS)
+    d.update(params)
+    kw = {}
+    for name, _ in Job._fields_:
+        if name not in d:
+            raise KeyError(f"job parameter {name!r} missing")
+        v = d[name]
+        if name in _NAMES and isinstance(v, str):
+            v = _NAMES[name][v]
+        kw[name] = v
+    return Job(**kw)
+
+
+_lock = threading.Lock()
+_lib = None
+
+EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_planes",
+           "art_trace_pixels", "art_ibar_int", "art_refine_level", "art_render",
+           "art_render_host", "art_metrics")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Build (if needed) and load libart_gb300.so; raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            lib = ctypes.CDLL(path)
+            P = ctypes.POINTER
+            vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+            lib.art_create.argtypes = [P(vp), ctypes.c_int, vp]
+            lib.art_destroy.argtypes = [vp]
+            lib.art_destroy.restype = None
+            lib.art_strerror.argtypes = [ctypes.c_int]
+            lib.art_strerror.restype = ctypes.c_char_p
+            lib.art_image_size.argtypes = [P(Job), P(i32), P(i32)]
+            lib.art_planes.argtypes = [P(Job)]
+            lib.art_trace_pixels.argtypes = [vp, P(Job), vp, i64, vp, P(RayAux)]
+            lib.art_ibar_int.argtypes = [vp, vp, i32, i32, i32, P(ctypes.c_double),
+                                         P(ctypes.c_double)]
+            lib.art_refine_level.argtypes = [vp, P(Job), vp, vp, i32, ctypes.c_double, vp, P(i64)]
+            lib.art_render.argtypes = [vp, P(Job), vp, vp, vp, P(Stats)]
+            lib.art_render_host.argtypes = [vp, P(Job), vp, vp, P(Stats)]
+            lib.art_metrics.argtypes = [vp, vp, vp, vp, i32, i32, P(ctypes.c_double)]
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != ART_OK:
+        msg = load().art_strerror(rc).decode()
+        raise RuntimeError(f"{what} failed: {msg} ({rc})")
+
+
+def art_strerror(code: int) -> str:
+    return load().art_strerror(int(code)).decode()
+
+
+def art_image_size(job: Job):
+    nx, ny = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().art_image_size(ctypes.byref(job), ctypes.byref(nx), ctypes.byref(ny)),
+           "art_image_size")
+    return nx.value, ny.value
+
+
+def art_planes(job: Job) -> int:
+    return int(load().art_planes(ctypes.byref(job)))
+
+
+def _dptr(t):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stats_dict(st: Stats, levels: int) -> dict:
+    return dict(rays_traced=st.rays_traced, rays_fp64=st.rays_fp64, steps=st.steps,
+                rays_capped=st.rays_capped, rays_nan=st.rays_nan, norm=st.norm,
+                rays_per_level=[st.rays_per_level[k] for k in range(levels + 1)])
+
+
+class Context:
+    """An art_ctx bound to a CUDA device and a torch stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libart_gb300 needs a CUDA device (no CPU fallback)")
+        self.device = device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self._ctx = ctypes.c_void_p()
+        _check(load().art_create(ctypes.byref(self._ctx), device,
+                                 ctypes.c_void_p(self.stream.cuda_stream)), "art_create")
+
+    def close(self):
+        if self._ctx:
+            load().art_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- C-ABI calls ---------------------------------------------------------------------
+    def art_trace_pixels(self, job: Job, pix, out, aux: dict | None = None):
+        ra = None
+        if aux is not None:
+            ra = RayAux(*[ctypes.c_void_p(aux[k].data_ptr()) if aux.get(k) is not None else None
+                          for k in ("status", "steps", "nturn", "min_r")])
+        _check(load().art_trace_pixels(self._ctx, ctypes.byref(job), _dptr(pix), pix.numel(),
+                                       _dptr(out), ctypes.byref(ra) if ra else None),
+               "art_trace_pixels")
+
+    def art_ibar_int(self, img, stride: int):
+        ib, pk = ctypes.c_double(), ctypes.c_double()
+        ny, nx = img.shape[-2], img.shape[-1]
+        _check(load().art_ibar_int(self._ctx, _dptr(img), nx, ny, stride, ctypes.byref(ib),
+                                   ctypes.byref(pk)), "art_ibar_int")
+        return ib.value, pk.value
+
+    def art_refine_level(self, job: Job, img, mask, level: int, norm: float, queue) -> int:
+        n = ctypes.c_int64()
+        _check(load().art_refine_level(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask),
+                                       level, norm, _dptr(queue), ctypes.byref(n)),
+               "art_refine_level")
+        return n.value
+
+    def art_render(self, job: Job, img, mask=None, truth=None, stats: bool = True):
+        st = Stats()
+        _check(load().art_render(self._ctx, ctypes.byref(job), _dptr(truth), _dptr(img),
+                                 _dptr(mask), ctypes.byref(st) if stats else None), "art_render")
+        return _stats_dict(st, job.levels) if stats else None
+
+    def art_render_host(self, job: Job, img: np.ndarray, mask: np.ndarray | None = None):
+        st = Stats()
+        assert img.flags.c_contiguous and img.dtype == np.float64
+        mp = mask.ctypes.data_as(ctypes.c_void_p) if mask is not None else None
+        _check(load().art_render_host(self._ctx, ctypes.byref(job),
+                                      img.ctypes.data_as(ctypes.c_void_p), mp, ctypes.byref(st)),
+               "art_render_host")
+        return _stats_dict(st, job.levels)
+
+    def art_metrics(self, truth, img, mask=None) -> dict:
+        out = (ctypes.c_double * 4)()
+        ny, nx = truth.shape[-2], truth.shape[-1]
+        _check(load().art_metrics(self._ctx, _dptr(truth), _dptr(img), _dptr(mask), nx, ny, out),
+               "art_metrics")
+        return dict(IF=out[0], FE=out[1], MSE=out[2], MSE_mean=out[3])
+
+    # -- conveniences ----------------------------------------------------------------------
+    def render(self, job: Job, truth=None):
+        """Allocate the image and mask on the device and run art_render."""
+        import torch
+        nx, ny = art_image_size(job)
+        planes = art_planes(job)
+        img = torch.empty((planes, ny, nx), dtype=torch.float64, device=f"cuda:{self.device}")
+        mask = torch.empty((ny, nx), dtype=torch.uint8, device=f"cuda:{self.device}")
+        stats = self.art_render(job, img, mask, truth)
+        return img, mask, stats
+
+    def trace_pixels(self, job: Job, pix):
+        import torch
+        planes = art_planes(job)
+        out = torch.empty((pix.numel(), planes), dtype=torch.float64, device=pix.device)
+        aux = dict(status=torch.empty(pix.numel(), dtype=torch.int32, device=pix.device),
+                   steps=torch.empty(pix.numel(), dtype=torch.int32, device=pix.device),
+                   nturn=torch.empty(pix.numel(), dtype=torch.int32, device=pix.device),
+                   min_r=torch.empty(pix.numel(), dtype=torch.float32, device=pix.device))
+        self.art_trace_pixels(job, pix, out, aux)
+        return out, aux

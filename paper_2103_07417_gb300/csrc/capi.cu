@@ -1,0 +1,438 @@
+// capi.cu -- the C-ABI of include/art.h: context, job validation, scratch management and the
+// level loop of Sec. 3.2 driven entirely on the device (one stream, no host round trip between
+// levels: queue lengths live in device counters that the persistent trace kernel reads).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.cuh"
+
+using namespace art;
+
+struct art_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int occ64 = 0, occ32 = 0;
+    // scratch owned by the library
+    int32_t* queue = nullptr;
+    int32_t* reroute = nullptr;
+    int64_t queue_cap = 0;
+    unsigned long long* counters = nullptr;
+    double* norm3 = nullptr;
+    Camera* cam = nullptr;
+    double* partials = nullptr;
+    double* out6 = nullptr;
+    double* himg = nullptr;   // art_render_host buffers
+    uint8_t* hmask = nullptr;
+    int64_t hcap = 0;
+    unsigned long long* pinned = nullptr;  // host copy of the counters
+    double* pinned_d = nullptr;
+};
+
+#define CK(x)                                    \
+    do {                                         \
+        cudaError_t e_ = (x);                    \
+        if (e_ != cudaSuccess) return err_of(e_); \
+    } while (0)
+
+static int err_of(cudaError_t e)
+{
+    return e == cudaErrorMemoryAllocation ? ART_ERR_OOM : ART_ERR_CUDA;
+}
+
+extern "C" const char* art_strerror(int code)
+{
+    switch (code) {
+    case ART_OK: return "ok";
+    case ART_ERR_ARG: return "invalid argument";
+    case ART_ERR_CUDA: return "CUDA runtime error";
+    case ART_ERR_OOM: return "device allocation failed";
+    case ART_ERR_UNSUPPORTED: return "unsupported option";
+    case ART_ERR_DEVICE: return "kernel reported an inconsistency";
+    default: return "unknown error";
+    }
+}
+
+extern "C" int art_image_size(const art_job* job, int32_t* nx, int32_t* ny)
+{
+    if (!job || !nx || !ny) return ART_ERR_ARG;
+    if (job->n0x < 2 || job->n0y < 1 || job->levels < 0 || job->levels > 14) return ART_ERR_ARG;
+    int64_t x = ((int64_t)1 << job->levels) * (job->n0x - 1) + 1;
+    int64_t y = ((int64_t)1 << job->levels) * (job->n0y - 1) + 1;
+    if (x * y >= ((int64_t)1 << 31)) return ART_ERR_ARG;
+    *nx = (int32_t)x;
+    *ny = (int32_t)y;
+    return ART_OK;
+}
+
+extern "C" int art_planes(const art_job* job)
+{
+    if (!job) return ART_ERR_ARG;
+    return (job->stokes == 4 ? 4 : 1) * (job->subrings > 0 ? job->subrings : 1);
+}
+
+static double horizon(double a) { return 1.0 + sqrt(1.0 - a * a); }
+
+// Validate the job and derive the kernels' view of it.
+static int make_devjob(const art_job* job, DevJob* J)
+{
+    if (!job) return ART_ERR_ARG;
+    int32_t nx, ny;
+    if (art_image_size(job, &nx, &ny) != ART_OK) return ART_ERR_ARG;
+    if (!(fabs(job->a) < 1.0) || !(job->r_obs > 10.0) || !(job->fov > 0.0)) return ART_ERR_ARG;
+    if (!(job->incl_deg > 0.0 && job->incl_deg < 180.0)) return ART_ERR_ARG;
+    if (!(job->step_frac > 0.0 && job->step_frac <= 0.5) || !(job->h_min > 0.0)) return ART_ERR_ARG;
+    if (job->max_steps < 1 || !(job->escape_frac > 1.0) || !(job->horizon_eps >= 0.0))
+        return ART_ERR_ARG;
+    if (job->stokes != 1) return ART_ERR_UNSUPPORTED;
+    if (job->subrings < 0 || job->subrings > 4) return ART_ERR_UNSUPPORTED;
+    if (job->emission != ART_EMIT_CFG0) return ART_ERR_UNSUPPORTED;
+    if (job->flow != ART_FLOW_KEPLER && job->flow != ART_FLOW_STATIC) return ART_ERR_ARG;
+    if (job->interp != ART_INTERP_LINEAR && job->interp != ART_INTERP_NEAREST) return ART_ERR_ARG;
+    if (job->edge_mode != ART_EDGE_ONESIDED && job->edge_mode != ART_EDGE_TRACE) return ART_ERR_ARG;
+    if (job->abs_norm != ART_NORM_IBAR_INT && job->abs_norm != ART_NORM_PEAK) return ART_ERR_ARG;
+    if (job->precision < ART_FP64 || job->precision > ART_FP32) return ART_ERR_ARG;
+    if (!(job->disk_w > 0.0)) return ART_ERR_ARG;
+    J->a = job->a;
+    J->a2 = job->a * job->a;
+    J->r_obs = job->r_obs;
+    J->pix = job->fov / (double)(nx - 1);
+    J->step_frac = job->step_frac;
+    J->h_min = job->h_min;
+    J->r_in_stop = (1.0 + job->horizon_eps) * horizon(job->a);
+    J->r_out_stop = job->escape_frac * job->r_obs;
+    J->inv_2w2 = 1.0 / (2.0 * job->disk_w * job->disk_w);
+    J->R_abs = job->R_abs;
+    J->R_rel = job->R_rel;
+    J->nx = nx;
+    J->ny = ny;
+    J->levels = job->levels;
+    J->emission = job->emission;
+    J->flow = job->flow;
+    J->stokes = job->stokes;
+    J->subrings = job->subrings;
+    J->planes = art_planes(job);
+    J->max_steps = job->max_steps;
+    J->fp64_nturn = job->fp64_nturn;
+    J->interp = job->interp;
+    J->edge_mode = job->edge_mode;
+    J->abs_norm = job->abs_norm;
+    J->precision = job->precision;
+    return ART_OK;
+}
+
+extern "C" int art_create(art_ctx** out, int device, void* stream)
+{
+    if (!out) return ART_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return ART_ERR_CUDA;
+    if (cudaSetDevice(device) != cudaSuccess) return ART_ERR_CUDA;
+    art_ctx* c = new art_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        trace_occupancy(false, &c->occ64) != cudaSuccess ||
+        trace_occupancy(true, &c->occ32) != cudaSuccess) {
+        delete c;
+        return ART_ERR_CUDA;
+    }
+    if (c->occ64 < 1) c->occ64 = 1;
+    if (c->occ32 < 1) c->occ32 = 1;
+    *out = c;
+    return ART_OK;
+}
+
+extern "C" void art_destroy(art_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->queue);
+    cudaFree(c->reroute);
+    cudaFree(c->counters);
+    cudaFree(c->norm3);
+    cudaFree(c->cam);
+    cudaFree(c->partials);
+    cudaFree(c->out6);
+    cudaFree(c->himg);
+    cudaFree(c->hmask);
+    cudaFreeHost(c->pinned);
+    cudaFreeHost(c->pinned_d);
+    delete c;
+}
+
+// Fixed-size scratch (counters, camera, normalisation, metric partials, pinned mirrors).
+static int ensure_fixed(art_ctx* c)
+{
+    if (c->counters) return ART_OK;
+    CK(cudaMalloc(&c->counters, sizeof(unsigned long long) * C_COUNT));
+    CK(cudaMalloc(&c->norm3, sizeof(double) * 4));
+    CK(cudaMalloc(&c->cam, sizeof(Camera)));
+    CK(cudaMalloc(&c->partials, sizeof(double) * 6 * METRIC_BLOCKS));
+    CK(cudaMalloc(&c->out6, sizeof(double) * 8));
+    CK(cudaMallocHost(&c->pinned, sizeof(unsigned long long) * C_COUNT));
+    CK(cudaMallocHost(&c->pinned_d, sizeof(double) * 8));
+    return ART_OK;
+}
+
+// Ray queues large enough for `cap` entries (grown, never shrunk).
+static int ensure_queue(art_ctx* c, int64_t cap)
+{
+    if (cap < 1) cap = 1;
+    if (cap <= c->queue_cap) return ART_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->queue);
+    cudaFree(c->reroute);
+    c->queue = c->reroute = nullptr;
+    c->queue_cap = 0;
+    CK(cudaMalloc(&c->queue, sizeof(int32_t) * cap));
+    CK(cudaMalloc(&c->reroute, sizeof(int32_t) * cap));
+    c->queue_cap = cap;
+    return ART_OK;
+}
+
+// Largest number of rays one level can queue: the base grid or the new points of level N.
+static int64_t max_level_rays(const DevJob& J)
+{
+    int64_t n0 = (int64_t)((J.nx - 1) / (1 << J.levels) + 1) * ((J.ny - 1) / (1 << J.levels) + 1);
+    if (J.levels == 0) return n0;
+    int64_t prev = (int64_t)((J.nx - 1) / 2 + 1) * ((J.ny - 1) / 2 + 1);
+    int64_t last = (int64_t)J.nx * J.ny - prev;
+    return n0 > last ? n0 : last;
+}
+
+// Trace the rays of the queue (length in counters[count_idx]) with the job's precision.
+static int trace_queue(art_ctx* c, const DevJob& J, const unsigned long long* count, double* img,
+                       uint8_t* mask, double* out, const art_rayaux* aux)
+{
+    TraceArgs a;
+    memset(&a, 0, sizeof a);
+    a.job = J;
+    a.cam = c->cam;
+    a.queue = c->queue;
+    a.count = count;
+    a.counters = c->counters;
+    a.img = img;
+    a.mask = mask;
+    a.out = out;
+    a.npix = (int64_t)J.nx * J.ny;
+    if (aux) {
+        a.aux_status = aux->status;
+        a.aux_steps = aux->steps;
+        a.aux_nturn = aux->nturn;
+        a.aux_minr = aux->min_r;
+    }
+    const int g64 = c->num_sms * c->occ64, g32 = c->num_sms * c->occ32;
+    if (J.precision == ART_FP64) {
+        a.fetch = c->counters + C_FETCH;
+        CK(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), c->stream));
+        CK(launch_trace(a, false, g64, c->stream));
+        return ART_OK;
+    }
+    a.fetch = c->counters + C_FETCH;
+    CK(cudaMemsetAsync(c->counters + C_FETCH, 0, sizeof(unsigned long long) * 3, c->stream));
+    if (J.precision == ART_MIXED) {
+        a.reroute = c->reroute;
+        a.reroute_count = c->counters + C_REROUTE;
+    }
+    CK(launch_trace(a, true, g32, c->stream));
+    if (J.precision == ART_MIXED) {
+        TraceArgs b = a;
+        b.reroute = nullptr;
+        b.reroute_count = nullptr;
+        b.indirect = c->reroute;
+        b.count = c->counters + C_REROUTE;
+        b.fetch = c->counters + C_FETCH2;
+        CK(launch_trace(b, false, g64, c->stream));
+    }
+    return ART_OK;
+}
+
+static int read_counters(art_ctx* c)
+{
+    CK(cudaMemcpyAsync(c->pinned, c->counters, sizeof(unsigned long long) * C_COUNT,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(c->pinned_d, c->norm3, sizeof(double) * 3, cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ART_OK;
+}
+
+extern "C" int art_trace_pixels(art_ctx* c, const art_job* job, const int32_t* pix_dev, int64_t n,
+                                double* out_dev, const art_rayaux* aux)
+{
+    if (!c || (n > 0 && (!pix_dev || !out_dev)) || n < 0) return ART_ERR_ARG;
+    DevJob J;
+    int rc = make_devjob(job, &J);
+    if (rc) return rc;
+    if (n == 0) return ART_OK;
+    CK(cudaSetDevice(c->device));
+    if ((rc = ensure_fixed(c)) || (rc = ensure_queue(c, n))) return rc;
+    CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * C_COUNT, c->stream));
+    CK(cudaMemcpyAsync(c->queue, pix_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
+    unsigned long long nn = (unsigned long long)n;
+    CK(cudaMemcpyAsync(c->counters + C_QUEUE, &nn, sizeof nn, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_camera_setup(*job, c->cam, c->stream));
+    if ((rc = trace_queue(c, J, c->counters + C_QUEUE, nullptr, nullptr, out_dev, aux))) return rc;
+    if ((rc = read_counters(c))) return rc;
+    if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
+    return ART_OK;
+}
+
+extern "C" int art_ibar_int(art_ctx* c, const double* img_dev, int32_t nx, int32_t ny,
+                            int32_t stride, double* ibar_host, double* peak_host)
+{
+    if (!c || !img_dev || nx < 1 || ny < 1 || stride < 1 || (nx - 1) % stride || (ny - 1) % stride)
+        return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    int rc = ensure_fixed(c);
+    if (rc) return rc;
+    DevJob J;
+    memset(&J, 0, sizeof J);
+    J.abs_norm = ART_NORM_IBAR_INT;
+    CK(launch_norm(J, img_dev, nx, ny, stride, c->norm3, c->stream));
+    CK(cudaMemcpyAsync(c->pinned_d, c->norm3, sizeof(double) * 3, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (ibar_host) *ibar_host = c->pinned_d[1];
+    if (peak_host) *peak_host = c->pinned_d[2];
+    return ART_OK;
+}
+
+extern "C" int art_refine_level(art_ctx* c, const art_job* job, double* img_dev, uint8_t* mask_dev,
+                                int32_t level, double norm, int32_t* queue_dev, int64_t* count_host)
+{
+    if (!c || !img_dev || !queue_dev) return ART_ERR_ARG;
+    DevJob J;
+    int rc = make_devjob(job, &J);
+    if (rc) return rc;
+    if (level < 1 || level > J.levels) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if ((rc = ensure_fixed(c))) return rc;
+    CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * C_COUNT, c->stream));
+    c->pinned_d[3] = norm;
+    CK(cudaMemcpyAsync(c->norm3, &c->pinned_d[3], sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(launch_refine(J, level, c->norm3, img_dev, mask_dev, queue_dev, c->counters + C_QUEUE,
+                     c->stream));
+    if ((rc = read_counters(c))) return rc;
+    if (count_host) *count_host = (int64_t)c->pinned[C_QUEUE];
+    return ART_OK;
+}
+
+extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_dev, double* img_dev,
+                          uint8_t* mask_dev, art_stats* stats)
+{
+    if (!c || !img_dev) return ART_ERR_ARG;
+    DevJob J;
+    int rc = make_devjob(job, &J);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    if ((rc = ensure_fixed(c)) || (rc = ensure_queue(c, max_level_rays(J)))) return rc;
+    cudaStream_t st = c->stream;
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    const int64_t cap = max_level_rays(J);
+    CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * C_COUNT, st));
+    if (!truth_dev) CK(launch_camera_setup(*job, c->cam, st));
+    CK(launch_enqueue_base(J, c->queue, c->counters, st));
+    for (int level = 0; level <= J.levels; ++level) {
+        if (level > 0) {
+            CK(cudaMemsetAsync(c->counters + C_QUEUE, 0, sizeof(unsigned long long), st));
+            CK(launch_refine(J, level, c->norm3, img_dev, mask_dev, c->queue, c->counters + C_QUEUE,
+                             st));
+            CK(cudaMemcpyAsync(c->counters + C_LEVEL0 + level, c->counters + C_QUEUE,
+                               sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+        }
+        if (truth_dev) {
+            CK(launch_gather_truth(J, c->queue, c->counters + C_QUEUE, truth_dev, img_dev, mask_dev,
+                                   cap, st));
+        } else {
+            if ((rc = trace_queue(c, J, c->counters + C_QUEUE, img_dev, mask_dev, nullptr, nullptr)))
+                return rc;
+        }
+        if (level == 0) CK(launch_norm(J, img_dev, J.nx, J.ny, 1 << J.levels, c->norm3, st));
+    }
+    (void)npix;
+    if (stats) {
+        if ((rc = read_counters(c))) return rc;
+        memset(stats, 0, sizeof *stats);
+        for (int k = 0; k <= J.levels && k < 16; ++k) {
+            stats->rays_per_level[k] = (int64_t)c->pinned[C_LEVEL0 + k];
+            stats->rays_traced += stats->rays_per_level[k];
+        }
+        stats->rays_fp64 = (int64_t)c->pinned[C_FP64];
+        stats->steps = (int64_t)c->pinned[C_STEPS];
+        stats->rays_capped = (int64_t)c->pinned[C_CAPPED];
+        stats->rays_nan = (int64_t)c->pinned[C_NAN];
+        stats->norm = c->pinned_d[0];
+        if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
+    }
+    return ART_OK;
+}
+
+extern "C" int art_render_host(art_ctx* c, const art_job* job, double* img_host, uint8_t* mask_host,
+                               art_stats* stats)
+{
+    if (!c || !img_host) return ART_ERR_ARG;
+    DevJob J;
+    int rc = make_devjob(job, &J);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    if (npix * J.planes > c->hcap) {
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->himg);
+        cudaFree(c->hmask);
+        c->himg = nullptr;
+        c->hmask = nullptr;
+        c->hcap = 0;
+        CK(cudaMalloc(&c->himg, sizeof(double) * npix * J.planes));
+        CK(cudaMalloc(&c->hmask, npix));
+        c->hcap = npix * J.planes;
+    }
+    if ((rc = art_render(c, job, nullptr, c->himg, c->hmask, nullptr))) return rc;
+    CK(cudaMemcpyAsync(img_host, c->himg, sizeof(double) * npix * J.planes, cudaMemcpyDeviceToHost,
+                       c->stream));
+    if (mask_host) CK(cudaMemcpyAsync(mask_host, c->hmask, npix, cudaMemcpyDeviceToHost, c->stream));
+    if (stats) {
+        if ((rc = read_counters(c))) return rc;
+        memset(stats, 0, sizeof *stats);
+        for (int k = 0; k <= J.levels && k < 16; ++k) {
+            stats->rays_per_level[k] = (int64_t)c->pinned[C_LEVEL0 + k];
+            stats->rays_traced += stats->rays_per_level[k];
+        }
+        stats->rays_fp64 = (int64_t)c->pinned[C_FP64];
+        stats->steps = (int64_t)c->pinned[C_STEPS];
+        stats->rays_capped = (int64_t)c->pinned[C_CAPPED];
+        stats->rays_nan = (int64_t)c->pinned[C_NAN];
+        stats->norm = c->pinned_d[0];
+    } else {
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return ART_OK;
+}
+
+extern "C" int art_metrics(art_ctx* c, const double* truth_dev, const double* img_dev,
+                           const uint8_t* mask_dev, int32_t nx, int32_t ny, double* out_host)
+{
+    if (!c || !truth_dev || !img_dev || !out_host || nx < 1 || ny < 1) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    int rc = ensure_fixed(c);
+    if (rc) return rc;
+    CK(launch_metrics(truth_dev, img_dev, mask_dev, nx, ny, c->partials, METRIC_BLOCKS, c->out6,
+                      c->stream));
+    double h[6];
+    CK(cudaMemcpyAsync(c->pinned_d, c->out6, sizeof(double) * 6, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    memcpy(h, c->pinned_d, sizeof h);
+    const double N = (double)nx * ny;
+    const double mean = h[5] / N;
+    out_host[0] = h[0] / N;
+    out_host[1] = fabs(h[1] - h[2]) / fabs(h[1]);
+    out_host[2] = h[3] / h[4];
+    out_host[3] = h[3] / (N * mean * mean);
+    return ART_OK;
+}

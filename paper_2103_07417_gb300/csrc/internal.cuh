@@ -1,0 +1,68 @@
+// internal.cuh -- declarations shared by the library's translation units (not part of the C-ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/art.h"
+#include "kerr.cuh"
+
+namespace art {
+
+// Device counters of one context (one array of unsigned long long in device memory).
+enum Counter {
+    C_QUEUE = 0,     // length of the ray queue of the current level
+    C_FETCH = 1,     // next queue slot to trace (persistent-kernel work counter)
+    C_REROUTE = 2,   // length of the FP64 re-trace queue (mixed precision)
+    C_FETCH2 = 3,    // work counter of the re-trace pass
+    C_STEPS = 4,     // RK4 steps, summed over rays
+    C_CAPPED = 5,    // rays that hit max_steps
+    C_NAN = 6,       // rays stopped by a non-finite state
+    C_BADIDX = 7,    // queue entries outside the image (skipped)
+    C_FP64 = 8,      // rays traced by the FP64 kernel in mixed mode
+    C_LEVEL0 = 16,   // C_LEVEL0 + k: rays of level k (16 slots)
+    C_COUNT = 32
+};
+
+struct TraceArgs {
+    DevJob job;
+    const Camera* cam;
+    const int32_t* queue;           // pixel indices
+    const int32_t* indirect;        // nullable: slot -> queue position (re-trace pass)
+    const unsigned long long* count;// number of slots to trace
+    unsigned long long* fetch;      // work counter, zeroed before the launch
+    unsigned long long* counters;   // the context's counter array
+    double* img;                    // image mode: planes x npix (nullable)
+    uint8_t* mask;                  // image mode: nullable
+    double* out;                    // ray mode: [queue position][plane] (nullable)
+    int32_t* reroute;               // mixed FP32 pass: queue positions to re-trace in FP64
+    unsigned long long* reroute_count;
+    int32_t* aux_status;
+    int32_t* aux_steps;
+    int32_t* aux_nturn;
+    float* aux_minr;
+    int64_t npix;
+};
+
+// trace.cu
+cudaError_t launch_camera_setup(const art_job& job, Camera* cam, cudaStream_t st);
+cudaError_t launch_trace(const TraceArgs& a, bool fp32, int grid, cudaStream_t st);
+cudaError_t trace_occupancy(bool fp32, int* blocks_per_sm);
+constexpr int TRACE_BLOCK = 128;
+
+// refine.cu
+cudaError_t launch_enqueue_base(const DevJob& J, int32_t* queue, unsigned long long* counters,
+                                cudaStream_t st);
+cudaError_t launch_gather_truth(const DevJob& J, const int32_t* queue,
+                                const unsigned long long* count, const double* truth,
+                                double* img, uint8_t* mask, int64_t cap, cudaStream_t st);
+cudaError_t launch_norm(const DevJob& J, const double* img, int nx, int ny, int stride,
+                        double* norm3, cudaStream_t st);
+cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double* img,
+                          uint8_t* mask, int32_t* queue, unsigned long long* count,
+                          cudaStream_t st);
+cudaError_t launch_metrics(const double* truth, const double* img, const uint8_t* mask, int nx,
+                           int ny, double* partials, int nblocks, double* out6, cudaStream_t st);
+constexpr int METRIC_BLOCKS = 304;
+
+}  // namespace art

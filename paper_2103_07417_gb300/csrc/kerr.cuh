@@ -1,0 +1,145 @@
+// kerr.cuh -- device geometry of the ray tracer: Kerr metric in outgoing Cartesian Kerr-Schild
+// coordinates, Hamilton's equations for null geodesics, the static camera and the emission models.
+//
+// Metric (Kerr & Schild 1965, outgoing form): g^{mu nu} = eta^{mu nu} - f l^mu l^nu with
+//   f = 2 r^3 / (r^4 + a^2 z^2),  l_mu = (1, -L_x, -L_y, -L_z),
+//   L = ((r x - a y)/(r^2 + a^2), (r y + a x)/(r^2 + a^2), z/r),
+//   r^4 - (x^2 + y^2 + z^2 - a^2) r^2 - a^2 z^2 = 0,   x + i y = (r - i a) sin(th) e^{i phi}.
+// Rays are traced backward from the camera (past-directed); these coordinates keep them regular
+// through the past horizon.  H = 1/2 g^{mu nu} k_mu k_nu does not depend on t, so k_t is exact
+// and t is not integrated; the state is (x, y, z, k_x, k_y, k_z).
+//
+// The partial derivatives below are derived by hand from H (the CPU oracle takes them by complex
+// steps instead).  With Lam = L.k, lk = l^mu k_mu = -k_t - Lam and
+//   dr/dx_i = (x r, y r, z (r^2 + a^2)/r) / Sigma,   Sigma = r^2 + a^2 z^2 / r^2,
+//   df/dx_i = B dr/dx_i - delta_iz 2 f a^2 z / Q,     B = (f/r)(3 - 4 r^4/Q),  Q = r^4 + a^2 z^2,
+//   dLam/dx_i = A dr/dx_i + T_i,  A = (x k_x + y k_y - 2 r (L_x k_x + L_y k_y))/(r^2+a^2) - k_z z/r^2,
+//   T = ((r k_x + a k_y)/(r^2+a^2), (r k_y - a k_x)/(r^2+a^2), k_z/r),
+// Hamilton's equations read
+//   dx_i/dlambda = k_i + f lk L_i,
+//   dk_i/dlambda = (B lk^2/2 - f lk A) dr/dx_i - f lk T_i - delta_iz f a^2 z lk^2 / Q.
+#pragma once
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define ART_HD __host__ __device__ __forceinline__
+#else
+#define ART_HD inline
+#endif
+
+namespace art {
+
+// Job parameters as the kernels see them (POD, passed by value).
+struct DevJob {
+    double a, a2, r_obs, pix, step_frac, h_min, r_in_stop, r_out_stop, inv_2w2;
+    double R_abs, R_rel;
+    int32_t nx, ny, levels, emission, flow, stokes, subrings, planes, max_steps, fp64_nturn;
+    int32_t interp, edge_mode, abs_norm, precision;
+};
+
+// Static camera: position and the covariant (lowered) tetrad E0 (observer), E1 (outward),
+// E2 (screen up), E3 (screen right), so that k_mu = -E0 + s (-E1 + (al/r_obs) E3 + (be/r_obs) E2).
+struct Camera {
+    double x0[3];
+    double E[4][4];  // E[a][mu]
+};
+
+template <class R>
+struct RayState {
+    R x, y, z, kx, ky, kz;
+};
+
+template <class R>
+ART_HD R ks_radius(R x, R y, R z, R a2)
+{
+    R b = x * x + y * y + z * z - a2;
+    R r2 = R(0.5) * (b + sqrt(b * b + R(4) * a2 * z * z));
+    return sqrt(r2);
+}
+
+// Hamilton's equations (see the header comment); returns r of the evaluation point.
+template <class R>
+ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
+{
+    const R x = s.x, y = s.y, z = s.z, kx = s.kx, ky = s.ky, kz = s.kz;
+    R z2 = z * z;
+    R a2z2 = a2 * z2;
+    R b = x * x + y * y + z2 - a2;
+    R r2 = R(0.5) * (b + sqrt(b * b + R(4) * a2z2));
+    R r = sqrt(r2);
+    R ir = R(1) / r;
+    R ir2 = ir * ir;
+    R r4 = r2 * r2;
+    R iQ = R(1) / (r4 + a2z2);
+    R f = R(2) * r2 * r * iQ;
+    R ira2 = R(1) / (r2 + a2);
+    R Lx = (r * x - a * y) * ira2;
+    R Ly = (r * y + a * x) * ira2;
+    R Lz = z * ir;
+    R Lkxy = Lx * kx + Ly * ky;
+    R lk = -kt - (Lkxy + Lz * kz);
+    R iSig = R(1) / (r2 + a2z2 * ir2);
+    R rs = r * iSig;
+    R drx = x * rs, dry = y * rs, drz = z * (r2 + a2) * ir * iSig;
+    R B = f * ir * (R(3) - R(4) * r4 * iQ);
+    R A = (x * kx + y * ky - R(2) * r * Lkxy) * ira2 - kz * z * ir2;
+    R flk = f * lk;
+    R C = R(0.5) * B * lk * lk - flk * A;
+    R Tx = (r * kx + a * ky) * ira2;
+    R Ty = (r * ky - a * kx) * ira2;
+    R Tz = kz * ir;
+    d.kx = C * drx - flk * Tx;
+    d.ky = C * dry - flk * Ty;
+    d.kz = C * drz - flk * Tz - flk * lk * a2 * z * iQ;
+    d.x = kx + flk * Lx;
+    d.y = ky + flk * Ly;
+    d.z = kz + flk * Lz;
+    return r;
+}
+
+// Invariant emissivity J = j_nu / nu^2 of the analytic model j = r^-2 exp(-z^2 / (2 (w r)^2))
+// (z = r cos(theta)) for a fluid that is Keplerian (Omega = 1/(r^{3/2} + a) at Boyer-Lindquist
+// (r, theta), zero where no timelike such orbit exists) or static; nu = k_mu u^mu.
+template <class R>
+ART_HD R emission_cfg0(const RayState<R>& s, R r, R kt, const DevJob& J)
+{
+    if (r < R(J.r_in_stop)) return R(0);
+    R ct = s.z / r;
+    R ct2 = ct * ct;
+    R r2 = r * r;
+    R jnu = exp(-ct2 * R(J.inv_2w2)) / r2;
+    R a = R(J.a), a2 = R(J.a2);
+    R nu;
+    if (J.flow == 0) {
+        R st2 = R(1) - ct2;
+        R iSig = R(1) / (r2 + a2 * ct2);
+        R gtt = -(R(1) - R(2) * r * iSig);
+        R gtp = -R(2) * a * r * st2 * iSig;
+        R gpp = (r2 + a2 + R(2) * a2 * r * st2 * iSig) * st2;
+        R Om = R(1) / (r * sqrt(r) + a);
+        R nrm = -(gtt + R(2) * Om * gtp + Om * Om * gpp);
+        if (!(nrm > R(0))) return R(0);
+        R ut = R(1) / sqrt(nrm);
+        nu = ut * (kt + Om * (s.x * s.ky - s.y * s.kx));
+    } else {
+        R z2 = s.z * s.z;
+        R f = R(2) * r2 * r / (r2 * r2 + a2 * z2);
+        if (!(f < R(1))) return R(0);
+        nu = kt / sqrt(R(1) - f);
+    }
+    if (!(nu > R(0))) return R(0);
+    return jnu / (nu * nu);
+}
+
+// Sign of d(theta)/d(lambda) from k_theta sin(theta) = (x k_x + y k_y) z/r - (r - z^2/r) k_z,
+// 0 inside a dead band of 1e-9 r (radial rays).  Sign flips count polar turning points, which
+// separate the passes of a ray through the equatorial plane (the subring index n).
+template <class R>
+ART_HD int polar_sign(const RayState<R>& s, R r)
+{
+    R q = (s.x * s.kx + s.y * s.ky) * s.z / r - (r - s.z * s.z / r) * s.kz;
+    R tol = R(1e-9) * r;
+    return q > tol ? 1 : (q < -tol ? -1 : 0);
+}
+
+}  // namespace art

@@ -1,0 +1,349 @@
+// refine.cu -- the adaptive-refinement kernels of Sec. 3.2: base-grid queue, I_bar_int, the fused
+// criterion + interpolation + ray-queue compaction of one level, the truth gather (refinement
+// run on a precomputed image) and the image metrics of Sec. 4.1.
+//
+// Layout: the image is the final nodal grid (planes x ny x nx doubles).  Level k points are the
+// sub-lattice of stride s = 2^(N-k); a point is new at level k when (i/s, j/s) are not both even,
+// and it reads only level-(k-1) points (stride 2s).  So no per-level copies exist and the new
+// points of a level never read each other: one kernel per level decides, interpolates and
+// compacts the rays to trace into the queue.  All of it is HBM/L2-bound stencil work.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace art {
+
+// --------------------------------------------------------------------------------------------
+// level 0
+// --------------------------------------------------------------------------------------------
+
+__global__ void enqueue_base_kernel(DevJob J, int32_t* queue, unsigned long long* counters)
+{
+    const int S0 = 1 << J.levels;
+    const int n0x = (J.nx - 1) / S0 + 1, n0y = (J.ny - 1) / S0 + 1;
+    const int64_t n = (int64_t)n0x * n0y;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        int ii = (int)(q % n0x), jj = (int)(q / n0x);
+        queue[q] = jj * S0 * J.nx + ii * S0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        counters[C_QUEUE] = (unsigned long long)n;
+        counters[C_LEVEL0] = (unsigned long long)n;
+    }
+}
+
+cudaError_t launch_enqueue_base(const DevJob& J, int32_t* queue, unsigned long long* counters,
+                                cudaStream_t st)
+{
+    const int S0 = 1 << J.levels;
+    int64_t n = (int64_t)((J.nx - 1) / S0 + 1) * ((J.ny - 1) / S0 + 1);
+    int grid = (int)((n + 255) / 256);
+    if (grid < 1) grid = 1;
+    if (grid > 4096) grid = 4096;
+    enqueue_base_kernel<<<grid, 256, 0, st>>>(J, queue, counters);
+    return cudaGetLastError();
+}
+
+// Refinement on a precomputed image: "tracing" a queued pixel copies it from `truth`.
+__global__ void gather_truth_kernel(int planes, int64_t npix, const int32_t* queue,
+                                    const unsigned long long* count, const double* truth,
+                                    double* img, uint8_t* mask)
+{
+    const unsigned long long n = *count;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        int32_t p = queue[q];
+        if (p < 0 || p >= npix) continue;
+        for (int c = 0; c < planes; ++c) img[c * npix + p] = truth[c * npix + p];
+        if (mask) mask[p] = ART_MASK_TRACED;
+    }
+}
+
+cudaError_t launch_gather_truth(const DevJob& J, const int32_t* queue,
+                                const unsigned long long* count, const double* truth,
+                                double* img, uint8_t* mask, int64_t cap, cudaStream_t st)
+{
+    int grid = (int)((cap + 255) / 256);
+    if (grid < 1) grid = 1;
+    if (grid > 8192) grid = 8192;
+    gather_truth_kernel<<<grid, 256, 0, st>>>(J.planes, (int64_t)J.nx * J.ny, queue, count, truth,
+                                              img, mask);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------------------------
+// I_bar_int: mean of the bilinear interpolant of the base samples = trapezoid weights
+// (1/2 on the edges of each axis); one block, fixed reduction order (deterministic).
+// norm3[0] = the criterion's normalisation (I_bar_int or the peak), [1] = I_bar_int, [2] = peak.
+// --------------------------------------------------------------------------------------------
+
+constexpr int NORM_THREADS = 1024;
+
+__global__ void __launch_bounds__(NORM_THREADS)
+    norm_kernel(const double* img, int nx, int ny, int stride, int abs_norm, double* norm3)
+{
+    const int n0x = (nx - 1) / stride + 1, n0y = (ny - 1) / stride + 1;
+    const int64_t n = (int64_t)n0x * n0y;
+    double s = 0.0, w = 0.0, mx = -INFINITY;
+    for (int64_t q = threadIdx.x; q < n; q += NORM_THREADS) {
+        int ii = (int)(q % n0x), jj = (int)(q / n0x);
+        double wx = (n0x > 1 && (ii == 0 || ii == n0x - 1)) ? 0.5 : 1.0;
+        double wy = (n0y > 1 && (jj == 0 || jj == n0y - 1)) ? 0.5 : 1.0;
+        double v = img[(int64_t)jj * stride * nx + (int64_t)ii * stride];
+        s += wx * wy * v;
+        w += wx * wy;
+        mx = fmax(mx, v);
+    }
+    __shared__ double ss[NORM_THREADS], sw[NORM_THREADS], sm[NORM_THREADS];
+    ss[threadIdx.x] = s;
+    sw[threadIdx.x] = w;
+    sm[threadIdx.x] = mx;
+    __syncthreads();
+    for (int h = NORM_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            ss[threadIdx.x] += ss[threadIdx.x + h];
+            sw[threadIdx.x] += sw[threadIdx.x + h];
+            sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double ibar = ss[0] / sw[0];
+        norm3[1] = ibar;
+        norm3[2] = sm[0];
+        norm3[0] = abs_norm == ART_NORM_PEAK ? sm[0] : ibar;
+    }
+}
+
+cudaError_t launch_norm(const DevJob& J, const double* img, int nx, int ny, int stride,
+                        double* norm3, cudaStream_t st)
+{
+    norm_kernel<<<1, NORM_THREADS, 0, st>>>(img, nx, ny, stride, J.abs_norm, norm3);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------------------------
+// criterion + interpolation + compaction of one level
+// --------------------------------------------------------------------------------------------
+
+// Sum of the two central second differences along one line through the point (inner
+// neighbours at -/+ d, outer at -/+ 3d): I(-3) - I(-1) - I(+1) + I(+3); where one outer point is
+// outside the image, twice the one second difference available; where none is, ok = false.
+__device__ __forceinline__ double second_diff_sum(const double* img, int nx, int ny, int i, int j,
+                                                  int di, int dj, double Im, double Ip, bool& ok)
+{
+    const int iom = i - 3 * di, jom = j - 3 * dj, iop = i + 3 * di, jop = j + 3 * dj;
+    const bool has_m = iom >= 0 && iom < nx && jom >= 0 && jom < ny;
+    const bool has_p = iop >= 0 && iop < nx && jop >= 0 && jop < ny;
+    if (has_m && has_p) {
+        double Om = __ldg(img + (int64_t)jom * nx + iom), Op = __ldg(img + (int64_t)jop * nx + iop);
+        return ((Om - Im) - Ip) + Op;
+    }
+    if (has_m) return 2.0 * ((__ldg(img + (int64_t)jom * nx + iom) - 2.0 * Im) + Ip);
+    if (has_p) return 2.0 * ((__ldg(img + (int64_t)jop * nx + iop) - 2.0 * Ip) + Im);
+    ok = false;
+    return 0.0;
+}
+
+// Estimated errors of Eqs. (epabs), (eprel), Appendix A, for the new point (i, j) of the level
+// with stride s.  Linear: eps_abs = |S_out - S_in| / (16 norm) [centre] or / (8 norm) [edge
+// midpoints, the 1-D form], eps_rel = |S_out - S_in| / (4 |S_in|), interpolant S_in/4 or S_in/2.
+// Nearest: sqrt(((I4-I1)/2)^2 + ((I3-I2)/2)^2) [centre] or |I2-I1|/2 [midpoints] over norm and
+// over |I1|, interpolant I1.  Decision: trace iff eps_abs > R_abs && eps_rel > R_rel (strict);
+// NaN traces; a line without any outer point gives +inf.
+__device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i, int j, int s,
+                                      double norm, int cat, double& w1, double& w2, int64_t& p1,
+                                      int64_t& p2, int64_t& p3, int64_t& p4)
+{
+    const int nx = J.nx, ny = J.ny;
+    bool ok = true;
+    double num, sin_, i1, den;
+    if (cat == 4) {
+        p1 = (int64_t)(j - s) * nx + (i - s);  // point 1
+        p4 = (int64_t)(j + s) * nx + (i + s);  // point 4 (opposite 1)
+        p2 = (int64_t)(j + s) * nx + (i - s);  // point 2
+        p3 = (int64_t)(j - s) * nx + (i + s);  // point 3 (opposite 2)
+        double I1 = __ldg(img + p1), I4 = __ldg(img + p4), I2 = __ldg(img + p2), I3 = __ldg(img + p3);
+        sin_ = ((I1 + I2) + I3) + I4;
+        i1 = I1;
+        if (J.interp == ART_INTERP_NEAREST) {
+            double d41 = I4 - I1, d32 = I3 - I2;
+            num = sqrt(__dadd_rn(__dmul_rn(__dmul_rn(0.25, d41), d41), __dmul_rn(__dmul_rn(0.25, d32), d32)));
+            w1 = 1.0;
+            w2 = 0.0;
+            den = fabs(i1);
+        } else {
+            double dA = second_diff_sum(img, nx, ny, i, j, s, s, I1, I4, ok);
+            double dB = second_diff_sum(img, nx, ny, i, j, s, -s, I2, I3, ok);
+            num = fabs(dA + dB) / 16.0;
+            w1 = 0.25;
+            w2 = 0.25;
+            den = fabs(sin_) / 4.0;
+        }
+    } else {
+        const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
+        p1 = (int64_t)(j - dj) * nx + (i - di);
+        p2 = (int64_t)(j + dj) * nx + (i + di);
+        p3 = p4 = -1;
+        double I1 = __ldg(img + p1), I2 = __ldg(img + p2);
+        sin_ = I1 + I2;
+        i1 = I1;
+        if (J.interp == ART_INTERP_NEAREST) {
+            num = fabs(I2 - I1) / 2.0;
+            w1 = 1.0;
+            w2 = 0.0;
+            den = fabs(i1);
+        } else {
+            double d = second_diff_sum(img, nx, ny, i, j, di, dj, I1, I2, ok);
+            num = fabs(d) / 8.0;
+            w1 = 0.5;
+            w2 = 0.5;
+            den = fabs(sin_) / 2.0;
+        }
+    }
+    double ea, er;
+    if (!ok && J.interp == ART_INTERP_LINEAR) {
+        ea = er = INFINITY;
+    } else {
+        ea = num / norm;
+        er = (den == 0.0) ? (num == 0.0 ? 0.0 : INFINITY) : num / den;
+    }
+    bool tr = (ea > J.R_abs) && (er > J.R_rel);
+    if (isnan(ea) || isnan(er) || isnan(sin_) || isnan(i1)) tr = true;
+    if (J.edge_mode == ART_EDGE_TRACE) {
+        const int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
+        if (i - 3 * di < 0 || i + 3 * di >= nx || j - 3 * dj < 0 || j + 3 * dj >= ny) tr = true;
+    }
+    return tr;
+}
+
+__global__ void __launch_bounds__(256)
+    refine_kernel(DevJob J, int level, const double* __restrict__ norm_ptr, double* img,
+                  uint8_t* mask, int32_t* queue, unsigned long long* qcount)
+{
+    const int s = 1 << (J.levels - level);
+    const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
+    const int64_t npts = (int64_t)nkx * nky;
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    const double norm = *norm_ptr;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npts;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        bool trace = false;
+        int32_t pix = 0;
+        if (t < npts) {
+            const int ii = (int)(t % nkx), jj = (int)(t / nkx);
+            const int oi = ii & 1, oj = jj & 1;
+            if (oi | oj) {
+                const int i = ii * s, j = jj * s;
+                const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+                double w1, w2;
+                int64_t p1, p2, p3, p4;
+                trace = decide(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4);
+                pix = j * J.nx + i;
+                if (trace) {
+                    if (mask) mask[pix] = ART_MASK_TRACED;
+                } else {
+                    for (int c = 0; c < J.planes; ++c) {
+                        const double* pl = img + c * npix;
+                        double v;
+                        if (cat == 4) {
+                            if (w2 == 0.0)
+                                v = __ldg(pl + p1);
+                            else
+                                v = 0.25 * (((__ldg(pl + p1) + __ldg(pl + p2)) + __ldg(pl + p3)) +
+                                            __ldg(pl + p4));
+                        } else {
+                            v = (w2 == 0.0) ? __ldg(pl + p1) : 0.5 * (__ldg(pl + p1) + __ldg(pl + p2));
+                        }
+                        img[c * npix + pix] = v;
+                    }
+                    if (mask) mask[pix] = ART_MASK_INTERP;
+                }
+            }
+        }
+        // warp-aggregated append to the ray queue (ballot -> popc -> one atomic per warp)
+        const unsigned b = __ballot_sync(0xffffffffu, trace);
+        if (b) {
+            unsigned long long w = 0;
+            if (lane == 0) w = atomicAdd(qcount, (unsigned long long)__popc(b));
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (trace) queue[w + __popc(b & ((1u << lane) - 1u))] = pix;
+        }
+    }
+}
+
+cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double* img,
+                          uint8_t* mask, int32_t* queue, unsigned long long* count,
+                          cudaStream_t st)
+{
+    const int s = 1 << (J.levels - level);
+    const int64_t npts = (int64_t)((J.nx - 1) / s + 1) * ((J.ny - 1) / s + 1);
+    int64_t grid = (npts + 255) / 256;
+    if (grid < 1) grid = 1;
+    if (grid > 152 * 64) grid = 152 * 64;
+    refine_kernel<<<(int)grid, 256, 0, st>>>(J, level, norm, img, mask, queue, count);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------------------------
+// metrics (Eqs. interpdef, fluxdef, msedef): per-block partial sums, then one block combines them
+// in a fixed order.  Sums: [0] interpolated points, [1] F (trapezoid), [2] F_hat, [3] sum dI^2,
+// [4] sum I^2, [5] sum I.
+// --------------------------------------------------------------------------------------------
+
+constexpr int MET_THREADS = 256;
+
+__global__ void __launch_bounds__(MET_THREADS)
+    metrics_partial_kernel(const double* truth, const double* img, const uint8_t* mask, int nx,
+                           int ny, double* partials)
+{
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const int64_t n = (int64_t)nx * ny;
+    for (int64_t p = blockIdx.x * (int64_t)MET_THREADS + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * MET_THREADS) {
+        int i = (int)(p % nx), j = (int)(p / nx);
+        double wx = (nx > 1 && (i == 0 || i == nx - 1)) ? 0.5 : 1.0;
+        double wy = (ny > 1 && (j == 0 || j == ny - 1)) ? 0.5 : 1.0;
+        double t = truth[p], v = img[p], d = t - v;
+        if (mask && mask[p] == ART_MASK_INTERP) acc[0] += 1.0;
+        acc[1] += wx * wy * t;
+        acc[2] += wx * wy * v;
+        acc[3] += d * d;
+        acc[4] += t * t;
+        acc[5] += t;
+    }
+    __shared__ double sh[6][MET_THREADS];
+    for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int h = MET_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int c = 0; c < 6; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) partials[blockIdx.x * 6 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void metrics_final_kernel(const double* partials, int nblocks, double* out6)
+{
+    if (threadIdx.x < 6) {
+        double s = 0.0;
+        for (int b = 0; b < nblocks; ++b) s += partials[b * 6 + threadIdx.x];
+        out6[threadIdx.x] = s;
+    }
+}
+
+cudaError_t launch_metrics(const double* truth, const double* img, const uint8_t* mask, int nx,
+                           int ny, double* partials, int nblocks, double* out6, cudaStream_t st)
+{
+    metrics_partial_kernel<<<nblocks, MET_THREADS, 0, st>>>(truth, img, mask, nx, ny, partials);
+    metrics_final_kernel<<<1, 32, 0, st>>>(partials, nblocks, out6);
+    return cudaGetLastError();
+}
+
+}  // namespace art

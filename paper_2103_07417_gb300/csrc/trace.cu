@@ -1,0 +1,308 @@
+// trace.cu -- the fused ray-tracing kernel: camera ray set-up, RK4 null geodesic integration in
+// outgoing Kerr-Schild coordinates and the covariant transfer step, with the whole ray state in
+// registers.  One persistent grid (SM count x resident blocks) drains a device-side queue; each
+// lane refills itself with the next ray as soon as its own ray terminates, so rays of very
+// different path length (photon-ring rays take many more steps, Sec. 4.2) do not idle a warp.
+//
+// Transfer per RK4 step of length h (the intensity function I(x) of Sec. 3): the invariant
+// emissivity J = j_nu/nu^2 is evaluated at the step's end point and averaged with the start
+// point (trapezoid); absorption A likewise; the segment adds T J h (1 - e^{-A h})/(A h) and
+// multiplies the transmission T by e^{-A h} (rays are traced from the camera outward, so T is
+// the transmission between the camera and the segment).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace art {
+
+// --------------------------------------------------------------------------------------------
+// camera
+// --------------------------------------------------------------------------------------------
+
+__device__ static void ks_metric_cov(double a, const double x[3], double g[4][4])
+{
+    double r = ks_radius<double>(x[0], x[1], x[2], a * a);
+    double r2 = r * r;
+    double f = 2.0 * r2 * r / (r2 * r2 + a * a * x[2] * x[2]);
+    double l[4] = {1.0, -(r * x[0] - a * x[1]) / (r2 + a * a), -(r * x[1] + a * x[0]) / (r2 + a * a),
+                   -x[2] / r};
+    for (int m = 0; m < 4; ++m)
+        for (int n = 0; n < 4; ++n) g[m][n] = (m == n ? (m == 0 ? -1.0 : 1.0) : 0.0) + f * l[m] * l[n];
+}
+
+// Static observer at (r_obs, theta_o, phi = 0): x = sqrt(r^2 + a^2) sin(th), y = 0, z = r cos(th).
+// Orthonormal tetrad by Gram-Schmidt in g from u = d_t / sqrt(-g_tt) and the coordinate vectors
+// (sin th, 0, cos th) [outward], (-cos th, 0, sin th) [screen up, toward the spin axis],
+// (0, 1, 0) [screen right]; stored lowered.
+__global__ void camera_setup_kernel(double a, double r_obs, double incl_deg, Camera* cam)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double th = incl_deg * 3.14159265358979323846 / 180.0;
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    double x0[3] = {sqrt(r_obs * r_obs + a * a) * sn, 0.0, r_obs * cs};
+    double g[4][4];
+    ks_metric_cov(a, x0, g);
+    double e[4][4] = {{1.0 / sqrt(-g[0][0]), 0, 0, 0},
+                      {0, sn, 0, cs},
+                      {0, -cs, 0, sn},
+                      {0, 0, 1, 0}};
+    auto dot = [&](const double* u, const double* v) {
+        double s = 0;
+        for (int m = 0; m < 4; ++m)
+            for (int n = 0; n < 4; ++n) s += g[m][n] * u[m] * v[n];
+        return s;
+    };
+    for (int q = 1; q < 4; ++q) {
+        double w[4], v[4];
+        for (int m = 0; m < 4; ++m) v[m] = w[m] = e[q][m];
+        double pu = dot(e[0], v);
+        for (int m = 0; m < 4; ++m) w[m] += pu * e[0][m];
+        for (int p = 1; p < q; ++p) {
+            double pe = dot(e[p], v);
+            for (int m = 0; m < 4; ++m) w[m] -= pe * e[p][m];
+        }
+        double nn = sqrt(dot(w, w));
+        for (int m = 0; m < 4; ++m) e[q][m] = w[m] / nn;
+    }
+    for (int m = 0; m < 3; ++m) cam->x0[m] = x0[m];
+    for (int q = 0; q < 4; ++q)
+        for (int m = 0; m < 4; ++m) {
+            double s = 0;
+            for (int n = 0; n < 4; ++n) s += g[m][n] * e[q][n];
+            cam->E[q][m] = s;
+        }
+}
+
+cudaError_t launch_camera_setup(const art_job& job, Camera* cam, cudaStream_t st)
+{
+    camera_setup_kernel<<<1, 32, 0, st>>>(job.a, job.r_obs, job.incl_deg, cam);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------------------------
+// tracing
+// --------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned long long warp_fetch(unsigned long long* counter)
+{
+    unsigned m = __activemask();
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+
+template <class R>
+struct Tracer {
+    RayState<R> s;
+    R kt, r, J0, A0, I, T;
+    R acc[4];     // subring planes (unpolarized)
+    float min_r;
+    int steps, nturn, tsign, status;
+    int32_t pix;
+    int64_t slot;  // queue position
+};
+
+template <class R>
+__device__ __forceinline__ R phi1(R x)
+{
+    return x > R(1e-8) ? -expm1(-x) / x : R(1) - R(0.5) * x;
+}
+
+template <class R>
+__device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Camera& cam,
+                                         int32_t pix)
+{
+    int i = pix % J.nx, j = pix / J.nx;
+    double al = (i - 0.5 * (J.nx - 1)) * J.pix;
+    double be = (j - 0.5 * (J.ny - 1)) * J.pix;
+    double ro = J.r_obs;
+    double sc = 1.0 / sqrt(1.0 + (al * al + be * be) / (ro * ro));
+    double k[4];
+    for (int m = 0; m < 4; ++m)
+        k[m] = -cam.E[0][m] + sc * (-cam.E[1][m] + (al / ro) * cam.E[3][m] + (be / ro) * cam.E[2][m]);
+    t.s.x = R(cam.x0[0]);
+    t.s.y = R(cam.x0[1]);
+    t.s.z = R(cam.x0[2]);
+    t.kt = R(k[0]);
+    t.s.kx = R(k[1]);
+    t.s.ky = R(k[2]);
+    t.s.kz = R(k[3]);
+    R a2 = R(J.a2);
+    t.r = ks_radius<R>(t.s.x, t.s.y, t.s.z, a2);
+    t.J0 = J.emission == ART_EMIT_CFG0 ? emission_cfg0<R>(t.s, t.r, t.kt, J) : R(0);
+    t.A0 = R(0);
+    t.I = R(0);
+    t.T = R(1);
+    for (int p = 0; p < 4; ++p) t.acc[p] = R(0);
+    t.min_r = float(t.r);
+    t.steps = 0;
+    t.nturn = 0;
+    t.tsign = polar_sign<R>(t.s, t.r);
+    t.status = ART_RAY_CAP;
+    t.pix = pix;
+}
+
+// One RK4 step plus the transfer segment; returns true when the ray has terminated.
+template <class R>
+__device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
+{
+    const R a = R(J.a), a2 = R(J.a2);
+    R h = R(J.step_frac) * t.r;
+    if (h < R(J.h_min)) h = R(J.h_min);
+    const R hh = R(0.5) * h;
+    RayState<R> k1, k2, k3, k4, y;
+    geodesic_rhs<R>(t.s, t.kt, a, a2, k1);
+    y.x = t.s.x + hh * k1.x; y.y = t.s.y + hh * k1.y; y.z = t.s.z + hh * k1.z;
+    y.kx = t.s.kx + hh * k1.kx; y.ky = t.s.ky + hh * k1.ky; y.kz = t.s.kz + hh * k1.kz;
+    geodesic_rhs<R>(y, t.kt, a, a2, k2);
+    y.x = t.s.x + hh * k2.x; y.y = t.s.y + hh * k2.y; y.z = t.s.z + hh * k2.z;
+    y.kx = t.s.kx + hh * k2.kx; y.ky = t.s.ky + hh * k2.ky; y.kz = t.s.kz + hh * k2.kz;
+    geodesic_rhs<R>(y, t.kt, a, a2, k3);
+    y.x = t.s.x + h * k3.x; y.y = t.s.y + h * k3.y; y.z = t.s.z + h * k3.z;
+    y.kx = t.s.kx + h * k3.kx; y.ky = t.s.ky + h * k3.ky; y.kz = t.s.kz + h * k3.kz;
+    geodesic_rhs<R>(y, t.kt, a, a2, k4);
+    const R h6 = h / R(6);
+    t.s.x += h6 * (k1.x + R(2) * k2.x + R(2) * k3.x + k4.x);
+    t.s.y += h6 * (k1.y + R(2) * k2.y + R(2) * k3.y + k4.y);
+    t.s.z += h6 * (k1.z + R(2) * k2.z + R(2) * k3.z + k4.z);
+    t.s.kx += h6 * (k1.kx + R(2) * k2.kx + R(2) * k3.kx + k4.kx);
+    t.s.ky += h6 * (k1.ky + R(2) * k2.ky + R(2) * k3.ky + k4.ky);
+    t.s.kz += h6 * (k1.kz + R(2) * k2.kz + R(2) * k3.kz + k4.kz);
+    ++t.steps;
+    if (!(isfinite(t.s.x) && isfinite(t.s.y) && isfinite(t.s.z) && isfinite(t.s.kx) &&
+          isfinite(t.s.ky) && isfinite(t.s.kz))) {
+        t.status = ART_RAY_NAN;
+        return true;
+    }
+    R rn = ks_radius<R>(t.s.x, t.s.y, t.s.z, a2);
+    R J1 = J.emission == ART_EMIT_CFG0 ? emission_cfg0<R>(t.s, rn, t.kt, J) : R(0);
+    R A1 = R(0);
+    int seg = t.nturn;
+    int sg = polar_sign<R>(t.s, rn);
+    if (sg != 0) {
+        if (t.tsign != 0 && sg != t.tsign) ++t.nturn;
+        t.tsign = sg;
+    }
+    R Jb = R(0.5) * (t.J0 + J1), Ab = R(0.5) * (t.A0 + A1);
+    R dtau = Ab * h;
+    R dI = t.T * Jb * h * phi1<R>(dtau);
+    if (J.subrings > 0) {
+        int p = seg < J.subrings ? seg : J.subrings - 1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (q == p) t.acc[q] += dI;
+    } else {
+        t.I += dI;
+    }
+    if (Ab != R(0)) t.T *= exp(-dtau);
+    t.J0 = J1;
+    t.A0 = A1;
+    t.r = rn;
+    if (float(rn) < t.min_r) t.min_r = float(rn);
+    if (rn < R(J.r_in_stop)) { t.status = ART_RAY_CAPTURED; return true; }
+    if (rn > R(J.r_out_stop)) { t.status = ART_RAY_ESCAPED; return true; }
+    if (t.steps >= J.max_steps) { t.status = ART_RAY_CAP; return true; }
+    return false;
+}
+
+template <class R>
+__global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
+{
+    __shared__ Camera cam_s;
+    {
+        const double* src = reinterpret_cast<const double*>(A.cam);
+        double* dst = reinterpret_cast<double*>(&cam_s);
+        for (int q = threadIdx.x; q < (int)(sizeof(Camera) / sizeof(double)); q += blockDim.x)
+            dst[q] = src[q];
+    }
+    __syncthreads();
+    const DevJob& J = A.job;
+    const unsigned long long n = *A.count;
+    const bool mixed32 = (A.reroute != nullptr);
+    Tracer<R> t;
+    bool active = false;
+    auto fetch_next = [&]() {
+        while (true) {
+            unsigned long long q = warp_fetch(A.fetch);
+            if (q >= n) return false;
+            int64_t slot = A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
+            int32_t pix = A.queue[slot];
+            if (pix < 0 || (int64_t)pix >= A.npix) {
+                atomicAdd(A.counters + C_BADIDX, 1ull);
+                continue;
+            }
+            ray_init<R>(t, J, cam_s, pix);
+            t.slot = slot;
+            return true;
+        }
+    };
+    active = fetch_next();
+    while (__any_sync(0xffffffffu, active)) {
+        if (active) {
+            if (ray_step<R>(t, J)) {
+                atomicAdd(A.counters + C_STEPS, (unsigned long long)t.steps);
+                bool rer = mixed32 && (t.nturn >= J.fp64_nturn || t.status == ART_RAY_NAN ||
+                                       t.status == ART_RAY_CAP);
+                if (rer) {
+                    unsigned long long w = atomicAdd(A.reroute_count, 1ull);
+                    A.reroute[w] = (int32_t)t.slot;
+                } else {
+                    if (t.status == ART_RAY_CAP) atomicAdd(A.counters + C_CAPPED, 1ull);
+                    if (t.status == ART_RAY_NAN) atomicAdd(A.counters + C_NAN, 1ull);
+                    if (sizeof(R) == 8 && J.precision == ART_MIXED)
+                        atomicAdd(A.counters + C_FP64, 1ull);
+                    const int np = J.planes;
+                    if (A.img) {
+                        if (J.subrings > 0) {
+                            for (int p = 0; p < np && p < 4; ++p)
+                                A.img[(int64_t)p * A.npix + t.pix] = double(t.acc[p]);
+                        } else {
+                            A.img[t.pix] = double(t.I);
+                        }
+                        if (A.mask) A.mask[t.pix] = ART_MASK_TRACED;
+                    }
+                    if (A.out) {
+                        if (J.subrings > 0) {
+                            for (int p = 0; p < np && p < 4; ++p)
+                                A.out[t.slot * np + p] = double(t.acc[p]);
+                        } else {
+                            A.out[t.slot * np] = double(t.I);
+                        }
+                    }
+                    if (A.aux_status) A.aux_status[t.slot] = t.status;
+                    if (A.aux_steps) A.aux_steps[t.slot] = t.steps;
+                    if (A.aux_nturn) A.aux_nturn[t.slot] = t.nturn;
+                    if (A.aux_minr) A.aux_minr[t.slot] = t.min_r;
+                }
+                active = fetch_next();
+            }
+        }
+    }
+}
+
+cudaError_t launch_trace(const TraceArgs& a, bool fp32, int grid, cudaStream_t st)
+{
+    if (fp32)
+        trace_kernel<float><<<grid, TRACE_BLOCK, 0, st>>>(a);
+    else
+        trace_kernel<double><<<grid, TRACE_BLOCK, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t trace_occupancy(bool fp32, int* blocks_per_sm)
+{
+    if (fp32)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<float>,
+                                                             TRACE_BLOCK, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double>,
+                                                         TRACE_BLOCK, 0);
+}
+
+}  // namespace art
