@@ -1,0 +1,305 @@
+#!/usr/bin/env python
+"""Benchmark of the adaptive black-hole ray tracer on GB300: rays/s of one adaptive render.
+
+One step = one whole adaptive render of the workload (trace the base grid, I_bar_int, then per
+level the criterion + interpolation + compaction kernel and the trace of the queued rays), on
+inputs already resident (the job's parameters; no input arrays exist).  The L2 is flushed before
+every step by writing a 512 MB buffer outside the CUDA-event-timed region.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+Under torchrun with N > 1 every rank renders its own image (replicas: no collective on the data
+path); the time is the maximum over ranks and `value` counts the rays of all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2103_07417_gb300 import workloads as W  # noqa: E402
+
+# Algorithmic FLOPs per RK4 step of the trace kernel, counting +, -, *, /, sqrt, rsqrt and exp
+# as one each (an FMA counts 2): 4 Hamiltonian right-hand sides of 97 (388), the RK4 stage and
+# update arithmetic for 6 variables (81), the new point's radius (15), the Keplerian emissivity
+# (44), the polar-turn test (11) and the transfer segment (11); the FP32 pass of the mixed path
+# adds the swept-angle accumulation (28).
+FLOPS_PER_STEP = {"trace_fp64": 550, "trace_fp32": 578}
+# Peaks for "alu"-bound kernels: FP32 = 152 SMs x 128 lanes x 2 flops x 2.07 GHz; FP64 = the
+# GB300's nominal dense FP64 rate.
+PEAK_TFLOPS = {"trace_fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "trace_fp64": 1.25}
+METRIC = "rays/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cfg1_analytic", choices=sorted(W.BENCH_WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--single", action="store_true",
+                    help="one warm-up and one render, nothing else (for profiler captures)")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-i", str(self.device), "-lms", "100"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(params: dict, sample_note: str):
+    import oracle as O
+    job = O.make_job(**params)
+    t0 = time.perf_counter()
+    img, mask, st = O.render(job, None)
+    dt = time.perf_counter() - t0
+    return {"value": st["rays_traced"] / dt, "unit": "rays/s", "cores": O.get_threads(),
+            "kind": "oracle", "sample": sample_note, "seconds": dt,
+            "rays": int(st["rays_traced"]), "steps_per_s": st["steps"] / dt}
+
+
+def run_reference(args, params, desc):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    job = O.make_job(**params)
+    for _ in range(args.warmup):
+        O.render(job, None)
+    times, rays, steps = [], 0, 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        _, _, st = O.render(job, None)
+        times.append(time.perf_counter() - t0)
+        rays, steps = st["rays_traced"], st["steps"]
+    total = sum(times)
+    value = rays * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "name": args.workload},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": O.get_threads(),
+                             "kind": "oracle", "sample": "one full adaptive render per step"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "geodesic_steps_per_s": steps * args.steps / total}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    desc, fn = W.BENCH_WORKLOADS[args.workload]
+    params = fn(precision=args.precision) if args.workload != "cfg0" else fn(
+        precision=args.precision)
+    if args.impl == "reference":
+        return run_reference(args, params, desc)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2103_07417_gb300 import art
+    ctx = art.Context(local)
+    stream = ctx.stream
+    job = art.make_job(**params)
+    nx, ny = art.art_image_size(job)
+    planes = art.art_planes(job)
+    img = torch.empty((planes, ny, nx), dtype=torch.float64, device=dev)
+    mask = torch.empty((ny, nx), dtype=torch.uint8, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    stats = None
+    if args.single:
+        ctx.art_render(job, img, mask, stats=True)
+        st = ctx.art_render(job, img, mask, stats=True)
+        print(json.dumps({"single": args.workload, "precision": args.precision, **st}))
+        ctx.close()
+        return
+    for _ in range(max(args.warmup, 1)):
+        stats = ctx.art_render(job, img, mask, stats=True)
+    rays = stats["rays_traced"]
+    steps_per_render = stats["steps"]
+
+    def timed(k, precision_job):
+        evs = []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.art_render(precision_job, img, mask, stats=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / 1000.0
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_dev = timed(args.steps, job)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = rays * args.steps * world / t_dev
+    clocks = clk.summary()
+
+    # per-kernel timing of one render with CUDA events on the library's stream
+    ctx.art_profile(True)
+    ctx.art_render(job, img, mask, stats=False)
+    recs = ctx.art_profile_read()
+    ctx.art_profile(False)
+    by_kind = {}
+    for r in recs:
+        d = by_kind.setdefault(r["kind"], {"launches": 0, "ms": 0.0, "steps": 0})
+        d["launches"] += 1
+        d["ms"] += r["ms"]
+        d["steps"] += r["steps"]
+    dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
+    total_ms = sum(v["ms"] for v in by_kind.values())
+    roofline = None
+    if dom in FLOPS_PER_STEP:
+        d = by_kind[dom]
+        achieved = d["steps"] * FLOPS_PER_STEP[dom] / (d["ms"] / 1000.0) / 1e12
+        peak = PEAK_TFLOPS[dom]
+        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
+                                    if dom == "trace_fp32" else "nominal GB300 dense FP64"),
+                    "launches": d["launches"], "steps": d["steps"],
+                    "share_of_step": d["ms"] / total_ms}
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                   "share": round(v["ms"] / total_ms, 4)} for k, v in by_kind.items()}
+
+    # plain FP64 path on the same workload, for comparison
+    paths = {}
+    if args.precision != "fp64":
+        job64 = art.make_job(**{**params, "precision": "fp64"})
+        st64 = ctx.art_render(job64, img, mask, stats=True)
+        k64 = max(3, args.steps // 5)
+        t64 = timed(k64, job64)
+        paths["fp64"] = {"rays_per_s": st64["rays_traced"] * k64 / t64,
+                         "geodesic_steps_per_s": st64["steps"] * k64 / t64,
+                         "ms_per_step": 1000 * t64 / k64}
+        ctx.art_render(job, img, mask, stats=False)
+    paths[args.precision] = {"rays_per_s": value / world,
+                             "geodesic_steps_per_s": steps_per_render * args.steps / t_dev,
+                             "ms_per_step": 1000 * t_dev / args.steps,
+                             "rays_fp64": stats["rays_fp64"]}
+
+    # end to end through the public C-ABI with host buffers (D2H of image + mask inside)
+    import numpy as np
+    himg = torch.empty((planes, ny, nx), dtype=torch.float64).pin_memory().numpy()
+    hmask = torch.empty((ny, nx), dtype=torch.uint8).pin_memory().numpy()
+    ctx.art_render_host(job, himg, hmask)
+    ke = max(3, args.steps // 3)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        ctx.art_render_host(job, himg, hmask)
+    te = time.perf_counter() - t0
+    e2e = {"value": rays * ke / te, "unit": "rays/s",
+           "h2d_bytes_per_step": int(ctypes_sizeof_job()),
+           "d2h_bytes_per_step": int(himg.nbytes + hmask.nbytes)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(params, "one full adaptive render of the same workload by the FP64 "
+                                   "oracle (OpenMP over rays, all host cores)")
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
+                "data": "synthetic",
+                "config": {"workload": desc, "name": args.workload, "image": f"{nx}x{ny}",
+                           "precision": args.precision, "rays_per_step": rays,
+                           "l2": "flushed (512 MB write) before every step, outside the timed "
+                                 "region", "parallelism": f"replicas x{world}"},
+                "geodesic_steps_per_s": steps_per_render * args.steps * world / t_dev,
+                "paths": paths, "roofline": roofline, "kernels": kernels,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": int(stats["kernel_launches"]) * args.steps}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def ctypes_sizeof_job():
+    import ctypes
+
+    from paper_2103_07417_gb300 import art
+    return ctypes.sizeof(art.Job)
+
+
+if __name__ == "__main__":
+    main()

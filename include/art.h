@@ -73,7 +73,10 @@ typedef struct art_job {
     int32_t subrings;    /* 0, or the number of subring planes n = 0..subrings-1 */
     int32_t precision;   /* ART_FP64, ART_MIXED (FP32 with FP64 re-trace), ART_FP32 */
     int32_t max_steps;   /* RK4 step cap per ray */
-    int32_t fp64_nturn;  /* ART_MIXED: re-trace in FP64 rays with >= this many polar turns */
+    double fp64_sweep;   /* ART_MIXED: re-trace in FP64 the rays whose position vector swept at
+                          * least this angle [rad] about the hole (3 pi: a full loop of
+                          * deflection beyond a straight pass), i.e. the near-critical rays
+                          * whose errors the photon-orbit instability amplifies */
     double step_frac;    /* RK4 step h = step_frac * r */
     double h_min;        /* floor of h */
     double horizon_eps;  /* stop rays at r < (1 + horizon_eps) r_+ */
@@ -90,7 +93,18 @@ typedef struct art_stats {
     int64_t rays_nan;           /* rays stopped by a non-finite state */
     int64_t rays_per_level[16]; /* rays traced at level 0..N */
     double norm;                /* I_bar_int (or the peak) used by the criterion */
+    int64_t kernel_launches;    /* CUDA kernels this call launched */
 } art_stats;
+
+/* One kernel launch timed by the profiler (art_profile). */
+enum { ART_K_TRACE_FP64 = 0, ART_K_TRACE_FP32 = 1, ART_K_REFINE = 2, ART_K_OTHER = 3 };
+typedef struct art_launch_record {
+    int32_t kind;   /* ART_K_* */
+    int32_t level;  /* refinement level of the launch (-1 outside a render) */
+    float ms;       /* duration between CUDA events recorded around the launch on its stream */
+    int64_t steps;  /* trace kernels: RK4 steps executed by this launch */
+    int64_t items;  /* trace: rays in its queue; refine: lattice points of the level */
+} art_launch_record;
 
 /* Per-ray diagnostics (device arrays, one entry per traced ray; nullable members). */
 typedef struct art_rayaux {
@@ -122,7 +136,7 @@ int art_planes(const art_job* job);
 /* Trace the pixels pix_dev[0..n) (linear indices j*nx + i of the job's final grid) and write
  * their planes to out_dev[q*planes + plane] (ray-major).  aux (nullable, and each member
  * nullable) receives per-ray diagnostics.  The precision is the job's (ART_MIXED: FP32 trace
- * then an FP64 re-trace of rays with >= fp64_nturn polar turns).  Errors: ART_ERR_ARG
+ * then an FP64 re-trace of the rays that swept >= fp64_sweep).  Errors: ART_ERR_ARG
  * (bad job, n < 0, pixel index not checked on the host: an index outside [0, nx*ny) is
  * skipped by the kernel and reported as ART_ERR_DEVICE), ART_ERR_CUDA, ART_ERR_OOM. */
 int art_trace_pixels(art_ctx* ctx, const art_job* job, const int32_t* pix_dev, int64_t n,
@@ -158,6 +172,15 @@ int art_render(art_ctx* ctx, const art_job* job, const double* truth_dev, double
  * bytes).  Synchronises the stream. */
 int art_render_host(art_ctx* ctx, const art_job* job, double* img_host, uint8_t* mask_host,
                     art_stats* stats_host);
+
+/* Per-launch profiling.  With enable != 0 every kernel launch of the following calls is
+ * bracketed by CUDA events on the context's stream (and the trace kernels' step counters are
+ * snapshotted), for at most 256 launches; enable == 0 stops recording.  art_profile_read
+ * synchronises the stream and copies up to `cap` records of the launches since the last
+ * art_profile(ctx, 1) into recs_host, *n receiving their number.  Errors: ART_ERR_ARG,
+ * ART_ERR_CUDA, ART_ERR_OOM. */
+int art_profile(art_ctx* ctx, int enable);
+int art_profile_read(art_ctx* ctx, art_launch_record* recs_host, int cap, int* n);
 
 /* Image metrics of plane 0 (Eqs. interpdef, fluxdef, msedef): out_host[0] = interpolation
  * fraction (mask_dev nullable -> 0), [1] = flux error with the trapezoid flux, [2] = MSE

@@ -38,7 +38,7 @@ class Job(ctypes.Structure):
         ("abs_norm", ctypes.c_int32), ("interp", ctypes.c_int32), ("edge_mode", ctypes.c_int32),
         ("emission", ctypes.c_int32), ("flow", ctypes.c_int32), ("stokes", ctypes.c_int32),
         ("subrings", ctypes.c_int32), ("precision", ctypes.c_int32),
-        ("max_steps", ctypes.c_int32), ("fp64_nturn", ctypes.c_int32),
+        ("max_steps", ctypes.c_int32), ("fp64_sweep", ctypes.c_double),
         ("step_frac", ctypes.c_double), ("h_min", ctypes.c_double),
         ("horizon_eps", ctypes.c_double), ("escape_frac", ctypes.c_double),
         ("disk_w", ctypes.c_double),
@@ -49,7 +49,15 @@ class Stats(ctypes.Structure):
     _fields_ = [("rays_traced", ctypes.c_int64), ("rays_fp64", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("rays_capped", ctypes.c_int64),
                 ("rays_nan", ctypes.c_int64), ("rays_per_level", ctypes.c_int64 * 16),
-                ("norm", ctypes.c_double)]
+                ("norm", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+
+
+class LaunchRecord(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("ms", ctypes.c_float),
+                ("steps", ctypes.c_int64), ("items", ctypes.c_int64)]
+
+
+KERNEL_KINDS = {0: "trace_fp64", 1: "trace_fp32", 2: "refine", 3: "other"}
 
 
 class RayAux(ctypes.Structure):
@@ -57,7 +65,7 @@ class RayAux(ctypes.Structure):
                 ("nturn", ctypes.c_void_p), ("min_r", ctypes.c_void_p)]
 
 
-_JOB_DEFAULTS = dict(fp64_nturn=2)
+_JOB_DEFAULTS = dict(fp64_sweep=3.0 * 3.141592653589793)
 
 
 def make_job(**params) -> Job:
@@ -80,7 +88,7 @@ _lib = None
 
 EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_planes",
            "art_trace_pixels", "art_ibar_int", "art_refine_level", "art_render",
-           "art_render_host", "art_metrics")
+           "art_render_host", "art_metrics", "art_profile", "art_profile_read")
 
 
 def lib_path() -> str:
@@ -110,6 +118,8 @@ def load():
             lib.art_render.argtypes = [vp, P(Job), vp, vp, vp, P(Stats)]
             lib.art_render_host.argtypes = [vp, P(Job), vp, vp, P(Stats)]
             lib.art_metrics.argtypes = [vp, vp, vp, vp, i32, i32, P(ctypes.c_double)]
+            lib.art_profile.argtypes = [vp, ctypes.c_int]
+            lib.art_profile_read.argtypes = [vp, P(LaunchRecord), ctypes.c_int, P(ctypes.c_int)]
             _lib = lib
     return _lib
 
@@ -147,6 +157,7 @@ def _dptr(t):
 def _stats_dict(st: Stats, levels: int) -> dict:
     return dict(rays_traced=st.rays_traced, rays_fp64=st.rays_fp64, steps=st.steps,
                 rays_capped=st.rays_capped, rays_nan=st.rays_nan, norm=st.norm,
+                kernel_launches=st.kernel_launches,
                 rays_per_level=[st.rays_per_level[k] for k in range(levels + 1)])
 
 
@@ -219,6 +230,16 @@ class Context:
         _check(load().art_metrics(self._ctx, _dptr(truth), _dptr(img), _dptr(mask), nx, ny, out),
                "art_metrics")
         return dict(IF=out[0], FE=out[1], MSE=out[2], MSE_mean=out[3])
+
+    def art_profile(self, enable: bool):
+        _check(load().art_profile(self._ctx, int(bool(enable))), "art_profile")
+
+    def art_profile_read(self, cap: int = 256):
+        recs = (LaunchRecord * cap)()
+        n = ctypes.c_int()
+        _check(load().art_profile_read(self._ctx, recs, cap, ctypes.byref(n)), "art_profile_read")
+        return [dict(kind=KERNEL_KINDS.get(r.kind, "other"), level=r.level, ms=r.ms, steps=r.steps,
+                     items=r.items) for r in recs[: n.value]]
 
     # -- conveniences ----------------------------------------------------------------------
     def render(self, job: Job, truth=None):

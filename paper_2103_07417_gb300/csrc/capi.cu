@@ -31,7 +31,41 @@ struct art_ctx {
     int64_t hcap = 0;
     unsigned long long* pinned = nullptr;  // host copy of the counters
     double* pinned_d = nullptr;
+    int64_t launches = 0;                  // kernels launched by the current call
+    // profiler
+    static const int PROF_MAX = 256;
+    bool prof_on = false;
+    int prof_n = 0;
+    cudaEvent_t ev[2 * PROF_MAX] = {};
+    art_launch_record rec[PROF_MAX];
+    unsigned long long* prof_steps = nullptr;  // device snapshots of C_STEPS after trace launches
+    int prof_level = -1;
 };
+
+// Profiler brackets: prof_begin before a launch, prof_end after it.
+static int prof_begin(art_ctx* c)
+{
+    ++c->launches;
+    if (!c->prof_on || c->prof_n >= art_ctx::PROF_MAX) return -1;
+    int k = c->prof_n;
+    if (cudaEventRecord(c->ev[2 * k], c->stream) != cudaSuccess) return -1;
+    return k;
+}
+
+static void prof_end(art_ctx* c, int k, int kind, int64_t items)
+{
+    if (k < 0) return;
+    cudaEventRecord(c->ev[2 * k + 1], c->stream);
+    c->rec[k].kind = kind;
+    c->rec[k].level = c->prof_level;
+    c->rec[k].ms = 0.f;
+    c->rec[k].steps = 0;
+    c->rec[k].items = items;
+    if (kind == ART_K_TRACE_FP64 || kind == ART_K_TRACE_FP32)
+        cudaMemcpyAsync(c->prof_steps + k, c->counters + C_STEPS, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, c->stream);
+    c->prof_n = k + 1;
+}
 
 #define CK(x)                                    \
     do {                                         \
@@ -97,6 +131,7 @@ static int make_devjob(const art_job* job, DevJob* J)
     if (job->abs_norm != ART_NORM_IBAR_INT && job->abs_norm != ART_NORM_PEAK) return ART_ERR_ARG;
     if (job->precision < ART_FP64 || job->precision > ART_FP32) return ART_ERR_ARG;
     if (!(job->disk_w > 0.0)) return ART_ERR_ARG;
+    if (!(job->fp64_sweep > 0.0)) return ART_ERR_ARG;
     J->a = job->a;
     J->a2 = job->a * job->a;
     J->r_obs = job->r_obs;
@@ -117,7 +152,7 @@ static int make_devjob(const art_job* job, DevJob* J)
     J->subrings = job->subrings;
     J->planes = art_planes(job);
     J->max_steps = job->max_steps;
-    J->fp64_nturn = job->fp64_nturn;
+    J->fp64_sweep = job->fp64_sweep;
     J->interp = job->interp;
     J->edge_mode = job->edge_mode;
     J->abs_norm = job->abs_norm;
@@ -163,6 +198,9 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFree(c->hmask);
     cudaFreeHost(c->pinned);
     cudaFreeHost(c->pinned_d);
+    cudaFree(c->prof_steps);
+    for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
 }
 
@@ -228,10 +266,13 @@ static int trace_queue(art_ctx* c, const DevJob& J, const unsigned long long* co
         a.aux_minr = aux->min_r;
     }
     const int g64 = c->num_sms * c->occ64, g32 = c->num_sms * c->occ32;
+    int k;
     if (J.precision == ART_FP64) {
         a.fetch = c->counters + C_FETCH;
         CK(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), c->stream));
+        k = prof_begin(c);
         CK(launch_trace(a, false, g64, c->stream));
+        prof_end(c, k, ART_K_TRACE_FP64, -1);
         return ART_OK;
     }
     a.fetch = c->counters + C_FETCH;
@@ -240,7 +281,9 @@ static int trace_queue(art_ctx* c, const DevJob& J, const unsigned long long* co
         a.reroute = c->reroute;
         a.reroute_count = c->counters + C_REROUTE;
     }
+    k = prof_begin(c);
     CK(launch_trace(a, true, g32, c->stream));
+    prof_end(c, k, ART_K_TRACE_FP32, -1);
     if (J.precision == ART_MIXED) {
         TraceArgs b = a;
         b.reroute = nullptr;
@@ -248,7 +291,9 @@ static int trace_queue(art_ctx* c, const DevJob& J, const unsigned long long* co
         b.indirect = c->reroute;
         b.count = c->counters + C_REROUTE;
         b.fetch = c->counters + C_FETCH2;
+        k = prof_begin(c);
         CK(launch_trace(b, false, g64, c->stream));
+        prof_end(c, k, ART_K_TRACE_FP64, -1);
     }
     return ART_OK;
 }
@@ -277,7 +322,10 @@ extern "C" int art_trace_pixels(art_ctx* c, const art_job* job, const int32_t* p
     CK(cudaMemcpyAsync(c->queue, pix_dev, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, c->stream));
     unsigned long long nn = (unsigned long long)n;
     CK(cudaMemcpyAsync(c->counters + C_QUEUE, &nn, sizeof nn, cudaMemcpyHostToDevice, c->stream));
+    c->launches = 0;
+    int k = prof_begin(c);
     CK(launch_camera_setup(*job, c->cam, c->stream));
+    prof_end(c, k, ART_K_OTHER, 1);
     if ((rc = trace_queue(c, J, c->counters + C_QUEUE, nullptr, nullptr, out_dev, aux))) return rc;
     if ((rc = read_counters(c))) return rc;
     if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
@@ -335,26 +383,46 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
     cudaStream_t st = c->stream;
     const int64_t npix = (int64_t)J.nx * J.ny;
     const int64_t cap = max_level_rays(J);
+    c->launches = 0;
     CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * C_COUNT, st));
-    if (!truth_dev) CK(launch_camera_setup(*job, c->cam, st));
+    int k;
+    c->prof_level = -1;
+    if (!truth_dev) {
+        k = prof_begin(c);
+        CK(launch_camera_setup(*job, c->cam, st));
+        prof_end(c, k, ART_K_OTHER, 1);
+    }
+    k = prof_begin(c);
     CK(launch_enqueue_base(J, c->queue, c->counters, st));
+    prof_end(c, k, ART_K_OTHER, -1);
     for (int level = 0; level <= J.levels; ++level) {
+        c->prof_level = level;
         if (level > 0) {
+            const int s = 1 << (J.levels - level);
             CK(cudaMemsetAsync(c->counters + C_QUEUE, 0, sizeof(unsigned long long), st));
+            k = prof_begin(c);
             CK(launch_refine(J, level, c->norm3, img_dev, mask_dev, c->queue, c->counters + C_QUEUE,
                              st));
+            prof_end(c, k, ART_K_REFINE, (int64_t)((J.nx - 1) / s + 1) * ((J.ny - 1) / s + 1));
             CK(cudaMemcpyAsync(c->counters + C_LEVEL0 + level, c->counters + C_QUEUE,
                                sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
         }
         if (truth_dev) {
+            k = prof_begin(c);
             CK(launch_gather_truth(J, c->queue, c->counters + C_QUEUE, truth_dev, img_dev, mask_dev,
                                    cap, st));
+            prof_end(c, k, ART_K_OTHER, -1);
         } else {
             if ((rc = trace_queue(c, J, c->counters + C_QUEUE, img_dev, mask_dev, nullptr, nullptr)))
                 return rc;
         }
-        if (level == 0) CK(launch_norm(J, img_dev, J.nx, J.ny, 1 << J.levels, c->norm3, st));
+        if (level == 0) {
+            k = prof_begin(c);
+            CK(launch_norm(J, img_dev, J.nx, J.ny, 1 << J.levels, c->norm3, st));
+            prof_end(c, k, ART_K_OTHER, -1);
+        }
     }
+    c->prof_level = -1;
     (void)npix;
     if (stats) {
         if ((rc = read_counters(c))) return rc;
@@ -368,6 +436,7 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
         stats->rays_capped = (int64_t)c->pinned[C_CAPPED];
         stats->rays_nan = (int64_t)c->pinned[C_NAN];
         stats->norm = c->pinned_d[0];
+        stats->kernel_launches = c->launches;
         if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
     }
     return ART_OK;
@@ -409,6 +478,7 @@ extern "C" int art_render_host(art_ctx* c, const art_job* job, double* img_host,
         stats->rays_capped = (int64_t)c->pinned[C_CAPPED];
         stats->rays_nan = (int64_t)c->pinned[C_NAN];
         stats->norm = c->pinned_d[0];
+        stats->kernel_launches = c->launches;
     } else {
         CK(cudaStreamSynchronize(c->stream));
     }
@@ -434,5 +504,53 @@ extern "C" int art_metrics(art_ctx* c, const double* truth_dev, const double* im
     out_host[1] = fabs(h[1] - h[2]) / fabs(h[1]);
     out_host[2] = h[3] / h[4];
     out_host[3] = h[3] / (N * mean * mean);
+    return ART_OK;
+}
+
+extern "C" int art_profile(art_ctx* c, int enable)
+{
+    if (!c) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (!enable) {
+        c->prof_on = false;
+        return ART_OK;
+    }
+    if (!c->prof_steps) {
+        CK(cudaMalloc(&c->prof_steps, sizeof(unsigned long long) * art_ctx::PROF_MAX));
+        for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k) CK(cudaEventCreate(&c->ev[k]));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->prof_on = true;
+    c->prof_n = 0;
+    return ART_OK;
+}
+
+extern "C" int art_profile_read(art_ctx* c, art_launch_record* recs, int cap, int* n)
+{
+    if (!c || !n || (cap > 0 && !recs)) return ART_ERR_ARG;
+    *n = 0;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    if (!c->prof_steps) return ART_OK;
+    unsigned long long snap[art_ctx::PROF_MAX];
+    CK(cudaMemcpy(snap, c->prof_steps, sizeof(unsigned long long) * c->prof_n,
+                  cudaMemcpyDeviceToHost));
+    unsigned long long prev = 0;
+    int out = 0;
+    for (int k = 0; k < c->prof_n; ++k) {
+        art_launch_record r = c->rec[k];
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
+        r.ms = ms;
+        if (r.kind == ART_K_TRACE_FP64 || r.kind == ART_K_TRACE_FP32) {
+            // the step counter restarts with every call: a snapshot below the previous one
+            // belongs to a new call
+            r.steps = (int64_t)(snap[k] >= prev ? snap[k] - prev : snap[k]);
+            prev = snap[k];
+        }
+        if (r.kind == ART_K_OTHER && r.items == 1) prev = 0;  // camera set-up opens a call
+        if (out < cap) recs[out++] = r;
+    }
+    *n = out;
     return ART_OK;
 }

@@ -29,11 +29,16 @@
 
 namespace art {
 
+#if !defined(__CUDACC__)
+inline double rsqrt(double v) { return 1.0 / sqrt(v); }
+inline float rsqrt(float v) { return 1.0f / sqrt(v); }
+#endif
+
 // Job parameters as the kernels see them (POD, passed by value).
 struct DevJob {
     double a, a2, r_obs, pix, step_frac, h_min, r_in_stop, r_out_stop, inv_2w2;
-    double R_abs, R_rel;
-    int32_t nx, ny, levels, emission, flow, stokes, subrings, planes, max_steps, fp64_nturn;
+    double R_abs, R_rel, fp64_sweep;
+    int32_t nx, ny, levels, emission, flow, stokes, subrings, planes, max_steps;
     int32_t interp, edge_mode, abs_norm, precision;
 };
 
@@ -66,8 +71,8 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
     R a2z2 = a2 * z2;
     R b = x * x + y * y + z2 - a2;
     R r2 = R(0.5) * (b + sqrt(b * b + R(4) * a2z2));
-    R r = sqrt(r2);
-    R ir = R(1) / r;
+    R ir = rsqrt(r2);
+    R r = r2 * ir;
     R ir2 = ir * ir;
     R r4 = r2 * r2;
     R iQ = R(1) / (r4 + a2z2);
@@ -78,7 +83,7 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
     R Lz = z * ir;
     R Lkxy = Lx * kx + Ly * ky;
     R lk = -kt - (Lkxy + Lz * kz);
-    R iSig = R(1) / (r2 + a2z2 * ir2);
+    R iSig = r2 * iQ;  // Sigma = r^2 + a^2 z^2 / r^2 = Q / r^2
     R rs = r * iSig;
     R drx = x * rs, dry = y * rs, drz = z * (r2 + a2) * ir * iSig;
     R B = f * ir * (R(3) - R(4) * r4 * iQ);
@@ -132,13 +137,13 @@ ART_HD R emission_cfg0(const RayState<R>& s, R r, R kt, const DevJob& J)
 }
 
 // Sign of d(theta)/d(lambda) from k_theta sin(theta) = (x k_x + y k_y) z/r - (r - z^2/r) k_z,
-// 0 inside a dead band of 1e-9 r (radial rays).  Sign flips count polar turning points, which
+// 0 inside a dead band of 1e-9 r (1e-5 r in FP32) so radial rays count no turns.  Sign flips count polar turning points, which
 // separate the passes of a ray through the equatorial plane (the subring index n).
 template <class R>
 ART_HD int polar_sign(const RayState<R>& s, R r)
 {
     R q = (s.x * s.kx + s.y * s.ky) * s.z / r - (r - s.z * s.z / r) * s.kz;
-    R tol = R(1e-9) * r;
+    R tol = R(sizeof(R) == 4 ? 1e-5 : 1e-9) * r;  // dead band above the rounding noise
     return q > tol ? 1 : (q < -tol ? -1 : 0);
 }
 

@@ -103,6 +103,7 @@ struct Tracer {
     RayState<R> s;
     R kt, r, J0, A0, I, T;
     R acc[4];     // subring planes (unpolarized)
+    R sweep;      // angle swept by the position vector (mixed-precision routing)
     float min_r;
     int steps, nturn, tsign, status;
     int32_t pix;
@@ -142,6 +143,7 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Ca
     t.T = R(1);
     for (int p = 0; p < 4; ++p) t.acc[p] = R(0);
     t.min_r = float(t.r);
+    t.sweep = R(0);
     t.steps = 0;
     t.nturn = 0;
     t.tsign = polar_sign<R>(t.s, t.r);
@@ -149,8 +151,9 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Ca
     t.pix = pix;
 }
 
-// One RK4 step plus the transfer segment; returns true when the ray has terminated.
-template <class R>
+// One RK4 step plus the transfer segment; returns true when the ray has terminated.  SWEEP
+// accumulates the angle swept by the position vector (used to route rays in mixed precision).
+template <class R, bool SWEEP>
 __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
 {
     const R a = R(J.a), a2 = R(J.a2);
@@ -169,6 +172,7 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
     y.kx = t.s.kx + h * k3.kx; y.ky = t.s.ky + h * k3.ky; y.kz = t.s.kz + h * k3.kz;
     geodesic_rhs<R>(y, t.kt, a, a2, k4);
     const R h6 = h / R(6);
+    const R ox = t.s.x, oy = t.s.y, oz = t.s.z;
     t.s.x += h6 * (k1.x + R(2) * k2.x + R(2) * k3.x + k4.x);
     t.s.y += h6 * (k1.y + R(2) * k2.y + R(2) * k3.y + k4.y);
     t.s.z += h6 * (k1.z + R(2) * k2.z + R(2) * k3.z + k4.z);
@@ -180,6 +184,12 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
           isfinite(t.s.ky) && isfinite(t.s.kz))) {
         t.status = ART_RAY_NAN;
         return true;
+    }
+    if (SWEEP) {
+        // |x_old x x_new| / (|x_old| |x_new|): the sine of the angle the position vector turns
+        R cx = oy * t.s.z - oz * t.s.y, cy = oz * t.s.x - ox * t.s.z, cz = ox * t.s.y - oy * t.s.x;
+        R n2 = (ox * ox + oy * oy + oz * oz) * (t.s.x * t.s.x + t.s.y * t.s.y + t.s.z * t.s.z);
+        t.sweep += sqrt((cx * cx + cy * cy + cz * cz) / n2);
     }
     R rn = ks_radius<R>(t.s.x, t.s.y, t.s.z, a2);
     R J1 = J.emission == ART_EMIT_CFG0 ? emission_cfg0<R>(t.s, rn, t.kt, J) : R(0);
@@ -212,7 +222,7 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
     return false;
 }
 
-template <class R>
+template <class R, bool SWEEP>
 __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
 {
     __shared__ Camera cam_s;
@@ -246,9 +256,9 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
     active = fetch_next();
     while (__any_sync(0xffffffffu, active)) {
         if (active) {
-            if (ray_step<R>(t, J)) {
+            if (ray_step<R, SWEEP>(t, J)) {
                 atomicAdd(A.counters + C_STEPS, (unsigned long long)t.steps);
-                bool rer = mixed32 && (t.nturn >= J.fp64_nturn || t.status == ART_RAY_NAN ||
+                bool rer = mixed32 && (t.sweep >= R(J.fp64_sweep) || t.status == ART_RAY_NAN ||
                                        t.status == ART_RAY_CAP);
                 if (rer) {
                     unsigned long long w = atomicAdd(A.reroute_count, 1ull);
@@ -289,19 +299,30 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
 
 cudaError_t launch_trace(const TraceArgs& a, bool fp32, int grid, cudaStream_t st)
 {
-    if (fp32)
-        trace_kernel<float><<<grid, TRACE_BLOCK, 0, st>>>(a);
+    if (fp32 && a.reroute)
+        trace_kernel<float, true><<<grid, TRACE_BLOCK, 0, st>>>(a);
+    else if (fp32)
+        trace_kernel<float, false><<<grid, TRACE_BLOCK, 0, st>>>(a);
     else
-        trace_kernel<double><<<grid, TRACE_BLOCK, 0, st>>>(a);
+        trace_kernel<double, false><<<grid, TRACE_BLOCK, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t trace_occupancy(bool fp32, int* blocks_per_sm)
 {
-    if (fp32)
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<float>,
-                                                             TRACE_BLOCK, 0);
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<double>,
+    int b1 = 0, b2 = 0;
+    cudaError_t e;
+    if (fp32) {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, trace_kernel<float, true>,
+                                                          TRACE_BLOCK, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, trace_kernel<float, false>,
+                                                              TRACE_BLOCK, 0);
+        *blocks_per_sm = b1 < b2 ? b1 : b2;
+        return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                         trace_kernel<double, false>,
                                                          TRACE_BLOCK, 0);
 }
 

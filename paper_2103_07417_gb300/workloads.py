@@ -89,3 +89,21 @@ def fbm(seed: int, n: int, hurst: float) -> np.ndarray:
     w = np.fft.fft(np.sqrt(lam / m) * z)
     fgn = w.real[:n]
     return np.concatenate([[0.0], np.cumsum(fgn)])
+
+
+def cfg1_analytic(**over) -> dict:
+    """The Kerr geometry of the 128^2 -> 2048^2 configuration (a = 0.94, inclination 17 deg,
+    FOV 40 M, base 129^2, 4 levels to 2049^2, R_rel = R_abs = 1e-3 of I_bar_int) with the
+    analytic emissivity j = r^-2 exp(-z^2/(2 (0.3 r)^2)) of a Keplerian flow, mixed precision."""
+    return job(**{**dict(a=0.94, incl_deg=17.0, fov=40.0, n0x=129, n0y=129, levels=4,
+                         R_rel=1e-3, R_abs=1e-3, abs_norm="ibar_int", emission="cfg0",
+                         disk_w=0.3, precision="mixed"), **over})
+
+
+BENCH_WORKLOADS = {
+    "cfg1_analytic": ("adaptive render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, "
+                      "FOV 40 M, r_obs 1000 M, RK4 h=0.05r, analytic Keplerian emissivity "
+                      "r^-2 exp(-z^2/(2(0.3r)^2)), R_rel=R_abs=1e-3", cfg1_analytic),
+    "cfg0": ("adaptive render 33^2 -> 129^2 (2 levels), Schwarzschild, i=60 deg, FOV 40 M, "
+             "R_rel=0.01, R_abs=1e-4 of peak", cfg0),
+}

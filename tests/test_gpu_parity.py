@@ -262,3 +262,56 @@ def test_mixed_precision_error_bound(ctx):
     mse_mean = np.sum((g - ref) ** 2) / (g.size * np.mean(ref) ** 2)
     assert mse_mean < 1e-5
     assert st["rays_traced"] == g.size
+
+
+# ------------------------------------------------------------------------------------------
+# the benchmark's own workload at full size (sampled against the oracle)
+# ------------------------------------------------------------------------------------------
+
+def _level_of(i, j, levels):
+    for k in range(1, levels + 1):
+        s = 1 << (levels - k)
+        if i % s == 0 and j % s == 0:
+            return k, s
+    return None, None
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bench_workload_sampled(ctx, precision):
+    """129^2 -> 2049^2 over 4 levels, exactly as bench.py renders it: sampled traced pixels are
+    re-traced by the oracle; sampled interpolated pixels must equal the mean of their 2 or 4
+    previous-level neighbours; level counts add up."""
+    art = _art()
+    params = W.cfg1_analytic(precision=precision)
+    job = art.make_job(**params)
+    img, mask, st = ctx.render(job)
+    g = img.cpu().numpy()[0]
+    m = mask.cpu().numpy()
+    ny, nx = g.shape
+    assert (m[::16, ::16] == art.MASK_TRACED).all()
+    assert set(np.unique(m)) <= {art.MASK_TRACED, art.MASK_INTERP}
+    assert (m == art.MASK_TRACED).sum() == st["rays_traced"] == sum(st["rays_per_level"])
+    rng = np.random.default_rng(42)
+    traced = np.flatnonzero(m.ravel() == art.MASK_TRACED)
+    pick = rng.choice(traced, size=256, replace=False)
+    ref, info = O.trace_pixels(O.make_job(**params), pick.astype(np.int64))
+    got = g.ravel()[pick]
+    if precision == "fp64":
+        assert _close(got, ref[:, 0]).sum() == 0
+    else:
+        mse = np.sum((got - ref[:, 0]) ** 2) / (got.size * np.mean(ref[:, 0]) ** 2)
+        assert mse < 1e-5, mse
+    interp = np.flatnonzero(m.ravel() == art.MASK_INTERP)
+    for p in rng.choice(interp, size=2000, replace=False):
+        j, i = divmod(int(p), nx)
+        k, s = _level_of(i, j, params["levels"])
+        oi, oj = (i // s) % 2, (j // s) % 2
+        if oi and oj:
+            ref_v = 0.25 * (((g[j - s, i - s] + g[j + s, i - s]) + g[j - s, i + s]) + g[j + s, i + s])
+        elif oi:
+            ref_v = 0.5 * (g[j, i - s] + g[j, i + s])
+        else:
+            ref_v = 0.5 * (g[j - s, i] + g[j + s, i])
+        assert g[j, i] == ref_v
+    if precision == "mixed":
+        assert st["rays_fp64"] < 0.2 * st["rays_traced"]
