@@ -182,6 +182,25 @@ int art_render_host(art_ctx* ctx, const art_job* job, double* img_host, uint8_t*
 int art_profile(art_ctx* ctx, int enable);
 int art_profile_read(art_ctx* ctx, art_launch_record* recs_host, int cap, int* n);
 
+/* art_trace_pixels for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant.  Some callers cannot let a library call cudaMalloc:
+ * a process whose device memory is reserved up front by its own allocator (a render service with
+ * a fixed budget per GPU), code running while another framework owns allocation, or a caller that
+ * must avoid the implicit synchronisation cudaMalloc and cudaFree can cause.  This call allocates
+ * nothing and needs no context: it traces on the current device and on `stream` (a cudaStream_t,
+ * NULL = legacy default stream), with the same arguments, output layout and precision handling as
+ * art_trace_pixels.  Its scratch (camera, counters, FP64 re-trace queue) is one static device
+ * array of about 4.2 MB, which every GPU that loads the library holds until the process exits.
+ *   - n may be at most ART_NOALLOC_MAX_RAYS; larger n returns ART_ERR_ARG before any GPU work.
+ *   - The first call on a device resolves the array's device address (cudaGetSymbolAddress) and
+ *     the launch geometry; make that first call before any stream capture.
+ *   - Every call shares the one array and clears its counters first; calls that overlap on the GPU
+ *     (on different streams, or from several host threads) race on it and must be serialised.
+ *   - Synchronises `stream` before returning.  Errors as art_trace_pixels. */
+#define ART_NOALLOC_MAX_RAYS (1 << 20)
+int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_dev, int64_t n,
+                             double* out_dev, const art_rayaux* aux, void* stream);
+
 /* Image metrics of plane 0 (Eqs. interpdef, fluxdef, msedef): out_host[0] = interpolation
  * fraction (mask_dev nullable -> 0), [1] = flux error with the trapezoid flux, [2] = MSE
  * sum|I - I_hat|^2 / sum|I|^2, [3] = sum|I - I_hat|^2 / (N mean(I)^2).  Synchronises. */

@@ -88,7 +88,9 @@ _lib = None
 
 EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_planes",
            "art_trace_pixels", "art_ibar_int", "art_refine_level", "art_render",
-           "art_render_host", "art_metrics", "art_profile", "art_profile_read")
+           "art_render_host", "art_metrics", "art_profile", "art_profile_read",
+           "art_trace_pixels_noalloc")
+NOALLOC_MAX_RAYS = 1 << 20
 
 
 def lib_path() -> str:
@@ -120,6 +122,7 @@ def load():
             lib.art_metrics.argtypes = [vp, vp, vp, vp, i32, i32, P(ctypes.c_double)]
             lib.art_profile.argtypes = [vp, ctypes.c_int]
             lib.art_profile_read.argtypes = [vp, P(LaunchRecord), ctypes.c_int, P(ctypes.c_int)]
+            lib.art_trace_pixels_noalloc.argtypes = [P(Job), vp, i64, vp, P(RayAux), vp]
             _lib = lib
     return _lib
 
@@ -143,6 +146,25 @@ def art_image_size(job: Job):
 
 def art_planes(job: Job) -> int:
     return int(load().art_planes(ctypes.byref(job)))
+
+
+def _rayaux(aux):
+    if aux is None:
+        return None
+    return RayAux(*[ctypes.c_void_p(aux[k].data_ptr()) if aux.get(k) is not None else None
+                    for k in ("status", "steps", "nturn", "min_r")])
+
+
+def art_trace_pixels_noalloc(job: Job, pix, out, aux: dict | None = None, stream=None) -> int:
+    """The allocation-free tracer (no context; current device; `stream` a torch stream or None
+    for torch's current stream).  Returns the C return code instead of raising, so callers can
+    see the size rejection."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    ra = _rayaux(aux)
+    return int(load().art_trace_pixels_noalloc(ctypes.byref(job), _dptr(pix), pix.numel(),
+                                                _dptr(out), ctypes.byref(ra) if ra else None,
+                                                ctypes.c_void_p(s.cuda_stream)))
 
 
 def _dptr(t):

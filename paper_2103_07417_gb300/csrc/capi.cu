@@ -160,6 +160,9 @@ static int make_devjob(const art_job* job, DevJob* J)
     return ART_OK;
 }
 
+// The same validation for the allocation-free entry point (noalloc.cu).
+int art_make_devjob(const art_job* job, DevJob* J) { return make_devjob(job, J); }
+
 extern "C" int art_create(art_ctx** out, int device, void* stream)
 {
     if (!out) return ART_ERR_ARG;
