@@ -30,10 +30,17 @@ from paper_2103_07417_gb300 import workloads as W  # noqa: E402
 # update arithmetic for 6 variables (81), the new point's radius (15), the Keplerian emissivity
 # (44), the polar-turn test (11) and the transfer segment (11); the FP32 pass of the mixed path
 # adds the swept-angle accumulation (28).
-FLOPS_PER_STEP = {"trace_fp64": 550, "trace_fp32": 578}
+# The double-float re-trace counts the same 550 algorithmic flops per step (each carried out as
+# a double-float operation of several FP32 instructions).
+FLOPS_PER_STEP = {"trace_fp64": 550, "trace_fp32": 578, "trace_df": 550}
 # Peaks for "alu"-bound kernels: FP32 = 152 SMs x 128 lanes x 2 flops x 2.07 GHz; FP64 = the
 # GB300's nominal dense FP64 rate.
-PEAK_TFLOPS = {"trace_fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "trace_fp64": 1.25}
+PEAK_TFLOPS = {"trace_fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "trace_fp64": 1.25,
+               "trace_df": 152 * 128 * 2 * 2.07e9 / 1e12}
+PEAK_SOURCE = {"trace_fp32": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+               "trace_df": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (FP32 pipes)",
+               "trace_fp64": "nominal GB300 dense FP64"}
+DTYPE = {"mixed": "f32+f64", "mixed_df": "f32+df32x2", "fp64": "f64", "fp32": "f32"}
 METRIC = "rays/s"
 
 
@@ -44,7 +51,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cfg1_analytic", choices=sorted(W.BENCH_WORKLOADS))
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df", "fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single", action="store_true",
                     help="one warm-up and one render, nothing else (for profiler captures)")
@@ -231,28 +238,29 @@ def main():
         peak = PEAK_TFLOPS[dom]
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"
-                                    if dom == "trace_fp32" else "nominal GB300 dense FP64"),
+                    "peak_source": PEAK_SOURCE[dom],
                     "launches": d["launches"], "steps": d["steps"],
                     "share_of_step": d["ms"] / total_ms}
     kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                    "share": round(v["ms"] / total_ms, 4)} for k, v in by_kind.items()}
 
-    # plain FP64 path on the same workload, for comparison
+    # the other precision paths on the same workload, for comparison
     paths = {}
-    if args.precision != "fp64":
-        job64 = art.make_job(**{**params, "precision": "fp64"})
-        st64 = ctx.art_render(job64, img, mask, stats=True)
-        k64 = max(3, args.steps // 5)
-        t64 = timed(k64, job64)
-        paths["fp64"] = {"rays_per_s": st64["rays_traced"] * k64 / t64,
-                         "geodesic_steps_per_s": st64["steps"] * k64 / t64,
-                         "ms_per_step": 1000 * t64 / k64}
-        ctx.art_render(job, img, mask, stats=False)
+    for prec in ("fp64", "mixed", "mixed_df"):
+        if prec == args.precision:
+            continue
+        jobp = art.make_job(**{**params, "precision": prec})
+        stp = ctx.art_render(jobp, img, mask, stats=True)
+        kp = max(3, args.steps // 5)
+        tp = timed(kp, jobp)
+        paths[prec] = {"rays_per_s": stp["rays_traced"] * kp / tp,
+                       "geodesic_steps_per_s": stp["steps"] * kp / tp,
+                       "ms_per_step": 1000 * tp / kp, "rays_high_precision": stp["rays_fp64"]}
+    ctx.art_render(job, img, mask, stats=False)
     paths[args.precision] = {"rays_per_s": value / world,
                              "geodesic_steps_per_s": steps_per_render * args.steps / t_dev,
                              "ms_per_step": 1000 * t_dev / args.steps,
-                             "rays_fp64": stats["rays_fp64"]}
+                             "rays_high_precision": stats["rays_fp64"]}
 
     # end to end through the public C-ABI with host buffers (D2H of image + mask inside)
     import numpy as np
@@ -278,7 +286,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1000 * t_dev / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
-                "dtype": {"mixed": "f32+f64", "fp64": "f64", "fp32": "f32"}[args.precision],
+                "dtype": DTYPE[args.precision],
                 "data": "synthetic",
                 "config": {"workload": desc, "name": args.workload, "image": f"{nx}x{ny}",
                            "precision": args.precision, "rays_per_step": rays,

@@ -50,7 +50,7 @@ enum { ART_FLOW_KEPLER = 0, ART_FLOW_STATIC = 1 };
 enum { ART_NORM_IBAR_INT = 0, ART_NORM_PEAK = 1 };
 enum { ART_INTERP_LINEAR = 0, ART_INTERP_NEAREST = 1 };
 enum { ART_EDGE_ONESIDED = 0, ART_EDGE_TRACE = 1 };
-enum { ART_FP64 = 0, ART_MIXED = 1, ART_FP32 = 2 };
+enum { ART_FP64 = 0, ART_MIXED = 1, ART_FP32 = 2, ART_MIXED_DF = 3 };
 enum { ART_MASK_UNSET = 0, ART_MASK_TRACED = 1, ART_MASK_INTERP = 2 };
 enum { ART_RAY_ESCAPED = 0, ART_RAY_CAPTURED = 1, ART_RAY_CAP = 2, ART_RAY_NAN = 3 };
 
@@ -71,7 +71,9 @@ typedef struct art_job {
     int32_t flow;        /* ART_FLOW_* */
     int32_t stokes;      /* 1 (unpolarized) */
     int32_t subrings;    /* 0, or the number of subring planes n = 0..subrings-1 */
-    int32_t precision;   /* ART_FP64, ART_MIXED (FP32 with FP64 re-trace), ART_FP32 */
+    int32_t precision;   /* ART_FP64; ART_MIXED: FP32 with an FP64 re-trace of near-critical rays;
+                          * ART_MIXED_DF: the same with the re-traced geodesic in double-float
+                          * (float pairs, ~48-bit significand) on the FP32 pipes; ART_FP32 */
     int32_t max_steps;   /* RK4 step cap per ray */
     double fp64_sweep;   /* ART_MIXED: re-trace in FP64 the rays whose position vector swept at
                           * least this angle [rad] about the hole (3 pi: a full loop of
@@ -87,7 +89,7 @@ typedef struct art_job {
 /* Statistics of one render (host struct, filled on return). */
 typedef struct art_stats {
     int64_t rays_traced;        /* rays whose result is in the image */
-    int64_t rays_fp64;          /* ART_MIXED: rays re-traced in FP64 */
+    int64_t rays_fp64;          /* mixed modes: rays re-traced at high precision */
     int64_t steps;              /* RK4 steps summed over all traced rays (incl. re-traces) */
     int64_t rays_capped;        /* rays that hit max_steps */
     int64_t rays_nan;           /* rays stopped by a non-finite state */
@@ -97,7 +99,8 @@ typedef struct art_stats {
 } art_stats;
 
 /* One kernel launch timed by the profiler (art_profile). */
-enum { ART_K_TRACE_FP64 = 0, ART_K_TRACE_FP32 = 1, ART_K_REFINE = 2, ART_K_OTHER = 3 };
+enum { ART_K_TRACE_FP64 = 0, ART_K_TRACE_FP32 = 1, ART_K_REFINE = 2, ART_K_OTHER = 3,
+       ART_K_TRACE_DF = 4 };
 typedef struct art_launch_record {
     int32_t kind;   /* ART_K_* */
     int32_t level;  /* refinement level of the launch (-1 outside a render) */

@@ -26,7 +26,7 @@ _NAMES = dict(
     abs_norm={"ibar_int": 0, "peak": 1},
     interp={"linear": 0, "nearest": 1},
     edge_mode={"onesided": 0, "trace": 1},
-    precision={"fp64": 0, "mixed": 1, "fp32": 2},
+    precision={"fp64": 0, "mixed": 1, "fp32": 2, "mixed_df": 3},
 )
 
 
@@ -57,7 +57,7 @@ class LaunchRecord(ctypes.Structure):
                 ("steps", ctypes.c_int64), ("items", ctypes.c_int64)]
 
 
-KERNEL_KINDS = {0: "trace_fp64", 1: "trace_fp32", 2: "refine", 3: "other"}
+KERNEL_KINDS = {0: "trace_fp64", 1: "trace_fp32", 2: "refine", 3: "other", 4: "trace_df"}
 
 
 class RayAux(ctypes.Structure):

@@ -16,7 +16,7 @@ struct art_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
-    int occ64 = 0, occ32 = 0;
+    int occ64 = 0, occ32 = 0, occdf = 0;
     // scratch owned by the library
     int32_t* queue = nullptr;
     int32_t* reroute = nullptr;
@@ -61,7 +61,7 @@ static void prof_end(art_ctx* c, int k, int kind, int64_t items)
     c->rec[k].ms = 0.f;
     c->rec[k].steps = 0;
     c->rec[k].items = items;
-    if (kind == ART_K_TRACE_FP64 || kind == ART_K_TRACE_FP32)
+    if (kind == ART_K_TRACE_FP64 || kind == ART_K_TRACE_FP32 || kind == ART_K_TRACE_DF)
         cudaMemcpyAsync(c->prof_steps + k, c->counters + C_STEPS, sizeof(unsigned long long),
                         cudaMemcpyDeviceToDevice, c->stream);
     c->prof_n = k + 1;
@@ -129,7 +129,7 @@ static int make_devjob(const art_job* job, DevJob* J)
     if (job->interp != ART_INTERP_LINEAR && job->interp != ART_INTERP_NEAREST) return ART_ERR_ARG;
     if (job->edge_mode != ART_EDGE_ONESIDED && job->edge_mode != ART_EDGE_TRACE) return ART_ERR_ARG;
     if (job->abs_norm != ART_NORM_IBAR_INT && job->abs_norm != ART_NORM_PEAK) return ART_ERR_ARG;
-    if (job->precision < ART_FP64 || job->precision > ART_FP32) return ART_ERR_ARG;
+    if (job->precision < ART_FP64 || job->precision > ART_MIXED_DF) return ART_ERR_ARG;
     if (!(job->disk_w > 0.0)) return ART_ERR_ARG;
     if (!(job->fp64_sweep > 0.0)) return ART_ERR_ARG;
     J->a = job->a;
@@ -174,13 +174,15 @@ extern "C" int art_create(art_ctx** out, int device, void* stream)
     c->device = device;
     c->stream = (cudaStream_t)stream;
     if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        trace_occupancy(false, &c->occ64) != cudaSuccess ||
-        trace_occupancy(true, &c->occ32) != cudaSuccess) {
+        trace_occupancy(TK_FP64, &c->occ64) != cudaSuccess ||
+        trace_occupancy(TK_FP32, &c->occ32) != cudaSuccess ||
+        trace_occupancy(TK_DF, &c->occdf) != cudaSuccess) {
         delete c;
         return ART_ERR_CUDA;
     }
     if (c->occ64 < 1) c->occ64 = 1;
     if (c->occ32 < 1) c->occ32 = 1;
+    if (c->occdf < 1) c->occdf = 1;
     *out = c;
     return ART_OK;
 }
@@ -269,34 +271,38 @@ static int trace_queue(art_ctx* c, const DevJob& J, const unsigned long long* co
         a.aux_minr = aux->min_r;
     }
     const int g64 = c->num_sms * c->occ64, g32 = c->num_sms * c->occ32;
+    const int gdf = c->num_sms * c->occdf;
     int k;
     if (J.precision == ART_FP64) {
         a.fetch = c->counters + C_FETCH;
         CK(cudaMemsetAsync(a.fetch, 0, sizeof(unsigned long long), c->stream));
         k = prof_begin(c);
-        CK(launch_trace(a, false, g64, c->stream));
+        CK(launch_trace(a, TK_FP64, g64, c->stream));
         prof_end(c, k, ART_K_TRACE_FP64, -1);
         return ART_OK;
     }
+    const bool mixed = J.precision == ART_MIXED || J.precision == ART_MIXED_DF;
     a.fetch = c->counters + C_FETCH;
     CK(cudaMemsetAsync(c->counters + C_FETCH, 0, sizeof(unsigned long long) * 3, c->stream));
-    if (J.precision == ART_MIXED) {
+    if (mixed) {
         a.reroute = c->reroute;
         a.reroute_count = c->counters + C_REROUTE;
     }
     k = prof_begin(c);
-    CK(launch_trace(a, true, g32, c->stream));
+    CK(launch_trace(a, TK_FP32, g32, c->stream));
     prof_end(c, k, ART_K_TRACE_FP32, -1);
-    if (J.precision == ART_MIXED) {
+    if (mixed) {
+        // high-precision re-trace of the near-critical rays the FP32 pass routed
         TraceArgs b = a;
         b.reroute = nullptr;
         b.reroute_count = nullptr;
         b.indirect = c->reroute;
         b.count = c->counters + C_REROUTE;
         b.fetch = c->counters + C_FETCH2;
+        const bool dfp = J.precision == ART_MIXED_DF;
         k = prof_begin(c);
-        CK(launch_trace(b, false, g64, c->stream));
-        prof_end(c, k, ART_K_TRACE_FP64, -1);
+        CK(launch_trace(b, dfp ? TK_DF : TK_FP64, dfp ? gdf : g64, c->stream));
+        prof_end(c, k, dfp ? ART_K_TRACE_DF : ART_K_TRACE_FP64, -1);
     }
     return ART_OK;
 }
@@ -545,7 +551,7 @@ extern "C" int art_profile_read(art_ctx* c, art_launch_record* recs, int cap, in
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
         r.ms = ms;
-        if (r.kind == ART_K_TRACE_FP64 || r.kind == ART_K_TRACE_FP32) {
+        if (r.kind == ART_K_TRACE_FP64 || r.kind == ART_K_TRACE_FP32 || r.kind == ART_K_TRACE_DF) {
             // the step counter restarts with every call: a snapshot below the previous one
             // belongs to a new call
             r.steps = (int64_t)(snap[k] >= prev ? snap[k] - prev : snap[k]);

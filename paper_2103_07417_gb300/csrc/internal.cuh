@@ -19,7 +19,7 @@ enum Counter {
     C_CAPPED = 5,    // rays that hit max_steps
     C_NAN = 6,       // rays stopped by a non-finite state
     C_BADIDX = 7,    // queue entries outside the image (skipped)
-    C_FP64 = 8,      // rays traced by the FP64 kernel in mixed mode
+    C_FP64 = 8,      // rays re-traced by the high-precision pass of the mixed modes
     C_LEVEL0 = 16,   // C_LEVEL0 + k: rays of level k (16 slots)
     C_COUNT = 32
 };
@@ -45,9 +45,10 @@ struct TraceArgs {
 };
 
 // trace.cu
+enum TraceKind { TK_FP64 = 0, TK_FP32 = 1, TK_DF = 2 };
 cudaError_t launch_camera_setup(const art_job& job, Camera* cam, cudaStream_t st);
-cudaError_t launch_trace(const TraceArgs& a, bool fp32, int grid, cudaStream_t st);
-cudaError_t trace_occupancy(bool fp32, int* blocks_per_sm);
+cudaError_t launch_trace(const TraceArgs& a, TraceKind kind, int grid, cudaStream_t st);
+cudaError_t trace_occupancy(TraceKind kind, int* blocks_per_sm);
 constexpr int TRACE_BLOCK = 128;
 
 // refine.cu

@@ -40,7 +40,7 @@ struct DeviceSlot {
     std::once_flag once;
     int rc = ART_ERR_CUDA;
     unsigned char* ptr = nullptr;  // device address of art_noalloc_scratch on that device
-    int num_sms = 0, occ64 = 0, occ32 = 0;
+    int num_sms = 0, occ64 = 0, occ32 = 0, occdf = 0;
 };
 DeviceSlot g_slots[MAX_DEVICES];
 
@@ -56,14 +56,16 @@ void setup_device(int dev)
         return;
     }
     if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        trace_occupancy(false, &s.occ64) != cudaSuccess ||
-        trace_occupancy(true, &s.occ32) != cudaSuccess) {
+        trace_occupancy(TK_FP64, &s.occ64) != cudaSuccess ||
+        trace_occupancy(TK_FP32, &s.occ32) != cudaSuccess ||
+        trace_occupancy(TK_DF, &s.occdf) != cudaSuccess) {
         cudaGetLastError();
         s.rc = ART_ERR_CUDA;
         return;
     }
     if (s.occ64 < 1) s.occ64 = 1;
     if (s.occ32 < 1) s.occ32 = 1;
+    if (s.occdf < 1) s.occdf = 1;
     s.ptr = static_cast<unsigned char*>(p);
     s.rc = ART_OK;
 }
@@ -118,22 +120,26 @@ extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_d
         a.aux_minr = aux->min_r;
     }
     const bool fp32_first = J.precision != ART_FP64;
+    const bool mixed = J.precision == ART_MIXED || J.precision == ART_MIXED_DF;
     a.fetch = counters + C_FETCH;
-    if (J.precision == ART_MIXED) {
+    if (mixed) {
         a.reroute = reroute;
         a.reroute_count = counters + C_REROUTE;
     }
-    if (launch_trace(a, fp32_first, s.num_sms * (fp32_first ? s.occ32 : s.occ64), st) !=
-        cudaSuccess)
+    if (launch_trace(a, fp32_first ? TK_FP32 : TK_FP64,
+                     s.num_sms * (fp32_first ? s.occ32 : s.occ64), st) != cudaSuccess)
         return ART_ERR_CUDA;
-    if (J.precision == ART_MIXED) {
+    if (mixed) {
         TraceArgs b = a;
         b.reroute = nullptr;
         b.reroute_count = nullptr;
         b.indirect = reroute;
         b.count = counters + C_REROUTE;
         b.fetch = counters + C_FETCH2;
-        if (launch_trace(b, false, s.num_sms * s.occ64, st) != cudaSuccess) return ART_ERR_CUDA;
+        const bool dfp = J.precision == ART_MIXED_DF;
+        if (launch_trace(b, dfp ? TK_DF : TK_FP64, s.num_sms * (dfp ? s.occdf : s.occ64), st) !=
+            cudaSuccess)
+            return ART_ERR_CUDA;
     }
     unsigned long long bad = 0;
     if (cudaMemcpyAsync(&bad, counters + C_BADIDX, sizeof bad, cudaMemcpyDeviceToHost, st) !=

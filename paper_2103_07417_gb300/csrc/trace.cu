@@ -14,9 +14,28 @@
 #include <cmath>
 #include <cstdint>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace art {
+
+// Arithmetic of the parts of a step outside the geodesic (radius for step size and stopping,
+// emission, transfer, turn counting): the geodesic type itself, except for double-float
+// geodesics, whose ray needs the extra precision only in its orbit.
+template <class R>
+struct Aux {
+    using Q = R;
+};
+template <>
+struct Aux<df> {
+    using Q = float;
+};
+
+template <class Q, class R>
+__device__ __forceinline__ RayState<Q> to_q(const RayState<R>& s)
+{
+    return RayState<Q>{Q(s.x), Q(s.y), Q(s.z), Q(s.kx), Q(s.ky), Q(s.kz)};
+}
 
 // --------------------------------------------------------------------------------------------
 // camera
@@ -100,10 +119,12 @@ __device__ __forceinline__ unsigned long long warp_fetch(unsigned long long* cou
 
 template <class R>
 struct Tracer {
+    using Q = typename Aux<R>::Q;
     RayState<R> s;
-    R kt, r, J0, A0, I, T;
-    R acc[4];     // subring planes (unpolarized)
-    R sweep;      // angle swept by the position vector (mixed-precision routing)
+    R kt;
+    Q r, J0, A0, I, T;
+    Q acc[4];     // subring planes (unpolarized)
+    Q sweep;      // angle swept by the position vector (mixed-precision routing)
     float min_r;
     int steps, nturn, tsign, status;
     int32_t pix;
@@ -120,6 +141,7 @@ template <class R>
 __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Camera& cam,
                                          int32_t pix)
 {
+    using Q = typename Aux<R>::Q;
     int i = pix % J.nx, j = pix / J.nx;
     double al = (i - 0.5 * (J.nx - 1)) * J.pix;
     double be = (j - 0.5 * (J.ny - 1)) * J.pix;
@@ -135,18 +157,18 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Ca
     t.s.kx = R(k[1]);
     t.s.ky = R(k[2]);
     t.s.kz = R(k[3]);
-    R a2 = R(J.a2);
-    t.r = ks_radius<R>(t.s.x, t.s.y, t.s.z, a2);
-    t.J0 = J.emission == ART_EMIT_CFG0 ? emission_cfg0<R>(t.s, t.r, t.kt, J) : R(0);
-    t.A0 = R(0);
-    t.I = R(0);
-    t.T = R(1);
-    for (int p = 0; p < 4; ++p) t.acc[p] = R(0);
+    RayState<Q> q = to_q<Q>(t.s);
+    t.r = ks_radius<Q>(q.x, q.y, q.z, Q(J.a2));
+    t.J0 = J.emission == ART_EMIT_CFG0 ? emission_cfg0<Q>(q, t.r, Q(t.kt), J) : Q(0);
+    t.A0 = Q(0);
+    t.I = Q(0);
+    t.T = Q(1);
+    for (int p = 0; p < 4; ++p) t.acc[p] = Q(0);
     t.min_r = float(t.r);
-    t.sweep = R(0);
+    t.sweep = Q(0);
     t.steps = 0;
     t.nturn = 0;
-    t.tsign = polar_sign<R>(t.s, t.r);
+    t.tsign = polar_sign<Q>(q, t.r);
     t.status = ART_RAY_CAP;
     t.pix = pix;
 }
@@ -156,9 +178,11 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Ca
 template <class R, bool SWEEP>
 __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
 {
+    using Q = typename Aux<R>::Q;
     const R a = R(J.a), a2 = R(J.a2);
-    R h = R(J.step_frac) * t.r;
-    if (h < R(J.h_min)) h = R(J.h_min);
+    Q hq = Q(J.step_frac) * t.r;
+    if (hq < Q(J.h_min)) hq = Q(J.h_min);
+    const R h = R(hq);
     const R hh = R(0.5) * h;
     RayState<R> k1, k2, k3, k4, y;
     geodesic_rhs<R>(t.s, t.kt, a, a2, k1);
@@ -172,7 +196,7 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
     y.kx = t.s.kx + h * k3.kx; y.ky = t.s.ky + h * k3.ky; y.kz = t.s.kz + h * k3.kz;
     geodesic_rhs<R>(y, t.kt, a, a2, k4);
     const R h6 = h / R(6);
-    const R ox = t.s.x, oy = t.s.y, oz = t.s.z;
+    const Q ox = Q(t.s.x), oy = Q(t.s.y), oz = Q(t.s.z);
     t.s.x += h6 * (k1.x + R(2) * k2.x + R(2) * k3.x + k4.x);
     t.s.y += h6 * (k1.y + R(2) * k2.y + R(2) * k3.y + k4.y);
     t.s.z += h6 * (k1.z + R(2) * k2.z + R(2) * k3.z + k4.z);
@@ -185,39 +209,40 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
         t.status = ART_RAY_NAN;
         return true;
     }
+    const RayState<Q> q = to_q<Q>(t.s);
     if (SWEEP) {
         // |x_old x x_new| / (|x_old| |x_new|): the sine of the angle the position vector turns
-        R cx = oy * t.s.z - oz * t.s.y, cy = oz * t.s.x - ox * t.s.z, cz = ox * t.s.y - oy * t.s.x;
-        R n2 = (ox * ox + oy * oy + oz * oz) * (t.s.x * t.s.x + t.s.y * t.s.y + t.s.z * t.s.z);
+        Q cx = oy * q.z - oz * q.y, cy = oz * q.x - ox * q.z, cz = ox * q.y - oy * q.x;
+        Q n2 = (ox * ox + oy * oy + oz * oz) * (q.x * q.x + q.y * q.y + q.z * q.z);
         t.sweep += sqrt((cx * cx + cy * cy + cz * cz) / n2);
     }
-    R rn = ks_radius<R>(t.s.x, t.s.y, t.s.z, a2);
-    R J1 = J.emission == ART_EMIT_CFG0 ? emission_cfg0<R>(t.s, rn, t.kt, J) : R(0);
-    R A1 = R(0);
+    Q rn = ks_radius<Q>(q.x, q.y, q.z, Q(J.a2));
+    Q J1 = J.emission == ART_EMIT_CFG0 ? emission_cfg0<Q>(q, rn, Q(t.kt), J) : Q(0);
+    Q A1 = Q(0);
     int seg = t.nturn;
-    int sg = polar_sign<R>(t.s, rn);
+    int sg = polar_sign<Q>(q, rn);
     if (sg != 0) {
         if (t.tsign != 0 && sg != t.tsign) ++t.nturn;
         t.tsign = sg;
     }
-    R Jb = R(0.5) * (t.J0 + J1), Ab = R(0.5) * (t.A0 + A1);
-    R dtau = Ab * h;
-    R dI = t.T * Jb * h * phi1<R>(dtau);
+    Q Jb = Q(0.5) * (t.J0 + J1), Ab = Q(0.5) * (t.A0 + A1);
+    Q dtau = Ab * hq;
+    Q dI = t.T * Jb * hq * phi1<Q>(dtau);
     if (J.subrings > 0) {
         int p = seg < J.subrings ? seg : J.subrings - 1;
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (q == p) t.acc[q] += dI;
+        for (int c = 0; c < 4; ++c)
+            if (c == p) t.acc[c] += dI;
     } else {
         t.I += dI;
     }
-    if (Ab != R(0)) t.T *= exp(-dtau);
+    if (Ab != Q(0)) t.T *= exp(-dtau);
     t.J0 = J1;
     t.A0 = A1;
     t.r = rn;
     if (float(rn) < t.min_r) t.min_r = float(rn);
-    if (rn < R(J.r_in_stop)) { t.status = ART_RAY_CAPTURED; return true; }
-    if (rn > R(J.r_out_stop)) { t.status = ART_RAY_ESCAPED; return true; }
+    if (rn < Q(J.r_in_stop)) { t.status = ART_RAY_CAPTURED; return true; }
+    if (rn > Q(J.r_out_stop)) { t.status = ART_RAY_ESCAPED; return true; }
     if (t.steps >= J.max_steps) { t.status = ART_RAY_CAP; return true; }
     return false;
 }
@@ -258,16 +283,15 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
         if (active) {
             if (ray_step<R, SWEEP>(t, J)) {
                 atomicAdd(A.counters + C_STEPS, (unsigned long long)t.steps);
-                bool rer = mixed32 && (t.sweep >= R(J.fp64_sweep) || t.status == ART_RAY_NAN ||
-                                       t.status == ART_RAY_CAP);
+                bool rer = mixed32 && (t.sweep >= typename Aux<R>::Q(J.fp64_sweep) ||
+                                       t.status == ART_RAY_NAN || t.status == ART_RAY_CAP);
                 if (rer) {
                     unsigned long long w = atomicAdd(A.reroute_count, 1ull);
                     A.reroute[w] = (int32_t)t.slot;
                 } else {
                     if (t.status == ART_RAY_CAP) atomicAdd(A.counters + C_CAPPED, 1ull);
                     if (t.status == ART_RAY_NAN) atomicAdd(A.counters + C_NAN, 1ull);
-                    if (sizeof(R) == 8 && J.precision == ART_MIXED)
-                        atomicAdd(A.counters + C_FP64, 1ull);
+                    if (A.indirect) atomicAdd(A.counters + C_FP64, 1ull);  // re-trace pass
                     const int np = J.planes;
                     if (A.img) {
                         if (J.subrings > 0) {
@@ -297,22 +321,30 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
     }
 }
 
-cudaError_t launch_trace(const TraceArgs& a, bool fp32, int grid, cudaStream_t st)
+cudaError_t launch_trace(const TraceArgs& a, TraceKind kind, int grid, cudaStream_t st)
 {
-    if (fp32 && a.reroute)
-        trace_kernel<float, true><<<grid, TRACE_BLOCK, 0, st>>>(a);
-    else if (fp32)
-        trace_kernel<float, false><<<grid, TRACE_BLOCK, 0, st>>>(a);
-    else
+    switch (kind) {
+    case TK_FP32:
+        if (a.reroute)
+            trace_kernel<float, true><<<grid, TRACE_BLOCK, 0, st>>>(a);
+        else
+            trace_kernel<float, false><<<grid, TRACE_BLOCK, 0, st>>>(a);
+        break;
+    case TK_DF:
+        trace_kernel<df, false><<<grid, TRACE_BLOCK, 0, st>>>(a);
+        break;
+    default:
         trace_kernel<double, false><<<grid, TRACE_BLOCK, 0, st>>>(a);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t trace_occupancy(bool fp32, int* blocks_per_sm)
+cudaError_t trace_occupancy(TraceKind kind, int* blocks_per_sm)
 {
     int b1 = 0, b2 = 0;
     cudaError_t e;
-    if (fp32) {
+    switch (kind) {
+    case TK_FP32:
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, trace_kernel<float, true>,
                                                           TRACE_BLOCK, 0);
         if (e == cudaSuccess)
@@ -320,10 +352,13 @@ cudaError_t trace_occupancy(bool fp32, int* blocks_per_sm)
                                                               TRACE_BLOCK, 0);
         *blocks_per_sm = b1 < b2 ? b1 : b2;
         return e;
+    case TK_DF:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<df, false>,
+                                                             TRACE_BLOCK, 0);
+    default:
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            blocks_per_sm, trace_kernel<double, false>, TRACE_BLOCK, 0);
     }
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                         trace_kernel<double, false>,
-                                                         TRACE_BLOCK, 0);
 }
 
 }  // namespace art

@@ -250,18 +250,39 @@ def test_metrics_match_oracle(ctx):
 # mixed precision
 # ------------------------------------------------------------------------------------------
 
-def test_mixed_precision_error_bound(ctx):
-    """FP32 geodesics with FP64 re-trace of rays with >= 2 polar turns: the image MSE relative
-    to the mean intensity squared stays below 1e-5 against the FP64 oracle."""
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df", "fp32"])
+def test_mixed_precision_error_bound(ctx, precision):
+    """FP32 geodesics with a high-precision re-trace (FP64 or double-float) of the rays that
+    swept >= 3 pi, and plain FP32: the image MSE relative to the mean intensity squared stays
+    below 1e-5 against the FP64 oracle (every pixel traced)."""
     art = _art()
     params = W.cfg0(a=0.94, incl_deg=17.0, n0x=17, n0y=17, levels=2, R_rel=-1.0, R_abs=-1.0)
-    job = art.make_job(**{**params, "precision": "mixed"})
+    job = art.make_job(**{**params, "precision": precision})
     img, mask, st = ctx.render(job)
     ref, _, _ = O.render(O.make_job(**params), None)
     g = img.cpu().numpy()[0]
     mse_mean = np.sum((g - ref) ** 2) / (g.size * np.mean(ref) ** 2)
     assert mse_mean < 1e-5
     assert st["rays_traced"] == g.size
+    if precision != "fp32":
+        assert st["rays_fp64"] > 0
+
+
+@pytest.mark.parametrize("geom", [dict(a=0.94, incl_deg=17.0), dict(a=-0.7, incl_deg=75.0)])
+def test_double_float_retrace_per_pixel(ctx, geom):
+    """Every ray routed to the double-float re-trace (threshold 1e-9 rad): the geodesic carries
+    ~48 bits, emission and transfer run in FP32, so each pixel matches the FP64 oracle to 2e-5."""
+    art = _art()
+    params = W.cfg0(n0x=13, n0y=13, levels=2, **geom)
+    job = art.make_job(**{**params, "precision": "mixed_df", "fp64_sweep": 1e-9})
+    nx, ny = art.art_image_size(job)
+    pix = np.arange(nx * ny, dtype=np.int32)
+    out, aux = ctx.trace_pixels(job, torch.from_numpy(pix).cuda())
+    ref, info = O.trace_pixels(O.make_job(**params), pix.astype(np.int64))
+    bad = _close(out.cpu().numpy()[:, 0], ref[:, 0], rtol=2e-5)
+    assert bad.sum() == 0, np.flatnonzero(bad)[:10]
+    st = aux["status"].cpu().numpy()
+    assert (st == info["status"]).mean() > 0.995
 
 
 # ------------------------------------------------------------------------------------------
@@ -276,7 +297,7 @@ def _level_of(i, j, levels):
     return None, None
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
 def test_bench_workload_sampled(ctx, precision):
     """129^2 -> 2049^2 over 4 levels, exactly as bench.py renders it: sampled traced pixels are
     re-traced by the oracle; sampled interpolated pixels must equal the mean of their 2 or 4
@@ -313,5 +334,5 @@ def test_bench_workload_sampled(ctx, precision):
         else:
             ref_v = 0.5 * (g[j - s, i] + g[j + s, i])
         assert g[j, i] == ref_v
-    if precision == "mixed":
-        assert st["rays_fp64"] < 0.2 * st["rays_traced"]
+    if precision != "fp64":
+        assert 0 < st["rays_fp64"] < 0.2 * st["rays_traced"]
