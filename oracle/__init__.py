@@ -64,7 +64,8 @@ class Job(ctypes.Structure):
         ("disk_w", ctypes.c_double), ("blob_sigma", ctypes.c_double),
         ("ne0", ctypes.c_double), ("thetae0", ctypes.c_double), ("b0", ctypes.c_double),
         ("nu_hz", ctypes.c_double), ("ne_slope", ctypes.c_double), ("te_slope", ctypes.c_double),
-        ("r_in", ctypes.c_double),
+        ("r_in", ctypes.c_double), ("length_cm", ctypes.c_double),
+        ("bz_ratio", ctypes.c_double),
     ]
 
 
@@ -85,7 +86,7 @@ _DEFAULTS = dict(a=0.0, mass=1.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33,
                  flow=FLOW_KEPLER, stokes=1, subrings=0, max_steps=100000, step_frac=0.05,
                  h_min=1e-4, horizon_eps=0.01, escape_frac=1.01, disk_w=0.3, blob_sigma=1.0,
                  ne0=0.0, thetae0=0.0, b0=0.0, nu_hz=230e9, ne_slope=-1.1, te_slope=-0.84,
-                 r_in=0.0)
+                 r_in=0.0, length_cm=9.6e14, bz_ratio=1.0)
 
 
 _NAMES = dict(
@@ -132,6 +133,10 @@ def _load():
                                              ctypes.c_int, ctypes.c_double, dp, dp]
             lib.orc_render.argtypes = [P(Job), dp, dp, u8p, P(Stats)]
             lib.orc_metrics.argtypes = [dp, dp, u8p, ctypes.c_int, ctypes.c_int, dp]
+            lib.orc_bessel_k.argtypes = [ctypes.c_int, ctypes.c_double]
+            lib.orc_bessel_k.restype = ctypes.c_double
+            lib.orc_synch_coeffs.argtypes = [ctypes.c_double] * 5 + [dp]
+            lib.orc_segment.argtypes = [dp, dp, ctypes.c_double, dp, dp]
             _lib = lib
     return _lib
 
@@ -190,8 +195,9 @@ def trace_pixels(job: Job, pix):
 
 
 def trace_record(job: Job, alpha: float, beta: float, maxrec: int = 200000):
-    """Per-step record of one ray: columns (affine lambda, x^mu, k_mu, I)."""
-    rec = np.zeros((maxrec, 10))
+    """Per-step record of one ray: columns (affine lambda, x^mu [1:5], k_mu [5:9],
+    f_mu [9:13] (polarization covector, zero when unpolarized), I [13])."""
+    rec = np.zeros((maxrec, 14))
     nrec = ctypes.c_int()
     status = _load().orc_trace_record(ctypes.byref(job), alpha, beta, maxrec, _ptr(rec),
                                       ctypes.byref(nrec))
@@ -228,16 +234,16 @@ def refine_level(job: Job, img, mask, level: int, norm: float):
 
 
 def render(job: Job, truth=None):
-    """The adaptive scheme; with `truth` (ny x nx) the tracer is replaced by a lookup.
-    Returns (img, mask, stats dict)."""
+    """The adaptive scheme; with `truth` (ny x nx, or planes x ny x nx) the tracer is replaced
+    by a lookup.  Returns (img [ny x nx, or planes x ny x nx], mask, stats dict)."""
     nx, ny = image_size(job)
-    img = np.zeros((ny, nx))
+    npl = planes(job)
+    img = np.zeros((npl, ny, nx))
     mask = np.zeros((ny, nx), dtype=np.uint8)
     st = Stats()
     tp = None
     if truth is not None:
-        t = np.ascontiguousarray(truth, dtype=np.float64)
-        assert t.shape == (ny, nx)
+        t = np.ascontiguousarray(truth, dtype=np.float64).reshape(npl, ny, nx)
         tp = _ptr(t)
     rc = _load().orc_render(ctypes.byref(job), tp, _ptr(img), _ptr(mask, ctypes.c_uint8),
                             ctypes.byref(st))
@@ -245,7 +251,30 @@ def render(job: Job, truth=None):
         raise RuntimeError(f"orc_render failed ({rc})")
     stats = dict(rays_traced=st.rays_traced, steps=st.steps, ibar=st.ibar,
                  rays_per_level=[st.rays_per_level[k] for k in range(job.levels + 1)])
-    return img, mask, stats
+    return (img[0] if npl == 1 else img), mask, stats
+
+
+def bessel_k(n: int, x: float) -> float:
+    return float(_load().orc_bessel_k(int(n), float(x)))
+
+
+def synch_coeffs(ne, thetae, B, nu, theta_b):
+    """{j_I, j_Q, j_V, alpha_I, alpha_Q, rho_Q, rho_V} (cgs) in the frame whose Q axis is the
+    emission's E-vector."""
+    out = np.zeros(7)
+    _load().orc_synch_coeffs(float(ne), float(thetae), float(B), float(nu), float(theta_b),
+                             _ptr(out))
+    return out
+
+
+def segment(K7, J4, h):
+    """(E, X): exact propagator exp(-K h) and source integral of one constant segment."""
+    K = np.ascontiguousarray(K7, dtype=np.float64)
+    J = np.ascontiguousarray(J4, dtype=np.float64)
+    E = np.zeros(16)
+    X = np.zeros(4)
+    _load().orc_segment(_ptr(K), _ptr(J), float(h), _ptr(E), _ptr(X))
+    return E.reshape(4, 4), X
 
 
 def metrics(truth, img, mask=None):

@@ -305,21 +305,333 @@ int orc_emission(const orc_job* job, const double* x, const double* k, double* j
     return 0;
 }
 
+
+/* ------------------------------------------------------------------------------------------ */
+/* Polarized transfer: parallel transport, thermal synchrotron, constant-coefficient segments  */
+/* ------------------------------------------------------------------------------------------ */
+
+static void metric_cov_c(double a, double M, const cplx* x, cplx g[4][4])
+{
+    cplx r = ks_radius(a, x[1], x[2], x[3]);
+    cplx r2 = r * r;
+    cplx f = 2.0 * M * r * r2 / (r2 * r2 + a * a * x[3] * x[3]);
+    cplx l[4] = {1.0, -(r * x[1] - a * x[2]) / (r2 + a * a), -(r * x[2] + a * x[1]) / (r2 + a * a),
+                 -x[3] / r};
+    for (int m = 0; m < 4; ++m)
+        for (int n = 0; n < 4; ++n)
+            g[m][n] = ((m == n) ? (m == 0 ? -1.0 : 1.0) : 0.0) + f * l[m] * l[n];
+}
+
+/* Inverse of a 4x4 matrix by Gauss-Jordan elimination with partial pivoting. */
+static void inv4(double A[4][4], double B[4][4])
+{
+    double W[4][8];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 8; ++j) W[i][j] = j < 4 ? A[i][j] : (j - 4 == i ? 1.0 : 0.0);
+    for (int c = 0; c < 4; ++c) {
+        int p = c;
+        for (int i = c + 1; i < 4; ++i)
+            if (fabs(W[i][c]) > fabs(W[p][c])) p = i;
+        for (int j = 0; j < 8; ++j) { double t = W[c][j]; W[c][j] = W[p][j]; W[p][j] = t; }
+        double d = W[c][c];
+        for (int j = 0; j < 8; ++j) W[c][j] /= d;
+        for (int i = 0; i < 4; ++i)
+            if (i != c) {
+                double m = W[i][c];
+                for (int j = 0; j < 8; ++j) W[i][j] -= m * W[c][j];
+            }
+    }
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) B[i][j] = W[i][j + 4];
+}
+
+static void raise4(double gi[4][4], const double* v, double* w)
+{
+    for (int m = 0; m < 4; ++m) {
+        w[m] = 0;
+        for (int n = 0; n < 4; ++n) w[m] += gi[m][n] * v[n];
+    }
+}
+
+/* Parallel transport of a covector along the geodesic:
+ * df_mu/dlambda = Gamma^alpha_{mu beta} k^beta f_alpha
+ *               = 1/2 f^alpha k^beta (d_mu g_{alpha beta} + d_beta g_{alpha mu} - d_alpha g_{mu beta}),
+ * with k^beta = dx^beta/dlambda; metric derivatives by complex steps. */
+static void transport_rhs(double a, double M, const double* x, const double* kup, const double* f,
+                          double* df)
+{
+    const double hstep = 1e-20;
+    double g[4][4], gi[4][4], dg[4][4][4], fup[4];
+    metric_cov(a, M, x, g);
+    inv4(g, gi);
+    raise4(gi, f, fup);
+    memset(dg, 0, sizeof dg);
+    for (int sdx = 1; sdx < 4; ++sdx) {
+        cplx xc[4], gc[4][4];
+        for (int m = 0; m < 4; ++m) xc[m] = x[m];
+        xc[sdx] += I * hstep;
+        metric_cov_c(a, M, xc, gc);
+        for (int m = 0; m < 4; ++m)
+            for (int n = 0; n < 4; ++n) dg[sdx][m][n] = cimag(gc[m][n]) / hstep;
+    }
+    for (int mu = 0; mu < 4; ++mu) {
+        double acc = 0;
+        for (int al = 0; al < 4; ++al)
+            for (int be = 0; be < 4; ++be)
+                acc += fup[al] * kup[be] * (dg[mu][al][be] + dg[be][al][mu] - dg[al][mu][be]);
+        df[mu] = 0.5 * acc;
+    }
+}
+
+/* Modified Bessel function of the second kind from its integral representation
+ * K_n(x) = int_0^inf exp(-x cosh t) cosh(n t) dt (Abramowitz & Stegun 9.6.24), by the trapezoid
+ * rule, which converges exponentially for this analytic, double-exponentially decaying integrand. */
+double orc_bessel_k(int n, double x)
+{
+    double T = acosh(1.0 + 60.0 / x) + 1.0, h = 1.0 / 64.0;
+    int m = (int)(T / h) + 1;
+    double s = 0.5 * exp(-x);
+    for (int i = 1; i <= m; ++i) {
+        double t = i * h;
+        s += exp(-x * cosh(t)) * cosh(n * t);
+    }
+    return s * h;
+}
+
+/* Thermal synchrotron coefficients in the frame whose Q axis is the emission's E-vector (normal
+ * to the projected field), cgs units, at frequency nu, for electron density ne, dimensionless
+ * temperature Th = kT/(m c^2), field B and angle theta_b between the wave vector and the field:
+ *   j_I: Leung, Gammie & Noble (2011): n sqrt2 pi e^2 nu_s / (3 K_2(1/Th) c)
+ *        (X^1/2 + 2^(11/12) X^1/6)^2 exp(-X^1/3), X = nu/nu_s, nu_s = (2/9) nu_B Th^2 sin theta,
+ *        nu_B = e B / (2 pi m c);
+ *   j_Q: the same with 2^(11/12) multiplied by (7 Th^0.96 + 35)/(10 Th^0.96 + 75)
+ *        (Pandya et al. 2016);
+ *   j_V = 0 (no intrinsic circular emission; V arises by Faraday conversion);
+ *   alpha_S = j_S / B_nu(T) (Kirchhoff);
+ *   rho_V = e^3 n B cos theta / (pi m^2 c^2 nu^2) K_0(1/Th)/K_2(1/Th),
+ *   rho_Q = e^4 n B^2 sin^2 theta / (4 pi^2 m^3 c^3 nu^3) (K_1(1/Th)/K_2(1/Th) + 6 Th)
+ *        (high-frequency thermal rotativities, e.g. Shcherbakov 2008; their cold-plasma limit is
+ *        the textbook rotation measure).
+ * out7 = {j_I, j_Q, j_V, alpha_I, alpha_Q, rho_Q, rho_V}. */
+int orc_synch_coeffs(double ne, double Th, double B, double nu, double thb, double* out)
+{
+    const double e = 4.80320471e-10, me = 9.1093837015e-28, c = 2.99792458e10;
+    const double hp = 6.62607015e-27;
+    for (int i = 0; i < 7; ++i) out[i] = 0.0;
+    if (!(ne > 0) || !(Th > 0) || !(B > 0) || !(nu > 0)) return 0;
+    double sn = sin(thb), cs = cos(thb);
+    double K0 = orc_bessel_k(0, 1.0 / Th), K1 = orc_bessel_k(1, 1.0 / Th), K2 = orc_bessel_k(2, 1.0 / Th);
+    double nuB = e * B / (2.0 * M_PI * me * c);
+    double Bnu = 2.0 * hp * nu * nu * nu / (c * c) / expm1(hp * nu / (Th * me * c * c));
+    if (fabs(sn) > 1e-12) {
+        double nus = 2.0 / 9.0 * nuB * Th * Th * fabs(sn);
+        double X = nu / nus;
+        double pre = ne * sqrt(2.0) * M_PI * e * e * nus / (3.0 * K2 * c) * exp(-cbrt(X));
+        double t96 = pow(Th, 24.0 / 25.0);
+        double q = (7.0 * t96 + 35.0) / (10.0 * t96 + 75.0);
+        double xa = sqrt(X), xb = pow(X, 1.0 / 6.0), k = pow(2.0, 11.0 / 12.0);
+        out[0] = pre * (xa + k * xb) * (xa + k * xb);
+        out[1] = pre * (xa + q * k * xb) * (xa + q * k * xb);
+    }
+    out[3] = out[0] / Bnu;
+    out[4] = out[1] / Bnu;
+    out[5] = e * e * e * e * ne * B * B * sn * sn / (4.0 * M_PI * M_PI * me * me * me * c * c * c * nu * nu * nu) *
+             (K1 / K2 + 6.0 * Th);
+    out[6] = e * e * e * ne * B * cs / (M_PI * me * me * c * c * nu * nu) * (K0 / K2);
+    return 0;
+}
+
+/* Exact solution over a segment of length h with constant coefficients of
+ * dS/ds = J - K S, K = [[aI,aQ,aU,aV],[aQ,aI,rV,-rU],[aU,-rV,aI,rQ],[aV,rU,-rQ,aI]]
+ * (Landi Degl'Innocenti & Landi Degl'Innocenti 1985 sign convention), K7 = {aI,aQ,aU,aV,rQ,rU,rV}:
+ * S(h) = E S(0) + X with E = exp(-K h), X = int_0^h exp(-K s) ds J, read off the exponential of
+ * the 5x5 augmented matrix [[-K h, J h], [0, 0]], computed by scaling and squaring with a
+ * Taylor series (Moler & Van Loan 2003). */
+void orc_segment(const double* K7, const double* J4, double h, double* E16, double* X4)
+{
+    double aI = K7[0], aQ = K7[1], aU = K7[2], aV = K7[3], rQ = K7[4], rU = K7[5], rV = K7[6];
+    double K[4][4] = {{aI, aQ, aU, aV}, {aQ, aI, rV, -rU}, {aU, -rV, aI, rQ}, {aV, rU, -rQ, aI}};
+    double A[5][5];
+    memset(A, 0, sizeof A);
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 4; ++j) A[i][j] = -K[i][j] * h;
+        A[i][4] = J4[i] * h;
+    }
+    double nrm = 0;
+    for (int i = 0; i < 5; ++i) {
+        double rs = 0;
+        for (int j = 0; j < 5; ++j) rs += fabs(A[i][j]);
+        if (rs > nrm) nrm = rs;
+    }
+    int sq = 0;
+    while (nrm > 0.125) { nrm *= 0.5; ++sq; }
+    double scale = ldexp(1.0, -sq);
+    double T[5][5], R[5][5], P[5][5];
+    for (int i = 0; i < 5; ++i)
+        for (int j = 0; j < 5; ++j) {
+            A[i][j] *= scale;
+            T[i][j] = (i == j) ? 1.0 : 0.0;
+            R[i][j] = T[i][j];
+        }
+    for (int k = 1; k <= 24; ++k) {
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) {
+                double v = 0;
+                for (int m = 0; m < 5; ++m) v += T[i][m] * A[m][j];
+                P[i][j] = v / k;
+            }
+        memcpy(T, P, sizeof T);
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) R[i][j] += T[i][j];
+    }
+    for (int q = 0; q < sq; ++q) {
+        for (int i = 0; i < 5; ++i)
+            for (int j = 0; j < 5; ++j) {
+                double v = 0;
+                for (int m = 0; m < 5; ++m) v += R[i][m] * R[m][j];
+                P[i][j] = v;
+            }
+        memcpy(R, P, sizeof R);
+    }
+    for (int i = 0; i < 4; ++i) {
+        for (int j = 0; j < 4; ++j) E16[4 * i + j] = R[i][j];
+        X4[i] = R[i][4];
+    }
+}
+
+/* Polarized emission at one point of the ray, in code units and in the polarization basis
+ * (e_N, e_E) carried by the transported covector f:  J4 = L j_S / nu^2 and
+ * K7 = L nu {alpha_I, alpha_Q, alpha_U, alpha_V, rho_Q, rho_U, rho_V}, with nu = k.u the fluid-frame
+ * frequency ratio and L = GM/c^2 in cm.  e_N is f projected normal to the fluid velocity u and
+ * to the propagation direction d = p/nu - u (p = -k); e_E = d x e_N in the fluid frame (at the
+ * camera: north = screen up, east = screen left, the IAU convention); the emission's E-vector
+ * d x b is at angle chi from e_N, so (Q, U) = P (cos 2 chi, sin 2 chi).
+ * Disk model: n_e = ne0 r^ne_slope exp(-cos^2(theta)/(2 w^2)), Th_e = thetae0 r^te_slope,
+ * |B| = b0 r^((ne_slope + te_slope)/2), direction (e_phi + q e_z)/sqrt(1 + q^2) in the fluid
+ * frame with q = bz_ratio (toroidal : vertical = 1 : q), Keplerian flow; zero inside r_in. */
+static void emission_pol(const orc_job* job, const double* y, const double* fcov, double* J4,
+                         double* K7)
+{
+    double a = job->a, M = job->mass;
+    for (int i = 0; i < 4; ++i) J4[i] = 0;
+    for (int i = 0; i < 7; ++i) K7[i] = 0;
+    double r = creal(ks_radius(a, y[1], y[2], y[3]));
+    double rstop = (1.0 + job->horizon_eps) * horizon_radius(a, M);
+    if (r < rstop || r < job->r_in) return;
+    double u[4];
+    if (!fluid_velocity(job, y, r, u)) return;
+    double ct = y[3] / r;
+    double ne = job->ne0 * pow(r, job->ne_slope) * exp(-ct * ct / (2.0 * job->disk_w * job->disk_w));
+    double Th = job->thetae0 * pow(r, job->te_slope);
+    double Bm = job->b0 * pow(r, 0.5 * (job->ne_slope + job->te_slope));
+    if (!(ne > 0)) return;
+    double g[4][4], gi[4][4];
+    metric_cov(a, M, y, g);
+    inv4(g, gi);
+    double kup[4], p[4], fup[4] = {0, 0, 0, 0};
+    raise4(gi, y + 4, kup);
+    if (fcov) raise4(gi, fcov, fup);
+    double nu = 0;
+    for (int m = 0; m < 4; ++m) nu += y[4 + m] * u[m];
+    if (!(nu > 0)) return;
+    double d[4];
+    for (int m = 0; m < 4; ++m) {
+        p[m] = -kup[m];
+        d[m] = p[m] / nu - u[m];
+    }
+    /* field direction: toroidal and vertical unit vectors of the fluid frame */
+    double vphi[4] = {0, -y[2], y[1], 0}, vz[4] = {0, 0, 0, 1}, ephi[4], ez[4], b[4];
+    double pu = dot_g(g, u, vphi);
+    for (int m = 0; m < 4; ++m) ephi[m] = vphi[m] + pu * u[m];
+    double nph = sqrt(dot_g(g, ephi, ephi));
+    for (int m = 0; m < 4; ++m) ephi[m] /= nph;
+    double pz = dot_g(g, u, vz), pe = dot_g(g, ephi, vz);
+    for (int m = 0; m < 4; ++m) ez[m] = vz[m] + pz * u[m] - pe * ephi[m];
+    double nz = sqrt(dot_g(g, ez, ez));
+    double bn = 1.0 / sqrt(1.0 + job->bz_ratio * job->bz_ratio);
+    for (int m = 0; m < 4; ++m) {
+        ez[m] /= nz;
+        b[m] = (ephi[m] + job->bz_ratio * ez[m]) * bn;
+    }
+    double cthb = dot_g(g, d, b);
+    if (cthb > 1) cthb = 1;
+    if (cthb < -1) cthb = -1;
+    double thb = acos(cthb);
+    if (!fcov) { /* unpolarized: total intensity only */
+        double co[7];
+        orc_synch_coeffs(ne, Th, Bm, job->nu_hz * nu, thb, co);
+        J4[0] = job->length_cm * co[0] / (nu * nu);
+        K7[0] = job->length_cm * nu * co[3];
+        return;
+    }
+    /* basis: e_N from f, e_E = d x e_N; E-vector of the emission: d x b */
+    double eN[4], fu = dot_g(g, fup, u), fd = dot_g(g, fup, d);
+    for (int m = 0; m < 4; ++m) eN[m] = fup[m] + fu * u[m] - fd * d[m];
+    double nN = sqrt(dot_g(g, eN, eN));
+    for (int m = 0; m < 4; ++m) eN[m] /= nN;
+    double eEc[4], eE[4], evc[4], ev[4];
+    for (int m = 0; m < 4; ++m) { eEc[m] = 0; evc[m] = 0; }
+    for (int m = 0; m < 4; ++m)
+        for (int n = 0; n < 4; ++n)
+            for (int q = 0; q < 4; ++q)
+                for (int w = 0; w < 4; ++w) {
+                    if (m == n || m == q || m == w || n == q || n == w || q == w) continue;
+                    /* sign of the permutation (m n q w) of (0 1 2 3) */
+                    int pidx[4] = {m, n, q, w}, sg = 1;
+                    for (int i = 0; i < 4; ++i)
+                        for (int j = i + 1; j < 4; ++j)
+                            if (pidx[i] > pidx[j]) sg = -sg;
+                    eEc[m] -= sg * u[n] * d[q] * eN[w];
+                    evc[m] -= sg * u[n] * d[q] * b[w];
+                }
+    raise4(gi, eEc, eE);
+    raise4(gi, evc, ev);
+    double nv = sqrt(dot_g(g, ev, ev));
+    double c1 = 0, s1 = 0;
+    if (nv > 0) {
+        c1 = dot_g(g, ev, eN) / nv;
+        s1 = dot_g(g, ev, eE) / nv;
+    }
+    double c2 = c1 * c1 - s1 * s1, s2 = 2.0 * c1 * s1;
+    double co[7];
+    orc_synch_coeffs(ne, Th, Bm, job->nu_hz * nu, thb, co);
+    double L = job->length_cm;
+    J4[0] = L * co[0] / (nu * nu);
+    J4[1] = L * co[1] * c2 / (nu * nu);
+    J4[2] = L * co[1] * s2 / (nu * nu);
+    J4[3] = L * co[2] / (nu * nu);
+    K7[0] = L * nu * co[3];
+    K7[1] = L * nu * co[4] * c2;
+    K7[2] = L * nu * co[4] * s2;
+    K7[3] = 0.0;
+    K7[4] = L * nu * co[5] * c2;
+    K7[5] = L * nu * co[5] * s2;
+    K7[6] = L * nu * co[6];
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Ray tracer                                                                                  */
 /* ------------------------------------------------------------------------------------------ */
 
-static void rk4_step(double a, double M, double h, const double* y, double* yn)
+/* Right-hand side of the ray ODE: y = (x^mu, k_mu[, f_mu]) with n = 8 (geodesic) or 12 (geodesic
+ * plus the parallel-transported polarization covector). */
+static void ray_rhs(double a, double M, int n, const double* y, double* dy)
 {
-    double k1[8], k2[8], k3[8], k4[8], t[8];
-    geodesic_rhs(a, M, y, k1);
-    for (int m = 0; m < 8; ++m) t[m] = y[m] + 0.5 * h * k1[m];
-    geodesic_rhs(a, M, t, k2);
-    for (int m = 0; m < 8; ++m) t[m] = y[m] + 0.5 * h * k2[m];
-    geodesic_rhs(a, M, t, k3);
-    for (int m = 0; m < 8; ++m) t[m] = y[m] + h * k3[m];
-    geodesic_rhs(a, M, t, k4);
-    for (int m = 0; m < 8; ++m) yn[m] = y[m] + h / 6.0 * (k1[m] + 2.0 * k2[m] + 2.0 * k3[m] + k4[m]);
+    geodesic_rhs(a, M, y, dy);
+    if (n == 12) transport_rhs(a, M, y, dy, y + 8, dy + 8);
+}
+
+static void rk4_step(double a, double M, int n, double h, const double* y, double* yn)
+{
+    double k1[12], k2[12], k3[12], k4[12], t[12];
+    ray_rhs(a, M, n, y, k1);
+    for (int m = 0; m < n; ++m) t[m] = y[m] + 0.5 * h * k1[m];
+    ray_rhs(a, M, n, t, k2);
+    for (int m = 0; m < n; ++m) t[m] = y[m] + 0.5 * h * k2[m];
+    ray_rhs(a, M, n, t, k3);
+    for (int m = 0; m < n; ++m) t[m] = y[m] + h * k3[m];
+    ray_rhs(a, M, n, t, k4);
+    for (int m = 0; m < n; ++m) yn[m] = y[m] + h / 6.0 * (k1[m] + 2.0 * k2[m] + 2.0 * k3[m] + k4[m]);
 }
 
 /* (1 - exp(-x))/x, continuous at 0. */
@@ -337,41 +649,80 @@ static int polar_sign(const double* y, double r)
     return q > tol ? 1 : (q < -tol ? -1 : 0);
 }
 
-/* Trace one ray backward from the camera.  out[] receives the planes of this ray. */
+/* Camera polarization reference: the screen's up vector e2 made normal to the pixel's line of
+ * sight n = s (-e1 + (alpha/r_obs) e3 + (beta/r_obs) e2), normalised and lowered. */
+static void camera_polbasis(const orc_job* job, const camera* c, double al, double be, double* fcov)
+{
+    double ro = job->r_obs;
+    double s = 1.0 / sqrt(1.0 + (al * al + be * be) / (ro * ro));
+    double en = s * be / ro, f[4];
+    for (int m = 0; m < 4; ++m) {
+        double n = s * (-c->e1[m] + (al / ro) * c->e3[m] + (be / ro) * c->e2[m]);
+        f[m] = c->e2[m] - en * n;
+    }
+    double nn = sqrt(dot_g((double(*)[4])c->g, f, f));
+    for (int m = 0; m < 4; ++m) f[m] /= nn;
+    for (int m = 0; m < 4; ++m) {
+        fcov[m] = 0;
+        for (int n = 0; n < 4; ++n) fcov[m] += c->g[m][n] * f[n];
+    }
+}
+
+/* Emission (J4) and absorption/rotation (K7) coefficients at one point, code units. */
+static void coefficients(const orc_job* job, const double* y, int pol, double* J4, double* K7)
+{
+    if (job->emission == ORC_EMIT_SYNCH_DISK) {
+        emission_pol(job, y, pol ? y + 8 : NULL, J4, K7);
+        return;
+    }
+    for (int i = 0; i < 4; ++i) J4[i] = 0;
+    for (int i = 0; i < 7; ++i) K7[i] = 0;
+    emission_unpol(job, y, &J4[0], &K7[0], NULL);
+}
+
+/* Trace one ray backward from the camera.  out[] receives the planes of this ray (Stokes inside
+ * subring index).  Per RK4 step, the coefficients at both ends are averaged and the segment is
+ * solved exactly; contributions are carried to the camera by the accumulated propagator. */
 static void trace_one(const orc_job* job, const camera* cam, double al, double be, double* out,
                       orc_rayinfo* info, double* rec, int maxrec, int* nrec)
 {
     double a = job->a, M = job->mass;
+    const int pol = job->stokes == 4;
+    const int n = pol ? 12 : 8;
+    const int nst = pol ? 4 : 1;
     int planes = orc_planes(job);
-    double y[8], yn[8];
+    double y[12], yn[12];
+    memset(y, 0, sizeof y);
     camera_ray(job, cam, al, be, y);
+    if (pol) camera_polbasis(job, cam, al, be, y + 8);
     for (int p = 0; p < planes; ++p) out[p] = 0.0;
     double rin = M > 0 ? (1.0 + job->horizon_eps) * horizon_radius(a, M) : 0.0;
     double rout = job->escape_frac * job->r_obs;
     double r = creal(ks_radius(a, y[1], y[2], y[3]));
-    double J0, A0, J1, A1;
-    emission_unpol(job, y, &J0, &A0, NULL);
-    double Iacc = 0.0, T = 1.0, lam_aff = 0.0;
+    double J0[4], K0[7], J1[4], K1[7];
+    coefficients(job, y, pol, J0, K0);
+    double T = 1.0, lam_aff = 0.0, Iacc = 0.0;
+    double P[16];
+    for (int i = 0; i < 16; ++i) P[i] = (i % 5 == 0) ? 1.0 : 0.0;
     double min_r = r;
     int nturn = 0, steps = 0, status = ORC_RAY_CAP;
     int theta_sign = polar_sign(y, r);
     if (rec && maxrec > 0) {
-        rec[0] = 0.0;
-        for (int m = 0; m < 8; ++m) rec[1 + m] = y[m];
-        rec[9] = 0.0;
+        memset(rec, 0, sizeof(double) * 14);
+        for (int m = 0; m < n; ++m) rec[1 + m] = y[m];
         *nrec = 1;
     }
     while (steps < job->max_steps) {
         double h = job->step_frac * r;
         if (h < job->h_min) h = job->h_min;
-        rk4_step(a, M, h, y, yn);
+        rk4_step(a, M, n, h, y, yn);
         ++steps;
         lam_aff += h;
         int finite = 1;
-        for (int m = 0; m < 8; ++m) finite &= isfinite(yn[m]);
+        for (int m = 0; m < n; ++m) finite &= isfinite(yn[m]);
         if (!finite) { status = ORC_RAY_NAN; break; }
         double rn = creal(ks_radius(a, yn[1], yn[2], yn[3]));
-        emission_unpol(job, yn, &J1, &A1, NULL);
+        coefficients(job, yn, pol, J1, K1);
         /* subring index of this segment: polar turning points before the segment starts */
         int seg_turn = nturn;
         int sg = polar_sign(yn, rn);
@@ -379,29 +730,56 @@ static void trace_one(const orc_job* job, const camera* cam, double al, double b
             if (theta_sign != 0 && sg != theta_sign) ++nturn;
             theta_sign = sg;
         }
-        /* trapezoid-averaged coefficients, exact constant-coefficient segment */
-        double Jb = 0.5 * (J0 + J1), Ab = 0.5 * (A0 + A1);
-        double dtau = Ab * h;
-        double dI = T * Jb * h * phi1(dtau);
-        Iacc += dI;
-        if (job->subrings > 0) out[seg_turn < job->subrings ? seg_turn : job->subrings - 1] += dI;
-        T *= exp(-dtau);
+        int plane0 = 0;
+        if (job->subrings > 0) plane0 = nst * (seg_turn < job->subrings ? seg_turn : job->subrings - 1);
+        if (!pol) {
+            /* trapezoid-averaged coefficients, exact constant-coefficient segment */
+            double Jb = 0.5 * (J0[0] + J1[0]), Ab = 0.5 * (K0[0] + K1[0]);
+            double dtau = Ab * h;
+            double dI = T * Jb * h * phi1(dtau);
+            Iacc += dI;
+            out[plane0] += dI;
+            T *= exp(-dtau);
+        } else {
+            double Jb[4], Kb[7], E[16], X[4];
+            for (int i = 0; i < 4; ++i) Jb[i] = 0.5 * (J0[i] + J1[i]);
+            for (int i = 0; i < 7; ++i) Kb[i] = 0.5 * (K0[i] + K1[i]);
+            int active = 0;
+            for (int i = 0; i < 4; ++i) active |= (Jb[i] != 0.0);
+            for (int i = 0; i < 7; ++i) active |= (Kb[i] != 0.0);
+            if (active) {
+                orc_segment(Kb, Jb, h, E, X);
+                double Pn[16];
+                for (int i = 0; i < 4; ++i) {
+                    double c = 0;
+                    for (int j = 0; j < 4; ++j) c += P[4 * i + j] * X[j];
+                    out[plane0 + i] += c;
+                    if (i == 0) Iacc += c;
+                    for (int j = 0; j < 4; ++j) {
+                        double v = 0;
+                        for (int m = 0; m < 4; ++m) v += P[4 * i + m] * E[4 * m + j];
+                        Pn[4 * i + j] = v;
+                    }
+                }
+                memcpy(P, Pn, sizeof P);
+            }
+        }
         memcpy(y, yn, sizeof y);
-        J0 = J1;
-        A0 = A1;
+        memcpy(J0, J1, sizeof J0);
+        memcpy(K0, K1, sizeof K0);
         r = rn;
         if (r < min_r) min_r = r;
         if (rec && *nrec < maxrec) {
-            double* row = rec + 10 * (*nrec);
+            double* row = rec + 14 * (*nrec);
+            memset(row, 0, sizeof(double) * 14);
             row[0] = lam_aff;
-            for (int m = 0; m < 8; ++m) row[1 + m] = y[m];
-            row[9] = Iacc;
+            for (int m = 0; m < n; ++m) row[1 + m] = y[m];
+            row[13] = Iacc;
             ++(*nrec);
         }
         if (r < rin) { status = ORC_RAY_CAPTURED; break; }
         if (r > rout) { status = ORC_RAY_ESCAPED; break; }
     }
-    if (job->subrings <= 0) out[0] = Iacc;
     if (info) {
         info->status = status;
         info->steps = steps;
@@ -416,7 +794,7 @@ static void trace_one(const orc_job* job, const camera* cam, double al, double b
 int orc_trace_screen(const orc_job* job, int n, const double* alpha, const double* beta,
                      double* out, orc_rayinfo* info)
 {
-    if (job->stokes != 1) return -2;
+    if (job->stokes != 1 && job->stokes != 4) return -2;
     camera cam;
     camera_setup(job, &cam);
     int planes = orc_planes(job);
@@ -450,6 +828,7 @@ int orc_trace_record(const orc_job* job, double alpha, double beta, int maxrec, 
     double out[64];
     orc_rayinfo info;
     *nrec = 0;
+    if (orc_planes(job) > 64) return -2;
     trace_one(job, &cam, alpha, beta, out, &info, rec, maxrec, nrec);
     return info.status;
 }
@@ -572,14 +951,16 @@ int orc_refine_level(const orc_job* job, double* img, uint8_t* mask, int nx, int
                      double norm, double* est_abs, double* est_rel)
 {
     if (level < 1 || level > job->levels) return -1;
+    const int planes = orc_planes(job);
+    const size_t npix = (size_t)nx * ny;
     int s = 1 << (job->levels - level);
     for (int j = 0; j < ny; j += s)
         for (int i = 0; i < nx; i += s) {
-            if (category(i, j, s) == 1) continue;
+            int cat = category(i, j, s);
+            if (cat == 1) continue;
             double interp, ea, er;
             int tr = estimate_point(job, img, nx, ny, i, j, s, norm, &interp, &ea, &er);
             if (job->edge_mode == ORC_EDGE_TRACE) {
-                int cat = category(i, j, s);
                 int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
                 if (i - 3 * di < 0 || i + 3 * di >= nx || j - 3 * dj < 0 || j + 3 * dj >= ny) tr = 1;
             }
@@ -588,9 +969,25 @@ int orc_refine_level(const orc_job* job, double* img, uint8_t* mask, int nx, int
             if (est_rel) est_rel[p] = er;
             if (tr) {
                 mask[p] = ORC_MASK_TRACED;
-            } else {
-                mask[p] = ORC_MASK_INTERP;
-                img[p] = interp;
+                continue;
+            }
+            mask[p] = ORC_MASK_INTERP;
+            img[p] = interp;
+            /* the other planes (Stokes Q, U, V; subrings) take the same interpolation weights */
+            for (int c = 1; c < planes; ++c) {
+                const double* pl = img + c * npix;
+                double v;
+                if (job->interp == ORC_INTERP_NEAREST) {
+                    v = (cat == 4) ? pl[(size_t)(j - s) * nx + (i - s)]
+                                   : pl[(size_t)(j - (cat == 2 ? s : 0)) * nx + (i - (cat == 3 ? s : 0))];
+                } else if (cat == 4) {
+                    v = 0.25 * (pl[(size_t)(j - s) * nx + (i - s)] + pl[(size_t)(j + s) * nx + (i - s)] +
+                                pl[(size_t)(j - s) * nx + (i + s)] + pl[(size_t)(j + s) * nx + (i + s)]);
+                } else {
+                    int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
+                    v = 0.5 * (pl[(size_t)(j - dj) * nx + (i - di)] + pl[(size_t)(j + dj) * nx + (i + di)]);
+                }
+                img[c * npix + p] = v;
             }
         }
     return 0;
@@ -603,12 +1000,13 @@ int orc_render(const orc_job* job, const double* truth, double* img, uint8_t* ma
 {
     int nx, ny;
     if (orc_image_size(job, &nx, &ny)) return -1;
-    if (job->stokes != 1 || job->subrings > 0) return -2;
+    if (job->stokes != 1 && job->stokes != 4) return -2;
+    const int planes = orc_planes(job);
     size_t npix = (size_t)nx * ny;
     memset(mask, 0, npix);
-    for (size_t p = 0; p < npix; ++p) img[p] = 0.0;
+    for (size_t p = 0; p < npix * planes; ++p) img[p] = 0.0;
     int64_t* list = malloc(sizeof(int64_t) * npix);
-    double* vals = malloc(sizeof(double) * npix);
+    double* vals = malloc(sizeof(double) * npix * planes);
     orc_rayinfo* info = malloc(sizeof(orc_rayinfo) * npix);
     orc_stats st;
     memset(&st, 0, sizeof st);
@@ -628,13 +1026,14 @@ int orc_render(const orc_job* job, const double* truth, double* img, uint8_t* ma
                 }
         }
         if (truth) {
-            for (int64_t q = 0; q < n; ++q) vals[q] = truth[list[q]];
+            for (int64_t q = 0; q < n; ++q)
+                for (int c = 0; c < planes; ++c) vals[q * planes + c] = truth[c * npix + list[q]];
         } else {
             rc = orc_trace_pixels(job, (int)n, list, vals, info);
             for (int64_t q = 0; q < n && rc == 0; ++q) st.steps += info[q].steps;
         }
         for (int64_t q = 0; q < n; ++q) {
-            img[list[q]] = vals[q];
+            for (int c = 0; c < planes; ++c) img[c * npix + list[q]] = vals[q * planes + c];
             mask[list[q]] = ORC_MASK_TRACED;
         }
         st.rays_traced += n;
@@ -642,7 +1041,7 @@ int orc_render(const orc_job* job, const double* truth, double* img, uint8_t* ma
         if (level == 0) {
             if (job->abs_norm == ORC_NORM_PEAK) {
                 st.ibar = -INFINITY;
-                for (int64_t q = 0; q < n; ++q) st.ibar = fmax(st.ibar, vals[q]);
+                for (int64_t q = 0; q < n; ++q) st.ibar = fmax(st.ibar, vals[q * planes]);
             } else {
                 st.ibar = orc_ibar_int(img, nx, ny, S0);
             }

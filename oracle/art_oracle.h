@@ -50,6 +50,8 @@ typedef struct orc_job {
     double blob_sigma;   /* flat-space blob width */
     /* thermal-synchrotron disk (ORC_EMIT_SYNCH_DISK) */
     double ne0, thetae0, b0, nu_hz, ne_slope, te_slope, r_in;
+    double length_cm;    /* GM/c^2 in cm (converts affine lengths to cm) */
+    double bz_ratio;     /* vertical / toroidal field ratio of the disk (1 = 1:1) */
 } orc_job;
 
 typedef struct orc_rayinfo {
@@ -73,6 +75,10 @@ int    orc_trace_pixels(const orc_job* job, int n, const int64_t* pix, double* o
                         orc_rayinfo* info);
 int    orc_trace_record(const orc_job* job, double alpha, double beta, int maxrec,
                         double* rec, int* nrec);
+double orc_bessel_k(int n, double x);
+int    orc_synch_coeffs(double ne, double thetae, double B, double nu, double theta_b,
+                        double* out7);
+void   orc_segment(const double* K7, const double* J4, double h, double* E16, double* X4);
 int    orc_emission(const orc_job* job, const double* x, const double* k, double* jnu,
                     double* nu_fl);
 double orc_ibar_int(const double* img, int nx, int ny, int stride);

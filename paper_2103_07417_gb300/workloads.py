@@ -26,7 +26,7 @@ BASE = dict(a=0.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33, n0y=33, levels
             emission="cfg0", flow="kepler", stokes=1, subrings=0, precision="fp64",
             max_steps=100000, step_frac=0.05, h_min=1e-4, horizon_eps=0.01, escape_frac=1.01,
             disk_w=0.3, blob_sigma=1.0, ne0=0.0, thetae0=0.0, b0=0.0, nu_hz=230e9,
-            ne_slope=-1.1, te_slope=-0.84, r_in=0.0)
+            ne_slope=-1.1, te_slope=-0.84, r_in=0.0, length_cm=9.6e14, bz_ratio=1.0)
 
 
 def job(**over) -> dict:
@@ -89,6 +89,28 @@ def fbm(seed: int, n: int, hurst: float) -> np.ndarray:
     w = np.fft.fft(np.sqrt(lam / m) * z)
     fgn = w.real[:n]
     return np.concatenate([[0.0], np.cumsum(fgn)])
+
+
+def r_isco(a: float) -> float:
+    """Prograde innermost stable circular orbit (Bardeen, Press & Teukolsky 1972)."""
+    z1 = 1 + (1 - a * a) ** (1 / 3) * ((1 + a) ** (1 / 3) + (1 - a) ** (1 / 3))
+    z2 = (3 * a * a + z1 * z1) ** 0.5
+    return 3 + z2 - ((3 - z1) * (3 + z1 + 2 * z2)) ** 0.5 * (1 if a >= 0 else -1)
+
+
+def cfg1(**over) -> dict:
+    """Kerr a = 0.94, inclination 17 deg, FOV 40 M; thermal-synchrotron thin disk
+    (n_e ~ r^-1.1, T_e ~ r^-0.84, toroidal : vertical field = 1 : 1, |B| ~ r^-0.97, Gaussian
+    vertical profile of width 0.1 r, Keplerian, inner edge at the ISCO) at 230 GHz for an M87*-mass
+    hole (GM/c^2 = 9.6e14 cm), normalised to n_e = 1e5 cm^-3, Theta_e = 20, |B| = 5 G at r = 5 M
+    (optical and Faraday depths of order unity through the disk); polarized IQUV transfer with
+    Faraday rotation and conversion; 129^2 -> 2049^2 over 4 levels, R_rel = R_abs = 1e-3."""
+    return job(**{**dict(a=0.94, incl_deg=17.0, fov=40.0, n0x=129, n0y=129, levels=4,
+                         R_rel=1e-3, R_abs=1e-3, abs_norm="ibar_int", emission="synch_disk",
+                         stokes=4, disk_w=0.1, ne0=1e5 * 5 ** 1.1, thetae0=20.0 * 5 ** 0.84,
+                         b0=5.0 * 5 ** 0.97, nu_hz=230e9, ne_slope=-1.1, te_slope=-0.84,
+                         r_in=r_isco(0.94), length_cm=9.6e14, bz_ratio=1.0,
+                         precision="mixed_df"), **over})
 
 
 def cfg1_analytic(**over) -> dict:

@@ -221,7 +221,7 @@ def test_flat_space_inverse_square(rho):
     b, s0 = _flat_impact(r_obs, rho)
     s_end = np.linalg.norm(rec[-1, 2:5] - rec[0, 2:5])
     expect = (np.arctan((s_end - s0) / b) + np.arctan(s0 / b)) / b
-    assert rec[-1, 9] == pytest.approx(expect, rel=2e-5)
+    assert rec[-1, 13] == pytest.approx(expect, rel=2e-5)
 
 
 def test_keplerian_redshift_schwarzschild():
