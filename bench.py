@@ -33,6 +33,10 @@ from paper_2103_07417_gb300 import workloads as W  # noqa: E402
 # The double-float re-trace counts the same 550 algorithmic flops per step (each carried out as
 # a double-float operation of several FP32 instructions).
 FLOPS_PER_STEP = {"trace_fp64": 550, "trace_fp32": 578, "trace_df": 550}
+# Polarized synchrotron steps, counted from the kernel's formulas (+-10 %): the geodesic (495),
+# parallel transport of the polarization covector at the 4 RK4 stages plus its update (1332), the
+# synchrotron coefficients in the fluid frame (590) and the exact Stokes segment (590).
+FLOPS_PER_STEP_POL = {"trace_fp64": 3007, "trace_fp32": 3035, "trace_df": 3007}
 # Peaks for "alu"-bound kernels: FP32 = 152 SMs x 128 lanes x 2 flops x 2.07 GHz; FP64 = the
 # GB300's nominal dense FP64 rate.
 PEAK_TFLOPS = {"trace_fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "trace_fp64": 1.25,
@@ -50,8 +54,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg1_analytic", choices=sorted(W.BENCH_WORKLOADS))
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df", "fp64", "fp32"])
+    ap.add_argument("--workload", default="cfg1", choices=sorted(W.BENCH_WORKLOADS))
+    ap.add_argument("--precision", default="mixed_df", choices=["mixed", "mixed_df", "fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--single", action="store_true",
                     help="one warm-up and one render, nothing else (for profiler captures)")
@@ -110,40 +114,79 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(params: dict, sample_note: str):
+def _base_pixels(params: dict, limit: int | None = None):
+    """Pixel indices of the base grid of the workload (optionally an evenly spaced subset)."""
+    import numpy as np
+    levels = params["levels"]
+    s0 = 1 << levels
+    nx = s0 * (params["n0x"] - 1) + 1
+    jj, ii = np.mgrid[0:params["n0y"], 0:params["n0x"]]
+    pix = (jj * s0 * nx + ii * s0).ravel().astype(np.int64)
+    if limit is not None and pix.size > limit:
+        pix = pix[np.linspace(0, pix.size - 1, limit).astype(np.int64)]
+    return pix
+
+
+def cpu_baseline(params: dict):
+    """The FP64 oracle on the host cores.  Unpolarized workloads: one full adaptive render.
+    Polarized ones (several ms of oracle time per ray): the whole base level of the workload."""
     import oracle as O
     job = O.make_job(**params)
-    t0 = time.perf_counter()
-    img, mask, st = O.render(job, None)
-    dt = time.perf_counter() - t0
-    return {"value": st["rays_traced"] / dt, "unit": "rays/s", "cores": O.get_threads(),
-            "kind": "oracle", "sample": sample_note, "seconds": dt,
-            "rays": int(st["rays_traced"]), "steps_per_s": st["steps"] / dt}
+    if params.get("stokes", 1) == 4:
+        pix = _base_pixels(params)
+        t0 = time.perf_counter()
+        _, info = O.trace_pixels(job, pix)
+        dt = time.perf_counter() - t0
+        rays, steps = pix.size, int(info["steps"].sum())
+        note = f"the {params['n0x']}x{params['n0y']} base level of the workload ({rays} rays)"
+    else:
+        t0 = time.perf_counter()
+        img, mask, st = O.render(job, None)
+        dt = time.perf_counter() - t0
+        rays, steps = int(st["rays_traced"]), int(st["steps"])
+        note = "one full adaptive render of the workload"
+    return {"value": rays / dt, "unit": "rays/s", "cores": O.get_threads(), "kind": "oracle",
+            "sample": note + " by the FP64 oracle (OpenMP over rays, all host cores)",
+            "seconds": dt, "rays": rays, "steps_per_s": steps / dt}
 
 
 def run_reference(args, params, desc):
+    """The reference arm: the FP64 oracle on the host cores.  Each step is a bounded sample of the
+    workload: one full adaptive render (unpolarized) or 2048 evenly spaced base-level rays
+    (polarized), so the whole run stays within a few minutes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle as O
     job = O.make_job(**params)
+    pol = params.get("stokes", 1) == 4
+    pix = _base_pixels(params, 2048) if pol else None
+
+    def step():
+        if pol:
+            _, info = O.trace_pixels(job, pix)
+            return pix.size, int(info["steps"].sum())
+        _, _, st = O.render(job, None)
+        return st["rays_traced"], st["steps"]
+
     for _ in range(args.warmup):
-        O.render(job, None)
+        step()
     times, rays, steps = [], 0, 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        _, _, st = O.render(job, None)
+        rays, steps = step()
         times.append(time.perf_counter() - t0)
-        rays, steps = st["rays_traced"], st["steps"]
     total = sum(times)
     value = rays * args.steps / total
+    sample = ("2048 evenly spaced base-level rays per step" if pol
+              else "one full adaptive render per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "name": args.workload},
             "cpu_baseline": {"value": value, "unit": "rays/s", "cores": O.get_threads(),
-                             "kind": "oracle", "sample": "one full adaptive render per step"},
+                             "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0},
             "geodesic_steps_per_s": steps * args.steps / total}
@@ -153,8 +196,7 @@ def run_reference(args, params, desc):
 def main():
     args = parse()
     desc, fn = W.BENCH_WORKLOADS[args.workload]
-    params = fn(precision=args.precision) if args.workload != "cfg0" else fn(
-        precision=args.precision)
+    params = fn(precision=args.precision)
     if args.impl == "reference":
         return run_reference(args, params, desc)
 
@@ -232,9 +274,10 @@ def main():
     dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
     total_ms = sum(v["ms"] for v in by_kind.values())
     roofline = None
-    if dom in FLOPS_PER_STEP:
+    fps = FLOPS_PER_STEP_POL if params.get("stokes", 1) == 4 else FLOPS_PER_STEP
+    if dom in fps:
         d = by_kind[dom]
-        achieved = d["steps"] * FLOPS_PER_STEP[dom] / (d["ms"] / 1000.0) / 1e12
+        achieved = d["steps"] * fps[dom] / (d["ms"] / 1000.0) / 1e12
         peak = PEAK_TFLOPS[dom]
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
@@ -279,8 +322,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(params, "one full adaptive render of the same workload by the FP64 "
-                                   "oracle (OpenMP over rays, all host cores)")
+        cpu = cpu_baseline(params)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,

@@ -69,7 +69,7 @@ typedef struct art_job {
     int32_t edge_mode;   /* ART_EDGE_ONESIDED or ART_EDGE_TRACE (trace points lacking a stencil) */
     int32_t emission;    /* ART_EMIT_* */
     int32_t flow;        /* ART_FLOW_* */
-    int32_t stokes;      /* 1 (unpolarized) */
+    int32_t stokes;      /* 1 (unpolarized) or 4 (I, Q, U, V; ART_EMIT_SYNCH_DISK) */
     int32_t subrings;    /* 0, or the number of subring planes n = 0..subrings-1 */
     int32_t precision;   /* ART_FP64; ART_MIXED: FP32 with an FP64 re-trace of near-critical rays;
                           * ART_MIXED_DF: the same with the re-traced geodesic in double-float
@@ -83,7 +83,12 @@ typedef struct art_job {
     double h_min;        /* floor of h */
     double horizon_eps;  /* stop rays at r < (1 + horizon_eps) r_+ */
     double escape_frac;  /* stop rays at r > escape_frac * r_obs */
-    double disk_w;       /* ART_EMIT_CFG0: vertical Gaussian width as a fraction of r */
+    double disk_w;       /* vertical Gaussian width of the emitter as a fraction of r */
+    /* ART_EMIT_SYNCH_DISK: thermal-synchrotron thin disk, n_e = ne0 r^ne_slope
+     * exp(-cos^2(theta)/(2 disk_w^2)) [cm^-3], Theta_e = thetae0 r^te_slope, |B| = b0
+     * r^((ne_slope + te_slope)/2) [G] along (e_phi + bz_ratio e_z) in the fluid frame, Keplerian,
+     * no emission inside r_in; observed at nu_hz for a hole with GM/c^2 = length_cm. */
+    double ne0, thetae0, b0, nu_hz, ne_slope, te_slope, r_in, length_cm, bz_ratio;
 } art_job;
 
 /* Statistics of one render (host struct, filled on return). */

@@ -137,6 +137,8 @@ def _load():
             lib.orc_bessel_k.restype = ctypes.c_double
             lib.orc_synch_coeffs.argtypes = [ctypes.c_double] * 5 + [dp]
             lib.orc_segment.argtypes = [dp, dp, ctypes.c_double, dp, dp]
+            lib.orc_transport_rhs.argtypes = [P(Job), dp, dp]
+            lib.orc_coefficients.argtypes = [P(Job), dp, ctypes.c_int, dp, dp]
             _lib = lib
     return _lib
 
@@ -265,6 +267,22 @@ def synch_coeffs(ne, thetae, B, nu, theta_b):
     _load().orc_synch_coeffs(float(ne), float(thetae), float(B), float(nu), float(theta_b),
                              _ptr(out))
     return out
+
+
+def transport_rhs(job: Job, y12):
+    """d f_mu / d lambda of the parallel-transported covector for state (x, k, f)."""
+    y = np.ascontiguousarray(y12, dtype=np.float64)
+    df = np.zeros(4)
+    _load().orc_transport_rhs(ctypes.byref(job), _ptr(y), _ptr(df))
+    return df
+
+
+def coefficients(job: Job, y12, pol: bool = True):
+    """(J4, K7) emission and absorption/rotation coefficients at state (x, k, f), code units."""
+    y = np.ascontiguousarray(y12, dtype=np.float64)
+    J4, K7 = np.zeros(4), np.zeros(7)
+    _load().orc_coefficients(ctypes.byref(job), _ptr(y), int(pol), _ptr(J4), _ptr(K7))
+    return J4, K7
 
 
 def segment(K7, J4, h):

@@ -539,6 +539,10 @@ static void emission_pol(const orc_job* job, const double* y, const double* fcov
         p[m] = -kup[m];
         d[m] = p[m] / nu - u[m];
     }
+    /* the propagation direction is a unit vector of the fluid frame; the integrated k is null only
+     * to the RK4 truncation error, so normalise it */
+    double dn = sqrt(dot_g(g, d, d));
+    for (int m = 0; m < 4; ++m) d[m] /= dn;
     /* field direction: toroidal and vertical unit vectors of the fluid frame */
     double vphi[4] = {0, -y[2], y[1], 0}, vz[4] = {0, 0, 0, 1}, ephi[4], ez[4], b[4];
     double pu = dot_g(g, u, vphi);
@@ -678,6 +682,19 @@ static void coefficients(const orc_job* job, const double* y, int pol, double* J
     for (int i = 0; i < 4; ++i) J4[i] = 0;
     for (int i = 0; i < 7; ++i) K7[i] = 0;
     emission_unpol(job, y, &J4[0], &K7[0], NULL);
+}
+
+/* Exported for tests: transport derivative and point coefficients of a 12-component state. */
+void orc_transport_rhs(const orc_job* job, const double* y, double* df)
+{
+    double dy[8];
+    geodesic_rhs(job->a, job->mass, y, dy);
+    transport_rhs(job->a, job->mass, y, dy, y + 8, df);
+}
+
+void orc_coefficients(const orc_job* job, const double* y, int pol, double* J4, double* K7)
+{
+    coefficients(job, y, pol, J4, K7);
 }
 
 /* Trace one ray backward from the camera.  out[] receives the planes of this ray (Stokes inside

@@ -79,6 +79,8 @@ double orc_bessel_k(int n, double x);
 int    orc_synch_coeffs(double ne, double thetae, double B, double nu, double theta_b,
                         double* out7);
 void   orc_segment(const double* K7, const double* J4, double h, double* E16, double* X4);
+void   orc_transport_rhs(const orc_job* job, const double* y12, double* df4);
+void   orc_coefficients(const orc_job* job, const double* y12, int pol, double* J4, double* K7);
 int    orc_emission(const orc_job* job, const double* x, const double* k, double* jnu,
                     double* nu_fl);
 double orc_ibar_int(const double* img, int nx, int ny, int stride);

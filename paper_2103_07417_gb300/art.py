@@ -41,7 +41,10 @@ class Job(ctypes.Structure):
         ("max_steps", ctypes.c_int32), ("fp64_sweep", ctypes.c_double),
         ("step_frac", ctypes.c_double), ("h_min", ctypes.c_double),
         ("horizon_eps", ctypes.c_double), ("escape_frac", ctypes.c_double),
-        ("disk_w", ctypes.c_double),
+        ("disk_w", ctypes.c_double), ("ne0", ctypes.c_double), ("thetae0", ctypes.c_double),
+        ("b0", ctypes.c_double), ("nu_hz", ctypes.c_double), ("ne_slope", ctypes.c_double),
+        ("te_slope", ctypes.c_double), ("r_in", ctypes.c_double), ("length_cm", ctypes.c_double),
+        ("bz_ratio", ctypes.c_double),
     ]
 
 

@@ -16,7 +16,7 @@ struct art_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
-    int occ64 = 0, occ32 = 0, occdf = 0;
+    int occ[3][2] = {};  // resident blocks per SM of the trace kernels [kind][polarized]
     // scratch owned by the library
     int32_t* queue = nullptr;
     int32_t* reroute = nullptr;
@@ -122,9 +122,15 @@ static int make_devjob(const art_job* job, DevJob* J)
     if (!(job->step_frac > 0.0 && job->step_frac <= 0.5) || !(job->h_min > 0.0)) return ART_ERR_ARG;
     if (job->max_steps < 1 || !(job->escape_frac > 1.0) || !(job->horizon_eps >= 0.0))
         return ART_ERR_ARG;
-    if (job->stokes != 1) return ART_ERR_UNSUPPORTED;
+    if (job->stokes != 1 && job->stokes != 4) return ART_ERR_UNSUPPORTED;
     if (job->subrings < 0 || job->subrings > 4) return ART_ERR_UNSUPPORTED;
-    if (job->emission != ART_EMIT_CFG0) return ART_ERR_UNSUPPORTED;
+    if (job->emission != ART_EMIT_CFG0 && job->emission != ART_EMIT_SYNCH_DISK)
+        return ART_ERR_UNSUPPORTED;
+    if (job->stokes == 4 && job->emission != ART_EMIT_SYNCH_DISK) return ART_ERR_UNSUPPORTED;
+    if (job->emission == ART_EMIT_SYNCH_DISK &&
+        (!(job->ne0 >= 0.0) || !(job->thetae0 > 0.0) || !(job->b0 > 0.0) || !(job->nu_hz > 0.0) ||
+         !(job->length_cm > 0.0) || !(job->r_in >= 0.0)))
+        return ART_ERR_ARG;
     if (job->flow != ART_FLOW_KEPLER && job->flow != ART_FLOW_STATIC) return ART_ERR_ARG;
     if (job->interp != ART_INTERP_LINEAR && job->interp != ART_INTERP_NEAREST) return ART_ERR_ARG;
     if (job->edge_mode != ART_EDGE_ONESIDED && job->edge_mode != ART_EDGE_TRACE) return ART_ERR_ARG;
@@ -160,8 +166,36 @@ static int make_devjob(const art_job* job, DevJob* J)
     return ART_OK;
 }
 
+// Constants of the synchrotron disk in the scaled form the kernels use (cgs constants, CODATA).
+static void make_synch(const art_job* job, SynchConst* S)
+{
+    const double e = 4.80320471e-10, me = 9.1093837015e-28, c = 2.99792458e10;
+    const double hp = 6.62607015e-27, pi = 3.14159265358979323846;
+    memset(S, 0, sizeof *S);
+    if (job->emission != ART_EMIT_SYNCH_DISK) return;
+    const double L = job->length_cm, nu = job->nu_hz;
+    S->ne0 = job->ne0;
+    S->th0 = job->thetae0;
+    S->b0 = job->b0;
+    S->ne_s = job->ne_slope;
+    S->te_s = job->te_slope;
+    S->b_s = 0.5 * (job->ne_slope + job->te_slope);
+    S->inv_2w2 = 1.0 / (2.0 * job->disk_w * job->disk_w);
+    S->r_in = job->r_in;
+    S->bz = job->bz_ratio;
+    S->bnorm = 1.0 / sqrt(1.0 + job->bz_ratio * job->bz_ratio);
+    S->LCj = L * sqrt(2.0) * pi * e * e / (3.0 * c);
+    S->CB = e / (2.0 * pi * me * c);
+    S->nu_obs = nu;
+    S->xB = hp * nu / (me * c * c);
+    S->invKB = c * c / (2.0 * hp * nu * nu * nu);
+    S->LCV = L * e * e * e / (pi * me * me * c * c * nu * nu);
+    S->LCQ = L * e * e * e * e / (4.0 * pi * pi * me * me * me * c * c * c * nu * nu * nu);
+}
+
 // The same validation for the allocation-free entry point (noalloc.cu).
 int art_make_devjob(const art_job* job, DevJob* J) { return make_devjob(job, J); }
+void art_make_synch(const art_job* job, SynchConst* S) { make_synch(job, S); }
 
 extern "C" int art_create(art_ctx** out, int device, void* stream)
 {
@@ -173,16 +207,18 @@ extern "C" int art_create(art_ctx** out, int device, void* stream)
     art_ctx* c = new art_ctx();
     c->device = device;
     c->stream = (cudaStream_t)stream;
-    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        trace_occupancy(TK_FP64, &c->occ64) != cudaSuccess ||
-        trace_occupancy(TK_FP32, &c->occ32) != cudaSuccess ||
-        trace_occupancy(TK_DF, &c->occdf) != cudaSuccess) {
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
         delete c;
         return ART_ERR_CUDA;
     }
-    if (c->occ64 < 1) c->occ64 = 1;
-    if (c->occ32 < 1) c->occ32 = 1;
-    if (c->occdf < 1) c->occdf = 1;
+    for (int kd = 0; kd < 3; ++kd)
+        for (int pl = 0; pl < 2; ++pl) {
+            if (trace_occupancy(TraceKind(kd), pl != 0, &c->occ[kd][pl]) != cudaSuccess) {
+                delete c;
+                return ART_ERR_CUDA;
+            }
+            if (c->occ[kd][pl] < 1) c->occ[kd][pl] = 1;
+        }
     *out = c;
     return ART_OK;
 }
@@ -250,12 +286,14 @@ static int64_t max_level_rays(const DevJob& J)
 }
 
 // Trace the rays of the queue (length in counters[count_idx]) with the job's precision.
-static int trace_queue(art_ctx* c, const DevJob& J, const unsigned long long* count, double* img,
-                       uint8_t* mask, double* out, const art_rayaux* aux)
+static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
+                       const unsigned long long* count, double* img, uint8_t* mask, double* out,
+                       const art_rayaux* aux)
 {
     TraceArgs a;
     memset(&a, 0, sizeof a);
     a.job = J;
+    make_synch(job, &a.synch);
     a.cam = c->cam;
     a.queue = c->queue;
     a.count = count;
@@ -270,8 +308,9 @@ static int trace_queue(art_ctx* c, const DevJob& J, const unsigned long long* co
         a.aux_nturn = aux->nturn;
         a.aux_minr = aux->min_r;
     }
-    const int g64 = c->num_sms * c->occ64, g32 = c->num_sms * c->occ32;
-    const int gdf = c->num_sms * c->occdf;
+    const int pl = J.stokes == 4 ? 1 : 0;
+    const int g64 = c->num_sms * c->occ[TK_FP64][pl], g32 = c->num_sms * c->occ[TK_FP32][pl];
+    const int gdf = c->num_sms * c->occ[TK_DF][pl];
     int k;
     if (J.precision == ART_FP64) {
         a.fetch = c->counters + C_FETCH;
@@ -335,7 +374,7 @@ extern "C" int art_trace_pixels(art_ctx* c, const art_job* job, const int32_t* p
     int k = prof_begin(c);
     CK(launch_camera_setup(*job, c->cam, c->stream));
     prof_end(c, k, ART_K_OTHER, 1);
-    if ((rc = trace_queue(c, J, c->counters + C_QUEUE, nullptr, nullptr, out_dev, aux))) return rc;
+    if ((rc = trace_queue(c, job, J, c->counters + C_QUEUE, nullptr, nullptr, out_dev, aux))) return rc;
     if ((rc = read_counters(c))) return rc;
     if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
     return ART_OK;
@@ -422,7 +461,8 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
                                    cap, st));
             prof_end(c, k, ART_K_OTHER, -1);
         } else {
-            if ((rc = trace_queue(c, J, c->counters + C_QUEUE, img_dev, mask_dev, nullptr, nullptr)))
+            if ((rc = trace_queue(c, job, J, c->counters + C_QUEUE, img_dev, mask_dev, nullptr,
+                                  nullptr)))
                 return rc;
         }
         if (level == 0) {

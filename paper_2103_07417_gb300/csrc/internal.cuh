@@ -6,6 +6,7 @@
 
 #include "../../include/art.h"
 #include "kerr.cuh"
+#include "synch.cuh"
 
 namespace art {
 
@@ -26,6 +27,7 @@ enum Counter {
 
 struct TraceArgs {
     DevJob job;
+    SynchConst synch;
     const Camera* cam;
     const int32_t* queue;           // pixel indices
     const int32_t* indirect;        // nullable: slot -> queue position (re-trace pass)
@@ -48,7 +50,7 @@ struct TraceArgs {
 enum TraceKind { TK_FP64 = 0, TK_FP32 = 1, TK_DF = 2 };
 cudaError_t launch_camera_setup(const art_job& job, Camera* cam, cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, TraceKind kind, int grid, cudaStream_t st);
-cudaError_t trace_occupancy(TraceKind kind, int* blocks_per_sm);
+cudaError_t trace_occupancy(TraceKind kind, bool pol, int* blocks_per_sm);
 constexpr int TRACE_BLOCK = 128;
 
 // refine.cu

@@ -40,7 +40,8 @@ struct DeviceSlot {
     std::once_flag once;
     int rc = ART_ERR_CUDA;
     unsigned char* ptr = nullptr;  // device address of art_noalloc_scratch on that device
-    int num_sms = 0, occ64 = 0, occ32 = 0, occdf = 0;
+    int num_sms = 0;
+    int occ[3][2] = {};  // resident blocks per SM [kind][polarized]
 };
 DeviceSlot g_slots[MAX_DEVICES];
 
@@ -55,25 +56,29 @@ void setup_device(int dev)
         s.rc = ART_ERR_CUDA;
         return;
     }
-    if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        trace_occupancy(TK_FP64, &s.occ64) != cudaSuccess ||
-        trace_occupancy(TK_FP32, &s.occ32) != cudaSuccess ||
-        trace_occupancy(TK_DF, &s.occdf) != cudaSuccess) {
+    if (cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         s.rc = ART_ERR_CUDA;
         return;
     }
-    if (s.occ64 < 1) s.occ64 = 1;
-    if (s.occ32 < 1) s.occ32 = 1;
-    if (s.occdf < 1) s.occdf = 1;
+    for (int kd = 0; kd < 3; ++kd)
+        for (int pl = 0; pl < 2; ++pl) {
+            if (trace_occupancy(TraceKind(kd), pl != 0, &s.occ[kd][pl]) != cudaSuccess) {
+                cudaGetLastError();
+                s.rc = ART_ERR_CUDA;
+                return;
+            }
+            if (s.occ[kd][pl] < 1) s.occ[kd][pl] = 1;
+        }
     s.ptr = static_cast<unsigned char*>(p);
     s.rc = ART_OK;
 }
 
 }  // namespace
 
-// Job validation shared with the context path lives in capi.cu.
+// Job validation and synchrotron constants shared with the context path live in capi.cu.
 int art_make_devjob(const art_job* job, DevJob* J);
+void art_make_synch(const art_job* job, SynchConst* S);
 
 extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_dev, int64_t n,
                                         double* out_dev, const art_rayaux* aux, void* stream)
@@ -107,6 +112,7 @@ extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_d
     TraceArgs a;
     memset(&a, 0, sizeof a);
     a.job = J;
+    art_make_synch(job, &a.synch);
     a.cam = cam;
     a.queue = pix_dev;
     a.count = counters + C_QUEUE;
@@ -126,8 +132,9 @@ extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_d
         a.reroute = reroute;
         a.reroute_count = counters + C_REROUTE;
     }
+    const int pl = J.stokes == 4 ? 1 : 0;
     if (launch_trace(a, fp32_first ? TK_FP32 : TK_FP64,
-                     s.num_sms * (fp32_first ? s.occ32 : s.occ64), st) != cudaSuccess)
+                     s.num_sms * s.occ[fp32_first ? TK_FP32 : TK_FP64][pl], st) != cudaSuccess)
         return ART_ERR_CUDA;
     if (mixed) {
         TraceArgs b = a;
@@ -137,8 +144,8 @@ extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_d
         b.count = counters + C_REROUTE;
         b.fetch = counters + C_FETCH2;
         const bool dfp = J.precision == ART_MIXED_DF;
-        if (launch_trace(b, dfp ? TK_DF : TK_FP64, s.num_sms * (dfp ? s.occdf : s.occ64), st) !=
-            cudaSuccess)
+        if (launch_trace(b, dfp ? TK_DF : TK_FP64, s.num_sms * s.occ[dfp ? TK_DF : TK_FP64][pl],
+                         st) != cudaSuccess)
             return ART_ERR_CUDA;
     }
     unsigned long long bad = 0;

@@ -16,6 +16,7 @@
 
 #include "dfloat.cuh"
 #include "internal.cuh"
+#include "synch.cuh"
 
 namespace art {
 
@@ -117,14 +118,18 @@ __device__ __forceinline__ unsigned long long warp_fetch(unsigned long long* cou
     return base + __popc(m & ((1u << lane) - 1u));
 }
 
+constexpr int MAXPL = 16;  // planes per ray: 4 Stokes x 4 subrings
+
 template <class R>
 struct Tracer {
     using Q = typename Aux<R>::Q;
     RayState<R> s;
     R kt;
-    Q r, J0, A0, I, T;
-    Q acc[4];     // subring planes (unpolarized)
-    Q sweep;      // angle swept by the position vector (mixed-precision routing)
+    Q r, T, sweep;
+    Q J0[4], K0[7];   // coefficients at the start of the current step
+    Q f[4];           // polarized rays: parallel-transported reference covector
+    Q P[16];          // polarized rays: accumulated Stokes propagator (camera <- here)
+    Q acc[MAXPL];     // accumulated planes
     float min_r;
     int steps, nturn, tsign, status;
     int32_t pix;
@@ -137,9 +142,23 @@ __device__ __forceinline__ R phi1(R x)
     return x > R(1e-8) ? -expm1(-x) / x : R(1) - R(0.5) * x;
 }
 
-template <class R>
-__device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Camera& cam,
-                                         int32_t pix)
+// Emission/absorption/rotation coefficients at a point (J4, K7 as in synch.cuh).
+template <class Q, bool POL>
+__device__ __forceinline__ void coefficients(const RayState<Q>& q, Q r, Q kt, const Q* f,
+                                             const DevJob& J, const SynchConst& S, Q* J4, Q* K7)
+{
+    if (J.emission == ART_EMIT_SYNCH_DISK) {
+        emission_synch<Q>(q, r, kt, POL ? f : nullptr, J, S, J4, K7);
+        return;
+    }
+    for (int i = 1; i < 4; ++i) J4[i] = Q(0);
+    for (int i = 0; i < 7; ++i) K7[i] = Q(0);
+    J4[0] = emission_cfg0<Q>(q, r, kt, J);
+}
+
+template <class R, bool POL>
+__device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const SynchConst& S,
+                                         const Camera& cam, int32_t pix)
 {
     using Q = typename Aux<R>::Q;
     int i = pix % J.nx, j = pix / J.nx;
@@ -157,13 +176,20 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Ca
     t.s.kx = R(k[1]);
     t.s.ky = R(k[2]);
     t.s.kz = R(k[3]);
+    if (POL) {
+        // screen-up vector made normal to the line of sight n: e2 - (e2.n) n, e2.n = sc be/ro
+        double c = sc * be / ro, nrm = 1.0 / sqrt(1.0 - c * c);
+        for (int m = 0; m < 4; ++m) {
+            double n = sc * (-cam.E[1][m] + (al / ro) * cam.E[3][m] + (be / ro) * cam.E[2][m]);
+            t.f[m] = Q((cam.E[2][m] - c * n) * nrm);
+        }
+        for (int m = 0; m < 16; ++m) t.P[m] = (m % 5 == 0) ? Q(1) : Q(0);
+    }
     RayState<Q> q = to_q<Q>(t.s);
     t.r = ks_radius<Q>(q.x, q.y, q.z, Q(J.a2));
-    t.J0 = J.emission == ART_EMIT_CFG0 ? emission_cfg0<Q>(q, t.r, Q(t.kt), J) : Q(0);
-    t.A0 = Q(0);
-    t.I = Q(0);
+    coefficients<Q, POL>(q, t.r, Q(t.kt), t.f, J, S, t.J0, t.K0);
     t.T = Q(1);
-    for (int p = 0; p < 4; ++p) t.acc[p] = Q(0);
+    for (int p = 0; p < MAXPL; ++p) t.acc[p] = Q(0);
     t.min_r = float(t.r);
     t.sweep = Q(0);
     t.steps = 0;
@@ -174,27 +200,44 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Ca
 }
 
 // One RK4 step plus the transfer segment; returns true when the ray has terminated.  SWEEP
-// accumulates the angle swept by the position vector (used to route rays in mixed precision).
-template <class R, bool SWEEP>
-__device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
+// accumulates the angle swept by the position vector (used to route rays in mixed precision);
+// POL carries the polarization covector through the RK4 stages and solves the Stokes segment.
+template <class R, bool SWEEP, bool POL>
+__device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const SynchConst& S)
 {
     using Q = typename Aux<R>::Q;
     const R a = R(J.a), a2 = R(J.a2);
+    const Q aq = Q(J.a), a2q = Q(J.a2);
     Q hq = Q(J.step_frac) * t.r;
     if (hq < Q(J.h_min)) hq = Q(J.h_min);
     const R h = R(hq);
     const R hh = R(0.5) * h;
+    const Q hhq = Q(0.5) * hq;
     RayState<R> k1, k2, k3, k4, y;
+    Q d1[4], d2[4], d3[4], d4[4], fy[4];
     geodesic_rhs<R>(t.s, t.kt, a, a2, k1);
+    if (POL) transport_rhs<Q>(to_q<Q>(t.s), Q(t.kt), t.f, aq, a2q, d1);
     y.x = t.s.x + hh * k1.x; y.y = t.s.y + hh * k1.y; y.z = t.s.z + hh * k1.z;
     y.kx = t.s.kx + hh * k1.kx; y.ky = t.s.ky + hh * k1.ky; y.kz = t.s.kz + hh * k1.kz;
     geodesic_rhs<R>(y, t.kt, a, a2, k2);
+    if (POL) {
+        for (int m = 0; m < 4; ++m) fy[m] = t.f[m] + hhq * d1[m];
+        transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d2);
+    }
     y.x = t.s.x + hh * k2.x; y.y = t.s.y + hh * k2.y; y.z = t.s.z + hh * k2.z;
     y.kx = t.s.kx + hh * k2.kx; y.ky = t.s.ky + hh * k2.ky; y.kz = t.s.kz + hh * k2.kz;
     geodesic_rhs<R>(y, t.kt, a, a2, k3);
+    if (POL) {
+        for (int m = 0; m < 4; ++m) fy[m] = t.f[m] + hhq * d2[m];
+        transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d3);
+    }
     y.x = t.s.x + h * k3.x; y.y = t.s.y + h * k3.y; y.z = t.s.z + h * k3.z;
     y.kx = t.s.kx + h * k3.kx; y.ky = t.s.ky + h * k3.ky; y.kz = t.s.kz + h * k3.kz;
     geodesic_rhs<R>(y, t.kt, a, a2, k4);
+    if (POL) {
+        for (int m = 0; m < 4; ++m) fy[m] = t.f[m] + hq * d3[m];
+        transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d4);
+    }
     const R h6 = h / R(6);
     const Q ox = Q(t.s.x), oy = Q(t.s.y), oz = Q(t.s.z);
     t.s.x += h6 * (k1.x + R(2) * k2.x + R(2) * k3.x + k4.x);
@@ -203,6 +246,10 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
     t.s.kx += h6 * (k1.kx + R(2) * k2.kx + R(2) * k3.kx + k4.kx);
     t.s.ky += h6 * (k1.ky + R(2) * k2.ky + R(2) * k3.ky + k4.ky);
     t.s.kz += h6 * (k1.kz + R(2) * k2.kz + R(2) * k3.kz + k4.kz);
+    if (POL) {
+        const Q h6q = hq / Q(6);
+        for (int m = 0; m < 4; ++m) t.f[m] += h6q * (d1[m] + Q(2) * d2[m] + Q(2) * d3[m] + d4[m]);
+    }
     ++t.steps;
     if (!(isfinite(t.s.x) && isfinite(t.s.y) && isfinite(t.s.z) && isfinite(t.s.kx) &&
           isfinite(t.s.ky) && isfinite(t.s.kz))) {
@@ -216,29 +263,45 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
         Q n2 = (ox * ox + oy * oy + oz * oz) * (q.x * q.x + q.y * q.y + q.z * q.z);
         t.sweep += sqrt((cx * cx + cy * cy + cz * cz) / n2);
     }
-    Q rn = ks_radius<Q>(q.x, q.y, q.z, Q(J.a2));
-    Q J1 = J.emission == ART_EMIT_CFG0 ? emission_cfg0<Q>(q, rn, Q(t.kt), J) : Q(0);
-    Q A1 = Q(0);
+    Q rn = ks_radius<Q>(q.x, q.y, q.z, a2q);
+    Q J1[4], K1[7];
+    coefficients<Q, POL>(q, rn, Q(t.kt), t.f, J, S, J1, K1);
     int seg = t.nturn;
     int sg = polar_sign<Q>(q, rn);
     if (sg != 0) {
         if (t.tsign != 0 && sg != t.tsign) ++t.nturn;
         t.tsign = sg;
     }
-    Q Jb = Q(0.5) * (t.J0 + J1), Ab = Q(0.5) * (t.A0 + A1);
-    Q dtau = Ab * hq;
-    Q dI = t.T * Jb * hq * phi1<Q>(dtau);
-    if (J.subrings > 0) {
-        int p = seg < J.subrings ? seg : J.subrings - 1;
+    const int sub = J.subrings > 0 ? (seg < J.subrings ? seg : J.subrings - 1) : 0;
+    if (POL) {
+        Q Jb[4], Kb[7];
+        bool active = false;
+        for (int i = 0; i < 4; ++i) {
+            Jb[i] = Q(0.5) * (t.J0[i] + J1[i]);
+            active |= Jb[i] != Q(0);
+        }
+        for (int i = 0; i < 7; ++i) {
+            Kb[i] = Q(0.5) * (t.K0[i] + K1[i]);
+            active |= Kb[i] != Q(0);
+        }
+        if (active) {
+            Q add[4] = {Q(0), Q(0), Q(0), Q(0)};
+            segment_pol<Q>(Kb, Jb, hq, t.P, add);
+#pragma unroll
+            for (int c = 0; c < MAXPL; ++c)
+                if ((c >> 2) == sub) t.acc[c] += add[c & 3];
+        }
+    } else {
+        Q Jb = Q(0.5) * (t.J0[0] + J1[0]), Ab = Q(0.5) * (t.K0[0] + K1[0]);
+        Q dtau = Ab * hq;
+        Q dI = t.T * Jb * hq * phi1<Q>(dtau);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (c == p) t.acc[c] += dI;
-    } else {
-        t.I += dI;
+            if (c == sub) t.acc[c] += dI;
+        if (Ab != Q(0)) t.T *= exp(-dtau);
     }
-    if (Ab != Q(0)) t.T *= exp(-dtau);
-    t.J0 = J1;
-    t.A0 = A1;
+    for (int i = 0; i < 4; ++i) t.J0[i] = J1[i];
+    for (int i = 0; i < 7; ++i) t.K0[i] = K1[i];
     t.r = rn;
     if (float(rn) < t.min_r) t.min_r = float(rn);
     if (rn < Q(J.r_in_stop)) { t.status = ART_RAY_CAPTURED; return true; }
@@ -247,7 +310,7 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J)
     return false;
 }
 
-template <class R, bool SWEEP>
+template <class R, bool SWEEP, bool POL>
 __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
 {
     __shared__ Camera cam_s;
@@ -259,6 +322,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
     }
     __syncthreads();
     const DevJob& J = A.job;
+    const SynchConst& S = A.synch;
     const unsigned long long n = *A.count;
     const bool mixed32 = (A.reroute != nullptr);
     Tracer<R> t;
@@ -273,7 +337,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
                 atomicAdd(A.counters + C_BADIDX, 1ull);
                 continue;
             }
-            ray_init<R>(t, J, cam_s, pix);
+            ray_init<R, POL>(t, J, S, cam_s, pix);
             t.slot = slot;
             return true;
         }
@@ -281,7 +345,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
     active = fetch_next();
     while (__any_sync(0xffffffffu, active)) {
         if (active) {
-            if (ray_step<R, SWEEP>(t, J)) {
+            if (ray_step<R, SWEEP, POL>(t, J, S)) {
                 atomicAdd(A.counters + C_STEPS, (unsigned long long)t.steps);
                 bool rer = mixed32 && (t.sweep >= typename Aux<R>::Q(J.fp64_sweep) ||
                                        t.status == ART_RAY_NAN || t.status == ART_RAY_CAP);
@@ -293,23 +357,14 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
                     if (t.status == ART_RAY_NAN) atomicAdd(A.counters + C_NAN, 1ull);
                     if (A.indirect) atomicAdd(A.counters + C_FP64, 1ull);  // re-trace pass
                     const int np = J.planes;
-                    if (A.img) {
-                        if (J.subrings > 0) {
-                            for (int p = 0; p < np && p < 4; ++p)
-                                A.img[(int64_t)p * A.npix + t.pix] = double(t.acc[p]);
-                        } else {
-                            A.img[t.pix] = double(t.I);
-                        }
-                        if (A.mask) A.mask[t.pix] = ART_MASK_TRACED;
-                    }
-                    if (A.out) {
-                        if (J.subrings > 0) {
-                            for (int p = 0; p < np && p < 4; ++p)
-                                A.out[t.slot * np + p] = double(t.acc[p]);
-                        } else {
-                            A.out[t.slot * np] = double(t.I);
+#pragma unroll
+                    for (int p = 0; p < MAXPL; ++p) {
+                        if (p < np) {
+                            if (A.img) A.img[(int64_t)p * A.npix + t.pix] = double(t.acc[p]);
+                            if (A.out) A.out[t.slot * np + p] = double(t.acc[p]);
                         }
                     }
+                    if (A.img && A.mask) A.mask[t.pix] = ART_MASK_TRACED;
                     if (A.aux_status) A.aux_status[t.slot] = t.status;
                     if (A.aux_steps) A.aux_steps[t.slot] = t.steps;
                     if (A.aux_nturn) A.aux_nturn[t.slot] = t.nturn;
@@ -321,44 +376,57 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
     }
 }
 
-cudaError_t launch_trace(const TraceArgs& a, TraceKind kind, int grid, cudaStream_t st)
+template <bool POL>
+static cudaError_t launch_trace_pol(const TraceArgs& a, TraceKind kind, int grid, cudaStream_t st)
 {
     switch (kind) {
     case TK_FP32:
         if (a.reroute)
-            trace_kernel<float, true><<<grid, TRACE_BLOCK, 0, st>>>(a);
+            trace_kernel<float, true, POL><<<grid, TRACE_BLOCK, 0, st>>>(a);
         else
-            trace_kernel<float, false><<<grid, TRACE_BLOCK, 0, st>>>(a);
+            trace_kernel<float, false, POL><<<grid, TRACE_BLOCK, 0, st>>>(a);
         break;
     case TK_DF:
-        trace_kernel<df, false><<<grid, TRACE_BLOCK, 0, st>>>(a);
+        trace_kernel<df, false, POL><<<grid, TRACE_BLOCK, 0, st>>>(a);
         break;
     default:
-        trace_kernel<double, false><<<grid, TRACE_BLOCK, 0, st>>>(a);
+        trace_kernel<double, false, POL><<<grid, TRACE_BLOCK, 0, st>>>(a);
     }
     return cudaGetLastError();
 }
 
-cudaError_t trace_occupancy(TraceKind kind, int* blocks_per_sm)
+cudaError_t launch_trace(const TraceArgs& a, TraceKind kind, int grid, cudaStream_t st)
+{
+    return a.job.stokes == 4 ? launch_trace_pol<true>(a, kind, grid, st)
+                             : launch_trace_pol<false>(a, kind, grid, st);
+}
+
+template <bool POL>
+static cudaError_t occupancy_pol(TraceKind kind, int* blocks_per_sm)
 {
     int b1 = 0, b2 = 0;
     cudaError_t e;
     switch (kind) {
     case TK_FP32:
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, trace_kernel<float, true>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, trace_kernel<float, true, POL>,
                                                           TRACE_BLOCK, 0);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, trace_kernel<float, false>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, trace_kernel<float, false, POL>,
                                                               TRACE_BLOCK, 0);
         *blocks_per_sm = b1 < b2 ? b1 : b2;
         return e;
     case TK_DF:
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, trace_kernel<df, false>,
-                                                             TRACE_BLOCK, 0);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            blocks_per_sm, trace_kernel<df, false, POL>, TRACE_BLOCK, 0);
     default:
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            blocks_per_sm, trace_kernel<double, false>, TRACE_BLOCK, 0);
+            blocks_per_sm, trace_kernel<double, false, POL>, TRACE_BLOCK, 0);
     }
+}
+
+cudaError_t trace_occupancy(TraceKind kind, bool pol, int* blocks_per_sm)
+{
+    return pol ? occupancy_pol<true>(kind, blocks_per_sm) : occupancy_pol<false>(kind, blocks_per_sm);
 }
 
 }  // namespace art

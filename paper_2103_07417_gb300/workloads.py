@@ -123,6 +123,10 @@ def cfg1_analytic(**over) -> dict:
 
 
 BENCH_WORKLOADS = {
+    "cfg1": ("adaptive polarized render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, FOV 40 M, "
+             "r_obs 1000 M, RK4 h=0.05r; thermal-synchrotron thin disk (n_e~r^-1.1, T_e~r^-0.84, "
+             "toroidal:vertical B = 1:1) at 230 GHz, Stokes IQUV with Faraday rotation/conversion; "
+             "R_rel=R_abs=1e-3", cfg1),
     "cfg1_analytic": ("adaptive render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, "
                       "FOV 40 M, r_obs 1000 M, RK4 h=0.05r, analytic Keplerian emissivity "
                       "r^-2 exp(-z^2/(2(0.3r)^2)), R_rel=R_abs=1e-3", cfg1_analytic),
