@@ -644,8 +644,9 @@ static double phi1(double x) { return x > 1e-8 ? -expm1(-x) / x : 1.0 - 0.5 * x;
 /* Sign of d(theta)/d(lambda) along the traced ray, from the covariant theta momentum in the
  * Kerr-Schild spherical angles: k_theta sin(theta) = (x k_x + y k_y) z/r - (r - z^2/r) k_z.
  * Values within 1e-9 r of zero return 0 (no decision), so radial rays count no turning points.
- * Turning points of theta separate the passes of the ray through the equatorial plane: the
- * subring index n of an emission point is the number of them between it and the camera. */
+ * Turning points of theta after the ray's first crossing of the equatorial plane separate its
+ * passes through that plane: the subring index n of an emission point is the number of them
+ * between it and the camera. */
 static int polar_sign(const double* y, double r)
 {
     double q = (y[1] * y[5] + y[2] * y[6]) * y[3] / r - (r - y[3] * y[3] / r) * y[7];
@@ -722,7 +723,7 @@ static void trace_one(const orc_job* job, const camera* cam, double al, double b
     double P[16];
     for (int i = 0; i < 16; ++i) P[i] = (i % 5 == 0) ? 1.0 : 0.0;
     double min_r = r;
-    int nturn = 0, steps = 0, status = ORC_RAY_CAP;
+    int nturn = 0, steps = 0, status = ORC_RAY_CAP, crossed = 0;
     int theta_sign = polar_sign(y, r);
     if (rec && maxrec > 0) {
         memset(rec, 0, sizeof(double) * 14);
@@ -740,11 +741,14 @@ static void trace_one(const orc_job* job, const camera* cam, double al, double b
         if (!finite) { status = ORC_RAY_NAN; break; }
         double rn = creal(ks_radius(a, yn[1], yn[2], yn[3]));
         coefficients(job, yn, pol, J1, K1);
-        /* subring index of this segment: polar turning points before the segment starts */
+        /* subring index of this segment: polar turning points before the segment starts,
+         * counted from the first crossing of the equatorial plane on (a turning point on the
+         * camera side of the first crossing does not end a half-orbit) */
         int seg_turn = nturn;
+        if (y[3] * yn[3] < 0) crossed = 1;
         int sg = polar_sign(yn, rn);
         if (sg != 0) {
-            if (theta_sign != 0 && sg != theta_sign) ++nturn;
+            if (crossed && theta_sign != 0 && sg != theta_sign) ++nturn;
             theta_sign = sg;
         }
         int plane0 = 0;

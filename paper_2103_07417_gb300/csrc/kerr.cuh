@@ -137,8 +137,7 @@ ART_HD R emission_cfg0(const RayState<R>& s, R r, R kt, const DevJob& J)
 }
 
 // Sign of d(theta)/d(lambda) from k_theta sin(theta) = (x k_x + y k_y) z/r - (r - z^2/r) k_z,
-// 0 inside a dead band of 1e-9 r (1e-5 r in FP32) so radial rays count no turns.  Sign flips count polar turning points, which
-// separate the passes of a ray through the equatorial plane (the subring index n).
+// 0 inside a dead band of 1e-9 r (1e-5 r in FP32) so radial rays count no turns.
 template <class R>
 ART_HD int polar_sign(const RayState<R>& s, R r)
 {

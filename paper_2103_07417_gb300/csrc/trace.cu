@@ -118,7 +118,8 @@ __device__ __forceinline__ unsigned long long warp_fetch(unsigned long long* cou
     return base + __popc(m & ((1u << lane) - 1u));
 }
 
-constexpr int MAXPL = 16;  // planes per ray: 4 Stokes x 4 subrings
+constexpr int MAXPL = 16;        // planes per ray: 4 Stokes x 4 subrings
+constexpr int RAY_REROUTE = 16;  // internal status: handed to the high-precision pass
 
 template <class R>
 struct Tracer {
@@ -131,7 +132,7 @@ struct Tracer {
     Q P[16];          // polarized rays: accumulated Stokes propagator (camera <- here)
     Q acc[MAXPL];     // accumulated planes
     float min_r;
-    int steps, nturn, tsign, status;
+    int steps, nturn, tsign, status, crossed;
     int32_t pix;
     int64_t slot;  // queue position
 };
@@ -194,6 +195,7 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Sy
     t.sweep = Q(0);
     t.steps = 0;
     t.nturn = 0;
+    t.crossed = 0;
     t.tsign = polar_sign<Q>(q, t.r);
     t.status = ART_RAY_CAP;
     t.pix = pix;
@@ -262,14 +264,22 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const Sy
         Q cx = oy * q.z - oz * q.y, cy = oz * q.x - ox * q.z, cz = ox * q.y - oy * q.x;
         Q n2 = (ox * ox + oy * oy + oz * oz) * (q.x * q.x + q.y * q.y + q.z * q.z);
         t.sweep += sqrt((cx * cx + cy * cy + cz * cz) / n2);
+        // a near-critical ray is re-traced at high precision anyway: stop it as soon as it is
+        // known to be one (these orbiting rays are also the longest of the FP32 pass)
+        if (t.sweep >= Q(J.fp64_sweep)) {
+            t.status = RAY_REROUTE;
+            return true;
+        }
     }
     Q rn = ks_radius<Q>(q.x, q.y, q.z, a2q);
     Q J1[4], K1[7];
     coefficients<Q, POL>(q, rn, Q(t.kt), t.f, J, S, J1, K1);
+    // subring index: polar turning points counted from the first equatorial crossing on
     int seg = t.nturn;
+    if (oz * q.z < Q(0)) t.crossed = 1;
     int sg = polar_sign<Q>(q, rn);
     if (sg != 0) {
-        if (t.tsign != 0 && sg != t.tsign) ++t.nturn;
+        if (t.crossed && t.tsign != 0 && sg != t.tsign) ++t.nturn;
         t.tsign = sg;
     }
     const int sub = J.subrings > 0 ? (seg < J.subrings ? seg : J.subrings - 1) : 0;
@@ -347,8 +357,8 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
         if (active) {
             if (ray_step<R, SWEEP, POL>(t, J, S)) {
                 atomicAdd(A.counters + C_STEPS, (unsigned long long)t.steps);
-                bool rer = mixed32 && (t.sweep >= typename Aux<R>::Q(J.fp64_sweep) ||
-                                       t.status == ART_RAY_NAN || t.status == ART_RAY_CAP);
+                bool rer = mixed32 && (t.status == RAY_REROUTE || t.status == ART_RAY_NAN ||
+                                       t.status == ART_RAY_CAP);
                 if (rer) {
                     unsigned long long w = atomicAdd(A.reroute_count, 1ull);
                     A.reroute[w] = (int32_t)t.slot;
