@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--workload", default="cfg1", choices=sorted(W.BENCH_WORKLOADS))
     ap.add_argument("--precision", default="mixed_df", choices=["mixed", "mixed_df", "fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-render measurement")
     ap.add_argument("--single", action="store_true",
                     help="one warm-up and one render, nothing else (for profiler captures)")
     return ap.parse_args()
@@ -320,6 +321,38 @@ def main():
            "h2d_bytes_per_step": int(ctypes_sizeof_job()),
            "d2h_bytes_per_step": int(himg.nbytes + hmask.nbytes)}
 
+    # the batched form (256 images of random spin, inclination, FOV, grid and depth, one pass per
+    # level for all of them) on the same GPU
+    batched = None
+    if not args.no_batch:
+        bparams = W.cfg3(seed=0, n=256)
+        bjobs = [art.make_job(**p) for p in bparams]
+        bimgs, bmasks = [], []
+        for bj in bjobs:
+            bnx, bny = art.art_image_size(bj)
+            bimgs.append(torch.empty((art.art_planes(bj), bny, bnx), dtype=torch.float64, device=dev))
+            bmasks.append(torch.empty((bny, bnx), dtype=torch.uint8, device=dev))
+        bst = ctx.art_render_batch(bjobs, bimgs, bmasks, stats=True)
+        brays = sum(x["rays_traced"] for x in bst)
+        bpix = sum(int(m.numel()) for m in bmasks)
+        evs = []
+        for _ in range(3):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.art_render_batch(bjobs, bimgs, bmasks, stats=False)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        tb = sum(a.elapsed_time(b) for a, b in evs) / 1000.0 / len(evs)
+        batched = {"workload": "256 images (config-3 recipe): a~U[-0.94,0.94], i~U[10,170] deg, "
+                               "FOV log-U[40,400] M, 65^2..513^2 over 2-6 levels, synchrotron "
+                               "disk, subrings n=0,1,2, mixed_df",
+                   "rays_per_s": brays / tb, "images_per_s": len(bjobs) / tb,
+                   "ms_per_batch": 1000 * tb, "rays": brays, "pixels": bpix,
+                   "geodesic_steps_per_s": bst[0]["steps"] / tb}
+        del bimgs, bmasks
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(params)
@@ -335,7 +368,7 @@ def main():
                            "l2": "flushed (512 MB write) before every step, outside the timed "
                                  "region", "parallelism": f"replicas x{world}"},
                 "geodesic_steps_per_s": steps_per_render * args.steps * world / t_dev,
-                "paths": paths, "roofline": roofline, "kernels": kernels,
+                "paths": paths, "batched": batched, "roofline": roofline, "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(stats["kernel_launches"]) * args.steps}
         print(json.dumps(line), flush=True)

@@ -175,6 +175,19 @@ int art_refine_level(art_ctx* ctx, const art_job* job, double* img_dev, uint8_t*
 int art_render(art_ctx* ctx, const art_job* job, const double* truth_dev, double* img_dev,
                uint8_t* mask_dev, art_stats* stats_host);
 
+/* The batched form: render n images in one pass per level.  Every kernel of a level works on all
+ * images that have that level, and the rays of all images share one device queue, so one
+ * persistent trace launch per level packs rays of uneven length from images of different spins,
+ * inclinations, fields of view, grids and depths.  jobs[i] may differ in everything except
+ * stokes, subrings and precision (one kernel kind and one plane count per batch; else
+ * ART_ERR_ARG).  imgs is a HOST array of n device pointers (planes x ny_i x nx_i doubles each);
+ * masks (nullable, entries nullable) a host array of n device pointers.  stats_host (nullable)
+ * receives n entries: rays per level and the normalisation per image; steps, re-traced, capped
+ * and NaN rays and kernel launches are batch totals repeated in every entry.  Synchronises when
+ * stats are requested.  Errors as art_render. */
+int art_render_batch(art_ctx* ctx, const art_job* jobs, int32_t n, double* const* imgs,
+                     uint8_t* const* masks, art_stats* stats_host);
+
 /* art_render into HOST buffers: the image and mask are rendered into context-owned device
  * buffers and copied to img_host (planes x ny x nx doubles) and mask_host (nullable, ny x nx
  * bytes).  Synchronises the stream. */

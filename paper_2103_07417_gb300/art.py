@@ -92,7 +92,7 @@ _lib = None
 EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_planes",
            "art_trace_pixels", "art_ibar_int", "art_refine_level", "art_render",
            "art_render_host", "art_metrics", "art_profile", "art_profile_read",
-           "art_trace_pixels_noalloc")
+           "art_trace_pixels_noalloc", "art_render_batch")
 NOALLOC_MAX_RAYS = 1 << 20
 
 
@@ -126,6 +126,7 @@ def load():
             lib.art_profile.argtypes = [vp, ctypes.c_int]
             lib.art_profile_read.argtypes = [vp, P(LaunchRecord), ctypes.c_int, P(ctypes.c_int)]
             lib.art_trace_pixels_noalloc.argtypes = [P(Job), vp, i64, vp, P(RayAux), vp]
+            lib.art_render_batch.argtypes = [vp, P(Job), i32, P(vp), P(vp), P(Stats)]
             _lib = lib
     return _lib
 
@@ -239,6 +240,28 @@ class Context:
         _check(load().art_render(self._ctx, ctypes.byref(job), _dptr(truth), _dptr(img),
                                  _dptr(mask), ctypes.byref(st) if stats else None), "art_render")
         return _stats_dict(st, job.levels) if stats else None
+
+    def art_render_batch(self, jobs, imgs, masks=None, stats: bool = True):
+        n = len(jobs)
+        jarr = (Job * n)(*jobs)
+        iarr = (ctypes.c_void_p * n)(*[t.data_ptr() for t in imgs])
+        marr = (ctypes.c_void_p * n)(*[m.data_ptr() for m in masks]) if masks is not None else None
+        st = (Stats * n)()
+        _check(load().art_render_batch(self._ctx, jarr, n, iarr, marr, st if stats else None),
+               "art_render_batch")
+        return [_stats_dict(st[i], jobs[i].levels) for i in range(n)] if stats else None
+
+    def render_batch(self, jobs):
+        """Allocate the images and masks of a batch on the device and run art_render_batch."""
+        import torch
+        imgs, masks = [], []
+        for j in jobs:
+            nx, ny = art_image_size(j)
+            imgs.append(torch.empty((art_planes(j), ny, nx), dtype=torch.float64,
+                                    device=f"cuda:{self.device}"))
+            masks.append(torch.empty((ny, nx), dtype=torch.uint8, device=f"cuda:{self.device}"))
+        stats = self.art_render_batch(jobs, imgs, masks)
+        return imgs, masks, stats
 
     def art_render_host(self, job: Job, img: np.ndarray, mask: np.ndarray | None = None):
         st = Stats()

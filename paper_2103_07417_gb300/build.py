@@ -20,7 +20,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 # The tracer's FP32 path uses the approximate single-precision divide and square root (the
 # double-float arithmetic calls the round-to-nearest intrinsics explicitly, FP64 is unaffected).
-PER_FILE = {"trace.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+PER_FILE = {"trace.cu": ["-prec-div=false", "-prec-sqrt=false"],
+            "trace_batch.cu": ["-prec-div=false", "-prec-sqrt=false"]}
 
 
 def _nvcc() -> str:

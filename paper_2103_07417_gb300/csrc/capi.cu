@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -16,7 +17,22 @@ struct art_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
-    int occ[3][2] = {};  // resident blocks per SM of the trace kernels [kind][polarized]
+    int occ[3][2] = {};   // resident blocks per SM of the trace kernels [kind][polarized]
+    int occb[3][2] = {};  // the same for the batched trace kernels
+    // batched rendering tables and queue (grown, never shrunk)
+    DevJob* bjobs = nullptr;
+    SynchConst* bsynch = nullptr;
+    Camera* bcams = nullptr;
+    double* bparams = nullptr;
+    double** bimgs = nullptr;
+    uint8_t** bmasks = nullptr;
+    double* bnorms = nullptr;
+    unsigned long long* bcounts = nullptr;
+    unsigned long long* bcounts_host = nullptr;
+    int bcap = 0;
+    int64_t* bqueue = nullptr;
+    int32_t* breroute = nullptr;
+    int64_t bqcap = 0;
     // scratch owned by the library
     int32_t* queue = nullptr;
     int32_t* reroute = nullptr;
@@ -218,6 +234,11 @@ extern "C" int art_create(art_ctx** out, int device, void* stream)
                 return ART_ERR_CUDA;
             }
             if (c->occ[kd][pl] < 1) c->occ[kd][pl] = 1;
+            if (trace_batch_occupancy(kd, pl != 0, &c->occb[kd][pl]) != cudaSuccess) {
+                delete c;
+                return ART_ERR_CUDA;
+            }
+            if (c->occb[kd][pl] < 1) c->occb[kd][pl] = 1;
         }
     *out = c;
     return ART_OK;
@@ -240,6 +261,17 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFreeHost(c->pinned);
     cudaFreeHost(c->pinned_d);
     cudaFree(c->prof_steps);
+    cudaFree(c->bjobs);
+    cudaFree(c->bsynch);
+    cudaFree(c->bcams);
+    cudaFree(c->bparams);
+    cudaFree(c->bimgs);
+    cudaFree(c->bmasks);
+    cudaFree(c->bnorms);
+    cudaFree(c->bcounts);
+    cudaFreeHost(c->bcounts_host);
+    cudaFree(c->bqueue);
+    cudaFree(c->breroute);
     for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -601,5 +633,195 @@ extern "C" int art_profile_read(art_ctx* c, art_launch_record* recs, int cap, in
         if (out < cap) recs[out++] = r;
     }
     *n = out;
+    return ART_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// batched rendering
+// --------------------------------------------------------------------------------------------
+
+static int ensure_batch(art_ctx* c, int n, int64_t qcap)
+{
+    if (n > c->bcap) {
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->bjobs);
+        cudaFree(c->bsynch);
+        cudaFree(c->bcams);
+        cudaFree(c->bparams);
+        cudaFree(c->bimgs);
+        cudaFree(c->bmasks);
+        cudaFree(c->bnorms);
+        cudaFree(c->bcounts);
+        cudaFreeHost(c->bcounts_host);
+        c->bcap = 0;
+        CK(cudaMalloc(&c->bjobs, sizeof(DevJob) * n));
+        CK(cudaMalloc(&c->bsynch, sizeof(SynchConst) * n));
+        CK(cudaMalloc(&c->bcams, sizeof(Camera) * n));
+        CK(cudaMalloc(&c->bparams, sizeof(double) * 3 * n));
+        CK(cudaMalloc(&c->bimgs, sizeof(double*) * n));
+        CK(cudaMalloc(&c->bmasks, sizeof(uint8_t*) * n));
+        CK(cudaMalloc(&c->bnorms, sizeof(double) * 4 * n));
+        CK(cudaMalloc(&c->bcounts, sizeof(unsigned long long) * 16 * n));
+        CK(cudaMallocHost(&c->bcounts_host, sizeof(unsigned long long) * 16 * n));
+        c->bcap = n;
+    }
+    if (qcap > c->bqcap) {
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->bqueue);
+        cudaFree(c->breroute);
+        c->bqcap = 0;
+        CK(cudaMalloc(&c->bqueue, sizeof(int64_t) * qcap));
+        CK(cudaMalloc(&c->breroute, sizeof(int32_t) * qcap));
+        c->bqcap = qcap;
+    }
+    return ART_OK;
+}
+
+static int trace_queue_batch(art_ctx* c, const DevJob& J0, int nimg)
+{
+    (void)nimg;
+    BatchTraceArgs a;
+    memset(&a, 0, sizeof a);
+    a.jobs = c->bjobs;
+    a.synchs = c->bsynch;
+    a.cams = c->bcams;
+    a.imgs = c->bimgs;
+    a.masks = c->bmasks;
+    a.queue = c->bqueue;
+    a.count = c->counters + C_QUEUE;
+    a.counters = c->counters;
+    a.planes = J0.planes;
+    a.stokes = J0.stokes;
+    a.precision = J0.precision;
+    const int pl = J0.stokes == 4 ? 1 : 0;
+    a.fetch = c->counters + C_FETCH;
+    CK(cudaMemsetAsync(c->counters + C_FETCH, 0, sizeof(unsigned long long) * 3, c->stream));
+    int k;
+    if (J0.precision == ART_FP64) {
+        k = prof_begin(c);
+        CK(launch_trace_batch(a, TK_FP64, c->num_sms * c->occb[TK_FP64][pl], c->stream));
+        prof_end(c, k, ART_K_TRACE_FP64, -1);
+        return ART_OK;
+    }
+    const bool mixed = J0.precision == ART_MIXED || J0.precision == ART_MIXED_DF;
+    if (mixed) {
+        a.reroute = c->breroute;
+        a.reroute_count = c->counters + C_REROUTE;
+    }
+    k = prof_begin(c);
+    CK(launch_trace_batch(a, TK_FP32, c->num_sms * c->occb[TK_FP32][pl], c->stream));
+    prof_end(c, k, ART_K_TRACE_FP32, -1);
+    if (mixed) {
+        BatchTraceArgs b = a;
+        b.reroute = nullptr;
+        b.reroute_count = nullptr;
+        b.indirect = c->breroute;
+        b.count = c->counters + C_REROUTE;
+        b.fetch = c->counters + C_FETCH2;
+        const int kd = J0.precision == ART_MIXED_DF ? TK_DF : TK_FP64;
+        k = prof_begin(c);
+        CK(launch_trace_batch(b, kd, c->num_sms * c->occb[kd][pl], c->stream));
+        prof_end(c, k, kd == TK_DF ? ART_K_TRACE_DF : ART_K_TRACE_FP64, -1);
+    }
+    return ART_OK;
+}
+
+extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const* imgs,
+                                uint8_t* const* masks, art_stats* stats)
+{
+    if (!c || !jobs || !imgs || n < 1) return ART_ERR_ARG;
+    std::vector<DevJob> J(n);
+    std::vector<SynchConst> S(n);
+    std::vector<double> p3(3 * (size_t)n);
+    std::vector<uint8_t*> mk(n, nullptr);
+    int64_t qcap = 0;
+    int max_base = 1, max_levels = 0;
+    for (int i = 0; i < n; ++i) {
+        int rc = make_devjob(&jobs[i], &J[i]);
+        if (rc) return rc;
+        if (!imgs[i]) return ART_ERR_ARG;
+        if (J[i].stokes != J[0].stokes || J[i].subrings != J[0].subrings ||
+            J[i].precision != J[0].precision)
+            return ART_ERR_ARG;  // one kernel kind and one plane count per batch
+        make_synch(&jobs[i], &S[i]);
+        p3[3 * i] = jobs[i].a;
+        p3[3 * i + 1] = jobs[i].r_obs;
+        p3[3 * i + 2] = jobs[i].incl_deg;
+        if (masks) mk[i] = masks[i];
+        qcap += max_level_rays(J[i]);
+        int S0 = 1 << J[i].levels;
+        int nb = ((J[i].nx - 1) / S0 + 1) * ((J[i].ny - 1) / S0 + 1);
+        if (nb > max_base) max_base = nb;
+        if (J[i].levels > max_levels) max_levels = J[i].levels;
+    }
+    CK(cudaSetDevice(c->device));
+    int rc;
+    if ((rc = ensure_fixed(c)) || (rc = ensure_batch(c, n, qcap))) return rc;
+    cudaStream_t st = c->stream;
+    c->launches = 0;
+    CK(cudaMemcpyAsync(c->bjobs, J.data(), sizeof(DevJob) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bsynch, S.data(), sizeof(SynchConst) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bparams, p3.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bimgs, imgs, sizeof(double*) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bmasks, mk.data(), sizeof(uint8_t*) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * C_COUNT, st));
+    CK(cudaMemsetAsync(c->bcounts, 0, sizeof(unsigned long long) * 16 * n, st));
+    c->prof_level = -1;
+    int k = prof_begin(c);
+    CK(launch_camera_setup_batch(c->bjobs, c->bparams, n, c->bcams, st));
+    prof_end(c, k, ART_K_OTHER, 1);
+    k = prof_begin(c);
+    CK(launch_enqueue_base_batch(c->bjobs, n, max_base, c->bqueue, c->counters + C_QUEUE,
+                                 c->bcounts, st));
+    prof_end(c, k, ART_K_OTHER, -1);
+    for (int level = 0; level <= max_levels; ++level) {
+        c->prof_level = level;
+        if (level > 0) {
+            int max_points = 1;
+            for (int i = 0; i < n; ++i)
+                if (J[i].levels >= level) {
+                    int s = 1 << (J[i].levels - level);
+                    int np = ((J[i].nx - 1) / s + 1) * ((J[i].ny - 1) / s + 1);
+                    if (np > max_points) max_points = np;
+                }
+            CK(cudaMemsetAsync(c->counters + C_QUEUE, 0, sizeof(unsigned long long), st));
+            k = prof_begin(c);
+            CK(launch_refine_batch(c->bjobs, n, level, max_points, c->bnorms, c->bimgs, c->bmasks,
+                                   c->bqueue, c->counters + C_QUEUE, c->bcounts, st));
+            prof_end(c, k, ART_K_REFINE, -1);
+        }
+        if ((rc = trace_queue_batch(c, J[0], n))) return rc;
+        if (level == 0) {
+            k = prof_begin(c);
+            CK(launch_norm_batch(c->bjobs, c->bimgs, n, c->bnorms, st));
+            prof_end(c, k, ART_K_OTHER, -1);
+        }
+    }
+    c->prof_level = -1;
+    if (stats) {
+        if ((rc = read_counters(c))) return rc;
+        std::vector<double> norms(4 * (size_t)n);
+        CK(cudaMemcpyAsync(c->bcounts_host, c->bcounts, sizeof(unsigned long long) * 16 * n,
+                           cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(norms.data(), c->bnorms, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost,
+                           st));
+        CK(cudaStreamSynchronize(st));
+        for (int i = 0; i < n; ++i) {
+            art_stats& o = stats[i];
+            memset(&o, 0, sizeof o);
+            for (int l = 0; l <= J[i].levels && l < 16; ++l) {
+                o.rays_per_level[l] = (int64_t)c->bcounts_host[16 * i + l];
+                o.rays_traced += o.rays_per_level[l];
+            }
+            o.norm = norms[4 * i];
+            // batch totals
+            o.steps = (int64_t)c->pinned[C_STEPS];
+            o.rays_fp64 = (int64_t)c->pinned[C_FP64];
+            o.rays_capped = (int64_t)c->pinned[C_CAPPED];
+            o.rays_nan = (int64_t)c->pinned[C_NAN];
+            o.kernel_launches = c->launches;
+        }
+        if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
+    }
     return ART_OK;
 }

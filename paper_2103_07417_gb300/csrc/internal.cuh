@@ -46,6 +46,41 @@ struct TraceArgs {
     int64_t npix;
 };
 
+// Batched rendering: the rays of many images share one queue whose entries are
+// (image << 32) | pixel; each image's job, synchrotron constants, camera and output live in tables.
+struct BatchTraceArgs {
+    const DevJob* jobs;
+    const SynchConst* synchs;
+    const Camera* cams;
+    double* const* imgs;
+    uint8_t* const* masks;           // table entries may be null
+    const int64_t* queue;
+    const int32_t* indirect;         // nullable: slot -> queue position (re-trace pass)
+    const unsigned long long* count;
+    unsigned long long* fetch;
+    unsigned long long* counters;
+    int32_t* reroute;
+    unsigned long long* reroute_count;
+    int planes, stokes, precision;
+};
+
+// trace_batch.cu
+cudaError_t launch_camera_setup_batch(const DevJob* jobs_host_unused, const double* params3,
+                                      int n, Camera* cams, cudaStream_t st);
+cudaError_t launch_trace_batch(const BatchTraceArgs& a, int kind, int grid, cudaStream_t st);
+cudaError_t trace_batch_occupancy(int kind, bool pol, int* blocks_per_sm);
+
+// refine.cu (batched)
+cudaError_t launch_enqueue_base_batch(const DevJob* jobs, int n, int max_base, int64_t* queue,
+                                      unsigned long long* qcount, unsigned long long* img_counts,
+                                      cudaStream_t st);
+cudaError_t launch_norm_batch(const DevJob* jobs, double* const* imgs, int n, double* norms,
+                              cudaStream_t st);
+cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_points,
+                                const double* norms, double* const* imgs, uint8_t* const* masks,
+                                int64_t* queue, unsigned long long* qcount,
+                                unsigned long long* img_counts, cudaStream_t st);
+
 // trace.cu
 enum TraceKind { TK_FP64 = 0, TK_FP32 = 1, TK_DF = 2 };
 cudaError_t launch_camera_setup(const art_job& job, Camera* cam, cudaStream_t st);

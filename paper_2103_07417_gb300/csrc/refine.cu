@@ -292,6 +292,174 @@ cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double
 }
 
 // --------------------------------------------------------------------------------------------
+// batched forms: blockIdx.y selects the image; queue entries are (image << 32) | pixel and the
+// rays of a level are also counted per image (img_counts[16 * image + level]).
+// --------------------------------------------------------------------------------------------
+
+__global__ void enqueue_base_batch_kernel(const DevJob* jobs, int64_t* queue,
+                                          unsigned long long* qcount,
+                                          unsigned long long* img_counts)
+{
+    const int img = blockIdx.y;
+    const DevJob& J = jobs[img];
+    const int S0 = 1 << J.levels;
+    const int n0x = (J.nx - 1) / S0 + 1, n0y = (J.ny - 1) / S0 + 1;
+    const int64_t n = (int64_t)n0x * n0y;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = base + threadIdx.x;
+        const bool have = q < n;
+        const unsigned b = __ballot_sync(0xffffffffu, have);
+        unsigned long long w = 0;
+        if (lane == 0 && b) w = atomicAdd(qcount, (unsigned long long)__popc(b));
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (have) {
+            int ii = (int)(q % n0x), jj = (int)(q / n0x);
+            int64_t pix = (int64_t)jj * S0 * J.nx + (int64_t)ii * S0;
+            queue[w + __popc(b & ((1u << lane) - 1u))] = ((int64_t)img << 32) | pix;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) img_counts[16 * img] = (unsigned long long)n;
+}
+
+cudaError_t launch_enqueue_base_batch(const DevJob* jobs, int n, int max_base, int64_t* queue,
+                                      unsigned long long* qcount, unsigned long long* img_counts,
+                                      cudaStream_t st)
+{
+    int gx = (max_base + 255) / 256;
+    if (gx < 1) gx = 1;
+    if (gx > 1024) gx = 1024;
+    enqueue_base_batch_kernel<<<dim3(gx, n), 256, 0, st>>>(jobs, queue, qcount, img_counts);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(NORM_THREADS)
+    norm_batch_kernel(const DevJob* jobs, double* const* imgs, double* norms)
+{
+    const DevJob& J = jobs[blockIdx.x];
+    const double* img = imgs[blockIdx.x];
+    const int stride = 1 << J.levels, nx = J.nx, ny = J.ny;
+    const int n0x = (nx - 1) / stride + 1, n0y = (ny - 1) / stride + 1;
+    const int64_t n = (int64_t)n0x * n0y;
+    double s = 0.0, w = 0.0, mx = -INFINITY;
+    for (int64_t q = threadIdx.x; q < n; q += NORM_THREADS) {
+        int ii = (int)(q % n0x), jj = (int)(q / n0x);
+        double wx = (n0x > 1 && (ii == 0 || ii == n0x - 1)) ? 0.5 : 1.0;
+        double wy = (n0y > 1 && (jj == 0 || jj == n0y - 1)) ? 0.5 : 1.0;
+        double v = img[(int64_t)jj * stride * nx + (int64_t)ii * stride];
+        s += wx * wy * v;
+        w += wx * wy;
+        mx = fmax(mx, v);
+    }
+    __shared__ double ss[NORM_THREADS], sw[NORM_THREADS], sm[NORM_THREADS];
+    ss[threadIdx.x] = s;
+    sw[threadIdx.x] = w;
+    sm[threadIdx.x] = mx;
+    __syncthreads();
+    for (int h = NORM_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            ss[threadIdx.x] += ss[threadIdx.x + h];
+            sw[threadIdx.x] += sw[threadIdx.x + h];
+            sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + h]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double ibar = ss[0] / sw[0];
+        double* o = norms + 4 * blockIdx.x;
+        o[1] = ibar;
+        o[2] = sm[0];
+        o[0] = J.abs_norm == ART_NORM_PEAK ? sm[0] : ibar;
+    }
+}
+
+cudaError_t launch_norm_batch(const DevJob* jobs, double* const* imgs, int n, double* norms,
+                              cudaStream_t st)
+{
+    norm_batch_kernel<<<n, NORM_THREADS, 0, st>>>(jobs, imgs, norms);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256)
+    refine_batch_kernel(const DevJob* jobs, int level, const double* __restrict__ norms,
+                        double* const* imgs, uint8_t* const* masks, int64_t* queue,
+                        unsigned long long* qcount, unsigned long long* img_counts)
+{
+    const int im = blockIdx.y;
+    const DevJob J = jobs[im];
+    if (level > J.levels) return;  // the whole block: this image has no such level
+    double* img = imgs[im];
+    uint8_t* mask = masks[im];
+    const int s = 1 << (J.levels - level);
+    const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
+    const int64_t npts = (int64_t)nkx * nky;
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    const double norm = norms[4 * im];
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npts;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = base + threadIdx.x;
+        bool trace = false;
+        int32_t pix = 0;
+        if (t < npts) {
+            const int ii = (int)(t % nkx), jj = (int)(t / nkx);
+            const int oi = ii & 1, oj = jj & 1;
+            if (oi | oj) {
+                const int i = ii * s, j = jj * s;
+                const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+                double w1, w2;
+                int64_t p1, p2, p3, p4;
+                trace = decide(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4);
+                pix = j * J.nx + i;
+                if (trace) {
+                    if (mask) mask[pix] = ART_MASK_TRACED;
+                } else {
+                    for (int c = 0; c < J.planes; ++c) {
+                        const double* pl = img + c * npix;
+                        double v;
+                        if (cat == 4) {
+                            if (w2 == 0.0)
+                                v = __ldg(pl + p1);
+                            else
+                                v = 0.25 * (((__ldg(pl + p1) + __ldg(pl + p2)) + __ldg(pl + p3)) +
+                                            __ldg(pl + p4));
+                        } else {
+                            v = (w2 == 0.0) ? __ldg(pl + p1) : 0.5 * (__ldg(pl + p1) + __ldg(pl + p2));
+                        }
+                        img[c * npix + pix] = v;
+                    }
+                    if (mask) mask[pix] = ART_MASK_INTERP;
+                }
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, trace);
+        if (b) {
+            unsigned long long w = 0;
+            if (lane == 0) {
+                w = atomicAdd(qcount, (unsigned long long)__popc(b));
+                atomicAdd(img_counts + 16 * im + level, (unsigned long long)__popc(b));
+            }
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (trace) queue[w + __popc(b & ((1u << lane) - 1u))] = ((int64_t)im << 32) | pix;
+        }
+    }
+}
+
+cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_points,
+                                const double* norms, double* const* imgs, uint8_t* const* masks,
+                                int64_t* queue, unsigned long long* qcount,
+                                unsigned long long* img_counts, cudaStream_t st)
+{
+    int gx = (max_points + 255) / 256;
+    if (gx < 1) gx = 1;
+    if (gx > 2048) gx = 2048;
+    refine_batch_kernel<<<dim3(gx, n), 256, 0, st>>>(jobs, level, norms, imgs, masks, queue, qcount,
+                                                     img_counts);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------------------------
 // metrics (Eqs. interpdef, fluxdef, msedef): per-block partial sums, then one block combines them
 // in a fixed order.  Sums: [0] interpolated points, [1] F (trapezoid), [2] F_hat, [3] sum dI^2,
 // [4] sum I^2, [5] sum I.

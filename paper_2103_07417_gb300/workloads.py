@@ -133,3 +133,24 @@ BENCH_WORKLOADS = {
     "cfg0": ("adaptive render 33^2 -> 129^2 (2 levels), Schwarzschild, i=60 deg, FOV 40 M, "
              "R_rel=0.01, R_abs=1e-4 of peak", cfg0),
 }
+
+
+def cfg3(seed: int = 0, n: int = 256, **over) -> list:
+    """A batch of n images: spin a ~ U[-0.94, 0.94], inclination ~ U[10, 170] deg, FOV log-uniform
+    in [40, 400] M, final grid 2^k + 1 with k ~ U{6..9} (65^2 .. 513^2) reached over N ~ U{2..6}
+    levels (base grid at least 5 points), the thermal-synchrotron disk model of config 1 (inner
+    edge at each spin's ISCO) traced unpolarized with subrings n = 0, 1, 2; mixed precision."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        a = float(rng.uniform(-0.94, 0.94))
+        k = int(rng.integers(6, 10))
+        N = int(rng.integers(2, 7))
+        N = min(N, k - 2)
+        n0 = (1 << (k - N)) + 1
+        p = cfg1(a=a, incl_deg=float(rng.uniform(10.0, 170.0)),
+                 fov=float(np.exp(rng.uniform(np.log(40.0), np.log(400.0)))),
+                 n0x=n0, n0y=n0, levels=N, r_in=r_isco(a), stokes=1, subrings=3)
+        p.update(over)
+        out.append(p)
+    return out
