@@ -25,7 +25,7 @@ _SRC = [os.path.join(_HERE, "art_oracle.c")]
 _lock = threading.Lock()
 _lib = None
 
-EMIT_CFG0, EMIT_SYNCH_DISK, EMIT_BLOB = 0, 1, 8
+EMIT_CFG0, EMIT_SYNCH_DISK, EMIT_GRID, EMIT_BLOB = 0, 1, 2, 8
 FLOW_KEPLER, FLOW_STATIC = 0, 1
 NORM_IBAR_INT, NORM_PEAK = 0, 1
 INTERP_LINEAR, INTERP_NEAREST = 0, 1
@@ -66,6 +66,11 @@ class Job(ctypes.Structure):
         ("nu_hz", ctypes.c_double), ("ne_slope", ctypes.c_double), ("te_slope", ctypes.c_double),
         ("r_in", ctypes.c_double), ("length_cm", ctypes.c_double),
         ("bz_ratio", ctypes.c_double),
+        ("grid", ctypes.POINTER(ctypes.c_float)),
+        ("gn1", ctypes.c_int), ("gn2", ctypes.c_int), ("gn3", ctypes.c_int), ("gpad", ctypes.c_int),
+        ("glogr_min", ctypes.c_double), ("glogr_max", ctypes.c_double),
+        ("gamma_ad", ctypes.c_double), ("m_unit", ctypes.c_double),
+        ("r_high", ctypes.c_double), ("r_low", ctypes.c_double), ("sigma_cut", ctypes.c_double),
     ]
 
 
@@ -86,11 +91,13 @@ _DEFAULTS = dict(a=0.0, mass=1.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33,
                  flow=FLOW_KEPLER, stokes=1, subrings=0, max_steps=100000, step_frac=0.05,
                  h_min=1e-4, horizon_eps=0.01, escape_frac=1.01, disk_w=0.3, blob_sigma=1.0,
                  ne0=0.0, thetae0=0.0, b0=0.0, nu_hz=230e9, ne_slope=-1.1, te_slope=-0.84,
-                 r_in=0.0, length_cm=9.6e14, bz_ratio=1.0)
+                 r_in=0.0, length_cm=9.6e14, bz_ratio=1.0, gamma_ad=13.0 / 9.0, m_unit=1e27,
+                 r_high=20.0, r_low=1.0, sigma_cut=1.0)
 
 
 _NAMES = dict(
-    emission={"cfg0": EMIT_CFG0, "synch_disk": EMIT_SYNCH_DISK, "blob": EMIT_BLOB},
+    emission={"cfg0": EMIT_CFG0, "synch_disk": EMIT_SYNCH_DISK, "grid": EMIT_GRID,
+              "blob": EMIT_BLOB},
     flow={"kepler": FLOW_KEPLER, "static": FLOW_STATIC},
     abs_norm={"ibar_int": NORM_IBAR_INT, "peak": NORM_PEAK},
     interp={"linear": INTERP_LINEAR, "nearest": INTERP_NEAREST},
@@ -98,9 +105,13 @@ _NAMES = dict(
 )
 
 
-def make_job(**params) -> Job:
+def make_job(grid=None, **params) -> Job:
     """Build the oracle's job from a parameter dict; option names ("cfg0", "peak", ...) are
-    mapped to the oracle's enums and keys the oracle does not use are ignored."""
+    mapped to the oracle's enums and keys the oracle does not use are ignored.
+
+    grid: the fluid snapshot for emission "grid", a dict with ``data`` (float32, shape
+    (n3, n2, n1, 8)), ``n1``, ``n2``, ``n3``, ``logr_min``, ``logr_max`` (and optionally
+    ``gamma``).  The job keeps a reference to the array."""
     d = dict(_DEFAULTS)
     for k, v in params.items():
         if k not in _DEFAULTS:
@@ -108,7 +119,19 @@ def make_job(**params) -> Job:
         if k in _NAMES and isinstance(v, str):
             v = _NAMES[k][v]
         d[k] = v
-    return Job(**d)
+    job = Job(**d)
+    if grid is not None:
+        arr = np.ascontiguousarray(grid["data"], dtype=np.float32)
+        n1, n2, n3 = int(grid["n1"]), int(grid["n2"]), int(grid["n3"])
+        if arr.shape != (n3, n2, n1, 8):
+            raise ValueError("grid data must have shape (n3, n2, n1, 8)")
+        job.grid = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        job.gn1, job.gn2, job.gn3 = n1, n2, n3
+        job.glogr_min, job.glogr_max = float(grid["logr_min"]), float(grid["logr_max"])
+        if "gamma" in grid and "gamma_ad" not in params:
+            job.gamma_ad = float(grid["gamma"])
+        job._grid_ref = arr
+    return job
 
 
 def _load():
@@ -127,6 +150,7 @@ def _load():
             lib.orc_trace_record.argtypes = [P(Job), ctypes.c_double, ctypes.c_double,
                                              ctypes.c_int, dp, P(ctypes.c_int)]
             lib.orc_emission.argtypes = [P(Job), dp, dp, dp, dp]
+            lib.orc_grid_fluid.argtypes = [P(Job), dp, dp, dp, dp, dp]
             lib.orc_ibar_int.argtypes = [dp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.orc_ibar_int.restype = ctypes.c_double
             lib.orc_refine_level.argtypes = [P(Job), dp, u8p, ctypes.c_int, ctypes.c_int,
@@ -204,6 +228,21 @@ def trace_record(job: Job, alpha: float, beta: float, maxrec: int = 200000):
     status = _load().orc_trace_record(ctypes.byref(job), alpha, beta, maxrec, _ptr(rec),
                                       ctypes.byref(nrec))
     return rec[: nrec.value].copy(), int(status)
+
+
+def grid_fluid(job: Job, x):
+    """Fluid state of the grid model at Cartesian Kerr-Schild points x (n, 4): returns a dict of
+    prim (n, 8) interpolated primitives, u (n, 4), b (n, 4) contravariant, plasma (n, 4) =
+    (n_e, Theta_e, |B|, sigma) and emits (n,) bool."""
+    x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+    n = x.shape[0]
+    prim, u, b, pl = (np.zeros((n, k)) for k in (8, 4, 4, 4))
+    em = np.zeros(n, bool)
+    lib = _load()
+    for i in range(n):
+        em[i] = bool(lib.orc_grid_fluid(ctypes.byref(job), _ptr(x[i]), _ptr(prim[i]), _ptr(u[i]),
+                                        _ptr(b[i]), _ptr(pl[i])))
+    return dict(prim=prim, u=u, b=b, plasma=pl, emits=em)
 
 
 def emission(job: Job, x, k):

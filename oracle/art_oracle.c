@@ -267,6 +267,134 @@ static int fluid_velocity(const orc_job* job, const double* x, double r, double*
     return 1;
 }
 
+/* Kerr-Schild spherical angles of a Cartesian point: theta = acos(z/r) and phi from
+ * x + i y = (r - i a) sin(theta) e^{i phi}, i.e. phi = atan2(y, x) + atan2(a, r), in [0, 2 pi). */
+static void ks_angles(double a, const double* x, double r, double* th, double* ph)
+{
+    double ct = x[3] / r;
+    if (ct > 1) ct = 1;
+    if (ct < -1) ct = -1;
+    *th = acos(ct);
+    double p = atan2(x[2], x[1]) + atan2(a, r);
+    if (p < 0) p += 2.0 * M_PI;
+    if (p >= 2.0 * M_PI) p -= 2.0 * M_PI;
+    *ph = p;
+}
+
+/* Trilinear interpolation of the eight cell-centred FP32 primitives at (ln r, theta, phi).
+ * Reading of the fluid-grid lookup: the coordinate of each axis in cell units is
+ * f = (coordinate - start)/spacing - 1/2; ln r and theta clamp f to [0, n - 1] (the outer half
+ * cells take the edge value), phi is periodic.  Points with ln r outside [glogr_min, glogr_max]
+ * are outside the fluid and return 0. */
+static int grid_prims(const orc_job* job, double r, double th, double ph, double* P)
+{
+    double x1 = log(r);
+    if (!(x1 >= job->glogr_min && x1 <= job->glogr_max)) return 0;
+    int n[3] = {job->gn1, job->gn2, job->gn3};
+    double f[3] = {(x1 - job->glogr_min) / ((job->glogr_max - job->glogr_min) / n[0]) - 0.5,
+                   th / (M_PI / n[1]) - 0.5, ph / (2.0 * M_PI / n[2]) - 0.5};
+    int lo[3], hi[3];
+    double w[3];
+    for (int d = 0; d < 2; ++d) {
+        double fd = f[d];
+        if (fd < 0) fd = 0;
+        if (fd > n[d] - 1) fd = n[d] - 1;
+        int i = (int)floor(fd);
+        if (i > n[d] - 2) i = n[d] - 2;
+        if (i < 0) i = 0;
+        lo[d] = i;
+        hi[d] = n[d] > 1 ? i + 1 : i;
+        w[d] = n[d] > 1 ? fd - i : 0.0;
+    }
+    {
+        double fl = floor(f[2]);
+        int i = (int)fl;
+        w[2] = f[2] - fl;
+        lo[2] = ((i % n[2]) + n[2]) % n[2];
+        hi[2] = (lo[2] + 1) % n[2];
+    }
+    for (int q = 0; q < 8; ++q) P[q] = 0.0;
+    for (int c = 0; c < 8; ++c) {
+        int ii = (c & 1) ? hi[0] : lo[0], jj = (c & 2) ? hi[1] : lo[1], kk = (c & 4) ? hi[2] : lo[2];
+        double wt = ((c & 1) ? w[0] : 1.0 - w[0]) * ((c & 2) ? w[1] : 1.0 - w[1]) *
+                    ((c & 4) ? w[2] : 1.0 - w[2]);
+        const float* cell = job->grid + (((size_t)kk * n[1] + jj) * n[0] + ii) * 8;
+        for (int q = 0; q < 8; ++q) P[q] += wt * (double)cell[q];
+    }
+    return 1;
+}
+
+/* Fluid state from the grid at a Cartesian point x (r its Kerr-Schild radius):
+ *   u^i, B^i: the interpolated spherical components mapped to Cartesian ones by the Jacobian of
+ *     x + i y = (r - i a) sin(theta) e^{i phi}, z = r cos(theta);
+ *   u^t: the positive root of g_{mu nu} u^mu u^nu = -1.  With q = 1 + g_ij u^i u^j and
+ *     p = g_ti u^i the equation is g_tt (u^t)^2 + 2 p u^t + q = 0, whose root continuous across
+ *     the ergosurface (g_tt = 0) is u^t = q / (sqrt(p^2 - g_tt q) - p);
+ *   b^mu from the ideal-MHD relations b^t = g_{i mu} B^i u^mu, b^i = (B^i + b^t u^i)/u^t
+ *     (Gammie, McKinney & Toth 2003);
+ *   electron temperature from the two-temperature prescription of Moscibrodzka, Falcke &
+ *     Shiokawa (2016): T_i/T_e = (R_high beta^2 + R_low)/(1 + beta^2) with the plasma
+ *     beta = (gamma - 1) u / (b^2/2), Theta_e = (m_p/m_e)(gamma - 1) u / (rho (1 + T_i/T_e));
+ *   n_e = rho m_unit / (L^3 (m_p + m_e)), |B| = sqrt(b^2) c sqrt(4 pi m_unit / L^3) gauss.
+ * plasma4 = {n_e, Theta_e, |B|, sigma = b^2/rho}.  Returns 1 where the point emits: inside the
+ * radial range of the grid, a timelike u, rho > 0, u > 0, b^2 > 0 and sigma <= sigma_cut
+ * (the magnetisation cut: more strongly magnetised fluid does not emit). */
+int orc_grid_fluid(const orc_job* job, const double* x, double* P, double* u, double* b,
+                   double* pl)
+{
+    const double mp = 1.67262192369e-24, me = 9.1093837015e-28, c = 2.99792458e10;
+    double a = job->a, M = job->mass;
+    double r = creal(ks_radius(a, x[1], x[2], x[3]));
+    double th, ph;
+    for (int q = 0; q < 8; ++q) P[q] = 0.0;
+    for (int m = 0; m < 4; ++m) u[m] = b[m] = 0.0;
+    for (int m = 0; m < 4; ++m) pl[m] = 0.0;
+    if (!job->grid) return 0;
+    ks_angles(a, x, r, &th, &ph);
+    if (!grid_prims(job, r, th, ph, P)) return 0;
+    double st = sin(th), ct = cos(th), cp = cos(ph), sp = sin(ph);
+    double Jm[3][3] = {{st * cp, ct * (r * cp + a * sp), -x[2]},
+                       {st * sp, ct * (r * sp - a * cp), x[1]},
+                       {ct, -r * st, 0.0}};
+    double uc[4] = {0, 0, 0, 0}, Bc[4] = {0, 0, 0, 0};
+    for (int i = 0; i < 3; ++i)
+        for (int m = 0; m < 3; ++m) {
+            uc[1 + i] += Jm[i][m] * P[2 + m];
+            Bc[1 + i] += Jm[i][m] * P[5 + m];
+        }
+    double g[4][4];
+    metric_cov(a, M, x, g);
+    double q = 1.0, p = 0.0;
+    for (int i = 1; i < 4; ++i) {
+        p += g[0][i] * uc[i];
+        for (int j = 1; j < 4; ++j) q += g[i][j] * uc[i] * uc[j];
+    }
+    double D = p * p - g[0][0] * q;
+    if (!(D >= 0)) return 0;
+    double den = sqrt(D) - p;
+    if (!(den > 0)) return 0;
+    uc[0] = q / den;
+    double bt = 0.0;
+    for (int i = 1; i < 4; ++i)
+        for (int m = 0; m < 4; ++m) bt += g[i][m] * Bc[i] * uc[m];
+    b[0] = bt;
+    for (int i = 1; i < 4; ++i) b[i] = (Bc[i] + bt * uc[i]) / uc[0];
+    for (int m = 0; m < 4; ++m) u[m] = uc[m];
+    double b2 = dot_g(g, b, b);
+    double rho = P[0], ug = P[1];
+    double L3 = job->length_cm * job->length_cm * job->length_cm;
+    double sigma = rho > 0 ? b2 / rho : 0.0;
+    double pg = (job->gamma_ad - 1.0) * ug, pm = 0.5 * b2;
+    double trat = (job->r_high * pg * pg + job->r_low * pm * pm) / (pg * pg + pm * pm);
+    pl[0] = rho * job->m_unit / (L3 * (mp + me));
+    pl[1] = (mp / me) * (job->gamma_ad - 1.0) * ug / (rho * (1.0 + trat));
+    pl[2] = sqrt(b2 > 0 ? b2 : 0.0) * c * sqrt(4.0 * M_PI * job->m_unit / L3);
+    pl[3] = sigma;
+    if (!(rho > 0) || !(ug > 0) || !(b2 > 0)) return 0;
+    if (sigma > job->sigma_cut) return 0;
+    return 1;
+}
+
 /* Invariant emission J = j_nu / nu^2 and absorption A = nu alpha_nu at one point (unpolarized
  * models), with nu = k_mu u^mu the fluid-frame frequency in units of the camera frequency. */
 static void emission_unpol(const orc_job* job, const double* y, double* J, double* A,
@@ -508,7 +636,8 @@ void orc_segment(const double* K7, const double* J4, double h, double* E16, doub
  * d x b is at angle chi from e_N, so (Q, U) = P (cos 2 chi, sin 2 chi).
  * Disk model: n_e = ne0 r^ne_slope exp(-cos^2(theta)/(2 w^2)), Th_e = thetae0 r^te_slope,
  * |B| = b0 r^((ne_slope + te_slope)/2), direction (e_phi + q e_z)/sqrt(1 + q^2) in the fluid
- * frame with q = bz_ratio (toroidal : vertical = 1 : q), Keplerian flow; zero inside r_in. */
+ * frame with q = bz_ratio (toroidal : vertical = 1 : q), Keplerian flow; zero inside r_in.
+ * Grid model: u, b, n_e, Theta_e and |B| from orc_grid_fluid. */
 static void emission_pol(const orc_job* job, const double* y, const double* fcov, double* J4,
                          double* K7)
 {
@@ -518,15 +647,40 @@ static void emission_pol(const orc_job* job, const double* y, const double* fcov
     double r = creal(ks_radius(a, y[1], y[2], y[3]));
     double rstop = (1.0 + job->horizon_eps) * horizon_radius(a, M);
     if (r < rstop || r < job->r_in) return;
-    double u[4];
-    if (!fluid_velocity(job, y, r, u)) return;
-    double ct = y[3] / r;
-    double ne = job->ne0 * pow(r, job->ne_slope) * exp(-ct * ct / (2.0 * job->disk_w * job->disk_w));
-    double Th = job->thetae0 * pow(r, job->te_slope);
-    double Bm = job->b0 * pow(r, 0.5 * (job->ne_slope + job->te_slope));
-    if (!(ne > 0)) return;
+    double u[4], b[4], ne, Th, Bm;
     double g[4][4], gi[4][4];
     metric_cov(a, M, y, g);
+    if (job->emission == ORC_EMIT_GRID) {
+        /* fluid grid: u, b and the plasma from the lookup; b made a unit vector */
+        double P[8], pl[4];
+        if (!orc_grid_fluid(job, y, P, u, b, pl)) return;
+        ne = pl[0];
+        Th = pl[1];
+        Bm = pl[2];
+        double bb = sqrt(dot_g(g, b, b));
+        for (int m = 0; m < 4; ++m) b[m] /= bb;
+    } else {
+        if (!fluid_velocity(job, y, r, u)) return;
+        double ct = y[3] / r;
+        ne = job->ne0 * pow(r, job->ne_slope) * exp(-ct * ct / (2.0 * job->disk_w * job->disk_w));
+        Th = job->thetae0 * pow(r, job->te_slope);
+        Bm = job->b0 * pow(r, 0.5 * (job->ne_slope + job->te_slope));
+        if (!(ne > 0)) return;
+        /* field direction: toroidal and vertical unit vectors of the fluid frame */
+        double vphi[4] = {0, -y[2], y[1], 0}, vz[4] = {0, 0, 0, 1}, ephi[4], ez[4];
+        double pu = dot_g(g, u, vphi);
+        for (int m = 0; m < 4; ++m) ephi[m] = vphi[m] + pu * u[m];
+        double nph = sqrt(dot_g(g, ephi, ephi));
+        for (int m = 0; m < 4; ++m) ephi[m] /= nph;
+        double pz = dot_g(g, u, vz), pe = dot_g(g, ephi, vz);
+        for (int m = 0; m < 4; ++m) ez[m] = vz[m] + pz * u[m] - pe * ephi[m];
+        double nz = sqrt(dot_g(g, ez, ez));
+        double bn = 1.0 / sqrt(1.0 + job->bz_ratio * job->bz_ratio);
+        for (int m = 0; m < 4; ++m) {
+            ez[m] /= nz;
+            b[m] = (ephi[m] + job->bz_ratio * ez[m]) * bn;
+        }
+    }
     inv4(g, gi);
     double kup[4], p[4], fup[4] = {0, 0, 0, 0};
     raise4(gi, y + 4, kup);
@@ -543,20 +697,6 @@ static void emission_pol(const orc_job* job, const double* y, const double* fcov
      * to the RK4 truncation error, so normalise it */
     double dn = sqrt(dot_g(g, d, d));
     for (int m = 0; m < 4; ++m) d[m] /= dn;
-    /* field direction: toroidal and vertical unit vectors of the fluid frame */
-    double vphi[4] = {0, -y[2], y[1], 0}, vz[4] = {0, 0, 0, 1}, ephi[4], ez[4], b[4];
-    double pu = dot_g(g, u, vphi);
-    for (int m = 0; m < 4; ++m) ephi[m] = vphi[m] + pu * u[m];
-    double nph = sqrt(dot_g(g, ephi, ephi));
-    for (int m = 0; m < 4; ++m) ephi[m] /= nph;
-    double pz = dot_g(g, u, vz), pe = dot_g(g, ephi, vz);
-    for (int m = 0; m < 4; ++m) ez[m] = vz[m] + pz * u[m] - pe * ephi[m];
-    double nz = sqrt(dot_g(g, ez, ez));
-    double bn = 1.0 / sqrt(1.0 + job->bz_ratio * job->bz_ratio);
-    for (int m = 0; m < 4; ++m) {
-        ez[m] /= nz;
-        b[m] = (ephi[m] + job->bz_ratio * ez[m]) * bn;
-    }
     double cthb = dot_g(g, d, b);
     if (cthb > 1) cthb = 1;
     if (cthb < -1) cthb = -1;
@@ -676,7 +816,7 @@ static void camera_polbasis(const orc_job* job, const camera* c, double al, doub
 /* Emission (J4) and absorption/rotation (K7) coefficients at one point, code units. */
 static void coefficients(const orc_job* job, const double* y, int pol, double* J4, double* K7)
 {
-    if (job->emission == ORC_EMIT_SYNCH_DISK) {
+    if (job->emission == ORC_EMIT_SYNCH_DISK || job->emission == ORC_EMIT_GRID) {
         emission_pol(job, y, pol ? y + 8 : NULL, J4, K7);
         return;
     }

@@ -17,6 +17,7 @@ extern "C" {
 /* Emission models. */
 enum { ORC_EMIT_CFG0 = 0,      /* j = r^-2 exp(-z^2/(2 (w r)^2)), Keplerian flow, no absorption */
        ORC_EMIT_SYNCH_DISK = 1,/* thermal synchrotron thin disk, polarized (Stokes IQUV)       */
+       ORC_EMIT_GRID = 2,      /* thermal synchrotron from a fluid grid (rho, u, u^i, B^i)      */
        ORC_EMIT_BLOB = 8 };    /* flat-space test: static Gaussian blob, sigma = blob_sigma    */
 enum { ORC_FLOW_KEPLER = 0, ORC_FLOW_STATIC = 1 };
 enum { ORC_NORM_IBAR_INT = 0, ORC_NORM_PEAK = 1 };
@@ -52,6 +53,17 @@ typedef struct orc_job {
     double ne0, thetae0, b0, nu_hz, ne_slope, te_slope, r_in;
     double length_cm;    /* GM/c^2 in cm (converts affine lengths to cm) */
     double bz_ratio;     /* vertical / toroidal field ratio of the disk (1 = 1:1) */
+    /* fluid grid (ORC_EMIT_GRID): cells (k, j, i) over phi, theta, ln r stored as
+     * grid[((k * gn2 + j) * gn1 + i) * 8 + q], q = rho, u, u^r, u^theta, u^phi, B^r, B^theta,
+     * B^phi (Kerr-Schild spherical components); cell centres at
+     * ln r = glogr_min + (i + 1/2) dx1, theta = (j + 1/2) pi/gn2, phi = (k + 1/2) 2 pi/gn3 */
+    const float* grid;
+    int gn1, gn2, gn3, gpad;
+    double glogr_min, glogr_max;
+    double gamma_ad;     /* adiabatic index of the fluid */
+    double m_unit;       /* mass unit (g): rho_cgs = rho m_unit / length_cm^3 */
+    double r_high, r_low;/* ion-to-electron temperature ratio at high / low plasma beta */
+    double sigma_cut;    /* no emission where b^2/rho > sigma_cut */
 } orc_job;
 
 typedef struct orc_rayinfo {
@@ -81,6 +93,8 @@ int    orc_synch_coeffs(double ne, double thetae, double B, double nu, double th
 void   orc_segment(const double* K7, const double* J4, double h, double* E16, double* X4);
 void   orc_transport_rhs(const orc_job* job, const double* y12, double* df4);
 void   orc_coefficients(const orc_job* job, const double* y12, int pol, double* J4, double* K7);
+int    orc_grid_fluid(const orc_job* job, const double* x, double* prim8, double* u4, double* b4,
+                      double* plasma4);
 int    orc_emission(const orc_job* job, const double* x, const double* k, double* jnu,
                     double* nu_fl);
 double orc_ibar_int(const double* img, int nx, int ny, int stride);

@@ -14,7 +14,7 @@ from __future__ import annotations
 import numpy as np
 
 # Options shared by both sides by NAME (each side owns its enum values).
-EMISSION = ("cfg0", "synch_disk", "blob")
+EMISSION = ("cfg0", "synch_disk", "grid", "blob")
 FLOW = ("kepler", "static")
 ABS_NORM = ("ibar_int", "peak")
 INTERP = ("linear", "nearest")
@@ -26,7 +26,8 @@ BASE = dict(a=0.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33, n0y=33, levels
             emission="cfg0", flow="kepler", stokes=1, subrings=0, precision="fp64",
             max_steps=100000, step_frac=0.05, h_min=1e-4, horizon_eps=0.01, escape_frac=1.01,
             disk_w=0.3, blob_sigma=1.0, ne0=0.0, thetae0=0.0, b0=0.0, nu_hz=230e9,
-            ne_slope=-1.1, te_slope=-0.84, r_in=0.0, length_cm=9.6e14, bz_ratio=1.0)
+            ne_slope=-1.1, te_slope=-0.84, r_in=0.0, length_cm=9.6e14, bz_ratio=1.0,
+            gamma_ad=13.0 / 9.0, m_unit=3e26, r_high=20.0, r_low=1.0, sigma_cut=1.0)
 
 
 def job(**over) -> dict:
@@ -122,6 +123,21 @@ def cfg1_analytic(**over) -> dict:
                          disk_w=0.3, precision="mixed"), **over})
 
 
+def cfg2(**over) -> dict:
+    """The seeded GRMHD-like snapshot (grmhd_snapshot(0): Fishbone-Moncrief torus, a = 0.94,
+    288 x 128 x 128 cells over ln r in [ln 1.2, ln 1000]) seen at inclination 163 deg with a
+    160 M field of view, 257^2 -> 8193^2 over 5 levels, at 230 GHz with R_high = 20, R_low = 1,
+    a magnetisation cut at sigma = 1 (Sec. 4.2 and 5), mass unit 3e26 g for an M87*-mass hole, and
+    the tolerances the paper chose for its GRMHD images, R_rel = 1e-3, R_abs = 0.025 (Sec. 4.1).
+    Unpolarized transfer with thermal-synchrotron emission and absorption; the snapshot itself
+    is passed separately (grid=)."""
+    return job(**{**dict(a=0.94, incl_deg=163.0, fov=160.0, n0x=257, n0y=257, levels=5,
+                         R_rel=1e-3, R_abs=0.025, abs_norm="ibar_int", emission="grid",
+                         stokes=1, nu_hz=230e9, length_cm=9.6e14, gamma_ad=13.0 / 9.0,
+                         m_unit=3e26, r_high=20.0, r_low=1.0, sigma_cut=1.0,
+                         precision="mixed_df"), **over})
+
+
 BENCH_WORKLOADS = {
     "cfg1": ("adaptive polarized render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, FOV 40 M, "
              "r_obs 1000 M, RK4 h=0.05r; thermal-synchrotron thin disk (n_e~r^-1.1, T_e~r^-0.84, "
@@ -154,3 +170,178 @@ def cfg3(seed: int = 0, n: int = 256, **over) -> list:
         p.update(over)
         out.append(p)
     return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Config 2: a seeded, GRMHD-like snapshot on a spherical Kerr-Schild grid
+# ---------------------------------------------------------------------------------------------
+
+GRID_FIELDS = ("rho", "uu", "U1", "U2", "U3", "B1", "B2", "B3")
+
+
+def _bl_metric(a, r, th):
+    s2, c2 = np.sin(th) ** 2, np.cos(th) ** 2
+    Sig = r * r + a * a * c2
+    gtt = -(1 - 2 * r / Sig)
+    gtp = -2 * a * r * s2 / Sig
+    gpp = (r * r + a * a + 2 * a * a * r * s2 / Sig) * s2
+    return gtt, gtp, gpp
+
+
+def _bl_geom(a, r, th):
+    """Boyer-Lindquist Sigma, Delta, A = (r^2+a^2)^2 - a^2 Delta sin^2 theta."""
+    Sig = r * r + a * a * np.cos(th) ** 2
+    Delta = r * r - 2 * r + a * a
+    A = (r * r + a * a) ** 2 - a * a * Delta * np.sin(th) ** 2
+    return Sig, Delta, A
+
+
+def fm_ell(a: float, r_max: float) -> float:
+    """u^t u_phi of the prograde circular geodesic at r_max in the equatorial plane: the
+    Fishbone-Moncrief constant that puts the pressure maximum of the torus at r_max."""
+    gtt, gtp, gpp = _bl_metric(a, np.array(r_max), np.array(np.pi / 2))
+    Om = 1.0 / (r_max ** 1.5 + a)
+    ut = 1.0 / np.sqrt(-(gtt + 2 * Om * gtp + Om * Om * gpp))
+    return float(ut * ut * (gtp + Om * gpp))
+
+
+def fm_lnh(a: float, ell: float, r, th):
+    """ln h + const of the Fishbone & Moncrief (1976) torus, u^t u_phi = ell.
+
+    With the zero-angular-momentum observers' lapse e^nu = sqrt(Sigma Delta / A), e^psi =
+    sqrt(g_phiphi), omega = 2 a r / A and the fluid's velocity v relative to them (Lorentz factor
+    G), u^t u_phi = ell gives G^2 = (1 + s)/2 with s = sqrt(1 + 4 ell^2 e^(2 nu - 2 psi)); the
+    Euler equation d ln h = u^t d u_t + u^phi d u_phi then integrates to
+    ln h = 1/2 ln((1 + s) A / (Sigma Delta)) - s/2 - ell omega + const."""
+    Sig, Delta, A = _bl_geom(a, r, th)
+    X = Sig * Sig * Delta / (A * A * np.sin(th) ** 2)
+    s = np.sqrt(1 + 4 * ell * ell * X)
+    return 0.5 * np.log((1 + s) * A / (Sig * Delta)) - 0.5 * s - ell * 2 * a * r / A
+
+
+def fm_velocity(a: float, ell: float, r, th):
+    """(u^t, u^phi) of the Fishbone-Moncrief torus flow (u^r = u^theta = 0)."""
+    Sig, Delta, A = _bl_geom(a, r, th)
+    X = Sig * Sig * Delta / (A * A * np.sin(th) ** 2)
+    s = np.sqrt(1 + 4 * ell * ell * X)
+    G2 = 0.5 * (1 + s)
+    v = np.sqrt(1 - 1 / G2) * np.sign(ell)
+    enu = np.sqrt(Sig * Delta / A)
+    epsi = np.sqrt(A / Sig) * np.sin(th)
+    ut = np.sqrt(G2) / enu
+    Om = 2 * a * r / A + v * enu / epsi
+    return ut, ut * Om
+
+
+def _ks_frame(a, r, th, ph):
+    """Outgoing Kerr-Schild Cartesian position, F, L and the Jacobian d(x,y,z)/d(r,theta,phi)."""
+    e = np.exp(1j * ph)
+    xy = (r - 1j * a) * np.sin(th) * e
+    x, y, z = xy.real, xy.imag, r * np.cos(th)
+    F = 2 * r ** 3 / (r ** 4 + a * a * z * z)
+    L = np.stack([(r * x - a * y) / (r * r + a * a), (r * y + a * x) / (r * r + a * a), z / r], -1)
+    dr = np.sin(th) * e
+    dth = (r - 1j * a) * np.cos(th) * e
+    dph = 1j * xy
+    Jm = np.stack([np.stack([dr.real, dth.real, dph.real], -1),
+                   np.stack([dr.imag, dth.imag, dph.imag], -1),
+                   np.stack([np.cos(th), -r * np.sin(th), np.zeros_like(r)], -1)], -2)
+    return F, L, Jm
+
+
+def grmhd_snapshot(seed: int = 0, n1: int = 288, n2: int = 128, n3: int = 128, a: float = 0.94,
+                   r_in: float = 6.0, r_max: float = 12.0, sigma: float = 0.3, beta_max: float = 10.0,
+                   gamma: float = 13.0 / 9.0, logr_min: float = np.log(1.2),
+                   logr_max: float = np.log(1000.0)) -> dict:
+    """A Fishbone-Moncrief torus with a lognormal turbulent density, on the grid x1 = ln r
+    (n1 cells in [logr_min, logr_max]), theta (n2 cells in [0, pi]), phi (n3 cells in [0, 2 pi))
+    of Kerr-Schild spherical coordinates, cell-centred.
+
+    Torus: u^t u_phi = ell with ell from the circular geodesic at r_max, enthalpy h from
+    fm_lnh normalised to h = 1 at (r_in, pi/2); polytrope rho ~ ((h - 1)(gamma - 1)/gamma)^(1/(gamma-1))
+    scaled to rho_max = 1, internal energy u = rho (h - 1)/gamma.  Density and internal energy are
+    multiplied by exp(sigma G - sigma^2/2), G a unit-variance Gaussian random field with
+    P(k) ~ k^-11/3 on the index grid (seeded FFT).  Field: B^r = -d_theta A_phi / sqrt(-g),
+    B^theta = d_r A_phi / sqrt(-g), sqrt(-g) = Sigma sin(theta), A_phi = max(rho/rho_max - 0.2, 0),
+    scaled to gas/magnetic pressure beta_max at the density maximum.  Outside the torus a floor
+    rho = 1e-4 r^-1.5, u = 1e-6 r^-2.5 moving with the zero-angular-momentum observers.
+    Velocities are the contravariant u^r, u^theta, u^phi (u^r = u^theta = 0: the same in
+    Boyer-Lindquist and Kerr-Schild coordinates).  Returns float32 (n3, n2, n1, 8) in the order
+    of GRID_FIELDS plus the grid description."""
+    rng = np.random.default_rng(seed)
+    x1 = logr_min + (np.arange(n1) + 0.5) * (logr_max - logr_min) / n1
+    th = (np.arange(n2) + 0.5) * np.pi / n2
+    r = np.exp(x1)
+    R, TH = np.meshgrid(r, th, indexing="ij")          # (n1, n2)
+    Sig, Delta, A_ = _bl_geom(a, R, TH)
+    ok = Delta > 0
+    ell = fm_ell(a, r_max)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        lnh = fm_lnh(a, ell, R, TH) - fm_lnh(a, ell, np.array(r_in), np.array(np.pi / 2))
+        h = np.where(ok & (R >= r_in), np.exp(np.where(ok, lnh, 0.0)), 0.0)
+        ut_t, uph_t = fm_velocity(a, ell, R, TH)
+    inside = h > 1.0
+    hm1 = np.where(inside, h - 1.0, 0.0)
+    rho_t = (hm1 * (gamma - 1) / gamma) ** (1 / (gamma - 1))
+    rho_t /= rho_t.max()
+    uu_t = rho_t * hm1 / gamma
+    rho = np.maximum(rho_t, 1e-4 * R ** -1.5)
+    uu = np.maximum(uu_t, 1e-6 * R ** -2.5)
+    gtt, gtp, gpp = _bl_metric(a, R, TH)
+    uph_z = np.where(ok, np.sqrt(np.clip(A_ / (Sig * np.where(ok, Delta, 1.0)), 0.0, None)), 0.0) \
+        * (-gtp / gpp)
+    ut = np.where(inside, ut_t, 0.0)
+    uph = np.where(inside, uph_t, uph_z)
+    Aphi = np.maximum(rho_t - 0.2, 0.0)
+    dAr = np.gradient(Aphi, r, axis=0)
+    dAth = np.gradient(Aphi, th, axis=1)
+    B1 = -dAth / (Sig * np.sin(TH))
+    B2 = dAr / (Sig * np.sin(TH))
+    # plasma beta at the density maximum (u^r = u^theta = 0 there: b^t = 0 in Boyer-Lindquist
+    # form, b^2 = (g_rr B1^2 + g_thth B2^2)/(u^t)^2 ... evaluated with the Kerr-Schild relation below)
+    imax = np.unravel_index(np.argmax(rho_t), rho_t.shape)
+    b2 = _b2_ks(a, R[imax], TH[imax], ut[imax], uph[imax], B1[imax], B2[imax])
+    pmax = (gamma - 1) * uu[imax]
+    scale = np.sqrt(2 * pmax / beta_max / b2) if b2 > 0 else 0.0
+    B1 *= scale
+    B2 *= scale
+    k1 = np.fft.fftfreq(n1)[:, None, None]
+    k2 = np.fft.fftfreq(n2)[None, :, None]
+    k3 = np.fft.rfftfreq(n3)[None, None, :]
+    kk = np.sqrt(k1 ** 2 + k2 ** 2 + k3 ** 2)
+    amp = np.where(kk > 0, np.where(kk > 0, kk, 1.0) ** (-11.0 / 6.0), 0.0)
+    noise = rng.standard_normal(amp.shape) + 1j * rng.standard_normal(amp.shape)
+    G = np.fft.irfftn(noise * amp, s=(n1, n2, n3), axes=(0, 1, 2))
+    G = (G - G.mean()) / G.std()
+    pert = np.exp(sigma * G - 0.5 * sigma * sigma)
+    out = np.zeros((n3, n2, n1, 8), np.float32)
+
+    def put(idx, field2d, p=None):
+        f = np.broadcast_to(field2d[:, :, None], (n1, n2, n3)) if p is None else field2d[:, :, None] * p
+        out[..., idx] = np.transpose(f, (2, 1, 0))
+
+    put(0, rho, pert)
+    put(1, uu, pert)
+    put(4, uph)
+    put(5, B1)
+    put(6, B2)
+    return dict(data=np.ascontiguousarray(out), n1=n1, n2=n2, n3=n3, logr_min=float(logr_min),
+                logr_max=float(logr_max), a=a, gamma=gamma)
+
+
+def _b2_ks(a, r, th, ut, uph, B1, B2):
+    """b^2 = b^mu b_mu from B^i and u^mu (u^r = u^theta = 0) with the Kerr-Schild metric:
+    b^t = B^i u^mu g_{i mu}, b^i = (B^i + b^t u^i)/u^t (Gammie, McKinney & Toth 2003)."""
+    F, L, Jm = _ks_frame(a, np.array(r), np.array(th), np.array(0.0))
+    uc = Jm[:, 2] * uph
+    Bc = Jm @ np.array([B1, B2, 0.0])
+    g = np.eye(4)
+    g[0, 0] = -1.0
+    l = np.concatenate([[1.0], -L])
+    g = g + F * np.outer(l, l)
+    u = np.concatenate([[ut], uc])
+    Bv = np.concatenate([[0.0], Bc])
+    bt = Bv @ g @ u
+    b = (Bv + bt * u) / ut
+    b[0] = bt
+    return float(b @ g @ b)
