@@ -45,7 +45,7 @@ extern "C" {
 #define ART_ERR_UNSUPPORTED (-4) /* option combination not built */
 #define ART_ERR_DEVICE (-5)      /* a kernel reported an internal inconsistency */
 
-enum { ART_EMIT_CFG0 = 0, ART_EMIT_SYNCH_DISK = 1 };
+enum { ART_EMIT_CFG0 = 0, ART_EMIT_SYNCH_DISK = 1, ART_EMIT_GRID = 2 };
 enum { ART_FLOW_KEPLER = 0, ART_FLOW_STATIC = 1 };
 enum { ART_NORM_IBAR_INT = 0, ART_NORM_PEAK = 1 };
 enum { ART_INTERP_LINEAR = 0, ART_INTERP_NEAREST = 1 };
@@ -69,7 +69,7 @@ typedef struct art_job {
     int32_t edge_mode;   /* ART_EDGE_ONESIDED or ART_EDGE_TRACE (trace points lacking a stencil) */
     int32_t emission;    /* ART_EMIT_* */
     int32_t flow;        /* ART_FLOW_* */
-    int32_t stokes;      /* 1 (unpolarized) or 4 (I, Q, U, V; ART_EMIT_SYNCH_DISK) */
+    int32_t stokes;      /* 1 (unpolarized) or 4 (I, Q, U, V; ART_EMIT_SYNCH_DISK or _GRID) */
     int32_t subrings;    /* 0, or the number of subring planes n = 0..subrings-1 */
     int32_t precision;   /* ART_FP64; ART_MIXED: FP32 with an FP64 re-trace of near-critical rays;
                           * ART_MIXED_DF: the same with the re-traced geodesic in double-float
@@ -89,6 +89,12 @@ typedef struct art_job {
      * r^((ne_slope + te_slope)/2) [G] along (e_phi + bz_ratio e_z) in the fluid frame, Keplerian,
      * no emission inside r_in; observed at nu_hz for a hole with GM/c^2 = length_cm. */
     double ne0, thetae0, b0, nu_hz, ne_slope, te_slope, r_in, length_cm, bz_ratio;
+    /* ART_EMIT_GRID: thermal synchrotron from the context's fluid grid (art_load_grid), the
+     * GRMHD-image model of Sec. 4.2 and 5: Theta_e = (m_p/m_e)(gamma_ad - 1) u / (rho (1 + R)),
+     * R = T_i/T_e = (r_high beta^2 + r_low)/(1 + beta^2) with beta = (gamma_ad - 1) u/(b^2/2);
+     * n_e = rho m_unit/(length_cm^3 (m_p + m_e)), |B| = |b| c sqrt(4 pi m_unit / length_cm^3);
+     * no emission where b^2/rho > sigma_cut; observed at nu_hz. */
+    double gamma_ad, m_unit, r_high, r_low, sigma_cut;
 } art_job;
 
 /* Statistics of one render (host struct, filled on return). */
@@ -179,9 +185,10 @@ int art_render(art_ctx* ctx, const art_job* job, const double* truth_dev, double
  * images that have that level, and the rays of all images share one device queue, so one
  * persistent trace launch per level packs rays of uneven length from images of different spins,
  * inclinations, fields of view, grids and depths.  jobs[i] may differ in everything except
- * stokes, subrings and precision (one kernel kind and one plane count per batch; else
- * ART_ERR_ARG).  imgs is a HOST array of n device pointers (planes x ny_i x nx_i doubles each);
- * masks (nullable, entries nullable) a host array of n device pointers.  stats_host (nullable)
+ * stokes, subrings, precision and whether the emission is ART_EMIT_GRID (one kernel kind and one
+ * plane count per batch; else ART_ERR_ARG); grid jobs all use the context's grid.  imgs is a
+ * HOST array of n device pointers (planes x ny_i x nx_i doubles each); masks (nullable, entries
+ * nullable) a host array of n device pointers.  stats_host (nullable)
  * receives n entries: rays per level and the normalisation per image; steps, re-traced, capped
  * and NaN rays and kernel launches are batch totals repeated in every entry.  Synchronises when
  * stats are requested.  Errors as art_render. */
@@ -221,6 +228,27 @@ int art_profile_read(art_ctx* ctx, art_launch_record* recs_host, int cap, int* n
 #define ART_NOALLOC_MAX_RAYS (1 << 20)
 int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_dev, int64_t n,
                              double* out_dev, const art_rayaux* aux, void* stream);
+
+/* The fluid snapshot of ART_EMIT_GRID jobs (Sec. 4.2: images of GRMHD snapshots; the lookup is
+ * this library's).  grid holds n3 x n2 x n1 cells of eight FP32 primitives, cell (k, j, i) at
+ * grid[((k * n2 + j) * n1 + i) * 8 + q], q = rho, u (internal energy), u^r, u^theta, u^phi
+ * (contravariant four-velocity), B^r, B^theta, B^phi (B^i = *F^{it}), all in Kerr-Schild spherical
+ * coordinates of the job's spin (x + i y = (r - i a) sin(theta) e^{i phi}, z = r cos(theta)),
+ * code units (G = c = M = 1; Heaviside-Lorentz field units, magnetic pressure b^2/2).
+ * Cell centres: ln r = logr_min + (i + 1/2)(logr_max - logr_min)/n1, theta = (j + 1/2) pi/n2,
+ * phi = (k + 1/2) 2 pi/n3.  Samples are trilinear in (ln r, theta, phi); ln r and theta clamp to
+ * the outer cell centres, phi is periodic, and points with ln r outside [logr_min, logr_max] do
+ * not emit.  u^t follows from u.u = -1.
+ *   - grid may be a device pointer on the context's device (16-byte aligned; referenced, not
+ *     copied: the caller keeps it alive and unchanged while jobs use it) or host memory (copied
+ *     into context-owned device memory before the call returns).
+ *   - grid == NULL unloads.  Loading replaces the previous grid (synchronises the stream first).
+ *   - n1, n2 >= 2, n3 >= 1, logr_max > logr_min, at most 2^30 cells; else ART_ERR_ARG (also
+ *     for a device pointer on another device or misaligned).  ART_ERR_OOM, ART_ERR_CUDA.
+ * Grid jobs on a context without a grid return ART_ERR_ARG; art_trace_pixels_noalloc has no
+ * context and returns ART_ERR_UNSUPPORTED for them. */
+int art_load_grid(art_ctx* ctx, const float* grid, int32_t n1, int32_t n2, int32_t n3,
+                  double logr_min, double logr_max);
 
 /* Image metrics of plane 0 (Eqs. interpdef, fluxdef, msedef): out_host[0] = interpolation
  * fraction (mask_dev nullable -> 0), [1] = flux error with the trapezoid flux, [2] = MSE

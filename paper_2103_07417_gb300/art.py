@@ -21,7 +21,7 @@ MASK_UNSET, MASK_TRACED, MASK_INTERP = 0, 1, 2
 RAY_ESCAPED, RAY_CAPTURED, RAY_CAP, RAY_NAN = 0, 1, 2, 3
 
 _NAMES = dict(
-    emission={"cfg0": 0, "synch_disk": 1},
+    emission={"cfg0": 0, "synch_disk": 1, "grid": 2},
     flow={"kepler": 0, "static": 1},
     abs_norm={"ibar_int": 0, "peak": 1},
     interp={"linear": 0, "nearest": 1},
@@ -44,7 +44,8 @@ class Job(ctypes.Structure):
         ("disk_w", ctypes.c_double), ("ne0", ctypes.c_double), ("thetae0", ctypes.c_double),
         ("b0", ctypes.c_double), ("nu_hz", ctypes.c_double), ("ne_slope", ctypes.c_double),
         ("te_slope", ctypes.c_double), ("r_in", ctypes.c_double), ("length_cm", ctypes.c_double),
-        ("bz_ratio", ctypes.c_double),
+        ("bz_ratio", ctypes.c_double), ("gamma_ad", ctypes.c_double), ("m_unit", ctypes.c_double),
+        ("r_high", ctypes.c_double), ("r_low", ctypes.c_double), ("sigma_cut", ctypes.c_double),
     ]
 
 
@@ -68,7 +69,8 @@ class RayAux(ctypes.Structure):
                 ("nturn", ctypes.c_void_p), ("min_r", ctypes.c_void_p)]
 
 
-_JOB_DEFAULTS = dict(fp64_sweep=3.0 * 3.141592653589793)
+_JOB_DEFAULTS = dict(fp64_sweep=3.0 * 3.141592653589793, gamma_ad=13.0 / 9.0, m_unit=3e26,
+                     r_high=20.0, r_low=1.0, sigma_cut=1.0)
 
 
 def make_job(**params) -> Job:
@@ -92,7 +94,7 @@ _lib = None
 EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_planes",
            "art_trace_pixels", "art_ibar_int", "art_refine_level", "art_render",
            "art_render_host", "art_metrics", "art_profile", "art_profile_read",
-           "art_trace_pixels_noalloc", "art_render_batch")
+           "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid")
 NOALLOC_MAX_RAYS = 1 << 20
 
 
@@ -127,6 +129,7 @@ def load():
             lib.art_profile_read.argtypes = [vp, P(LaunchRecord), ctypes.c_int, P(ctypes.c_int)]
             lib.art_trace_pixels_noalloc.argtypes = [P(Job), vp, i64, vp, P(RayAux), vp]
             lib.art_render_batch.argtypes = [vp, P(Job), i32, P(vp), P(vp), P(Stats)]
+            lib.art_load_grid.argtypes = [vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double]
             _lib = lib
     return _lib
 
@@ -278,6 +281,34 @@ class Context:
         _check(load().art_metrics(self._ctx, _dptr(truth), _dptr(img), _dptr(mask), nx, ny, out),
                "art_metrics")
         return dict(IF=out[0], FE=out[1], MSE=out[2], MSE_mean=out[3])
+
+    def art_load_grid(self, grid, n1: int, n2: int, n3: int, logr_min: float, logr_max: float):
+        """Load the fluid snapshot of grid jobs: a contiguous float32 CUDA tensor (referenced; the
+        context keeps a Python reference) or a numpy array (copied), shape (n3, n2, n1, 8)."""
+        if grid is None:
+            ptr = None
+        elif isinstance(grid, np.ndarray):
+            if not (grid.flags.c_contiguous and grid.dtype == np.float32):
+                raise ValueError("grid must be a contiguous float32 array")
+            ptr = grid.ctypes.data_as(ctypes.c_void_p)
+        else:
+            import torch
+            if grid.dtype != torch.float32:
+                raise ValueError("grid must be float32")
+            ptr = _dptr(grid)
+        _check(load().art_load_grid(self._ctx, ptr, int(n1), int(n2), int(n3), float(logr_min),
+                                    float(logr_max)), "art_load_grid")
+        self._grid_ref = grid if (grid is not None and not isinstance(grid, np.ndarray)) else None
+
+    def load_grid(self, snap: dict, on_device: bool = True):
+        """Load a snapshot dict (data, n1, n2, n3, logr_min, logr_max), by default as a device
+        tensor."""
+        data = snap["data"]
+        if on_device:
+            import torch
+            data = torch.from_numpy(np.ascontiguousarray(data, np.float32)).to(f"cuda:{self.device}")
+        self.art_load_grid(data, snap["n1"], snap["n2"], snap["n3"], snap["logr_min"],
+                           snap["logr_max"])
 
     def art_profile(self, enable: bool):
         _check(load().art_profile(self._ctx, int(bool(enable))), "art_profile")

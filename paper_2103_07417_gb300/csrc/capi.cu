@@ -17,8 +17,13 @@ struct art_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
-    int occ[3][2] = {};   // resident blocks per SM of the trace kernels [kind][polarized]
-    int occb[3][2] = {};  // the same for the batched trace kernels
+    int occ[3][TV_COUNT] = {};   // resident blocks per SM of the trace kernels [kind][variant]
+    int occb[3][TV_COUNT] = {};  // the same for the batched trace kernels
+    // fluid grid of ART_EMIT_GRID (art_load_grid): referenced, or owned when copied from the host
+    const float* grid = nullptr;
+    float* grid_owned = nullptr;
+    int32_t g_n1 = 0, g_n2 = 0, g_n3 = 0;
+    double g_x1min = 0.0, g_x1max = 0.0;
     // batched rendering tables and queue (grown, never shrunk)
     DevJob* bjobs = nullptr;
     SynchConst* bsynch = nullptr;
@@ -140,12 +145,18 @@ static int make_devjob(const art_job* job, DevJob* J)
         return ART_ERR_ARG;
     if (job->stokes != 1 && job->stokes != 4) return ART_ERR_UNSUPPORTED;
     if (job->subrings < 0 || job->subrings > 4) return ART_ERR_UNSUPPORTED;
-    if (job->emission != ART_EMIT_CFG0 && job->emission != ART_EMIT_SYNCH_DISK)
+    if (job->emission != ART_EMIT_CFG0 && job->emission != ART_EMIT_SYNCH_DISK &&
+        job->emission != ART_EMIT_GRID)
         return ART_ERR_UNSUPPORTED;
-    if (job->stokes == 4 && job->emission != ART_EMIT_SYNCH_DISK) return ART_ERR_UNSUPPORTED;
+    if (job->stokes == 4 && job->emission == ART_EMIT_CFG0) return ART_ERR_UNSUPPORTED;
     if (job->emission == ART_EMIT_SYNCH_DISK &&
         (!(job->ne0 >= 0.0) || !(job->thetae0 > 0.0) || !(job->b0 > 0.0) || !(job->nu_hz > 0.0) ||
          !(job->length_cm > 0.0) || !(job->r_in >= 0.0)))
+        return ART_ERR_ARG;
+    if (job->emission == ART_EMIT_GRID &&
+        (!(job->nu_hz > 0.0) || !(job->length_cm > 0.0) || !(job->gamma_ad > 1.0) ||
+         !(job->m_unit > 0.0) || !(job->r_high > 0.0) || !(job->r_low > 0.0) ||
+         !(job->sigma_cut > 0.0)))
         return ART_ERR_ARG;
     if (job->flow != ART_FLOW_KEPLER && job->flow != ART_FLOW_STATIC) return ART_ERR_ARG;
     if (job->interp != ART_INTERP_LINEAR && job->interp != ART_INTERP_NEAREST) return ART_ERR_ARG;
@@ -182,24 +193,45 @@ static int make_devjob(const art_job* job, DevJob* J)
     return ART_OK;
 }
 
-// Constants of the synchrotron disk in the scaled form the kernels use (cgs constants, CODATA).
-static void make_synch(const art_job* job, SynchConst* S)
+// Constants of the synchrotron models in the scaled form the kernels use (cgs constants, CODATA).
+// g: the context's fluid grid (ART_EMIT_GRID), null where there is none.
+static void make_synch(const art_job* job, const art_ctx* g, SynchConst* S)
 {
     const double e = 4.80320471e-10, me = 9.1093837015e-28, c = 2.99792458e10;
-    const double hp = 6.62607015e-27, pi = 3.14159265358979323846;
+    const double hp = 6.62607015e-27, pi = 3.14159265358979323846, mp = 1.67262192369e-24;
     memset(S, 0, sizeof *S);
-    if (job->emission != ART_EMIT_SYNCH_DISK) return;
+    if (job->emission != ART_EMIT_SYNCH_DISK && job->emission != ART_EMIT_GRID) return;
     const double L = job->length_cm, nu = job->nu_hz;
-    S->ne0 = job->ne0;
-    S->th0 = job->thetae0;
-    S->b0 = job->b0;
-    S->ne_s = job->ne_slope;
-    S->te_s = job->te_slope;
-    S->b_s = 0.5 * (job->ne_slope + job->te_slope);
-    S->inv_2w2 = 1.0 / (2.0 * job->disk_w * job->disk_w);
-    S->r_in = job->r_in;
-    S->bz = job->bz_ratio;
-    S->bnorm = 1.0 / sqrt(1.0 + job->bz_ratio * job->bz_ratio);
+    if (job->emission == ART_EMIT_SYNCH_DISK) {
+        S->ne0 = job->ne0;
+        S->th0 = job->thetae0;
+        S->b0 = job->b0;
+        S->ne_s = job->ne_slope;
+        S->te_s = job->te_slope;
+        S->b_s = 0.5 * (job->ne_slope + job->te_slope);
+        S->inv_2w2 = 1.0 / (2.0 * job->disk_w * job->disk_w);
+        S->r_in = job->r_in;
+        S->bz = job->bz_ratio;
+        S->bnorm = 1.0 / sqrt(1.0 + job->bz_ratio * job->bz_ratio);
+    } else if (g && g->grid) {
+        const double L3 = L * L * L;
+        S->grid = reinterpret_cast<const float4*>(g->grid);
+        S->g_n1 = g->g_n1;
+        S->g_n2 = g->g_n2;
+        S->g_n3 = g->g_n3;
+        S->g_x1min = g->g_x1min;
+        S->g_x1max = g->g_x1max;
+        S->g_inv_dx1 = g->g_n1 / (g->g_x1max - g->g_x1min);
+        S->g_inv_dth = g->g_n2 / pi;
+        S->g_inv_dph = g->g_n3 / (2.0 * pi);
+        S->g_gm1 = job->gamma_ad - 1.0;
+        S->g_ne_unit = job->m_unit / (L3 * (mp + me));
+        S->g_b_unit = c * sqrt(4.0 * pi * job->m_unit / L3);
+        S->g_th_unit = (mp / me) * (job->gamma_ad - 1.0);
+        S->g_r_high = job->r_high;
+        S->g_r_low = job->r_low;
+        S->g_sigma_cut = job->sigma_cut;
+    }
     S->LCj = L * sqrt(2.0) * pi * e * e / (3.0 * c);
     S->CB = e / (2.0 * pi * me * c);
     S->nu_obs = nu;
@@ -209,9 +241,21 @@ static void make_synch(const art_job* job, SynchConst* S)
     S->LCQ = L * e * e * e * e / (4.0 * pi * pi * me * me * me * c * c * c * nu * nu * nu);
 }
 
+// A grid job needs the context's grid.
+static int check_grid(const art_ctx* c, const art_job* job)
+{
+    return (job->emission == ART_EMIT_GRID && !c->grid) ? ART_ERR_ARG : ART_OK;
+}
+
+// Trace-kernel variant of a job (occupancy table index).
+static int variant_of(const DevJob& J)
+{
+    return (J.stokes == 4 ? TV_POL : 0) | (J.emission == ART_EMIT_GRID ? TV_GRID : 0);
+}
+
 // The same validation for the allocation-free entry point (noalloc.cu).
 int art_make_devjob(const art_job* job, DevJob* J) { return make_devjob(job, J); }
-void art_make_synch(const art_job* job, SynchConst* S) { make_synch(job, S); }
+void art_make_synch(const art_job* job, SynchConst* S) { make_synch(job, nullptr, S); }
 
 extern "C" int art_create(art_ctx** out, int device, void* stream)
 {
@@ -228,17 +272,17 @@ extern "C" int art_create(art_ctx** out, int device, void* stream)
         return ART_ERR_CUDA;
     }
     for (int kd = 0; kd < 3; ++kd)
-        for (int pl = 0; pl < 2; ++pl) {
-            if (trace_occupancy(TraceKind(kd), pl != 0, &c->occ[kd][pl]) != cudaSuccess) {
+        for (int v = 0; v < TV_COUNT; ++v) {
+            if (trace_occupancy(TraceKind(kd), v, &c->occ[kd][v]) != cudaSuccess) {
                 delete c;
                 return ART_ERR_CUDA;
             }
-            if (c->occ[kd][pl] < 1) c->occ[kd][pl] = 1;
-            if (trace_batch_occupancy(kd, pl != 0, &c->occb[kd][pl]) != cudaSuccess) {
+            if (c->occ[kd][v] < 1) c->occ[kd][v] = 1;
+            if (trace_batch_occupancy(kd, v, &c->occb[kd][v]) != cudaSuccess) {
                 delete c;
                 return ART_ERR_CUDA;
             }
-            if (c->occb[kd][pl] < 1) c->occb[kd][pl] = 1;
+            if (c->occb[kd][v] < 1) c->occb[kd][v] = 1;
         }
     *out = c;
     return ART_OK;
@@ -272,6 +316,7 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFreeHost(c->bcounts_host);
     cudaFree(c->bqueue);
     cudaFree(c->breroute);
+    cudaFree(c->grid_owned);
     for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -325,7 +370,7 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
     TraceArgs a;
     memset(&a, 0, sizeof a);
     a.job = J;
-    make_synch(job, &a.synch);
+    make_synch(job, c, &a.synch);
     a.cam = c->cam;
     a.queue = c->queue;
     a.count = count;
@@ -340,7 +385,7 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
         a.aux_nturn = aux->nturn;
         a.aux_minr = aux->min_r;
     }
-    const int pl = J.stokes == 4 ? 1 : 0;
+    const int pl = variant_of(J);
     const int g64 = c->num_sms * c->occ[TK_FP64][pl], g32 = c->num_sms * c->occ[TK_FP32][pl];
     const int gdf = c->num_sms * c->occ[TK_DF][pl];
     int k;
@@ -394,7 +439,7 @@ extern "C" int art_trace_pixels(art_ctx* c, const art_job* job, const int32_t* p
     if (!c || (n > 0 && (!pix_dev || !out_dev)) || n < 0) return ART_ERR_ARG;
     DevJob J;
     int rc = make_devjob(job, &J);
-    if (rc) return rc;
+    if (rc || (rc = check_grid(c, job))) return rc;
     if (n == 0) return ART_OK;
     CK(cudaSetDevice(c->device));
     if ((rc = ensure_fixed(c)) || (rc = ensure_queue(c, n))) return rc;
@@ -457,7 +502,7 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
     if (!c || !img_dev) return ART_ERR_ARG;
     DevJob J;
     int rc = make_devjob(job, &J);
-    if (rc) return rc;
+    if (rc || (rc = check_grid(c, job))) return rc;
     CK(cudaSetDevice(c->device));
     if ((rc = ensure_fixed(c)) || (rc = ensure_queue(c, max_level_rays(J)))) return rc;
     cudaStream_t st = c->stream;
@@ -529,7 +574,7 @@ extern "C" int art_render_host(art_ctx* c, const art_job* job, double* img_host,
     if (!c || !img_host) return ART_ERR_ARG;
     DevJob J;
     int rc = make_devjob(job, &J);
-    if (rc) return rc;
+    if (rc || (rc = check_grid(c, job))) return rc;
     CK(cudaSetDevice(c->device));
     const int64_t npix = (int64_t)J.nx * J.ny;
     if (npix * J.planes > c->hcap) {
@@ -693,7 +738,8 @@ static int trace_queue_batch(art_ctx* c, const DevJob& J0, int nimg)
     a.planes = J0.planes;
     a.stokes = J0.stokes;
     a.precision = J0.precision;
-    const int pl = J0.stokes == 4 ? 1 : 0;
+    a.emission = J0.emission;
+    const int pl = variant_of(J0);
     a.fetch = c->counters + C_FETCH;
     CK(cudaMemsetAsync(c->counters + C_FETCH, 0, sizeof(unsigned long long) * 3, c->stream));
     int k;
@@ -741,9 +787,11 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
         if (rc) return rc;
         if (!imgs[i]) return ART_ERR_ARG;
         if (J[i].stokes != J[0].stokes || J[i].subrings != J[0].subrings ||
-            J[i].precision != J[0].precision)
+            J[i].precision != J[0].precision ||
+            (J[i].emission == ART_EMIT_GRID) != (J[0].emission == ART_EMIT_GRID))
             return ART_ERR_ARG;  // one kernel kind and one plane count per batch
-        make_synch(&jobs[i], &S[i]);
+        if ((rc = check_grid(c, &jobs[i]))) return rc;
+        make_synch(&jobs[i], c, &S[i]);
         p3[3 * i] = jobs[i].a;
         p3[3 * i + 1] = jobs[i].r_obs;
         p3[3 * i + 2] = jobs[i].incl_deg;
@@ -823,5 +871,51 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
         }
         if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
     }
+    return ART_OK;
+}
+
+extern "C" int art_load_grid(art_ctx* c, const float* grid, int32_t n1, int32_t n2, int32_t n3,
+                             double logr_min, double logr_max)
+{
+    if (!c) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    if (!grid) {  // unload
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->grid_owned);
+        c->grid_owned = nullptr;
+        c->grid = nullptr;
+        c->g_n1 = c->g_n2 = c->g_n3 = 0;
+        return ART_OK;
+    }
+    if (n1 < 2 || n2 < 2 || n3 < 1 || !(logr_max > logr_min)) return ART_ERR_ARG;
+    const int64_t cells = (int64_t)n1 * n2 * n3;
+    if (cells > ((int64_t)1 << 30)) return ART_ERR_ARG;
+    const size_t bytes = (size_t)cells * 8 * sizeof(float);
+    cudaPointerAttributes at;
+    memset(&at, 0, sizeof at);
+    if (cudaPointerGetAttributes(&at, grid) != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    const bool on_device = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (on_device && at.device != c->device) return ART_ERR_ARG;
+    if (on_device && (reinterpret_cast<uintptr_t>(grid) & 15)) return ART_ERR_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->grid_owned);
+    c->grid_owned = nullptr;
+    c->grid = nullptr;
+    if (on_device) {
+        c->grid = grid;
+    } else {
+        CK(cudaMalloc(&c->grid_owned, bytes));
+        CK(cudaMemcpyAsync(c->grid_owned, grid, bytes, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->grid = c->grid_owned;
+    }
+    c->g_n1 = n1;
+    c->g_n2 = n2;
+    c->g_n3 = n3;
+    c->g_x1min = logr_min;
+    c->g_x1max = logr_max;
     return ART_OK;
 }

@@ -1,0 +1,137 @@
+// grid.cuh -- emission from a fluid snapshot on a spherical Kerr-Schild grid (a GRMHD-like
+// model, Sec. 4.2 and 5 of the paper: electron temperatures from the R_high prescription and a
+// magnetisation cut).
+//
+// Lookup: the snapshot holds eight FP32 primitives per cell (rho, u, u^r, u^theta, u^phi, B^r,
+// B^theta, B^phi; contravariant Kerr-Schild spherical components) as two float4, cell-centred on
+// a uniform grid in (ln r, theta, phi).  A sample at (ln r, theta, phi) is the trilinear
+// interpolant of the eight surrounding cells: per axis f = (coordinate - start)/spacing - 1/2;
+// ln r and theta clamp f to [0, n - 1], phi wraps; points with ln r outside the grid do not emit.
+// A sample reads 8 cells x 32 B = 256 B through the read-only data path; consecutive samples of a
+// ray fall in the same or neighbouring cells, so most of them hit in L1/L2.
+//
+// Fluid reconstruction (Gammie, McKinney & Toth 2003 for b):
+//   u^t = q / (sqrt(p^2 - g_tt q) - p),  q = 1 + g_ij u^i u^j,  p = g_ti u^i
+//     (the positive root of g_mu nu u^mu u^nu = -1 that stays continuous through g_tt = 0);
+//   b^t = g_{i mu} B^i u^mu,  b^i = (B^i + b^t u^i)/u^t;
+//   T_i/T_e = (R_high beta^2 + R_low)/(1 + beta^2), beta = (gamma - 1) u / (b^2/2)
+//     (Moscibrodzka, Falcke & Shiokawa 2016), Theta_e = (m_p/m_e)(gamma - 1) u/(rho (1 + T_i/T_e));
+//   n_e = rho * ne_unit, |B| = sqrt(b^2) * b_unit;  no emission where b^2/rho > sigma_cut.
+// In outgoing Cartesian Kerr-Schild form g_tt = F - 1, g_ti = -F L_i, g_ij = delta_ij + F L_i L_j.
+#pragma once
+#include "synch.cuh"
+
+namespace art {
+
+template <class Q>
+ART_HD void grid_axis_clamped(Q f, int n, int& i0, Q& w)
+{
+    f = f < Q(0) ? Q(0) : (f > Q(n - 1) ? Q(n - 1) : f);
+    int i = int(floor(f));
+    i = i > n - 2 ? n - 2 : i;
+    i = i < 0 ? 0 : i;
+    i0 = i;
+    w = n > 1 ? f - Q(i) : Q(0);
+}
+
+// Emission of the grid model at one point (J4, K7 as emission_synch).  f nullable.
+template <class Q>
+__device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, const Q* f,
+                                              const DevJob& J, const SynchConst& S, Q* J4, Q* K7)
+{
+    for (int i = 0; i < 4; ++i) J4[i] = Q(0);
+    for (int i = 0; i < 7; ++i) K7[i] = Q(0);
+    if (r < Q(J.r_in_stop)) return;
+    const Q lr = log(r);
+    if (!(lr >= Q(S.g_x1min) && lr <= Q(S.g_x1max))) return;
+    const Q a = Q(J.a), a2 = Q(J.a2);
+    Q ct = s.z / r;
+    ct = ct > Q(1) ? Q(1) : (ct < Q(-1) ? Q(-1) : ct);
+    const Q th = acos(ct);
+    const Q twopi = Q(6.283185307179586476925);
+    Q ph = atan2(s.y, s.x) + atan2(a, r);
+    if (ph < Q(0)) ph += twopi;
+    if (ph >= twopi) ph -= twopi;
+    const int n1 = S.g_n1, n2 = S.g_n2, n3 = S.g_n3;
+    int i0, j0;
+    Q w1, w2;
+    grid_axis_clamped<Q>((lr - Q(S.g_x1min)) * Q(S.g_inv_dx1) - Q(0.5), n1, i0, w1);
+    grid_axis_clamped<Q>(th * Q(S.g_inv_dth) - Q(0.5), n2, j0, w2);
+    const int i1 = n1 > 1 ? i0 + 1 : i0, j1 = n2 > 1 ? j0 + 1 : j0;
+    Q f3 = ph * Q(S.g_inv_dph) - Q(0.5);
+    Q fl = floor(f3);
+    Q w3 = f3 - fl;
+    int k0 = int(fl);
+    k0 = ((k0 % n3) + n3) % n3;
+    const int k1 = k0 + 1 == n3 ? 0 : k0 + 1;
+    Q P[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) P[q] = Q(0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int ii = (c & 1) ? i1 : i0, jj = (c & 2) ? j1 : j0, kk = (c & 4) ? k1 : k0;
+        const Q wt = ((c & 1) ? w1 : Q(1) - w1) * ((c & 2) ? w2 : Q(1) - w2) *
+                     ((c & 4) ? w3 : Q(1) - w3);
+        const float4* cell = S.grid + 2 * (((int64_t)kk * n2 + jj) * n1 + ii);
+        const float4 v0 = __ldg(cell), v1 = __ldg(cell + 1);
+        P[0] += wt * Q(v0.x);
+        P[1] += wt * Q(v0.y);
+        P[2] += wt * Q(v0.z);
+        P[3] += wt * Q(v0.w);
+        P[4] += wt * Q(v1.x);
+        P[5] += wt * Q(v1.y);
+        P[6] += wt * Q(v1.z);
+        P[7] += wt * Q(v1.w);
+    }
+    const Q rho = P[0], ug = P[1];
+    if (!(rho > Q(0)) || !(ug > Q(0))) return;
+    // d(x, y, z)/d(r, theta, phi) of x + i y = (r - i a) sin(theta) e^{i phi}, z = r cos(theta)
+    Q sp, cp;
+    sincos(ph, &sp, &cp);
+    const Q st = sqrt(Q(1) - ct * ct);
+    const Q Jm[3][3] = {{st * cp, ct * (r * cp + a * sp), -s.y},
+                        {st * sp, ct * (r * sp - a * cp), s.x},
+                        {ct, -r * st, Q(0)}};
+    Q u[4], B[4];
+    u[0] = B[0] = Q(0);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        u[1 + i] = Jm[i][0] * P[2] + Jm[i][1] * P[3] + Jm[i][2] * P[4];
+        B[1 + i] = Jm[i][0] * P[5] + Jm[i][1] * P[6] + Jm[i][2] * P[7];
+    }
+    const KSPoint<Q> G = ks_point<Q>(s.x, s.y, s.z, r, a, a2);
+    const Q Lu = G.Lx * u[1] + G.Ly * u[2] + G.Lz * u[3];
+    const Q LB = G.Lx * B[1] + G.Ly * B[2] + G.Lz * B[3];
+    const Q uu = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
+    const Q qn = Q(1) + uu + G.F * Lu * Lu;
+    const Q pn = -G.F * Lu;
+    const Q D = pn * pn - (G.F - Q(1)) * qn;
+    if (!(D >= Q(0))) return;
+    const Q den = sqrt(D) - pn;
+    if (!(den > Q(0))) return;
+    u[0] = qn / den;
+    const Q Bu = B[1] * u[1] + B[2] * u[2] + B[3] * u[3];
+    Q b[4];
+    b[0] = Bu + G.F * LB * (Lu - u[0]);
+    const Q iut = Q(1) / u[0];
+#pragma unroll
+    for (int i = 1; i < 4; ++i) b[i] = (B[i] + b[0] * u[i]) * iut;
+    const Q b2 = G.dot(b, b);
+    if (!(b2 > Q(0))) return;
+    if (b2 > Q(S.g_sigma_cut) * rho) return;
+    const Q pg = Q(S.g_gm1) * ug, pm = Q(0.5) * b2;
+    const Q pg2 = pg * pg, pm2 = pm * pm;
+    const Q trat = (Q(S.g_r_high) * pg2 + Q(S.g_r_low) * pm2) / (pg2 + pm2);
+    const Q Th = Q(S.g_th_unit) * ug / (rho * (Q(1) + trat));
+    const Q ne = Q(S.g_ne_unit) * rho;
+    const Q bm = sqrt(b2);
+    const Q Bm = Q(S.g_b_unit) * bm;
+    const Q ib = Q(1) / bm;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) b[m] *= ib;
+    const Q nu = kt * u[0] + s.kx * u[1] + s.ky * u[2] + s.kz * u[3];
+    if (!(nu > Q(0))) return;
+    synch_coeffs<Q>(G, s, kt, u, b, nu, ne, Th, Bm, f, S, J4, K7);
+}
+
+}  // namespace art

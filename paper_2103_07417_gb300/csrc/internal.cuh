@@ -61,14 +61,19 @@ struct BatchTraceArgs {
     unsigned long long* counters;
     int32_t* reroute;
     unsigned long long* reroute_count;
-    int planes, stokes, precision;
+    int planes, stokes, precision, emission;
 };
 
-// trace_batch.cu
+// Trace-kernel variants for occupancy queries: polarized and/or fluid-grid emission.
+enum TraceVariant { TV_POL = 1, TV_GRID = 2, TV_COUNT = 4 };
+
+// trace.cu / trace_batch.cu (dispatch) and trace_grid.cu / trace_grid_batch.cu (grid kernels)
 cudaError_t launch_camera_setup_batch(const DevJob* jobs_host_unused, const double* params3,
                                       int n, Camera* cams, cudaStream_t st);
 cudaError_t launch_trace_batch(const BatchTraceArgs& a, int kind, int grid, cudaStream_t st);
-cudaError_t trace_batch_occupancy(int kind, bool pol, int* blocks_per_sm);
+cudaError_t trace_batch_occupancy(int kind, int variant, int* blocks_per_sm);
+cudaError_t launch_trace_batch_grid(const BatchTraceArgs& a, int kind, int grid, cudaStream_t st);
+cudaError_t trace_batch_occupancy_grid(int kind, int variant, int* blocks_per_sm);
 
 // refine.cu (batched)
 cudaError_t launch_enqueue_base_batch(const DevJob* jobs, int n, int max_base, int64_t* queue,
@@ -85,7 +90,9 @@ cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_po
 enum TraceKind { TK_FP64 = 0, TK_FP32 = 1, TK_DF = 2 };
 cudaError_t launch_camera_setup(const art_job& job, Camera* cam, cudaStream_t st);
 cudaError_t launch_trace(const TraceArgs& a, TraceKind kind, int grid, cudaStream_t st);
-cudaError_t trace_occupancy(TraceKind kind, bool pol, int* blocks_per_sm);
+cudaError_t trace_occupancy(TraceKind kind, int variant, int* blocks_per_sm);
+cudaError_t launch_trace_grid(const TraceArgs& a, TraceKind kind, int grid, cudaStream_t st);
+cudaError_t trace_occupancy_grid(TraceKind kind, int variant, int* blocks_per_sm);
 constexpr int TRACE_BLOCK = 128;
 
 // refine.cu

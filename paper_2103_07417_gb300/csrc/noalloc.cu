@@ -88,6 +88,7 @@ extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_d
     DevJob J;
     int rc = art_make_devjob(job, &J);
     if (rc) return rc;
+    if (J.emission == ART_EMIT_GRID) return ART_ERR_UNSUPPORTED;  // the grid lives in a context
     if (n == 0) return ART_OK;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return ART_ERR_CUDA;

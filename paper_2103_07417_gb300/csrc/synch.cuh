@@ -31,7 +31,7 @@
 
 namespace art {
 
-// Constants of the synchrotron disk, precomputed on the host in double (keeps FP32 in range).
+// Constants of the synchrotron models, precomputed on the host in double (keeps FP32 in range).
 struct SynchConst {
     double ne0, th0, b0, ne_s, te_s, b_s, inv_2w2, r_in, bz, bnorm;
     double LCj;    // L sqrt2 pi e^2 / (3 c)
@@ -41,10 +41,23 @@ struct SynchConst {
     double invKB;  // c^2 / (2 h nu_obs^3)
     double LCV;    // L e^3 / (pi m^2 c^2 nu_obs^2)
     double LCQ;    // L e^4 / (4 pi^2 m^3 c^3 nu_obs^3)
+    // fluid grid (ART_EMIT_GRID): cells of 8 FP32 primitives as two float4
+    // {rho, u, u^r, u^theta}, {u^phi, B^r, B^theta, B^phi}, cell (k, j, i) at float4 index
+    // 2 ((k n2 + j) n1 + i); cell centres at ln r = x1_min + (i + 1/2)/inv_dx1, theta = (j + 1/2)
+    // pi/n2, phi = (k + 1/2) 2 pi/n3
+    const float4* grid;
+    int32_t g_n1, g_n2, g_n3, g_pad;
+    double g_x1min, g_x1max, g_inv_dx1, g_inv_dth, g_inv_dph;
+    double g_gm1;        // gamma_ad - 1
+    double g_ne_unit;    // m_unit / (L^3 (m_p + m_e))      [cm^-3 per code density]
+    double g_b_unit;     // c sqrt(4 pi m_unit / L^3)       [gauss per code field]
+    double g_th_unit;    // (m_p / m_e)(gamma_ad - 1)
+    double g_r_high, g_r_low, g_sigma_cut;
 };
 
+// K_0, K_1, K_2 scaled by e^x (K_n(x) e^x), so that FP32 stays finite for cold plasma (large x).
 template <class Q>
-ART_HD void bessel_k012(Q x, Q& K0, Q& K1, Q& K2)
+ART_HD void bessel_k012_scaled(Q x, Q& K0, Q& K1, Q& K2)
 {
     if (x <= Q(2)) {
         Q t = x / Q(3.75), t2 = t * t;
@@ -52,13 +65,13 @@ ART_HD void bessel_k012(Q x, Q& K0, Q& K1, Q& K2)
                t2 * (Q(0.2659732) + t2 * (Q(0.0360768) + t2 * Q(0.0045813))))));
         Q i1 = x * (Q(0.5) + t2 * (Q(0.87890594) + t2 * (Q(0.51498869) + t2 * (Q(0.15084934) +
                t2 * (Q(0.02658733) + t2 * (Q(0.00301532) + t2 * Q(0.00032411)))))));
-        Q y = Q(0.25) * x * x, lg = log(Q(0.5) * x);
-        K0 = -lg * i0 + (Q(-0.57721566) + y * (Q(0.42278420) + y * (Q(0.23069756) +
-             y * (Q(0.03488590) + y * (Q(0.00262698) + y * (Q(0.00010750) + y * Q(0.0000074)))))));
-        K1 = lg * i1 + (Q(1) / x) * (Q(1) + y * (Q(0.15443144) + y * (Q(-0.67278579) +
-             y * (Q(-0.18156897) + y * (Q(-0.01919402) + y * (Q(-0.00110404) + y * Q(-0.00004686)))))));
+        Q y = Q(0.25) * x * x, lg = log(Q(0.5) * x), ex = exp(x);
+        K0 = ex * (-lg * i0 + (Q(-0.57721566) + y * (Q(0.42278420) + y * (Q(0.23069756) +
+             y * (Q(0.03488590) + y * (Q(0.00262698) + y * (Q(0.00010750) + y * Q(0.0000074))))))));
+        K1 = ex * (lg * i1 + (Q(1) / x) * (Q(1) + y * (Q(0.15443144) + y * (Q(-0.67278579) +
+             y * (Q(-0.18156897) + y * (Q(-0.01919402) + y * (Q(-0.00110404) + y * Q(-0.00004686))))))));
     } else {
-        Q y = Q(2) / x, pre = exp(-x) / sqrt(x);
+        Q y = Q(2) / x, pre = Q(1) / sqrt(x);
         K0 = pre * (Q(1.25331414) + y * (Q(-0.07832358) + y * (Q(0.02189568) + y * (Q(-0.01062446) +
              y * (Q(0.00587872) + y * (Q(-0.00251540) + y * Q(0.00053208)))))));
         K1 = pre * (Q(1.25331414) + y * (Q(0.23498619) + y * (Q(-0.03655620) + y * (Q(0.01504268) +
@@ -113,36 +126,14 @@ ART_HD Q det4(const Q* A, const Q* B, const Q* C, const Q* D)
     return A[0] * c0 - A[1] * c1 + A[2] * c2 - A[3] * c3;
 }
 
-// Emission J4 and K7 = {aI,aQ,aU,aV,rQ,rU,rV} of the synchrotron disk at one point, code units.
-// f (nullable) is the transported covector; without it only the I terms are returned.
+// Thermal-synchrotron coefficients of a fluid element (velocity u, unit field direction b in its
+// frame, density ne [cm^-3], temperature Th, field Bm [G]) seen by the ray with covariant k
+// (kt, s.k) and fluid-frame frequency ratio nu = k.u > 0; f (nullable) is the transported
+// covector.  J4, K7 in code units, in the (e_N, e_E) basis of f.
 template <class Q>
-ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const DevJob& J,
-                           const SynchConst& S, Q* J4, Q* K7)
+ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const Q* u, const Q* b,
+                         Q nu, Q ne, Q Th, Q Bm, const Q* f, const SynchConst& S, Q* J4, Q* K7)
 {
-    for (int i = 0; i < 4; ++i) J4[i] = Q(0);
-    for (int i = 0; i < 7; ++i) K7[i] = Q(0);
-    if (r < Q(J.r_in_stop) || r < Q(S.r_in)) return;
-    const Q a = Q(J.a), a2 = Q(J.a2);
-    Q ct = s.z / r, ct2 = ct * ct, r2 = r * r;
-    // Keplerian flow (Omega at Boyer-Lindquist r, theta)
-    Q st2 = Q(1) - ct2;
-    Q iSig = Q(1) / (r2 + a2 * ct2);
-    Q gtt = -(Q(1) - Q(2) * r * iSig);
-    Q gtp = -Q(2) * a * r * st2 * iSig;
-    Q gpp = (r2 + a2 + Q(2) * a2 * r * st2 * iSig) * st2;
-    Q Om = Q(1) / (r * sqrt(r) + a);
-    Q nrm = -(gtt + Q(2) * Om * gtp + Om * Om * gpp);
-    if (!(nrm > Q(0))) return;
-    Q ut = Q(1) / sqrt(nrm);
-    Q u[4] = {ut, -Om * s.y * ut, Om * s.x * ut, Q(0)};
-    Q nu = ut * (kt + Om * (s.x * s.ky - s.y * s.kx));
-    if (!(nu > Q(0))) return;
-    Q lr = log(r);
-    Q ne = Q(S.ne0) * exp(Q(S.ne_s) * lr - ct2 * Q(S.inv_2w2));
-    Q Th = Q(S.th0) * exp(Q(S.te_s) * lr);
-    Q Bm = Q(S.b0) * exp(Q(S.b_s) * lr);
-    if (!(ne > Q(0))) return;
-    KSPoint<Q> G = ks_point<Q>(s.x, s.y, s.z, r, a, a2);
     Q kc[4] = {kt, s.kx, s.ky, s.kz}, ku[4];
     G.raise(kc, ku);
     Q d[4];
@@ -150,31 +141,19 @@ ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const De
     // unit propagation direction (the integrated k is null only to the truncation error)
     Q dn = Q(1) / sqrt(G.dot(d, d));
     for (int m = 0; m < 4; ++m) d[m] *= dn;
-    // field direction (e_phi + q e_z)/sqrt(1 + q^2) in the fluid frame
-    Q ephi[4] = {Q(0), -s.y, s.x, Q(0)};
-    Q pu = G.dot(u, ephi);
-    for (int m = 0; m < 4; ++m) ephi[m] += pu * u[m];
-    Q nph = Q(1) / sqrt(G.dot(ephi, ephi));
-    for (int m = 0; m < 4; ++m) ephi[m] *= nph;
-    Q ez[4] = {Q(0), Q(0), Q(0), Q(1)};
-    Q pz = G.dot(u, ez), pe = G.dot(ephi, ez);
-    for (int m = 0; m < 4; ++m) ez[m] += pz * u[m] - pe * ephi[m];
-    Q nz = Q(1) / sqrt(G.dot(ez, ez));
-    Q b[4];
-    for (int m = 0; m < 4; ++m) b[m] = (ephi[m] + Q(S.bz) * ez[m] * nz) * Q(S.bnorm);
     Q cth = G.dot(d, b);
     cth = cth > Q(1) ? Q(1) : (cth < Q(-1) ? Q(-1) : cth);
     Q sth2 = Q(1) - cth * cth;
     Q sth = sqrt(sth2);
-    // coefficients in the E-vector frame
+    // coefficients in the E-vector frame; K_n e^x keeps 1/K_2 finite, e^(x - X^1/3) recombines
     Q x = Q(1) / Th, K0, K1, K2;
-    bessel_k012<Q>(x, K0, K1, K2);
+    bessel_k012_scaled<Q>(x, K0, K1, K2);
     Q jI = Q(0), jQ = Q(0);
     if (sth > Q(1e-12)) {
         Q nus = Q(2.0 / 9.0) * Q(S.CB) * Bm * Th * Th * sth;
         Q X = Q(S.nu_obs) * nu / nus;
         Q x3 = cbrt(X), x6 = sqrt(x3), x2 = x3 * x6;  // X^1/3, X^1/6, X^1/2
-        Q pre = Q(S.LCj) * ne * nus / K2 * exp(-x3) / (nu * nu);
+        Q pre = Q(S.LCj) * ne * nus / K2 * exp(x - x3) / (nu * nu);
         Q t96 = exp(Q(0.96) * log(Th));
         Q q = (Q(7) * t96 + Q(35)) / (Q(10) * t96 + Q(75));
         const Q k1112 = Q(1.8877486253633868);  // 2^(11/12)
@@ -211,6 +190,51 @@ ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const De
     K7[4] = rQ * c2;
     K7[5] = rQ * s2;
     K7[6] = rV;
+}
+
+// Emission J4 and K7 = {aI,aQ,aU,aV,rQ,rU,rV} of the synchrotron disk at one point, code units.
+// f (nullable) is the transported covector; without it only the I terms are returned.
+template <class Q>
+ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const DevJob& J,
+                           const SynchConst& S, Q* J4, Q* K7)
+{
+    for (int i = 0; i < 4; ++i) J4[i] = Q(0);
+    for (int i = 0; i < 7; ++i) K7[i] = Q(0);
+    if (r < Q(J.r_in_stop) || r < Q(S.r_in)) return;
+    const Q a = Q(J.a), a2 = Q(J.a2);
+    Q ct = s.z / r, ct2 = ct * ct, r2 = r * r;
+    // Keplerian flow (Omega at Boyer-Lindquist r, theta)
+    Q st2 = Q(1) - ct2;
+    Q iSig = Q(1) / (r2 + a2 * ct2);
+    Q gtt = -(Q(1) - Q(2) * r * iSig);
+    Q gtp = -Q(2) * a * r * st2 * iSig;
+    Q gpp = (r2 + a2 + Q(2) * a2 * r * st2 * iSig) * st2;
+    Q Om = Q(1) / (r * sqrt(r) + a);
+    Q nrm = -(gtt + Q(2) * Om * gtp + Om * Om * gpp);
+    if (!(nrm > Q(0))) return;
+    Q ut = Q(1) / sqrt(nrm);
+    Q u[4] = {ut, -Om * s.y * ut, Om * s.x * ut, Q(0)};
+    Q nu = ut * (kt + Om * (s.x * s.ky - s.y * s.kx));
+    if (!(nu > Q(0))) return;
+    Q lr = log(r);
+    Q ne = Q(S.ne0) * exp(Q(S.ne_s) * lr - ct2 * Q(S.inv_2w2));
+    Q Th = Q(S.th0) * exp(Q(S.te_s) * lr);
+    Q Bm = Q(S.b0) * exp(Q(S.b_s) * lr);
+    if (!(ne > Q(0))) return;
+    KSPoint<Q> G = ks_point<Q>(s.x, s.y, s.z, r, a, a2);
+    // field direction (e_phi + q e_z)/sqrt(1 + q^2) in the fluid frame
+    Q ephi[4] = {Q(0), -s.y, s.x, Q(0)};
+    Q pu = G.dot(u, ephi);
+    for (int m = 0; m < 4; ++m) ephi[m] += pu * u[m];
+    Q nph = Q(1) / sqrt(G.dot(ephi, ephi));
+    for (int m = 0; m < 4; ++m) ephi[m] *= nph;
+    Q ez[4] = {Q(0), Q(0), Q(0), Q(1)};
+    Q pz = G.dot(u, ez), pe = G.dot(ephi, ez);
+    for (int m = 0; m < 4; ++m) ez[m] += pz * u[m] - pe * ephi[m];
+    Q nz = Q(1) / sqrt(G.dot(ez, ez));
+    Q b[4];
+    for (int m = 0; m < 4; ++m) b[m] = (ephi[m] + Q(S.bz) * ez[m] * nz) * Q(S.bnorm);
+    synch_coeffs<Q>(G, s, kt, u, b, nu, ne, Th, Bm, f, S, J4, K7);
 }
 
 // Parallel transport of the covector f along the geodesic (outgoing Kerr-Schild form):

@@ -19,6 +19,7 @@
 
 #include "dfloat.cuh"
 #include "internal.cuh"
+#include "grid.cuh"
 #include "synch.cuh"
 
 namespace art {
@@ -139,11 +140,19 @@ __device__ __forceinline__ R phi1(R x)
     return x > R(1e-8) ? -expm1(-x) / x : R(1) - R(0.5) * x;
 }
 
+// Emission models as a compile-time choice of the trace kernels: the analytic models (selected at
+// run time by the job) or the fluid grid, whose lookup is kept out of the other kernels' code.
+enum EmitKernel { EM_ANALYTIC = 0, EM_GRID = 1 };
+
 // Emission/absorption/rotation coefficients at a point (J4, K7 as in synch.cuh).
-template <class Q, bool POL>
+template <class Q, bool POL, int EM>
 __device__ __forceinline__ void coefficients(const RayState<Q>& q, Q r, Q kt, const Q* f,
                                              const DevJob& J, const SynchConst& S, Q* J4, Q* K7)
 {
+    if (EM == EM_GRID) {
+        emission_grid<Q>(q, r, kt, POL ? f : nullptr, J, S, J4, K7);
+        return;
+    }
     if (J.emission == ART_EMIT_SYNCH_DISK) {
         emission_synch<Q>(q, r, kt, POL ? f : nullptr, J, S, J4, K7);
         return;
@@ -153,7 +162,7 @@ __device__ __forceinline__ void coefficients(const RayState<Q>& q, Q r, Q kt, co
     J4[0] = emission_cfg0<Q>(q, r, kt, J);
 }
 
-template <class R, bool POL>
+template <class R, bool POL, int EM>
 __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const SynchConst& S,
                                          const Camera& cam, int32_t pix)
 {
@@ -184,7 +193,7 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Sy
     }
     RayState<Q> q = to_q<Q>(t.s);
     t.r = ks_radius<Q>(q.x, q.y, q.z, Q(J.a2));
-    coefficients<Q, POL>(q, t.r, Q(t.kt), t.f, J, S, t.J0, t.K0);
+    coefficients<Q, POL, EM>(q, t.r, Q(t.kt), t.f, J, S, t.J0, t.K0);
     t.T = Q(1);
     for (int p = 0; p < MAXPL; ++p) t.acc[p] = Q(0);
     t.min_r = float(t.r);
@@ -200,7 +209,7 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Sy
 // One RK4 step plus the transfer segment; returns true when the ray has terminated.  SWEEP
 // accumulates the angle swept by the position vector (used to route rays in mixed precision);
 // POL carries the polarization covector through the RK4 stages and solves the Stokes segment.
-template <class R, bool SWEEP, bool POL>
+template <class R, bool SWEEP, bool POL, int EM>
 __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const SynchConst& S)
 {
     using Q = typename Aux<R>::Q;
@@ -269,7 +278,7 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const Sy
     }
     Q rn = ks_radius<Q>(q.x, q.y, q.z, a2q);
     Q J1[4], K1[7];
-    coefficients<Q, POL>(q, rn, Q(t.kt), t.f, J, S, J1, K1);
+    coefficients<Q, POL, EM>(q, rn, Q(t.kt), t.f, J, S, J1, K1);
     // subring index: polar turning points counted from the first equatorial crossing on
     int seg = t.nturn;
     if (oz * q.z < Q(0)) t.crossed = 1;

@@ -57,3 +57,35 @@ def test_no_device_fails_loudly():
     assert rc == art.ART_ERR_CUDA
     with pytest.raises(RuntimeError):
         art.Context(0)
+
+
+def _struct_fields(name):
+    src = open(os.path.join(ROOT, "include", "art.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, flags=re.S).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, rest = decl.split(None, 1)
+        for nm in rest.split(","):
+            out.append((ctype, nm.strip().lstrip("*")))
+    return out
+
+
+def test_job_struct_matches_header():
+    """The binding's art_job mirrors the header field by field (names, order, widths)."""
+    fields = _struct_fields("art_job")
+    width = {"double": ctypes.c_double, "int32_t": ctypes.c_int32}
+    assert [n for _, n in fields] == [n for n, _ in art.Job._fields_]
+    for (ctype, n), (pn, pt) in zip(fields, art.Job._fields_):
+        assert width[ctype] == pt, n
+
+
+def test_noalloc_rejects_grid_jobs_before_gpu_work():
+    """A grid job has no context to hold its grid: the allocation-free call refuses it before
+    touching any device state (checked on the host: an empty ray list, null pointers)."""
+    job = art.make_job(**W.cfg2(n0x=9, n0y=9, levels=0))
+    rc = art.load().art_trace_pixels_noalloc(ctypes.byref(job), None, 0, None, None, None)
+    assert rc == art.ART_ERR_UNSUPPORTED

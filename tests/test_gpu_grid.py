@@ -1,0 +1,186 @@
+"""GPU parity of the fluid-grid emission model (the seeded GRMHD-like torus snapshot, 288 x 128 x
+128 cells) against the CPU oracle, through the C-ABI.
+
+FP64 path: per pixel |I_gpu - I_oracle| <= 1e-6 max(I, 1e-6 I_peak) (the device's Bessel
+functions are polynomial approximations good to ~2e-7; the lookup itself agrees to rounding);
+polarized: every Stokes parameter within 2e-6 of max(I, 1e-6 I_peak).  Mixed paths:
+sum (dI)^2 / (N mean(I)^2) <= 1e-5.  Masks of adaptive renders identical except for points whose
+estimate ties the threshold to rounding."""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2103_07417_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _art():
+    from paper_2103_07417_gb300 import art
+    return art
+
+
+@pytest.fixture(scope="module")
+def snap():
+    return W.grmhd_snapshot(seed=0)
+
+
+@pytest.fixture(scope="module")
+def ctx(snap):
+    art = _art()
+    c = art.Context(0)
+    c.load_grid(snap)
+    yield c
+    c.close()
+
+
+def _close(g, r, tol):
+    I = r[:, 0]
+    floor = 1e-6 * np.max(np.abs(I))
+    lim = tol * np.maximum(np.abs(I), floor)
+    return np.abs(g - r) <= lim[:, None]
+
+
+def _trace_both(ctx, snap, params):
+    art = _art()
+    job = art.make_job(**params)
+    nx, ny = art.art_image_size(job)
+    pix = np.arange(nx * ny, dtype=np.int32)
+    out, aux = ctx.trace_pixels(job, torch.from_numpy(pix).cuda())
+    ref, info = O.trace_pixels(O.make_job(grid=snap, **params), pix.astype(np.int64))
+    return out.cpu().numpy(), ref, aux, info
+
+
+CASES = [
+    ("cfg2_center", W.cfg2(n0x=33, n0y=33, levels=1, fov=60.0)),
+    ("cfg2_ragged_i100", W.cfg2(incl_deg=100.0, n0x=21, n0y=13, levels=1, fov=50.0)),
+    ("cfg2_edge_on_r_high80", W.cfg2(incl_deg=88.0, r_high=80.0, n0x=17, n0y=17, levels=1,
+                                     fov=40.0)),
+]
+
+
+@pytest.mark.parametrize("name,params", CASES, ids=[c[0] for c in CASES])
+def test_grid_trace_fp64_matches_oracle(ctx, snap, name, params):
+    params = {**params, "precision": "fp64"}
+    g, ref, aux, info = _trace_both(ctx, snap, params)
+    assert ref[:, 0].max() > 0
+    assert (ref[:, 0] > 1e-3 * ref[:, 0].max()).sum() > 20, "the case should see the torus"
+    ok = _close(g, ref, 1e-6)
+    assert ok.all(), (name, np.argwhere(~ok)[:5], g[~ok[:, 0]][:3], ref[~ok[:, 0]][:3])
+    np.testing.assert_array_equal(aux["status"].cpu().numpy(), info["status"])
+
+
+def test_grid_polarized_fp64_matches_oracle(ctx, snap):
+    """Polarized transfer through the snapshot with a mass unit that keeps the Faraday depth of
+    order unity (rotation ~2 rad): every Stokes parameter within 2e-6."""
+    params = {**W.cfg2(n0x=15, n0y=15, levels=1, fov=50.0, stokes=4, incl_deg=60.0, m_unit=3e24),
+              "precision": "fp64"}
+    g, ref, _, _ = _trace_both(ctx, snap, params)
+    ok = _close(g, ref, 2e-6)
+    assert ok.all(), np.argwhere(~ok)[:5]
+    assert np.abs(ref[:, 1:3]).max() > 0.5 * ref[:, 0].max()
+
+
+def test_grid_polarized_faraday_thick_fp64(ctx, snap):
+    """At the workload's mass unit the torus is Faraday thick (rotation up to ~1e3 rad), so the
+    ~2e-7 relative accuracy of the device's Bessel-function ratios turns into ~1e-4 rad of EVPA:
+    I within 2e-6, Q, U, V within 2e-3 I_peak."""
+    params = {**W.cfg2(n0x=15, n0y=15, levels=1, fov=50.0, stokes=4, incl_deg=60.0),
+              "precision": "fp64"}
+    g, ref, _, _ = _trace_both(ctx, snap, params)
+    assert _close(g[:, :1], ref[:, :1], 2e-6).all()
+    assert np.abs(g[:, 1:] - ref[:, 1:]).max() <= 2e-3 * ref[:, 0].max()
+
+
+def test_grid_render_fp64_matches_oracle(ctx, snap):
+    """33^2 -> 129^2 adaptive render with the paper's GRMHD tolerances."""
+    art = _art()
+    params = {**W.cfg2(n0x=33, n0y=33, levels=2, fov=60.0), "precision": "fp64"}
+    img, mask, st = ctx.render(art.make_job(**params))
+    g, gm = img.cpu().numpy()[0], mask.cpu().numpy()
+    ref, ref_mask, ref_st = O.render(O.make_job(grid=snap, **params), None)
+    same = gm == ref_mask
+    assert (~same).sum() <= 2
+    assert 0 < st["rays_traced"] < g.size
+    ok = _close(g[same][:, None], ref[same][:, None], 1e-6)
+    assert ok.all()
+    assert abs(st["rays_traced"] - ref_st["rays_traced"]) <= (~same).sum()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df", "fp32"])
+def test_grid_mixed_precision_error_bound(ctx, snap, precision):
+    art = _art()
+    params = W.cfg2(n0x=33, n0y=33, levels=1, fov=60.0, R_rel=-1.0, R_abs=-1.0)
+    img, _, _ = ctx.render(art.make_job(**{**params, "precision": precision}))
+    ref, _, _ = O.render(O.make_job(grid=snap, **{**params, "precision": "fp64"}), None)
+    g = img.cpu().numpy()[0]
+    mse = np.sum((g - ref) ** 2) / (g.size * np.mean(ref) ** 2)
+    assert mse < 1e-5, (precision, mse)
+
+
+def test_grid_load_host_equals_device_and_errors(snap):
+    art = _art()
+    params = {**W.cfg2(n0x=9, n0y=9, levels=1, fov=50.0), "precision": "fp64"}
+    job = art.make_job(**params)
+    pix = torch.arange(17 * 17, dtype=torch.int32, device="cuda")
+    c = art.Context(0)
+    try:
+        with pytest.raises(RuntimeError):       # no grid loaded
+            c.trace_pixels(job, pix)
+        c.load_grid(snap, on_device=False)      # host copy
+        a, _ = c.trace_pixels(job, pix)
+        c.load_grid(snap, on_device=True)       # device reference
+        b, _ = c.trace_pixels(job, pix)
+        assert torch.equal(a, b)
+        with pytest.raises(RuntimeError):       # bad shape
+            c.art_load_grid(snap["data"], 1, 128, 128, 0.0, 1.0)
+        c.art_load_grid(None, 0, 0, 0, 0.0, 0.0)
+        with pytest.raises(RuntimeError):       # unloaded
+            c.trace_pixels(job, pix)
+    finally:
+        c.close()
+    out = torch.empty((pix.numel(), 1), dtype=torch.float64, device="cuda")
+    rc = art.art_trace_pixels_noalloc(job, pix, out)
+    assert rc == art.ART_ERR_UNSUPPORTED
+
+
+def test_grid_workload_full_render_sampled(ctx, snap):
+    """The 257^2 -> 8193^2 (5 levels) render of the snapshot at the benchmark's settings
+    (FP32 + double-float re-trace): 128 sampled traced pixels re-traced by the oracle in FP64,
+    MSE relative to mean(I)^2 <= 1e-5; sampled interpolated pixels equal the mean of their
+    previous-level neighbours."""
+    art = _art()
+    params = W.cfg2()
+    img, mask, st = ctx.render(art.make_job(**params))
+    g = img[0].cpu().numpy()
+    m = mask.cpu().numpy()
+    ny, nx = m.shape
+    assert (nx, ny) == (8193, 8193)
+    assert (m == art.MASK_TRACED).sum() == st["rays_traced"]
+    assert st["rays_nan"] == 0
+    rng = np.random.default_rng(5)
+    traced = np.flatnonzero(m.ravel() == art.MASK_TRACED)
+    bright = traced[g.ravel()[traced] > 1e-3 * g.max()]
+    pick = np.concatenate([rng.choice(traced, 64, replace=False), rng.choice(bright, 64, replace=False)])
+    ref, _ = O.trace_pixels(O.make_job(grid=snap, **{**params, "precision": "fp64"}),
+                            pick.astype(np.int64))
+    got = g.ravel()[pick]
+    mean_i = np.mean(ref[:, 0])
+    assert np.sum((got - ref[:, 0]) ** 2) / (len(pick) * mean_i ** 2) < 1e-5
+    interp = np.flatnonzero(m.ravel() == art.MASK_INTERP)
+    for p in rng.choice(interp, size=300, replace=False):
+        j, i = divmod(int(p), nx)
+        for k in range(1, params["levels"] + 1):
+            s_ = 1 << (params["levels"] - k)
+            if i % s_ == 0 and j % s_ == 0:
+                break
+        oi, oj = (i // s_) % 2, (j // s_) % 2
+        if oi and oj:
+            want = 0.25 * (((g[j - s_, i - s_] + g[j + s_, i - s_]) + g[j - s_, i + s_]) + g[j + s_, i + s_])
+        elif oi:
+            want = 0.5 * (g[j, i - s_] + g[j, i + s_])
+        else:
+            want = 0.5 * (g[j - s_, i] + g[j + s_, i])
+        assert g[j, i] == want
