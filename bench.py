@@ -37,6 +37,14 @@ FLOPS_PER_STEP = {"trace_fp64": 550, "trace_fp32": 578, "trace_df": 550}
 # parallel transport of the polarization covector at the 4 RK4 stages plus its update (1332), the
 # synchrotron coefficients in the fluid frame (590) and the exact Stokes segment (590).
 FLOPS_PER_STEP_POL = {"trace_fp64": 3007, "trace_fp32": 3035, "trace_df": 3007}
+# Fluid-grid (GRMHD-like snapshot) steps, unpolarized: the geodesic and transfer as above (506)
+# plus the grid emission instead of the analytic one: angles and cell coordinates (22), the
+# trilinear interpolation of 8 fields from 8 cells (147), the Jacobian to Cartesian components and
+# u, B (46), Kerr-Schild metric pieces (18), u^t from the normalisation (28), b^mu and b^2 (41),
+# the two-temperature plasma state (29) and the thermal-synchrotron j_I, alpha_I (164).
+FLOPS_PER_STEP_GRID = {"trace_fp64": 999, "trace_fp32": 1027, "trace_df": 999}
+# Algorithmic bytes of one grid sample: 8 cells x 8 FP32 fields (before any cache reuse).
+GRID_BYTES_PER_SAMPLE = 256
 # Peaks for "alu"-bound kernels: FP32 = 152 SMs x 128 lanes x 2 flops x 2.07 GHz; FP64 = the
 # GB300's nominal dense FP64 rate.
 PEAK_TFLOPS = {"trace_fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "trace_fp64": 1.25,
@@ -44,6 +52,7 @@ PEAK_TFLOPS = {"trace_fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "trace_fp64": 1.25,
 PEAK_SOURCE = {"trace_fp32": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                "trace_df": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (FP32 pipes)",
                "trace_fp64": "nominal GB300 dense FP64"}
+HBM_PEAK_GBPS = 6779.0  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 DTYPE = {"mixed": "f32+f64", "mixed_df": "f32+df32x2", "fp64": "f64", "fp32": "f32"}
 METRIC = "rays/s"
 
@@ -128,12 +137,18 @@ def _base_pixels(params: dict, limit: int | None = None):
     return pix
 
 
-def cpu_baseline(params: dict):
-    """The FP64 oracle on the host cores.  Unpolarized workloads: one full adaptive render.
-    Polarized ones (several ms of oracle time per ray): the whole base level of the workload."""
+def _sampled_on_cpu(params: dict) -> bool:
+    """Workloads whose full render takes the oracle too long: polarized ones (several ms per ray)
+    and the 8193^2 grid render; the CPU legs trace base-level rays of them instead."""
+    return params.get("stokes", 1) == 4 or params.get("emission") == "grid"
+
+
+def cpu_baseline(params: dict, snap=None):
+    """The FP64 oracle on the host cores.  Unpolarized analytic workloads: one full adaptive
+    render.  Polarized and grid ones: the whole base level of the workload."""
     import oracle as O
-    job = O.make_job(**params)
-    if params.get("stokes", 1) == 4:
+    job = O.make_job(grid=snap, **params)
+    if _sampled_on_cpu(params):
         pix = _base_pixels(params)
         t0 = time.perf_counter()
         _, info = O.trace_pixels(job, pix)
@@ -153,14 +168,15 @@ def cpu_baseline(params: dict):
 
 def run_reference(args, params, desc):
     """The reference arm: the FP64 oracle on the host cores.  Each step is a bounded sample of the
-    workload: one full adaptive render (unpolarized) or 2048 evenly spaced base-level rays
-    (polarized), so the whole run stays within a few minutes."""
+    workload: one full adaptive render (unpolarized analytic) or 2048 evenly spaced base-level
+    rays (polarized, grid), so the whole run stays within a few minutes."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle as O
-    job = O.make_job(**params)
-    pol = params.get("stokes", 1) == 4
+    snap = W.grmhd_snapshot(seed=0) if params.get("emission") == "grid" else None
+    job = O.make_job(grid=snap, **params)
+    pol = _sampled_on_cpu(params)
     pix = _base_pixels(params, 2048) if pol else None
 
     def step():
@@ -216,6 +232,11 @@ def main():
     from paper_2103_07417_gb300 import art
     ctx = art.Context(local)
     stream = ctx.stream
+    snap = None
+    if params.get("emission") == "grid":
+        # the seeded snapshot, resident on the device before timing (151 MB of FP32)
+        snap = W.grmhd_snapshot(seed=0)
+        ctx.load_grid(snap)
     job = art.make_job(**params)
     nx, ny = art.art_image_size(job)
     planes = art.art_planes(job)
@@ -275,7 +296,9 @@ def main():
     dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
     total_ms = sum(v["ms"] for v in by_kind.values())
     roofline = None
-    fps = FLOPS_PER_STEP_POL if params.get("stokes", 1) == 4 else FLOPS_PER_STEP
+    grid_em = params.get("emission") == "grid"
+    fps = (FLOPS_PER_STEP_POL if params.get("stokes", 1) == 4
+           else FLOPS_PER_STEP_GRID if grid_em else FLOPS_PER_STEP)
     if dom in fps:
         d = by_kind[dom]
         achieved = d["steps"] * fps[dom] / (d["ms"] / 1000.0) / 1e12
@@ -285,6 +308,15 @@ def main():
                     "peak_source": PEAK_SOURCE[dom],
                     "launches": d["launches"], "steps": d["steps"],
                     "share_of_step": d["ms"] / total_ms}
+        if grid_em:
+            # every RK4 step samples the grid once (the start point of a ray once more)
+            gbs = d["steps"] * GRID_BYTES_PER_SAMPLE / (d["ms"] / 1000.0) / 1e9
+            roofline["grid_lookup"] = {
+                "bytes_per_sample": GRID_BYTES_PER_SAMPLE, "samples": d["steps"],
+                "achieved_GBps": gbs, "hbm_peak_GBps": HBM_PEAK_GBPS, "frac_of_hbm": gbs / HBM_PEAK_GBPS,
+                "note": "algorithmic bytes (8 cells x 32 B per sample) over the kernel time; most "
+                        "are served from L1/L2 (neighbouring samples share cells), so DRAM "
+                        "traffic is far lower"}
     kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                    "share": round(v["ms"] / total_ms, 4)} for k, v in by_kind.items()}
 
@@ -312,19 +344,30 @@ def main():
     hmask = torch.empty((ny, nx), dtype=torch.uint8).pin_memory().numpy()
     ctx.art_render_host(job, himg, hmask)
     ke = max(3, args.steps // 3)
+    hgrid = None
+    if snap is not None:
+        # a new snapshot per frame: its upload from pinned host memory is inside the timed loop
+        hgrid = torch.from_numpy(snap["data"]).pin_memory().numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(ke):
+        if hgrid is not None:
+            ctx.art_load_grid(hgrid, snap["n1"], snap["n2"], snap["n3"], snap["logr_min"],
+                              snap["logr_max"])
         ctx.art_render_host(job, himg, hmask)
     te = time.perf_counter() - t0
     e2e = {"value": rays * ke / te, "unit": "rays/s",
-           "h2d_bytes_per_step": int(ctypes_sizeof_job()),
+           "h2d_bytes_per_step": int(ctypes_sizeof_job()) + (int(hgrid.nbytes) if hgrid is not None else 0),
            "d2h_bytes_per_step": int(himg.nbytes + hmask.nbytes)}
+    if snap is not None:
+        ctx.load_grid(snap)
 
     # the batched form (256 images of random spin, inclination, FOV, grid and depth, one pass per
     # level for all of them) on the same GPU
     batched = None
     if not args.no_batch:
+        if snap is None:   # the batch renders config 2's emission model: load its snapshot
+            ctx.load_grid(W.grmhd_snapshot(seed=0))
         bparams = W.cfg3(seed=0, n=256)
         bjobs = [art.make_job(**p) for p in bparams]
         bimgs, bmasks = [], []
@@ -346,8 +389,9 @@ def main():
         torch.cuda.synchronize()
         tb = sum(a.elapsed_time(b) for a, b in evs) / 1000.0 / len(evs)
         batched = {"workload": "256 images (config-3 recipe): a~U[-0.94,0.94], i~U[10,170] deg, "
-                               "FOV log-U[40,400] M, 65^2..513^2 over 2-6 levels, synchrotron "
-                               "disk, subrings n=0,1,2, mixed_df",
+                               "FOV log-U[40,400] M, 65^2..513^2 over 2-6 levels, emission from "
+                               "the config-2 snapshot (288x128x128 grid), subrings n=0,1,2, "
+                               "mixed_df",
                    "rays_per_s": brays / tb, "images_per_s": len(bjobs) / tb,
                    "ms_per_batch": 1000 * tb, "rays": brays, "pixels": bpix,
                    "geodesic_steps_per_s": bst[0]["steps"] / tb}
@@ -355,7 +399,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(params)
+        cpu = cpu_baseline(params, snap)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,

@@ -221,50 +221,217 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
     return tr;
 }
 
+// ---- FP32 screen of the linear criterion ------------------------------------------------------
+// GB300 issues FP64 at 1/64 of the FP32 rate, and a decision in FP64 (two divisions plus the
+// stencil sums) made this HBM-bound pass FP64-bound.  The screen evaluates the same sums in FP32
+// from the high words of the doubles with a rigorous error bound and decides only where the
+// estimate clears both thresholds by more than that bound; every other point (and every point
+// of the nearest-neighbour scheme, of a non-positive or non-finite normalisation, or with a value
+// outside the FP32 range) takes the FP64 decision above, so the decisions are those of decide()
+// for every point.
+//   Value: the double's high word gives sign, exponent and 20 mantissa bits, a truncation with
+//   relative error < 2^-20; magnitudes below 2^-126 are taken as 0 (absolute error < 2^-126).
+//   Sums of c_k v_k in FP32 (|c_k| <= 4, at most 8 operations): |error| <= 2^-19 C + 2^-120 with
+//   C = sum |c_k v_k|; the screen uses twice that.
+// Linear scheme, X = |S_out - S_in| (the sum of the available second differences): eps_abs >
+// R_abs <=> X > 16 R_abs norm (centre) or 8 R_abs norm (edge midpoints); eps_rel > R_rel <=>
+// X > 4 R_rel |S_in| in both cases.
+struct Screen {
+    float tabs4, tabs2, rrel4;
+    bool abs_any, rel_any;  // negative tolerance: every estimate exceeds it
+    bool on;
+};
+
+__device__ __forceinline__ Screen make_screen(const DevJob& J, double norm)
+{
+    Screen sc;
+    sc.on = J.interp == ART_INTERP_LINEAR && norm > 0.0 && norm < 1e300;
+    sc.abs_any = J.R_abs < 0.0;
+    sc.rel_any = J.R_rel < 0.0;
+    const double t4 = 16.0 * J.R_abs * norm, t2 = 8.0 * J.R_abs * norm, r4 = 4.0 * J.R_rel;
+    // thresholds must be zero or normal FP32 numbers
+    auto fits = [](double v) { double m = fabs(v); return m == 0.0 || (m > 1e-37 && m < 1e37); };
+    if (!sc.abs_any && !(fits(t4) && fits(t2))) sc.on = false;
+    if (!sc.rel_any && !fits(r4)) sc.on = false;
+    sc.tabs4 = (float)t4;
+    sc.tabs2 = (float)t2;
+    sc.rrel4 = (float)r4;
+    return sc;
+}
+
+// High-word FP32 value of a double; ok = false for |x| >= 2^128, infinities and NaN.
+__device__ __forceinline__ float hiword_f32(double x, bool& ok)
+{
+    const int hi = __double2hiint(x);
+    const int e = (hi >> 20) & 0x7ff;
+    if (e > 1150) {
+        ok = false;
+        return 0.f;
+    }
+    if (e < 897) return 0.f;
+    return __int_as_float((hi & 0x80000000) | ((e - 896) << 23) | ((hi & 0xfffff) << 3));
+}
+
+// FP32 second-difference sum along one line (as second_diff_sum) and its sum of |c_k v_k|.
+__device__ __forceinline__ float second_diff_f(const double* img, int nx, int ny, int i, int j,
+                                               int di, int dj, float Im, float Ip, float& C,
+                                               bool& ok)
+{
+    const int iom = i - 3 * di, jom = j - 3 * dj, iop = i + 3 * di, jop = j + 3 * dj;
+    const bool has_m = iom >= 0 && iom < nx && jom >= 0 && jom < ny;
+    const bool has_p = iop >= 0 && iop < nx && jop >= 0 && jop < ny;
+    if (has_m && has_p) {
+        float Om = hiword_f32(__ldg(img + (int64_t)jom * nx + iom), ok);
+        float Op = hiword_f32(__ldg(img + (int64_t)jop * nx + iop), ok);
+        C += ((fabsf(Om) + fabsf(Im)) + fabsf(Ip)) + fabsf(Op);
+        return ((Om - Im) - Ip) + Op;
+    }
+    if (has_m) {
+        float Om = hiword_f32(__ldg(img + (int64_t)jom * nx + iom), ok);
+        C += 2.f * fabsf(Om) + 4.f * fabsf(Im) + 2.f * fabsf(Ip);
+        return 2.f * ((Om - 2.f * Im) + Ip);
+    }
+    if (has_p) {
+        float Op = hiword_f32(__ldg(img + (int64_t)jop * nx + iop), ok);
+        C += 2.f * fabsf(Op) + 4.f * fabsf(Ip) + 2.f * fabsf(Im);
+        return 2.f * ((Op - 2.f * Ip) + Im);
+    }
+    ok = false;
+    return 0.f;
+}
+
+// Screened decision: 1 = trace, 0 = interpolate, -1 = undecided (take the FP64 decision).
+__device__ __forceinline__ int screen_decide(const Screen& sc, const double* img, int nx, int ny,
+                                             int i, int j, int s, int cat)
+{
+    if (!sc.on) return -1;
+    bool ok = true;
+    float X, C = 0.f, Sin, Cin;
+    float tabs;
+    if (cat == 4) {
+        float I1 = hiword_f32(__ldg(img + (int64_t)(j - s) * nx + (i - s)), ok);
+        float I4 = hiword_f32(__ldg(img + (int64_t)(j + s) * nx + (i + s)), ok);
+        float I2 = hiword_f32(__ldg(img + (int64_t)(j + s) * nx + (i - s)), ok);
+        float I3 = hiword_f32(__ldg(img + (int64_t)(j - s) * nx + (i + s)), ok);
+        Sin = ((I1 + I2) + I3) + I4;
+        Cin = ((fabsf(I1) + fabsf(I2)) + fabsf(I3)) + fabsf(I4);
+        float dA = second_diff_f(img, nx, ny, i, j, s, s, I1, I4, C, ok);
+        float dB = second_diff_f(img, nx, ny, i, j, s, -s, I2, I3, C, ok);
+        X = fabsf(dA + dB);
+        tabs = sc.tabs4;
+    } else {
+        const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
+        float I1 = hiword_f32(__ldg(img + (int64_t)(j - dj) * nx + (i - di)), ok);
+        float I2 = hiword_f32(__ldg(img + (int64_t)(j + dj) * nx + (i + di)), ok);
+        Sin = I1 + I2;
+        Cin = fabsf(I1) + fabsf(I2);
+        X = fabsf(second_diff_f(img, nx, ny, i, j, di, dj, I1, I2, C, ok));
+        tabs = sc.tabs2;
+    }
+    if (!ok) return -1;
+    const float E = 0x1p-18f * C + 0x1p-118f;
+    const float Es = 0x1p-18f * Cin + 0x1p-118f;
+    const float up = 1.f + 0x1p-18f, dn = 1.f - 0x1p-18f;
+    bool abs_t, abs_f, rel_t, rel_f;
+    if (sc.abs_any) {
+        abs_t = true;
+        abs_f = false;
+    } else {
+        abs_t = X - E > tabs * up;
+        abs_f = X + E < tabs * dn;
+    }
+    if (sc.rel_any) {
+        rel_t = true;
+        rel_f = false;
+    } else {
+        const float lo = fabsf(Sin) - Es, hi = fabsf(Sin) + Es;
+        rel_t = X - E > sc.rrel4 * hi * up;
+        rel_f = lo > 0.f && X + E < sc.rrel4 * lo * dn;
+    }
+    if (abs_f || rel_f) return 0;
+    if (abs_t && rel_t) return 1;
+    return -1;
+}
+
+// One new point of a level: decide (screen, else FP64), then mark it for tracing or write its
+// interpolant into every plane.  Returns true when the point is to be traced.
+__device__ __forceinline__ bool refine_point(const DevJob& J, const Screen& sc, double* img,
+                                             uint8_t* mask, int i, int j, int s, int cat,
+                                             double norm, int64_t npix)
+{
+    double w1, w2;
+    int64_t p1, p2, p3, p4;
+    const int scr = screen_decide(sc, img, J.nx, J.ny, i, j, s, cat);
+    bool trace;
+    if (scr < 0) {
+        trace = decide(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4);
+    } else {
+        trace = scr == 1;
+        if (J.edge_mode == ART_EDGE_TRACE) {
+            const int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
+            if (i - 3 * di < 0 || i + 3 * di >= J.nx || j - 3 * dj < 0 || j + 3 * dj >= J.ny)
+                trace = true;
+        }
+        // stencil of the (linear) interpolant, as decide() sets it
+        const int nx = J.nx;
+        if (cat == 4) {
+            p1 = (int64_t)(j - s) * nx + (i - s);
+            p4 = (int64_t)(j + s) * nx + (i + s);
+            p2 = (int64_t)(j + s) * nx + (i - s);
+            p3 = (int64_t)(j - s) * nx + (i + s);
+        } else {
+            const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
+            p1 = (int64_t)(j - dj) * nx + (i - di);
+            p2 = (int64_t)(j + dj) * nx + (i + di);
+            p3 = p4 = -1;
+        }
+        w1 = w2 = 0.5;
+    }
+    const int64_t pix = (int64_t)j * J.nx + i;
+    if (trace) {
+        if (mask) mask[pix] = ART_MASK_TRACED;
+        return true;
+    }
+    for (int c = 0; c < J.planes; ++c) {
+        const double* pl = img + c * npix;
+        double v;
+        if (cat == 4) {
+            if (w2 == 0.0)
+                v = __ldg(pl + p1);
+            else
+                v = 0.25 * (((__ldg(pl + p1) + __ldg(pl + p2)) + __ldg(pl + p3)) + __ldg(pl + p4));
+        } else {
+            v = (w2 == 0.0) ? __ldg(pl + p1) : 0.5 * (__ldg(pl + p1) + __ldg(pl + p2));
+        }
+        img[c * npix + pix] = v;
+    }
+    if (mask) mask[pix] = ART_MASK_INTERP;
+    return false;
+}
+
 __global__ void __launch_bounds__(256)
     refine_kernel(DevJob J, int level, const double* __restrict__ norm_ptr, double* img,
                   uint8_t* mask, int32_t* queue, unsigned long long* qcount)
 {
     const int s = 1 << (J.levels - level);
-    const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
-    const int64_t npts = (int64_t)nkx * nky;
+    const unsigned nkx = (unsigned)((J.nx - 1) / s + 1), nky = (unsigned)((J.ny - 1) / s + 1);
+    const unsigned npts = nkx * nky;  // < 2^31 (art_image_size)
     const int64_t npix = (int64_t)J.nx * J.ny;
     const double norm = *norm_ptr;
+    const Screen sc = make_screen(J, norm);
     const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npts;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = base + threadIdx.x;
+    for (unsigned base = blockIdx.x * blockDim.x; base < npts; base += gridDim.x * blockDim.x) {
+        const unsigned t = base + threadIdx.x;
         bool trace = false;
         int32_t pix = 0;
         if (t < npts) {
-            const int ii = (int)(t % nkx), jj = (int)(t / nkx);
+            const unsigned jj = t / nkx, ii = t - jj * nkx;
             const int oi = ii & 1, oj = jj & 1;
             if (oi | oj) {
-                const int i = ii * s, j = jj * s;
+                const int i = (int)ii * s, j = (int)jj * s;
                 const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                double w1, w2;
-                int64_t p1, p2, p3, p4;
-                trace = decide(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4);
+                trace = refine_point(J, sc, img, mask, i, j, s, cat, norm, npix);
                 pix = j * J.nx + i;
-                if (trace) {
-                    if (mask) mask[pix] = ART_MASK_TRACED;
-                } else {
-                    for (int c = 0; c < J.planes; ++c) {
-                        const double* pl = img + c * npix;
-                        double v;
-                        if (cat == 4) {
-                            if (w2 == 0.0)
-                                v = __ldg(pl + p1);
-                            else
-                                v = 0.25 * (((__ldg(pl + p1) + __ldg(pl + p2)) + __ldg(pl + p3)) +
-                                            __ldg(pl + p4));
-                        } else {
-                            v = (w2 == 0.0) ? __ldg(pl + p1) : 0.5 * (__ldg(pl + p1) + __ldg(pl + p2));
-                        }
-                        img[c * npix + pix] = v;
-                    }
-                    if (mask) mask[pix] = ART_MASK_INTERP;
-                }
             }
         }
         // warp-aggregated append to the ray queue (ballot -> popc -> one atomic per warp)
@@ -392,45 +559,24 @@ __global__ void __launch_bounds__(256)
     double* img = imgs[im];
     uint8_t* mask = masks[im];
     const int s = 1 << (J.levels - level);
-    const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
-    const int64_t npts = (int64_t)nkx * nky;
+    const unsigned nkx = (unsigned)((J.nx - 1) / s + 1), nky = (unsigned)((J.ny - 1) / s + 1);
+    const unsigned npts = nkx * nky;
     const int64_t npix = (int64_t)J.nx * J.ny;
     const double norm = norms[4 * im];
+    const Screen sc = make_screen(J, norm);
     const int lane = threadIdx.x & 31;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npts;
-         base += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = base + threadIdx.x;
+    for (unsigned base = blockIdx.x * blockDim.x; base < npts; base += gridDim.x * blockDim.x) {
+        const unsigned t = base + threadIdx.x;
         bool trace = false;
         int32_t pix = 0;
         if (t < npts) {
-            const int ii = (int)(t % nkx), jj = (int)(t / nkx);
+            const unsigned jj = t / nkx, ii = t - jj * nkx;
             const int oi = ii & 1, oj = jj & 1;
             if (oi | oj) {
-                const int i = ii * s, j = jj * s;
+                const int i = (int)ii * s, j = (int)jj * s;
                 const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                double w1, w2;
-                int64_t p1, p2, p3, p4;
-                trace = decide(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4);
+                trace = refine_point(J, sc, img, mask, i, j, s, cat, norm, npix);
                 pix = j * J.nx + i;
-                if (trace) {
-                    if (mask) mask[pix] = ART_MASK_TRACED;
-                } else {
-                    for (int c = 0; c < J.planes; ++c) {
-                        const double* pl = img + c * npix;
-                        double v;
-                        if (cat == 4) {
-                            if (w2 == 0.0)
-                                v = __ldg(pl + p1);
-                            else
-                                v = 0.25 * (((__ldg(pl + p1) + __ldg(pl + p2)) + __ldg(pl + p3)) +
-                                            __ldg(pl + p4));
-                        } else {
-                            v = (w2 == 0.0) ? __ldg(pl + p1) : 0.5 * (__ldg(pl + p1) + __ldg(pl + p2));
-                        }
-                        img[c * npix + pix] = v;
-                    }
-                    if (mask) mask[pix] = ART_MASK_INTERP;
-                }
             }
         }
         const unsigned b = __ballot_sync(0xffffffffu, trace);

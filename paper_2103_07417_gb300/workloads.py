@@ -146,6 +146,11 @@ BENCH_WORKLOADS = {
     "cfg1_analytic": ("adaptive render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, "
                       "FOV 40 M, r_obs 1000 M, RK4 h=0.05r, analytic Keplerian emissivity "
                       "r^-2 exp(-z^2/(2(0.3r)^2)), R_rel=R_abs=1e-3", cfg1_analytic),
+    "cfg2": ("adaptive render 257^2 -> 8193^2 (5 levels) of a seeded GRMHD-like snapshot "
+             "(Fishbone-Moncrief torus a=0.94 + lognormal k^-11/3 turbulence, 288x128x128 FP32 "
+             "cells over ln r in [ln 1.2, ln 1000]), i=163 deg, FOV 160 M, r_obs 1000 M, RK4 "
+             "h=0.05r, thermal synchrotron at 230 GHz with R_high=20, sigma cut 1; "
+             "R_rel=1e-3, R_abs=0.025", cfg2),
     "cfg0": ("adaptive render 33^2 -> 129^2 (2 levels), Schwarzschild, i=60 deg, FOV 40 M, "
              "R_rel=0.01, R_abs=1e-4 of peak", cfg0),
 }
@@ -154,8 +159,9 @@ BENCH_WORKLOADS = {
 def cfg3(seed: int = 0, n: int = 256, **over) -> list:
     """A batch of n images: spin a ~ U[-0.94, 0.94], inclination ~ U[10, 170] deg, FOV log-uniform
     in [40, 400] M, final grid 2^k + 1 with k ~ U{6..9} (65^2 .. 513^2) reached over N ~ U{2..6}
-    levels (base grid at least 5 points), the thermal-synchrotron disk model of config 1 (inner
-    edge at each spin's ISCO) traced unpolarized with subrings n = 0, 1, 2; mixed precision."""
+    levels (base grid at least 5 points), the emission model of config 2 (the seeded snapshot
+    grmhd_snapshot(0), shared by every image whatever its spin) traced unpolarized with subrings
+    n = 0, 1, 2; FP32 with the double-float re-trace."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(n):
@@ -164,9 +170,9 @@ def cfg3(seed: int = 0, n: int = 256, **over) -> list:
         N = int(rng.integers(2, 7))
         N = min(N, k - 2)
         n0 = (1 << (k - N)) + 1
-        p = cfg1(a=a, incl_deg=float(rng.uniform(10.0, 170.0)),
+        p = cfg2(a=a, incl_deg=float(rng.uniform(10.0, 170.0)),
                  fov=float(np.exp(rng.uniform(np.log(40.0), np.log(400.0)))),
-                 n0x=n0, n0y=n0, levels=N, r_in=r_isco(a), stokes=1, subrings=3)
+                 n0x=n0, n0y=n0, levels=N, stokes=1, subrings=3)
         p.update(over)
         out.append(p)
     return out

@@ -94,6 +94,18 @@ def test_grid_polarized_faraday_thick_fp64(ctx, snap):
     assert np.abs(g[:, 1:] - ref[:, 1:]).max() <= 2e-3 * ref[:, 0].max()
 
 
+def test_grid_subrings_fp64_matches_oracle(ctx, snap):
+    """Subring planes n = 0, 1, 2 of the snapshot image (face-on, the torus lensed into rings)."""
+    params = {**W.cfg2(n0x=17, n0y=17, levels=1, fov=30.0, subrings=3, incl_deg=163.0),
+              "precision": "fp64"}
+    g, ref, aux, info = _trace_both(ctx, snap, params)
+    I = ref.sum(axis=1)
+    lim = 1e-6 * np.maximum(I, 1e-6 * I.max())
+    assert (np.abs(g - ref) <= lim[:, None]).all()
+    assert ref[:, 1].max() > 1e-3 * ref[:, 0].max()      # the n = 1 ring is present
+    assert (aux["nturn"].cpu().numpy() == info["nturn"]).mean() > 0.999
+
+
 def test_grid_render_fp64_matches_oracle(ctx, snap):
     """33^2 -> 129^2 adaptive render with the paper's GRMHD tolerances."""
     art = _art()

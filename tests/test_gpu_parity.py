@@ -147,6 +147,51 @@ def test_refine_level_matches_oracle(ctx, case):
         assert len(np.unique(q)) == n
 
 
+SCREEN_CASES = ["wide_range", "below_fp32", "quantile_thresholds", "signed_planes"]
+
+
+@pytest.mark.parametrize("kind", SCREEN_CASES)
+def test_refine_fp32_screen_keeps_fp64_decisions(ctx, kind):
+    """The refinement kernel decides most points with an FP32 screen of the estimate and falls
+    back to FP64 near the thresholds: its masks must equal the oracle's FP64 decisions except
+    for estimates within 1e-12 of a tolerance, on images built to stress the screen: magnitudes
+    spanning 1e-300 .. 1e30, values below the FP32 range, tolerances placed at quantiles of the
+    estimates (many points just above / below them), and signed values."""
+    art = _art()
+    rng = np.random.default_rng(SCREEN_CASES.index(kind) + 11)
+    n0, levels = 17, 3
+    params = W.job(n0x=n0, n0y=n0, levels=levels, R_abs=2e-3, R_rel=5e-3)
+    nx = ny = (1 << levels) * (n0 - 1) + 1
+    if kind == "wide_range":
+        truth = 10.0 ** rng.uniform(-300, 30, (ny, nx))
+    elif kind == "below_fp32":
+        truth = 1e-40 * W.smooth_image(3, nx, ny)
+    elif kind == "signed_planes":
+        truth = W.smooth_image(4, nx, ny, noise=0.2) - 0.5
+    else:
+        truth = W.ring_image(5, nx, ny)
+    for level in range(1, levels + 1):
+        img, mask = _level_input(truth, levels, level)
+        norm = float(np.mean(np.abs(truth)))
+        if kind == "quantile_thresholds":
+            _, _, ea0, er0 = O.refine_level(O.make_job(**params), img, mask, level, norm)
+            fin = np.isfinite(ea0) & np.isfinite(er0) & (ea0 > 0)
+            params = {**params, "R_abs": float(np.quantile(ea0[fin], 0.4)),
+                      "R_rel": float(np.quantile(er0[fin], 0.3))}
+        ref_img, ref_mask, ea, er = O.refine_level(O.make_job(**params), img, mask, level, norm)
+        img_d = torch.from_numpy(img).cuda()
+        mask_d = torch.from_numpy(mask).cuda()
+        queue = torch.full((nx * ny,), -1, dtype=torch.int32, device="cuda")
+        ctx.art_refine_level(art.make_job(**params), img_d, mask_d, level, norm, queue)
+        gm = mask_d.cpu().numpy()
+        near = ((np.abs(ea - params["R_abs"]) <= 1e-12 * abs(params["R_abs"]))
+                | (np.abs(er - params["R_rel"]) <= 1e-12 * abs(params["R_rel"])))
+        diff = (gm != ref_mask) & ~near
+        assert diff.sum() == 0, (kind, level, np.argwhere(diff)[:5])
+        interp = (ref_mask == 2) & (gm == 2)
+        np.testing.assert_array_equal(img_d.cpu().numpy()[interp], ref_img[interp])
+
+
 def test_ibar_int_matches_oracle(ctx):
     for (nx0, ny0, stride, seed) in [(17, 17, 8, 1), (13, 5, 4, 2), (2, 2, 1, 3), (65, 33, 16, 4)]:
         nx, ny = (nx0 - 1) * stride + 1, (ny0 - 1) * stride + 1
