@@ -351,3 +351,30 @@ def _b2_ks(a, r, th, ut, uph, B1, B2):
     b = (Bv + bt * u) / ut
     b[0] = bt
     return float(b @ g @ b)
+
+
+# ---------------------------------------------------------------------------------------------
+# Learned proposal: the seeded starting weights of the block-proposal network
+# ---------------------------------------------------------------------------------------------
+
+CNN_CH = 32
+CNN_SHAPES = [("W1", (CNN_CH, 3, 3, 3)), ("b1", (CNN_CH,)), ("W2", (CNN_CH, 3, 3, CNN_CH)),
+              ("b2", (CNN_CH,)), ("W3", (CNN_CH, 3, 3, CNN_CH)), ("b3", (CNN_CH,)),
+              ("W4", (CNN_CH, 3, 3, CNN_CH)), ("b4", (CNN_CH,)), ("wh", (CNN_CH,)), ("bh", (1,))]
+
+
+def cnn_init(seed: int) -> np.ndarray:
+    """Flat FP32 parameter vector in the documented order (conv weights [out][ky][kx][in]):
+    He-normal conv weights (std sqrt(2 / fan_in)), zero biases, head weights N(0, 1/32), head
+    bias 0."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, shp in CNN_SHAPES:
+        if name.startswith("W"):
+            fan_in = shp[1] * shp[2] * shp[3]
+            parts.append(rng.standard_normal(shp) * np.sqrt(2.0 / fan_in))
+        elif name == "wh":
+            parts.append(rng.standard_normal(shp) / np.sqrt(CNN_CH))
+        else:
+            parts.append(np.zeros(shp))
+    return np.concatenate([q.ravel() for q in parts]).astype(np.float32)
