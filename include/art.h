@@ -250,6 +250,36 @@ int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_dev, int64_t
 int art_load_grid(art_ctx* ctx, const float* grid, int32_t n1, int32_t n2, int32_t n3,
                   double logr_min, double logr_max);
 
+/* ---- Learned block proposal (not in the paper) -------------------------------------------
+ * A small convolutional network predicts, from the completed level-k lattice, which blocks the
+ * exact criterion of Sec. 3.2 will refine two levels later (the learned path traces them early;
+ * the exact criterion still decides every point).  Network: features f = (asinh(I / I_norm),
+ * 3 / max(r_min, 1), polar turns) per lattice point; four 3x3 convolutions with 32 channels
+ * (strides 1, 1, 2, 2, zero padding 1, bias, ReLU) and a 1x1 head with a logistic output: one
+ * probability per 4 x 4 lattice cells, i.e. an output grid of ceil(ceil(H/2)/2) x
+ * ceil(ceil(W/2)/2).  Runs on the tensor cores in BF16 with FP32 accumulation; head, loss
+ * (mean binary cross-entropy) and Adam in FP32.
+ * Parameters: ART_CNN_PARAMS floats, in this order: W1 [32][3][3][3], b1 [32], W2 [32][3][3][32],
+ * b2, W3, b3, W4, b4 (conv weights indexed [out][ky][kx][in]), w_head [32], b_head [1].
+ * Feature maps are H x W x 3 FP32 device arrays (row-major, features fastest); probabilities and
+ * targets are Ho x Wo FP32 device arrays.  Every call is stream-ordered on the context's stream
+ * and synchronises it.  Errors: ART_ERR_ARG (no network loaded, H or W < 1 or H W > 2^26),
+ * ART_ERR_OOM, ART_ERR_CUDA, ART_ERR_DEVICE (a tensor-core wait timed out). */
+#define ART_CNN_PARAMS 28673
+/* Load (host FP32 parameters) and reset the optimizer state. */
+int art_cnn_load(art_ctx* ctx, const float* params_host);
+/* Copy the current parameters to the host. */
+int art_cnn_read(art_ctx* ctx, float* params_host);
+/* Forward pass: probabilities of the blocks of one lattice. */
+int art_cnn_forward(art_ctx* ctx, const float* feat_dev, int32_t H, int32_t W, float* prob_dev);
+/* Loss and gradients (no update): *loss_host = mean cross-entropy against target_dev (0/1),
+ * grad_host (nullable) receives ART_CNN_PARAMS gradient entries. */
+int art_cnn_grad(art_ctx* ctx, const float* feat_dev, int32_t H, int32_t W,
+                 const float* target_dev, float* loss_host, float* grad_host);
+/* One Adam step (learning rate lr, beta1 0.9, beta2 0.999, eps 1e-8) on one lattice. */
+int art_cnn_train_step(art_ctx* ctx, const float* feat_dev, int32_t H, int32_t W,
+                       const float* target_dev, float lr, float* loss_host);
+
 /* Image metrics of plane 0 (Eqs. interpdef, fluxdef, msedef): out_host[0] = interpolation
  * fraction (mask_dev nullable -> 0), [1] = flux error with the trapezoid flux, [2] = MSE
  * sum|I - I_hat|^2 / sum|I|^2, [3] = sum|I - I_hat|^2 / (N mean(I)^2).  Synchronises. */

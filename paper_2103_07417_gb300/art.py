@@ -94,7 +94,9 @@ _lib = None
 EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_planes",
            "art_trace_pixels", "art_ibar_int", "art_refine_level", "art_render",
            "art_render_host", "art_metrics", "art_profile", "art_profile_read",
-           "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid")
+           "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid", "art_cnn_load",
+           "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step")
+CNN_PARAMS = 28673
 NOALLOC_MAX_RAYS = 1 << 20
 
 
@@ -130,6 +132,12 @@ def load():
             lib.art_trace_pixels_noalloc.argtypes = [P(Job), vp, i64, vp, P(RayAux), vp]
             lib.art_render_batch.argtypes = [vp, P(Job), i32, P(vp), P(vp), P(Stats)]
             lib.art_load_grid.argtypes = [vp, vp, i32, i32, i32, ctypes.c_double, ctypes.c_double]
+            fp = P(ctypes.c_float)
+            lib.art_cnn_load.argtypes = [vp, vp]
+            lib.art_cnn_read.argtypes = [vp, vp]
+            lib.art_cnn_forward.argtypes = [vp, vp, i32, i32, vp]
+            lib.art_cnn_grad.argtypes = [vp, vp, i32, i32, vp, fp, vp]
+            lib.art_cnn_train_step.argtypes = [vp, vp, i32, i32, vp, ctypes.c_float, fp]
             _lib = lib
     return _lib
 
@@ -309,6 +317,46 @@ class Context:
             data = torch.from_numpy(np.ascontiguousarray(data, np.float32)).to(f"cuda:{self.device}")
         self.art_load_grid(data, snap["n1"], snap["n2"], snap["n3"], snap["logr_min"],
                            snap["logr_max"])
+
+    # -- learned block proposal ----------------------------------------------------------------
+    def art_cnn_load(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        if p.size != CNN_PARAMS:
+            raise ValueError(f"expected {CNN_PARAMS} parameters")
+        _check(load().art_cnn_load(self._ctx, p.ctypes.data_as(ctypes.c_void_p)), "art_cnn_load")
+
+    def art_cnn_read(self) -> np.ndarray:
+        p = np.empty(CNN_PARAMS, dtype=np.float32)
+        _check(load().art_cnn_read(self._ctx, p.ctypes.data_as(ctypes.c_void_p)), "art_cnn_read")
+        return p
+
+    @staticmethod
+    def cnn_out_shape(H: int, W: int):
+        o = lambda n: ((n - 1) // 2 + 1 - 1) // 2 + 1
+        return o(H), o(W)
+
+    def art_cnn_forward(self, feat):
+        """feat: contiguous float32 CUDA tensor (H, W, 3); returns the (Ho, Wo) probabilities."""
+        import torch
+        H, W = int(feat.shape[0]), int(feat.shape[1])
+        prob = torch.empty(self.cnn_out_shape(H, W), dtype=torch.float32, device=feat.device)
+        _check(load().art_cnn_forward(self._ctx, _dptr(feat), H, W, _dptr(prob)), "art_cnn_forward")
+        return prob
+
+    def art_cnn_grad(self, feat, target):
+        H, W = int(feat.shape[0]), int(feat.shape[1])
+        loss = ctypes.c_float()
+        g = np.empty(CNN_PARAMS, dtype=np.float32)
+        _check(load().art_cnn_grad(self._ctx, _dptr(feat), H, W, _dptr(target), ctypes.byref(loss),
+                                   g.ctypes.data_as(ctypes.c_void_p)), "art_cnn_grad")
+        return loss.value, g
+
+    def art_cnn_train_step(self, feat, target, lr: float) -> float:
+        H, W = int(feat.shape[0]), int(feat.shape[1])
+        loss = ctypes.c_float()
+        _check(load().art_cnn_train_step(self._ctx, _dptr(feat), H, W, _dptr(target), float(lr),
+                                         ctypes.byref(loss)), "art_cnn_train_step")
+        return loss.value
 
     def art_profile(self, enable: bool):
         _check(load().art_profile(self._ctx, int(bool(enable))), "art_profile")

@@ -3,6 +3,7 @@
 // levels: queue lengths live in device counters that the persistent trace kernel reads).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -24,6 +25,8 @@ struct art_ctx {
     float* grid_owned = nullptr;
     int32_t g_n1 = 0, g_n2 = 0, g_n3 = 0;
     double g_x1min = 0.0, g_x1max = 0.0;
+    // learned block proposal (cnn.cu)
+    CnnState* cnn = nullptr;
     // batched rendering tables and queue (grown, never shrunk)
     DevJob* bjobs = nullptr;
     SynchConst* bsynch = nullptr;
@@ -317,6 +320,7 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFree(c->bqueue);
     cudaFree(c->breroute);
     cudaFree(c->grid_owned);
+    cnn_destroy(c->cnn);
     for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -825,16 +829,16 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
     for (int level = 0; level <= max_levels; ++level) {
         c->prof_level = level;
         if (level > 0) {
-            int max_points = 1;
+            int max_kx = 1, max_ky = 1;
             for (int i = 0; i < n; ++i)
                 if (J[i].levels >= level) {
                     int s = 1 << (J[i].levels - level);
-                    int np = ((J[i].nx - 1) / s + 1) * ((J[i].ny - 1) / s + 1);
-                    if (np > max_points) max_points = np;
+                    max_kx = std::max(max_kx, (J[i].nx - 1) / s + 1);
+                    max_ky = std::max(max_ky, (J[i].ny - 1) / s + 1);
                 }
             CK(cudaMemsetAsync(c->counters + C_QUEUE, 0, sizeof(unsigned long long), st));
             k = prof_begin(c);
-            CK(launch_refine_batch(c->bjobs, n, level, max_points, c->bnorms, c->bimgs, c->bmasks,
+            CK(launch_refine_batch(c->bjobs, n, level, max_kx, max_ky, c->bnorms, c->bimgs, c->bmasks,
                                    c->bqueue, c->counters + C_QUEUE, c->bcounts, st));
             prof_end(c, k, ART_K_REFINE, -1);
         }
@@ -918,4 +922,52 @@ extern "C" int art_load_grid(art_ctx* c, const float* grid, int32_t n1, int32_t 
     c->g_x1min = logr_min;
     c->g_x1max = logr_max;
     return ART_OK;
+}
+
+// ---- learned block proposal -------------------------------------------------------------------
+
+static bool cnn_dims_ok(int32_t H, int32_t W)
+{
+    return H >= 1 && W >= 1 && (int64_t)H * W <= ((int64_t)1 << 26);
+}
+
+extern "C" int art_cnn_load(art_ctx* c, const float* params_host)
+{
+    if (!c || !params_host) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cnn_load(c->cnn, params_host, c->stream));
+    return ART_OK;
+}
+
+extern "C" int art_cnn_read(art_ctx* c, float* params_host)
+{
+    if (!c || !params_host || !c->cnn) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cnn_read(c->cnn, params_host, c->stream));
+    return ART_OK;
+}
+
+extern "C" int art_cnn_forward(art_ctx* c, const float* feat_dev, int32_t H, int32_t W,
+                               float* prob_dev)
+{
+    if (!c || !c->cnn || !feat_dev || !prob_dev || !cnn_dims_ok(H, W)) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    return cnn_forward(c->cnn, feat_dev, H, W, prob_dev, c->stream);
+}
+
+extern "C" int art_cnn_grad(art_ctx* c, const float* feat_dev, int32_t H, int32_t W,
+                            const float* target_dev, float* loss_host, float* grad_host)
+{
+    if (!c || !c->cnn || !feat_dev || !target_dev || !cnn_dims_ok(H, W)) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    return cnn_grad(c->cnn, feat_dev, H, W, target_dev, loss_host, grad_host, c->stream);
+}
+
+extern "C" int art_cnn_train_step(art_ctx* c, const float* feat_dev, int32_t H, int32_t W,
+                                  const float* target_dev, float lr, float* loss_host)
+{
+    if (!c || !c->cnn || !feat_dev || !target_dev || !cnn_dims_ok(H, W) || !(lr > 0.f))
+        return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    return cnn_train_step(c->cnn, feat_dev, H, W, target_dev, lr, loss_host, c->stream);
 }

@@ -1,0 +1,674 @@
+// cnn.cu -- the learned block proposal: a small convolutional network run and trained on the
+// 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
+//
+// The paper has no learned component.  The network predicts, from the completed level-k lattice
+// (features: asinh(I / I_norm), 3 / max(r_min, 1), polar turns), which 4 x 4-cell blocks of that
+// lattice the exact criterion of Sec. 3.2 will refine two levels later; those rays can then be
+// traced early.  Layers: four 3x3 convolutions with 32 channels (strides 1, 1, 2, 2, pad 1, ReLU)
+// and a 1x1 head with a logistic output; loss = mean binary cross-entropy.
+//
+// Every convolution is an implicit GEMM on the tensor cores:
+//   forward  D[o][co]        = sum_{t, ci} X[s o + t - 1][ci] W[co][t][ci]        (M = output pixels)
+//   dgrad    D[i][ci]        = sum_{t, co} dY[(i + 1 - t)/s][co] W[co][t][ci]     (M = input pixels)
+//   wgrad    D[(t, ci)][co]  = sum_o X[s o + t - 1][ci] dY[o][co]                 (K = output pixels)
+// with 128-row tiles gathered into shared memory in the canonical K-major layout (umma.cuh), one
+// thread issuing the MMAs, completion through an mbarrier, and the epilogue reading D from tensor
+// memory.  The weight gradient carries one extra row of ones so the same GEMM yields the bias
+// gradient.  Activations are NHWC BF16 (32 channels, 64 B per pixel; the 3 input features padded
+// to 8 channels); the head, the loss and the optimizer (Adam) run in FP32 on the CUDA cores.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "internal.cuh"
+#include "umma.cuh"
+
+namespace art {
+
+using bf16 = __nv_bfloat16;
+constexpr int CH = 32;       // channels of every hidden layer
+constexpr int CIN0 = 8;      // input features padded to 16 bytes per pixel
+constexpr int NFEAT = 3;     // real input features
+constexpr int K1 = 80;       // 9 x 8 = 72 padded to a multiple of 16
+constexpr int KH = 288;      // 9 x 32
+constexpr int GEMM_THREADS = 128;
+constexpr int WG_PIX = 64;   // output pixels per weight-gradient stage (K of the stage)
+
+// offsets of the parameter vector (FP32): W1, b1, W2, b2, W3, b3, W4, b4, w_head, b_head
+constexpr int P_W1 = 0, P_B1 = P_W1 + CH * 9 * NFEAT, P_W2 = P_B1 + CH, P_B2 = P_W2 + CH * 9 * CH,
+              P_W3 = P_B2 + CH, P_B3 = P_W3 + CH * 9 * CH, P_W4 = P_B3 + CH,
+              P_B4 = P_W4 + CH * 9 * CH, P_WH = P_B4 + CH, P_BH = P_WH + CH, P_N = P_BH + 1;
+static_assert(P_N == ART_CNN_PARAMS, "parameter layout");
+
+struct ConvArgs {
+    const bf16* src;    // forward: X (H x W x CIN); dgrad: dY (Ho x Wo x 32)
+    const bf16* B;      // 32 x KPAD BF16 (forward [co][t CIN + ci], dgrad [ci][t 32 + co])
+    const float* bias;  // forward only
+    const bf16* mask;   // dgrad only: the forward input X (H x W x 32); output *= (X > 0)
+    bf16* out;          // forward: Ho x Wo x 32; dgrad: H x W x 32
+    int H, W, Ho, Wo, stride;
+    int* err;
+};
+
+__device__ __forceinline__ uint4 bf16x8_zero() { return make_uint4(0, 0, 0, 0); }
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Implicit-GEMM convolution (forward, MODE 0) or its input gradient (MODE 1), one 128-row tile
+// of pixels per CTA, N = 32 channels, K = KPAD.
+template <int CIN, int KPAD, int MODE>
+__global__ void __launch_bounds__(GEMM_THREADS) conv_gemm_kernel(ConvArgs a)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + 128 * KPAD * 2;
+    constexpr int KC = KPAD / 8, TAPC = CIN / 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rows = MODE == 0 ? a.Ho * a.Wo : a.H * a.W;
+    const int p0 = blockIdx.x * 128;
+    const int sW = MODE == 0 ? a.W : a.Wo, sH = MODE == 0 ? a.H : a.Ho;  // source grid
+    const int rW = MODE == 0 ? a.Wo : a.W;                             // row grid width
+    // A: chunk (row m, column group kc); rows fastest within an 8-row group
+    for (int q = tid; q < 128 * KC; q += GEMM_THREADS) {
+        const int r = q & 7, rest = q >> 3;
+        const int kc = rest % KC, g = rest / KC;
+        const int m = g * 8 + r, p = p0 + m;
+        uint4 v = bf16x8_zero();
+        const int tap = kc / TAPC, cg = kc - tap * TAPC;
+        if (p < rows && tap < 9) {
+            const int py = p / rW, px = p - py * rW;
+            const int ky = tap / 3, kx = tap - ky * 3;
+            int sy, sx;
+            bool ok;
+            if (MODE == 0) {
+                sy = a.stride * py + ky - 1;
+                sx = a.stride * px + kx - 1;
+                ok = true;
+            } else {
+                const int ny = py + 1 - ky, nx = px + 1 - kx;
+                sy = ny / a.stride;
+                sx = nx / a.stride;
+                ok = ny >= 0 && nx >= 0 && sy * a.stride == ny && sx * a.stride == nx;
+            }
+            if (ok && sy >= 0 && sy < sH && sx >= 0 && sx < sW)
+                v = __ldg(reinterpret_cast<const uint4*>(a.src + ((int64_t)sy * sW + sx) * CIN) + cg);
+        }
+        *reinterpret_cast<uint4*>(sA + umma::chunk_off(m, kc, KPAD)) = v;
+    }
+    for (int q = tid; q < CH * KC; q += GEMM_THREADS) {
+        const int r = q & 7, rest = q >> 3;
+        const int kc = rest % KC, g = rest / KC;
+        const int n = g * 8 + r;
+        *reinterpret_cast<uint4*>(sB + umma::chunk_off(n, kc, KPAD)) =
+            __ldg(reinterpret_cast<const uint4*>(a.B + (int64_t)n * KPAD) + kc);
+    }
+    if (tid == 0) umma::mbar_init(&bar);
+    if (warp == 0) umma::tmem_alloc(&tslot, 32);
+    umma::fence_smem_async();
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = tslot;
+    if (tid == 0) {
+        const uint32_t ab = umma::smem_u32(sA), bb = umma::smem_u32(sB), sbo = KC * 128;
+        for (int kb = 0; kb < KPAD / 16; ++kb)
+            umma::mma(tmem, umma::desc(ab + kb * 256, 128, sbo), umma::desc(bb + kb * 256, 128, sbo),
+                      umma::idesc_bf16(128, CH), kb > 0);
+        umma::commit(&bar);
+    }
+    const bool ok = __syncthreads_and(umma::wait(&bar, 0));
+    umma::fence_after();
+    if (ok) {
+        float v[32];
+        umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+        const int p = p0 + warp * 32 + lane;
+        if (p < rows) {
+            uint32_t w[16];
+            if (MODE == 0) {
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    w[c] = pack_bf16x2(fmaxf(v[2 * c] + __ldg(a.bias + 2 * c), 0.f),
+                                       fmaxf(v[2 * c + 1] + __ldg(a.bias + 2 * c + 1), 0.f));
+            } else {
+                const uint4* mk = reinterpret_cast<const uint4*>(a.mask + (int64_t)p * CH);
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    uint4 mv = __ldg(mk + c4);
+                    const __nv_bfloat162* mh = reinterpret_cast<const __nv_bfloat162*>(&mv);
+#pragma unroll
+                    for (int h = 0; h < 4; ++h) {
+                        float2 f = __bfloat1622float2(mh[h]);
+                        const int c = c4 * 8 + 2 * h;
+                        w[c / 2] = pack_bf16x2(f.x > 0.f ? v[c] : 0.f, f.y > 0.f ? v[c + 1] : 0.f);
+                    }
+                }
+            }
+            uint4* o = reinterpret_cast<uint4*>(a.out + (int64_t)p * CH);
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4)
+                o[c4] = make_uint4(w[4 * c4], w[4 * c4 + 1], w[4 * c4 + 2], w[4 * c4 + 3]);
+        }
+    } else if (tid == 0) {
+        atomicExch(a.err, 1);
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, 32);
+}
+
+struct WgradArgs {
+    const bf16* X;     // forward input, H x W x CIN
+    const bf16* dY;    // Ho x Wo x 32
+    float* grad;       // parameter-gradient vector (accumulated with atomics)
+    int w_off, b_off;  // offsets of this layer's W and b in the vector
+    int cin_real;      // channels of the layer's real input (3 or 32)
+    int H, W, Ho, Wo, stride;
+    int pix_per_cta;   // output pixels reduced by one CTA (a multiple of WG_PIX)
+    int* err;
+};
+
+// Weight and bias gradient: rows (t, ci) of one 128-row tile (blockIdx.y), K = output pixels of
+// this CTA's range, in stages of WG_PIX; row 9 CIN is all ones and yields the bias gradient.
+template <int CIN>
+__global__ void __launch_bounds__(GEMM_THREADS) conv_wgrad_kernel(WgradArgs a)
+{
+    __shared__ __align__(1024) uint8_t sA[128 * WG_PIX * 2];
+    __shared__ __align__(1024) uint8_t sB[CH * WG_PIX * 2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    constexpr int KC = WG_PIX / 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int npo = a.Ho * a.Wo;
+    const int o_begin = blockIdx.x * a.pix_per_cta;
+    if (o_begin >= npo) return;  // uniform over the CTA
+    const int o_end = min(npo, o_begin + a.pix_per_cta);
+    const int m0 = blockIdx.y * 128;
+    if (tid == 0) umma::mbar_init(&bar);
+    if (warp == 0) umma::tmem_alloc(&tslot, 32);
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = tslot;
+    bool ok = true;
+    int stage = 0;
+    for (int ob = o_begin; ob < o_end; ob += WG_PIX, ++stage) {
+        // A chunk (row m, pixel octet c8): 8 values of row m at 8 consecutive output pixels
+        for (int q = tid; q < 128 * KC; q += GEMM_THREADS) {
+            const int r = q & 7, rest = q >> 3;
+            const int c8 = rest % KC, g = rest / KC;
+            const int m = m0 + g * 8 + r;
+            uint32_t w[4] = {0, 0, 0, 0};
+            if (m <= 9 * CIN) {
+                const int tap = m / CIN, ci = m - tap * CIN;
+                const int ky = tap / 3, kx = tap - ky * 3;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int o = ob + c8 * 8 + j;
+                    float v = 0.f;
+                    if (o < o_end) {
+                        if (m == 9 * CIN) {
+                            v = 1.f;
+                        } else {
+                            const int oy = o / a.Wo, ox = o - oy * a.Wo;
+                            const int iy = a.stride * oy + ky - 1, ix = a.stride * ox + kx - 1;
+                            if (iy >= 0 && iy < a.H && ix >= 0 && ix < a.W)
+                                v = __bfloat162float(a.X[((int64_t)iy * a.W + ix) * CIN + ci]);
+                        }
+                    }
+                    const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+                    w[j >> 1] |= h << (16 * (j & 1));
+                }
+            }
+            *reinterpret_cast<uint4*>(sA + umma::chunk_off(g * 8 + r, c8, WG_PIX)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        for (int q = tid; q < CH * KC; q += GEMM_THREADS) {
+            const int r = q & 7, rest = q >> 3;
+            const int c8 = rest % KC, g = rest / KC;
+            const int n = g * 8 + r;
+            uint32_t w[4] = {0, 0, 0, 0};
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int o = ob + c8 * 8 + j;
+                const uint32_t h = o < o_end ? __bfloat16_as_ushort(a.dY[(int64_t)o * CH + n]) : 0u;
+                w[j >> 1] |= h << (16 * (j & 1));
+            }
+            *reinterpret_cast<uint4*>(sB + umma::chunk_off(n, c8, WG_PIX)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        umma::fence_smem_async();
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
+        if (tid == 0) {
+            const uint32_t ab = umma::smem_u32(sA), bb = umma::smem_u32(sB), sbo = KC * 128;
+            for (int kb = 0; kb < WG_PIX / 16; ++kb)
+                umma::mma(tmem, umma::desc(ab + kb * 256, 128, sbo),
+                          umma::desc(bb + kb * 256, 128, sbo), umma::idesc_bf16(128, CH),
+                          stage > 0 || kb > 0);
+            umma::commit(&bar);
+        }
+        ok = __syncthreads_and(umma::wait(&bar, stage & 1));
+        umma::fence_after();
+        if (!ok) break;
+    }
+    if (ok) {
+        float v[32];
+        umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+        const int m = m0 + warp * 32 + lane;
+        if (m < 9 * CIN) {
+            const int tap = m / CIN, ci = m - tap * CIN;
+            if (ci < a.cin_real)
+                for (int co = 0; co < CH; ++co)
+                    atomicAdd(a.grad + a.w_off + (co * 9 + tap) * a.cin_real + ci, v[co]);
+        } else if (m == 9 * CIN) {
+            for (int co = 0; co < CH; ++co) atomicAdd(a.grad + a.b_off + co, v[co]);
+        }
+    } else if (tid == 0) {
+        atomicExch(a.err, 1);
+    }
+    umma::fence_before();
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, 32);
+}
+
+// BF16 GEMM operands from the FP32 parameters: forward B[co][t CIN + ci] per layer and the input
+// gradient's B[ci][t 32 + co] for layers 2-4.
+__global__ void cnn_prep_weights_kernel(const float* prm, bf16* f1, bf16* f2, bf16* f3, bf16* f4,
+                                        bf16* d2, bf16* d3, bf16* d4)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < CH * K1) {
+        const int co = i / K1, k = i - co * K1, t = k / CIN0, ci = k - t * CIN0;
+        const float v = (t < 9 && ci < NFEAT) ? prm[P_W1 + (co * 9 + t) * NFEAT + ci] : 0.f;
+        f1[i] = __float2bfloat16_rn(v);
+    }
+    if (i < CH * KH) {
+        const int r = i / KH, k = i - r * KH;
+        {   // forward: r = co, k = t 32 + ci
+            const int t = k / CH, ci = k - t * CH, idx = (r * 9 + t) * CH + ci;
+            f2[i] = __float2bfloat16_rn(prm[P_W2 + idx]);
+            f3[i] = __float2bfloat16_rn(prm[P_W3 + idx]);
+            f4[i] = __float2bfloat16_rn(prm[P_W4 + idx]);
+        }
+        {   // input gradient: r = ci, k = t 32 + co
+            const int t = k / CH, co = k - t * CH, idx = (co * 9 + t) * CH + r;
+            d2[i] = __float2bfloat16_rn(prm[P_W2 + idx]);
+            d3[i] = __float2bfloat16_rn(prm[P_W3 + idx]);
+            d4[i] = __float2bfloat16_rn(prm[P_W4 + idx]);
+        }
+    }
+}
+
+// FP32 features (H x W x 3) -> BF16 NHWC with 8 channels.
+__global__ void cnn_input_kernel(const float* feat, int n, bf16* x0)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint4 v;
+    v.x = pack_bf16x2(feat[3 * p], feat[3 * p + 1]);
+    v.y = pack_bf16x2(feat[3 * p + 2], 0.f);
+    v.z = 0u;
+    v.w = 0u;
+    reinterpret_cast<uint4*>(x0)[p] = v;
+}
+
+// Head (1x1 conv 32 -> 1 + logistic), the loss and, with a target, the head's backward pass:
+// dY4 = (p - t)/n w_head (Y4 > 0) in BF16, gradients of w_head and b_head, loss sum.
+constexpr int HEAD_THREADS = 256;
+__global__ void __launch_bounds__(HEAD_THREADS)
+    cnn_head_kernel(const bf16* y4, int n, const float* prm, const float* target, float* prob,
+                    bf16* dy4, float* grad, float* loss_sum)
+{
+    __shared__ float red[CH + 2][HEAD_THREADS / 32];
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    float h[CH];
+    float dlog = 0.f, l = 0.f;
+    if (p < n) {
+        const uint4* src = reinterpret_cast<const uint4*>(y4 + (int64_t)p * CH);
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4) {
+            uint4 v = src[c4];
+            const __nv_bfloat162* hv = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float2 f = __bfloat1622float2(hv[k]);
+                h[c4 * 8 + 2 * k] = f.x;
+                h[c4 * 8 + 2 * k + 1] = f.y;
+            }
+        }
+        float z = prm[P_BH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) z += prm[P_WH + c] * h[c];
+        const float pr = 1.f / (1.f + expf(-z));
+        if (prob) prob[p] = pr;
+        if (target) {
+            const float t = target[p];
+            l = fmaxf(z, 0.f) - z * t + log1pf(expf(-fabsf(z)));
+            dlog = (pr - t) / (float)n;
+            uint32_t w[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c)
+                w[c] = pack_bf16x2(h[2 * c] > 0.f ? dlog * prm[P_WH + 2 * c] : 0.f,
+                                   h[2 * c + 1] > 0.f ? dlog * prm[P_WH + 2 * c + 1] : 0.f);
+            uint4* o = reinterpret_cast<uint4*>(dy4 + (int64_t)p * CH);
+#pragma unroll
+            for (int c4 = 0; c4 < 4; ++c4)
+                o[c4] = make_uint4(w[4 * c4], w[4 * c4 + 1], w[4 * c4 + 2], w[4 * c4 + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < CH; ++c) h[c] = 0.f;
+    }
+    if (!target) return;  // uniform over the grid
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    auto wsum = [&](float v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+        const float s = wsum(dlog * h[c]);
+        if (lane == 0) red[c][wid] = s;
+    }
+    {
+        const float s = wsum(dlog), s2 = wsum(l);
+        if (lane == 0) {
+            red[CH][wid] = s;
+            red[CH + 1][wid] = s2;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < CH + 2) {
+        float s = 0.f;
+        for (int w = 0; w < HEAD_THREADS / 32; ++w) s += red[threadIdx.x][w];
+        if (threadIdx.x < CH)
+            atomicAdd(grad + P_WH + threadIdx.x, s);
+        else if (threadIdx.x == CH)
+            atomicAdd(grad + P_BH, s);
+        else
+            atomicAdd(loss_sum, s);
+    }
+}
+
+// Adam (Kingma & Ba 2015) on the FP32 parameters; clears the gradients.
+__global__ void cnn_adam_kernel(float* prm, float* grad, float* m, float* v, int n, float lr,
+                                float b1t, float b2t)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = grad[i];
+    const float mi = 0.9f * m[i] + 0.1f * g, vi = 0.999f * v[i] + 0.001f * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    prm[i] -= lr * (mi / (1.f - b1t)) / (sqrtf(vi / (1.f - b2t)) + 1e-8f);
+    grad[i] = 0.f;
+}
+
+// --------------------------------------------------------------------------------------------
+// host side: the network's device state and its passes
+// --------------------------------------------------------------------------------------------
+
+struct CnnState {
+    float *prm = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
+    bf16 *f1 = nullptr, *f2 = nullptr, *f3 = nullptr, *f4 = nullptr, *d2 = nullptr, *d3 = nullptr,
+         *d4 = nullptr;
+    int* err = nullptr;
+    int step = 0;
+    bool weights_ready = false;
+    // activations, sized for the largest lattice seen
+    int64_t cap = 0;
+    bf16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *a4 = nullptr;
+    bf16 *g1 = nullptr, *g2 = nullptr, *g3 = nullptr, *g4 = nullptr;
+};
+
+static int conv_smem(int kpad) { return (128 + CH) * kpad * 2; }
+
+template <int CIN, int KPAD, int MODE>
+static cudaError_t run_conv(const ConvArgs& a, cudaStream_t st)
+{
+    static bool attr = false;  // one device per process is the supported configuration
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv_gemm_kernel<CIN, KPAD, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             conv_smem(KPAD));
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int rows = MODE == 0 ? a.Ho * a.Wo : a.H * a.W;
+    conv_gemm_kernel<CIN, KPAD, MODE><<<(rows + 127) / 128, GEMM_THREADS, conv_smem(KPAD), st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int CIN>
+static cudaError_t run_wgrad(WgradArgs a, cudaStream_t st)
+{
+    const int npo = a.Ho * a.Wo;
+    int ctas = (npo + 2047) / 2048;
+    if (ctas < 1) ctas = 1;
+    a.pix_per_cta = ((npo + ctas - 1) / ctas + WG_PIX - 1) / WG_PIX * WG_PIX;
+    const int mtiles = (9 * CIN + 1 + 127) / 128;
+    conv_wgrad_kernel<CIN><<<dim3(ctas, mtiles), GEMM_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+#define CKE(x)                                 \
+    do {                                       \
+        cudaError_t e_ = (x);                  \
+        if (e_ != cudaSuccess) return e_;      \
+    } while (0)
+
+static cudaError_t ensure_state(CnnState*& s)
+{
+    if (s) return cudaSuccess;
+    s = new CnnState();
+    CKE(cudaMalloc(&s->prm, sizeof(float) * P_N));
+    CKE(cudaMalloc(&s->grad, sizeof(float) * P_N));
+    CKE(cudaMalloc(&s->m, sizeof(float) * P_N));
+    CKE(cudaMalloc(&s->v, sizeof(float) * P_N));
+    CKE(cudaMalloc(&s->loss, sizeof(float) * 2));
+    CKE(cudaMalloc(&s->err, sizeof(int)));
+    CKE(cudaMemset(s->err, 0, sizeof(int)));
+    CKE(cudaMalloc(&s->f1, sizeof(bf16) * CH * K1));
+    for (bf16** p : {&s->f2, &s->f3, &s->f4, &s->d2, &s->d3, &s->d4})
+        CKE(cudaMalloc(p, sizeof(bf16) * CH * KH));
+    return cudaSuccess;
+}
+
+static cudaError_t ensure_acts(CnnState* s, int H, int W)
+{
+    const int64_t n = (int64_t)H * W;
+    if (n <= s->cap) return cudaSuccess;
+    for (bf16** p : {&s->x0, &s->a1, &s->a2, &s->a3, &s->a4, &s->g1, &s->g2, &s->g3, &s->g4}) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    s->cap = 0;
+    CKE(cudaMalloc(&s->x0, sizeof(bf16) * n * CIN0));
+    for (bf16** p : {&s->a1, &s->a2, &s->a3, &s->a4, &s->g1, &s->g2, &s->g3, &s->g4})
+        CKE(cudaMalloc(p, sizeof(bf16) * n * CH));
+    s->cap = n;
+    return cudaSuccess;
+}
+
+void cnn_destroy(CnnState* s)
+{
+    if (!s) return;
+    for (float* p : {s->prm, s->grad, s->m, s->v, s->loss}) cudaFree(p);
+    for (bf16* p : {s->f1, s->f2, s->f3, s->f4, s->d2, s->d3, s->d4, s->x0, s->a1, s->a2, s->a3,
+                    s->a4, s->g1, s->g2, s->g3, s->g4})
+        cudaFree(p);
+    cudaFree(s->err);
+    delete s;
+}
+
+cudaError_t cnn_load(CnnState*& s, const float* host_params, cudaStream_t st)
+{
+    CKE(ensure_state(s));
+    CKE(cudaMemcpyAsync(s->prm, host_params, sizeof(float) * P_N, cudaMemcpyHostToDevice, st));
+    CKE(cudaMemsetAsync(s->grad, 0, sizeof(float) * P_N, st));
+    CKE(cudaMemsetAsync(s->m, 0, sizeof(float) * P_N, st));
+    CKE(cudaMemsetAsync(s->v, 0, sizeof(float) * P_N, st));
+    s->step = 0;
+    s->weights_ready = false;
+    return cudaStreamSynchronize(st);
+}
+
+cudaError_t cnn_read(CnnState* s, float* host_params, cudaStream_t st)
+{
+    CKE(cudaMemcpyAsync(host_params, s->prm, sizeof(float) * P_N, cudaMemcpyDeviceToHost, st));
+    return cudaStreamSynchronize(st);
+}
+
+static cudaError_t prep_weights(CnnState* s, cudaStream_t st)
+{
+    if (s->weights_ready) return cudaSuccess;
+    cnn_prep_weights_kernel<<<(CH * KH + 255) / 256, 256, 0, st>>>(s->prm, s->f1, s->f2, s->f3,
+                                                                   s->f4, s->d2, s->d3, s->d4);
+    CKE(cudaGetLastError());
+    s->weights_ready = true;
+    return cudaSuccess;
+}
+
+static inline int osz(int n, int s) { return (n - 1) / s + 1; }
+
+// Forward from s->x0 (already filled); probabilities to prob (nullable); with target, the backward
+// pass accumulates into s->grad and the loss sum into s->loss[0].
+static cudaError_t forward_backward(CnnState* s, int H, int W, const float* target, float* prob,
+                                    cudaStream_t st)
+{
+    CKE(prep_weights(s, st));
+    const int H2 = osz(H, 2), W2 = osz(W, 2), H4 = osz(H2, 2), W4 = osz(W2, 2);
+    ConvArgs c{};
+    c.err = s->err;
+    // c1, c2 (stride 1), c3, c4 (stride 2)
+    c.src = s->x0; c.B = s->f1; c.bias = s->prm + P_B1; c.out = s->a1;
+    c.H = H; c.W = W; c.Ho = H; c.Wo = W; c.stride = 1;
+    CKE((run_conv<CIN0, K1, 0>(c, st)));
+    c.src = s->a1; c.B = s->f2; c.bias = s->prm + P_B2; c.out = s->a2;
+    CKE((run_conv<CH, KH, 0>(c, st)));
+    c.src = s->a2; c.B = s->f3; c.bias = s->prm + P_B3; c.out = s->a3;
+    c.Ho = H2; c.Wo = W2; c.stride = 2;
+    CKE((run_conv<CH, KH, 0>(c, st)));
+    c.src = s->a3; c.B = s->f4; c.bias = s->prm + P_B4; c.out = s->a4;
+    c.H = H2; c.W = W2; c.Ho = H4; c.Wo = W4;
+    CKE((run_conv<CH, KH, 0>(c, st)));
+    const int n4 = H4 * W4;
+    if (target) CKE(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
+    cnn_head_kernel<<<(n4 + HEAD_THREADS - 1) / HEAD_THREADS, HEAD_THREADS, 0, st>>>(
+        s->a4, n4, s->prm, target, prob, s->g4, s->grad, s->loss);
+    CKE(cudaGetLastError());
+    if (!target) return cudaSuccess;
+    WgradArgs w{};
+    w.grad = s->grad;
+    w.err = s->err;
+    ConvArgs d{};
+    d.err = s->err;
+    // layer 4: X = a3 (H2 x W2), dY = g4 (H4 x W4)
+    w.X = s->a3; w.dY = s->g4; w.w_off = P_W4; w.b_off = P_B4; w.cin_real = CH;
+    w.H = H2; w.W = W2; w.Ho = H4; w.Wo = W4; w.stride = 2;
+    CKE(run_wgrad<CH>(w, st));
+    d.src = s->g4; d.B = s->d4; d.mask = s->a3; d.out = s->g3;
+    d.H = H2; d.W = W2; d.Ho = H4; d.Wo = W4; d.stride = 2;
+    CKE((run_conv<CH, KH, 1>(d, st)));
+    // layer 3: X = a2 (H x W), dY = g3 (H2 x W2)
+    w.X = s->a2; w.dY = s->g3; w.w_off = P_W3; w.b_off = P_B3;
+    w.H = H; w.W = W; w.Ho = H2; w.Wo = W2; w.stride = 2;
+    CKE(run_wgrad<CH>(w, st));
+    d.src = s->g3; d.B = s->d3; d.mask = s->a2; d.out = s->g2;
+    d.H = H; d.W = W; d.Ho = H2; d.Wo = W2; d.stride = 2;
+    CKE((run_conv<CH, KH, 1>(d, st)));
+    // layer 2: X = a1, dY = g2 (stride 1)
+    w.X = s->a1; w.dY = s->g2; w.w_off = P_W2; w.b_off = P_B2;
+    w.Ho = H; w.Wo = W; w.stride = 1;
+    CKE(run_wgrad<CH>(w, st));
+    d.src = s->g2; d.B = s->d2; d.mask = s->a1; d.out = s->g1;
+    d.Ho = H; d.Wo = W; d.stride = 1;
+    CKE((run_conv<CH, KH, 1>(d, st)));
+    // layer 1: X = x0 (8 channels, 3 real), dY = g1
+    w.X = s->x0; w.dY = s->g1; w.w_off = P_W1; w.b_off = P_B1; w.cin_real = NFEAT;
+    CKE(run_wgrad<CIN0>(w, st));
+    return cudaSuccess;
+}
+
+static int check_err(CnnState* s, cudaStream_t st)
+{
+    int e = 0;
+    if (cudaMemcpyAsync(&e, s->err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return ART_ERR_CUDA;
+    if (e) {
+        cudaMemsetAsync(s->err, 0, sizeof(int), st);
+        return ART_ERR_DEVICE;
+    }
+    return ART_OK;
+}
+
+int cnn_forward(CnnState* s, const float* feat, int H, int W, float* prob, cudaStream_t st)
+{
+    if (!s) return ART_ERR_ARG;
+    if (ensure_acts(s, H, W) != cudaSuccess) return ART_ERR_OOM;
+    cnn_input_kernel<<<(H * W + 255) / 256, 256, 0, st>>>(feat, H * W, s->x0);
+    if (cudaGetLastError() != cudaSuccess) return ART_ERR_CUDA;
+    if (forward_backward(s, H, W, nullptr, prob, st) != cudaSuccess) return ART_ERR_CUDA;
+    return check_err(s, st);
+}
+
+// Forward from the BF16 input already in the state (used by the render's proposal step).
+cudaError_t cnn_forward_x0(CnnState* s, int H, int W, float* prob, cudaStream_t st)
+{
+    return forward_backward(s, H, W, nullptr, prob, st);
+}
+
+cudaError_t cnn_ensure_input(CnnState* s, int H, int W, bf16** x0)
+{
+    CKE(ensure_acts(s, H, W));
+    *x0 = s->x0;
+    return cudaSuccess;
+}
+
+int cnn_grad(CnnState* s, const float* feat, int H, int W, const float* target, float* loss,
+             float* grad_host, cudaStream_t st)
+{
+    if (!s) return ART_ERR_ARG;
+    if (ensure_acts(s, H, W) != cudaSuccess) return ART_ERR_OOM;
+    if (cudaMemsetAsync(s->grad, 0, sizeof(float) * P_N, st) != cudaSuccess) return ART_ERR_CUDA;
+    cnn_input_kernel<<<(H * W + 255) / 256, 256, 0, st>>>(feat, H * W, s->x0);
+    if (cudaGetLastError() != cudaSuccess) return ART_ERR_CUDA;
+    if (forward_backward(s, H, W, target, nullptr, st) != cudaSuccess) return ART_ERR_CUDA;
+    const int H4 = osz(osz(H, 2), 2), W4 = osz(osz(W, 2), 2);
+    float lsum = 0.f;
+    if (cudaMemcpyAsync(&lsum, s->loss, sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ART_ERR_CUDA;
+    if (grad_host &&
+        cudaMemcpyAsync(grad_host, s->grad, sizeof(float) * P_N, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+        return ART_ERR_CUDA;
+    int rc = check_err(s, st);
+    if (loss) *loss = lsum / (float)(H4 * W4);
+    return rc;
+}
+
+int cnn_train_step(CnnState* s, const float* feat, int H, int W, const float* target, float lr,
+                   float* loss, cudaStream_t st)
+{
+    int rc = cnn_grad(s, feat, H, W, target, loss, nullptr, st);
+    if (rc) return rc;
+    s->step += 1;
+    const float b1t = powf(0.9f, (float)s->step), b2t = powf(0.999f, (float)s->step);
+    cnn_adam_kernel<<<(P_N + 255) / 256, 256, 0, st>>>(s->prm, s->grad, s->m, s->v, P_N, lr, b1t, b2t);
+    if (cudaGetLastError() != cudaSuccess) return ART_ERR_CUDA;
+    s->weights_ready = false;
+    return ART_OK;
+}
+
+}  // namespace art

@@ -81,7 +81,7 @@ cudaError_t launch_enqueue_base_batch(const DevJob* jobs, int n, int max_base, i
                                       cudaStream_t st);
 cudaError_t launch_norm_batch(const DevJob* jobs, double* const* imgs, int n, double* norms,
                               cudaStream_t st);
-cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_points,
+cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_kx, int max_ky,
                                 const double* norms, double* const* imgs, uint8_t* const* masks,
                                 int64_t* queue, unsigned long long* qcount,
                                 unsigned long long* img_counts, cudaStream_t st);
@@ -109,5 +109,16 @@ cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double
 cudaError_t launch_metrics(const double* truth, const double* img, const uint8_t* mask, int nx,
                            int ny, double* partials, int nblocks, double* out6, cudaStream_t st);
 constexpr int METRIC_BLOCKS = 304;
+
+// cnn.cu
+struct CnnState;
+void cnn_destroy(CnnState* s);
+cudaError_t cnn_load(CnnState*& s, const float* host_params, cudaStream_t st);
+cudaError_t cnn_read(CnnState* s, float* host_params, cudaStream_t st);
+int cnn_forward(CnnState* s, const float* feat, int H, int W, float* prob, cudaStream_t st);
+int cnn_grad(CnnState* s, const float* feat, int H, int W, const float* target, float* loss,
+             float* grad_host, cudaStream_t st);
+int cnn_train_step(CnnState* s, const float* feat, int H, int W, const float* target, float lr,
+                   float* loss, cudaStream_t st);
 
 }  // namespace art
