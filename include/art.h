@@ -95,6 +95,17 @@ typedef struct art_job {
      * n_e = rho m_unit/(length_cm^3 (m_p + m_e)), |B| = |b| c sqrt(4 pi m_unit / length_cm^3);
      * no emission where b^2/rho > sigma_cut; observed at nu_hz. */
     double gamma_ad, m_unit, r_high, r_low, sigma_cut;
+    /* Learned path (not in the paper): with proposal = 1, after the criterion of every level
+     * k = 1, 1 + D, 1 + 2D, ... (D = proposal_depth >= 1) the loaded network (art_cnn_load) reads
+     * the completed level-(k-1) lattice, and in every block whose probability exceeds proposal_p
+     * the points of levels k+1 .. k+D next to the refinement front (a corner of their level-k
+     * cell is traced) are traced speculatively together with level k's rays.  The exact criterion still decides
+     * every point: a speculative ray it asks for is used, one it does not ask for is discarded
+     * (interpolated), so image and mask equal those of the same render without the proposal.
+     * Requires a loaded network and no truth image (else ART_ERR_ARG); a scratch mask is used
+     * when mask_dev is NULL. */
+    int32_t proposal, proposal_depth;
+    double proposal_p;
 } art_job;
 
 /* Statistics of one render (host struct, filled on return). */
@@ -107,11 +118,14 @@ typedef struct art_stats {
     int64_t rays_per_level[16]; /* rays traced at level 0..N */
     double norm;                /* I_bar_int (or the peak) used by the criterion */
     int64_t kernel_launches;    /* CUDA kernels this call launched */
+    int64_t rays_speculative;   /* learned path: rays traced speculatively */
+    int64_t rays_spec_used;     /* learned path: speculative rays the criterion asked for (these
+                                 * are included in rays_traced; the rest were wasted) */
 } art_stats;
 
 /* One kernel launch timed by the profiler (art_profile). */
 enum { ART_K_TRACE_FP64 = 0, ART_K_TRACE_FP32 = 1, ART_K_REFINE = 2, ART_K_OTHER = 3,
-       ART_K_TRACE_DF = 4 };
+       ART_K_TRACE_DF = 4, ART_K_PROPOSE = 5 };
 typedef struct art_launch_record {
     int32_t kind;   /* ART_K_* */
     int32_t level;  /* refinement level of the launch (-1 outside a render) */
@@ -279,6 +293,14 @@ int art_cnn_grad(art_ctx* ctx, const float* feat_dev, int32_t H, int32_t W,
 /* One Adam step (learning rate lr, beta1 0.9, beta2 0.999, eps 1e-8) on one lattice. */
 int art_cnn_train_step(art_ctx* ctx, const float* feat_dev, int32_t H, int32_t W,
                        const float* target_dev, float lr, float* loss_host);
+
+/* Training sample from the context's last render of `job` (which recorded per-pixel ray
+ * diagnostics because a network was loaded): feat_dev (H x W x 3 FP32) = the features of the
+ * level-`level` lattice of img_dev, target_dev (Ho x Wo FP32) = 1 where that render's mask traced
+ * a point of level level + 2 or level + 3 inside the block, else 0.  level + 2 <= levels.  ART_ERR_ARG if the
+ * last render did not record diagnostics for this grid. */
+int art_cnn_sample(art_ctx* ctx, const art_job* job, const double* img_dev,
+                   const uint8_t* mask_dev, int32_t level, float* feat_dev, float* target_dev);
 
 /* Image metrics of plane 0 (Eqs. interpdef, fluxdef, msedef): out_host[0] = interpolation
  * fraction (mask_dev nullable -> 0), [1] = flux error with the trapezoid flux, [2] = MSE

@@ -6,8 +6,10 @@ predict, from the completed level-k lattice, which blocks the exact criterion of
 refine two levels later, so those rays can be traced early.  The exact criterion still decides
 every point.  This module is the plain reference the GPU kernels are checked against:
 
-    features  f0 = asinh(I / I_norm), f1 = 3 / max(r_min, 1), f2 = polar turns, on the level-k
-              lattice (stride 2^(N-k) of the final grid); I_norm = the criterion's normalisation.
+    features  f0 = asinh(I / (R_abs I_norm)), f1 = 3 / max(r_min, 1), f2 = polar turns, on the
+              level-k lattice (stride 2^(N-k) of the final grid); I_norm = the criterion's
+              normalisation, R_abs its absolute tolerance (I_norm alone when R_abs <= 0; f0 = 0
+              when that scale is not positive).
     c1  3x3 conv,  3 -> 32, stride 1, pad 1, + bias, ReLU
     c2  3x3 conv, 32 -> 32, stride 1, pad 1, + bias, ReLU
     c3  3x3 conv, 32 -> 32, stride 2, pad 1, + bias, ReLU
@@ -73,13 +75,16 @@ def head_size(n: int) -> int:
     return out_size(out_size(n, 2), 2)
 
 
-def features(img, min_r, nturn, norm: float, level: int, levels: int):
+def features(img, min_r, nturn, norm: float, level: int, levels: int, r_abs: float = 0.0):
     """(H, W, 3) features of the level-`level` lattice of final-resolution planes."""
+    if r_abs > 0:
+        norm = norm * r_abs
     s = 1 << (levels - level)
     I = np.asarray(img, dtype=np.float64)[::s, ::s]
     mr = np.asarray(min_r, dtype=np.float64)[::s, ::s]
     nt = np.asarray(nturn, dtype=np.float64)[::s, ::s]
-    return np.stack([np.arcsinh(I / norm), 3.0 / np.maximum(mr, 1.0), nt], axis=-1)
+    f0 = np.arcsinh(I / norm) if norm > 0 else np.zeros_like(I)   # a dark image gives 0
+    return np.stack([f0, 3.0 / np.maximum(mr, 1.0), nt], axis=-1)
 
 
 def _im2col(x, stride):

@@ -46,6 +46,8 @@ class Job(ctypes.Structure):
         ("te_slope", ctypes.c_double), ("r_in", ctypes.c_double), ("length_cm", ctypes.c_double),
         ("bz_ratio", ctypes.c_double), ("gamma_ad", ctypes.c_double), ("m_unit", ctypes.c_double),
         ("r_high", ctypes.c_double), ("r_low", ctypes.c_double), ("sigma_cut", ctypes.c_double),
+        ("proposal", ctypes.c_int32), ("proposal_depth", ctypes.c_int32),
+        ("proposal_p", ctypes.c_double),
     ]
 
 
@@ -53,7 +55,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("rays_traced", ctypes.c_int64), ("rays_fp64", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("rays_capped", ctypes.c_int64),
                 ("rays_nan", ctypes.c_int64), ("rays_per_level", ctypes.c_int64 * 16),
-                ("norm", ctypes.c_double), ("kernel_launches", ctypes.c_int64)]
+                ("norm", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+                ("rays_speculative", ctypes.c_int64), ("rays_spec_used", ctypes.c_int64)]
 
 
 class LaunchRecord(ctypes.Structure):
@@ -61,7 +64,8 @@ class LaunchRecord(ctypes.Structure):
                 ("steps", ctypes.c_int64), ("items", ctypes.c_int64)]
 
 
-KERNEL_KINDS = {0: "trace_fp64", 1: "trace_fp32", 2: "refine", 3: "other", 4: "trace_df"}
+KERNEL_KINDS = {0: "trace_fp64", 1: "trace_fp32", 2: "refine", 3: "other", 4: "trace_df",
+                5: "propose"}
 
 
 class RayAux(ctypes.Structure):
@@ -70,7 +74,8 @@ class RayAux(ctypes.Structure):
 
 
 _JOB_DEFAULTS = dict(fp64_sweep=3.0 * 3.141592653589793, gamma_ad=13.0 / 9.0, m_unit=3e26,
-                     r_high=20.0, r_low=1.0, sigma_cut=1.0)
+                     r_high=20.0, r_low=1.0, sigma_cut=1.0, proposal=0, proposal_depth=2,
+                     proposal_p=0.5)
 
 
 def make_job(**params) -> Job:
@@ -95,7 +100,8 @@ EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_p
            "art_trace_pixels", "art_ibar_int", "art_refine_level", "art_render",
            "art_render_host", "art_metrics", "art_profile", "art_profile_read",
            "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid", "art_cnn_load",
-           "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step")
+           "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step",
+           "art_cnn_sample")
 CNN_PARAMS = 28673
 NOALLOC_MAX_RAYS = 1 << 20
 
@@ -138,6 +144,7 @@ def load():
             lib.art_cnn_forward.argtypes = [vp, vp, i32, i32, vp]
             lib.art_cnn_grad.argtypes = [vp, vp, i32, i32, vp, fp, vp]
             lib.art_cnn_train_step.argtypes = [vp, vp, i32, i32, vp, ctypes.c_float, fp]
+            lib.art_cnn_sample.argtypes = [vp, P(Job), vp, vp, i32, vp, vp]
             _lib = lib
     return _lib
 
@@ -194,7 +201,8 @@ def _dptr(t):
 def _stats_dict(st: Stats, levels: int) -> dict:
     return dict(rays_traced=st.rays_traced, rays_fp64=st.rays_fp64, steps=st.steps,
                 rays_capped=st.rays_capped, rays_nan=st.rays_nan, norm=st.norm,
-                kernel_launches=st.kernel_launches,
+                kernel_launches=st.kernel_launches, rays_speculative=st.rays_speculative,
+                rays_spec_used=st.rays_spec_used,
                 rays_per_level=[st.rays_per_level[k] for k in range(levels + 1)])
 
 
@@ -357,6 +365,18 @@ class Context:
         _check(load().art_cnn_train_step(self._ctx, _dptr(feat), H, W, _dptr(target), float(lr),
                                          ctypes.byref(loss)), "art_cnn_train_step")
         return loss.value
+
+    def art_cnn_sample(self, job: Job, img, mask, level: int):
+        """(features (H, W, 3), targets (Ho, Wo)) of one level of the context's last render."""
+        import torch
+        s = 1 << (job.levels - level)
+        nx, ny = art_image_size(job)
+        H, W = (ny - 1) // s + 1, (nx - 1) // s + 1
+        feat = torch.empty((H, W, 3), dtype=torch.float32, device=img.device)
+        tgt = torch.empty(self.cnn_out_shape(H, W), dtype=torch.float32, device=img.device)
+        _check(load().art_cnn_sample(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask), level,
+                                     _dptr(feat), _dptr(tgt)), "art_cnn_sample")
+        return feat, tgt
 
     def art_profile(self, enable: bool):
         _check(load().art_profile(self._ctx, int(bool(enable))), "art_profile")

@@ -25,8 +25,15 @@ struct art_ctx {
     float* grid_owned = nullptr;
     int32_t g_n1 = 0, g_n2 = 0, g_n3 = 0;
     double g_x1min = 0.0, g_x1max = 0.0;
-    // learned block proposal (cnn.cu)
+    // learned block proposal (cnn.cu): the network, per-pixel diagnostics planes of the last
+    // render (min r, polar turns), a scratch mask and the proposal probabilities
     CnnState* cnn = nullptr;
+    float* aux = nullptr;
+    int64_t aux_cap = 0, aux_npix = 0;
+    uint8_t* smask = nullptr;
+    int64_t smask_cap = 0;
+    float* prob = nullptr;
+    int64_t prob_cap = 0;
     // batched rendering tables and queue (grown, never shrunk)
     DevJob* bjobs = nullptr;
     SynchConst* bsynch = nullptr;
@@ -321,6 +328,9 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFree(c->breroute);
     cudaFree(c->grid_owned);
     cnn_destroy(c->cnn);
+    cudaFree(c->aux);
+    cudaFree(c->smask);
+    cudaFree(c->prob);
     for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -356,6 +366,20 @@ static int ensure_queue(art_ctx* c, int64_t cap)
     return ART_OK;
 }
 
+// Grow a context-owned device buffer to at least `n` elements (synchronises first).
+template <class T>
+static int grow(art_ctx* c, T*& buf, int64_t& cap, int64_t n)
+{
+    if (n <= cap) return ART_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(buf);
+    buf = nullptr;
+    cap = 0;
+    CK(cudaMalloc(&buf, sizeof(T) * n));
+    cap = n;
+    return ART_OK;
+}
+
 // Largest number of rays one level can queue: the base grid or the new points of level N.
 static int64_t max_level_rays(const DevJob& J)
 {
@@ -369,11 +393,15 @@ static int64_t max_level_rays(const DevJob& J)
 // Trace the rays of the queue (length in counters[count_idx]) with the job's precision.
 static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
                        const unsigned long long* count, double* img, uint8_t* mask, double* out,
-                       const art_rayaux* aux)
+                       const art_rayaux* aux, float* pix_minr = nullptr, float* pix_turn = nullptr,
+                       const unsigned long long* spec_from = nullptr)
 {
     TraceArgs a;
     memset(&a, 0, sizeof a);
     a.job = J;
+    a.pix_minr = pix_minr;
+    a.pix_turn = pix_turn;
+    a.spec_from = spec_from;
     make_synch(job, c, &a.synch);
     a.cam = c->cam;
     a.queue = c->queue;
@@ -507,11 +535,38 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
     DevJob J;
     int rc = make_devjob(job, &J);
     if (rc || (rc = check_grid(c, job))) return rc;
+    const bool learned = job->proposal != 0;
+    if (learned && (!c->cnn || truth_dev || !(job->proposal_p >= 0.0) || !(job->proposal_p <= 1.0) ||
+                    job->proposal_depth < 1))
+        return ART_ERR_ARG;
     CK(cudaSetDevice(c->device));
-    if ((rc = ensure_fixed(c)) || (rc = ensure_queue(c, max_level_rays(J)))) return rc;
+    const int64_t cap = max_level_rays(J);
+    // the learned path appends speculative rays of later levels to a level's queue
+    const int64_t qcap = learned ? cap + std::min<int64_t>((int64_t)J.nx * J.ny, 4 * cap) : cap;
+    if ((rc = ensure_fixed(c)) || (rc = ensure_queue(c, qcap))) return rc;
     cudaStream_t st = c->stream;
     const int64_t npix = (int64_t)J.nx * J.ny;
-    const int64_t cap = max_level_rays(J);
+    // per-pixel diagnostics (network features) are recorded whenever a network is loaded
+    float *aminr = nullptr, *aturn = nullptr;
+    if (c->cnn && !truth_dev) {
+        if ((rc = grow(c, c->aux, c->aux_cap, 2 * npix))) return rc;
+        aminr = c->aux;
+        aturn = c->aux + npix;
+        c->aux_npix = npix;
+    } else {
+        c->aux_npix = 0;
+    }
+    uint8_t* mask = mask_dev;
+    if (learned) {
+        if (!mask) {
+            if ((rc = grow(c, c->smask, c->smask_cap, npix))) return rc;
+            mask = c->smask;
+        }
+        int64_t pc = 1;
+        for (int lv = 0; lv + 2 <= J.levels; ++lv) pc = std::max(pc, cnn_head_cells(J, lv));
+        if ((rc = grow(c, c->prob, c->prob_cap, pc))) return rc;
+        CK(cudaMemsetAsync(mask, 0, npix, st));  // speculation claims points whose mask is unset
+    }
     c->launches = 0;
     CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * C_COUNT, st));
     int k;
@@ -526,15 +581,29 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
     prof_end(c, k, ART_K_OTHER, -1);
     for (int level = 0; level <= J.levels; ++level) {
         c->prof_level = level;
+        bool spec = false;
         if (level > 0) {
             const int s = 1 << (J.levels - level);
             CK(cudaMemsetAsync(c->counters + C_QUEUE, 0, sizeof(unsigned long long), st));
             k = prof_begin(c);
-            CK(launch_refine(J, level, c->norm3, img_dev, mask_dev, c->queue, c->counters + C_QUEUE,
-                             st));
+            CK(launch_refine(J, level, c->norm3, img_dev, mask, c->queue, c->counters + C_QUEUE, st,
+                             aminr, aturn, learned ? c->counters : nullptr));
             prof_end(c, k, ART_K_REFINE, (int64_t)((J.nx - 1) / s + 1) * ((J.ny - 1) / s + 1));
-            CK(cudaMemcpyAsync(c->counters + C_LEVEL0 + level, c->counters + C_QUEUE,
-                               sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st));
+            CK(launch_level_count(c->counters, level, st));
+            if (learned && level + 1 <= J.levels && (level - 1) % job->proposal_depth == 0) {
+                // every D = proposal_depth levels the network reads the completed level-(k-1)
+                // lattice and proposes points of levels k+1 .. k+D, traced now together with
+                // level k's rays; the D - 1 levels in between trace only what was not proposed
+                CK(launch_spec_mark(c->counters, st));
+                k = prof_begin(c);
+                CK(cnn_propose(c->cnn, J, level - 1, job->proposal_depth, img_dev, aminr, aturn,
+                               c->norm3,
+                               (float)job->proposal_p, c->prob, mask, c->queue, c->counters,
+                               (unsigned long long)qcap, st));
+                prof_end(c, k, ART_K_PROPOSE, -1);
+                CK(launch_queue_clamp(c->counters, (unsigned long long)qcap, st));
+                spec = true;
+            }
         }
         if (truth_dev) {
             k = prof_begin(c);
@@ -542,8 +611,8 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
                                    cap, st));
             prof_end(c, k, ART_K_OTHER, -1);
         } else {
-            if ((rc = trace_queue(c, job, J, c->counters + C_QUEUE, img_dev, mask_dev, nullptr,
-                                  nullptr)))
+            if ((rc = trace_queue(c, job, J, c->counters + C_QUEUE, img_dev, mask, nullptr, nullptr,
+                                  aminr, aturn, spec ? c->counters + C_SPECFROM : nullptr)))
                 return rc;
         }
         if (level == 0) {
@@ -553,7 +622,6 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
         }
     }
     c->prof_level = -1;
-    (void)npix;
     if (stats) {
         if ((rc = read_counters(c))) return rc;
         memset(stats, 0, sizeof *stats);
@@ -567,6 +635,8 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
         stats->rays_nan = (int64_t)c->pinned[C_NAN];
         stats->norm = c->pinned_d[0];
         stats->kernel_launches = c->launches;
+        stats->rays_speculative = (int64_t)c->pinned[C_SPEC];
+        stats->rays_spec_used = (int64_t)c->pinned[C_SPECUSED];
         if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
     }
     return ART_OK;
@@ -970,4 +1040,22 @@ extern "C" int art_cnn_train_step(art_ctx* c, const float* feat_dev, int32_t H, 
         return ART_ERR_ARG;
     CK(cudaSetDevice(c->device));
     return cnn_train_step(c->cnn, feat_dev, H, W, target_dev, lr, loss_host, c->stream);
+}
+
+extern "C" int art_cnn_sample(art_ctx* c, const art_job* job, const double* img_dev,
+                              const uint8_t* mask_dev, int32_t level, float* feat_dev,
+                              float* target_dev)
+{
+    if (!c || !img_dev || !mask_dev || !feat_dev || !target_dev) return ART_ERR_ARG;
+    DevJob J;
+    int rc = make_devjob(job, &J);
+    if (rc) return rc;
+    if (level < 0 || level + 2 > J.levels) return ART_ERR_ARG;
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    if (!c->aux || c->aux_npix != npix) return ART_ERR_ARG;  // no diagnostics of this grid
+    CK(cudaSetDevice(c->device));
+    CK(cnn_features_f32(J, level, img_dev, c->aux, c->aux + npix, c->norm3, feat_dev, c->stream));
+    CK(cnn_targets(J, level, mask_dev, target_dev, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return ART_OK;
 }

@@ -661,14 +661,176 @@ int cnn_grad(CnnState* s, const float* feat, int H, int W, const float* target, 
 int cnn_train_step(CnnState* s, const float* feat, int H, int W, const float* target, float lr,
                    float* loss, cudaStream_t st)
 {
-    int rc = cnn_grad(s, feat, H, W, target, loss, nullptr, st);
+    float l = 0.f;
+    int rc = cnn_grad(s, feat, H, W, target, &l, nullptr, st);
+    if (loss) *loss = l;
     if (rc) return rc;
+    if (!std::isfinite(l)) {  // a non-finite sample leaves the parameters unchanged
+        if (cudaMemsetAsync(s->grad, 0, sizeof(float) * P_N, st) != cudaSuccess) return ART_ERR_CUDA;
+        return ART_OK;
+    }
     s->step += 1;
     const float b1t = powf(0.9f, (float)s->step), b2t = powf(0.999f, (float)s->step);
     cnn_adam_kernel<<<(P_N + 255) / 256, 256, 0, st>>>(s->prm, s->grad, s->m, s->v, P_N, lr, b1t, b2t);
     if (cudaGetLastError() != cudaSuccess) return ART_ERR_CUDA;
     s->weights_ready = false;
     return ART_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// the learned path inside the render: features of a level lattice, the proposal, training targets
+// --------------------------------------------------------------------------------------------
+
+// Features of the level-`level` lattice (stride s of the final grid): asinh(I / (R_abs I_norm))
+// (the intensity in units of the absolute tolerance, so one network serves every tolerance),
+// 3 / max(r_min, 1), polar turns.  BF16 NHWC with 8 channels (x0) or FP32 with 3 (f32).
+__global__ void cnn_features_kernel(const double* img, const float* minr, const float* turn,
+                                    const double* norm, double r_abs, int nx, int ny, int s,
+                                    bf16* x0, float* f32)
+{
+    const int kx = (nx - 1) / s + 1, ky = (ny - 1) / s + 1;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= kx * ky) return;
+    const int jj = q / kx, ii = q - jj * kx;
+    const int64_t p = (int64_t)jj * s * nx + (int64_t)ii * s;
+    const double scale = r_abs > 0.0 ? r_abs * *norm : *norm;
+    const double x = img[p] / scale;
+    const float f0 = (scale > 0.0 && isfinite(x)) ? (float)asinh(x) : 0.f;  // dark image: 0
+    const float f1 = 3.f / fmaxf(minr[p], 1.f);
+    const float f2 = turn[p];
+    if (x0) {
+        uint4 v;
+        v.x = pack_bf16x2(f0, f1);
+        v.y = pack_bf16x2(f2, 0.f);
+        v.z = 0u;
+        v.w = 0u;
+        reinterpret_cast<uint4*>(x0)[q] = v;
+    }
+    if (f32) {
+        f32[3 * q] = f0;
+        f32[3 * q + 1] = f1;
+        f32[3 * q + 2] = f2;
+    }
+}
+
+static inline int head_dim(int n) { return osz(osz(n, 2), 2); }
+
+int64_t cnn_head_cells(const DevJob& J, int level)
+{
+    const int s = 1 << (J.levels - level);
+    return (int64_t)head_dim((J.nx - 1) / s + 1) * head_dim((J.ny - 1) / s + 1);
+}
+
+// One block per head cell (4 x 4 cells of the input lattice, level L, stride s_in): where the
+// probability exceeds thr, every point of levels L+2 .. L+1+depth inside the block (lattice of
+// stride s_t = s_in / 2^(depth+1), minus the level-(L+1) lattice of stride s_in / 2) whose mask is
+// still unset and whose enclosing level-(L+1) cell has a traced corner (the refinement front of
+// the exact criterion, just decided for level L+1) is queued for a speculative trace and marked
+// pending.  Blocks are disjoint, so each
+// point has one candidate thread; queue slots beyond `cap` are skipped.
+__global__ void __launch_bounds__(256)
+    cnn_propose_kernel(const float* prob, int hw, float thr, int nx, int ny, int s_in, int s_t,
+                       uint8_t* mask, int32_t* queue, unsigned long long* counters,
+                       unsigned long long cap)
+{
+    const int cell = blockIdx.x;
+    if (!(prob[cell] > thr)) return;  // uniform over the block
+    const int hy = cell / hw, hx = cell - hy * hw;
+    const int side = 4 * s_in / s_t, half = s_in / 2;
+    const int lane = threadIdx.x & 31;
+    for (int c0 = 0; c0 < side * side; c0 += 256) {
+        const int c = c0 + threadIdx.x;
+        const int cy = c / side, cx = c - cy * side;
+        const int i = hx * 4 * s_in + cx * s_t, j = hy * 4 * s_in + cy * s_t;
+        bool want = c < side * side && i < nx && j < ny && (i % half != 0 || j % half != 0);
+        const int64_t pix = (int64_t)j * nx + i;
+        if (want) want = mask[pix] == ART_MASK_UNSET;
+        if (want) {
+            // refinement front: a corner of the enclosing level-(L+1) cell (stride `half`) is
+            // traced -- the exact criterion has just queued it or traced it earlier
+            const int i0 = (i / half) * half, j0 = (j / half) * half;
+            const int i1 = min(i0 + half, nx - 1), j1 = min(j0 + half, ny - 1);
+            want = mask[(int64_t)j0 * nx + i0] == ART_MASK_TRACED ||
+                   mask[(int64_t)j0 * nx + i1] == ART_MASK_TRACED ||
+                   mask[(int64_t)j1 * nx + i0] == ART_MASK_TRACED ||
+                   mask[(int64_t)j1 * nx + i1] == ART_MASK_TRACED;
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, want);
+        if (!b) continue;
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(counters + C_QUEUE, (unsigned long long)__popc(b));
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (want) {
+            const unsigned long long slot = w + __popc(b & ((1u << lane) - 1u));
+            if (slot < cap) {
+                queue[slot] = (int32_t)pix;
+                mask[pix] = MASK_SPEC_PENDING;
+                atomicAdd(counters + C_SPEC, 1ull);
+            }
+        }
+    }
+}
+
+cudaError_t cnn_propose(CnnState* s, const DevJob& J, int level_in, int depth, const double* img,
+                        const float* minr, const float* turn, const double* norm, float thr,
+                        float* prob, uint8_t* mask, int32_t* queue, unsigned long long* counters,
+                        unsigned long long cap, cudaStream_t st)
+{
+    const int sin_ = 1 << (J.levels - level_in);
+    const int H = (J.ny - 1) / sin_ + 1, W = (J.nx - 1) / sin_ + 1;
+    const int last = level_in + 1 + depth < J.levels ? level_in + 1 + depth : J.levels;
+    CKE(ensure_acts(s, H, W));
+    cnn_features_kernel<<<(H * W + 255) / 256, 256, 0, st>>>(img, minr, turn, norm, J.R_abs, J.nx,
+                                                             J.ny, sin_, s->x0, nullptr);
+    CKE(cudaGetLastError());
+    CKE(forward_backward(s, H, W, nullptr, prob, st));
+    const int hh = head_dim(H), hw = head_dim(W);
+    cnn_propose_kernel<<<hh * hw, 256, 0, st>>>(prob, hw, thr, J.nx, J.ny, sin_,
+                                                1 << (J.levels - last), mask, queue, counters, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t cnn_features_f32(const DevJob& J, int level, const double* img, const float* minr,
+                             const float* turn, const double* norm, float* feat, cudaStream_t st)
+{
+    const int s = 1 << (J.levels - level);
+    const int H = (J.ny - 1) / s + 1, W = (J.nx - 1) / s + 1;
+    cnn_features_kernel<<<(H * W + 255) / 256, 256, 0, st>>>(img, minr, turn, norm, J.R_abs, J.nx,
+                                                             J.ny, s, nullptr, feat);
+    return cudaGetLastError();
+}
+
+// Training target of each head cell of the level-L lattice (stride s): 1 if the exact method
+// traced a point of level L + 2 or L + 3 inside the block (the levels a proposal made after
+// level L + 1's criterion covers with the default depth 2), else 0.  Points of those levels lie on
+// the lattice of stride s_t = max(s / 8, 1) and off the level-(L+1) lattice (stride s / 2).
+__global__ void __launch_bounds__(256)
+    cnn_targets_kernel(const uint8_t* mask, int nx, int ny, int hw, int s, float* target)
+{
+    const int cell = blockIdx.x;
+    const int hy = cell / hw, hx = cell - hy * hw;
+    const int st = s >= 8 ? s / 8 : 1, half = s / 2;
+    const int side = 4 * s / st;
+    int hit = 0;
+    for (int c = threadIdx.x; c < side * side; c += 256) {
+        const int cy = c / side, cx = c - cy * side;
+        const int i = hx * 4 * s + cx * st, j = hy * 4 * s + cy * st;
+        if (i < nx && j < ny && (i % half != 0 || j % half != 0) &&
+            mask[(int64_t)j * nx + i] == ART_MASK_TRACED)
+            hit = 1;
+    }
+    const int any = __syncthreads_or(hit);
+    if (threadIdx.x == 0) target[cell] = any ? 1.f : 0.f;
+}
+
+cudaError_t cnn_targets(const DevJob& J, int level, const uint8_t* mask, float* target,
+                        cudaStream_t st)
+{
+    const int s = 1 << (J.levels - level);
+    const int H = (J.ny - 1) / s + 1, W = (J.nx - 1) / s + 1;
+    cnn_targets_kernel<<<head_dim(H) * head_dim(W), 256, 0, st>>>(mask, J.nx, J.ny, head_dim(W), s,
+                                                                  target);
+    return cudaGetLastError();
 }
 
 }  // namespace art

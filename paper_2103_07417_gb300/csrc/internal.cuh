@@ -21,6 +21,9 @@ enum Counter {
     C_NAN = 6,       // rays stopped by a non-finite state
     C_BADIDX = 7,    // queue entries outside the image (skipped)
     C_FP64 = 8,      // rays re-traced by the high-precision pass of the mixed modes
+    C_SPECFROM = 9,  // learned path: first queue slot of the speculative rays of this level
+    C_SPEC = 10,     // learned path: rays queued speculatively (all levels)
+    C_SPECUSED = 11, // learned path: speculative rays the exact criterion asked for
     C_LEVEL0 = 16,   // C_LEVEL0 + k: rays of level k (16 slots)
     C_COUNT = 32
 };
@@ -44,7 +47,15 @@ struct TraceArgs {
     int32_t* aux_nturn;
     float* aux_minr;
     int64_t npix;
+    // image mode, learned path: per-pixel diagnostics planes (nullable) and the first queue slot
+    // of speculative rays (nullable; slots at or beyond it are marked MASK_SPEC_DONE)
+    float* pix_minr;
+    float* pix_turn;
+    const unsigned long long* spec_from;
 };
+
+// Transient mask values of the learned path (a render ends with every point TRACED or INTERP).
+constexpr uint8_t MASK_SPEC_PENDING = 3, MASK_SPEC_DONE = 4;
 
 // Batched rendering: the rays of many images share one queue whose entries are
 // (image << 32) | pixel; each image's job, synchrotron constants, camera and output live in tables.
@@ -105,7 +116,12 @@ cudaError_t launch_norm(const DevJob& J, const double* img, int nx, int ny, int 
                         double* norm3, cudaStream_t st);
 cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double* img,
                           uint8_t* mask, int32_t* queue, unsigned long long* count,
-                          cudaStream_t st);
+                          cudaStream_t st, float* aux_minr = nullptr, float* aux_turn = nullptr,
+                          unsigned long long* spec_used = nullptr);
+cudaError_t launch_level_count(unsigned long long* counters, int level, cudaStream_t st);
+cudaError_t launch_spec_mark(unsigned long long* counters, cudaStream_t st);
+cudaError_t launch_queue_clamp(unsigned long long* counters, unsigned long long cap,
+                               cudaStream_t st);
 cudaError_t launch_metrics(const double* truth, const double* img, const uint8_t* mask, int nx,
                            int ny, double* partials, int nblocks, double* out6, cudaStream_t st);
 constexpr int METRIC_BLOCKS = 304;
@@ -120,5 +136,16 @@ int cnn_grad(CnnState* s, const float* feat, int H, int W, const float* target, 
              float* grad_host, cudaStream_t st);
 int cnn_train_step(CnnState* s, const float* feat, int H, int W, const float* target, float lr,
                    float* loss, cudaStream_t st);
+// learned path: features of a level lattice from the image and diagnostics planes (BF16 into the
+// network's input, or FP32 for training), the proposal of speculative rays, training targets
+cudaError_t cnn_propose(CnnState* s, const DevJob& J, int level_in, int depth, const double* img,
+                        const float* minr, const float* turn, const double* norm, float thr,
+                        float* prob_scratch, uint8_t* mask, int32_t* queue,
+                        unsigned long long* counters, unsigned long long cap, cudaStream_t st);
+cudaError_t cnn_features_f32(const DevJob& J, int level, const double* img, const float* minr,
+                             const float* turn, const double* norm, float* feat, cudaStream_t st);
+cudaError_t cnn_targets(const DevJob& J, int level, const uint8_t* mask, float* target,
+                        cudaStream_t st);
+int64_t cnn_head_cells(const DevJob& J, int level);
 
 }  // namespace art

@@ -353,11 +353,26 @@ __device__ __forceinline__ int screen_decide(const Screen& sc, const double* img
     return -1;
 }
 
+// v * 2^-k (k = 1, 2), bit-identical to the FP64 product: for a normal v whose result stays
+// normal the product only lowers the exponent, done here on the integer pipes (GB300's FP64 pipe
+// issues 2 operations per SM and cycle); zeros, subnormal results, infinities and NaN multiply.
+__device__ __forceinline__ double scale_pow2(double v, int k)
+{
+    const int hi = __double2hiint(v), lo = __double2loint(v);
+    const int e = (hi >> 20) & 0x7ff;
+    if (e > k && e < 0x7ff) return __hiloint2double(hi - (k << 20), lo);
+    return v * (k == 1 ? 0.5 : 0.25);
+}
+
 // One new point of a level: decide (screen, else FP64), then mark it for tracing or write its
 // interpolant into every plane.  Returns true when the point is to be traced.
-__device__ __forceinline__ bool refine_point(const DevJob& J, const Screen& sc, double* img,
-                                             uint8_t* mask, int i, int j, int s, int cat,
-                                             double norm, int64_t npix)
+// Learned path (spec = true): a point the criterion traces whose ray was already traced
+// speculatively (mask MASK_SPEC_DONE) is marked traced and not queued again (return 2).
+// Diagnostics planes (nullable) receive the mean of the interpolation parents.
+__device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, double* img,
+                                            uint8_t* mask, int i, int j, int s, int cat,
+                                            double norm, int64_t npix, bool spec, float* aminr,
+                                            float* aturn)
 {
     double w1, w2;
     int64_t p1, p2, p3, p4;
@@ -389,72 +404,149 @@ __device__ __forceinline__ bool refine_point(const DevJob& J, const Screen& sc, 
     }
     const int64_t pix = (int64_t)j * J.nx + i;
     if (trace) {
-        if (mask) mask[pix] = ART_MASK_TRACED;
-        return true;
+        if (mask) {
+            const bool done = spec && mask[pix] == MASK_SPEC_DONE;
+            mask[pix] = ART_MASK_TRACED;
+            if (done) return 2;
+        }
+        return 1;
     }
+    if (aminr) {
+        if (cat == 4) {
+            aminr[pix] = 0.25f * (((aminr[p1] + aminr[p2]) + aminr[p3]) + aminr[p4]);
+            aturn[pix] = 0.25f * (((aturn[p1] + aturn[p2]) + aturn[p3]) + aturn[p4]);
+        } else {
+            aminr[pix] = 0.5f * (aminr[p1] + aminr[p2]);
+            aturn[pix] = 0.5f * (aturn[p1] + aturn[p2]);
+        }
+    }
+    const bool nearest = J.interp == ART_INTERP_NEAREST;
+    (void)w1;
+    (void)w2;
     for (int c = 0; c < J.planes; ++c) {
         const double* pl = img + c * npix;
         double v;
-        if (cat == 4) {
-            if (w2 == 0.0)
-                v = __ldg(pl + p1);
-            else
-                v = 0.25 * (((__ldg(pl + p1) + __ldg(pl + p2)) + __ldg(pl + p3)) + __ldg(pl + p4));
-        } else {
-            v = (w2 == 0.0) ? __ldg(pl + p1) : 0.5 * (__ldg(pl + p1) + __ldg(pl + p2));
-        }
+        if (nearest)
+            v = __ldg(pl + p1);
+        else if (cat == 4)
+            v = scale_pow2(((__ldg(pl + p1) + __ldg(pl + p2)) + __ldg(pl + p3)) + __ldg(pl + p4), 2);
+        else
+            v = scale_pow2(__ldg(pl + p1) + __ldg(pl + p2), 1);
         img[c * npix + pix] = v;
     }
     if (mask) mask[pix] = ART_MASK_INTERP;
-    return false;
+    return 0;
 }
 
+// Rows of the level lattice over blockIdx.y, columns over blockIdx.x and the threads: no index
+// division, and a warp covers 32 consecutive lattice points of one row.
 __global__ void __launch_bounds__(256)
     refine_kernel(DevJob J, int level, const double* __restrict__ norm_ptr, double* img,
-                  uint8_t* mask, int32_t* queue, unsigned long long* qcount)
+                  uint8_t* mask, int32_t* queue, unsigned long long* qcount, float* aminr,
+                  float* aturn, unsigned long long* counters)
 {
     const int s = 1 << (J.levels - level);
-    const unsigned nkx = (unsigned)((J.nx - 1) / s + 1), nky = (unsigned)((J.ny - 1) / s + 1);
-    const unsigned npts = nkx * nky;  // < 2^31 (art_image_size)
+    const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
     const int64_t npix = (int64_t)J.nx * J.ny;
     const double norm = *norm_ptr;
     const Screen sc = make_screen(J, norm);
     const int lane = threadIdx.x & 31;
-    for (unsigned base = blockIdx.x * blockDim.x; base < npts; base += gridDim.x * blockDim.x) {
-        const unsigned t = base + threadIdx.x;
-        bool trace = false;
-        int32_t pix = 0;
-        if (t < npts) {
-            const unsigned jj = t / nkx, ii = t - jj * nkx;
-            const int oi = ii & 1, oj = jj & 1;
-            if (oi | oj) {
-                const int i = (int)ii * s, j = (int)jj * s;
-                const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                trace = refine_point(J, sc, img, mask, i, j, s, cat, norm, npix);
-                pix = j * J.nx + i;
+    for (int jj = blockIdx.y; jj < nky; jj += gridDim.y) {
+        const int oj = jj & 1;
+        for (int i0 = blockIdx.x * blockDim.x; i0 < nkx; i0 += gridDim.x * blockDim.x) {
+            const int ii = i0 + (int)threadIdx.x;
+            bool trace = false, used = false;
+            int32_t pix = 0;
+            if (ii < nkx) {
+                const int oi = ii & 1;
+                if (oi | oj) {
+                    const int i = ii * s, j = jj * s;
+                    const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+                    const int r = refine_point(J, sc, img, mask, i, j, s, cat, norm, npix,
+                                               counters != nullptr, aminr, aturn);
+                    trace = r == 1;
+                    used = r == 2;
+                    pix = j * J.nx + i;
+                }
             }
-        }
-        // warp-aggregated append to the ray queue (ballot -> popc -> one atomic per warp)
-        const unsigned b = __ballot_sync(0xffffffffu, trace);
-        if (b) {
-            unsigned long long w = 0;
-            if (lane == 0) w = atomicAdd(qcount, (unsigned long long)__popc(b));
-            w = __shfl_sync(0xffffffffu, w, 0);
-            if (trace) queue[w + __popc(b & ((1u << lane) - 1u))] = pix;
+            // warp-aggregated append to the ray queue (ballot -> popc -> one atomic per warp)
+            const unsigned b = __ballot_sync(0xffffffffu, trace);
+            if (b) {
+                unsigned long long w = 0;
+                if (lane == 0) w = atomicAdd(qcount, (unsigned long long)__popc(b));
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (trace) queue[w + __popc(b & ((1u << lane) - 1u))] = pix;
+            }
+            if (counters) {
+                const unsigned u = __ballot_sync(0xffffffffu, used);
+                if (u && lane == 0) {
+                    atomicAdd(counters + C_SPECUSED, (unsigned long long)__popc(u));
+                    atomicAdd(counters + C_LEVEL0 + level, (unsigned long long)__popc(u));
+                }
+            }
         }
     }
 }
 
+// Launch shape of the row-wise kernels: enough blocks along a row to cover it (at most 16), and
+// rows spread so that the grid holds about 152 x 16 blocks.
+static dim3 refine_grid(int nkx, int nky)
+{
+    int gx = (nkx + 255) / 256;
+    if (gx > 16) gx = 16;
+    if (gx < 1) gx = 1;
+    int gy = (152 * 16) / gx;
+    if (gy > nky) gy = nky;
+    if (gy < 1) gy = 1;
+    return dim3(gx, gy);
+}
+
 cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double* img,
                           uint8_t* mask, int32_t* queue, unsigned long long* count,
-                          cudaStream_t st)
+                          cudaStream_t st, float* aux_minr, float* aux_turn,
+                          unsigned long long* spec_counters)
 {
     const int s = 1 << (J.levels - level);
-    const int64_t npts = (int64_t)((J.nx - 1) / s + 1) * ((J.ny - 1) / s + 1);
-    int64_t grid = (npts + 255) / 256;
-    if (grid < 1) grid = 1;
-    if (grid > 152 * 64) grid = 152 * 64;
-    refine_kernel<<<(int)grid, 256, 0, st>>>(J, level, norm, img, mask, queue, count);
+    const dim3 g = refine_grid((J.nx - 1) / s + 1, (J.ny - 1) / s + 1);
+    refine_kernel<<<g, 256, 0, st>>>(J, level, norm, img, mask, queue, count, aux_minr, aux_turn,
+                                     spec_counters);
+    return cudaGetLastError();
+}
+
+// counters[C_LEVEL0 + level] += counters[C_QUEUE] (rays of the level: queued + consumed speculative)
+__global__ void level_count_kernel(unsigned long long* counters, int level)
+{
+    counters[C_LEVEL0 + level] += counters[C_QUEUE];
+}
+
+cudaError_t launch_level_count(unsigned long long* counters, int level, cudaStream_t st)
+{
+    level_count_kernel<<<1, 1, 0, st>>>(counters, level);
+    return cudaGetLastError();
+}
+
+// counters[C_SPECFROM] = counters[C_QUEUE]: speculative rays are appended after this slot
+__global__ void spec_mark_kernel(unsigned long long* counters)
+{
+    counters[C_SPECFROM] = counters[C_QUEUE];
+}
+
+cudaError_t launch_spec_mark(unsigned long long* counters, cudaStream_t st)
+{
+    spec_mark_kernel<<<1, 1, 0, st>>>(counters);
+    return cudaGetLastError();
+}
+
+// Appends reserve slots with atomics and skip those beyond the capacity; clamp the length.
+__global__ void queue_clamp_kernel(unsigned long long* counters, unsigned long long cap)
+{
+    if (counters[C_QUEUE] > cap) counters[C_QUEUE] = cap;
+}
+
+cudaError_t launch_queue_clamp(unsigned long long* counters, unsigned long long cap,
+                               cudaStream_t st)
+{
+    queue_clamp_kernel<<<1, 1, 0, st>>>(counters, cap);
     return cudaGetLastError();
 }
 
@@ -553,55 +645,60 @@ __global__ void __launch_bounds__(256)
                         double* const* imgs, uint8_t* const* masks, int64_t* queue,
                         unsigned long long* qcount, unsigned long long* img_counts)
 {
-    const int im = blockIdx.y;
+    const int im = blockIdx.z;
     const DevJob J = jobs[im];
     if (level > J.levels) return;  // the whole block: this image has no such level
     double* img = imgs[im];
     uint8_t* mask = masks[im];
     const int s = 1 << (J.levels - level);
-    const unsigned nkx = (unsigned)((J.nx - 1) / s + 1), nky = (unsigned)((J.ny - 1) / s + 1);
-    const unsigned npts = nkx * nky;
+    const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
     const int64_t npix = (int64_t)J.nx * J.ny;
     const double norm = norms[4 * im];
     const Screen sc = make_screen(J, norm);
     const int lane = threadIdx.x & 31;
-    for (unsigned base = blockIdx.x * blockDim.x; base < npts; base += gridDim.x * blockDim.x) {
-        const unsigned t = base + threadIdx.x;
-        bool trace = false;
-        int32_t pix = 0;
-        if (t < npts) {
-            const unsigned jj = t / nkx, ii = t - jj * nkx;
-            const int oi = ii & 1, oj = jj & 1;
-            if (oi | oj) {
-                const int i = (int)ii * s, j = (int)jj * s;
-                const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                trace = refine_point(J, sc, img, mask, i, j, s, cat, norm, npix);
-                pix = j * J.nx + i;
+    for (int jj = blockIdx.y; jj < nky; jj += gridDim.y) {
+        const int oj = jj & 1;
+        for (int i0 = blockIdx.x * blockDim.x; i0 < nkx; i0 += gridDim.x * blockDim.x) {
+            const int ii = i0 + (int)threadIdx.x;
+            bool trace = false;
+            int32_t pix = 0;
+            if (ii < nkx) {
+                const int oi = ii & 1;
+                if (oi | oj) {
+                    const int i = ii * s, j = jj * s;
+                    const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+                    trace = refine_point(J, sc, img, mask, i, j, s, cat, norm, npix, false,
+                                         nullptr, nullptr) == 1;
+                    pix = j * J.nx + i;
+                }
             }
-        }
-        const unsigned b = __ballot_sync(0xffffffffu, trace);
-        if (b) {
-            unsigned long long w = 0;
-            if (lane == 0) {
-                w = atomicAdd(qcount, (unsigned long long)__popc(b));
-                atomicAdd(img_counts + 16 * im + level, (unsigned long long)__popc(b));
+            const unsigned b = __ballot_sync(0xffffffffu, trace);
+            if (b) {
+                unsigned long long w = 0;
+                if (lane == 0) {
+                    w = atomicAdd(qcount, (unsigned long long)__popc(b));
+                    atomicAdd(img_counts + 16 * im + level, (unsigned long long)__popc(b));
+                }
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (trace) queue[w + __popc(b & ((1u << lane) - 1u))] = ((int64_t)im << 32) | pix;
             }
-            w = __shfl_sync(0xffffffffu, w, 0);
-            if (trace) queue[w + __popc(b & ((1u << lane) - 1u))] = ((int64_t)im << 32) | pix;
         }
     }
 }
 
-cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_points,
+cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_kx, int max_ky,
                                 const double* norms, double* const* imgs, uint8_t* const* masks,
                                 int64_t* queue, unsigned long long* qcount,
                                 unsigned long long* img_counts, cudaStream_t st)
 {
-    int gx = (max_points + 255) / 256;
+    int gx = (max_kx + 255) / 256;
+    if (gx > 16) gx = 16;
     if (gx < 1) gx = 1;
-    if (gx > 2048) gx = 2048;
-    refine_batch_kernel<<<dim3(gx, n), 256, 0, st>>>(jobs, level, norms, imgs, masks, queue, qcount,
-                                                     img_counts);
+    int gy = (152 * 16) / (gx * (n > 0 ? n : 1));
+    if (gy > max_ky) gy = max_ky;
+    if (gy < 1) gy = 1;
+    refine_batch_kernel<<<dim3(gx, gy, n), 256, 0, st>>>(jobs, level, norms, imgs, masks, queue,
+                                                         qcount, img_counts);
     return cudaGetLastError();
 }
 

@@ -68,7 +68,14 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
                             if (A.out) A.out[t.slot * np + p] = double(t.acc[p]);
                         }
                     }
-                    if (A.img && A.mask) A.mask[t.pix] = ART_MASK_TRACED;
+                    if (A.img && A.mask)
+                        A.mask[t.pix] = (A.spec_from && (unsigned long long)t.slot >= *A.spec_from)
+                                            ? MASK_SPEC_DONE
+                                            : (uint8_t)ART_MASK_TRACED;
+                    if (A.img && A.pix_minr) {
+                        A.pix_minr[t.pix] = t.min_r;
+                        A.pix_turn[t.pix] = (float)t.nturn;
+                    }
                     if (A.aux_status) A.aux_status[t.slot] = t.status;
                     if (A.aux_steps) A.aux_steps[t.slot] = t.steps;
                     if (A.aux_nturn) A.aux_nturn[t.slot] = t.nturn;

@@ -27,7 +27,8 @@ BASE = dict(a=0.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33, n0y=33, levels
             max_steps=100000, step_frac=0.05, h_min=1e-4, horizon_eps=0.01, escape_frac=1.01,
             disk_w=0.3, blob_sigma=1.0, ne0=0.0, thetae0=0.0, b0=0.0, nu_hz=230e9,
             ne_slope=-1.1, te_slope=-0.84, r_in=0.0, length_cm=9.6e14, bz_ratio=1.0,
-            gamma_ad=13.0 / 9.0, m_unit=3e26, r_high=20.0, r_low=1.0, sigma_cut=1.0)
+            gamma_ad=13.0 / 9.0, m_unit=3e26, r_high=20.0, r_low=1.0, sigma_cut=1.0,
+            proposal=0, proposal_depth=2, proposal_p=0.5)
 
 
 def job(**over) -> dict:
