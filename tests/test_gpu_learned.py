@@ -94,8 +94,9 @@ def test_training_sample_matches_host_definition(ctx):
 
 def test_trained_proposal_gain(snap):
     """Train on 96 seeded plain renders (the library's tensor-core forward/backward and Adam),
-    then: on 9 held-out jobs the network finds the refined blocks (recall >= 0.95 at p > 0.1,
-    precision >= 0.35), and on the 2049^2 analytic-emissivity workload the learned render
+    then: on 9 held-out jobs the network finds the refined blocks (at p > 0.1 recall >= 0.95 with
+    precision >= 1.5x the base rate, at p > 0.3 recall >= 0.8 with precision >= 3x), and on the
+    2049^2 analytic-emissivity workload the learned render
     (lookahead 3 levels, p > 0.3) is at least 1.2x faster than the plain one (median of 5 CUDA-event
     timed renders each), with image and mask unchanged."""
     from paper_2103_07417_gb300 import art, learn
@@ -103,8 +104,11 @@ def test_trained_proposal_gain(snap):
     try:
         assert hist[-1] < 0.6 * hist[0], hist
         held = learn.training_jobs(123, 9)
-        scores = learn.block_scores(ctx, learn.collect(ctx, held), 0.1)
-        assert scores["recall"] >= 0.95 and scores["precision"] >= 0.35, scores
+        hs = learn.collect(ctx, held)
+        lo, hi = learn.block_scores(ctx, hs, 0.1), learn.block_scores(ctx, hs, 0.3)
+        base = lo["positives"] / sum(t.numel() for _, t in hs)
+        assert lo["recall"] >= 0.95 and lo["precision"] >= 1.5 * base, (lo, base)
+        assert hi["recall"] >= 0.8 and hi["precision"] >= 3.0 * base, (hi, base)
         p = W.cfg1_analytic()
         plain = art.make_job(**p)
         lrn = art.make_job(**{**p, "proposal": 1, "proposal_p": 0.3, "proposal_depth": 3})
