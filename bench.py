@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--precision", default="mixed_df", choices=["mixed", "mixed_df", "fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-render measurement")
+    ap.add_argument("--no-mse", action="store_true",
+                    help="skip the time-to-0.1%%-MSE sweep (needs a full FP64 trace as truth)")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip training the block-proposal network and the learned path")
     ap.add_argument("--single", action="store_true",
                     help="one warm-up and one render, nothing else (for profiler captures)")
     return ap.parse_args()
@@ -397,6 +401,74 @@ def main():
                    "geodesic_steps_per_s": bst[0]["steps"] / tb}
         del bimgs, bmasks
 
+    # the learned path: train the block-proposal network on seeded plain renders (the library's
+    # own tensor-core forward/backward and Adam), then render the workload with it
+    learned = None
+    lctx = None
+    if not args.no_learned:
+        from paper_2103_07417_gb300 import learn
+        t0 = time.perf_counter()
+        lctx, hist = learn.trained_context(seed=0, n_jobs=96, epochs=12, device=local,
+                                           snapshot=snap if snap is not None else W.grmhd_snapshot(seed=0))
+        t_train = time.perf_counter() - t0
+        best = None
+        for depth in (2, 3):
+            for thr in (0.2, 0.3):
+                lj = art.make_job(**{**params, "proposal": 1, "proposal_p": thr,
+                                     "proposal_depth": depth})
+                lst = lctx.art_render(lj, img, mask, stats=True)
+                tl = _timed_ctx(lctx, lj, img, mask, flush, 5)
+                cand = dict(depth=depth, threshold=thr, ms_per_step=1000 * tl,
+                            rays_per_s=lst["rays_traced"] / tl,
+                            rays_speculative=lst["rays_speculative"],
+                            rays_spec_used=lst["rays_spec_used"])
+                if best is None or cand["ms_per_step"] < best["ms_per_step"]:
+                    best = cand
+        learned = {"training": {"jobs": 96, "epochs": 12, "seconds": t_train,
+                                "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]},
+                   "best": best,
+                   "gain_vs_plain": (1000 * t_dev / args.steps) / best["ms_per_step"],
+                   "note": "same image and mask as the plain render (the exact criterion decides "
+                           "every point); the lookahead depth and threshold are chosen among "
+                           "{2,3} x {0.2,0.3} by timing"}
+
+    # time to a 0.1 %-MSE image (paper MSE vs the full FP64 trace) for each path: the fastest
+    # tolerance R = R_rel = R_abs meeting it
+    time_to_mse = None
+    if not args.no_mse and not args.gpus > 1:
+        if nx * ny <= (1 << 23):
+            tjob = art.make_job(**{**params, "precision": "fp64", "R_rel": -1.0, "R_abs": -1.0})
+            truth = torch.empty_like(img)
+            ctx.art_render(tjob, truth, mask, stats=False)
+            rlist = (3e-3, 1e-3, 3e-4, 1e-4) if params.get("emission") != "grid" else (0.1, 0.025, 1e-2, 3e-3)
+            time_to_mse = {"target_mse": 1e-3, "truth": "full FP64 trace of the final grid",
+                           "sweep_R": list(rlist), "paths": {}}
+            variants = [("fp64", ctx, {"precision": "fp64"}), ("mixed_df", ctx, {"precision": "mixed_df"})]
+            if lctx is not None:
+                variants.append(("mixed_df+learned", lctx,
+                                 {"precision": "mixed_df", "proposal": 1,
+                                  "proposal_p": learned["best"]["threshold"],
+                                  "proposal_depth": learned["best"]["depth"]}))
+            for name, cx, over in variants:
+                rec, sweep = None, []
+                for R in rlist:
+                    rr = {"R_abs": R} if params.get("emission") == "grid" else {"R_abs": R, "R_rel": R}
+                    vj = art.make_job(**{**params, **over, **rr})
+                    vst = cx.art_render(vj, img, mask, stats=True)
+                    met = cx.art_metrics(truth[0], img[0], mask)
+                    tv = _timed_ctx(cx, vj, img, mask, flush, 3)
+                    sweep.append({"R": R, "mse": met["MSE"], "IF": met["IF"], "seconds": tv,
+                                  "rays": vst["rays_traced"]})
+                    if met["MSE"] <= 1e-3 and (rec is None or tv < rec["seconds"]):
+                        rec = {"seconds": tv, "R": R, "mse": met["MSE"]}
+                time_to_mse["paths"][name] = {"best": rec, "sweep": sweep}
+            del truth
+        else:
+            time_to_mse = {"skipped": "final grid above 2^23 points: the FP64 truth trace is too "
+                                      "long for the default run"}
+    if lctx is not None:
+        lctx.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(params, snap)
@@ -412,13 +484,30 @@ def main():
                            "l2": "flushed (512 MB write) before every step, outside the timed "
                                  "region", "parallelism": f"replicas x{world}"},
                 "geodesic_steps_per_s": steps_per_render * args.steps * world / t_dev,
-                "paths": paths, "batched": batched, "roofline": roofline, "kernels": kernels,
+                "paths": paths, "batched": batched, "learned": learned,
+                "time_to_mse": time_to_mse, "roofline": roofline, "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(stats["kernel_launches"]) * args.steps}
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def _timed_ctx(c, job, img, mask, flush, k):
+    """Median seconds of k renders of `job` on context c (CUDA events on its stream, L2 flushed
+    before each)."""
+    import torch
+    ts = []
+    for _ in range(k):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(c.stream)
+        c.art_render(job, img, mask, stats=False)
+        e1.record(c.stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1) / 1000.0)
+    return float(statistics.median(ts))
 
 
 def ctypes_sizeof_job():
