@@ -73,6 +73,9 @@ def parse():
                     help="skip training the block-proposal network and the learned path")
     ap.add_argument("--single", action="store_true",
                     help="one warm-up and one render, nothing else (for profiler captures)")
+    ap.add_argument("--cnn", action="store_true",
+                    help="one forward and one gradient pass of the block-proposal network on a "
+                         "seeded 1025 x 1025 lattice, nothing else (for profiler captures)")
     return ap.parse_args()
 
 
@@ -249,6 +252,12 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     stats = None
+    if args.cnn:
+        ctx.art_cnn_load(W.cnn_init(0))
+        cnn_measure(ctx, 1025, reps=1)
+        print(json.dumps({"cnn": 1025}))
+        ctx.close()
+        return
     if args.single:
         ctx.art_render(job, img, mask, stats=True)
         st = ctx.art_render(job, img, mask, stats=True)
@@ -432,6 +441,21 @@ def main():
                            "every point); the lookahead depth and threshold are chosen among "
                            "{2,3} x {0.2,0.3} by timing"}
 
+    # the proposal network's tensor-core kernels alone: forward (4 implicit-GEMM convolutions +
+    # head) and forward + backward on a 2049 x 2049 lattice, host-timed (each call synchronises)
+    cnn = None
+    if lctx is not None:
+        nlat = 2049
+        t_fw, t_fb = cnn_measure(lctx, nlat)
+        fl = cnn_flops(nlat, nlat)
+        peak = 1941.4  # measured cuBLAS BF16 burst TFLOP/s of the GB300s
+        cnn = {"lattice": f"{nlat}x{nlat}", "forward_ms": 1000 * t_fw,
+               "forward_backward_ms": 1000 * t_fb,
+               "roofline": {"bound": "tensor", "achieved": fl / t_fw / 1e12, "peak": peak,
+                            "unit": "TFLOP/s", "frac": fl / t_fw / 1e12 / peak,
+                            "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
+                            "flops_per_forward": fl}}
+
     # time to a 0.1 %-MSE image (paper MSE vs the full FP64 trace) for each path: the fastest
     # tolerance R = R_rel = R_abs meeting it
     time_to_mse = None
@@ -484,7 +508,7 @@ def main():
                            "l2": "flushed (512 MB write) before every step, outside the timed "
                                  "region", "parallelism": f"replicas x{world}"},
                 "geodesic_steps_per_s": steps_per_render * args.steps * world / t_dev,
-                "paths": paths, "batched": batched, "learned": learned,
+                "paths": paths, "batched": batched, "learned": learned, "cnn": cnn,
                 "time_to_mse": time_to_mse, "roofline": roofline, "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(stats["kernel_launches"]) * args.steps}
@@ -508,6 +532,39 @@ def _timed_ctx(c, job, img, mask, flush, k):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1) / 1000.0)
     return float(statistics.median(ts))
+
+
+def cnn_flops(H: int, W: int) -> float:
+    """Algorithmic FLOPs of one forward pass of the proposal network on an H x W lattice (2 per
+    multiply-add): 3x3 convolutions 3 -> 32 at H x W, 32 -> 32 at H x W, H/2 x W/2 and H/4 x W/4,
+    and the 32 -> 1 head."""
+    o = lambda n: (n - 1) // 2 + 1
+    H2, W2, H4, W4 = o(H), o(W), o(o(H)), o(o(W))
+    return 2.0 * (H * W * 32 * 27 + H * W * 32 * 288 + H2 * W2 * 32 * 288 + H4 * W4 * 32 * 288
+                  + H4 * W4 * 32)
+
+
+def cnn_measure(ctx, n: int, reps: int = 5):
+    """Forward and forward+backward times of the proposal network on a seeded n x n lattice."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(0)
+    feat = torch.from_numpy(np.stack([rng.normal(0, 1, (n, n)), rng.uniform(0, 2, (n, n)),
+                                      rng.integers(0, 3, (n, n)).astype(float)], -1)
+                            .astype(np.float32)).cuda()
+    H4 = ((n - 1) // 2) // 2 + 1
+    tgt = torch.from_numpy((rng.uniform(size=(H4, H4)) < 0.3).astype(np.float32)).cuda()
+    ctx.art_cnn_forward(feat)
+    ctx.art_cnn_grad(feat, tgt)
+    fw, fb = [], []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ctx.art_cnn_forward(feat)      # synchronises
+        fw.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        ctx.art_cnn_grad(feat, tgt)
+        fb.append(time.perf_counter() - t0)
+    return statistics.median(fw), statistics.median(fb)
 
 
 def ctypes_sizeof_job():
