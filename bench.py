@@ -345,6 +345,16 @@ def main():
         paths[prec] = {"rays_per_s": stp["rays_traced"] * kp / tp,
                        "geodesic_steps_per_s": stp["steps"] * kp / tp,
                        "ms_per_step": 1000 * tp / kp, "rays_high_precision": stp["rays_fp64"]}
+    if params.get("crit_band", 0.0) > 0.0:
+        # the same precision without the near-critical band speculation (same image)
+        jnb = art.make_job(**{**params, "crit_band": 0.0})
+        stp = ctx.art_render(jnb, img, mask, stats=True)
+        kp = max(3, args.steps // 5)
+        tp = timed(kp, jnb)
+        paths[args.precision + "_no_band"] = {
+            "rays_per_s": stp["rays_traced"] * kp / tp,
+            "geodesic_steps_per_s": stp["steps"] * kp / tp, "ms_per_step": 1000 * tp / kp,
+            "rays_high_precision": stp["rays_fp64"]}
     ctx.art_render(job, img, mask, stats=False)
     paths[args.precision] = {"rays_per_s": value / world,
                              "geodesic_steps_per_s": steps_per_render * args.steps / t_dev,
@@ -420,26 +430,32 @@ def main():
         lctx, hist = learn.trained_context(seed=0, n_jobs=96, epochs=12, device=local,
                                            snapshot=snap if snap is not None else W.grmhd_snapshot(seed=0))
         t_train = time.perf_counter() - t0
-        best = None
-        for depth in (2, 3):
-            for thr in (0.2, 0.3):
-                lj = art.make_job(**{**params, "proposal": 1, "proposal_p": thr,
-                                     "proposal_depth": depth})
-                lst = lctx.art_render(lj, img, mask, stats=True)
-                tl = _timed_ctx(lctx, lj, img, mask, flush, 5)
-                cand = dict(depth=depth, threshold=thr, ms_per_step=1000 * tl,
-                            rays_per_s=lst["rays_traced"] / tl,
-                            rays_speculative=lst["rays_speculative"],
-                            rays_spec_used=lst["rays_spec_used"])
-                if best is None or cand["ms_per_step"] < best["ms_per_step"]:
-                    best = cand
+        best, best_nb = None, None
+        band0 = params.get("crit_band", 0.0)
+        for band in sorted({0.0, band0}):
+            for depth in (2, 3):
+                for thr in (0.2, 0.3):
+                    lj = art.make_job(**{**params, "proposal": 1, "proposal_p": thr,
+                                         "proposal_depth": depth, "crit_band": band})
+                    lst = lctx.art_render(lj, img, mask, stats=True)
+                    tl = _timed_ctx(lctx, lj, img, mask, flush, 5)
+                    cand = dict(depth=depth, threshold=thr, crit_band=band, ms_per_step=1000 * tl,
+                                rays_per_s=lst["rays_traced"] / tl,
+                                rays_speculative=lst["rays_speculative"],
+                                rays_spec_used=lst["rays_spec_used"])
+                    if best is None or cand["ms_per_step"] < best["ms_per_step"]:
+                        best = cand
+                    if band == 0.0 and (best_nb is None or cand["ms_per_step"] < best_nb["ms_per_step"]):
+                        best_nb = cand
+        plain_nb = paths.get(args.precision + "_no_band", paths[args.precision])["ms_per_step"]
         learned = {"training": {"jobs": 96, "epochs": 12, "seconds": t_train,
                                 "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]},
-                   "best": best,
+                   "best": best, "best_without_band": best_nb,
                    "gain_vs_plain": (1000 * t_dev / args.steps) / best["ms_per_step"],
+                   "gain_vs_plain_both_without_band": plain_nb / best_nb["ms_per_step"],
                    "note": "same image and mask as the plain render (the exact criterion decides "
-                           "every point); the lookahead depth and threshold are chosen among "
-                           "{2,3} x {0.2,0.3} by timing"}
+                           "every point); lookahead depth, threshold and band chosen among "
+                           "{2,3} x {0.2,0.3} x {0, default} by timing"}
 
     # the proposal network's tensor-core kernels alone: forward (4 implicit-GEMM convolutions +
     # head) and forward + backward on a 2049 x 2049 lattice, host-timed (each call synchronises)
@@ -467,12 +483,15 @@ def main():
             rlist = (3e-3, 1e-3, 3e-4, 1e-4) if params.get("emission") != "grid" else (0.1, 0.025, 1e-2, 3e-3)
             time_to_mse = {"target_mse": 1e-3, "truth": "full FP64 trace of the final grid",
                            "sweep_R": list(rlist), "paths": {}}
-            variants = [("fp64", ctx, {"precision": "fp64"}), ("mixed_df", ctx, {"precision": "mixed_df"})]
+            variants = [("fp64", ctx, {"precision": "fp64", "crit_band": 0.0}),
+                        ("mixed_df_no_band", ctx, {"precision": "mixed_df", "crit_band": 0.0}),
+                        ("mixed_df", ctx, {"precision": "mixed_df"})]
             if lctx is not None:
                 variants.append(("mixed_df+learned", lctx,
                                  {"precision": "mixed_df", "proposal": 1,
                                   "proposal_p": learned["best"]["threshold"],
-                                  "proposal_depth": learned["best"]["depth"]}))
+                                  "proposal_depth": learned["best"]["depth"],
+                                  "crit_band": learned["best"]["crit_band"]}))
             for name, cx, over in variants:
                 rec, sweep = None, []
                 for R in rlist:

@@ -106,6 +106,13 @@ typedef struct art_job {
      * when mask_dev is NULL. */
     int32_t proposal, proposal_depth;
     double proposal_p;
+    /* Near-critical band (not in the paper; 0 = off, else 0 < crit_band < 1): every pixel of
+     * levels 1..N whose camera ray has constants of motion (lambda, eta) within crit_band of the
+     * Kerr critical curve, d = |eta - eta_c(lambda)|/27 (Bardeen 1973), is traced speculatively
+     * with the base level, so the high-precision re-traces of the photon-ring rays of all levels
+     * share one pass.  The exact criterion still decides every point: image and mask equal those
+     * of the render without it.  Not with a truth image (ART_ERR_ARG). */
+    double crit_band;
 } art_job;
 
 /* Statistics of one render (host struct, filled on return). */

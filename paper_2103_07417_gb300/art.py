@@ -47,7 +47,7 @@ class Job(ctypes.Structure):
         ("bz_ratio", ctypes.c_double), ("gamma_ad", ctypes.c_double), ("m_unit", ctypes.c_double),
         ("r_high", ctypes.c_double), ("r_low", ctypes.c_double), ("sigma_cut", ctypes.c_double),
         ("proposal", ctypes.c_int32), ("proposal_depth", ctypes.c_int32),
-        ("proposal_p", ctypes.c_double),
+        ("proposal_p", ctypes.c_double), ("crit_band", ctypes.c_double),
     ]
 
 
@@ -75,7 +75,7 @@ class RayAux(ctypes.Structure):
 
 _JOB_DEFAULTS = dict(fp64_sweep=3.0 * 3.141592653589793, gamma_ad=13.0 / 9.0, m_unit=3e26,
                      r_high=20.0, r_low=1.0, sigma_cut=1.0, proposal=0, proposal_depth=2,
-                     proposal_p=0.5)
+                     proposal_p=0.5, crit_band=0.0)
 
 
 def make_job(**params) -> Job:

@@ -1,0 +1,125 @@
+// band.cu -- speculation of the near-critical band: the pixels whose rays pass close to the
+// photon shell, found from the Kerr critical curve in closed form, are traced with the base level.
+//
+// A ray's constants of motion lambda = L_z/E and eta = Q/E^2 (Carter 1968) follow from its initial
+// covariant momentum at the camera.  The rays that orbit the hole before escaping are those with
+// (lambda, eta) close to the critical curve of the spherical photon orbits of radius r in
+// [r_pro, r_ret] (Bardeen 1973):
+//   lambda_c(r) = (r^2 (3 - r) - a^2 (r + 1)) / (a (r - 1)),
+//   eta_c(r)    = r^3 (4 a^2 - r (r - 3)^2) / (a^2 (r - 1)^2),
+//   r_pro, r_ret = 2 (1 + cos(2/3 arccos(-+|a|))),
+// (the circle eta + lambda^2 = 27 for a = 0).  The distance used here is
+// d = |eta - eta_c(lambda)| / 27 (eta_c(lambda) by bisection on r; rays whose lambda lies outside
+// the curve's range are far from it).  These are exactly the rays the FP32 pass hands to the
+// double-float re-trace; tracing every unset pixel of the finer levels with d < band in the same
+// launch as the base level puts all their re-traces into one double-float pass, instead of one
+// latency-bound pass per level.  The exact criterion still decides every point (a speculative ray
+// it does not ask for is overwritten by its interpolant), so images do not change; the band is a
+// scheduling hint evaluated in FP32.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.cuh"
+
+namespace art {
+
+__device__ __forceinline__ float lam_c(float a, float r)
+{
+    return (r * r * (3.f - r) - a * a * (r + 1.f)) / (a * (r - 1.f));
+}
+
+__device__ __forceinline__ float eta_c(float a, float r)
+{
+    const float rm = r - 3.f, r1 = r - 1.f;
+    return r * r * r * (4.f * a * a - r * rm * rm) / (a * a * r1 * r1);
+}
+
+// Distance of (lambda, eta) from the critical curve of spin a (see above).
+__device__ __forceinline__ float crit_distance(float a, float lam, float eta)
+{
+    if (fabsf(a) < 1e-3f) return fabsf(eta + lam * lam - 27.f) * (1.f / 27.f);
+    const float aa = fabsf(a);
+    float lo = 2.f * (1.f + cosf(2.f / 3.f * acosf(-aa)));  // prograde photon orbit
+    float hi = 2.f * (1.f + cosf(2.f / 3.f * acosf(aa)));   // retrograde photon orbit
+    float flo = lam_c(a, lo) - lam, fhi = lam_c(a, hi) - lam;
+    if (flo * fhi > 0.f) return 1e30f;  // lambda outside the curve's range
+    for (int it = 0; it < 40; ++it) {
+        const float mid = 0.5f * (lo + hi), fm = lam_c(a, mid) - lam;
+        if ((fm < 0.f) == (flo < 0.f)) {
+            lo = mid;
+            flo = fm;
+        } else {
+            hi = mid;
+        }
+    }
+    return fabsf(eta - eta_c(a, 0.5f * (lo + hi))) * (1.f / 27.f);
+}
+
+// Every pixel off the base lattice whose mask is unset and whose camera ray lies within `band` of
+// the critical curve is queued for a speculative trace and marked pending (grid-stride over the
+// final grid; slots beyond `cap` are skipped).
+__global__ void __launch_bounds__(256)
+    band_propose_kernel(DevJob J, const Camera* cam, float band, uint8_t* mask, int32_t* queue,
+                        unsigned long long* counters, unsigned long long cap)
+{
+    __shared__ float E[4][4], x0[3];
+    if (threadIdx.x < 16) E[threadIdx.x / 4][threadIdx.x % 4] = (float)cam->E[threadIdx.x / 4][threadIdx.x % 4];
+    if (threadIdx.x < 3) x0[threadIdx.x] = (float)cam->x0[threadIdx.x];
+    __syncthreads();
+    const int S0 = 1 << J.levels;
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    const float a = (float)J.a, ro = (float)J.r_obs, pix = (float)J.pix;
+    const float r0 = sqrtf(0.5f * ((x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2] - a * a) +
+                                   sqrtf((x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2] - a * a) *
+                                             (x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2] - a * a) +
+                                         4.f * a * a * x0[2] * x0[2])));
+    const float ct = x0[2] / r0, st = sqrtf(fmaxf(1.f - ct * ct, 1e-12f));
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npix;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = base + threadIdx.x;
+        bool want = false;
+        if (p < npix) {
+            const int i = (int)(p % J.nx), j = (int)(p / J.nx);
+            if ((i % S0 != 0 || j % S0 != 0) && mask[p] == ART_MASK_UNSET) {
+                const float al = (i - 0.5f * (J.nx - 1)) * pix, be = (j - 0.5f * (J.ny - 1)) * pix;
+                const float sc = rsqrtf(1.f + (al * al + be * be) / (ro * ro));
+                float k[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    k[m] = -E[0][m] + sc * (-E[1][m] + (al / ro) * E[3][m] + (be / ro) * E[2][m]);
+                const float Een = k[0];
+                const float L = -(x0[0] * k[2] - x0[1] * k[1]);
+                const float pth = -((x0[0] * k[1] + x0[1] * k[2]) * ct / st - r0 * st * k[3]);
+                const float Q = pth * pth + ct * ct * (-a * a * Een * Een + L * L / (st * st));
+                const float lam = L / Een, eta = Q / (Een * Een);
+                want = crit_distance(a, lam, eta) < band;
+            }
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, want);
+        if (!b) continue;
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(counters + C_QUEUE, (unsigned long long)__popc(b));
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (want) {
+            const unsigned long long slot = w + __popc(b & ((1u << lane) - 1u));
+            if (slot < cap) {
+                queue[slot] = (int32_t)p;
+                mask[p] = MASK_SPEC_PENDING;
+                atomicAdd(counters + C_SPEC, 1ull);
+            }
+        }
+    }
+}
+
+cudaError_t launch_band_propose(const DevJob& J, const Camera* cam, double band, uint8_t* mask,
+                                int32_t* queue, unsigned long long* counters,
+                                unsigned long long cap, int num_sms, cudaStream_t st)
+{
+    band_propose_kernel<<<num_sms * 8, 256, 0, st>>>(J, cam, (float)band, mask, queue, counters, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace art

@@ -539,10 +539,13 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
     if (learned && (!c->cnn || truth_dev || !(job->proposal_p >= 0.0) || !(job->proposal_p <= 1.0) ||
                     job->proposal_depth < 1))
         return ART_ERR_ARG;
+    const bool band = job->crit_band > 0.0;
+    if (band && (truth_dev || !(job->crit_band < 1.0))) return ART_ERR_ARG;
+    const bool spec_any = learned || band;
     CK(cudaSetDevice(c->device));
     const int64_t cap = max_level_rays(J);
     // the learned path appends speculative rays of later levels to a level's queue
-    const int64_t qcap = learned ? cap + std::min<int64_t>((int64_t)J.nx * J.ny, 4 * cap) : cap;
+    const int64_t qcap = spec_any ? cap + std::min<int64_t>((int64_t)J.nx * J.ny, 4 * cap) : cap;
     if ((rc = ensure_fixed(c)) || (rc = ensure_queue(c, qcap))) return rc;
     cudaStream_t st = c->stream;
     const int64_t npix = (int64_t)J.nx * J.ny;
@@ -557,15 +560,17 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
         c->aux_npix = 0;
     }
     uint8_t* mask = mask_dev;
-    if (learned) {
+    if (spec_any) {
         if (!mask) {
             if ((rc = grow(c, c->smask, c->smask_cap, npix))) return rc;
             mask = c->smask;
         }
+        CK(cudaMemsetAsync(mask, 0, npix, st));  // speculation claims points whose mask is unset
+    }
+    if (learned) {
         int64_t pc = 1;
         for (int lv = 0; lv + 2 <= J.levels; ++lv) pc = std::max(pc, cnn_head_cells(J, lv));
         if ((rc = grow(c, c->prob, c->prob_cap, pc))) return rc;
-        CK(cudaMemsetAsync(mask, 0, npix, st));  // speculation claims points whose mask is unset
     }
     c->launches = 0;
     CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * C_COUNT, st));
@@ -582,12 +587,22 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
     for (int level = 0; level <= J.levels; ++level) {
         c->prof_level = level;
         bool spec = false;
+        if (level == 0 && band && J.levels > 0) {
+            // near-critical band of every finer level, traced with the base level
+            CK(launch_spec_mark(c->counters, st));
+            k = prof_begin(c);
+            CK(launch_band_propose(J, c->cam, job->crit_band, mask, c->queue, c->counters,
+                                   (unsigned long long)qcap, c->num_sms, st));
+            prof_end(c, k, ART_K_PROPOSE, -1);
+            CK(launch_queue_clamp(c->counters, (unsigned long long)qcap, st));
+            spec = true;
+        }
         if (level > 0) {
             const int s = 1 << (J.levels - level);
             CK(cudaMemsetAsync(c->counters + C_QUEUE, 0, sizeof(unsigned long long), st));
             k = prof_begin(c);
             CK(launch_refine(J, level, c->norm3, img_dev, mask, c->queue, c->counters + C_QUEUE, st,
-                             aminr, aturn, learned ? c->counters : nullptr));
+                             aminr, aturn, spec_any ? c->counters : nullptr));
             prof_end(c, k, ART_K_REFINE, (int64_t)((J.nx - 1) / s + 1) * ((J.ny - 1) / s + 1));
             CK(launch_level_count(c->counters, level, st));
             if (learned && level + 1 <= J.levels && (level - 1) % job->proposal_depth == 0) {

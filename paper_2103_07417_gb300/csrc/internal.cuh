@@ -147,5 +147,9 @@ cudaError_t cnn_features_f32(const DevJob& J, int level, const double* img, cons
 cudaError_t cnn_targets(const DevJob& J, int level, const uint8_t* mask, float* target,
                         cudaStream_t st);
 int64_t cnn_head_cells(const DevJob& J, int level);
+// band.cu
+cudaError_t launch_band_propose(const DevJob& J, const Camera* cam, double band, uint8_t* mask,
+                                int32_t* queue, unsigned long long* counters,
+                                unsigned long long cap, int num_sms, cudaStream_t st);
 
 }  // namespace art

@@ -28,10 +28,11 @@ def ctx(snap):
 
 
 CASES = [
-    ("cfg2", W.cfg2(n0x=33, n0y=33, levels=4, fov=60.0)),
-    ("cfg1_unpolarized", W.cfg1(n0x=17, n0y=17, levels=4, stokes=1)),
-    ("cfg1_polarized_ragged", W.cfg1(n0x=17, n0y=13, levels=3)),
+    ("cfg2", W.cfg2(n0x=33, n0y=33, levels=4, fov=60.0, crit_band=0.0)),
+    ("cfg1_unpolarized", W.cfg1(n0x=17, n0y=17, levels=4, stokes=1, crit_band=0.0)),
+    ("cfg1_polarized_ragged", W.cfg1(n0x=17, n0y=13, levels=3, crit_band=0.0)),
     ("cfg0_fp64", W.cfg0(precision="fp64", n0x=17, n0y=17, levels=3)),
+    ("cfg1_with_band", W.cfg1(n0x=17, n0y=17, levels=4, stokes=1)),
 ]
 
 
@@ -50,7 +51,7 @@ def test_learned_render_equals_plain(ctx, name, params, thr, depth):
     assert st1["rays_spec_used"] <= st1["rays_speculative"]
     if thr == 0.0:
         assert st1["rays_speculative"] > 0 and st1["rays_spec_used"] > 0
-    if thr == 1.0:
+    if thr == 1.0 and params.get("crit_band", 0.0) == 0.0:
         assert st1["rays_speculative"] == 0
     assert int(((mask1 == 1) | (mask1 == 2)).sum()) == mask1.numel()
 
@@ -98,7 +99,8 @@ def test_trained_proposal_gain(snap):
     precision >= 1.5x the base rate, at p > 0.3 recall >= 0.8 with precision >= 3x), and on the
     2049^2 analytic-emissivity workload the learned render
     (lookahead 3 levels, p > 0.3) is at least 1.2x faster than the plain one (median of 5 CUDA-event
-    timed renders each), with image and mask unchanged."""
+    timed renders each), with image and mask unchanged.  Both renders leave the near-critical band
+    speculation off, so the gain is the network's own."""
     from paper_2103_07417_gb300 import art, learn
     ctx, hist = learn.trained_context(seed=0, n_jobs=96, epochs=12, snapshot=snap)
     try:
@@ -109,7 +111,7 @@ def test_trained_proposal_gain(snap):
         base = lo["positives"] / sum(t.numel() for _, t in hs)
         assert lo["recall"] >= 0.95 and lo["precision"] >= 1.5 * base, (lo, base)
         assert hi["recall"] >= 0.8 and hi["precision"] >= 3.0 * base, (hi, base)
-        p = W.cfg1_analytic()
+        p = W.cfg1_analytic(crit_band=0.0)
         plain = art.make_job(**p)
         lrn = art.make_job(**{**p, "proposal": 1, "proposal_p": 0.3, "proposal_depth": 3})
         img0, mask0, st0 = ctx.render(plain)
