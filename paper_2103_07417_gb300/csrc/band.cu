@@ -83,8 +83,14 @@ __global__ void __launch_bounds__(256)
         bool want = false;
         if (p < npix) {
             const int i = (int)(p % J.nx), j = (int)(p / J.nx);
-            if ((i % S0 != 0 || j % S0 != 0) && mask[p] == ART_MASK_UNSET) {
-                const float al = (i - 0.5f * (J.nx - 1)) * pix, be = (j - 0.5f * (J.ny - 1)) * pix;
+            const float al = (i - 0.5f * (J.nx - 1)) * pix, be = (j - 0.5f * (J.ny - 1)) * pix;
+            // the critical curve of every spin and inclination lies at impact parameters between
+            // 2 M and 7 M (prograde and retrograde photon orbits of an extremal hole); the
+            // pinhole's screen radius approximates the impact parameter, so screen radii outside
+            // (0.5 M, 20 M) are rejected before the bisection
+            const float b2 = al * al + be * be;
+            if (b2 > 0.25f && b2 < 400.f && (i % S0 != 0 || j % S0 != 0) &&
+                mask[p] == ART_MASK_UNSET) {
                 const float sc = rsqrtf(1.f + (al * al + be * be) / (ro * ro));
                 float k[4];
 #pragma unroll
