@@ -426,12 +426,28 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
     for (int c = 0; c < J.planes; ++c) {
         const double* pl = img + c * npix;
         double v;
-        if (nearest)
+        if (nearest) {
             v = __ldg(pl + p1);
-        else if (cat == 4)
-            v = scale_pow2(((__ldg(pl + p1) + __ldg(pl + p2)) + __ldg(pl + p3)) + __ldg(pl + p4), 2);
-        else
-            v = scale_pow2(__ldg(pl + p1) + __ldg(pl + p2), 1);
+        } else if (cat == 4) {
+            const double v1 = __ldg(pl + p1), v2 = __ldg(pl + p2), v3 = __ldg(pl + p3),
+                         v4 = __ldg(pl + p4);
+            const long long b1 = __double_as_longlong(v1);
+            // equal parents (the dark background): ((v + v) + v) + v = 4 v and 4 v / 4 = v exactly
+            // (|v| < 2^1021: no overflow; NaN stays NaN); compared on the bits, which spares the
+            // FP64 pipe
+            if (b1 == __double_as_longlong(v2) && b1 == __double_as_longlong(v3) &&
+                b1 == __double_as_longlong(v4) && ((b1 >> 52) & 0x7ff) < 0x7fc)
+                v = v1;
+            else
+                v = scale_pow2(((v1 + v2) + v3) + v4, 2);
+        } else {
+            const double v1 = __ldg(pl + p1), v2 = __ldg(pl + p2);
+            const long long b1 = __double_as_longlong(v1);
+            if (b1 == __double_as_longlong(v2) && ((b1 >> 52) & 0x7ff) < 0x7fc)
+                v = v1;  // (v + v) / 2 = v exactly
+            else
+                v = scale_pow2(v1 + v2, 1);
+        }
         img[c * npix + pix] = v;
     }
     if (mask) mask[pix] = ART_MASK_INTERP;
