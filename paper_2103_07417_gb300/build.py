@@ -20,8 +20,11 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 # The tracer's FP32 path uses the approximate single-precision divide and square root (the
 # double-float arithmetic calls the round-to-nearest intrinsics explicitly, FP64 is unaffected).
-PER_FILE = {"trace.cu": ["-prec-div=false", "-prec-sqrt=false"],
-            "trace_batch.cu": ["-prec-div=false", "-prec-sqrt=false"]}
+# The tracer is compiled without automatic multiply-add contraction: its fused multiply-adds are
+# written out, so that every kernel form that inlines a step rounds it the same way.
+_FAST_F32 = ["-prec-div=false", "-prec-sqrt=false", "-fmad=false"]
+PER_FILE = {"trace.cu": _FAST_F32, "trace_batch.cu": _FAST_F32, "trace_grid.cu": _FAST_F32,
+            "trace_grid_batch.cu": _FAST_F32}
 
 
 def _nvcc() -> str:

@@ -485,7 +485,7 @@ extern "C" int art_trace_pixels(art_ctx* c, const art_job* job, const int32_t* p
     prof_end(c, k, ART_K_OTHER, 1);
     if ((rc = trace_queue(c, job, J, c->counters + C_QUEUE, nullptr, nullptr, out_dev, aux))) return rc;
     if ((rc = read_counters(c))) return rc;
-    if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
+    if (c->pinned[C_BADIDX] || c->pinned[C_SYNCERR]) return ART_ERR_DEVICE;
     return ART_OK;
 }
 
@@ -652,7 +652,7 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
         stats->kernel_launches = c->launches;
         stats->rays_speculative = (int64_t)c->pinned[C_SPEC];
         stats->rays_spec_used = (int64_t)c->pinned[C_SPECUSED];
-        if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
+        if (c->pinned[C_BADIDX] || c->pinned[C_SYNCERR]) return ART_ERR_DEVICE;
     }
     return ART_OK;
 }
@@ -958,7 +958,7 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
             o.rays_nan = (int64_t)c->pinned[C_NAN];
             o.kernel_launches = c->launches;
         }
-        if (c->pinned[C_BADIDX]) return ART_ERR_DEVICE;
+        if (c->pinned[C_BADIDX] || c->pinned[C_SYNCERR]) return ART_ERR_DEVICE;
     }
     return ART_OK;
 }

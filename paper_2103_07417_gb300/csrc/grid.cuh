@@ -55,10 +55,10 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     const int n1 = S.g_n1, n2 = S.g_n2, n3 = S.g_n3;
     int i0, j0;
     Q w1, w2;
-    grid_axis_clamped<Q>((lr - Q(S.g_x1min)) * Q(S.g_inv_dx1) - Q(0.5), n1, i0, w1);
-    grid_axis_clamped<Q>(th * Q(S.g_inv_dth) - Q(0.5), n2, j0, w2);
+    grid_axis_clamped<Q>(fmad(lr - Q(S.g_x1min), Q(S.g_inv_dx1), Q(-0.5)), n1, i0, w1);
+    grid_axis_clamped<Q>(fmad(th, Q(S.g_inv_dth), Q(-0.5)), n2, j0, w2);
     const int i1 = n1 > 1 ? i0 + 1 : i0, j1 = n2 > 1 ? j0 + 1 : j0;
-    Q f3 = ph * Q(S.g_inv_dph) - Q(0.5);
+    Q f3 = fmad(ph, Q(S.g_inv_dph), Q(-0.5));
     Q fl = floor(f3);
     Q w3 = f3 - fl;
     int k0 = int(fl);
@@ -74,14 +74,14 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
                      ((c & 4) ? w3 : Q(1) - w3);
         const float4* cell = S.grid + 2 * (((int64_t)kk * n2 + jj) * n1 + ii);
         const float4 v0 = __ldg(cell), v1 = __ldg(cell + 1);
-        P[0] += wt * Q(v0.x);
-        P[1] += wt * Q(v0.y);
-        P[2] += wt * Q(v0.z);
-        P[3] += wt * Q(v0.w);
-        P[4] += wt * Q(v1.x);
-        P[5] += wt * Q(v1.y);
-        P[6] += wt * Q(v1.z);
-        P[7] += wt * Q(v1.w);
+        P[0] = fmad(wt, Q(v0.x), P[0]);
+        P[1] = fmad(wt, Q(v0.y), P[1]);
+        P[2] = fmad(wt, Q(v0.z), P[2]);
+        P[3] = fmad(wt, Q(v0.w), P[3]);
+        P[4] = fmad(wt, Q(v1.x), P[4]);
+        P[5] = fmad(wt, Q(v1.y), P[5]);
+        P[6] = fmad(wt, Q(v1.z), P[6]);
+        P[7] = fmad(wt, Q(v1.w), P[7]);
     }
     const Q rho = P[0], ug = P[1];
     if (!(rho > Q(0)) || !(ug > Q(0))) return;
@@ -89,39 +89,39 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     Q sp, cp;
     sincos(ph, &sp, &cp);
     const Q st = sqrt(Q(1) - ct * ct);
-    const Q Jm[3][3] = {{st * cp, ct * (r * cp + a * sp), -s.y},
-                        {st * sp, ct * (r * sp - a * cp), s.x},
+    const Q Jm[3][3] = {{st * cp, ct * fmad(r, cp, a * sp), -s.y},
+                        {st * sp, ct * fmad(r, sp, -(a * cp)), s.x},
                         {ct, -r * st, Q(0)}};
     Q u[4], B[4];
     u[0] = B[0] = Q(0);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        u[1 + i] = Jm[i][0] * P[2] + Jm[i][1] * P[3] + Jm[i][2] * P[4];
-        B[1 + i] = Jm[i][0] * P[5] + Jm[i][1] * P[6] + Jm[i][2] * P[7];
+        u[1 + i] = fmad(Jm[i][2], P[4], fmad(Jm[i][1], P[3], Jm[i][0] * P[2]));
+        B[1 + i] = fmad(Jm[i][2], P[7], fmad(Jm[i][1], P[6], Jm[i][0] * P[5]));
     }
     const KSPoint<Q> G = ks_point<Q>(s.x, s.y, s.z, r, a, a2);
-    const Q Lu = G.Lx * u[1] + G.Ly * u[2] + G.Lz * u[3];
-    const Q LB = G.Lx * B[1] + G.Ly * B[2] + G.Lz * B[3];
-    const Q uu = u[1] * u[1] + u[2] * u[2] + u[3] * u[3];
-    const Q qn = Q(1) + uu + G.F * Lu * Lu;
+    const Q Lu = fmad(G.Lz, u[3], fmad(G.Ly, u[2], G.Lx * u[1]));
+    const Q LB = fmad(G.Lz, B[3], fmad(G.Ly, B[2], G.Lx * B[1]));
+    const Q uu = fmad(u[3], u[3], fmad(u[2], u[2], u[1] * u[1]));
+    const Q qn = fmad(G.F * Lu, Lu, Q(1) + uu);
     const Q pn = -G.F * Lu;
-    const Q D = pn * pn - (G.F - Q(1)) * qn;
+    const Q D = fmad(pn, pn, -((G.F - Q(1)) * qn));
     if (!(D >= Q(0))) return;
     const Q den = sqrt(D) - pn;
     if (!(den > Q(0))) return;
     u[0] = qn / den;
-    const Q Bu = B[1] * u[1] + B[2] * u[2] + B[3] * u[3];
+    const Q Bu = fmad(B[3], u[3], fmad(B[2], u[2], B[1] * u[1]));
     Q b[4];
-    b[0] = Bu + G.F * LB * (Lu - u[0]);
+    b[0] = fmad(G.F * LB, Lu - u[0], Bu);
     const Q iut = Q(1) / u[0];
 #pragma unroll
-    for (int i = 1; i < 4; ++i) b[i] = (B[i] + b[0] * u[i]) * iut;
+    for (int i = 1; i < 4; ++i) b[i] = fmad(b[0], u[i], B[i]) * iut;
     const Q b2 = G.dot(b, b);
     if (!(b2 > Q(0))) return;
     if (b2 > Q(S.g_sigma_cut) * rho) return;
     const Q pg = Q(S.g_gm1) * ug, pm = Q(0.5) * b2;
     const Q pg2 = pg * pg, pm2 = pm * pm;
-    const Q trat = (Q(S.g_r_high) * pg2 + Q(S.g_r_low) * pm2) / (pg2 + pm2);
+    const Q trat = fmad(Q(S.g_r_high), pg2, Q(S.g_r_low) * pm2) / (pg2 + pm2);
     const Q Th = Q(S.g_th_unit) * ug / (rho * (Q(1) + trat));
     const Q ne = Q(S.g_ne_unit) * rho;
     const Q bm = sqrt(b2);
@@ -129,7 +129,7 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     const Q ib = Q(1) / bm;
 #pragma unroll
     for (int m = 0; m < 4; ++m) b[m] *= ib;
-    const Q nu = kt * u[0] + s.kx * u[1] + s.ky * u[2] + s.kz * u[3];
+    const Q nu = fmad(s.kz, u[3], fmad(s.ky, u[2], fmad(s.kx, u[1], kt * u[0])));
     if (!(nu > Q(0))) return;
     synch_coeffs<Q>(G, s, kt, u, b, nu, ne, Th, Bm, f, S, J4, K7);
 }

@@ -24,6 +24,7 @@ enum Counter {
     C_SPECFROM = 9,  // learned path: first queue slot of the speculative rays of this level
     C_SPEC = 10,     // learned path: rays queued speculatively (all levels)
     C_SPECUSED = 11, // learned path: speculative rays the exact criterion asked for
+    C_SYNCERR = 12,  // warp-pair trace kernels: a hand-over wait that ran out of time
     C_LEVEL0 = 16,   // C_LEVEL0 + k: rays of level k (16 slots)
     C_COUNT = 32
 };

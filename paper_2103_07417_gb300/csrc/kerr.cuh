@@ -19,6 +19,7 @@
 //   dx_i/dlambda = k_i + f lk L_i,
 //   dk_i/dlambda = (B lk^2/2 - f lk A) dr/dx_i - f lk T_i - delta_iz f a^2 z lk^2 / Q.
 #pragma once
+#include <cmath>
 #include <cstdint>
 
 #if defined(__CUDACC__)
@@ -33,6 +34,26 @@ namespace art {
 inline double rsqrt(double v) { return 1.0 / sqrt(v); }
 inline float rsqrt(float v) { return 1.0f / sqrt(v); }
 #endif
+
+// Fused multiply-add a b + c, written out.  The trace kernels are compiled without automatic
+// contraction, so that a step rounds the same way in every kernel that inlines it (the one-thread
+// and the warp-pair forms give bit-identical rays); the fused operations are the ones written with
+// fmad.  For double-float values it is a b + c in that arithmetic.
+template <class R>
+ART_HD R fmad(R a, R b, R c)
+{
+    return a * b + c;
+}
+template <>
+ART_HD float fmad<float>(float a, float b, float c)
+{
+    return fmaf(a, b, c);
+}
+template <>
+ART_HD double fmad<double>(double a, double b, double c)
+{
+    return fma(a, b, c);
+}
 
 // Job parameters as the kernels see them (POD, passed by value).
 struct DevJob {
@@ -57,8 +78,9 @@ struct RayState {
 template <class R>
 ART_HD R ks_radius(R x, R y, R z, R a2)
 {
-    R b = x * x + y * y + z * z - a2;
-    R r2 = R(0.5) * (b + sqrt(b * b + R(4) * a2 * z * z));
+    R z2 = z * z;
+    R b = (fmad(y, y, x * x) + z2) - a2;
+    R r2 = R(0.5) * (b + sqrt(fmad(b, b, R(4) * a2 * z2)));
     return sqrt(r2);
 }
 
@@ -69,8 +91,8 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
     const R x = s.x, y = s.y, z = s.z, kx = s.kx, ky = s.ky, kz = s.kz;
     R z2 = z * z;
     R a2z2 = a2 * z2;
-    R b = x * x + y * y + z2 - a2;
-    R r2 = R(0.5) * (b + sqrt(b * b + R(4) * a2z2));
+    R b = (fmad(y, y, x * x) + z2) - a2;
+    R r2 = R(0.5) * (b + sqrt(fmad(b, b, R(4) * a2z2)));
     R ir = rsqrt(r2);
     R r = r2 * ir;
     R ir2 = ir * ir;
@@ -78,27 +100,27 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
     R iQ = R(1) / (r4 + a2z2);
     R f = R(2) * r2 * r * iQ;
     R ira2 = R(1) / (r2 + a2);
-    R Lx = (r * x - a * y) * ira2;
-    R Ly = (r * y + a * x) * ira2;
+    R Lx = fmad(r, x, -(a * y)) * ira2;
+    R Ly = fmad(r, y, a * x) * ira2;
     R Lz = z * ir;
-    R Lkxy = Lx * kx + Ly * ky;
-    R lk = -kt - (Lkxy + Lz * kz);
+    R Lkxy = fmad(Ly, ky, Lx * kx);
+    R lk = -kt - fmad(Lz, kz, Lkxy);
     R iSig = r2 * iQ;  // Sigma = r^2 + a^2 z^2 / r^2 = Q / r^2
     R rs = r * iSig;
     R drx = x * rs, dry = y * rs, drz = z * (r2 + a2) * ir * iSig;
-    R B = f * ir * (R(3) - R(4) * r4 * iQ);
-    R A = (x * kx + y * ky - R(2) * r * Lkxy) * ira2 - kz * z * ir2;
+    R B = f * ir * fmad(R(-4) * r4, iQ, R(3));
+    R A = fmad(fmad(R(-2) * r, Lkxy, fmad(y, ky, x * kx)), ira2, -(kz * z * ir2));
     R flk = f * lk;
-    R C = R(0.5) * B * lk * lk - flk * A;
-    R Tx = (r * kx + a * ky) * ira2;
-    R Ty = (r * ky - a * kx) * ira2;
+    R C = fmad(R(0.5) * B * lk, lk, -(flk * A));
+    R Tx = fmad(r, kx, a * ky) * ira2;
+    R Ty = fmad(r, ky, -(a * kx)) * ira2;
     R Tz = kz * ir;
-    d.kx = C * drx - flk * Tx;
-    d.ky = C * dry - flk * Ty;
-    d.kz = C * drz - flk * Tz - flk * lk * a2 * z * iQ;
-    d.x = kx + flk * Lx;
-    d.y = ky + flk * Ly;
-    d.z = kz + flk * Lz;
+    d.kx = fmad(C, drx, -(flk * Tx));
+    d.ky = fmad(C, dry, -(flk * Ty));
+    d.kz = fmad(C, drz, -(flk * Tz)) - flk * lk * a2 * z * iQ;
+    d.x = fmad(flk, Lx, kx);
+    d.y = fmad(flk, Ly, ky);
+    d.z = fmad(flk, Lz, kz);
     return r;
 }
 
@@ -120,15 +142,15 @@ ART_HD R emission_cfg0(const RayState<R>& s, R r, R kt, const DevJob& J)
         R iSig = R(1) / (r2 + a2 * ct2);
         R gtt = -(R(1) - R(2) * r * iSig);
         R gtp = -R(2) * a * r * st2 * iSig;
-        R gpp = (r2 + a2 + R(2) * a2 * r * st2 * iSig) * st2;
-        R Om = R(1) / (r * sqrt(r) + a);
-        R nrm = -(gtt + R(2) * Om * gtp + Om * Om * gpp);
+        R gpp = fmad(R(2) * a2 * r * st2, iSig, r2 + a2) * st2;
+        R Om = R(1) / fmad(r, sqrt(r), a);
+        R nrm = -fmad(Om * Om, gpp, fmad(R(2) * Om, gtp, gtt));
         if (!(nrm > R(0))) return R(0);
         R ut = R(1) / sqrt(nrm);
-        nu = ut * (kt + Om * (s.x * s.ky - s.y * s.kx));
+        nu = ut * fmad(Om, fmad(s.x, s.ky, -(s.y * s.kx)), kt);
     } else {
         R z2 = s.z * s.z;
-        R f = R(2) * r2 * r / (r2 * r2 + a2 * z2);
+        R f = R(2) * r2 * r / fmad(r2, r2, a2 * z2);
         if (!(f < R(1))) return R(0);
         nu = kt / sqrt(R(1) - f);
     }
@@ -141,7 +163,7 @@ ART_HD R emission_cfg0(const RayState<R>& s, R r, R kt, const DevJob& J)
 template <class R>
 ART_HD int polar_sign(const RayState<R>& s, R r)
 {
-    R q = (s.x * s.kx + s.y * s.ky) * s.z / r - (r - s.z * s.z / r) * s.kz;
+    R q = fmad(s.y, s.ky, s.x * s.kx) * s.z / r - (r - s.z * s.z / r) * s.kz;
     R tol = R(sizeof(R) == 4 ? 1e-5 : 1e-9) * r;  // dead band above the rounding noise
     return q > tol ? 1 : (q < -tol ? -1 : 0);
 }

@@ -149,10 +149,11 @@ extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_d
                          st) != cudaSuccess)
             return ART_ERR_CUDA;
     }
-    unsigned long long bad = 0;
-    if (cudaMemcpyAsync(&bad, counters + C_BADIDX, sizeof bad, cudaMemcpyDeviceToHost, st) !=
+    // counters C_BADIDX .. C_SYNCERR: skipped queue entries and timed-out hand-overs
+    unsigned long long bad[C_SYNCERR - C_BADIDX + 1] = {};
+    if (cudaMemcpyAsync(bad, counters + C_BADIDX, sizeof bad, cudaMemcpyDeviceToHost, st) !=
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return ART_ERR_CUDA;
-    return bad ? ART_ERR_DEVICE : ART_OK;
+    return (bad[0] || bad[C_SYNCERR - C_BADIDX]) ? ART_ERR_DEVICE : ART_OK;
 }

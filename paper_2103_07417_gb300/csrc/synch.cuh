@@ -57,46 +57,55 @@ struct SynchConst {
 
 // K_0, K_1, K_2 scaled by e^x (K_n(x) e^x), so that FP32 stays finite for cold plasma (large x).
 template <class Q>
+ART_HD Q horner7(Q t, Q c0, Q c1, Q c2, Q c3, Q c4, Q c5, Q c6)
+{
+    return fmad(t, fmad(t, fmad(t, fmad(t, fmad(t, fmad(t, c6, c5), c4), c3), c2), c1), c0);
+}
+
+template <class Q>
 ART_HD void bessel_k012_scaled(Q x, Q& K0, Q& K1, Q& K2)
 {
     if (x <= Q(2)) {
         Q t = x / Q(3.75), t2 = t * t;
-        Q i0 = Q(1) + t2 * (Q(3.5156229) + t2 * (Q(3.0899424) + t2 * (Q(1.2067492) +
-               t2 * (Q(0.2659732) + t2 * (Q(0.0360768) + t2 * Q(0.0045813))))));
-        Q i1 = x * (Q(0.5) + t2 * (Q(0.87890594) + t2 * (Q(0.51498869) + t2 * (Q(0.15084934) +
-               t2 * (Q(0.02658733) + t2 * (Q(0.00301532) + t2 * Q(0.00032411)))))));
+        Q i0 = horner7<Q>(t2, Q(1), Q(3.5156229), Q(3.0899424), Q(1.2067492), Q(0.2659732),
+                          Q(0.0360768), Q(0.0045813));
+        Q i1 = x * horner7<Q>(t2, Q(0.5), Q(0.87890594), Q(0.51498869), Q(0.15084934),
+                              Q(0.02658733), Q(0.00301532), Q(0.00032411));
         Q y = Q(0.25) * x * x, lg = log(Q(0.5) * x), ex = exp(x);
-        K0 = ex * (-lg * i0 + (Q(-0.57721566) + y * (Q(0.42278420) + y * (Q(0.23069756) +
-             y * (Q(0.03488590) + y * (Q(0.00262698) + y * (Q(0.00010750) + y * Q(0.0000074))))))));
-        K1 = ex * (lg * i1 + (Q(1) / x) * (Q(1) + y * (Q(0.15443144) + y * (Q(-0.67278579) +
-             y * (Q(-0.18156897) + y * (Q(-0.01919402) + y * (Q(-0.00110404) + y * Q(-0.00004686))))))));
+        K0 = ex * fmad(-lg, i0, horner7<Q>(y, Q(-0.57721566), Q(0.42278420), Q(0.23069756),
+                                           Q(0.03488590), Q(0.00262698), Q(0.00010750),
+                                           Q(0.0000074)));
+        K1 = ex * fmad(lg, i1, (Q(1) / x) * horner7<Q>(y, Q(1), Q(0.15443144), Q(-0.67278579),
+                                                       Q(-0.18156897), Q(-0.01919402),
+                                                       Q(-0.00110404), Q(-0.00004686)));
     } else {
         Q y = Q(2) / x, pre = Q(1) / sqrt(x);
-        K0 = pre * (Q(1.25331414) + y * (Q(-0.07832358) + y * (Q(0.02189568) + y * (Q(-0.01062446) +
-             y * (Q(0.00587872) + y * (Q(-0.00251540) + y * Q(0.00053208)))))));
-        K1 = pre * (Q(1.25331414) + y * (Q(0.23498619) + y * (Q(-0.03655620) + y * (Q(0.01504268) +
-             y * (Q(-0.00780353) + y * (Q(0.00325614) + y * Q(-0.00068245)))))));
+        K0 = pre * horner7<Q>(y, Q(1.25331414), Q(-0.07832358), Q(0.02189568), Q(-0.01062446),
+                              Q(0.00587872), Q(-0.00251540), Q(0.00053208));
+        K1 = pre * horner7<Q>(y, Q(1.25331414), Q(0.23498619), Q(-0.03655620), Q(0.01504268),
+                              Q(-0.00780353), Q(0.00325614), Q(-0.00068245));
     }
-    K2 = K0 + Q(2) * K1 / x;
+    K2 = fmad(Q(2), K1 / x, K0);
 }
 
 // Minkowski + Kerr-Schild pieces at a point: F = 2 r^3 / (r^4 + a^2 z^2), L (outgoing l = (1,-L)).
 template <class Q>
 struct KSPoint {
     Q F, Lx, Ly, Lz;
-    ART_HD Q ldot(const Q* v) const { return v[0] - (Lx * v[1] + Ly * v[2] + Lz * v[3]); }
+    ART_HD Q ldot(const Q* v) const { return v[0] - fmad(Lz, v[3], fmad(Ly, v[2], Lx * v[1])); }
     ART_HD Q dot(const Q* u, const Q* v) const
     {
-        return -u[0] * v[0] + u[1] * v[1] + u[2] * v[2] + u[3] * v[3] + F * ldot(u) * ldot(v);
+        return fmad(F * ldot(u), ldot(v),
+                    fmad(u[3], v[3], fmad(u[2], v[2], fmad(u[1], v[1], -(u[0] * v[0])))));
     }
     // raise a covector: w^t = -w_t + F lw, w^i = w_i + F L_i lw, lw = l^mu w_mu = -w_t - L.w
     ART_HD void raise(const Q* w, Q* up) const
     {
-        Q lw = -w[0] - (Lx * w[1] + Ly * w[2] + Lz * w[3]);
-        up[0] = -w[0] + F * lw;
-        up[1] = w[1] + F * Lx * lw;
-        up[2] = w[2] + F * Ly * lw;
-        up[3] = w[3] + F * Lz * lw;
+        Q lw = -w[0] - fmad(Lz, w[3], fmad(Ly, w[2], Lx * w[1]));
+        up[0] = fmad(F, lw, -w[0]);
+        up[1] = fmad(F * Lx, lw, w[1]);
+        up[2] = fmad(F * Ly, lw, w[2]);
+        up[3] = fmad(F * Lz, lw, w[3]);
     }
 };
 
@@ -105,10 +114,10 @@ ART_HD KSPoint<Q> ks_point(Q x, Q y, Q z, Q r, Q a, Q a2)
 {
     KSPoint<Q> P;
     Q r2 = r * r;
-    P.F = Q(2) * r2 * r / (r2 * r2 + a2 * z * z);
+    P.F = Q(2) * r2 * r / fmad(r2, r2, a2 * z * z);
     Q ira2 = Q(1) / (r2 + a2);
-    P.Lx = (r * x - a * y) * ira2;
-    P.Ly = (r * y + a * x) * ira2;
+    P.Lx = fmad(r, x, -(a * y)) * ira2;
+    P.Ly = fmad(r, y, a * x) * ira2;
     P.Lz = z / r;
     return P;
 }
@@ -117,13 +126,14 @@ ART_HD KSPoint<Q> ks_point(Q x, Q y, Q z, Q r, Q a, Q a2)
 template <class Q>
 ART_HD Q det4(const Q* A, const Q* B, const Q* C, const Q* D)
 {
-    Q m01 = C[0] * D[1] - C[1] * D[0], m02 = C[0] * D[2] - C[2] * D[0], m03 = C[0] * D[3] - C[3] * D[0];
-    Q m12 = C[1] * D[2] - C[2] * D[1], m13 = C[1] * D[3] - C[3] * D[1], m23 = C[2] * D[3] - C[3] * D[2];
-    Q c0 = B[1] * m23 - B[2] * m13 + B[3] * m12;
-    Q c1 = B[0] * m23 - B[2] * m03 + B[3] * m02;
-    Q c2 = B[0] * m13 - B[1] * m03 + B[3] * m01;
-    Q c3 = B[0] * m12 - B[1] * m02 + B[2] * m01;
-    return A[0] * c0 - A[1] * c1 + A[2] * c2 - A[3] * c3;
+    Q m01 = fmad(C[0], D[1], -(C[1] * D[0])), m02 = fmad(C[0], D[2], -(C[2] * D[0]));
+    Q m03 = fmad(C[0], D[3], -(C[3] * D[0])), m12 = fmad(C[1], D[2], -(C[2] * D[1]));
+    Q m13 = fmad(C[1], D[3], -(C[3] * D[1])), m23 = fmad(C[2], D[3], -(C[3] * D[2]));
+    Q c0 = fmad(B[3], m12, fmad(B[1], m23, -(B[2] * m13)));
+    Q c1 = fmad(B[3], m02, fmad(B[0], m23, -(B[2] * m03)));
+    Q c2 = fmad(B[3], m01, fmad(B[0], m13, -(B[1] * m03)));
+    Q c3 = fmad(B[2], m01, fmad(B[0], m12, -(B[1] * m02)));
+    return fmad(-A[3], c3, fmad(A[2], c2, fmad(A[0], c0, -(A[1] * c1))));
 }
 
 // Thermal-synchrotron coefficients of a fluid element (velocity u, unit field direction b in its
@@ -143,7 +153,7 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
     for (int m = 0; m < 4; ++m) d[m] *= dn;
     Q cth = G.dot(d, b);
     cth = cth > Q(1) ? Q(1) : (cth < Q(-1) ? Q(-1) : cth);
-    Q sth2 = Q(1) - cth * cth;
+    Q sth2 = fmad(-cth, cth, Q(1));
     Q sth = sqrt(sth2);
     // coefficients in the E-vector frame; K_n e^x keeps 1/K_2 finite, e^(x - X^1/3) recombines
     Q x = Q(1) / Th, K0, K1, K2;
@@ -155,9 +165,9 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
         Q x3 = cbrt(X), x6 = sqrt(x3), x2 = x3 * x6;  // X^1/3, X^1/6, X^1/2
         Q pre = Q(S.LCj) * ne * nus / K2 * exp(x - x3) / (nu * nu);
         Q t96 = exp(Q(0.96) * log(Th));
-        Q q = (Q(7) * t96 + Q(35)) / (Q(10) * t96 + Q(75));
+        Q q = fmad(Q(7), t96, Q(35)) / fmad(Q(10), t96, Q(75));
         const Q k1112 = Q(1.8877486253633868);  // 2^(11/12)
-        Q vi = x2 + k1112 * x6, vq = x2 + q * k1112 * x6;
+        Q vi = fmad(k1112, x6, x2), vq = fmad(q * k1112, x6, x2);
         jI = pre * vi * vi;
         jQ = pre * vq * vq;
     }
@@ -166,21 +176,21 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
     K7[0] = jI * kir;
     if (!f) return;
     Q rV = Q(S.LCV) * ne * Bm * cth / nu * (K0 / K2);
-    Q rQ = Q(S.LCQ) * ne * Bm * Bm * sth2 / (nu * nu) * (K1 / K2 + Q(6) * Th);
+    Q rQ = Q(S.LCQ) * ne * Bm * Bm * sth2 / (nu * nu) * fmad(Q(6), Th, K1 / K2);
     // polarization basis from the transported covector
     Q fu_[4];
     G.raise(f, fu_);
     Q fuu = G.dot(fu_, u), fud = G.dot(fu_, d), eN[4];
-    for (int m = 0; m < 4; ++m) eN[m] = fu_[m] + fuu * u[m] - fud * d[m];
+    for (int m = 0; m < 4; ++m) eN[m] = fmad(-fud, d[m], fmad(fuu, u[m], fu_[m]));
     Q nN = Q(1) / sqrt(G.dot(eN, eN));
     for (int m = 0; m < 4; ++m) eN[m] *= nN;
     Q bN = G.dot(b, eN);
     Q bE = -det4<Q>(b, u, d, eN);
-    Q bp2 = bN * bN + bE * bE;
+    Q bp2 = fmad(bE, bE, bN * bN);
     Q c2 = Q(1), s2 = Q(0);
     if (bp2 > Q(0)) {
         // E-vector at angle chi from north: cos chi = -bE/|b_perp|, sin chi = bN/|b_perp|
-        c2 = (bE * bE - bN * bN) / bp2;
+        c2 = fmad(bE, bE, -(bN * bN)) / bp2;
         s2 = Q(-2) * bE * bN / bp2;
     }
     J4[1] = jQ * c2;
@@ -208,16 +218,16 @@ ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const De
     Q iSig = Q(1) / (r2 + a2 * ct2);
     Q gtt = -(Q(1) - Q(2) * r * iSig);
     Q gtp = -Q(2) * a * r * st2 * iSig;
-    Q gpp = (r2 + a2 + Q(2) * a2 * r * st2 * iSig) * st2;
-    Q Om = Q(1) / (r * sqrt(r) + a);
-    Q nrm = -(gtt + Q(2) * Om * gtp + Om * Om * gpp);
+    Q gpp = fmad(Q(2) * a2 * r * st2, iSig, r2 + a2) * st2;
+    Q Om = Q(1) / fmad(r, sqrt(r), a);
+    Q nrm = -fmad(Om * Om, gpp, fmad(Q(2) * Om, gtp, gtt));
     if (!(nrm > Q(0))) return;
     Q ut = Q(1) / sqrt(nrm);
     Q u[4] = {ut, -Om * s.y * ut, Om * s.x * ut, Q(0)};
-    Q nu = ut * (kt + Om * (s.x * s.ky - s.y * s.kx));
+    Q nu = ut * fmad(Om, fmad(s.x, s.ky, -(s.y * s.kx)), kt);
     if (!(nu > Q(0))) return;
     Q lr = log(r);
-    Q ne = Q(S.ne0) * exp(Q(S.ne_s) * lr - ct2 * Q(S.inv_2w2));
+    Q ne = Q(S.ne0) * exp(fmad(Q(S.ne_s), lr, -(ct2 * Q(S.inv_2w2))));
     Q Th = Q(S.th0) * exp(Q(S.te_s) * lr);
     Q Bm = Q(S.b0) * exp(Q(S.b_s) * lr);
     if (!(ne > Q(0))) return;
@@ -225,15 +235,15 @@ ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const De
     // field direction (e_phi + q e_z)/sqrt(1 + q^2) in the fluid frame
     Q ephi[4] = {Q(0), -s.y, s.x, Q(0)};
     Q pu = G.dot(u, ephi);
-    for (int m = 0; m < 4; ++m) ephi[m] += pu * u[m];
+    for (int m = 0; m < 4; ++m) ephi[m] = fmad(pu, u[m], ephi[m]);
     Q nph = Q(1) / sqrt(G.dot(ephi, ephi));
     for (int m = 0; m < 4; ++m) ephi[m] *= nph;
     Q ez[4] = {Q(0), Q(0), Q(0), Q(1)};
     Q pz = G.dot(u, ez), pe = G.dot(ephi, ez);
-    for (int m = 0; m < 4; ++m) ez[m] += pz * u[m] - pe * ephi[m];
+    for (int m = 0; m < 4; ++m) ez[m] = fmad(-pe, ephi[m], fmad(pz, u[m], ez[m]));
     Q nz = Q(1) / sqrt(G.dot(ez, ez));
     Q b[4];
-    for (int m = 0; m < 4; ++m) b[m] = (ephi[m] + Q(S.bz) * ez[m] * nz) * Q(S.bnorm);
+    for (int m = 0; m < 4; ++m) b[m] = fmad(Q(S.bz) * nz, ez[m], ephi[m]) * Q(S.bnorm);
     synch_coeffs<Q>(G, s, kt, u, b, nu, ne, Th, Bm, f, S, J4, K7);
 }
 
@@ -244,73 +254,97 @@ ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const De
 //   T2_mu = (k.gF) lf l_mu - F (k.Jm.f) l_mu + F lf Dk(l_mu),  Dk(l_j) = -(k.Jm)_j, Dk(l_t) = 0,
 //   T3_mu = (f.gF) lk l_mu - F (f.Jm.k) l_mu + F lk Df(l_mu),  Df(l_j) = -(f.Jm)_j.
 template <class Q>
+ART_HD Q dot3(Q a0, Q b0, Q a1, Q b1, Q a2, Q b2)
+{
+    return fmad(a2, b2, fmad(a1, b1, a0 * b0));
+}
+
+template <class Q>
 ART_HD void transport_rhs(const RayState<Q>& s, Q kt, const Q* f, Q a, Q a2, Q* df)
 {
     const Q x = s.x, y = s.y, z = s.z;
     Q z2 = z * z, a2z2 = a2 * z2;
-    Q bb = x * x + y * y + z2 - a2;
-    Q r2 = Q(0.5) * (bb + sqrt(bb * bb + Q(4) * a2z2));
+    Q bb = (fmad(y, y, x * x) + z2) - a2;
+    Q r2 = Q(0.5) * (bb + sqrt(fmad(bb, bb, Q(4) * a2z2)));
     Q r = sqrt(r2), ir = Q(1) / r;
     Q r4 = r2 * r2, iQ = Q(1) / (r4 + a2z2);
     Q F = Q(2) * r2 * r * iQ;
     Q ira2 = Q(1) / (r2 + a2);
-    Q Lx = (r * x - a * y) * ira2, Ly = (r * y + a * x) * ira2, Lz = z * ir;
+    Q Lx = fmad(r, x, -(a * y)) * ira2, Ly = fmad(r, y, a * x) * ira2, Lz = z * ir;
     Q iSig = r2 * iQ;
     Q dr[3] = {x * r * iSig, y * r * iSig, z * (r2 + a2) * ir * iSig};
-    Q B = F * ir * (Q(3) - Q(4) * r4 * iQ);
-    Q gF[3] = {B * dr[0], B * dr[1], B * dr[2] - Q(2) * F * a2 * z * iQ};
+    Q B = F * ir * fmad(Q(-4) * r4, iQ, Q(3));
+    Q gF[3] = {B * dr[0], B * dr[1], fmad(B, dr[2], -(Q(2) * F * a2 * z * iQ))};
     // Jm[i][j] = d_i L_j
     Q Jm[3][3];
     for (int i = 0; i < 3; ++i) {
-        Jm[i][0] = (x * dr[i] + (i == 0 ? r : Q(0)) - (i == 1 ? a : Q(0)) - Q(2) * r * Lx * dr[i]) * ira2;
-        Jm[i][1] = (y * dr[i] + (i == 1 ? r : Q(0)) + (i == 0 ? a : Q(0)) - Q(2) * r * Ly * dr[i]) * ira2;
-        Jm[i][2] = (i == 2 ? ir : Q(0)) - z * dr[i] * ir * ir;
+        const Q tr = Q(-2) * r * dr[i];
+        Jm[i][0] = (fmad(tr, Lx, x * dr[i]) + ((i == 0 ? r : Q(0)) - (i == 1 ? a : Q(0)))) * ira2;
+        Jm[i][1] = (fmad(tr, Ly, y * dr[i]) + ((i == 1 ? r : Q(0)) + (i == 0 ? a : Q(0)))) * ira2;
+        Jm[i][2] = fmad(-z * dr[i], ir * ir, (i == 2 ? ir : Q(0)));
     }
     // contravariant k and f
-    Q lkc = -kt - (Lx * s.kx + Ly * s.ky + Lz * s.kz);
-    Q ku[4] = {-kt + F * lkc, s.kx + F * Lx * lkc, s.ky + F * Ly * lkc, s.kz + F * Lz * lkc};
-    Q lfc = -f[0] - (Lx * f[1] + Ly * f[2] + Lz * f[3]);
-    Q fu[4] = {-f[0] + F * lfc, f[1] + F * Lx * lfc, f[2] + F * Ly * lfc, f[3] + F * Lz * lfc};
-    Q lk = ku[0] - (Lx * ku[1] + Ly * ku[2] + Lz * ku[3]);
-    Q lf = fu[0] - (Lx * fu[1] + Ly * fu[2] + Lz * fu[3]);
+    Q lkc = -kt - dot3(Lx, s.kx, Ly, s.ky, Lz, s.kz);
+    Q ku[4] = {fmad(F, lkc, -kt), fmad(F * Lx, lkc, s.kx), fmad(F * Ly, lkc, s.ky),
+               fmad(F * Lz, lkc, s.kz)};
+    Q lfc = -f[0] - dot3(Lx, f[1], Ly, f[2], Lz, f[3]);
+    Q fu[4] = {fmad(F, lfc, -f[0]), fmad(F * Lx, lfc, f[1]), fmad(F * Ly, lfc, f[2]),
+               fmad(F * Lz, lfc, f[3])};
+    Q lk = ku[0] - dot3(Lx, ku[1], Ly, ku[2], Lz, ku[3]);
+    Q lf = fu[0] - dot3(Lx, fu[1], Ly, fu[2], Lz, fu[3]);
     Q Jf[3], Jk[3], kJ[3], fJ[3];
     for (int i = 0; i < 3; ++i) {
-        Jf[i] = Jm[i][0] * fu[1] + Jm[i][1] * fu[2] + Jm[i][2] * fu[3];
-        Jk[i] = Jm[i][0] * ku[1] + Jm[i][1] * ku[2] + Jm[i][2] * ku[3];
-        kJ[i] = ku[1] * Jm[0][i] + ku[2] * Jm[1][i] + ku[3] * Jm[2][i];
-        fJ[i] = fu[1] * Jm[0][i] + fu[2] * Jm[1][i] + fu[3] * Jm[2][i];
+        Jf[i] = dot3(Jm[i][0], fu[1], Jm[i][1], fu[2], Jm[i][2], fu[3]);
+        Jk[i] = dot3(Jm[i][0], ku[1], Jm[i][1], ku[2], Jm[i][2], ku[3]);
+        kJ[i] = dot3(ku[1], Jm[0][i], ku[2], Jm[1][i], ku[3], Jm[2][i]);
+        fJ[i] = dot3(fu[1], Jm[0][i], fu[2], Jm[1][i], fu[3], Jm[2][i]);
     }
-    Q kgF = ku[1] * gF[0] + ku[2] * gF[1] + ku[3] * gF[2];
-    Q fgF = fu[1] * gF[0] + fu[2] * gF[1] + fu[3] * gF[2];
-    Q kJf = ku[1] * Jf[0] + ku[2] * Jf[1] + ku[3] * Jf[2];
-    Q fJk = fu[1] * Jk[0] + fu[2] * Jk[1] + fu[3] * Jk[2];
+    Q kgF = dot3(ku[1], gF[0], ku[2], gF[1], ku[3], gF[2]);
+    Q fgF = dot3(fu[1], gF[0], fu[2], gF[1], fu[3], gF[2]);
+    Q kJf = dot3(ku[1], Jf[0], ku[2], Jf[1], ku[3], Jf[2]);
+    Q fJk = dot3(fu[1], Jk[0], fu[2], Jk[1], fu[3], Jk[2]);
     Q l[4] = {Q(1), -Lx, -Ly, -Lz};
-    Q c2 = kgF * lf - F * kJf;   // T2 = c2 l_mu + F lf Dk(l_mu)
-    Q c3 = fgF * lk - F * fJk;   // T3 = c3 l_mu + F lk Df(l_mu)
+    Q c2 = fmad(kgF, lf, -(F * kJf));   // T2 = c2 l_mu + F lf Dk(l_mu)
+    Q c3 = fmad(fgF, lk, -(F * fJk));   // T3 = c3 l_mu + F lk Df(l_mu)
     df[0] = Q(0.5) * (c2 - c3);
     for (int i = 0; i < 3; ++i) {
-        Q t1 = gF[i] * lf * lk - F * (Jf[i] * lk + lf * Jk[i]);
-        Q t2 = c2 * l[i + 1] - F * lf * kJ[i];
-        Q t3 = c3 * l[i + 1] - F * lk * fJ[i];
-        df[i + 1] = Q(0.5) * (t1 + t2 - t3);
+        Q t1 = fmad(gF[i] * lf, lk, -(F * fmad(Jf[i], lk, lf * Jk[i])));
+        Q t2 = fmad(c2, l[i + 1], -(F * lf * kJ[i]));
+        Q t3 = fmad(c3, l[i + 1], -(F * lk * fJ[i]));
+        df[i + 1] = Q(0.5) * ((t1 + t2) - t3);
     }
 }
 
-// psi_n(x) = int_0^1 t^n e^{-x t} dt (series for small x, closed forms otherwise)
-template <class Q>
-ART_HD Q psi_n(int n, Q x)
+// psi_n(x) = int_0^1 t^n e^{-x t} dt = sum_k (-x)^k / (k! (n + k + 1)) for small x (18 terms,
+// Horner form with the coefficients 1/(k! (n + k + 1)) fixed at compile time), closed forms
+// otherwise.
+template <int N, int K>
+struct PsiCoef {
+    static constexpr double fact = PsiCoef<N, K - 1>::fact * K;
+    static constexpr double v = 1.0 / (fact * (N + K + 1));
+};
+template <int N>
+struct PsiCoef<N, 0> {
+    static constexpr double fact = 1.0;
+    static constexpr double v = 1.0 / (N + 1);
+};
+
+template <class Q, int N, int K>
+ART_HD Q psi_series(Q mx)
 {
-    if (x < Q(1.5)) {
-        Q term = Q(1), sum = Q(0);
-        for (int k = 0; k < 18; ++k) {
-            sum += term / Q(n + k + 1);
-            term *= -x / Q(k + 1);
-        }
-        return sum;
-    }
+    if constexpr (K == 17)
+        return Q(PsiCoef<N, K>::v);
+    else
+        return fmad(mx, psi_series<Q, N, K + 1>(mx), Q(PsiCoef<N, K>::v));
+}
+
+template <class Q, int N>
+ART_HD Q psi_n(Q x)
+{
+    if (x < Q(1.5)) return psi_series<Q, N, 0>(-x);
     Q e = exp(-x), x2 = x * x;
-    if (n == 1) return (Q(1) - e * (Q(1) + x)) / x2;
-    if (n == 2) return (Q(2) - e * (x2 + Q(2) * x + Q(2))) / (x2 * x);
+    if (N == 1) return (Q(1) - e * (Q(1) + x)) / x2;
+    if (N == 2) return (Q(2) - e * (x2 + Q(2) * x + Q(2))) / (x2 * x);
     return (Q(6) - e * (x2 * x + Q(3) * x2 + Q(6) * x + Q(6))) / (x2 * x2);
 }
 
@@ -324,7 +358,7 @@ ART_HD Q phi_r(Q x)
 template <class Q>
 ART_HD void phi_c(Q x, Q y, Q& re, Q& im)
 {
-    Q d = x * x + y * y;
+    Q d = fmad(y, y, x * x);
     if (d < Q(1e-12)) {  // 1 - z/2
         re = Q(1) - Q(0.5) * x;
         im = Q(-0.5) * y;
@@ -332,10 +366,10 @@ ART_HD void phi_c(Q x, Q y, Q& re, Q& im)
     }
     Q e = exp(-x), sh = sin(Q(0.5) * y);
     // numerator 1 - e^{-x}(cos y - i sin y), with 1 - e^{-x} cos y = -expm1(-x) cos y + 2 sin^2(y/2)
-    Q nr = -expm1(-x) * cos(y) + Q(2) * sh * sh;
+    Q nr = fmad(Q(2) * sh, sh, -expm1(-x) * cos(y));
     Q ni = e * sin(y);
-    re = (nr * x + ni * y) / d;
-    im = (ni * x - nr * y) / d;
+    re = fmad(ni, y, nr * x) / d;
+    im = fmad(ni, x, -(nr * y)) / d;
 }
 
 // K' v for the traceless polarized part of K.
@@ -343,10 +377,10 @@ template <class Q>
 ART_HD void kprime_v(const Q* K7, const Q* v, Q* o)
 {
     const Q aQ = K7[1], aU = K7[2], aV = K7[3], rQ = K7[4], rU = K7[5], rV = K7[6];
-    o[0] = aQ * v[1] + aU * v[2] + aV * v[3];
-    o[1] = aQ * v[0] + rV * v[2] - rU * v[3];
-    o[2] = aU * v[0] - rV * v[1] + rQ * v[3];
-    o[3] = aV * v[0] + rU * v[1] - rQ * v[2];
+    o[0] = fmad(aV, v[3], fmad(aU, v[2], aQ * v[1]));
+    o[1] = fmad(-rU, v[3], fmad(rV, v[2], aQ * v[0]));
+    o[2] = fmad(rQ, v[3], fmad(-rV, v[1], aU * v[0]));
+    o[3] = fmad(-rQ, v[2], fmad(rU, v[1], aV * v[0]));
 }
 
 // row-vector times K' (P K' for one row of P)
@@ -354,10 +388,10 @@ template <class Q>
 ART_HD void v_kprime(const Q* K7, const Q* v, Q* o)
 {
     const Q aQ = K7[1], aU = K7[2], aV = K7[3], rQ = K7[4], rU = K7[5], rV = K7[6];
-    o[0] = v[1] * aQ + v[2] * aU + v[3] * aV;
-    o[1] = v[0] * aQ - v[2] * rV + v[3] * rU;
-    o[2] = v[0] * aU + v[1] * rV - v[3] * rQ;
-    o[3] = v[0] * aV - v[1] * rU + v[2] * rQ;
+    o[0] = fmad(v[3], aV, fmad(v[2], aU, v[1] * aQ));
+    o[1] = fmad(v[3], rU, fmad(-v[2], rV, v[0] * aQ));
+    o[2] = fmad(-v[3], rQ, fmad(v[1], rV, v[0] * aU));
+    o[3] = fmad(v[2], rQ, fmad(-v[1], rU, v[0] * aV));
 }
 
 // One constant-coefficient Stokes segment of length h: adds P X to acc (4 Stokes) and replaces the
@@ -369,39 +403,48 @@ ART_HD void segment_pol(const Q* K7, const Q* J4, Q h, Q* P, Q* acc)
 {
     const Q tiny = Q(sizeof(Q) == 4 ? 1e-3 : 1e-7);
     const Q aI = K7[0];
-    Q al2 = K7[1] * K7[1] + K7[2] * K7[2] + K7[3] * K7[3];
-    Q rh2 = K7[4] * K7[4] + K7[5] * K7[5] + K7[6] * K7[6];
-    Q ar = K7[1] * K7[4] + K7[2] * K7[5] + K7[3] * K7[6];
-    Q t = Q(0.5) * (al2 - rh2), sq = sqrt(t * t + ar * ar);
+    Q al2 = fmad(K7[3], K7[3], fmad(K7[2], K7[2], K7[1] * K7[1]));
+    Q rh2 = fmad(K7[6], K7[6], fmad(K7[5], K7[5], K7[4] * K7[4]));
+    Q ar = fmad(K7[3], K7[6], fmad(K7[2], K7[5], K7[1] * K7[4]));
+    Q t = Q(0.5) * (al2 - rh2), sq = sqrt(fmad(ar, ar, t * t));
     Q L1 = sqrt(fmax(t + sq, Q(0))), L2 = sqrt(fmax(sq - t, Q(0)));
-    Q D = L1 * L1 + L2 * L2;
+    const Q L11 = L1 * L1, L22 = L2 * L2;
+    Q D = L11 + L22;
     Q a = L1 * h, b = L2 * h, Dh2 = D * h * h;
     const Q ea = exp(-aI * h);
-    // ea cosh(a), ea sinh(a)/a, ea sinh^2(a/2)
-    Q eCh, eSha, eSa2;
-    if (a < Q(20)) {
-        Q sa2 = sinh(Q(0.5) * a);
-        eCh = ea * cosh(a);
-        eSha = ea * (a < tiny ? Q(1) + a * a / Q(6) : sinh(a) / a);
-        eSa2 = ea * sa2 * sa2;
-    } else {
-        Q e1 = exp(-(aI - L1) * h), e2 = exp(-(aI + L1) * h);
-        eCh = Q(0.5) * (e1 + e2);
-        eSha = Q(0.5) * (e1 - e2) / a;
-        eSa2 = Q(0.5) * (eCh - ea);
-    }
-    Q cb = cos(b), sb2 = sin(Q(0.5) * b);
-    Q sbb = b < tiny ? Q(1) - b * b / Q(6) : sin(b) / b;
     Q C0, C1, C2, C3;  // exp(-K h) = C0 + C1 K' + C2 K'^2 + C3 K'^3 (attenuation included)
+    Q X0, X1, X2, X3;  // source integral = X0 J + X1 K'J + X2 K'^2 J + X3 K'^3 J
     if (Dh2 < tiny * tiny) {
+        // weakly polarizing segment (the common case of an optically thin flow): the series of
+        // exp(-K' s) to third order; only the attenuation's functions are needed
+        const Q x = aI * h;
         C0 = ea;
         C1 = -h * ea;
         C2 = Q(0.5) * h * h * ea;
         C3 = -h * h * h * ea / Q(6);
+        X0 = h * phi_r<Q>(x);
+        X1 = -h * h * psi_n<Q, 1>(x);
+        X2 = Q(0.5) * h * h * h * psi_n<Q, 2>(x);
+        X3 = -h * h * h * h * psi_n<Q, 3>(x) / Q(6);
     } else {
-        C0 = (L2 * L2 * eCh + L1 * L1 * ea * cb) / D;
-        C1 = -h * (L2 * L2 * eSha + L1 * L1 * ea * sbb) / D;
-        C2 = Q(2) * (eSa2 + ea * sb2 * sb2) / D;
+        // ea cosh(a), ea sinh(a)/a, ea sinh^2(a/2)
+        Q eCh, eSha, eSa2;
+        if (a < Q(20)) {
+            Q sa2 = sinh(Q(0.5) * a);
+            eCh = ea * cosh(a);
+            eSha = ea * (a < tiny ? Q(1) + a * a / Q(6) : sinh(a) / a);
+            eSa2 = ea * sa2 * sa2;
+        } else {
+            Q e1 = exp(-(aI - L1) * h), e2 = exp(-(aI + L1) * h);
+            eCh = Q(0.5) * (e1 + e2);
+            eSha = Q(0.5) * (e1 - e2) / a;
+            eSa2 = Q(0.5) * (eCh - ea);
+        }
+        Q cb = cos(b), sb2 = sin(Q(0.5) * b);
+        Q sbb = b < tiny ? Q(1) - b * b / Q(6) : sin(b) / b;
+        C0 = fmad(L22, eCh, L11 * ea * cb) / D;
+        C1 = -h * fmad(L22, eSha, L11 * ea * sbb) / D;
+        C2 = Q(2) * fmad(ea * sb2, sb2, eSa2) / D;
         if (a * a + b * b < Q(0.1) && a < Q(20)) {
             Q a2_ = a * a, b2_ = b * b;
             C3 = -h * h * h * ea *
@@ -409,25 +452,17 @@ ART_HD void segment_pol(const Q* K7, const Q* J4, Q h, Q* P, Q* acc)
         } else {
             C3 = -h * (eSha - ea * sbb) / D;
         }
-    }
-    // source coefficients: the same functions of s integrated against exp(-aI s)
-    Q r1 = fmax((aI - L1) * h, Q(0)), r2 = (aI + L1) * h;
-    Q p1 = phi_r<Q>(r1), p2 = phi_r<Q>(r2);
-    Q Ic = Q(0.5) * h * (p1 + p2);
-    Q IsL1 = a < tiny ? h * h * psi_n<Q>(1, aI * h) : Q(0.5) * h * (p1 - p2) / L1;
-    Q pcr, pci;
-    phi_c<Q>(aI * h, -b, pcr, pci);
-    Q Icos = h * pcr;
-    Q IsinL2 = b < tiny ? h * h * psi_n<Q>(1, aI * h) : h * pci / L2;
-    Q X0, X1, X2, X3;
-    if (Dh2 < tiny * tiny) {
-        X0 = h * phi_r<Q>(aI * h);
-        X1 = -h * h * psi_n<Q>(1, aI * h);
-        X2 = Q(0.5) * h * h * h * psi_n<Q>(2, aI * h);
-        X3 = -h * h * h * h * psi_n<Q>(3, aI * h) / Q(6);
-    } else {
-        X0 = (L2 * L2 * Ic + L1 * L1 * Icos) / D;
-        X1 = -(L2 * L2 * IsL1 + L1 * L1 * IsinL2) / D;
+        // source coefficients: the same functions of s integrated against exp(-aI s)
+        Q r1 = fmax((aI - L1) * h, Q(0)), r2 = (aI + L1) * h;
+        Q p1 = phi_r<Q>(r1), p2 = phi_r<Q>(r2);
+        Q Ic = Q(0.5) * h * (p1 + p2);
+        Q IsL1 = a < tiny ? h * h * psi_n<Q, 1>(aI * h) : Q(0.5) * h * (p1 - p2) / L1;
+        Q pcr, pci;
+        phi_c<Q>(aI * h, -b, pcr, pci);
+        Q Icos = h * pcr;
+        Q IsinL2 = b < tiny ? h * h * psi_n<Q, 1>(aI * h) : h * pci / L2;
+        X0 = fmad(L22, Ic, L11 * Icos) / D;
+        X1 = -fmad(L22, IsL1, L11 * IsinL2) / D;
         X2 = (Ic - Icos) / D;
         X3 = -(IsL1 - IsinL2) / D;
     }
@@ -436,16 +471,17 @@ ART_HD void segment_pol(const Q* K7, const Q* J4, Q h, Q* P, Q* acc)
     kprime_v<Q>(K7, J4, v1);
     kprime_v<Q>(K7, v1, v2);
     kprime_v<Q>(K7, v2, v3);
-    for (int i = 0; i < 4; ++i) Xv[i] = X0 * J4[i] + X1 * v1[i] + X2 * v2[i] + X3 * v3[i];
+    for (int i = 0; i < 4; ++i) Xv[i] = fmad(X3, v3[i], fmad(X2, v2[i], fmad(X1, v1[i], X0 * J4[i])));
     // acc += P X ;  P <- P exp(-K h)
     for (int i = 0; i < 4; ++i) {
         Q* row = P + 4 * i;
-        acc[i] += row[0] * Xv[0] + row[1] * Xv[1] + row[2] * Xv[2] + row[3] * Xv[3];
+        acc[i] += fmad(row[3], Xv[3], fmad(row[2], Xv[2], fmad(row[1], Xv[1], row[0] * Xv[0])));
         Q w1[4], w2[4], w3[4];
         v_kprime<Q>(K7, row, w1);
         v_kprime<Q>(K7, w1, w2);
         v_kprime<Q>(K7, w2, w3);
-        for (int j = 0; j < 4; ++j) row[j] = C0 * row[j] + C1 * w1[j] + C2 * w2[j] + C3 * w3[j];
+        for (int j = 0; j < 4; ++j)
+            row[j] = fmad(C3, w3[j], fmad(C2, w2[j], fmad(C1, w1[j], C0 * row[j])));
     }
 }
 

@@ -117,19 +117,46 @@ __device__ __forceinline__ unsigned long long warp_fetch(unsigned long long* cou
 
 constexpr int MAXPL = 16;        // planes per ray: 4 Stokes x 4 subrings
 constexpr int RAY_REROUTE = 16;  // internal status: handed to the high-precision pass
+constexpr int RAY_GOING = -1;    // internal status: the ray continues
+
+// A ray's state is kept in two parts, so that the geodesic and the transfer can run on different
+// warps (trace_kernels.cuh): the geodesic part (position, momentum, transported covector, step
+// count, swept angle) and the transfer part (coefficients at the current point, accumulated
+// propagator and planes, turn counting).  The one-thread kernels hold both in one thread.
+template <class R>
+struct GeoState {
+    using Q = typename Aux<R>::Q;
+    RayState<R> s;
+    R kt;
+    Q r, sweep;
+    Q f[4];  // polarized rays: parallel-transported reference covector
+    int steps;
+};
+
+template <class Q>
+struct XferState {
+    Q J0[4], K0[7];  // coefficients at the start of the current step
+    Q P[16];         // polarized rays: accumulated Stokes propagator (camera <- here)
+    Q acc[MAXPL];    // accumulated planes
+    Q T, oz;         // transmission (unpolarized); z of the current point
+    float min_r;
+    int nturn, tsign, crossed;
+};
+
+// The end point of a geodesic step as the transfer part needs it.
+template <class Q>
+struct StepPoint {
+    RayState<Q> q;
+    Q kt, r, h;
+    Q f[4];
+};
 
 template <class R>
 struct Tracer {
     using Q = typename Aux<R>::Q;
-    RayState<R> s;
-    R kt;
-    Q r, T, sweep;
-    Q J0[4], K0[7];   // coefficients at the start of the current step
-    Q f[4];           // polarized rays: parallel-transported reference covector
-    Q P[16];          // polarized rays: accumulated Stokes propagator (camera <- here)
-    Q acc[MAXPL];     // accumulated planes
-    float min_r;
-    int steps, nturn, tsign, status, crossed;
+    GeoState<R> g;
+    XferState<Q> x;
+    int status;
     int32_t pix, img;
     int64_t slot;  // queue position
 };
@@ -162,9 +189,11 @@ __device__ __forceinline__ void coefficients(const RayState<Q>& q, Q r, Q kt, co
     J4[0] = emission_cfg0<Q>(q, r, kt, J);
 }
 
-template <class R, bool POL, int EM>
-__device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const SynchConst& S,
-                                         const Camera& cam, int32_t pix)
+// Geodesic part of a ray's start: camera ray of pixel pix; fills the start point for the transfer
+// part's initialisation.
+template <class R, bool POL>
+__device__ __forceinline__ void geo_init(GeoState<R>& g, const DevJob& J, const Camera& cam,
+                                         int32_t pix, StepPoint<typename Aux<R>::Q>& pt)
 {
     using Q = typename Aux<R>::Q;
     int i = pix % J.nx, j = pix / J.nx;
@@ -175,42 +204,81 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const Sy
     double k[4];
     for (int m = 0; m < 4; ++m)
         k[m] = -cam.E[0][m] + sc * (-cam.E[1][m] + (al / ro) * cam.E[3][m] + (be / ro) * cam.E[2][m]);
-    t.s.x = R(cam.x0[0]);
-    t.s.y = R(cam.x0[1]);
-    t.s.z = R(cam.x0[2]);
-    t.kt = R(k[0]);
-    t.s.kx = R(k[1]);
-    t.s.ky = R(k[2]);
-    t.s.kz = R(k[3]);
+    g.s.x = R(cam.x0[0]);
+    g.s.y = R(cam.x0[1]);
+    g.s.z = R(cam.x0[2]);
+    g.kt = R(k[0]);
+    g.s.kx = R(k[1]);
+    g.s.ky = R(k[2]);
+    g.s.kz = R(k[3]);
     if (POL) {
         // screen-up vector made normal to the line of sight n: e2 - (e2.n) n, e2.n = sc be/ro
         double c = sc * be / ro, nrm = 1.0 / sqrt(1.0 - c * c);
         for (int m = 0; m < 4; ++m) {
             double n = sc * (-cam.E[1][m] + (al / ro) * cam.E[3][m] + (be / ro) * cam.E[2][m]);
-            t.f[m] = Q((cam.E[2][m] - c * n) * nrm);
+            g.f[m] = Q((cam.E[2][m] - c * n) * nrm);
         }
-        for (int m = 0; m < 16; ++m) t.P[m] = (m % 5 == 0) ? Q(1) : Q(0);
     }
-    RayState<Q> q = to_q<Q>(t.s);
-    t.r = ks_radius<Q>(q.x, q.y, q.z, Q(J.a2));
-    coefficients<Q, POL, EM>(q, t.r, Q(t.kt), t.f, J, S, t.J0, t.K0);
-    t.T = Q(1);
-    for (int p = 0; p < MAXPL; ++p) t.acc[p] = Q(0);
-    t.min_r = float(t.r);
-    t.sweep = Q(0);
-    t.steps = 0;
-    t.nturn = 0;
-    t.crossed = 0;
-    t.tsign = polar_sign<Q>(q, t.r);
+    pt.q = to_q<Q>(g.s);
+    g.r = ks_radius<Q>(pt.q.x, pt.q.y, pt.q.z, Q(J.a2));
+    g.sweep = Q(0);
+    g.steps = 0;
+    pt.kt = Q(g.kt);
+    pt.r = g.r;
+    pt.h = Q(0);
+    if (POL)
+        for (int m = 0; m < 4; ++m) pt.f[m] = g.f[m];
+}
+
+// Transfer part of a ray's start: coefficients at the camera point, identity propagator.
+template <class Q, bool POL, int EM>
+__device__ __forceinline__ void xfer_init(XferState<Q>& x, const StepPoint<Q>& pt, const DevJob& J,
+                                          const SynchConst& S)
+{
+    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, x.J0, x.K0);
+    if (POL)
+        for (int m = 0; m < 16; ++m) x.P[m] = (m % 5 == 0) ? Q(1) : Q(0);
+    x.T = Q(1);
+    for (int p = 0; p < MAXPL; ++p) x.acc[p] = Q(0);
+    x.min_r = float(pt.r);
+    x.nturn = 0;
+    x.crossed = 0;
+    x.tsign = polar_sign<Q>(pt.q, pt.r);
+    x.oz = pt.q.z;
+}
+
+template <class R, bool POL, int EM>
+__device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const SynchConst& S,
+                                         const Camera& cam, int32_t pix)
+{
+    StepPoint<typename Aux<R>::Q> pt;
+    geo_init<R, POL>(t.g, J, cam, pix, pt);
+    xfer_init<typename Aux<R>::Q, POL, EM>(t.x, pt, J, S);
     t.status = ART_RAY_CAP;
     t.pix = pix;
 }
 
-// One RK4 step plus the transfer segment; returns true when the ray has terminated.  SWEEP
-// accumulates the angle swept by the position vector (used to route rays in mixed precision);
-// POL carries the polarization covector through the RK4 stages and solves the Stokes segment.
+// y = s + c k (the state of an intermediate RK4 stage)
+template <class R>
+__device__ __forceinline__ void rk4_offset(const RayState<R>& s, R c, const RayState<R>& k,
+                                           RayState<R>& y)
+{
+    y.x = fmad(c, k.x, s.x);
+    y.y = fmad(c, k.y, s.y);
+    y.z = fmad(c, k.z, s.z);
+    y.kx = fmad(c, k.kx, s.kx);
+    y.ky = fmad(c, k.ky, s.ky);
+    y.kz = fmad(c, k.kz, s.kz);
+}
+
+// Geodesic part of one step: RK4 of (x, k) (and of the covector f for polarized rays), the
+// non-finite and swept-angle tests, the end point's radius and the stopping tests.  Returns
+// RAY_GOING, or the ray's final status: ART_RAY_NAN and RAY_REROUTE end the ray before the
+// segment, the other statuses after it.  SWEEP accumulates the angle swept by the position vector
+// (used to route rays in mixed precision).
 template <class R, bool SWEEP, bool POL, int EM>
-__device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const SynchConst& S)
+__device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
+                                        StepPoint<typename Aux<R>::Q>& pt)
 {
     using Q = typename Aux<R>::Q;
     const R a = R(J.a), a2 = R(J.a2);
@@ -220,73 +288,135 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const Sy
     const R h = R(hq);
     const R hh = R(0.5) * h;
     const Q hhq = Q(0.5) * hq;
-    RayState<R> k1, k2, k3, k4, y;
-    Q d1[4], d2[4], d3[4], d4[4], fy[4];
-    geodesic_rhs<R>(t.s, t.kt, a, a2, k1);
-    if (POL) transport_rhs<Q>(to_q<Q>(t.s), Q(t.kt), t.f, aq, a2q, d1);
-    y.x = t.s.x + hh * k1.x; y.y = t.s.y + hh * k1.y; y.z = t.s.z + hh * k1.z;
-    y.kx = t.s.kx + hh * k1.kx; y.ky = t.s.ky + hh * k1.ky; y.kz = t.s.kz + hh * k1.kz;
-    geodesic_rhs<R>(y, t.kt, a, a2, k2);
-    if (POL) {
-        for (int m = 0; m < 4; ++m) fy[m] = t.f[m] + hhq * d1[m];
-        transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d2);
-    }
-    y.x = t.s.x + hh * k2.x; y.y = t.s.y + hh * k2.y; y.z = t.s.z + hh * k2.z;
-    y.kx = t.s.kx + hh * k2.kx; y.ky = t.s.ky + hh * k2.ky; y.kz = t.s.kz + hh * k2.kz;
-    geodesic_rhs<R>(y, t.kt, a, a2, k3);
-    if (POL) {
-        for (int m = 0; m < 4; ++m) fy[m] = t.f[m] + hhq * d2[m];
-        transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d3);
-    }
-    y.x = t.s.x + h * k3.x; y.y = t.s.y + h * k3.y; y.z = t.s.z + h * k3.z;
-    y.kx = t.s.kx + h * k3.kx; y.ky = t.s.ky + h * k3.ky; y.kz = t.s.kz + h * k3.kz;
-    geodesic_rhs<R>(y, t.kt, a, a2, k4);
-    if (POL) {
-        for (int m = 0; m < 4; ++m) fy[m] = t.f[m] + hq * d3[m];
-        transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d4);
+    // ks = k1 + 2 k2 + 2 k3 + k4 (summed in that order) and likewise ds for the polarization.
+    // The polarized analytic-emission kernels run the four stages as one rolled loop, so the
+    // geodesic and transport right-hand sides appear once in their code: the trace kernels are
+    // latency-bound with few warps per SM, and their fully unrolled step no longer fits the
+    // instruction cache (measured: the double-float pass of the polarized disk 2.3x faster).  The
+    // other kernels keep the unrolled stages, which measured faster for them.
+    constexpr bool ROLLED = POL && EM == EM_ANALYTIC;
+    RayState<R> ks;
+    Q ds[4];
+    if (ROLLED) {
+        RayState<R> k, y = t.s;
+        Q d[4], fy[4];
+        for (int m = 0; m < 4; ++m) fy[m] = t.f[m];
+#pragma unroll 1
+        for (int st = 0; st < 4; ++st) {
+            geodesic_rhs<R>(y, t.kt, a, a2, k);
+            transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d);
+            if (st == 0) {
+                ks = k;
+                for (int m = 0; m < 4; ++m) ds[m] = d[m];
+            } else if (st < 3) {
+                ks.x = fmad(R(2), k.x, ks.x); ks.y = fmad(R(2), k.y, ks.y);
+                ks.z = fmad(R(2), k.z, ks.z); ks.kx = fmad(R(2), k.kx, ks.kx);
+                ks.ky = fmad(R(2), k.ky, ks.ky); ks.kz = fmad(R(2), k.kz, ks.kz);
+                for (int m = 0; m < 4; ++m) ds[m] = fmad(Q(2), d[m], ds[m]);
+            } else {
+                ks.x = ks.x + k.x; ks.y = ks.y + k.y; ks.z = ks.z + k.z;
+                ks.kx = ks.kx + k.kx; ks.ky = ks.ky + k.ky; ks.kz = ks.kz + k.kz;
+                for (int m = 0; m < 4; ++m) ds[m] = ds[m] + d[m];
+                break;
+            }
+            const R c = st < 2 ? hh : h;  // offset of the next stage
+            const Q cq = st < 2 ? hhq : hq;
+            rk4_offset(t.s, c, k, y);
+            for (int m = 0; m < 4; ++m) fy[m] = fmad(cq, d[m], t.f[m]);
+        }
+    } else {
+        RayState<R> k1, k2, k3, k4, y;
+        Q d1[4], d2[4], d3[4], d4[4], fy[4];
+        geodesic_rhs<R>(t.s, t.kt, a, a2, k1);
+        if (POL) transport_rhs<Q>(to_q<Q>(t.s), Q(t.kt), t.f, aq, a2q, d1);
+        rk4_offset(t.s, hh, k1, y);
+        geodesic_rhs<R>(y, t.kt, a, a2, k2);
+        if (POL) {
+            for (int m = 0; m < 4; ++m) fy[m] = fmad(hhq, d1[m], t.f[m]);
+            transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d2);
+        }
+        rk4_offset(t.s, hh, k2, y);
+        geodesic_rhs<R>(y, t.kt, a, a2, k3);
+        if (POL) {
+            for (int m = 0; m < 4; ++m) fy[m] = fmad(hhq, d2[m], t.f[m]);
+            transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d3);
+        }
+        rk4_offset(t.s, h, k3, y);
+        geodesic_rhs<R>(y, t.kt, a, a2, k4);
+        if (POL) {
+            for (int m = 0; m < 4; ++m) fy[m] = fmad(hq, d3[m], t.f[m]);
+            transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d4);
+        }
+        ks.x = fmad(R(2), k3.x, fmad(R(2), k2.x, k1.x)) + k4.x;
+        ks.y = fmad(R(2), k3.y, fmad(R(2), k2.y, k1.y)) + k4.y;
+        ks.z = fmad(R(2), k3.z, fmad(R(2), k2.z, k1.z)) + k4.z;
+        ks.kx = fmad(R(2), k3.kx, fmad(R(2), k2.kx, k1.kx)) + k4.kx;
+        ks.ky = fmad(R(2), k3.ky, fmad(R(2), k2.ky, k1.ky)) + k4.ky;
+        ks.kz = fmad(R(2), k3.kz, fmad(R(2), k2.kz, k1.kz)) + k4.kz;
+        if (POL)
+            for (int m = 0; m < 4; ++m)
+                ds[m] = fmad(Q(2), d3[m], fmad(Q(2), d2[m], d1[m])) + d4[m];
     }
     const R h6 = h / R(6);
     const Q ox = Q(t.s.x), oy = Q(t.s.y), oz = Q(t.s.z);
-    t.s.x += h6 * (k1.x + R(2) * k2.x + R(2) * k3.x + k4.x);
-    t.s.y += h6 * (k1.y + R(2) * k2.y + R(2) * k3.y + k4.y);
-    t.s.z += h6 * (k1.z + R(2) * k2.z + R(2) * k3.z + k4.z);
-    t.s.kx += h6 * (k1.kx + R(2) * k2.kx + R(2) * k3.kx + k4.kx);
-    t.s.ky += h6 * (k1.ky + R(2) * k2.ky + R(2) * k3.ky + k4.ky);
-    t.s.kz += h6 * (k1.kz + R(2) * k2.kz + R(2) * k3.kz + k4.kz);
+    t.s.x = fmad(h6, ks.x, t.s.x);
+    t.s.y = fmad(h6, ks.y, t.s.y);
+    t.s.z = fmad(h6, ks.z, t.s.z);
+    t.s.kx = fmad(h6, ks.kx, t.s.kx);
+    t.s.ky = fmad(h6, ks.ky, t.s.ky);
+    t.s.kz = fmad(h6, ks.kz, t.s.kz);
     if (POL) {
         const Q h6q = hq / Q(6);
-        for (int m = 0; m < 4; ++m) t.f[m] += h6q * (d1[m] + Q(2) * d2[m] + Q(2) * d3[m] + d4[m]);
+        for (int m = 0; m < 4; ++m) t.f[m] = fmad(h6q, ds[m], t.f[m]);
     }
     ++t.steps;
     if (!(isfinite(t.s.x) && isfinite(t.s.y) && isfinite(t.s.z) && isfinite(t.s.kx) &&
-          isfinite(t.s.ky) && isfinite(t.s.kz))) {
-        t.status = ART_RAY_NAN;
-        return true;
-    }
+          isfinite(t.s.ky) && isfinite(t.s.kz)))
+        return ART_RAY_NAN;
     const RayState<Q> q = to_q<Q>(t.s);
     if (SWEEP) {
         // |x_old x x_new| / (|x_old| |x_new|): the sine of the angle the position vector turns
-        Q cx = oy * q.z - oz * q.y, cy = oz * q.x - ox * q.z, cz = ox * q.y - oy * q.x;
-        Q n2 = (ox * ox + oy * oy + oz * oz) * (q.x * q.x + q.y * q.y + q.z * q.z);
-        t.sweep += sqrt((cx * cx + cy * cy + cz * cz) / n2);
+        Q cx = fmad(oy, q.z, -(oz * q.y)), cy = fmad(oz, q.x, -(ox * q.z));
+        Q cz = fmad(ox, q.y, -(oy * q.x));
+        Q n2 = fmad(oz, oz, fmad(oy, oy, ox * ox)) * fmad(q.z, q.z, fmad(q.y, q.y, q.x * q.x));
+        t.sweep += sqrt(fmad(cz, cz, fmad(cy, cy, cx * cx)) / n2);
         // a near-critical ray is re-traced at high precision anyway: stop it as soon as it is
         // known to be one (these orbiting rays are also the longest of the FP32 pass)
-        if (t.sweep >= Q(J.fp64_sweep)) {
-            t.status = RAY_REROUTE;
-            return true;
-        }
+        if (t.sweep >= Q(J.fp64_sweep)) return RAY_REROUTE;
     }
     Q rn = ks_radius<Q>(q.x, q.y, q.z, a2q);
+    t.r = rn;
+    pt.q = q;
+    pt.kt = Q(t.kt);
+    pt.r = rn;
+    pt.h = hq;
+    if (POL)
+        for (int m = 0; m < 4; ++m) pt.f[m] = t.f[m];
+    if (rn < Q(J.r_in_stop)) return ART_RAY_CAPTURED;
+    if (rn > Q(J.r_out_stop)) return ART_RAY_ESCAPED;
+    if (t.steps >= J.max_steps) return ART_RAY_CAP;
+    return RAY_GOING;
+}
+
+// Transfer part of one step ending at pt: the coefficients there, the subring index (polar
+// turning points counted from the first equatorial crossing on) and the segment (trapezoid in
+// J and A, or the exact Stokes segment of the averaged coefficients).
+template <class Q, bool POL, int EM>
+__device__ __forceinline__ void xfer_step(XferState<Q>& t, const StepPoint<Q>& pt, const DevJob& J,
+                                          const SynchConst& S)
+{
+    const RayState<Q>& q = pt.q;
+    const Q rn = pt.r, hq = pt.h;
     Q J1[4], K1[7];
-    coefficients<Q, POL, EM>(q, rn, Q(t.kt), t.f, J, S, J1, K1);
-    // subring index: polar turning points counted from the first equatorial crossing on
+    coefficients<Q, POL, EM>(q, rn, pt.kt, pt.f, J, S, J1, K1);
     int seg = t.nturn;
-    if (oz * q.z < Q(0)) t.crossed = 1;
+    if (t.oz * q.z < Q(0)) t.crossed = 1;
     int sg = polar_sign<Q>(q, rn);
     if (sg != 0) {
         if (t.crossed && t.tsign != 0 && sg != t.tsign) ++t.nturn;
         t.tsign = sg;
     }
+    t.oz = q.z;
     const int sub = J.subrings > 0 ? (seg < J.subrings ? seg : J.subrings - 1) : 0;
     if (POL) {
         Q Jb[4], Kb[7];
@@ -317,12 +447,23 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const Sy
     }
     for (int i = 0; i < 4; ++i) t.J0[i] = J1[i];
     for (int i = 0; i < 7; ++i) t.K0[i] = K1[i];
-    t.r = rn;
     if (float(rn) < t.min_r) t.min_r = float(rn);
-    if (rn < Q(J.r_in_stop)) { t.status = ART_RAY_CAPTURED; return true; }
-    if (rn > Q(J.r_out_stop)) { t.status = ART_RAY_ESCAPED; return true; }
-    if (t.steps >= J.max_steps) { t.status = ART_RAY_CAP; return true; }
-    return false;
+}
+
+// One RK4 step plus the transfer segment in one thread; returns true when the ray has terminated.
+template <class R, bool SWEEP, bool POL, int EM>
+__device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const SynchConst& S)
+{
+    StepPoint<typename Aux<R>::Q> pt;
+    const int st = geo_step<R, SWEEP, POL, EM>(t.g, J, pt);
+    if (st == ART_RAY_NAN || st == RAY_REROUTE) {
+        t.status = st;
+        return true;
+    }
+    xfer_step<typename Aux<R>::Q, POL, EM>(t.x, pt, J, S);
+    if (st == RAY_GOING) return false;
+    t.status = st;
+    return true;
 }
 
 }  // namespace art

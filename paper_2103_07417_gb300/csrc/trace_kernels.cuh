@@ -10,25 +10,58 @@
 // of view and depths keep every SM busy; only where a ray's job, camera and output come from
 // differs from the single-image kernel.
 #pragma once
+#include <type_traits>
+
 #include "trace_impl.cuh"
 
 namespace art {
 
-template <class R, bool SWEEP, bool POL, int EM>
-__global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
+// Outputs of a finished ray of the single-image kernels: the re-trace list (FP32 pass of the mixed
+// modes), else its planes, mask, diagnostics and counters.
+template <class Q>
+__device__ __forceinline__ void finish_ray(const TraceArgs& A, int status, int steps,
+                                           const XferState<Q>& x, int32_t pix, int64_t slot)
 {
-    __shared__ Camera cam_s;
-    {
-        const double* src = reinterpret_cast<const double*>(A.cam);
-        double* dst = reinterpret_cast<double*>(&cam_s);
-        for (int q = threadIdx.x; q < (int)(sizeof(Camera) / sizeof(double)); q += blockDim.x)
-            dst[q] = src[q];
+    atomicAdd(A.counters + C_STEPS, (unsigned long long)steps);
+    const bool rer = A.reroute != nullptr &&
+                     (status == RAY_REROUTE || status == ART_RAY_NAN || status == ART_RAY_CAP);
+    if (rer) {
+        unsigned long long w = atomicAdd(A.reroute_count, 1ull);
+        A.reroute[w] = (int32_t)slot;
+        return;
     }
-    __syncthreads();
+    if (status == ART_RAY_CAP) atomicAdd(A.counters + C_CAPPED, 1ull);
+    if (status == ART_RAY_NAN) atomicAdd(A.counters + C_NAN, 1ull);
+    if (A.indirect) atomicAdd(A.counters + C_FP64, 1ull);  // re-trace pass
+    const int np = A.job.planes;
+#pragma unroll
+    for (int p = 0; p < MAXPL; ++p) {
+        if (p < np) {
+            if (A.img) A.img[(int64_t)p * A.npix + pix] = double(x.acc[p]);
+            if (A.out) A.out[slot * np + p] = double(x.acc[p]);
+        }
+    }
+    if (A.img && A.mask)
+        A.mask[pix] = (A.spec_from && (unsigned long long)slot >= *A.spec_from)
+                          ? MASK_SPEC_DONE
+                          : (uint8_t)ART_MASK_TRACED;
+    if (A.img && A.pix_minr) {
+        A.pix_minr[pix] = x.min_r;
+        A.pix_turn[pix] = (float)x.nturn;
+    }
+    if (A.aux_status) A.aux_status[slot] = status;
+    if (A.aux_steps) A.aux_steps[slot] = steps;
+    if (A.aux_nturn) A.aux_nturn[slot] = x.nturn;
+    if (A.aux_minr) A.aux_minr[slot] = x.min_r;
+}
+
+// One-thread form: each lane traces its ray's whole step and refills itself from the queue.
+template <class R, bool SWEEP, bool POL, int EM>
+__device__ __forceinline__ void trace_lanes(const TraceArgs& A, const Camera& cam_s)
+{
     const DevJob& J = A.job;
     const SynchConst& S = A.synch;
     const unsigned long long n = *A.count;
-    const bool mixed32 = (A.reroute != nullptr);
     Tracer<R> t;
     bool active = false;
     auto fetch_next = [&]() {
@@ -50,40 +83,239 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
     while (__any_sync(0xffffffffu, active)) {
         if (active) {
             if (ray_step<R, SWEEP, POL, EM>(t, J, S)) {
-                atomicAdd(A.counters + C_STEPS, (unsigned long long)t.steps);
-                bool rer = mixed32 && (t.status == RAY_REROUTE || t.status == ART_RAY_NAN ||
-                                       t.status == ART_RAY_CAP);
-                if (rer) {
-                    unsigned long long w = atomicAdd(A.reroute_count, 1ull);
-                    A.reroute[w] = (int32_t)t.slot;
-                } else {
-                    if (t.status == ART_RAY_CAP) atomicAdd(A.counters + C_CAPPED, 1ull);
-                    if (t.status == ART_RAY_NAN) atomicAdd(A.counters + C_NAN, 1ull);
-                    if (A.indirect) atomicAdd(A.counters + C_FP64, 1ull);  // re-trace pass
-                    const int np = J.planes;
-#pragma unroll
-                    for (int p = 0; p < MAXPL; ++p) {
-                        if (p < np) {
-                            if (A.img) A.img[(int64_t)p * A.npix + t.pix] = double(t.acc[p]);
-                            if (A.out) A.out[t.slot * np + p] = double(t.acc[p]);
-                        }
-                    }
-                    if (A.img && A.mask)
-                        A.mask[t.pix] = (A.spec_from && (unsigned long long)t.slot >= *A.spec_from)
-                                            ? MASK_SPEC_DONE
-                                            : (uint8_t)ART_MASK_TRACED;
-                    if (A.img && A.pix_minr) {
-                        A.pix_minr[t.pix] = t.min_r;
-                        A.pix_turn[t.pix] = (float)t.nturn;
-                    }
-                    if (A.aux_status) A.aux_status[t.slot] = t.status;
-                    if (A.aux_steps) A.aux_steps[t.slot] = t.steps;
-                    if (A.aux_nturn) A.aux_nturn[t.slot] = t.nturn;
-                    if (A.aux_minr) A.aux_minr[t.slot] = t.min_r;
-                }
+                finish_ray(A, t.status, t.g.steps, t.x, t.pix, t.slot);
                 active = fetch_next();
             }
         }
+    }
+}
+
+// --------------------------------------------------------------------------------------------
+// Warp-pair form.  The trace kernels are latency-bound on most levels: a level's few thousand to
+// few tens of thousands of rays leave most schedulers with one warp or none, so a step costs its
+// whole dependent instruction chain.  Here each pair of warps shares 32 rays: the even warp
+// integrates their geodesics (geo_step), the odd warp their transfer (xfer_step) one step behind,
+// so the two halves of a step overlap.  The geodesic warp hands each step's end point over through
+// a two-slot ring in shared memory guarded by mbarriers (full: written by the geodesic warp;
+// empty: released by the transfer warp).  Records per lane: a new ray (its start point, pixel and
+// queue slot), a step (its end point and the ray's status after it) or idle; the geodesic warp
+// marks the record after which none follows.  Every wait is bounded in time: when a wait runs out
+// on any lane, the warp counts C_SYNCERR and leaves its loop, and the other warp of the pair then
+// runs out of time on its next wait and leaves too.  The arithmetic is that of the one-thread form
+// (the same geo_step and xfer_step, compiled without automatic contraction), so both forms give
+// bit-identical rays.
+// --------------------------------------------------------------------------------------------
+
+constexpr int REC_IDLE = -3, REC_INIT = -2;
+constexpr int SPLIT_SLOTS = 2;
+constexpr long long SPLIT_WAIT_CYCLES = 1ll << 32;  // about 2 s at the SM clock
+
+__device__ __forceinline__ void pair_bar_init(uint64_t* bar, int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(bar)),
+                 "r"(count));
+}
+
+__device__ __forceinline__ void pair_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(bar))
+                 : "memory");
+}
+
+// Wait for the phase of parity `parity` to complete; false once SPLIT_WAIT_CYCLES have passed.
+__device__ __forceinline__ bool pair_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > SPLIT_WAIT_CYCLES) return false;
+    }
+}
+
+// Shared memory of the warp-pair form: the hand-over rings and their mbarriers.
+template <class Q>
+struct PairRing {
+    static constexpr int NPAIR = TRACE_BLOCK / 64;
+    static constexpr int NF = 13;  // x y z kx ky kz kt r h f0..f3
+    Q v[NPAIR][SPLIT_SLOTS][NF][32];
+    int32_t code[NPAIR][SPLIT_SLOTS][32], pix[NPAIR][SPLIT_SLOTS][32];
+    int64_t slot[NPAIR][SPLIT_SLOTS][32];
+    int32_t last[NPAIR][SPLIT_SLOTS];
+    uint64_t full[NPAIR][SPLIT_SLOTS], empty[NPAIR][SPLIT_SLOTS];
+};
+
+template <class Q>
+__device__ __forceinline__ void pair_ring_init(PairRing<Q>& sm)
+{
+    if (threadIdx.x == 0)
+        for (int p = 0; p < PairRing<Q>::NPAIR; ++p)
+            for (int k = 0; k < SPLIT_SLOTS; ++k) {
+                pair_bar_init(&sm.full[p][k], 32);
+                pair_bar_init(&sm.empty[p][k], 32);
+            }
+}
+
+// Warp-pair form (the ring's mbarriers initialised and the block synchronised before the call).
+template <class R, bool SWEEP, bool POL, int EM>
+__device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& cam_s,
+                                            PairRing<typename Aux<R>::Q>& sm)
+{
+    using Q = typename Aux<R>::Q;
+    constexpr int NSL = SPLIT_SLOTS;
+    const DevJob& J = A.job;
+    const SynchConst& S = A.synch;
+    const unsigned long long n = *A.count;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, pr = warp >> 1;
+    if ((warp & 1) == 0) {
+        // geodesic warp
+        GeoState<R> g;
+        bool has = false, drained = false;
+        int32_t pix = 0;
+        int64_t slot = 0;
+        for (int it = 0;; ++it) {
+            const int sl = it % NSL;
+            const uint32_t ph = (uint32_t)(it / NSL) & 1u;
+            if (it >= NSL &&
+                !__all_sync(0xffffffffu, pair_wait(&sm.empty[pr][sl], ph ^ 1u))) {
+                if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
+                return;
+            }
+            StepPoint<Q> pt;
+            int code = REC_IDLE;
+            if (has) {
+                code = geo_step<R, SWEEP, POL, EM>(g, J, pt);
+                if (code != RAY_GOING) has = false;
+            } else if (!drained) {
+                while (true) {
+                    const unsigned long long q = warp_fetch(A.fetch);
+                    if (q >= n) {
+                        drained = true;
+                        break;
+                    }
+                    const int64_t sq = A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
+                    const int32_t px = A.queue[sq];
+                    if (px < 0 || (int64_t)px >= A.npix) {
+                        atomicAdd(A.counters + C_BADIDX, 1ull);
+                        continue;
+                    }
+                    geo_init<R, POL>(g, J, cam_s, px, pt);
+                    pix = px;
+                    slot = sq;
+                    has = true;
+                    code = REC_INIT;
+                    break;
+                }
+            }
+            if (code != REC_IDLE) {
+                Q* v = &sm.v[pr][sl][0][lane];
+                v[0 * 32] = pt.q.x;
+                v[1 * 32] = pt.q.y;
+                v[2 * 32] = pt.q.z;
+                v[3 * 32] = pt.q.kx;
+                v[4 * 32] = pt.q.ky;
+                v[5 * 32] = pt.q.kz;
+                v[6 * 32] = pt.kt;
+                v[7 * 32] = pt.r;
+                v[8 * 32] = pt.h;
+                if (POL)
+                    for (int m = 0; m < 4; ++m) v[(9 + m) * 32] = pt.f[m];
+            }
+            sm.code[pr][sl][lane] = code;
+            sm.pix[pr][sl][lane] = pix;
+            sm.slot[pr][sl][lane] = slot;
+            const bool last = __all_sync(0xffffffffu, code == REC_IDLE && drained);
+            if (lane == 0) sm.last[pr][sl] = last ? 1 : 0;
+            __syncwarp();
+            pair_arrive(&sm.full[pr][sl]);
+            if (last) return;
+        }
+    } else {
+        // transfer warp
+        XferState<Q> x;
+        int32_t pix = 0;
+        int64_t slot = 0;
+        int steps = 0;
+        for (int it = 0;; ++it) {
+            const int sl = it % NSL;
+            const uint32_t ph = (uint32_t)(it / NSL) & 1u;
+            if (!__all_sync(0xffffffffu, pair_wait(&sm.full[pr][sl], ph))) {
+                if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
+                return;
+            }
+            const int code = sm.code[pr][sl][lane];
+            const bool last = sm.last[pr][sl] != 0;
+            StepPoint<Q> pt;
+            if (code != REC_IDLE) {
+                const Q* v = &sm.v[pr][sl][0][lane];
+                pt.q.x = v[0 * 32];
+                pt.q.y = v[1 * 32];
+                pt.q.z = v[2 * 32];
+                pt.q.kx = v[3 * 32];
+                pt.q.ky = v[4 * 32];
+                pt.q.kz = v[5 * 32];
+                pt.kt = v[6 * 32];
+                pt.r = v[7 * 32];
+                pt.h = v[8 * 32];
+                if (POL)
+                    for (int m = 0; m < 4; ++m) pt.f[m] = v[(9 + m) * 32];
+            }
+            if (code == REC_INIT) {
+                pix = sm.pix[pr][sl][lane];
+                slot = sm.slot[pr][sl][lane];
+            }
+            __syncwarp();
+            pair_arrive(&sm.empty[pr][sl]);
+            if (code == REC_INIT) {
+                xfer_init<Q, POL, EM>(x, pt, J, S);
+                steps = 0;
+            } else if (code != REC_IDLE) {
+                ++steps;
+                if (code != ART_RAY_NAN && code != RAY_REROUTE) xfer_step<Q, POL, EM>(x, pt, J, S);
+                if (code != RAY_GOING) finish_ray(A, code, steps, x, pix, slot);
+            }
+            if (last) return;
+        }
+    }
+}
+
+// The single-image trace kernel.  A launch whose queue fits the warp pairs of the grid at once
+// (the latency-bound regime of most levels) runs the warp-pair form; a longer queue, where
+// throughput counts, the one-thread form with twice the rays in flight.  The FP64 kernel is
+// always one-thread.  The choice is uniform over the grid (it depends on the queue length only).
+template <class R, bool SWEEP, bool POL, int EM>
+__global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
+{
+    using Q = typename Aux<R>::Q;
+    __shared__ Camera cam_s;
+    {
+        const double* src = reinterpret_cast<const double*>(A.cam);
+        double* dst = reinterpret_cast<double*>(&cam_s);
+        for (int q = threadIdx.x; q < (int)(sizeof(Camera) / sizeof(double)); q += blockDim.x)
+            dst[q] = src[q];
+    }
+    if constexpr (std::is_same<R, double>::value) {
+        __syncthreads();
+        trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
+    } else {
+        __shared__ __align__(16) PairRing<Q> ring;
+        pair_ring_init(ring);
+        __syncthreads();
+        const unsigned long long pair_lanes =
+            (unsigned long long)gridDim.x * PairRing<Q>::NPAIR * 32ull;
+        if (*A.count <= pair_lanes)
+            trace_pairs<R, SWEEP, POL, EM>(A, cam_s, ring);
+        else
+            trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
     }
 }
 
@@ -117,7 +349,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_batch_kernel(BatchTraceArgs
         if (active) {
             const DevJob& J = A.jobs[t.img];
             if (ray_step<R, SWEEP, POL, EM>(t, J, A.synchs[t.img])) {
-                atomicAdd(A.counters + C_STEPS, (unsigned long long)t.steps);
+                atomicAdd(A.counters + C_STEPS, (unsigned long long)t.g.steps);
                 bool rer = mixed32 && (t.status == RAY_REROUTE || t.status == ART_RAY_NAN ||
                                        t.status == ART_RAY_CAP);
                 if (rer) {
@@ -131,7 +363,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_batch_kernel(BatchTraceArgs
                     double* img = A.imgs[t.img];
 #pragma unroll
                     for (int p = 0; p < MAXPL; ++p)
-                        if (p < A.planes) img[(int64_t)p * npix + t.pix] = double(t.acc[p]);
+                        if (p < A.planes) img[(int64_t)p * npix + t.pix] = double(t.x.acc[p]);
                     uint8_t* mask = A.masks[t.img];
                     if (mask) mask[t.pix] = ART_MASK_TRACED;
                 }

@@ -51,16 +51,27 @@ def test_batch_equals_single_renders(snap, precision, stokes, model):
         else:
             scale = np.maximum(np.abs(r), 1e-6 * np.abs(r).max())
         rel = np.max(np.abs(g - r) / scale)
-        # The two kernels differ only in where the job comes from (a table in memory or a kernel
-        # parameter), which changes the compiler's contraction of multiply-adds: the analytic
-        # models agree to ~1e-13; the grid model's longer chains (exp of arguments ~ -60) to a
-        # few ulps more in FP64.  In its FP32 pass the last-bit differences can also move a ray
-        # whose swept angle sits at the re-trace threshold from one precision to the other, a
-        # change of the size of the FP32 error itself (~1e-4 of I, inside the 1e-5 MSE bound).
-        tol = 1e-12 if model == "disk" else (1e-10 if precision == "fp64" else 1e-3)
-        assert rel <= tol, rel
+        # The two renders run different kernels (the batched one reads each ray's job from a table;
+        # the single-image FP32 and double-float passes may split each step over a pair of warps):
+        # in FP64 the analytic models agree to ~1e-13 and the grid model's longer chains (exp of
+        # arguments ~ -60) to a few ulps more.  In the FP32 pass the last-bit differences are FP32
+        # rounding (~1e-7 of I) and can also move a ray whose swept angle sits at the re-trace
+        # threshold from one precision to the other, a change of the size of the FP32 error
+        # itself (~1e-4 of I, inside the 1e-5 MSE bound).  So the paths with an FP32 pass are held
+        # to: 1e-3 of the pixel's I except on at most 1 % of the pixels (a moved ray and the
+        # pixels interpolated from it), and an MSE between the two (all Stokes planes, relative to
+        # the mean intensity squared) 10x below the mixed path's 1e-5 bound.
+        if precision != "fp64":
+            tol = 1e-3
+            moved = np.abs(g - r) > tol * scale
+            assert moved.mean() <= 1e-2, moved.mean()
+            assert np.mean((g - r) ** 2) / np.mean(r[0]) ** 2 < 1e-6
+        else:
+            tol = 1e-12 if model == "disk" else 1e-10
+            assert rel <= tol, rel
         assert st["rays_per_level"] == ref_st["rays_per_level"]
-        assert st["norm"] == pytest.approx(ref_st["norm"], rel=1e-13)
+        # the normalisation is a statistic of the traced intensities: the same bound
+        assert st["norm"] == pytest.approx(ref_st["norm"], rel=max(tol, 1e-13))
     ctx.close()
 
 
