@@ -16,6 +16,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "dfloat.cuh"
 #include "internal.cuh"
@@ -133,8 +134,19 @@ struct GeoState {
     int steps;
 };
 
+// Where the polarization covector's transport runs: with the geodesic, except for double-float
+// geodesics, whose step is the longer half; there the geodesic half records the intermediate RK4
+// states and the transfer half transports the covector along them.
+template <class R, bool POL>
+struct XportOnGeo {
+    static constexpr bool value = !(std::is_same<R, df>::value && POL);
+};
+constexpr int NSTG = 18;  // the intermediate RK4 states of one step: 3 x (x y z kx ky kz)
+
 template <class Q>
 struct XferState {
+    Q f[4];          // covector, when the transfer half transports it
+    RayState<Q> y0;  // start of the current step, for that transport
     Q J0[4], K0[7];  // coefficients at the start of the current step
     Q P[16];         // polarized rays: accumulated Stokes propagator (camera <- here)
     Q acc[MAXPL];    // accumulated planes
@@ -245,6 +257,9 @@ __device__ __forceinline__ void xfer_init(XferState<Q>& x, const StepPoint<Q>& p
     x.crossed = 0;
     x.tsign = polar_sign<Q>(pt.q, pt.r);
     x.oz = pt.q.z;
+    if (POL)
+        for (int m = 0; m < 4; ++m) x.f[m] = pt.f[m];
+    x.y0 = pt.q;
 }
 
 template <class R, bool POL, int EM>
@@ -276,9 +291,12 @@ __device__ __forceinline__ void rk4_offset(const RayState<R>& s, R c, const RayS
 // RAY_GOING, or the ray's final status: ART_RAY_NAN and RAY_REROUTE end the ray before the
 // segment, the other statuses after it.  SWEEP accumulates the angle swept by the position vector
 // (used to route rays in mixed precision).
+// Stage states are stored at stg[(3 stage + component) * sstride] when the transport runs on the
+// transfer half.
 template <class R, bool SWEEP, bool POL, int EM>
 __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
-                                        StepPoint<typename Aux<R>::Q>& pt)
+                                        StepPoint<typename Aux<R>::Q>& pt,
+                                        typename Aux<R>::Q* stg, int sstride)
 {
     using Q = typename Aux<R>::Q;
     const R a = R(J.a), a2 = R(J.a2);
@@ -289,40 +307,72 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
     const R hh = R(0.5) * h;
     const Q hhq = Q(0.5) * hq;
     // ks = k1 + 2 k2 + 2 k3 + k4 (summed in that order) and likewise ds for the polarization.
-    // The polarized analytic-emission kernels run the four stages as one rolled loop, so the
-    // geodesic and transport right-hand sides appear once in their code: the trace kernels are
-    // latency-bound with few warps per SM, and their fully unrolled step no longer fits the
-    // instruction cache (measured: the double-float pass of the polarized disk 2.3x faster).  The
-    // other kernels keep the unrolled stages, which measured faster for them.
-    constexpr bool ROLLED = POL && EM == EM_ANALYTIC;
+    // The double-float and the polarized analytic-emission kernels run the four stages as one
+    // rolled loop, so the geodesic (and transport) right-hand sides appear once in their code: the
+    // trace kernels are latency-bound with few warps per SM, and their fully unrolled step no
+    // longer fits the instruction cache (measured: the double-float pass of the polarized disk
+    // 2.3x faster).  The other kernels keep the unrolled stages, which measured faster for them.
+    constexpr bool ROLLED = (POL && EM == EM_ANALYTIC) || std::is_same<R, df>::value;
+    constexpr bool XP = XportOnGeo<R, POL>::value;
     RayState<R> ks;
     Q ds[4];
-    if (ROLLED) {
+    if (!XP) {
+        // geodesic only, recording the stage states; rolled for the same reason
+        RayState<R> k, y = t.s;
+#pragma unroll(ROLLED ? 1 : 4)
+        for (int st = 0; st < 4; ++st) {
+            geodesic_rhs<R>(y, t.kt, a, a2, k);
+            if (st == 0) {
+                ks = k;
+            } else if (st < 3) {
+                ks.x = fmad(R(2), k.x, ks.x); ks.y = fmad(R(2), k.y, ks.y);
+                ks.z = fmad(R(2), k.z, ks.z); ks.kx = fmad(R(2), k.kx, ks.kx);
+                ks.ky = fmad(R(2), k.ky, ks.ky); ks.kz = fmad(R(2), k.kz, ks.kz);
+            } else {
+                ks.x = ks.x + k.x; ks.y = ks.y + k.y; ks.z = ks.z + k.z;
+                ks.kx = ks.kx + k.kx; ks.ky = ks.ky + k.ky; ks.kz = ks.kz + k.kz;
+                break;
+            }
+            rk4_offset(t.s, st < 2 ? hh : h, k, y);
+            const RayState<Q> yq = to_q<Q>(y);
+            Q* o = stg + 6 * st * sstride;
+            o[0] = yq.x;
+            o[sstride] = yq.y;
+            o[2 * sstride] = yq.z;
+            o[3 * sstride] = yq.kx;
+            o[4 * sstride] = yq.ky;
+            o[5 * sstride] = yq.kz;
+        }
+    } else if (ROLLED) {
         RayState<R> k, y = t.s;
         Q d[4], fy[4];
         for (int m = 0; m < 4; ++m) fy[m] = t.f[m];
 #pragma unroll 1
         for (int st = 0; st < 4; ++st) {
             geodesic_rhs<R>(y, t.kt, a, a2, k);
-            transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d);
+            if (POL) transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d);
             if (st == 0) {
                 ks = k;
-                for (int m = 0; m < 4; ++m) ds[m] = d[m];
+                if (POL)
+                    for (int m = 0; m < 4; ++m) ds[m] = d[m];
             } else if (st < 3) {
                 ks.x = fmad(R(2), k.x, ks.x); ks.y = fmad(R(2), k.y, ks.y);
                 ks.z = fmad(R(2), k.z, ks.z); ks.kx = fmad(R(2), k.kx, ks.kx);
                 ks.ky = fmad(R(2), k.ky, ks.ky); ks.kz = fmad(R(2), k.kz, ks.kz);
-                for (int m = 0; m < 4; ++m) ds[m] = fmad(Q(2), d[m], ds[m]);
+                if (POL)
+                    for (int m = 0; m < 4; ++m) ds[m] = fmad(Q(2), d[m], ds[m]);
             } else {
                 ks.x = ks.x + k.x; ks.y = ks.y + k.y; ks.z = ks.z + k.z;
                 ks.kx = ks.kx + k.kx; ks.ky = ks.ky + k.ky; ks.kz = ks.kz + k.kz;
-                for (int m = 0; m < 4; ++m) ds[m] = ds[m] + d[m];
+                if (POL)
+                    for (int m = 0; m < 4; ++m) ds[m] = ds[m] + d[m];
                 break;
             }
             const R c = st < 2 ? hh : h;  // offset of the next stage
             const Q cq = st < 2 ? hhq : hq;
             rk4_offset(t.s, c, k, y);
-            for (int m = 0; m < 4; ++m) fy[m] = fmad(cq, d[m], t.f[m]);
+            if (POL)
+                for (int m = 0; m < 4; ++m) fy[m] = fmad(cq, d[m], t.f[m]);
         }
     } else {
         RayState<R> k1, k2, k3, k4, y;
@@ -365,7 +415,7 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
     t.s.kx = fmad(h6, ks.kx, t.s.kx);
     t.s.ky = fmad(h6, ks.ky, t.s.ky);
     t.s.kz = fmad(h6, ks.kz, t.s.kz);
-    if (POL) {
+    if (POL && XP) {
         const Q h6q = hq / Q(6);
         for (int m = 0; m < 4; ++m) t.f[m] = fmad(h6q, ds[m], t.f[m]);
     }
@@ -390,7 +440,7 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
     pt.kt = Q(t.kt);
     pt.r = rn;
     pt.h = hq;
-    if (POL)
+    if (POL && XP)
         for (int m = 0; m < 4; ++m) pt.f[m] = t.f[m];
     if (rn < Q(J.r_in_stop)) return ART_RAY_CAPTURED;
     if (rn > Q(J.r_out_stop)) return ART_RAY_ESCAPED;
@@ -450,17 +500,59 @@ __device__ __forceinline__ void xfer_step(XferState<Q>& t, const StepPoint<Q>& p
     if (float(rn) < t.min_r) t.min_r = float(rn);
 }
 
+// The covector's RK4 step on the transfer half, along the stage states recorded by the geodesic
+// half (stg as in geo_step); leaves the transported covector in pt.f and the step's end point as
+// the next start.
+template <class Q>
+__device__ __forceinline__ void xfer_transport(XferState<Q>& x, StepPoint<Q>& pt, const Q* stg,
+                                               int sstride, const DevJob& J)
+{
+    const Q aq = Q(J.a), a2q = Q(J.a2), hq = pt.h, hhq = Q(0.5) * hq;
+    Q d[4], ds[4], fy[4];
+    RayState<Q> y = x.y0;
+#pragma unroll 1
+    for (int st = 0; st < 4; ++st) {
+        transport_rhs<Q>(y, pt.kt, st == 0 ? x.f : fy, aq, a2q, d);
+        if (st == 0) {
+            for (int m = 0; m < 4; ++m) ds[m] = d[m];
+        } else if (st < 3) {
+            for (int m = 0; m < 4; ++m) ds[m] = fmad(Q(2), d[m], ds[m]);
+        } else {
+            for (int m = 0; m < 4; ++m) ds[m] = ds[m] + d[m];
+            break;
+        }
+        const Q cq = st < 2 ? hhq : hq;
+        for (int m = 0; m < 4; ++m) fy[m] = fmad(cq, d[m], x.f[m]);
+        const Q* o = stg + 6 * st * sstride;
+        y.x = o[0];
+        y.y = o[sstride];
+        y.z = o[2 * sstride];
+        y.kx = o[3 * sstride];
+        y.ky = o[4 * sstride];
+        y.kz = o[5 * sstride];
+    }
+    const Q h6q = hq / Q(6);
+    for (int m = 0; m < 4; ++m) {
+        x.f[m] = fmad(h6q, ds[m], x.f[m]);
+        pt.f[m] = x.f[m];
+    }
+    x.y0 = pt.q;
+}
+
 // One RK4 step plus the transfer segment in one thread; returns true when the ray has terminated.
 template <class R, bool SWEEP, bool POL, int EM>
 __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const SynchConst& S)
 {
-    StepPoint<typename Aux<R>::Q> pt;
-    const int st = geo_step<R, SWEEP, POL, EM>(t.g, J, pt);
+    using Q = typename Aux<R>::Q;
+    StepPoint<Q> pt;
+    Q stg[XportOnGeo<R, POL>::value ? 1 : NSTG];
+    const int st = geo_step<R, SWEEP, POL, EM>(t.g, J, pt, stg, 1);
     if (st == ART_RAY_NAN || st == RAY_REROUTE) {
         t.status = st;
         return true;
     }
-    xfer_step<typename Aux<R>::Q, POL, EM>(t.x, pt, J, S);
+    if (!XportOnGeo<R, POL>::value) xfer_transport<Q>(t.x, pt, stg, 1, J);
+    xfer_step<Q, POL, EM>(t.x, pt, J, S);
     if (st == RAY_GOING) return false;
     t.status = st;
     return true;

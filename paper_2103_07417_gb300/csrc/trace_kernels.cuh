@@ -142,11 +142,12 @@ __device__ __forceinline__ bool pair_wait(uint64_t* bar, uint32_t parity)
     }
 }
 
-// Shared memory of the warp-pair form: the hand-over rings and their mbarriers.
-template <class Q>
+// Shared memory of the warp-pair form: the hand-over rings and their mbarriers.  Fields per lane:
+// x y z kx ky kz kt r h f0..f3, then (transport on the transfer half) the NSTG stage values.
+template <class Q, int NF>
 struct PairRing {
     static constexpr int NPAIR = TRACE_BLOCK / 64;
-    static constexpr int NF = 13;  // x y z kx ky kz kt r h f0..f3
+    static constexpr int STG = NF > 13 ? 13 : 0;  // first stage field (0: none carried)
     Q v[NPAIR][SPLIT_SLOTS][NF][32];
     int32_t code[NPAIR][SPLIT_SLOTS][32], pix[NPAIR][SPLIT_SLOTS][32];
     int64_t slot[NPAIR][SPLIT_SLOTS][32];
@@ -154,11 +155,11 @@ struct PairRing {
     uint64_t full[NPAIR][SPLIT_SLOTS], empty[NPAIR][SPLIT_SLOTS];
 };
 
-template <class Q>
-__device__ __forceinline__ void pair_ring_init(PairRing<Q>& sm)
+template <class Ring>
+__device__ __forceinline__ void pair_ring_init(Ring& sm)
 {
     if (threadIdx.x == 0)
-        for (int p = 0; p < PairRing<Q>::NPAIR; ++p)
+        for (int p = 0; p < Ring::NPAIR; ++p)
             for (int k = 0; k < SPLIT_SLOTS; ++k) {
                 pair_bar_init(&sm.full[p][k], 32);
                 pair_bar_init(&sm.empty[p][k], 32);
@@ -166,9 +167,12 @@ __device__ __forceinline__ void pair_ring_init(PairRing<Q>& sm)
 }
 
 // Warp-pair form (the ring's mbarriers initialised and the block synchronised before the call).
+template <class R, bool POL>
+using PairRingOf = PairRing<typename Aux<R>::Q, XportOnGeo<R, POL>::value ? 13 : 13 + NSTG>;
+
 template <class R, bool SWEEP, bool POL, int EM>
 __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& cam_s,
-                                            PairRing<typename Aux<R>::Q>& sm)
+                                            PairRingOf<R, POL>& sm)
 {
     using Q = typename Aux<R>::Q;
     constexpr int NSL = SPLIT_SLOTS;
@@ -193,7 +197,7 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
             StepPoint<Q> pt;
             int code = REC_IDLE;
             if (has) {
-                code = geo_step<R, SWEEP, POL, EM>(g, J, pt);
+                code = geo_step<R, SWEEP, POL, EM>(g, J, pt, &sm.v[pr][sl][PairRingOf<R, POL>::STG][lane], 32);
                 if (code != RAY_GOING) has = false;
             } else if (!drained) {
                 while (true) {
@@ -273,6 +277,10 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
                 pix = sm.pix[pr][sl][lane];
                 slot = sm.slot[pr][sl][lane];
             }
+            const bool moving = code != REC_IDLE && code != REC_INIT && code != ART_RAY_NAN &&
+                                code != RAY_REROUTE;
+            if (!XportOnGeo<R, POL>::value && moving)
+                xfer_transport<Q>(x, pt, &sm.v[pr][sl][PairRingOf<R, POL>::STG][lane], 32, J);
             __syncwarp();
             pair_arrive(&sm.empty[pr][sl]);
             if (code == REC_INIT) {
@@ -280,7 +288,7 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
                 steps = 0;
             } else if (code != REC_IDLE) {
                 ++steps;
-                if (code != ART_RAY_NAN && code != RAY_REROUTE) xfer_step<Q, POL, EM>(x, pt, J, S);
+                if (moving) xfer_step<Q, POL, EM>(x, pt, J, S);
                 if (code != RAY_GOING) finish_ray(A, code, steps, x, pix, slot);
             }
             if (last) return;
@@ -307,11 +315,11 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
         __syncthreads();
         trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
     } else {
-        __shared__ __align__(16) PairRing<Q> ring;
+        __shared__ __align__(16) PairRingOf<R, POL> ring;
         pair_ring_init(ring);
         __syncthreads();
         const unsigned long long pair_lanes =
-            (unsigned long long)gridDim.x * PairRing<Q>::NPAIR * 32ull;
+            (unsigned long long)gridDim.x * PairRingOf<R, POL>::NPAIR * 32ull;
         if (*A.count <= pair_lanes)
             trace_pairs<R, SWEEP, POL, EM>(A, cam_s, ring);
         else
