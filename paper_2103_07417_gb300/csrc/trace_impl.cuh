@@ -242,12 +242,14 @@ __device__ __forceinline__ void geo_init(GeoState<R>& g, const DevJob& J, const 
         for (int m = 0; m < 4; ++m) pt.f[m] = g.f[m];
 }
 
-// Transfer part of a ray's start: coefficients at the camera point, identity propagator.
-template <class Q, bool POL, int EM>
-__device__ __forceinline__ void xfer_init(XferState<Q>& x, const StepPoint<Q>& pt, const DevJob& J,
-                                          const SynchConst& S)
+// Transfer part of a ray's start, given the coefficients J1, K1 at the camera point: identity
+// propagator, empty planes, turn counting from there.
+template <class Q, bool POL>
+__device__ __forceinline__ void xfer_init_with(XferState<Q>& x, const StepPoint<Q>& pt,
+                                               const Q* J1, const Q* K1)
 {
-    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, x.J0, x.K0);
+    for (int i = 0; i < 4; ++i) x.J0[i] = J1[i];
+    for (int i = 0; i < 7; ++i) x.K0[i] = K1[i];
     if (POL)
         for (int m = 0; m < 16; ++m) x.P[m] = (m % 5 == 0) ? Q(1) : Q(0);
     x.T = Q(1);
@@ -260,6 +262,16 @@ __device__ __forceinline__ void xfer_init(XferState<Q>& x, const StepPoint<Q>& p
     if (POL)
         for (int m = 0; m < 4; ++m) x.f[m] = pt.f[m];
     x.y0 = pt.q;
+}
+
+// Transfer part of a ray's start: coefficients at the camera point, identity propagator.
+template <class Q, bool POL, int EM>
+__device__ __forceinline__ void xfer_init(XferState<Q>& x, const StepPoint<Q>& pt, const DevJob& J,
+                                          const SynchConst& S)
+{
+    Q J1[4], K1[7];
+    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1);
+    xfer_init_with<Q, POL>(x, pt, J1, K1);
 }
 
 template <class R, bool POL, int EM>
@@ -448,17 +460,15 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
     return RAY_GOING;
 }
 
-// Transfer part of one step ending at pt: the coefficients there, the subring index (polar
-// turning points counted from the first equatorial crossing on) and the segment (trapezoid in
-// J and A, or the exact Stokes segment of the averaged coefficients).
-template <class Q, bool POL, int EM>
-__device__ __forceinline__ void xfer_step(XferState<Q>& t, const StepPoint<Q>& pt, const DevJob& J,
-                                          const SynchConst& S)
+// Transfer part of one step ending at pt, given the coefficients J1, K1 there: the subring index
+// (polar turning points counted from the first equatorial crossing on) and the segment (trapezoid
+// in J and A, or the exact Stokes segment of the averaged coefficients).
+template <class Q, bool POL>
+__device__ __forceinline__ void xfer_apply(XferState<Q>& t, const StepPoint<Q>& pt, const Q* J1,
+                                           const Q* K1, const DevJob& J)
 {
     const RayState<Q>& q = pt.q;
     const Q rn = pt.r, hq = pt.h;
-    Q J1[4], K1[7];
-    coefficients<Q, POL, EM>(q, rn, pt.kt, pt.f, J, S, J1, K1);
     int seg = t.nturn;
     if (t.oz * q.z < Q(0)) t.crossed = 1;
     int sg = polar_sign<Q>(q, rn);
@@ -498,6 +508,16 @@ __device__ __forceinline__ void xfer_step(XferState<Q>& t, const StepPoint<Q>& p
     for (int i = 0; i < 4; ++i) t.J0[i] = J1[i];
     for (int i = 0; i < 7; ++i) t.K0[i] = K1[i];
     if (float(rn) < t.min_r) t.min_r = float(rn);
+}
+
+// Transfer part of one step ending at pt: the coefficients there, then xfer_apply.
+template <class Q, bool POL, int EM>
+__device__ __forceinline__ void xfer_step(XferState<Q>& t, const StepPoint<Q>& pt, const DevJob& J,
+                                          const SynchConst& S)
+{
+    Q J1[4], K1[7];
+    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1);
+    xfer_apply<Q, POL>(t, pt, J1, K1, J);
 }
 
 // The covector's RK4 step on the transfer half, along the stage states recorded by the geodesic

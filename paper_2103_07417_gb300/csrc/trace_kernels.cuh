@@ -296,6 +296,221 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
     }
 }
 
+// --------------------------------------------------------------------------------------------
+// Warp-quad form (FP32 kernels).  In the warp-pair form the transfer warp is the slower half: the
+// emission coefficients at a point are a long dependent chain, but a pure function of the point,
+// so consecutive steps' coefficients can be computed at the same time.  Here a block's four warps
+// share 32 rays: warp 0 integrates the geodesics (and transports the covector), warps 1 and 2
+// compute the coefficients at the end points of the even and the odd steps, and warp 3 applies
+// the segments in order and finishes the rays.  Ring A (four slots) carries the geodesic warp's
+// records to the coefficient warp of that step's parity and to the segment warp (its slot is free
+// once both have read it); ring C (four slots) carries the coefficients to the segment warp.  The
+// geodesic warp ends with two records marked last, one for each coefficient warp; the segment
+// warp leaves after the second.  Waits are bounded as in the pair form.  The arithmetic is that of
+// the other forms (the same geo_step, coefficients and xfer_apply), so the rays are identical.
+// --------------------------------------------------------------------------------------------
+
+constexpr int QUAD_SLOTS = 4;
+// Queues of up to this many rays per block take the quad form (one group of 32 rays per block
+// at once; longer queues are drained by the same warps in turn).
+constexpr unsigned long long QUAD_RAYS = 32;
+
+template <class Q>
+struct QuadRing {
+    Q a[QUAD_SLOTS][13][32];  // end point records: x y z kx ky kz kt r h f0..f3
+    int32_t code[QUAD_SLOTS][32], pix[QUAD_SLOTS][32];
+    int64_t slot[QUAD_SLOTS][32];
+    int32_t last[QUAD_SLOTS];
+    Q c[QUAD_SLOTS][11][32];  // J1 (4) and K1 (7) at the record's point
+    uint64_t a_full[QUAD_SLOTS], a_empty[QUAD_SLOTS], c_full[QUAD_SLOTS], c_empty[QUAD_SLOTS];
+};
+
+template <class Q>
+__device__ __forceinline__ void quad_ring_init(QuadRing<Q>& sm)
+{
+    if (threadIdx.x == 0)
+        for (int k = 0; k < QUAD_SLOTS; ++k) {
+            pair_bar_init(&sm.a_full[k], 32);
+            pair_bar_init(&sm.a_empty[k], 64);  // the coefficient warp of the step and the segment warp
+            pair_bar_init(&sm.c_full[k], 32);
+            pair_bar_init(&sm.c_empty[k], 32);
+        }
+}
+
+template <class Q, bool POL>
+__device__ __forceinline__ void quad_read_point(const QuadRing<Q>& sm, int sl, int lane,
+                                                StepPoint<Q>& pt)
+{
+    pt.q.x = sm.a[sl][0][lane];
+    pt.q.y = sm.a[sl][1][lane];
+    pt.q.z = sm.a[sl][2][lane];
+    pt.q.kx = sm.a[sl][3][lane];
+    pt.q.ky = sm.a[sl][4][lane];
+    pt.q.kz = sm.a[sl][5][lane];
+    pt.kt = sm.a[sl][6][lane];
+    pt.r = sm.a[sl][7][lane];
+    pt.h = sm.a[sl][8][lane];
+    if (POL)
+        for (int m = 0; m < 4; ++m) pt.f[m] = sm.a[sl][9 + m][lane];
+}
+
+// Warp-quad form (ring mbarriers initialised and the block synchronised before the call).
+template <bool SWEEP, bool POL, int EM>
+__device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& cam_s,
+                                            QuadRing<float>& sm)
+{
+    using Q = float;
+    constexpr int NSL = QUAD_SLOTS;
+    const DevJob& J = A.job;
+    const SynchConst& S = A.synch;
+    const unsigned long long n = *A.count;
+    const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
+    if (role == 0) {
+        // geodesic warp
+        GeoState<float> g;
+        bool has = false, drained = false;
+        int32_t pix = 0;
+        int64_t slot = 0;
+        int nlast = 0;
+        for (int it = 0;; ++it) {
+            const int sl = it % NSL;
+            const uint32_t ph = (uint32_t)(it / NSL) & 1u;
+            if (it >= NSL && !__all_sync(0xffffffffu, pair_wait(&sm.a_empty[sl], ph ^ 1u))) {
+                if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
+                return;
+            }
+            StepPoint<Q> pt;
+            int code = REC_IDLE;
+            if (has) {
+                code = geo_step<float, SWEEP, POL, EM>(g, J, pt, nullptr, 0);
+                if (code != RAY_GOING) has = false;
+            } else if (!drained) {
+                while (true) {
+                    const unsigned long long q = warp_fetch(A.fetch);
+                    if (q >= n) {
+                        drained = true;
+                        break;
+                    }
+                    const int64_t sq = A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
+                    const int32_t px = A.queue[sq];
+                    if (px < 0 || (int64_t)px >= A.npix) {
+                        atomicAdd(A.counters + C_BADIDX, 1ull);
+                        continue;
+                    }
+                    geo_init<float, POL>(g, J, cam_s, px, pt);
+                    pix = px;
+                    slot = sq;
+                    has = true;
+                    code = REC_INIT;
+                    break;
+                }
+            }
+            if (code != REC_IDLE) {
+                sm.a[sl][0][lane] = pt.q.x;
+                sm.a[sl][1][lane] = pt.q.y;
+                sm.a[sl][2][lane] = pt.q.z;
+                sm.a[sl][3][lane] = pt.q.kx;
+                sm.a[sl][4][lane] = pt.q.ky;
+                sm.a[sl][5][lane] = pt.q.kz;
+                sm.a[sl][6][lane] = pt.kt;
+                sm.a[sl][7][lane] = pt.r;
+                sm.a[sl][8][lane] = pt.h;
+                if (POL)
+                    for (int m = 0; m < 4; ++m) sm.a[sl][9 + m][lane] = pt.f[m];
+            }
+            sm.code[sl][lane] = code;
+            sm.pix[sl][lane] = pix;
+            sm.slot[sl][lane] = slot;
+            const bool last = __all_sync(0xffffffffu, code == REC_IDLE && drained);
+            if (lane == 0) sm.last[sl] = last ? 1 : 0;
+            __syncwarp();
+            pair_arrive(&sm.a_full[sl]);
+            if (last && ++nlast == 2) return;  // one last record for each coefficient warp
+        }
+    } else if (role < 3) {
+        // coefficient warp of the even (role 1) or odd (role 2) steps
+        for (int it = role - 1;; it += 2) {
+            const int sl = it % NSL;
+            const uint32_t ph = (uint32_t)(it / NSL) & 1u;
+            if (!__all_sync(0xffffffffu, pair_wait(&sm.a_full[sl], ph))) {
+                if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
+                return;
+            }
+            const int code = sm.code[sl][lane];
+            const bool last = sm.last[sl] != 0;
+            StepPoint<Q> pt;
+            const bool need = code == REC_INIT ||
+                              (code != REC_IDLE && code != ART_RAY_NAN && code != RAY_REROUTE);
+            if (need) quad_read_point<Q, POL>(sm, sl, lane, pt);
+            __syncwarp();
+            pair_arrive(&sm.a_empty[sl]);
+            Q J1[4], K1[7];
+            if (need) coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1);
+            if (it >= NSL && !__all_sync(0xffffffffu, pair_wait(&sm.c_empty[sl], ph ^ 1u))) {
+                if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
+                return;
+            }
+            if (need) {
+                for (int i = 0; i < 4; ++i) sm.c[sl][i][lane] = J1[i];
+                for (int i = 0; i < 7; ++i) sm.c[sl][4 + i][lane] = K1[i];
+            }
+            __syncwarp();
+            pair_arrive(&sm.c_full[sl]);
+            if (last) return;
+        }
+    } else {
+        // segment warp
+        XferState<Q> x;
+        int32_t pix = 0;
+        int64_t slot = 0;
+        int steps = 0;
+        bool prev_last = false;
+        for (int it = 0;; ++it) {
+            const int sl = it % NSL;
+            const uint32_t ph = (uint32_t)(it / NSL) & 1u;
+            if (!__all_sync(0xffffffffu, pair_wait(&sm.a_full[sl], ph))) {
+                if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
+                return;
+            }
+            const int code = sm.code[sl][lane];
+            const bool last = sm.last[sl] != 0;
+            const bool moving = code != REC_IDLE && code != REC_INIT && code != ART_RAY_NAN &&
+                                code != RAY_REROUTE;
+            StepPoint<Q> pt;
+            if (code == REC_INIT || moving) quad_read_point<Q, POL>(sm, sl, lane, pt);
+            if (code == REC_INIT) {
+                pix = sm.pix[sl][lane];
+                slot = sm.slot[sl][lane];
+            }
+            __syncwarp();
+            pair_arrive(&sm.a_empty[sl]);
+            if (!__all_sync(0xffffffffu, pair_wait(&sm.c_full[sl], ph))) {
+                if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
+                return;
+            }
+            Q J1[4], K1[7];
+            if (code == REC_INIT || moving) {
+                for (int i = 0; i < 4; ++i) J1[i] = sm.c[sl][i][lane];
+                for (int i = 0; i < 7; ++i) K1[i] = sm.c[sl][4 + i][lane];
+            }
+            __syncwarp();
+            pair_arrive(&sm.c_empty[sl]);
+            if (code == REC_INIT) {
+                xfer_init_with<Q, POL>(x, pt, J1, K1);
+                steps = 0;
+            } else if (code != REC_IDLE) {
+                ++steps;
+                if (moving) xfer_apply<Q, POL>(x, pt, J1, K1, J);
+                if (code != RAY_GOING) finish_ray(A, code, steps, x, pix, slot);
+            }
+            if (last) {
+                if (prev_last) return;
+                prev_last = true;
+            }
+        }
+    }
+}
+
 // The single-image trace kernel.  A launch whose queue fits the warp pairs of the grid at once
 // (the latency-bound regime of most levels) runs the warp-pair form; a longer queue, where
 // throughput counts, the one-thread form with twice the rays in flight.  The FP64 kernel is
@@ -317,13 +532,26 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
     } else {
         __shared__ __align__(16) PairRingOf<R, POL> ring;
         pair_ring_init(ring);
-        __syncthreads();
-        const unsigned long long pair_lanes =
-            (unsigned long long)gridDim.x * PairRingOf<R, POL>::NPAIR * 32ull;
-        if (*A.count <= pair_lanes)
-            trace_pairs<R, SWEEP, POL, EM>(A, cam_s, ring);
-        else
-            trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
+        if constexpr (std::is_same<R, float>::value) {
+            __shared__ __align__(16) QuadRing<float> qring;
+            quad_ring_init(qring);
+            __syncthreads();
+            const unsigned long long n = *A.count, blocks = gridDim.x;
+            if (n <= blocks * QUAD_RAYS)
+                trace_quads<SWEEP, POL, EM>(A, cam_s, qring);
+            else if (n <= blocks * PairRingOf<R, POL>::NPAIR * 32ull)
+                trace_pairs<R, SWEEP, POL, EM>(A, cam_s, ring);
+            else
+                trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
+        } else {
+            __syncthreads();
+            const unsigned long long pair_lanes =
+                (unsigned long long)gridDim.x * PairRingOf<R, POL>::NPAIR * 32ull;
+            if (*A.count <= pair_lanes)
+                trace_pairs<R, SWEEP, POL, EM>(A, cam_s, ring);
+            else
+                trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
+        }
     }
 }
 
