@@ -311,9 +311,10 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
 // --------------------------------------------------------------------------------------------
 
 constexpr int QUAD_SLOTS = 4;
-// Queues of up to this many rays per block take the quad form (one group of 32 rays per block
-// at once; longer queues are drained by the same warps in turn).
-constexpr unsigned long long QUAD_RAYS = 32;
+// Queues of up to QUAD_RAYS rays per block take the quad form (one group of 32 rays per block at
+// once; longer queues are drained by the same warps in turn), up to PAIR_RAYS the pair form
+// (FP32 kernels).
+constexpr unsigned long long QUAD_RAYS = 32, PAIR_RAYS = 64;
 
 template <class Q>
 struct QuadRing {
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
             const unsigned long long n = *A.count, blocks = gridDim.x;
             if (n <= blocks * QUAD_RAYS)
                 trace_quads<SWEEP, POL, EM>(A, cam_s, qring);
-            else if (n <= blocks * PairRingOf<R, POL>::NPAIR * 32ull)
+            else if (n <= blocks * PAIR_RAYS)
                 trace_pairs<R, SWEEP, POL, EM>(A, cam_s, ring);
             else
                 trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
