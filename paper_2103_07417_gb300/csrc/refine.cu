@@ -133,6 +133,7 @@ cudaError_t launch_norm(const DevJob& J, const double* img, int nx, int ny, int 
 // Sum of the two central second differences along one line through the point (inner
 // neighbours at -/+ d, outer at -/+ 3d): I(-3) - I(-1) - I(+1) + I(+3); where one outer point is
 // outside the image, twice the one second difference available; where none is, ok = false.
+template <class IX>
 __device__ __forceinline__ double second_diff_sum(const double* img, int nx, int ny, int i, int j,
                                                   int di, int dj, double Im, double Ip, bool& ok)
 {
@@ -140,11 +141,11 @@ __device__ __forceinline__ double second_diff_sum(const double* img, int nx, int
     const bool has_m = iom >= 0 && iom < nx && jom >= 0 && jom < ny;
     const bool has_p = iop >= 0 && iop < nx && jop >= 0 && jop < ny;
     if (has_m && has_p) {
-        double Om = __ldg(img + (int64_t)jom * nx + iom), Op = __ldg(img + (int64_t)jop * nx + iop);
+        double Om = __ldg(img + (IX)jom * nx + iom), Op = __ldg(img + (IX)jop * nx + iop);
         return ((Om - Im) - Ip) + Op;
     }
-    if (has_m) return 2.0 * ((__ldg(img + (int64_t)jom * nx + iom) - 2.0 * Im) + Ip);
-    if (has_p) return 2.0 * ((__ldg(img + (int64_t)jop * nx + iop) - 2.0 * Ip) + Im);
+    if (has_m) return 2.0 * ((__ldg(img + (IX)jom * nx + iom) - 2.0 * Im) + Ip);
+    if (has_p) return 2.0 * ((__ldg(img + (IX)jop * nx + iop) - 2.0 * Ip) + Im);
     ok = false;
     return 0.0;
 }
@@ -155,18 +156,19 @@ __device__ __forceinline__ double second_diff_sum(const double* img, int nx, int
 // Nearest: sqrt(((I4-I1)/2)^2 + ((I3-I2)/2)^2) [centre] or |I2-I1|/2 [midpoints] over norm and
 // over |I1|, interpolant I1.  Decision: trace iff eps_abs > R_abs && eps_rel > R_rel (strict);
 // NaN traces; a line without any outer point gives +inf.
+template <class IX>
 __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i, int j, int s,
-                                      double norm, int cat, double& w1, double& w2, int64_t& p1,
-                                      int64_t& p2, int64_t& p3, int64_t& p4)
+                                      double norm, int cat, double& w1, double& w2, IX& p1, IX& p2,
+                                      IX& p3, IX& p4)
 {
     const int nx = J.nx, ny = J.ny;
     bool ok = true;
     double num, sin_, i1, den;
     if (cat == 4) {
-        p1 = (int64_t)(j - s) * nx + (i - s);  // point 1
-        p4 = (int64_t)(j + s) * nx + (i + s);  // point 4 (opposite 1)
-        p2 = (int64_t)(j + s) * nx + (i - s);  // point 2
-        p3 = (int64_t)(j - s) * nx + (i + s);  // point 3 (opposite 2)
+        p1 = (IX)(j - s) * nx + (i - s);  // point 1
+        p4 = (IX)(j + s) * nx + (i + s);  // point 4 (opposite 1)
+        p2 = (IX)(j + s) * nx + (i - s);  // point 2
+        p3 = (IX)(j - s) * nx + (i + s);  // point 3 (opposite 2)
         double I1 = __ldg(img + p1), I4 = __ldg(img + p4), I2 = __ldg(img + p2), I3 = __ldg(img + p3);
         sin_ = ((I1 + I2) + I3) + I4;
         i1 = I1;
@@ -177,8 +179,8 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
             w2 = 0.0;
             den = fabs(i1);
         } else {
-            double dA = second_diff_sum(img, nx, ny, i, j, s, s, I1, I4, ok);
-            double dB = second_diff_sum(img, nx, ny, i, j, s, -s, I2, I3, ok);
+            double dA = second_diff_sum<IX>(img, nx, ny, i, j, s, s, I1, I4, ok);
+            double dB = second_diff_sum<IX>(img, nx, ny, i, j, s, -s, I2, I3, ok);
             num = fabs(dA + dB) / 16.0;
             w1 = 0.25;
             w2 = 0.25;
@@ -186,8 +188,8 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
         }
     } else {
         const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
-        p1 = (int64_t)(j - dj) * nx + (i - di);
-        p2 = (int64_t)(j + dj) * nx + (i + di);
+        p1 = (IX)(j - dj) * nx + (i - di);
+        p2 = (IX)(j + dj) * nx + (i + di);
         p3 = p4 = -1;
         double I1 = __ldg(img + p1), I2 = __ldg(img + p2);
         sin_ = I1 + I2;
@@ -198,7 +200,7 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
             w2 = 0.0;
             den = fabs(i1);
         } else {
-            double d = second_diff_sum(img, nx, ny, i, j, di, dj, I1, I2, ok);
+            double d = second_diff_sum<IX>(img, nx, ny, i, j, di, dj, I1, I2, ok);
             num = fabs(d) / 8.0;
             w1 = 0.5;
             w2 = 0.5;
@@ -273,6 +275,7 @@ __device__ __forceinline__ float hiword_f32(double x, bool& ok)
 }
 
 // FP32 second-difference sum along one line (as second_diff_sum) and its sum of |c_k v_k|.
+template <class IX>
 __device__ __forceinline__ float second_diff_f(const double* img, int nx, int ny, int i, int j,
                                                int di, int dj, float Im, float Ip, float& C,
                                                bool& ok)
@@ -281,18 +284,18 @@ __device__ __forceinline__ float second_diff_f(const double* img, int nx, int ny
     const bool has_m = iom >= 0 && iom < nx && jom >= 0 && jom < ny;
     const bool has_p = iop >= 0 && iop < nx && jop >= 0 && jop < ny;
     if (has_m && has_p) {
-        float Om = hiword_f32(__ldg(img + (int64_t)jom * nx + iom), ok);
-        float Op = hiword_f32(__ldg(img + (int64_t)jop * nx + iop), ok);
+        float Om = hiword_f32(__ldg(img + (IX)jom * nx + iom), ok);
+        float Op = hiword_f32(__ldg(img + (IX)jop * nx + iop), ok);
         C += ((fabsf(Om) + fabsf(Im)) + fabsf(Ip)) + fabsf(Op);
         return ((Om - Im) - Ip) + Op;
     }
     if (has_m) {
-        float Om = hiword_f32(__ldg(img + (int64_t)jom * nx + iom), ok);
+        float Om = hiword_f32(__ldg(img + (IX)jom * nx + iom), ok);
         C += 2.f * fabsf(Om) + 4.f * fabsf(Im) + 2.f * fabsf(Ip);
         return 2.f * ((Om - 2.f * Im) + Ip);
     }
     if (has_p) {
-        float Op = hiword_f32(__ldg(img + (int64_t)jop * nx + iop), ok);
+        float Op = hiword_f32(__ldg(img + (IX)jop * nx + iop), ok);
         C += 2.f * fabsf(Op) + 4.f * fabsf(Ip) + 2.f * fabsf(Im);
         return 2.f * ((Op - 2.f * Ip) + Im);
     }
@@ -301,6 +304,7 @@ __device__ __forceinline__ float second_diff_f(const double* img, int nx, int ny
 }
 
 // Screened decision: 1 = trace, 0 = interpolate, -1 = undecided (take the FP64 decision).
+template <class IX>
 __device__ __forceinline__ int screen_decide(const Screen& sc, const double* img, int nx, int ny,
                                              int i, int j, int s, int cat)
 {
@@ -309,23 +313,23 @@ __device__ __forceinline__ int screen_decide(const Screen& sc, const double* img
     float X, C = 0.f, Sin, Cin;
     float tabs;
     if (cat == 4) {
-        float I1 = hiword_f32(__ldg(img + (int64_t)(j - s) * nx + (i - s)), ok);
-        float I4 = hiword_f32(__ldg(img + (int64_t)(j + s) * nx + (i + s)), ok);
-        float I2 = hiword_f32(__ldg(img + (int64_t)(j + s) * nx + (i - s)), ok);
-        float I3 = hiword_f32(__ldg(img + (int64_t)(j - s) * nx + (i + s)), ok);
+        float I1 = hiword_f32(__ldg(img + (IX)(j - s) * nx + (i - s)), ok);
+        float I4 = hiword_f32(__ldg(img + (IX)(j + s) * nx + (i + s)), ok);
+        float I2 = hiword_f32(__ldg(img + (IX)(j + s) * nx + (i - s)), ok);
+        float I3 = hiword_f32(__ldg(img + (IX)(j - s) * nx + (i + s)), ok);
         Sin = ((I1 + I2) + I3) + I4;
         Cin = ((fabsf(I1) + fabsf(I2)) + fabsf(I3)) + fabsf(I4);
-        float dA = second_diff_f(img, nx, ny, i, j, s, s, I1, I4, C, ok);
-        float dB = second_diff_f(img, nx, ny, i, j, s, -s, I2, I3, C, ok);
+        float dA = second_diff_f<IX>(img, nx, ny, i, j, s, s, I1, I4, C, ok);
+        float dB = second_diff_f<IX>(img, nx, ny, i, j, s, -s, I2, I3, C, ok);
         X = fabsf(dA + dB);
         tabs = sc.tabs4;
     } else {
         const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
-        float I1 = hiword_f32(__ldg(img + (int64_t)(j - dj) * nx + (i - di)), ok);
-        float I2 = hiword_f32(__ldg(img + (int64_t)(j + dj) * nx + (i + di)), ok);
+        float I1 = hiword_f32(__ldg(img + (IX)(j - dj) * nx + (i - di)), ok);
+        float I2 = hiword_f32(__ldg(img + (IX)(j + dj) * nx + (i + di)), ok);
         Sin = I1 + I2;
         Cin = fabsf(I1) + fabsf(I2);
-        X = fabsf(second_diff_f(img, nx, ny, i, j, di, dj, I1, I2, C, ok));
+        X = fabsf(second_diff_f<IX>(img, nx, ny, i, j, di, dj, I1, I2, C, ok));
         tabs = sc.tabs2;
     }
     if (!ok) return -1;
@@ -369,17 +373,18 @@ __device__ __forceinline__ double scale_pow2(double v, int k)
 // Learned path (spec = true): a point the criterion traces whose ray was already traced
 // speculatively (mask MASK_SPEC_DONE) is marked traced and not queued again (return 2).
 // Diagnostics planes (nullable) receive the mean of the interpolation parents.
+template <class IX>
 __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, double* img,
                                             uint8_t* mask, int i, int j, int s, int cat,
                                             double norm, int64_t npix, bool spec, float* aminr,
                                             float* aturn)
 {
     double w1, w2;
-    int64_t p1, p2, p3, p4;
-    const int scr = screen_decide(sc, img, J.nx, J.ny, i, j, s, cat);
+    IX p1, p2, p3, p4;
+    const int scr = screen_decide<IX>(sc, img, J.nx, J.ny, i, j, s, cat);
     bool trace;
     if (scr < 0) {
-        trace = decide(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4);
+        trace = decide<IX>(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4);
     } else {
         trace = scr == 1;
         if (J.edge_mode == ART_EDGE_TRACE) {
@@ -390,19 +395,19 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
         // stencil of the (linear) interpolant, as decide() sets it
         const int nx = J.nx;
         if (cat == 4) {
-            p1 = (int64_t)(j - s) * nx + (i - s);
-            p4 = (int64_t)(j + s) * nx + (i + s);
-            p2 = (int64_t)(j + s) * nx + (i - s);
-            p3 = (int64_t)(j - s) * nx + (i + s);
+            p1 = (IX)(j - s) * nx + (i - s);
+            p4 = (IX)(j + s) * nx + (i + s);
+            p2 = (IX)(j + s) * nx + (i - s);
+            p3 = (IX)(j - s) * nx + (i + s);
         } else {
             const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
-            p1 = (int64_t)(j - dj) * nx + (i - di);
-            p2 = (int64_t)(j + dj) * nx + (i + di);
+            p1 = (IX)(j - dj) * nx + (i - di);
+            p2 = (IX)(j + dj) * nx + (i + di);
             p3 = p4 = -1;
         }
         w1 = w2 = 0.5;
     }
-    const int64_t pix = (int64_t)j * J.nx + i;
+    const IX pix = (IX)j * J.nx + i;
     if (trace) {
         if (mask) {
             const bool done = spec && mask[pix] == MASK_SPEC_DONE;
@@ -455,7 +460,9 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
 }
 
 // Rows of the level lattice over blockIdx.y, columns over blockIdx.x and the threads: no index
-// division, and a warp covers 32 consecutive lattice points of one row.
+// division, and a warp covers 32 consecutive lattice points of one row.  Pixel offsets within a
+// plane are 32-bit (images are below 2^31 pixels: the ray queue holds 32-bit pixel indices), which
+// keeps the stencil's address arithmetic off the wide-multiply path.
 __global__ void __launch_bounds__(256)
     refine_kernel(DevJob J, int level, const double* __restrict__ norm_ptr, double* img,
                   uint8_t* mask, int32_t* queue, unsigned long long* qcount, float* aminr,
@@ -465,7 +472,12 @@ __global__ void __launch_bounds__(256)
     const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
     const int64_t npix = (int64_t)J.nx * J.ny;
     const double norm = *norm_ptr;
-    const Screen sc = make_screen(J, norm);
+    // the screen's thresholds once per block: made per thread, the compiler recomputed their
+    // FP64 products inside the loop (to save registers), which kept GB300's FP64 pipe 75 % busy
+    __shared__ Screen sc_s;
+    if (threadIdx.x == 0) sc_s = make_screen(J, norm);
+    __syncthreads();
+    const Screen sc = sc_s;
     const int lane = threadIdx.x & 31;
     for (int jj = blockIdx.y; jj < nky; jj += gridDim.y) {
         const int oj = jj & 1;
@@ -478,7 +490,7 @@ __global__ void __launch_bounds__(256)
                 if (oi | oj) {
                     const int i = ii * s, j = jj * s;
                     const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                    const int r = refine_point(J, sc, img, mask, i, j, s, cat, norm, npix,
+                    const int r = refine_point<int>(J, sc, img, mask, i, j, s, cat, norm, npix,
                                                counters != nullptr, aminr, aturn);
                     trace = r == 1;
                     used = r == 2;
@@ -670,7 +682,10 @@ __global__ void __launch_bounds__(256)
     const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
     const int64_t npix = (int64_t)J.nx * J.ny;
     const double norm = norms[4 * im];
-    const Screen sc = make_screen(J, norm);
+    __shared__ Screen sc_s;  // once per block, as in refine_kernel
+    if (threadIdx.x == 0) sc_s = make_screen(J, norm);
+    __syncthreads();
+    const Screen sc = sc_s;
     const int lane = threadIdx.x & 31;
     for (int jj = blockIdx.y; jj < nky; jj += gridDim.y) {
         const int oj = jj & 1;
@@ -683,7 +698,7 @@ __global__ void __launch_bounds__(256)
                 if (oi | oj) {
                     const int i = ii * s, j = jj * s;
                     const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                    trace = refine_point(J, sc, img, mask, i, j, s, cat, norm, npix, false,
+                    trace = refine_point<int>(J, sc, img, mask, i, j, s, cat, norm, npix, false,
                                          nullptr, nullptr) == 1;
                     pix = j * J.nx + i;
                 }
