@@ -165,6 +165,166 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_gemm_kernel(ConvArgs a)
     if (warp == 0) umma::tmem_free(tmem, 32);
 }
 
+// Forward convolution of a 32-channel layer (stride S = 1 or 2) from a halo tile: one CTA computes an
+// output tile of 8 x 16 pixels (M = 128: row group g = output row y0 + g, row r = column x0 + r).
+// The CTA loads the input rows and columns under the tile once (coalesced 16-byte chunks, zeros
+// outside the image) into planes of 16-byte entries, one per (channel group of 8, column parity
+// for S = 2); within a plane an input row is PITCH consecutive entries.  The A operand of tap
+// (ky, kx) for channels 16 h .. 16 h + 15 is then the same tile viewed at an offset: start at row
+// ky, entry kx / S of parity kx % S, core matrices 8 consecutive entries (the 8 output columns),
+// K step (next channel group) = one parity-plane pair, M step (next output row) = S rows.  18 MMAs
+// (9 taps x 2 K-halves) accumulate D in tensor memory, as the im2col kernel, with the same
+// operand values in the same order.
+template <int S, int CIN>
+struct Halo {
+    static constexpr int TW = 8, TH = 16;
+    static constexpr int HR = S * (TH - 1) + 3, HC = S * (TW - 1) + 3;  // rows, columns of input
+    static constexpr int NPAR = S, PITCH = (HC + S - 1) / S;            // entries per plane row
+    static constexpr int PLANE = HR * PITCH * 16;                       // bytes per plane
+    static constexpr int CG = CIN / 8;                                  // channel groups
+    static constexpr int KPAD = CIN == CH ? KH : K1;
+    static constexpr int ABYTES = CG * NPAR * PLANE;
+    static constexpr int BOFF = (ABYTES + 1023) / 1024 * 1024;
+    static constexpr int SMEM = BOFF + CH * KPAD * 2;
+};
+
+// CIN = 8 (the 3 input features, S = 1): one channel group per pixel, so a K = 16 slice holds two
+// taps; its second core matrix is the next tap's view of the same plane (LBO = the taps' address
+// difference, 16 B along a row), matching the weights' [tap][channel] columns.
+template <int S, int CIN>
+__global__ void __launch_bounds__(GEMM_THREADS) conv_halo_kernel(ConvArgs a)
+{
+    static_assert(CIN == CH || (CIN == CIN0 && S == 1), "halo convolution variants");
+    using HT = Halo<S, CIN>;
+    constexpr int CGR = HT::CG;
+    constexpr int NQ = HT::HR * HT::HC * CGR;                    // 16-byte chunks of one halo
+    constexpr int NPT = (NQ + GEMM_THREADS - 1) / GEMM_THREADS;  // per thread
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + HT::BOFF;
+    constexpr int KC = HT::KPAD / 8;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_x = (a.Wo + HT::TW - 1) / HT::TW;
+    const int ntiles = tiles_x * ((a.Ho + HT::TH - 1) / HT::TH);
+    // persistent: the weights once per CTA, then tiles blockIdx.x, + gridDim.x, ...; the next
+    // tile's halo is fetched into registers while the current tile's MMAs run
+    for (int q = tid; q < CH * KC; q += GEMM_THREADS) {
+        const int r = q & 7, rest = q >> 3;
+        const int kc = rest % KC, g = rest / KC;
+        const int n = g * 8 + r;
+        *reinterpret_cast<uint4*>(sB + umma::chunk_off(n, kc, HT::KPAD)) =
+            __ldg(reinterpret_cast<const uint4*>(a.B + (int64_t)n * HT::KPAD) + kc);
+    }
+    // the gap between the halo and the weights is read (times zero weights) by the padding
+    // slice of the 8-channel layer: keep it finite
+    for (int q = HT::ABYTES / 16 + tid; q < HT::BOFF / 16; q += GEMM_THREADS)
+        reinterpret_cast<uint4*>(sA)[q] = bf16x8_zero();
+    if (tid == 0) umma::mbar_init(&bar);
+    if (warp == 0) umma::tmem_alloc(&tslot, 32);
+    umma::fence_before();
+    __syncthreads();
+    umma::fence_after();
+    const uint32_t tmem = tslot;
+    // halo chunk q of the tile at (x0, y0): input rows S y0 - 1 .., columns S x0 - 1 ..; zeros
+    // outside the image
+    auto fetch = [&](int tile, uint4* R) {
+        const int x0 = (tile % tiles_x) * HT::TW, y0 = (tile / tiles_x) * HT::TH;
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int q = tid + k * GEMM_THREADS;
+            uint4 v = bf16x8_zero();
+            if (q < NQ) {
+                const int cg = q % CGR, pe = q / CGR;
+                const int yy = pe / HT::HC, cc = pe - yy * HT::HC;
+                const int iy = S * y0 - 1 + yy, ix = S * x0 - 1 + cc;
+                if (iy >= 0 && iy < a.H && ix >= 0 && ix < a.W)
+                    v = __ldg(reinterpret_cast<const uint4*>(a.src + ((int64_t)iy * a.W + ix) * CIN) + cg);
+            }
+            R[k] = v;
+        }
+    };
+    uint4 R[NPT];
+    int tile = blockIdx.x;
+    if (tile < ntiles) fetch(tile, R);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (; tile < ntiles && ok; tile += gridDim.x, phase ^= 1u) {
+#pragma unroll
+        for (int k = 0; k < NPT; ++k) {
+            const int q = tid + k * GEMM_THREADS;
+            if (q < NQ) {
+                const int cg = q % CGR, pe = q / CGR;
+                const int yy = pe / HT::HC, cc = pe - yy * HT::HC;
+                const int par = cc % S, e = cc / S;
+                *reinterpret_cast<uint4*>(sA + (cg * HT::NPAR + par) * HT::PLANE +
+                                          (yy * HT::PITCH + e) * 16) = R[k];
+            }
+        }
+        umma::fence_smem_async();
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
+        if (tid == 0) {
+            const uint32_t ab = umma::smem_u32(sA), bb = umma::smem_u32(sB);
+            const uint32_t sbo = S * HT::PITCH * 16;
+            auto tap_addr = [&](int t) {
+                const int ky = t / 3, kx = t - 3 * ky, par = kx % S, eoff = kx / S;
+                return ab + par * HT::PLANE + (ky * HT::PITCH + eoff) * 16;
+            };
+            if (CIN == CH) {
+                const uint32_t lbo = HT::NPAR * HT::PLANE;
+                for (int t = 0; t < 9; ++t)
+                    for (int h = 0; h < 2; ++h)
+                        umma::mma(tmem, umma::desc(tap_addr(t) + 2 * h * HT::NPAR * HT::PLANE, lbo, sbo),
+                                  umma::desc(bb + (2 * t + h) * 256, 128, KC * 128),
+                                  umma::idesc_bf16(128, CH), t > 0 || h > 0);
+            } else {
+                for (int j = 0; j < K1 / 16; ++j) {
+                    const int t0 = 2 * j, t1 = 2 * j + 1;  // t1 = 9: the zero-weight padding
+                    const uint32_t a0 = tap_addr(t0);
+                    const uint32_t lbo = t1 < 9 ? tap_addr(t1) - a0 : 16;
+                    umma::mma(tmem, umma::desc(a0, lbo, sbo),
+                              umma::desc(bb + j * 256, 128, KC * 128),
+                              umma::idesc_bf16(128, CH), j > 0);
+                }
+            }
+            umma::commit(&bar);
+        }
+        const int next = tile + gridDim.x;
+        if (next < ntiles) fetch(next, R);  // in flight during the MMAs
+        ok = __syncthreads_and(umma::wait(&bar, phase));
+        umma::fence_after();
+        if (ok) {
+            float v[32];
+            umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+            const int x0 = (tile % tiles_x) * HT::TW, y0 = (tile / tiles_x) * HT::TH;
+            const int m = warp * 32 + lane;
+            const int oy = y0 + (m >> 3), ox = x0 + (m & 7);
+            if (oy < a.Ho && ox < a.Wo) {
+                uint32_t w[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    w[c] = pack_bf16x2(fmaxf(v[2 * c] + __ldg(a.bias + 2 * c), 0.f),
+                                       fmaxf(v[2 * c + 1] + __ldg(a.bias + 2 * c + 1), 0.f));
+                uint4* o = reinterpret_cast<uint4*>(a.out + ((int64_t)oy * a.Wo + ox) * CH);
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4)
+                    o[c4] = make_uint4(w[4 * c4], w[4 * c4 + 1], w[4 * c4 + 2], w[4 * c4 + 3]);
+            }
+        } else if (tid == 0) {
+            atomicExch(a.err, 1);
+        }
+        // the tensor-memory reads and the shared-memory tile are done before the next tile
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
+    }
+    __syncthreads();
+    if (warp == 0) umma::tmem_free(tmem, 32);
+}
+
 struct WgradArgs {
     const bf16* X;     // forward input, H x W x CIN
     const bf16* dY;    // Ho x Wo x 32
@@ -449,6 +609,42 @@ static cudaError_t run_conv(const ConvArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Forward convolution of stride S through the halo-tile kernel.
+template <int S, int CIN>
+static cudaError_t run_conv_halo(const ConvArgs& a, cudaStream_t st)
+{
+    using HT = Halo<S, CIN>;
+    static bool attr = false;  // one device per process is the supported configuration
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(conv_halo_kernel<S, CIN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             HT::SMEM);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    static int grid_cap = 0;  // resident CTAs of the device (persistent grid)
+    if (!grid_cap) {
+        // CTAs per SM from the kernel's registers and shared memory (the occupancy query
+        // answered 1 here)
+        int dev = 0, sms = 0, smem_sm = 0;
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv_halo_kernel<S, CIN>);
+        if (e != cudaSuccess) return e;
+        const int by_smem = smem_sm / (HT::SMEM + (int)fa.sharedSizeBytes + 1024);
+        const int by_regs = 65536 / ((fa.numRegs > 0 ? fa.numRegs : 255) * GEMM_THREADS);
+        int per = by_smem < by_regs ? by_smem : by_regs;
+        if (per > 8) per = 8;  // 8 x 32 tensor-memory columns of 512
+        grid_cap = sms * (per > 0 ? per : 1);
+    }
+    const int tiles = ((a.Wo + HT::TW - 1) / HT::TW) * ((a.Ho + HT::TH - 1) / HT::TH);
+    conv_halo_kernel<S, CIN><<<tiles < grid_cap ? tiles : grid_cap, GEMM_THREADS, HT::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <int CIN>
 static cudaError_t run_wgrad(WgradArgs a, cudaStream_t st)
 {
@@ -553,15 +749,15 @@ static cudaError_t forward_backward(CnnState* s, int H, int W, const float* targ
     // c1, c2 (stride 1), c3, c4 (stride 2)
     c.src = s->x0; c.B = s->f1; c.bias = s->prm + P_B1; c.out = s->a1;
     c.H = H; c.W = W; c.Ho = H; c.Wo = W; c.stride = 1;
-    CKE((run_conv<CIN0, K1, 0>(c, st)));
+    CKE((run_conv_halo<1, CIN0>(c, st)));
     c.src = s->a1; c.B = s->f2; c.bias = s->prm + P_B2; c.out = s->a2;
-    CKE((run_conv<CH, KH, 0>(c, st)));
+    CKE((run_conv_halo<1, CH>(c, st)));
     c.src = s->a2; c.B = s->f3; c.bias = s->prm + P_B3; c.out = s->a3;
     c.Ho = H2; c.Wo = W2; c.stride = 2;
-    CKE((run_conv<CH, KH, 0>(c, st)));
+    CKE((run_conv_halo<2, CH>(c, st)));
     c.src = s->a3; c.B = s->f4; c.bias = s->prm + P_B4; c.out = s->a4;
     c.H = H2; c.W = W2; c.Ho = H4; c.Wo = W4;
-    CKE((run_conv<CH, KH, 0>(c, st)));
+    CKE((run_conv_halo<2, CH>(c, st)));
     const int n4 = H4 * W4;
     if (target) CKE(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
     cnn_head_kernel<<<(n4 + HEAD_THREADS - 1) / HEAD_THREADS, HEAD_THREADS, 0, st>>>(
