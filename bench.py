@@ -434,7 +434,7 @@ def main():
         band0 = params.get("crit_band", 0.0)
         for band in sorted({0.0, band0}):
             for depth in (2, 3):
-                for thr in (0.2, 0.3):
+                for thr in (0.2, 0.3, 0.5, 0.7):
                     lj = art.make_job(**{**params, "proposal": 1, "proposal_p": thr,
                                          "proposal_depth": depth, "crit_band": band})
                     lst = lctx.art_render(lj, img, mask, stats=True)
@@ -455,7 +455,7 @@ def main():
                    "gain_vs_plain_both_without_band": plain_nb / best_nb["ms_per_step"],
                    "note": "same image and mask as the plain render (the exact criterion decides "
                            "every point); lookahead depth, threshold and band chosen among "
-                           "{2,3} x {0.2,0.3} x {0, default} by timing"}
+                           "{2,3} x {0.2,0.3,0.5,0.7} x {0, default} by timing"}
 
     # the proposal network's tensor-core kernels alone: forward (4 implicit-GEMM convolutions +
     # head) and forward + backward on a 2049 x 2049 lattice, host-timed (each call synchronises)
