@@ -357,6 +357,37 @@ __device__ __forceinline__ int screen_decide(const Screen& sc, const double* img
     return -1;
 }
 
+// Whether the linear scheme's whole stencil of a point (parents and outer points) holds one finite
+// value, bit for bit, with every outer point inside the image: then both second differences are
+// exactly 0, eps_abs = 0 / norm = 0 for a positive finite norm, and with R_abs >= 0 the FP64
+// decision is "interpolate" whatever R_rel is.  The dark background of a wide field takes this
+// exit on the integer pipes.
+template <class IX>
+__device__ __forceinline__ bool uniform_stencil(const double* img, int nx, int ny, int i, int j,
+                                                int s, int cat)
+{
+    int di1, dj1, di2 = 0, dj2 = 0;  // the one or two lines of the stencil
+    if (cat == 4) {
+        di1 = s; dj1 = s; di2 = s; dj2 = -s;
+    } else {
+        di1 = (cat == 3) ? s : 0;
+        dj1 = (cat == 2) ? s : 0;
+    }
+    const int ri = 3 * (di1 > di2 ? di1 : di2), rj = 3 * s * (cat != 3);
+    if (i - ri < 0 || i + ri >= nx || j - rj < 0 || j + rj >= ny) return false;
+    const long long v = __double_as_longlong(__ldg(img + (IX)(j - dj1) * nx + (i - di1)));
+    if (((v >> 52) & 0x7ff) == 0x7ff) return false;
+    auto same = [&](int ii, int jj) {
+        return __double_as_longlong(__ldg(img + (IX)jj * nx + ii)) == v;
+    };
+    if (!same(i + di1, j + dj1) || !same(i - 3 * di1, j - 3 * dj1) || !same(i + 3 * di1, j + 3 * dj1))
+        return false;
+    if (cat == 4 && (!same(i - di2, j - dj2) || !same(i + di2, j + dj2) ||
+                     !same(i - 3 * di2, j - 3 * dj2) || !same(i + 3 * di2, j + 3 * dj2)))
+        return false;
+    return true;
+}
+
 // v * 2^-k (k = 1, 2), bit-identical to the FP64 product: for a normal v whose result stays
 // normal the product only lowers the exponent, done here on the integer pipes (GB300's FP64 pipe
 // issues 2 operations per SM and cycle); zeros, subnormal results, infinities and NaN multiply.
@@ -381,7 +412,9 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
 {
     double w1, w2;
     IX p1, p2, p3, p4;
-    const int scr = screen_decide<IX>(sc, img, J.nx, J.ny, i, j, s, cat);
+    const bool flat = sc.on && !sc.abs_any && J.interp == ART_INTERP_LINEAR &&
+                      uniform_stencil<IX>(img, J.nx, J.ny, i, j, s, cat);
+    const int scr = flat ? 0 : screen_decide<IX>(sc, img, J.nx, J.ny, i, j, s, cat);
     bool trace;
     if (scr < 0) {
         trace = decide<IX>(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4);

@@ -144,6 +144,13 @@ def cfg2(**over) -> dict:
                          precision="mixed_df", crit_band=CRIT_BAND), **over})
 
 
+def cfg4(**over) -> dict:
+    """Evaluation workload of the learned block proposal: config 2's snapshot and emission seen
+    with a 1000 M field of view, 257^2 -> 16385^2 over 6 levels (the photon ring and the torus
+    cover a small part of the image; most blocks of the finer levels are never refined)."""
+    return cfg2(**{**dict(fov=1000.0, levels=6), **over})
+
+
 BENCH_WORKLOADS = {
     "cfg1": ("adaptive polarized render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, FOV 40 M, "
              "r_obs 1000 M, RK4 h=0.05r; thermal-synchrotron thin disk (n_e~r^-1.1, T_e~r^-0.84, "
@@ -157,6 +164,9 @@ BENCH_WORKLOADS = {
              "cells over ln r in [ln 1.2, ln 1000]), i=163 deg, FOV 160 M, r_obs 1000 M, RK4 "
              "h=0.05r, thermal synchrotron at 230 GHz with R_high=20, sigma cut 1; "
              "R_rel=1e-3, R_abs=0.025", cfg2),
+    "cfg4": ("learned-proposal evaluation render 257^2 -> 16385^2 (6 levels) of the config-2 "
+             "snapshot and emission, i=163 deg, FOV 1000 M, r_obs 1000 M, RK4 h=0.05r; "
+             "R_rel=1e-3, R_abs=0.025", cfg4),
     "cfg0": ("adaptive render 33^2 -> 129^2 (2 levels), Schwarzschild, i=60 deg, FOV 40 M, "
              "R_rel=0.01, R_abs=1e-4 of peak", cfg0),
 }
