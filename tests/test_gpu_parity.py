@@ -105,12 +105,21 @@ REFINE_CASES = [
     dict(n0x=9, n0y=21, levels=2, kind="noisy", interp="nearest", edge_mode="onesided"),
     dict(n0x=33, n0y=1, levels=3, kind="noisy", interp="linear", edge_mode="onesided"),
     dict(n0x=3, n0y=3, levels=4, kind="ring", interp="linear", edge_mode="onesided"),
+    # wide exactly uniform regions (zero background, a constant plateau) next to structure:
+    # the kernel's uniform-stencil exit must give the FP64 decisions and interpolants
+    dict(n0x=17, n0y=17, levels=3, kind="plateau", interp="linear", edge_mode="onesided"),
+    dict(n0x=17, n0y=13, levels=3, kind="plateau", interp="linear", edge_mode="trace"),
 ]
 
 
 def _image(kind, nx, ny, seed):
     if kind == "ring":
         return W.ring_image(seed, nx, ny)
+    if kind == "plateau":
+        img = W.ring_image(seed, nx, ny)
+        img[img < np.quantile(img, 0.6)] = 0.0
+        img[: ny // 3, : nx // 3] = 0.37
+        return img
     if kind == "smooth":
         return W.smooth_image(seed, nx, ny)
     return W.smooth_image(seed, nx, ny, noise=0.05)
