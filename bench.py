@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--precision", default="mixed_df", choices=["mixed", "mixed_df", "fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-render measurement")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default kernel-form thresholds (skip the autotuner)")
     ap.add_argument("--no-mse", action="store_true",
                     help="skip the time-to-0.1%%-MSE sweep (needs a full FP64 trace as truth)")
     ap.add_argument("--no-learned", action="store_true",
@@ -264,6 +266,13 @@ def main():
         print(json.dumps({"single": args.workload, "precision": args.precision, **st}))
         ctx.close()
         return
+    # the library's autotuner picks the FP32 kernel-form thresholds for this workload (outside
+    # the timed region; every setting renders the same image)
+    tune = None
+    if not args.no_tune:
+        (tq, tp), tms = ctx.art_autotune(job, img, mask, reps=3)
+        tune = {"quad_rays": tq, "pair_rays": tp, "median_ms": tms,
+                "default": list(art.TUNE_DEFAULT)}
     for _ in range(max(args.warmup, 1)):
         stats = ctx.art_render(job, img, mask, stats=True)
     rays = stats["rays_traced"]
@@ -523,7 +532,7 @@ def main():
                 "dtype": DTYPE[args.precision],
                 "data": "synthetic",
                 "config": {"workload": desc, "name": args.workload, "image": f"{nx}x{ny}",
-                           "precision": args.precision, "rays_per_step": rays,
+                           "precision": args.precision, "rays_per_step": rays, "tune": tune,
                            "l2": "flushed (512 MB write) before every step, outside the timed "
                                  "region", "parallelism": f"replicas x{world}"},
                 "geodesic_steps_per_s": steps_per_render * args.steps * world / t_dev,

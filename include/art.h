@@ -222,6 +222,35 @@ int art_render_batch(art_ctx* ctx, const art_job* jobs, int32_t n, double* const
 int art_render_host(art_ctx* ctx, const art_job* job, double* img_host, uint8_t* mask_host,
                     art_stats* stats_host);
 
+/* Kernel forms of the FP32 pass (the paper has no counterpart: a scheduling choice of this
+ * implementation).  A level's FP32 launch whose queue holds at most quad_rays rays per block of
+ * the persistent grid splits each step over four warps per 32 rays (geodesic, two warps for the
+ * emission coefficients of alternate steps, segment); at most pair_rays, over two warps (geodesic,
+ * transfer); longer queues run one thread per ray.  The forms give bit-identical rays, so the
+ * setting changes speed only.  Defaults ART_TUNE_QUAD_DEFAULT and ART_TUNE_PAIR_DEFAULT; valid
+ * settings have 0 <= quad_rays <= pair_rays <= 4096. */
+#define ART_TUNE_QUAD_DEFAULT 32
+#define ART_TUNE_PAIR_DEFAULT 64
+typedef struct art_tune {
+    int32_t quad_rays;
+    int32_t pair_rays;
+} art_tune;
+
+/* Set the context's kernel-form thresholds (t == NULL restores the defaults), or read them.
+ * Errors: ART_ERR_ARG (null context, invalid setting). */
+int art_set_tune(art_ctx* ctx, const art_tune* t);
+int art_get_tune(art_ctx* ctx, art_tune* t_out);
+
+/* Autotuner: renders `job` (as art_render, into img_dev / mask_dev) with each of a fixed list of
+ * kernel-form thresholds, once to warm up and `reps` times timed with CUDA events on the context's
+ * stream, keeps the setting with the lowest median time in the context and returns it in *best
+ * (nullable) with that median in *best_ms (nullable).  img_dev and mask_dev hold the job's image
+ * afterwards (the same for every setting).  Synchronises the stream.  Errors: ART_ERR_ARG (reps
+ * outside 1..32, or as art_render), and those of art_render, after which the previous setting is
+ * kept. */
+int art_autotune(art_ctx* ctx, const art_job* job, double* img_dev, uint8_t* mask_dev,
+                 int32_t reps, art_tune* best, float* best_ms);
+
 /* Per-launch profiling.  With enable != 0 every kernel launch of the following calls is
  * bracketed by CUDA events on the context's stream (and the trace kernels' step counters are
  * snapshotted), for at most 256 launches; enable == 0 stops recording.  art_profile_read

@@ -51,6 +51,15 @@ class Job(ctypes.Structure):
     ]
 
 
+class Tune(ctypes.Structure):
+    """art_tune: FP32 kernel-form thresholds in rays per block (quad form up to quad_rays, pair
+    form up to pair_rays)."""
+    _fields_ = [("quad_rays", ctypes.c_int32), ("pair_rays", ctypes.c_int32)]
+
+
+TUNE_DEFAULT = (32, 64)
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("rays_traced", ctypes.c_int64), ("rays_fp64", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("rays_capped", ctypes.c_int64),
@@ -101,7 +110,7 @@ EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_p
            "art_render_host", "art_metrics", "art_profile", "art_profile_read",
            "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid", "art_cnn_load",
            "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step",
-           "art_cnn_sample")
+           "art_cnn_sample", "art_set_tune", "art_get_tune", "art_autotune")
 CNN_PARAMS = 28673
 NOALLOC_MAX_RAYS = 1 << 20
 
@@ -145,6 +154,9 @@ def load():
             lib.art_cnn_grad.argtypes = [vp, vp, i32, i32, vp, fp, vp]
             lib.art_cnn_train_step.argtypes = [vp, vp, i32, i32, vp, ctypes.c_float, fp]
             lib.art_cnn_sample.argtypes = [vp, P(Job), vp, vp, i32, vp, vp]
+            lib.art_set_tune.argtypes = [vp, P(Tune)]
+            lib.art_get_tune.argtypes = [vp, P(Tune)]
+            lib.art_autotune.argtypes = [vp, P(Job), vp, vp, i32, P(Tune), fp]
             _lib = lib
     return _lib
 
@@ -377,6 +389,28 @@ class Context:
         _check(load().art_cnn_sample(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask), level,
                                      _dptr(feat), _dptr(tgt)), "art_cnn_sample")
         return feat, tgt
+
+    def art_set_tune(self, quad_rays: int | None = None, pair_rays: int | None = None):
+        """Set the FP32 kernel-form thresholds; no arguments restore the defaults."""
+        if quad_rays is None and pair_rays is None:
+            _check(load().art_set_tune(self._ctx, None), "art_set_tune")
+            return
+        t = Tune(int(quad_rays), int(pair_rays))
+        _check(load().art_set_tune(self._ctx, ctypes.byref(t)), "art_set_tune")
+
+    def art_get_tune(self) -> tuple:
+        t = Tune()
+        _check(load().art_get_tune(self._ctx, ctypes.byref(t)), "art_get_tune")
+        return t.quad_rays, t.pair_rays
+
+    def art_autotune(self, job: Job, img, mask, reps: int = 3):
+        """Time `job` under each candidate setting, keep the fastest in the context; returns
+        ((quad_rays, pair_rays), median ms)."""
+        t = Tune()
+        ms = ctypes.c_float()
+        _check(load().art_autotune(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask), int(reps),
+                                   ctypes.byref(t), ctypes.byref(ms)), "art_autotune")
+        return (t.quad_rays, t.pair_rays), ms.value
 
     def art_profile(self, enable: bool):
         _check(load().art_profile(self._ctx, int(bool(enable))), "art_profile")

@@ -15,6 +15,7 @@
 using namespace art;
 
 struct art_ctx {
+    art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT};
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
@@ -399,6 +400,8 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
     TraceArgs a;
     memset(&a, 0, sizeof a);
     a.job = J;
+    a.quad_rays = c->tune.quad_rays;
+    a.pair_rays = c->tune.pair_rays;
     a.pix_minr = pix_minr;
     a.pix_turn = pix_turn;
     a.spec_from = spec_from;
@@ -1072,5 +1075,81 @@ extern "C" int art_cnn_sample(art_ctx* c, const art_job* job, const double* img_
     CK(cnn_features_f32(J, level, img_dev, c->aux, c->aux + npix, c->norm3, feat_dev, c->stream));
     CK(cnn_targets(J, level, mask_dev, target_dev, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return ART_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// kernel-form thresholds and their autotuner
+// --------------------------------------------------------------------------------------------
+
+static bool tune_valid(const art_tune* t)
+{
+    return t->quad_rays >= 0 && t->pair_rays >= t->quad_rays && t->pair_rays <= 4096;
+}
+
+extern "C" int art_set_tune(art_ctx* c, const art_tune* t)
+{
+    if (!c) return ART_ERR_ARG;
+    if (!t) {
+        c->tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT};
+        return ART_OK;
+    }
+    if (!tune_valid(t)) return ART_ERR_ARG;
+    c->tune = *t;
+    return ART_OK;
+}
+
+extern "C" int art_get_tune(art_ctx* c, art_tune* t)
+{
+    if (!c || !t) return ART_ERR_ARG;
+    *t = c->tune;
+    return ART_OK;
+}
+
+extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uint8_t* mask_dev,
+                            int32_t reps, art_tune* best, float* best_ms)
+{
+    if (!c || !job || !img_dev || reps < 1 || reps > 32) return ART_ERR_ARG;
+    // candidates: one-thread only, pair only, and quad/pair splits around the defaults
+    static const art_tune cand[] = {{0, 0},    {0, 64},  {32, 64},  {32, 96},
+                                    {64, 96},  {32, 128}, {64, 128}, {16, 64}};
+    const int ncand = (int)(sizeof cand / sizeof cand[0]);
+    CK(cudaSetDevice(c->device));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return ART_ERR_CUDA;
+    }
+    const art_tune saved = c->tune;
+    art_tune win = saved;
+    float win_ms = INFINITY;
+    int rc = ART_OK;
+    std::vector<float> t(reps);
+    for (int k = 0; k < ncand && rc == ART_OK; ++k) {
+        c->tune = cand[k];
+        if ((rc = art_render(c, job, nullptr, img_dev, mask_dev, nullptr))) break;  // warm-up
+        for (int r = 0; r < reps && rc == ART_OK; ++r) {
+            if (cudaEventRecord(e0, c->stream) != cudaSuccess) rc = ART_ERR_CUDA;
+            if (!rc) rc = art_render(c, job, nullptr, img_dev, mask_dev, nullptr);
+            if (!rc && cudaEventRecord(e1, c->stream) != cudaSuccess) rc = ART_ERR_CUDA;
+            if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = ART_ERR_CUDA;
+            if (!rc && cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess) rc = ART_ERR_CUDA;
+        }
+        if (rc) break;
+        std::vector<float> s(t);
+        std::sort(s.begin(), s.end());
+        const float med = s[reps / 2];
+        if (med < win_ms) {
+            win_ms = med;
+            win = cand[k];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tune = rc == ART_OK ? win : saved;
+    if (rc) return rc;
+    if (best) *best = win;
+    if (best_ms) *best_ms = win_ms;
     return ART_OK;
 }

@@ -53,6 +53,9 @@ struct TraceArgs {
     float* pix_minr;
     float* pix_turn;
     const unsigned long long* spec_from;
+    // kernel forms of the FP32 pass (trace_kernels.cuh): queues of at most quad_rays rays per
+    // block take the four-warp form, of at most pair_rays the two-warp form (art_tune)
+    int32_t quad_rays, pair_rays;
 };
 
 // Transient mask values of the learned path (a render ends with every point TRACED or INTERP).

@@ -113,6 +113,8 @@ extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_d
     TraceArgs a;
     memset(&a, 0, sizeof a);
     a.job = J;
+    a.quad_rays = ART_TUNE_QUAD_DEFAULT;
+    a.pair_rays = ART_TUNE_PAIR_DEFAULT;
     art_make_synch(job, &a.synch);
     a.cam = cam;
     a.queue = pix_dev;

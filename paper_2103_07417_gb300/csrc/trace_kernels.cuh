@@ -311,10 +311,10 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
 // --------------------------------------------------------------------------------------------
 
 constexpr int QUAD_SLOTS = 4;
-// Queues of up to QUAD_RAYS rays per block take the quad form (one group of 32 rays per block at
-// once; longer queues are drained by the same warps in turn), up to PAIR_RAYS the pair form
-// (FP32 kernels).
-constexpr unsigned long long QUAD_RAYS = 32, PAIR_RAYS = 64;
+// FP32 kernels: queues of up to A.quad_rays rays per block take the quad form (one group of 32
+// rays per block at once; longer queues are drained by the same warps in turn), up to
+// A.pair_rays the pair form, longer ones the one-thread form (defaults 32 and 64, set per context
+// by art_set_tune or art_autotune).
 
 template <class Q>
 struct QuadRing {
@@ -512,10 +512,11 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
     }
 }
 
-// The single-image trace kernel.  A launch whose queue fits the warp pairs of the grid at once
-// (the latency-bound regime of most levels) runs the warp-pair form; a longer queue, where
-// throughput counts, the one-thread form with twice the rays in flight.  The FP64 kernel is
-// always one-thread.  The choice is uniform over the grid (it depends on the queue length only).
+// The single-image trace kernel.  The form follows the queue length (uniform over the grid): short
+// queues (the latency-bound regime of most levels) take the warp-quad (FP32) or warp-pair form, a
+// longer queue, where throughput counts, the one-thread form with the most rays in flight.  The
+// double-float kernel takes the pair form whenever its queue fits the grid's pairs; the FP64
+// kernel is always one-thread.
 template <class R, bool SWEEP, bool POL, int EM>
 __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
 {
@@ -538,9 +539,9 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
             quad_ring_init(qring);
             __syncthreads();
             const unsigned long long n = *A.count, blocks = gridDim.x;
-            if (n <= blocks * QUAD_RAYS)
+            if (n <= blocks * (unsigned long long)A.quad_rays)
                 trace_quads<SWEEP, POL, EM>(A, cam_s, qring);
-            else if (n <= blocks * PAIR_RAYS)
+            else if (n <= blocks * (unsigned long long)A.pair_rays)
                 trace_pairs<R, SWEEP, POL, EM>(A, cam_s, ring);
             else
                 trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
