@@ -364,6 +364,24 @@ def main():
             "rays_per_s": stp["rays_traced"] * kp / tp,
             "geodesic_steps_per_s": stp["steps"] * kp / tp, "ms_per_step": 1000 * tp / kp,
             "rays_high_precision": stp["rays_fp64"]}
+    # the same render replayed from a CUDA graph (one capture of the whole level loop)
+    if not params.get("proposal", 0):
+        ctx.art_graph_render(job, img, mask)
+        kp = max(3, args.steps // 5)
+        evs = []
+        for _ in range(kp):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.art_graph_render(job, img, mask)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        tg = sum(a.elapsed_time(b) for a, b in evs) / 1000.0
+        paths[args.precision + "_graph"] = {"rays_per_s": rays * kp / tg,
+                                            "geodesic_steps_per_s": steps_per_render * kp / tg,
+                                            "ms_per_step": 1000 * tg / kp,
+                                            "rays_high_precision": stats["rays_fp64"]}
     ctx.art_render(job, img, mask, stats=False)
     paths[args.precision] = {"rays_per_s": value / world,
                              "geodesic_steps_per_s": steps_per_render * args.steps / t_dev,

@@ -251,6 +251,18 @@ int art_get_tune(art_ctx* ctx, art_tune* t_out);
 int art_autotune(art_ctx* ctx, const art_job* job, double* img_dev, uint8_t* mask_dev,
                  int32_t reps, art_tune* best, float* best_ms);
 
+/* art_render replayed from a CUDA graph (no stats; the paper has no counterpart).  The first call
+ * for a given job, image and mask pointers, kernel-form setting and fluid grid renders once
+ * normally (which sizes every scratch buffer), then captures the whole level loop (every launch
+ * and memset of art_render) on a stream of the context's own and instantiates it; that call and
+ * every later call with the same key launch the graph, ordered after prior work on the context's
+ * stream and before later work (two events).  A different key captures again, replacing the
+ * graph.  Since the first call of a key synchronises the context's stream and captures, it must
+ * not itself be made while that stream is being captured.  Jobs with the learned proposal return
+ * ART_ERR_UNSUPPORTED (the network's weights may change between calls), as does a capture the
+ * driver refuses.  Other errors as art_render. */
+int art_graph_render(art_ctx* ctx, const art_job* job, double* img_dev, uint8_t* mask_dev);
+
 /* Per-launch profiling.  With enable != 0 every kernel launch of the following calls is
  * bracketed by CUDA events on the context's stream (and the trace kernels' step counters are
  * snapshotted), for at most 256 launches; enable == 0 stops recording.  art_profile_read

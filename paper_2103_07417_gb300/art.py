@@ -110,7 +110,7 @@ EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_p
            "art_render_host", "art_metrics", "art_profile", "art_profile_read",
            "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid", "art_cnn_load",
            "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step",
-           "art_cnn_sample", "art_set_tune", "art_get_tune", "art_autotune")
+           "art_cnn_sample", "art_set_tune", "art_get_tune", "art_autotune", "art_graph_render")
 CNN_PARAMS = 28673
 NOALLOC_MAX_RAYS = 1 << 20
 
@@ -157,6 +157,7 @@ def load():
             lib.art_set_tune.argtypes = [vp, P(Tune)]
             lib.art_get_tune.argtypes = [vp, P(Tune)]
             lib.art_autotune.argtypes = [vp, P(Job), vp, vp, i32, P(Tune), fp]
+            lib.art_graph_render.argtypes = [vp, P(Job), vp, vp]
             _lib = lib
     return _lib
 
@@ -389,6 +390,11 @@ class Context:
         _check(load().art_cnn_sample(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask), level,
                                      _dptr(feat), _dptr(tgt)), "art_cnn_sample")
         return feat, tgt
+
+    def art_graph_render(self, job: Job, img, mask):
+        """art_render through a CUDA graph captured on the first call for this job and buffers."""
+        _check(load().art_graph_render(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask)),
+               "art_graph_render")
 
     def art_set_tune(self, quad_rays: int | None = None, pair_rays: int | None = None):
         """Set the FP32 kernel-form thresholds; no arguments restore the defaults."""

@@ -16,6 +16,17 @@ using namespace art;
 
 struct art_ctx {
     art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT};
+    // CUDA-graph replay of the level loop (art_graph_render): the captured graph, the call it
+    // replays, and a capture stream ordered against the context's stream by two events
+    cudaGraphExec_t gexec = nullptr;
+    art_job gjob = {};
+    double* gimg = nullptr;
+    uint8_t* gmask = nullptr;
+    art_tune gtune = {};
+    const float* ggrid = nullptr;
+    double ggmeta[5] = {};  // grid dimensions and radial range baked into the captured launches
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t gev_in = nullptr, gev_out = nullptr;
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
@@ -304,6 +315,11 @@ extern "C" void art_destroy(art_ctx* c)
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    if (c->gstream) cudaStreamSynchronize(c->gstream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gstream) cudaStreamDestroy(c->gstream);
+    if (c->gev_in) cudaEventDestroy(c->gev_in);
+    if (c->gev_out) cudaEventDestroy(c->gev_out);
     cudaFree(c->queue);
     cudaFree(c->reroute);
     cudaFree(c->counters);
@@ -1151,5 +1167,71 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
     if (rc) return rc;
     if (best) *best = win;
     if (best_ms) *best_ms = win_ms;
+    return ART_OK;
+}
+
+// --------------------------------------------------------------------------------------------
+// CUDA-graph replay of the level loop
+// --------------------------------------------------------------------------------------------
+
+extern "C" int art_graph_render(art_ctx* c, const art_job* job, double* img_dev, uint8_t* mask_dev)
+{
+    if (!c || !job || !img_dev) return ART_ERR_ARG;
+    if (job->proposal) return ART_ERR_UNSUPPORTED;  // the network's weights may change between calls
+    CK(cudaSetDevice(c->device));
+    if (!c->gstream) {
+        CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming));
+    }
+    const double gmeta[5] = {(double)c->g_n1, (double)c->g_n2, (double)c->g_n3, c->g_x1min,
+                             c->g_x1max};
+    const bool same = c->gexec && memcmp(&c->gjob, job, sizeof(art_job)) == 0 &&
+                      c->gimg == img_dev && c->gmask == mask_dev &&
+                      c->gtune.quad_rays == c->tune.quad_rays &&
+                      c->gtune.pair_rays == c->tune.pair_rays && c->ggrid == c->grid &&
+                      memcmp(c->ggmeta, gmeta, sizeof gmeta) == 0;
+    if (!same) {
+        // one ordinary render sizes every scratch buffer (no allocation or synchronisation may
+        // happen while capturing), then the same call is captured on the capture stream
+        int rc = art_render(c, job, nullptr, img_dev, mask_dev, nullptr);
+        if (rc) return rc;
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        const bool prof = c->prof_on;
+        cudaStream_t user = c->stream;
+        c->prof_on = false;
+        c->stream = c->gstream;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = art_render(c, job, nullptr, img_dev, mask_dev, nullptr);
+            e = cudaStreamEndCapture(c->gstream, &graph);
+        }
+        c->stream = user;
+        c->prof_on = prof;
+        if (e == cudaSuccess && rc == ART_OK) e = cudaGraphInstantiate(&c->gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (rc) return rc;
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            cudaGetLastError();
+            return ART_ERR_UNSUPPORTED;
+        }
+        c->gjob = *job;
+        c->gimg = img_dev;
+        c->gmask = mask_dev;
+        c->gtune = c->tune;
+        c->ggrid = c->grid;
+        memcpy(c->ggmeta, gmeta, sizeof gmeta);
+    }
+    CK(cudaEventRecord(c->gev_in, c->stream));
+    CK(cudaStreamWaitEvent(c->gstream, c->gev_in, 0));
+    CK(cudaGraphLaunch(c->gexec, c->gstream));
+    CK(cudaEventRecord(c->gev_out, c->gstream));
+    CK(cudaStreamWaitEvent(c->stream, c->gev_out, 0));
     return ART_OK;
 }
