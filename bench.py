@@ -438,12 +438,25 @@ def main():
             evs.append((e0, e1))
         torch.cuda.synchronize()
         tb = sum(a.elapsed_time(b) for a, b in evs) / 1000.0 / len(evs)
+        # the same batch replayed from a CUDA graph (captured on the first call)
+        ctx.art_graph_render_batch(bjobs, bimgs, bmasks)
+        evs = []
+        for _ in range(3):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.art_graph_render_batch(bjobs, bimgs, bmasks)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        tg = sum(a.elapsed_time(b) for a, b in evs) / 1000.0 / len(evs)
         batched = {"workload": "256 images (config-3 recipe): a~U[-0.94,0.94], i~U[10,170] deg, "
                                "FOV log-U[40,400] M, 65^2..513^2 over 2-6 levels, emission from "
                                "the config-2 snapshot (288x128x128 grid), subrings n=0,1,2, "
                                "mixed_df",
                    "rays_per_s": brays / tb, "images_per_s": len(bjobs) / tb,
-                   "ms_per_batch": 1000 * tb, "rays": brays, "pixels": bpix,
+                   "ms_per_batch": 1000 * tb, "ms_per_batch_graph": 1000 * tg,
+                   "rays": brays, "pixels": bpix,
                    "geodesic_steps_per_s": bst[0]["steps"] / tb}
         del bimgs, bmasks
 

@@ -257,11 +257,21 @@ int art_autotune(art_ctx* ctx, const art_job* job, double* img_dev, uint8_t* mas
  * and memset of art_render) on a stream of the context's own and instantiates it; that call and
  * every later call with the same key launch the graph, ordered after prior work on the context's
  * stream and before later work (two events).  A different key captures again, replacing the
- * graph.  Since the first call of a key synchronises the context's stream and captures, it must
- * not itself be made while that stream is being captured.  Jobs with the learned proposal return
+ * graph, as does any scratch buffer the context reallocated since the capture.  Since the first
+ * call of a key synchronises the context's stream and captures, it must not itself be made while
+ * that stream is being captured.  Jobs with the learned proposal return
  * ART_ERR_UNSUPPORTED (the network's weights may change between calls), as does a capture the
  * driver refuses.  Other errors as art_render. */
 int art_graph_render(art_ctx* ctx, const art_job* job, double* img_dev, uint8_t* mask_dev);
+
+/* art_render_batch replayed from a CUDA graph (no stats), on the same terms as art_graph_render:
+ * the first call for a given batch (job structs, image and mask pointers) and fluid grid renders
+ * it once normally, then captures its device part (every memset and launch of the level loop) and
+ * instantiates it; every call uploads the batch's job tables (from a host copy the context keeps)
+ * and launches the graph.  A scratch buffer reallocated by any later call of the context makes the
+ * next call capture again.  Learned jobs: ART_ERR_UNSUPPORTED. */
+int art_graph_render_batch(art_ctx* ctx, const art_job* jobs, int32_t n, double* const* imgs,
+                           uint8_t* const* masks);
 
 /* Per-launch profiling.  With enable != 0 every kernel launch of the following calls is
  * bracketed by CUDA events on the context's stream (and the trace kernels' step counters are

@@ -110,7 +110,8 @@ EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_p
            "art_render_host", "art_metrics", "art_profile", "art_profile_read",
            "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid", "art_cnn_load",
            "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step",
-           "art_cnn_sample", "art_set_tune", "art_get_tune", "art_autotune", "art_graph_render")
+           "art_cnn_sample", "art_set_tune", "art_get_tune", "art_autotune", "art_graph_render",
+           "art_graph_render_batch")
 CNN_PARAMS = 28673
 NOALLOC_MAX_RAYS = 1 << 20
 
@@ -158,6 +159,7 @@ def load():
             lib.art_get_tune.argtypes = [vp, P(Tune)]
             lib.art_autotune.argtypes = [vp, P(Job), vp, vp, i32, P(Tune), fp]
             lib.art_graph_render.argtypes = [vp, P(Job), vp, vp]
+            lib.art_graph_render_batch.argtypes = [vp, P(Job), i32, P(vp), P(vp)]
             _lib = lib
     return _lib
 
@@ -282,6 +284,15 @@ class Context:
         _check(load().art_render_batch(self._ctx, jarr, n, iarr, marr, st if stats else None),
                "art_render_batch")
         return [_stats_dict(st[i], jobs[i].levels) for i in range(n)] if stats else None
+
+    def art_graph_render_batch(self, jobs, imgs, masks=None):
+        """art_render_batch through a CUDA graph captured on the first call for this batch."""
+        n = len(jobs)
+        jarr = (Job * n)(*jobs)
+        iarr = (ctypes.c_void_p * n)(*[t.data_ptr() for t in imgs])
+        marr = (ctypes.c_void_p * n)(*[m.data_ptr() for m in masks]) if masks is not None else None
+        _check(load().art_graph_render_batch(self._ctx, jarr, n, iarr, marr),
+               "art_graph_render_batch")
 
     def render_batch(self, jobs):
         """Allocate the images and masks of a batch on the device and run art_render_batch."""

@@ -16,6 +16,10 @@ using namespace art;
 
 struct art_ctx {
     art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT};
+    // bumped whenever a scratch buffer is (re)allocated: a captured graph holds the pointers of
+    // its capture and is replayed only while this is unchanged
+    uint64_t scratch_gen = 0;
+    uint64_t ggen = 0, gbgen = 0;
     // CUDA-graph replay of the level loop (art_graph_render): the captured graph, the call it
     // replays, and a capture stream ordered against the context's stream by two events
     cudaGraphExec_t gexec = nullptr;
@@ -27,6 +31,14 @@ struct art_ctx {
     double ggmeta[5] = {};  // grid dimensions and radial range baked into the captured launches
     cudaStream_t gstream = nullptr;
     cudaEvent_t gev_in = nullptr, gev_out = nullptr;
+    // the same for art_graph_render_batch: graph, the batch it replays and its host plan
+    cudaGraphExec_t gbexec = nullptr;
+    std::vector<art_job> gbjobs;
+    std::vector<double*> gbimgs;
+    std::vector<uint8_t*> gbmasks;
+    const float* gbgrid = nullptr;
+    double gbgmeta[5] = {};
+    struct BatchPlan* gbplan = nullptr;
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 0;
@@ -84,6 +96,9 @@ struct art_ctx {
     unsigned long long* prof_steps = nullptr;  // device snapshots of C_STEPS after trace launches
     int prof_level = -1;
 };
+
+struct BatchPlan;
+static void destroy_plan(BatchPlan* p);
 
 // Profiler brackets: prof_begin before a launch, prof_end after it.
 static int prof_begin(art_ctx* c)
@@ -317,6 +332,8 @@ extern "C" void art_destroy(art_ctx* c)
     cudaStreamSynchronize(c->stream);
     if (c->gstream) cudaStreamSynchronize(c->gstream);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->gbexec) cudaGraphExecDestroy(c->gbexec);
+    destroy_plan(c->gbplan);
     if (c->gstream) cudaStreamDestroy(c->gstream);
     if (c->gev_in) cudaEventDestroy(c->gev_in);
     if (c->gev_out) cudaEventDestroy(c->gev_out);
@@ -357,6 +374,7 @@ extern "C" void art_destroy(art_ctx* c)
 static int ensure_fixed(art_ctx* c)
 {
     if (c->counters) return ART_OK;
+    ++c->scratch_gen;
     CK(cudaMalloc(&c->counters, sizeof(unsigned long long) * C_COUNT));
     CK(cudaMalloc(&c->norm3, sizeof(double) * 4));
     CK(cudaMalloc(&c->cam, sizeof(Camera)));
@@ -372,6 +390,7 @@ static int ensure_queue(art_ctx* c, int64_t cap)
 {
     if (cap < 1) cap = 1;
     if (cap <= c->queue_cap) return ART_OK;
+    ++c->scratch_gen;
     CK(cudaStreamSynchronize(c->stream));
     cudaFree(c->queue);
     cudaFree(c->reroute);
@@ -388,6 +407,7 @@ template <class T>
 static int grow(art_ctx* c, T*& buf, int64_t& cap, int64_t n)
 {
     if (n <= cap) return ART_OK;
+    ++c->scratch_gen;
     CK(cudaStreamSynchronize(c->stream));
     cudaFree(buf);
     buf = nullptr;
@@ -796,6 +816,7 @@ extern "C" int art_profile_read(art_ctx* c, art_launch_record* recs, int cap, in
 static int ensure_batch(art_ctx* c, int n, int64_t qcap)
 {
     if (n > c->bcap) {
+        ++c->scratch_gen;
         CK(cudaStreamSynchronize(c->stream));
         cudaFree(c->bjobs);
         cudaFree(c->bsynch);
@@ -819,6 +840,7 @@ static int ensure_batch(art_ctx* c, int n, int64_t qcap)
         c->bcap = n;
     }
     if (qcap > c->bqcap) {
+        ++c->scratch_gen;
         CK(cudaStreamSynchronize(c->stream));
         cudaFree(c->bqueue);
         cudaFree(c->breroute);
@@ -880,46 +902,83 @@ static int trace_queue_batch(art_ctx* c, const DevJob& J0, int nimg)
     return ART_OK;
 }
 
-extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const* imgs,
-                                uint8_t* const* masks, art_stats* stats)
-{
-    if (!c || !jobs || !imgs || n < 1) return ART_ERR_ARG;
-    std::vector<DevJob> J(n);
-    std::vector<SynchConst> S(n);
-    std::vector<double> p3(3 * (size_t)n);
-    std::vector<uint8_t*> mk(n, nullptr);
+// A batch's host-side plan: validated device jobs, synchrotron constants, camera parameters,
+// output tables, and the launch extents of every level.
+struct BatchPlan {
+    int n = 0;
+    std::vector<DevJob> J;
+    std::vector<SynchConst> S;
+    std::vector<double> p3;
+    std::vector<double*> im;
+    std::vector<uint8_t*> mk;
     int64_t qcap = 0;
     int max_base = 1, max_levels = 0;
+    std::vector<int> kx, ky;  // per level >= 1: the largest lattice extents
+};
+
+static int plan_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const* imgs,
+                      uint8_t* const* masks, BatchPlan& P)
+{
+    P.n = n;
+    P.J.assign(n, DevJob{});
+    P.S.assign(n, SynchConst{});
+    P.p3.assign(3 * (size_t)n, 0.0);
+    P.im.assign(imgs, imgs + n);
+    P.mk.assign(n, nullptr);
+    P.qcap = 0;
+    P.max_base = 1;
+    P.max_levels = 0;
     for (int i = 0; i < n; ++i) {
-        int rc = make_devjob(&jobs[i], &J[i]);
+        int rc = make_devjob(&jobs[i], &P.J[i]);
         if (rc) return rc;
         if (!imgs[i]) return ART_ERR_ARG;
-        if (J[i].stokes != J[0].stokes || J[i].subrings != J[0].subrings ||
-            J[i].precision != J[0].precision ||
-            (J[i].emission == ART_EMIT_GRID) != (J[0].emission == ART_EMIT_GRID))
+        if (P.J[i].stokes != P.J[0].stokes || P.J[i].subrings != P.J[0].subrings ||
+            P.J[i].precision != P.J[0].precision ||
+            (P.J[i].emission == ART_EMIT_GRID) != (P.J[0].emission == ART_EMIT_GRID))
             return ART_ERR_ARG;  // one kernel kind and one plane count per batch
         if ((rc = check_grid(c, &jobs[i]))) return rc;
-        make_synch(&jobs[i], c, &S[i]);
-        p3[3 * i] = jobs[i].a;
-        p3[3 * i + 1] = jobs[i].r_obs;
-        p3[3 * i + 2] = jobs[i].incl_deg;
-        if (masks) mk[i] = masks[i];
-        qcap += max_level_rays(J[i]);
-        int S0 = 1 << J[i].levels;
-        int nb = ((J[i].nx - 1) / S0 + 1) * ((J[i].ny - 1) / S0 + 1);
-        if (nb > max_base) max_base = nb;
-        if (J[i].levels > max_levels) max_levels = J[i].levels;
+        make_synch(&jobs[i], c, &P.S[i]);
+        P.p3[3 * i] = jobs[i].a;
+        P.p3[3 * i + 1] = jobs[i].r_obs;
+        P.p3[3 * i + 2] = jobs[i].incl_deg;
+        if (masks) P.mk[i] = masks[i];
+        P.qcap += max_level_rays(P.J[i]);
+        int S0 = 1 << P.J[i].levels;
+        int nb = ((P.J[i].nx - 1) / S0 + 1) * ((P.J[i].ny - 1) / S0 + 1);
+        if (nb > P.max_base) P.max_base = nb;
+        if (P.J[i].levels > P.max_levels) P.max_levels = P.J[i].levels;
     }
-    CK(cudaSetDevice(c->device));
-    int rc;
-    if ((rc = ensure_fixed(c)) || (rc = ensure_batch(c, n, qcap))) return rc;
+    P.kx.assign(P.max_levels + 1, 1);
+    P.ky.assign(P.max_levels + 1, 1);
+    for (int level = 1; level <= P.max_levels; ++level)
+        for (int i = 0; i < n; ++i)
+            if (P.J[i].levels >= level) {
+                int s = 1 << (P.J[i].levels - level);
+                P.kx[level] = std::max(P.kx[level], (P.J[i].nx - 1) / s + 1);
+                P.ky[level] = std::max(P.ky[level], (P.J[i].ny - 1) / s + 1);
+            }
+    return ART_OK;
+}
+
+// The plan's tables into the context's device tables (outside any graph: host sources).
+static int upload_batch(art_ctx* c, const BatchPlan& P)
+{
     cudaStream_t st = c->stream;
-    c->launches = 0;
-    CK(cudaMemcpyAsync(c->bjobs, J.data(), sizeof(DevJob) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->bsynch, S.data(), sizeof(SynchConst) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->bparams, p3.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->bimgs, imgs, sizeof(double*) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->bmasks, mk.data(), sizeof(uint8_t*) * n, cudaMemcpyHostToDevice, st));
+    const int n = P.n;
+    CK(cudaMemcpyAsync(c->bjobs, P.J.data(), sizeof(DevJob) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bsynch, P.S.data(), sizeof(SynchConst) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bparams, P.p3.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bimgs, P.im.data(), sizeof(double*) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bmasks, P.mk.data(), sizeof(uint8_t*) * n, cudaMemcpyHostToDevice, st));
+    return ART_OK;
+}
+
+// The device part of a batched render: memsets and launches only (capturable).
+static int run_batch(art_ctx* c, const BatchPlan& P)
+{
+    cudaStream_t st = c->stream;
+    const int n = P.n;
+    int rc;
     CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * C_COUNT, st));
     CK(cudaMemsetAsync(c->bcounts, 0, sizeof(unsigned long long) * 16 * n, st));
     c->prof_level = -1;
@@ -927,26 +986,20 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
     CK(launch_camera_setup_batch(c->bjobs, c->bparams, n, c->bcams, st));
     prof_end(c, k, ART_K_OTHER, 1);
     k = prof_begin(c);
-    CK(launch_enqueue_base_batch(c->bjobs, n, max_base, c->bqueue, c->counters + C_QUEUE,
+    CK(launch_enqueue_base_batch(c->bjobs, n, P.max_base, c->bqueue, c->counters + C_QUEUE,
                                  c->bcounts, st));
     prof_end(c, k, ART_K_OTHER, -1);
-    for (int level = 0; level <= max_levels; ++level) {
+    for (int level = 0; level <= P.max_levels; ++level) {
         c->prof_level = level;
         if (level > 0) {
-            int max_kx = 1, max_ky = 1;
-            for (int i = 0; i < n; ++i)
-                if (J[i].levels >= level) {
-                    int s = 1 << (J[i].levels - level);
-                    max_kx = std::max(max_kx, (J[i].nx - 1) / s + 1);
-                    max_ky = std::max(max_ky, (J[i].ny - 1) / s + 1);
-                }
             CK(cudaMemsetAsync(c->counters + C_QUEUE, 0, sizeof(unsigned long long), st));
             k = prof_begin(c);
-            CK(launch_refine_batch(c->bjobs, n, level, max_kx, max_ky, c->bnorms, c->bimgs, c->bmasks,
-                                   c->bqueue, c->counters + C_QUEUE, c->bcounts, st));
+            CK(launch_refine_batch(c->bjobs, n, level, P.kx[level], P.ky[level], c->bnorms,
+                                   c->bimgs, c->bmasks, c->bqueue, c->counters + C_QUEUE,
+                                   c->bcounts, st));
             prof_end(c, k, ART_K_REFINE, -1);
         }
-        if ((rc = trace_queue_batch(c, J[0], n))) return rc;
+        if ((rc = trace_queue_batch(c, P.J[0], n))) return rc;
         if (level == 0) {
             k = prof_begin(c);
             CK(launch_norm_batch(c->bjobs, c->bimgs, n, c->bnorms, st));
@@ -954,6 +1007,23 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
         }
     }
     c->prof_level = -1;
+    return ART_OK;
+}
+
+static void destroy_plan(BatchPlan* p) { delete p; }
+
+extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const* imgs,
+                                uint8_t* const* masks, art_stats* stats)
+{
+    if (!c || !jobs || !imgs || n < 1) return ART_ERR_ARG;
+    BatchPlan P;
+    int rc = plan_batch(c, jobs, n, imgs, masks, P);
+    if (rc) return rc;
+    CK(cudaSetDevice(c->device));
+    if ((rc = ensure_fixed(c)) || (rc = ensure_batch(c, n, P.qcap))) return rc;
+    cudaStream_t st = c->stream;
+    c->launches = 0;
+    if ((rc = upload_batch(c, P)) || (rc = run_batch(c, P))) return rc;
     if (stats) {
         if ((rc = read_counters(c))) return rc;
         std::vector<double> norms(4 * (size_t)n);
@@ -965,7 +1035,7 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
         for (int i = 0; i < n; ++i) {
             art_stats& o = stats[i];
             memset(&o, 0, sizeof o);
-            for (int l = 0; l <= J[i].levels && l < 16; ++l) {
+            for (int l = 0; l <= P.J[i].levels && l < 16; ++l) {
                 o.rays_per_level[l] = (int64_t)c->bcounts_host[16 * i + l];
                 o.rays_traced += o.rays_per_level[l];
             }
@@ -1190,7 +1260,7 @@ extern "C" int art_graph_render(art_ctx* c, const art_job* job, double* img_dev,
                       c->gimg == img_dev && c->gmask == mask_dev &&
                       c->gtune.quad_rays == c->tune.quad_rays &&
                       c->gtune.pair_rays == c->tune.pair_rays && c->ggrid == c->grid &&
-                      memcmp(c->ggmeta, gmeta, sizeof gmeta) == 0;
+                      memcmp(c->ggmeta, gmeta, sizeof gmeta) == 0 && c->ggen == c->scratch_gen;
     if (!same) {
         // one ordinary render sizes every scratch buffer (no allocation or synchronisation may
         // happen while capturing), then the same call is captured on the capture stream
@@ -1227,10 +1297,89 @@ extern "C" int art_graph_render(art_ctx* c, const art_job* job, double* img_dev,
         c->gtune = c->tune;
         c->ggrid = c->grid;
         memcpy(c->ggmeta, gmeta, sizeof gmeta);
+        c->ggen = c->scratch_gen;
     }
     CK(cudaEventRecord(c->gev_in, c->stream));
     CK(cudaStreamWaitEvent(c->gstream, c->gev_in, 0));
     CK(cudaGraphLaunch(c->gexec, c->gstream));
+    CK(cudaEventRecord(c->gev_out, c->gstream));
+    CK(cudaStreamWaitEvent(c->stream, c->gev_out, 0));
+    return ART_OK;
+}
+
+extern "C" int art_graph_render_batch(art_ctx* c, const art_job* jobs, int32_t n,
+                                      double* const* imgs, uint8_t* const* masks)
+{
+    if (!c || !jobs || !imgs || n < 1) return ART_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (jobs[i].proposal) return ART_ERR_UNSUPPORTED;
+    CK(cudaSetDevice(c->device));
+    if (!c->gstream) {
+        CK(cudaStreamCreateWithFlags(&c->gstream, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming));
+    }
+    const double gmeta[5] = {(double)c->g_n1, (double)c->g_n2, (double)c->g_n3, c->g_x1min,
+                             c->g_x1max};
+    bool same = c->gbexec && c->gbplan && (int)c->gbjobs.size() == n && c->gbgrid == c->grid &&
+                memcmp(c->gbgmeta, gmeta, sizeof gmeta) == 0 && c->gbgen == c->scratch_gen &&
+                memcmp(c->gbjobs.data(), jobs, sizeof(art_job) * n) == 0;
+    for (int i = 0; same && i < n; ++i)
+        same = c->gbimgs[i] == imgs[i] && c->gbmasks[i] == (masks ? masks[i] : nullptr);
+    if (!same) {
+        BatchPlan* P = new BatchPlan();
+        int rc = plan_batch(c, jobs, n, imgs, masks, *P);
+        // one ordinary batch render sizes the scratch; then the device part is captured
+        if (!rc) rc = art_render_batch(c, jobs, n, imgs, masks, nullptr);
+        if (rc) {
+            delete P;
+            return rc;
+        }
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            delete P;
+            return ART_ERR_CUDA;
+        }
+        if (c->gbexec) {
+            cudaGraphExecDestroy(c->gbexec);
+            c->gbexec = nullptr;
+        }
+        destroy_plan(c->gbplan);
+        c->gbplan = nullptr;
+        const bool prof = c->prof_on;
+        cudaStream_t user = c->stream;
+        c->prof_on = false;
+        c->stream = c->gstream;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->gstream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            rc = run_batch(c, *P);
+            e = cudaStreamEndCapture(c->gstream, &graph);
+        }
+        c->stream = user;
+        c->prof_on = prof;
+        if (e == cudaSuccess && rc == ART_OK) e = cudaGraphInstantiate(&c->gbexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (rc || e != cudaSuccess) {
+            delete P;
+            c->gbexec = nullptr;
+            cudaGetLastError();
+            return rc ? rc : ART_ERR_UNSUPPORTED;
+        }
+        c->gbplan = P;
+        c->gbjobs.assign(jobs, jobs + n);
+        c->gbimgs.assign(imgs, imgs + n);
+        c->gbmasks.assign(n, nullptr);
+        if (masks) c->gbmasks.assign(masks, masks + n);
+        c->gbgrid = c->grid;
+        memcpy(c->gbgmeta, gmeta, sizeof gmeta);
+        c->gbgen = c->scratch_gen;
+    }
+    // the job tables are re-uploaded every call (another batch call may have replaced them)
+    int rc = upload_batch(c, *c->gbplan);
+    if (rc) return rc;
+    CK(cudaEventRecord(c->gev_in, c->stream));
+    CK(cudaStreamWaitEvent(c->gstream, c->gev_in, 0));
+    CK(cudaGraphLaunch(c->gbexec, c->gstream));
     CK(cudaEventRecord(c->gev_out, c->gstream));
     CK(cudaStreamWaitEvent(c->stream, c->gev_out, 0));
     return ART_OK;

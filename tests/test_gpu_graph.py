@@ -63,3 +63,47 @@ def test_graph_refuses_learned_jobs(ctx):
     mask = torch.empty((129, 129), dtype=torch.uint8, device="cuda")
     with pytest.raises(RuntimeError, match="unsupported"):
         ctx.art_graph_render(job, img, mask)
+
+
+def test_graph_batch_replay_equals_batch_render(ctx):
+    """A config-3 style batch (mixed sizes and levels) replayed from its graph: images and masks
+    of art_render_batch, on two consecutive calls, and again after a larger single render made the
+    context reallocate its ray queue (the graph is captured anew)."""
+    from paper_2103_07417_gb300 import art
+    params = W.cfg3(seed=5, n=6)
+    for i, p in enumerate(params):
+        k = 5 + (i % 2)
+        N = [1, 2, 3, 2, 3, 1][i]
+        p.update(n0x=(1 << (k - N)) + 1, n0y=(1 << (k - N)) + 1, levels=N)
+    jobs = [art.make_job(**p) for p in params]
+    ref_imgs, ref_masks, _ = ctx.render_batch(jobs)
+    imgs = [torch.full_like(t, np.nan) for t in ref_imgs]
+    masks = [torch.zeros_like(m) for m in ref_masks]
+    for rnd in range(3):
+        if rnd == 2:   # a larger render grows the single-image scratch (and not the batch's)
+            ctx.render(art.make_job(**W.cfg1(n0x=129, n0y=129, levels=3)))
+        for t in imgs:
+            t.fill_(np.nan)
+        for m in masks:
+            m.zero_()
+        ctx.art_graph_render_batch(jobs, imgs, masks)
+        torch.cuda.synchronize()
+        for a, b in zip(imgs, ref_imgs):
+            assert torch.equal(a, b)
+        for a, b in zip(masks, ref_masks):
+            assert torch.equal(a, b)
+
+
+def test_graph_single_recaptures_after_scratch_growth(ctx):
+    """A replayed graph must not use buffers a later, larger render reallocated."""
+    from paper_2103_07417_gb300 import art
+    small = art.make_job(**W.cfg1(n0x=33, n0y=33, levels=2))
+    img, mask, _ = ctx.render(small)
+    ref = img.clone()
+    ctx.art_graph_render(small, img, mask)
+    big = art.make_job(**W.cfg1(n0x=257, n0y=257, levels=3))
+    ctx.render(big)      # grows the ray queue
+    img.fill_(np.nan)
+    ctx.art_graph_render(small, img, mask)
+    torch.cuda.synchronize()
+    assert torch.equal(img, ref)
