@@ -111,7 +111,8 @@ typedef struct art_job {
      * Kerr critical curve, d = |eta - eta_c(lambda)|/27 (Bardeen 1973), is traced speculatively
      * with the base level, so the high-precision re-traces of the photon-ring rays of all levels
      * share one pass.  The exact criterion still decides every point: image and mask equal those
-     * of the render without it.  Not with a truth image (ART_ERR_ARG). */
+     * of the render without it.  Not with a truth image (ART_ERR_ARG).  art_render_batch applies
+     * each job's band to its image, all in the batch's base-level pass. */
     double crit_band;
 } art_job;
 
@@ -209,10 +210,11 @@ int art_render(art_ctx* ctx, const art_job* job, const double* truth_dev, double
  * stokes, subrings, precision and whether the emission is ART_EMIT_GRID (one kernel kind and one
  * plane count per batch; else ART_ERR_ARG); grid jobs all use the context's grid.  imgs is a
  * HOST array of n device pointers (planes x ny_i x nx_i doubles each); masks (nullable, entries
- * nullable) a host array of n device pointers.  stats_host (nullable)
- * receives n entries: rays per level and the normalisation per image; steps, re-traced, capped
- * and NaN rays and kernel launches are batch totals repeated in every entry.  Synchronises when
- * stats are requested.  Errors as art_render. */
+ * nullable) a host array of n device pointers.  Jobs with crit_band > 0 speculate as in
+ * art_render (an image without a mask then uses a context-owned scratch mask).  stats_host
+ * (nullable) receives n entries: rays per level and the normalisation per image; steps,
+ * re-traced, capped, NaN and speculative rays and kernel launches are batch totals repeated in
+ * every entry.  Synchronises when stats are requested.  Errors as art_render. */
 int art_render_batch(art_ctx* ctx, const art_job* jobs, int32_t n, double* const* imgs,
                      uint8_t* const* masks, art_stats* stats_host);
 

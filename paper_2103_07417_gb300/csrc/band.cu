@@ -57,6 +57,50 @@ __device__ __forceinline__ float crit_distance(float a, float lam, float eta)
     return fabsf(eta - eta_c(a, 0.5f * (lo + hi))) * (1.f / 27.f);
 }
 
+// The camera quantities the band test needs, in FP32: the covariant tetrad, the position and its
+// Kerr-Schild radius and polar angle.
+struct BandCam {
+    float E[4][4], x0[3], r0, ct, st;
+};
+
+__device__ __forceinline__ void band_cam_setup(const Camera* cam, float a, BandCam& c)
+{
+    if (threadIdx.x < 16) c.E[threadIdx.x / 4][threadIdx.x % 4] = (float)cam->E[threadIdx.x / 4][threadIdx.x % 4];
+    if (threadIdx.x < 3) c.x0[threadIdx.x] = (float)cam->x0[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const float q = c.x0[0] * c.x0[0] + c.x0[1] * c.x0[1] + c.x0[2] * c.x0[2] - a * a;
+        c.r0 = sqrtf(0.5f * (q + sqrtf(q * q + 4.f * a * a * c.x0[2] * c.x0[2])));
+        c.ct = c.x0[2] / c.r0;
+        c.st = sqrtf(fmaxf(1.f - c.ct * c.ct, 1e-12f));
+    }
+    __syncthreads();
+}
+
+// Whether pixel (i, j) of a job lies within `band` of the critical curve.
+__device__ __forceinline__ bool in_band(const DevJob& J, const BandCam& c, float band, int i, int j)
+{
+    const float a = (float)J.a, ro = (float)J.r_obs, pix = (float)J.pix;
+    const float al = (i - 0.5f * (J.nx - 1)) * pix, be = (j - 0.5f * (J.ny - 1)) * pix;
+    // the critical curve of every spin and inclination lies at impact parameters between 2 M and
+    // 7 M (prograde and retrograde photon orbits of an extremal hole); the pinhole's screen
+    // radius approximates the impact parameter, so screen radii outside (0.5 M, 20 M) are
+    // rejected before the bisection
+    const float b2 = al * al + be * be;
+    if (!(b2 > 0.25f && b2 < 400.f)) return false;
+    const float sc = rsqrtf(1.f + (al * al + be * be) / (ro * ro));
+    float k[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        k[m] = -c.E[0][m] + sc * (-c.E[1][m] + (al / ro) * c.E[3][m] + (be / ro) * c.E[2][m]);
+    const float Een = k[0];
+    const float L = -(c.x0[0] * k[2] - c.x0[1] * k[1]);
+    const float pth = -((c.x0[0] * k[1] + c.x0[1] * k[2]) * c.ct / c.st - c.r0 * c.st * k[3]);
+    const float Q = pth * pth + c.ct * c.ct * (-a * a * Een * Een + L * L / (c.st * c.st));
+    const float lam = L / Een, eta = Q / (Een * Een);
+    return crit_distance(a, lam, eta) < band;
+}
+
 // Every pixel off the base lattice whose mask is unset and whose camera ray lies within `band` of
 // the critical curve is queued for a speculative trace and marked pending (grid-stride over the
 // final grid; slots beyond `cap` are skipped).
@@ -64,18 +108,10 @@ __global__ void __launch_bounds__(256)
     band_propose_kernel(DevJob J, const Camera* cam, float band, uint8_t* mask, int32_t* queue,
                         unsigned long long* counters, unsigned long long cap)
 {
-    __shared__ float E[4][4], x0[3];
-    if (threadIdx.x < 16) E[threadIdx.x / 4][threadIdx.x % 4] = (float)cam->E[threadIdx.x / 4][threadIdx.x % 4];
-    if (threadIdx.x < 3) x0[threadIdx.x] = (float)cam->x0[threadIdx.x];
-    __syncthreads();
+    __shared__ BandCam c;
+    band_cam_setup(cam, (float)J.a, c);
     const int S0 = 1 << J.levels;
     const int64_t npix = (int64_t)J.nx * J.ny;
-    const float a = (float)J.a, ro = (float)J.r_obs, pix = (float)J.pix;
-    const float r0 = sqrtf(0.5f * ((x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2] - a * a) +
-                                   sqrtf((x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2] - a * a) *
-                                             (x0[0] * x0[0] + x0[1] * x0[1] + x0[2] * x0[2] - a * a) +
-                                         4.f * a * a * x0[2] * x0[2])));
-    const float ct = x0[2] / r0, st = sqrtf(fmaxf(1.f - ct * ct, 1e-12f));
     const int lane = threadIdx.x & 31;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npix;
          base += (int64_t)gridDim.x * blockDim.x) {
@@ -83,26 +119,8 @@ __global__ void __launch_bounds__(256)
         bool want = false;
         if (p < npix) {
             const int i = (int)(p % J.nx), j = (int)(p / J.nx);
-            const float al = (i - 0.5f * (J.nx - 1)) * pix, be = (j - 0.5f * (J.ny - 1)) * pix;
-            // the critical curve of every spin and inclination lies at impact parameters between
-            // 2 M and 7 M (prograde and retrograde photon orbits of an extremal hole); the
-            // pinhole's screen radius approximates the impact parameter, so screen radii outside
-            // (0.5 M, 20 M) are rejected before the bisection
-            const float b2 = al * al + be * be;
-            if (b2 > 0.25f && b2 < 400.f && (i % S0 != 0 || j % S0 != 0) &&
-                mask[p] == ART_MASK_UNSET) {
-                const float sc = rsqrtf(1.f + (al * al + be * be) / (ro * ro));
-                float k[4];
-#pragma unroll
-                for (int m = 0; m < 4; ++m)
-                    k[m] = -E[0][m] + sc * (-E[1][m] + (al / ro) * E[3][m] + (be / ro) * E[2][m]);
-                const float Een = k[0];
-                const float L = -(x0[0] * k[2] - x0[1] * k[1]);
-                const float pth = -((x0[0] * k[1] + x0[1] * k[2]) * ct / st - r0 * st * k[3]);
-                const float Q = pth * pth + ct * ct * (-a * a * Een * Een + L * L / (st * st));
-                const float lam = L / Een, eta = Q / (Een * Een);
-                want = crit_distance(a, lam, eta) < band;
-            }
+            want = (i % S0 != 0 || j % S0 != 0) && mask[p] == ART_MASK_UNSET &&
+                   in_band(J, c, band, i, j);
         }
         const unsigned b = __ballot_sync(0xffffffffu, want);
         if (!b) continue;
@@ -120,11 +138,69 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Batched form: blockIdx.y is the image (band[image] <= 0: none), queue entries
+// (image << 32) | pixel.  The kernel also initialises every mask: each pixel of each image is
+// written, pending where queued and unset elsewhere, so no separate clear is needed.
+__global__ void __launch_bounds__(256)
+    band_propose_batch_kernel(const DevJob* jobs, const Camera* cams, const float* bands,
+                              uint8_t* const* masks, int64_t* queue,
+                              unsigned long long* counters, unsigned long long cap)
+{
+    const int im = blockIdx.y;
+    const DevJob J = jobs[im];
+    const float band = bands[im];
+    uint8_t* mask = masks[im];
+    __shared__ BandCam c;
+    band_cam_setup(cams + im, (float)J.a, c);
+    const int S0 = 1 << J.levels;
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < npix;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = base + threadIdx.x;
+        bool want = false;
+        if (p < npix) {
+            const int i = (int)(p % J.nx), j = (int)(p / J.nx);
+            want = band > 0.f && J.levels > 0 && (i % S0 != 0 || j % S0 != 0) &&
+                   in_band(J, c, band, i, j);
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, want);
+        bool queued = false;
+        if (b) {
+            unsigned long long w = 0;
+            if (lane == 0) w = atomicAdd(counters + C_QUEUE, (unsigned long long)__popc(b));
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (want) {
+                const unsigned long long slot = w + __popc(b & ((1u << lane) - 1u));
+                if (slot < cap) {
+                    queue[slot] = ((int64_t)im << 32) | p;
+                    queued = true;
+                    atomicAdd(counters + C_SPEC, 1ull);
+                }
+            }
+        }
+        if (p < npix) mask[p] = queued ? MASK_SPEC_PENDING : (uint8_t)ART_MASK_UNSET;
+    }
+}
+
 cudaError_t launch_band_propose(const DevJob& J, const Camera* cam, double band, uint8_t* mask,
                                 int32_t* queue, unsigned long long* counters,
                                 unsigned long long cap, int num_sms, cudaStream_t st)
 {
     band_propose_kernel<<<num_sms * 8, 256, 0, st>>>(J, cam, (float)band, mask, queue, counters, cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_propose_batch(const DevJob* jobs, const Camera* cams, const float* bands,
+                                      uint8_t* const* masks, int n, int64_t max_npix,
+                                      int64_t* queue, unsigned long long* counters,
+                                      unsigned long long cap, cudaStream_t st)
+{
+    int64_t gx = (max_npix + 255) / 256;
+    if (gx > 64) gx = 64;
+    if (gx < 1) gx = 1;
+    band_propose_batch_kernel<<<dim3((unsigned)gx, n), 256, 0, st>>>(jobs, cams, bands, masks, queue,
+                                                                    counters, cap);
     return cudaGetLastError();
 }
 

@@ -72,6 +72,9 @@ struct art_ctx {
     int64_t* bqueue = nullptr;
     int32_t* breroute = nullptr;
     int64_t bqcap = 0;
+    float* bband = nullptr;      // per image: near-critical band width (0: none)
+    uint8_t* bsmask = nullptr;   // scratch masks of band batches whose caller passed none
+    int64_t bsmask_cap = 0;
     // scratch owned by the library
     int32_t* queue = nullptr;
     int32_t* reroute = nullptr;
@@ -360,6 +363,8 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFreeHost(c->bcounts_host);
     cudaFree(c->bqueue);
     cudaFree(c->breroute);
+    cudaFree(c->bband);
+    cudaFree(c->bsmask);
     cudaFree(c->grid_owned);
     cnn_destroy(c->cnn);
     cudaFree(c->aux);
@@ -827,6 +832,7 @@ static int ensure_batch(art_ctx* c, int n, int64_t qcap)
         cudaFree(c->bnorms);
         cudaFree(c->bcounts);
         cudaFreeHost(c->bcounts_host);
+        cudaFree(c->bband);
         c->bcap = 0;
         CK(cudaMalloc(&c->bjobs, sizeof(DevJob) * n));
         CK(cudaMalloc(&c->bsynch, sizeof(SynchConst) * n));
@@ -837,6 +843,7 @@ static int ensure_batch(art_ctx* c, int n, int64_t qcap)
         CK(cudaMalloc(&c->bnorms, sizeof(double) * 4 * n));
         CK(cudaMalloc(&c->bcounts, sizeof(unsigned long long) * 16 * n));
         CK(cudaMallocHost(&c->bcounts_host, sizeof(unsigned long long) * 16 * n));
+        CK(cudaMalloc(&c->bband, sizeof(float) * n));
         c->bcap = n;
     }
     if (qcap > c->bqcap) {
@@ -852,11 +859,11 @@ static int ensure_batch(art_ctx* c, int n, int64_t qcap)
     return ART_OK;
 }
 
-static int trace_queue_batch(art_ctx* c, const DevJob& J0, int nimg)
+static int trace_queue_batch(art_ctx* c, const DevJob& J0, const unsigned long long* spec_from)
 {
-    (void)nimg;
     BatchTraceArgs a;
     memset(&a, 0, sizeof a);
+    a.spec_from = spec_from;
     a.jobs = c->bjobs;
     a.synchs = c->bsynch;
     a.cams = c->bcams;
@@ -914,6 +921,12 @@ struct BatchPlan {
     int64_t qcap = 0;
     int max_base = 1, max_levels = 0;
     std::vector<int> kx, ky;  // per level >= 1: the largest lattice extents
+    // near-critical band: per-image widths, and where the scratch masks of images without a
+    // caller mask start in the context's scratch (-1: the caller's)
+    bool band = false;
+    std::vector<float> bands;
+    std::vector<int64_t> smask_off;
+    int64_t smask_bytes = 0, max_npix = 1;
 };
 
 static int plan_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const* imgs,
@@ -928,10 +941,22 @@ static int plan_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const*
     P.qcap = 0;
     P.max_base = 1;
     P.max_levels = 0;
+    P.band = false;
+    P.bands.assign(n, 0.f);
+    P.smask_off.assign(n, -1);
+    P.smask_bytes = 0;
+    P.max_npix = 1;
     for (int i = 0; i < n; ++i) {
         int rc = make_devjob(&jobs[i], &P.J[i]);
         if (rc) return rc;
         if (!imgs[i]) return ART_ERR_ARG;
+        if (jobs[i].crit_band > 0.0) {
+            if (!(jobs[i].crit_band < 1.0)) return ART_ERR_ARG;
+            if (P.J[i].levels > 0) {
+                P.bands[i] = (float)jobs[i].crit_band;
+                P.band = true;
+            }
+        }
         if (P.J[i].stokes != P.J[0].stokes || P.J[i].subrings != P.J[0].subrings ||
             P.J[i].precision != P.J[0].precision ||
             (P.J[i].emission == ART_EMIT_GRID) != (P.J[0].emission == ART_EMIT_GRID))
@@ -942,7 +967,10 @@ static int plan_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const*
         P.p3[3 * i + 1] = jobs[i].r_obs;
         P.p3[3 * i + 2] = jobs[i].incl_deg;
         if (masks) P.mk[i] = masks[i];
-        P.qcap += max_level_rays(P.J[i]);
+        const int64_t cap = max_level_rays(P.J[i]), npix = (int64_t)P.J[i].nx * P.J[i].ny;
+        // the band appends speculative rays of later levels to the base level's queue
+        P.qcap += cap + (P.bands[i] > 0.f ? std::min<int64_t>(npix, 4 * cap) : 0);
+        P.max_npix = std::max(P.max_npix, npix);
         int S0 = 1 << P.J[i].levels;
         int nb = ((P.J[i].nx - 1) / S0 + 1) * ((P.J[i].ny - 1) / S0 + 1);
         if (nb > P.max_base) P.max_base = nb;
@@ -957,6 +985,24 @@ static int plan_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const*
                 P.kx[level] = std::max(P.kx[level], (P.J[i].nx - 1) / s + 1);
                 P.ky[level] = std::max(P.ky[level], (P.J[i].ny - 1) / s + 1);
             }
+    // speculation keeps its state in the masks: images without one get a scratch mask
+    if (P.band)
+        for (int i = 0; i < n; ++i)
+            if (!P.mk[i]) {
+                P.smask_off[i] = P.smask_bytes;
+                P.smask_bytes += ((int64_t)P.J[i].nx * P.J[i].ny + 15) & ~(int64_t)15;
+            }
+    return ART_OK;
+}
+
+// Point the plan's missing masks at the context's scratch (grown to fit first).
+static int bind_batch_scratch(art_ctx* c, BatchPlan& P)
+{
+    if (!P.smask_bytes) return ART_OK;
+    int rc = grow(c, c->bsmask, c->bsmask_cap, P.smask_bytes);
+    if (rc) return rc;
+    for (int i = 0; i < P.n; ++i)
+        if (P.smask_off[i] >= 0) P.mk[i] = c->bsmask + P.smask_off[i];
     return ART_OK;
 }
 
@@ -970,6 +1016,7 @@ static int upload_batch(art_ctx* c, const BatchPlan& P)
     CK(cudaMemcpyAsync(c->bparams, P.p3.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->bimgs, P.im.data(), sizeof(double*) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->bmasks, P.mk.data(), sizeof(uint8_t*) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bband, P.bands.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
     return ART_OK;
 }
 
@@ -996,10 +1043,22 @@ static int run_batch(art_ctx* c, const BatchPlan& P)
             k = prof_begin(c);
             CK(launch_refine_batch(c->bjobs, n, level, P.kx[level], P.ky[level], c->bnorms,
                                    c->bimgs, c->bmasks, c->bqueue, c->counters + C_QUEUE,
-                                   c->bcounts, st));
+                                   c->bcounts, st, P.band ? c->counters : nullptr));
             prof_end(c, k, ART_K_REFINE, -1);
         }
-        if ((rc = trace_queue_batch(c, P.J[0], n))) return rc;
+        bool spec = false;
+        if (level == 0 && P.band) {
+            // near-critical band of every finer level of every image, traced with the base level
+            CK(launch_spec_mark(c->counters, st));
+            k = prof_begin(c);
+            CK(launch_band_propose_batch(c->bjobs, c->bcams, c->bband, c->bmasks, n, P.max_npix,
+                                         c->bqueue, c->counters, (unsigned long long)P.qcap, st));
+            prof_end(c, k, ART_K_PROPOSE, -1);
+            CK(launch_queue_clamp(c->counters, (unsigned long long)P.qcap, st));
+            spec = true;
+        }
+        if ((rc = trace_queue_batch(c, P.J[0], spec ? c->counters + C_SPECFROM : nullptr)))
+            return rc;
         if (level == 0) {
             k = prof_begin(c);
             CK(launch_norm_batch(c->bjobs, c->bimgs, n, c->bnorms, st));
@@ -1020,7 +1079,9 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
     int rc = plan_batch(c, jobs, n, imgs, masks, P);
     if (rc) return rc;
     CK(cudaSetDevice(c->device));
-    if ((rc = ensure_fixed(c)) || (rc = ensure_batch(c, n, P.qcap))) return rc;
+    if ((rc = ensure_fixed(c)) || (rc = ensure_batch(c, n, P.qcap)) ||
+        (rc = bind_batch_scratch(c, P)))
+        return rc;
     cudaStream_t st = c->stream;
     c->launches = 0;
     if ((rc = upload_batch(c, P)) || (rc = run_batch(c, P))) return rc;
@@ -1045,6 +1106,8 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
             o.rays_fp64 = (int64_t)c->pinned[C_FP64];
             o.rays_capped = (int64_t)c->pinned[C_CAPPED];
             o.rays_nan = (int64_t)c->pinned[C_NAN];
+            o.rays_speculative = (int64_t)c->pinned[C_SPEC];
+            o.rays_spec_used = (int64_t)c->pinned[C_SPECUSED];
             o.kernel_launches = c->launches;
         }
         if (c->pinned[C_BADIDX] || c->pinned[C_SYNCERR]) return ART_ERR_DEVICE;
@@ -1331,6 +1394,7 @@ extern "C" int art_graph_render_batch(art_ctx* c, const art_job* jobs, int32_t n
         int rc = plan_batch(c, jobs, n, imgs, masks, *P);
         // one ordinary batch render sizes the scratch; then the device part is captured
         if (!rc) rc = art_render_batch(c, jobs, n, imgs, masks, nullptr);
+        if (!rc) rc = bind_batch_scratch(c, *P);
         if (rc) {
             delete P;
             return rc;

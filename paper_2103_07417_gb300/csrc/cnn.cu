@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_halo_kernel(ConvArgs a)
 struct WgradArgs {
     const bf16* X;     // forward input, H x W x CIN
     const bf16* dY;    // Ho x Wo x 32
-    float* grad;       // parameter-gradient vector (accumulated with atomics)
+    float* part;       // per-CTA partial sums: [blockIdx.x][layer parameter]
     int w_off, b_off;  // offsets of this layer's W and b in the vector
     int cin_real;      // channels of the layer's real input (3 or 32)
     int H, W, Ho, Wo, stride;
@@ -422,16 +423,18 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_wgrad_kernel(WgradArgs a)
         if (!ok) break;
     }
     if (ok) {
+        // this CTA's sums over its pixel range, reduced across CTAs in a fixed order afterwards
+        // (wgrad_reduce_kernel), so that training is reproducible
         float v[32];
         umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
         const int m = m0 + warp * 32 + lane;
+        float* part = a.part + (int64_t)blockIdx.x * (CH * 9 * a.cin_real + CH);
         if (m < 9 * CIN) {
             const int tap = m / CIN, ci = m - tap * CIN;
             if (ci < a.cin_real)
-                for (int co = 0; co < CH; ++co)
-                    atomicAdd(a.grad + a.w_off + (co * 9 + tap) * a.cin_real + ci, v[co]);
+                for (int co = 0; co < CH; ++co) part[(co * 9 + tap) * a.cin_real + ci] = v[co];
         } else if (m == 9 * CIN) {
-            for (int co = 0; co < CH; ++co) atomicAdd(a.grad + a.b_off + co, v[co]);
+            for (int co = 0; co < CH; ++co) part[CH * 9 * a.cin_real + co] = v[co];
         }
     } else if (tid == 0) {
         atomicExch(a.err, 1);
@@ -439,6 +442,19 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_wgrad_kernel(WgradArgs a)
     umma::fence_before();
     __syncthreads();
     if (warp == 0) umma::tmem_free(tmem, 32);
+}
+
+// grad[w_off + i] (i < 9 CH cin) or grad[b_off + i - 9 CH cin] += the sum over the CTAs' partials,
+// in CTA order.
+__global__ void wgrad_reduce_kernel(const float* part, int nblk, int cin_real, float* grad,
+                                    int w_off, int b_off)
+{
+    const int nw = CH * 9 * cin_real, np = nw + CH;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * np + i];
+    grad[i < nw ? w_off + i : b_off + (i - nw)] += s;
 }
 
 // BF16 GEMM operands from the FP32 parameters: forward B[co][t CIN + ci] per layer and the input
@@ -487,7 +503,7 @@ __global__ void cnn_input_kernel(const float* feat, int n, bf16* x0)
 constexpr int HEAD_THREADS = 256;
 __global__ void __launch_bounds__(HEAD_THREADS)
     cnn_head_kernel(const bf16* y4, int n, const float* prm, const float* target, float* prob,
-                    bf16* dy4, float* grad, float* loss_sum)
+                    bf16* dy4, float* part)
 {
     __shared__ float red[CH + 2][HEAD_THREADS / 32];
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -548,16 +564,27 @@ __global__ void __launch_bounds__(HEAD_THREADS)
         }
     }
     __syncthreads();
+    // the block's sums of dL/dw_head (CH), dL/db_head and the loss, reduced over the blocks in a
+    // fixed order by head_reduce_kernel
     if (threadIdx.x < CH + 2) {
         float s = 0.f;
         for (int w = 0; w < HEAD_THREADS / 32; ++w) s += red[threadIdx.x][w];
-        if (threadIdx.x < CH)
-            atomicAdd(grad + P_WH + threadIdx.x, s);
-        else if (threadIdx.x == CH)
-            atomicAdd(grad + P_BH, s);
-        else
-            atomicAdd(loss_sum, s);
+        part[(int64_t)blockIdx.x * (CH + 2) + threadIdx.x] = s;
     }
+}
+
+__global__ void head_reduce_kernel(const float* part, int nblk, float* grad, float* loss_sum)
+{
+    const int c = threadIdx.x;
+    if (c >= CH + 2) return;
+    float s = 0.f;
+    for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * (CH + 2) + c];
+    if (c < CH)
+        grad[P_WH + c] += s;
+    else if (c == CH)
+        grad[P_BH] += s;
+    else
+        *loss_sum = s;
 }
 
 // Adam (Kingma & Ba 2015) on the FP32 parameters; clears the gradients.
@@ -589,6 +616,9 @@ struct CnnState {
     int64_t cap = 0;
     bf16 *x0 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *a4 = nullptr;
     bf16 *g1 = nullptr, *g2 = nullptr, *g3 = nullptr, *g4 = nullptr;
+    // per-CTA partial sums of the gradient kernels (reduced in a fixed order)
+    float* part = nullptr;
+    int64_t part_cap = 0;
 };
 
 static int conv_smem(int kpad) { return (128 + CH) * kpad * 2; }
@@ -645,15 +675,32 @@ static cudaError_t run_conv_halo(const ConvArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
-template <int CIN>
-static cudaError_t run_wgrad(WgradArgs a, cudaStream_t st)
+// CTAs along the pixels of a weight-gradient launch: about 2048 output pixels each, at most
+// WG_CTAS (their partial sums are reduced afterwards), every one with a non-empty range.
+constexpr int WG_CTAS = 608;
+static int wgrad_ctas(int npo, int* ppc)
 {
-    const int npo = a.Ho * a.Wo;
     int ctas = (npo + 2047) / 2048;
     if (ctas < 1) ctas = 1;
-    a.pix_per_cta = ((npo + ctas - 1) / ctas + WG_PIX - 1) / WG_PIX * WG_PIX;
+    if (ctas > WG_CTAS) ctas = WG_CTAS;
+    *ppc = ((npo + ctas - 1) / ctas + WG_PIX - 1) / WG_PIX * WG_PIX;
+    return (npo + *ppc - 1) / *ppc;
+}
+
+// Weight and bias gradients of one layer: the tensor-core partial sums, then their reduction into
+// grad (a.part must hold wgrad_ctas() x (9 CH cin_real + CH) floats).
+template <int CIN>
+static cudaError_t run_wgrad(WgradArgs a, float* grad, cudaStream_t st)
+{
+    const int npo = a.Ho * a.Wo;
+    const int ctas = wgrad_ctas(npo, &a.pix_per_cta);
     const int mtiles = (9 * CIN + 1 + 127) / 128;
     conv_wgrad_kernel<CIN><<<dim3(ctas, mtiles), GEMM_THREADS, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int np = CH * 9 * a.cin_real + CH;
+    wgrad_reduce_kernel<<<(np + 255) / 256, 256, 0, st>>>(a.part, ctas, a.cin_real, grad, a.w_off,
+                                                          a.b_off);
     return cudaGetLastError();
 }
 
@@ -704,6 +751,7 @@ void cnn_destroy(CnnState* s)
                     s->a4, s->g1, s->g2, s->g3, s->g4})
         cudaFree(p);
     cudaFree(s->err);
+    cudaFree(s->part);
     delete s;
 }
 
@@ -759,40 +807,56 @@ static cudaError_t forward_backward(CnnState* s, int H, int W, const float* targ
     c.H = H2; c.W = W2; c.Ho = H4; c.Wo = W4;
     CKE((run_conv_halo<2, CH>(c, st)));
     const int n4 = H4 * W4;
-    if (target) CKE(cudaMemsetAsync(s->loss, 0, sizeof(float), st));
-    cnn_head_kernel<<<(n4 + HEAD_THREADS - 1) / HEAD_THREADS, HEAD_THREADS, 0, st>>>(
-        s->a4, n4, s->prm, target, prob, s->g4, s->grad, s->loss);
+    const int hblk = (n4 + HEAD_THREADS - 1) / HEAD_THREADS;
+    if (target) {
+        // partial-sum scratch: the head's blocks, and the largest weight-gradient launch
+        int ppc;
+        int64_t need = (int64_t)hblk * (CH + 2);
+        need = std::max<int64_t>(need, (int64_t)wgrad_ctas(H * W, &ppc) * (CH * 9 * CH + CH));
+        if (need > s->part_cap) {
+            CKE(cudaStreamSynchronize(st));
+            cudaFree(s->part);
+            s->part = nullptr;
+            s->part_cap = 0;
+            CKE(cudaMalloc(&s->part, sizeof(float) * need));
+            s->part_cap = need;
+        }
+    }
+    cnn_head_kernel<<<hblk, HEAD_THREADS, 0, st>>>(s->a4, n4, s->prm, target, prob, s->g4,
+                                                   s->part);
     CKE(cudaGetLastError());
     if (!target) return cudaSuccess;
+    head_reduce_kernel<<<1, 64, 0, st>>>(s->part, hblk, s->grad, s->loss);
+    CKE(cudaGetLastError());
     WgradArgs w{};
-    w.grad = s->grad;
+    w.part = s->part;
     w.err = s->err;
     ConvArgs d{};
     d.err = s->err;
     // layer 4: X = a3 (H2 x W2), dY = g4 (H4 x W4)
     w.X = s->a3; w.dY = s->g4; w.w_off = P_W4; w.b_off = P_B4; w.cin_real = CH;
     w.H = H2; w.W = W2; w.Ho = H4; w.Wo = W4; w.stride = 2;
-    CKE(run_wgrad<CH>(w, st));
+    CKE(run_wgrad<CH>(w, s->grad, st));
     d.src = s->g4; d.B = s->d4; d.mask = s->a3; d.out = s->g3;
     d.H = H2; d.W = W2; d.Ho = H4; d.Wo = W4; d.stride = 2;
     CKE((run_conv<CH, KH, 1>(d, st)));
     // layer 3: X = a2 (H x W), dY = g3 (H2 x W2)
     w.X = s->a2; w.dY = s->g3; w.w_off = P_W3; w.b_off = P_B3;
     w.H = H; w.W = W; w.Ho = H2; w.Wo = W2; w.stride = 2;
-    CKE(run_wgrad<CH>(w, st));
+    CKE(run_wgrad<CH>(w, s->grad, st));
     d.src = s->g3; d.B = s->d3; d.mask = s->a2; d.out = s->g2;
     d.H = H; d.W = W; d.Ho = H2; d.Wo = W2; d.stride = 2;
     CKE((run_conv<CH, KH, 1>(d, st)));
     // layer 2: X = a1, dY = g2 (stride 1)
     w.X = s->a1; w.dY = s->g2; w.w_off = P_W2; w.b_off = P_B2;
     w.Ho = H; w.Wo = W; w.stride = 1;
-    CKE(run_wgrad<CH>(w, st));
+    CKE(run_wgrad<CH>(w, s->grad, st));
     d.src = s->g2; d.B = s->d2; d.mask = s->a1; d.out = s->g1;
     d.Ho = H; d.Wo = W; d.stride = 1;
     CKE((run_conv<CH, KH, 1>(d, st)));
     // layer 1: X = x0 (8 channels, 3 real), dY = g1
     w.X = s->x0; w.dY = s->g1; w.w_off = P_W1; w.b_off = P_B1; w.cin_real = NFEAT;
-    CKE(run_wgrad<CIN0>(w, st));
+    CKE(run_wgrad<CIN0>(w, s->grad, st));
     return cudaSuccess;
 }
 

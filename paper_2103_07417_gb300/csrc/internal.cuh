@@ -76,6 +76,9 @@ struct BatchTraceArgs {
     unsigned long long* counters;
     int32_t* reroute;
     unsigned long long* reroute_count;
+    // first queue slot of the speculative (near-critical band) rays: slots at or beyond it are
+    // marked MASK_SPEC_DONE (nullable)
+    const unsigned long long* spec_from;
     int planes, stokes, precision, emission;
 };
 
@@ -99,7 +102,8 @@ cudaError_t launch_norm_batch(const DevJob* jobs, double* const* imgs, int n, do
 cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_kx, int max_ky,
                                 const double* norms, double* const* imgs, uint8_t* const* masks,
                                 int64_t* queue, unsigned long long* qcount,
-                                unsigned long long* img_counts, cudaStream_t st);
+                                unsigned long long* img_counts, cudaStream_t st,
+                                unsigned long long* spec_counters = nullptr);
 
 // trace.cu
 enum TraceKind { TK_FP64 = 0, TK_FP32 = 1, TK_DF = 2 };
@@ -155,5 +159,9 @@ int64_t cnn_head_cells(const DevJob& J, int level);
 cudaError_t launch_band_propose(const DevJob& J, const Camera* cam, double band, uint8_t* mask,
                                 int32_t* queue, unsigned long long* counters,
                                 unsigned long long cap, int num_sms, cudaStream_t st);
+cudaError_t launch_band_propose_batch(const DevJob* jobs, const Camera* cams, const float* bands,
+                                      uint8_t* const* masks, int n, int64_t max_npix,
+                                      int64_t* queue, unsigned long long* counters,
+                                      unsigned long long cap, cudaStream_t st);
 
 }  // namespace art

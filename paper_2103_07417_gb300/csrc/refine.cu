@@ -704,7 +704,8 @@ cudaError_t launch_norm_batch(const DevJob* jobs, double* const* imgs, int n, do
 __global__ void __launch_bounds__(256)
     refine_batch_kernel(const DevJob* jobs, int level, const double* __restrict__ norms,
                         double* const* imgs, uint8_t* const* masks, int64_t* queue,
-                        unsigned long long* qcount, unsigned long long* img_counts)
+                        unsigned long long* qcount, unsigned long long* img_counts,
+                        unsigned long long* counters)
 {
     const int im = blockIdx.z;
     const DevJob J = jobs[im];
@@ -724,15 +725,17 @@ __global__ void __launch_bounds__(256)
         const int oj = jj & 1;
         for (int i0 = blockIdx.x * blockDim.x; i0 < nkx; i0 += gridDim.x * blockDim.x) {
             const int ii = i0 + (int)threadIdx.x;
-            bool trace = false;
+            bool trace = false, used = false;
             int32_t pix = 0;
             if (ii < nkx) {
                 const int oi = ii & 1;
                 if (oi | oj) {
                     const int i = ii * s, j = jj * s;
                     const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                    trace = refine_point<int>(J, sc, img, mask, i, j, s, cat, norm, npix, false,
-                                         nullptr, nullptr) == 1;
+                    const int r = refine_point<int>(J, sc, img, mask, i, j, s, cat, norm, npix,
+                                                    counters != nullptr, nullptr, nullptr);
+                    trace = r == 1;
+                    used = r == 2;
                     pix = j * J.nx + i;
                 }
             }
@@ -746,6 +749,14 @@ __global__ void __launch_bounds__(256)
                 w = __shfl_sync(0xffffffffu, w, 0);
                 if (trace) queue[w + __popc(b & ((1u << lane) - 1u))] = ((int64_t)im << 32) | pix;
             }
+            // speculative rays of this level the criterion asked for count as its rays
+            if (counters) {
+                const unsigned u = __ballot_sync(0xffffffffu, used);
+                if (u && lane == 0) {
+                    atomicAdd(counters + C_SPECUSED, (unsigned long long)__popc(u));
+                    atomicAdd(img_counts + 16 * im + level, (unsigned long long)__popc(u));
+                }
+            }
         }
     }
 }
@@ -753,7 +764,8 @@ __global__ void __launch_bounds__(256)
 cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_kx, int max_ky,
                                 const double* norms, double* const* imgs, uint8_t* const* masks,
                                 int64_t* queue, unsigned long long* qcount,
-                                unsigned long long* img_counts, cudaStream_t st)
+                                unsigned long long* img_counts, cudaStream_t st,
+                                unsigned long long* spec_counters)
 {
     int gx = (max_kx + 255) / 256;
     if (gx > 16) gx = 16;
@@ -762,7 +774,7 @@ cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_kx
     if (gy > max_ky) gy = max_ky;
     if (gy < 1) gy = 1;
     refine_batch_kernel<<<dim3(gx, gy, n), 256, 0, st>>>(jobs, level, norms, imgs, masks, queue,
-                                                         qcount, img_counts);
+                                                         qcount, img_counts, spec_counters);
     return cudaGetLastError();
 }
 

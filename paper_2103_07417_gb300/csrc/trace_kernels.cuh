@@ -603,7 +603,10 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_batch_kernel(BatchTraceArgs
                     for (int p = 0; p < MAXPL; ++p)
                         if (p < A.planes) img[(int64_t)p * npix + t.pix] = double(t.x.acc[p]);
                     uint8_t* mask = A.masks[t.img];
-                    if (mask) mask[t.pix] = ART_MASK_TRACED;
+                    if (mask)
+                        mask[t.pix] = (A.spec_from && (unsigned long long)t.slot >= *A.spec_from)
+                                          ? MASK_SPEC_DONE
+                                          : (uint8_t)ART_MASK_TRACED;
                 }
                 active = fetch_next();
             }

@@ -83,3 +83,78 @@ def test_batch_rejects_mixed_kinds():
     with pytest.raises(RuntimeError):
         ctx.render_batch([a, b])
     ctx.close()
+
+
+def _small_batch(seed, n, band):
+    """A config-3 style batch of small images (65^2 and 129^2, 2-4 levels) with the given
+    near-critical band width on every image (or a list of widths, one per image)."""
+    params = W.cfg3(seed=seed, n=n)
+    bands = band if isinstance(band, list) else [band] * n
+    for i, p in enumerate(params):
+        k = 6 + (i % 2)
+        N = 2 + (i % 3)
+        p.update(n0x=(1 << (k - N)) + 1, n0y=(1 << (k - N)) + 1, levels=N, crit_band=bands[i])
+    return params
+
+
+@pytest.mark.parametrize("band", [0.03, 0.5, "mixed"])
+def test_batch_band_equals_plain_batch(snap, band):
+    """The near-critical band in the batched path: every image and mask equals the batch rendered
+    without it bit for bit, with the same rays per level; speculative rays were traced."""
+    from paper_2103_07417_gb300 import art
+    ctx = art.Context(0)
+    ctx.load_grid(snap)
+    n = 12
+    widths = [0.03 if i % 2 else 0.0 for i in range(n)] if band == "mixed" else band
+    plain = [art.make_job(**p) for p in _small_batch(11, n, 0.0)]
+    banded = [art.make_job(**p) for p in _small_batch(11, n, widths)]
+    i0, m0, s0 = ctx.render_batch(plain)
+    i1, m1, s1 = ctx.render_batch(banded)
+    torch.cuda.synchronize()
+    for a, b in zip(i0, i1):
+        assert torch.equal(a, b)
+    for a, b in zip(m0, m1):
+        assert torch.equal(a, b)
+    for a, b in zip(s0, s1):
+        assert a["rays_per_level"] == b["rays_per_level"]
+    assert s0[0]["rays_speculative"] == 0
+    assert 0 < s1[0]["rays_spec_used"] <= s1[0]["rays_speculative"]
+    assert s1[0]["rays_fp64"] >= s0[0]["rays_fp64"]
+    ctx.close()
+
+
+def test_batch_band_without_masks(snap):
+    """Images whose caller passes no mask speculate on context-owned scratch masks: the images
+    equal those rendered with masks."""
+    from paper_2103_07417_gb300 import art
+    ctx = art.Context(0)
+    ctx.load_grid(snap)
+    jobs = [art.make_job(**p) for p in _small_batch(12, 6, 0.03)]
+    imgs, masks, _ = ctx.render_batch(jobs)
+    bare = [torch.full_like(t, float("nan")) for t in imgs]
+    ctx.art_render_batch(jobs, bare, None, stats=False)
+    torch.cuda.synchronize()
+    for a, b in zip(imgs, bare):
+        assert torch.equal(a, b)
+    ctx.close()
+
+
+def test_batch_band_moves_retraces_to_the_base_pass(snap):
+    """With the band, the double-float passes after the base level of a config-3 style batch
+    re-trace (almost) nothing: the photon-ring rays of every level of every image were traced
+    with the base level."""
+    from paper_2103_07417_gb300 import art
+    ctx = art.Context(0)
+    ctx.load_grid(snap)
+    jobs = [art.make_job(**p) for p in W.cfg3(seed=0, n=32)]
+    imgs, masks, st = ctx.render_batch(jobs)
+    ctx.art_profile(True)
+    ctx.art_render_batch(jobs, imgs, masks, stats=False)
+    recs = ctx.art_profile_read()
+    ctx.art_profile(False)
+    df = [r for r in recs if r["kind"] == "trace_df"]
+    later = sum(r["steps"] for r in df if r["level"] > 0)
+    print("df steps per level", [(r["level"], r["steps"]) for r in df])
+    assert df[0]["level"] == 0 and df[0]["steps"] > 0
+    assert later <= 0.02 * df[0]["steps"], [(r["level"], r["steps"]) for r in df]
+    ctx.close()

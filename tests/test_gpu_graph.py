@@ -107,3 +107,23 @@ def test_graph_single_recaptures_after_scratch_growth(ctx):
     ctx.art_graph_render(small, img, mask)
     torch.cuda.synchronize()
     assert torch.equal(img, ref)
+
+
+def test_graph_batch_without_masks(ctx):
+    """A batch replayed without caller masks: the near-critical band keeps its state in
+    context-owned scratch masks, bound before the capture; images equal the batch render's."""
+    from paper_2103_07417_gb300 import art
+    params = W.cfg3(seed=8, n=5)
+    for i, p in enumerate(params):
+        N = 2 + (i % 2)
+        p.update(n0x=(1 << (6 - N)) + 1, n0y=(1 << (6 - N)) + 1, levels=N, crit_band=0.03)
+    jobs = [art.make_job(**p) for p in params]
+    ref_imgs, _, _ = ctx.render_batch(jobs)
+    imgs = [torch.full_like(t, np.nan) for t in ref_imgs]
+    for _ in range(2):
+        for t in imgs:
+            t.fill_(np.nan)
+        ctx.art_graph_render_batch(jobs, imgs, None)
+        torch.cuda.synchronize()
+        for a, b in zip(imgs, ref_imgs):
+            assert torch.equal(a, b)
