@@ -108,7 +108,9 @@ typedef struct art_job {
     double proposal_p;
     /* Near-critical band (not in the paper; 0 = off, else 0 < crit_band < 1): every pixel of
      * levels 1..N whose camera ray has constants of motion (lambda, eta) within crit_band of the
-     * Kerr critical curve, d = |eta - eta_c(lambda)|/27 (Bardeen 1973), is traced speculatively
+     * Kerr critical curve (Bardeen 1973), measured as d = |R(r_m)| / r_m^4 with R the photon's
+     * radial potential at its minimum r_m over the photon-orbit radii (|27 - eta - lambda^2|/27
+     * for a = 0), is traced speculatively
      * with the base level, so the high-precision re-traces of the photon-ring rays of all levels
      * share one pass.  The exact criterion still decides every point: image and mask equal those
      * of the render without it.  Not with a truth image (ART_ERR_ARG).  art_render_batch applies

@@ -3,19 +3,22 @@
 //
 // A ray's constants of motion lambda = L_z/E and eta = Q/E^2 (Carter 1968) follow from its initial
 // covariant momentum at the camera.  The rays that orbit the hole before escaping are those with
-// (lambda, eta) close to the critical curve of the spherical photon orbits of radius r in
-// [r_pro, r_ret] (Bardeen 1973):
-//   lambda_c(r) = (r^2 (3 - r) - a^2 (r + 1)) / (a (r - 1)),
-//   eta_c(r)    = r^3 (4 a^2 - r (r - 3)^2) / (a^2 (r - 1)^2),
-//   r_pro, r_ret = 2 (1 + cos(2/3 arccos(-+|a|))),
-// (the circle eta + lambda^2 = 27 for a = 0).  The distance used here is
-// d = |eta - eta_c(lambda)| / 27 (eta_c(lambda) by bisection on r; rays whose lambda lies outside
-// the curve's range are far from it).  These are exactly the rays the FP32 pass hands to the
-// double-float re-trace; tracing every unset pixel of the finer levels with d < band in the same
-// launch as the base level puts all their re-traces into one double-float pass, instead of one
-// latency-bound pass per level.  The exact criterion still decides every point (a speculative ray
-// it does not ask for is overwritten by its interpolant), so images do not change; the band is a
-// scheduling hint evaluated in FP32.
+// (lambda, eta) close to the critical curve of the spherical photon orbits (Bardeen 1973), whose
+// radii lie between the prograde and retrograde equatorial orbits,
+//   r_pro, r_ret = 2 (1 + cos(2/3 arccos(-+|a|))).
+// On the curve the radial potential R(r) (below) has a double root at the orbit's radius: its
+// minimum over [r_pro, r_ret] is zero, slightly positive for rays just inside the shadow and
+// slightly negative for rays just outside.  The distance used here is that minimum over r^4 at
+// the minimiser, d = |R(r_m)| / r_m^4: for a = 0, |27 - eta - lambda^2| / 27, the relative
+// deviation of the impact parameter squared from 27.  Unlike a distance along eta at fixed
+// lambda, it stays proportional to the offset at the two ends of the curve, where it meets the
+// equatorial orbits (eta = 0) with a vertical tangent; those ends are in view for observers near
+// the equatorial plane.  These are exactly the rays the FP32 pass hands to the double-float
+// re-trace; tracing every unset pixel of the finer levels with d < band in the same launch as the
+// base level puts all their re-traces into one double-float pass, instead of one latency-bound
+// pass per level.  The exact criterion still decides every point (a speculative ray it does not
+// ask for is overwritten by its interpolant), so images do not change; the band is a scheduling
+// hint evaluated in FP32.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -25,36 +28,53 @@
 
 namespace art {
 
-__device__ __forceinline__ float lam_c(float a, float r)
+// Radial potential of a photon with constants (lambda, eta) in Boyer-Lindquist r (M = E = 1):
+// R(r) = (r^2 + a^2 - a lambda)^2 - Delta (eta + (lambda - a)^2), Delta = r^2 - 2 r + a^2; the
+// photon moves where R >= 0.
+__device__ __forceinline__ float radial_potential(float a, float lam, float eta, float r)
 {
-    return (r * r * (3.f - r) - a * a * (r + 1.f)) / (a * (r - 1.f));
+    const float A = r * r + a * a - a * lam, D = r * r - 2.f * r + a * a, lm = lam - a;
+    return A * A - D * (eta + lm * lm);
 }
 
-__device__ __forceinline__ float eta_c(float a, float r)
-{
-    const float rm = r - 3.f, r1 = r - 1.f;
-    return r * r * r * (4.f * a * a - r * rm * rm) / (a * a * r1 * r1);
-}
-
-// Distance of (lambda, eta) from the critical curve of spin a (see above).
+// Distance of (lambda, eta) from the critical curve of spin a (see above): |R| at its minimum
+// over the photon-orbit radii [r_pro, r_ret] (golden-section search), over r^4 there.
 __device__ __forceinline__ float crit_distance(float a, float lam, float eta)
 {
-    if (fabsf(a) < 1e-3f) return fabsf(eta + lam * lam - 27.f) * (1.f / 27.f);
     const float aa = fabsf(a);
     float lo = 2.f * (1.f + cosf(2.f / 3.f * acosf(-aa)));  // prograde photon orbit
     float hi = 2.f * (1.f + cosf(2.f / 3.f * acosf(aa)));   // retrograde photon orbit
-    float flo = lam_c(a, lo) - lam, fhi = lam_c(a, hi) - lam;
-    if (flo * fhi > 0.f) return 1e30f;  // lambda outside the curve's range
-    for (int it = 0; it < 40; ++it) {
-        const float mid = 0.5f * (lo + hi), fm = lam_c(a, mid) - lam;
-        if ((fm < 0.f) == (flo < 0.f)) {
-            lo = mid;
-            flo = fm;
+    const float rl = lo, rh = hi;
+    const float g = 0.618034f;
+    float x1 = hi - g * (hi - lo), x2 = lo + g * (hi - lo);
+    float f1 = radial_potential(a, lam, eta, x1), f2 = radial_potential(a, lam, eta, x2);
+    for (int it = 0; it < 24; ++it) {
+        if (f1 < f2) {
+            hi = x2;
+            x2 = x1;
+            f2 = f1;
+            x1 = hi - g * (hi - lo);
+            f1 = radial_potential(a, lam, eta, x1);
         } else {
-            hi = mid;
+            lo = x1;
+            x1 = x2;
+            f1 = f2;
+            x2 = lo + g * (hi - lo);
+            f2 = radial_potential(a, lam, eta, x2);
         }
     }
-    return fabsf(eta - eta_c(a, 0.5f * (lo + hi))) * (1.f / 27.f);
+    float rm = 0.5f * (lo + hi), fm = radial_potential(a, lam, eta, rm);
+    const float fl = radial_potential(a, lam, eta, rl), fh = radial_potential(a, lam, eta, rh);
+    if (fl < fm) {
+        fm = fl;
+        rm = rl;
+    }
+    if (fh < fm) {
+        fm = fh;
+        rm = rh;
+    }
+    const float r2 = rm * rm;
+    return fabsf(fm) / (r2 * r2);
 }
 
 // The camera quantities the band test needs, in FP32: the covariant tetrad, the position and its
