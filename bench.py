@@ -170,9 +170,22 @@ def cpu_baseline(params: dict, snap=None):
         dt = time.perf_counter() - t0
         rays, steps = int(st["rays_traced"]), int(st["steps"])
         note = "one full adaptive render of the workload"
-    return {"value": rays / dt, "unit": "rays/s", "cores": O.get_threads(), "kind": "oracle",
+    cores = O.get_threads()
+    # one core: every 16th base-level ray (a bounded sample of a few seconds)
+    pix1 = _base_pixels(params)[::16]
+    O.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        O.trace_pixels(job, pix1)
+        dt1 = time.perf_counter() - t0
+    finally:
+        O.set_threads(cores)
+    return {"value": rays / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
             "sample": note + " by the FP64 oracle (OpenMP over rays, all host cores)",
-            "seconds": dt, "rays": rays, "steps_per_s": steps / dt}
+            "seconds": dt, "rays": rays, "steps_per_s": steps / dt,
+            "single_core": {"value": pix1.size / dt1, "unit": "rays/s", "cores": 1,
+                            "sample": f"every 16th base-level ray ({pix1.size} rays)",
+                            "seconds": dt1}}
 
 
 def run_reference(args, params, desc):
@@ -330,6 +343,11 @@ def main():
                     "peak_source": PEAK_SOURCE[dom],
                     "launches": d["launches"], "steps": d["steps"],
                     "share_of_step": d["ms"] / total_ms}
+        # the same against this GPU's measured fused multiply-add throughput (own microbenchmark)
+        meas = ctx.art_measure_alu_peaks()
+        mp = meas["fp64_tflops"] if dom == "trace_fp64" else meas["fp32_tflops"]
+        roofline["peak_measured"] = {**meas, "frac": achieved / mp if mp > 0 else None,
+                                     "source": "art_measure_alu_peaks: FMA chains on every SM"}
         if grid_em:
             # every RK4 step samples the grid once (the start point of a ray once more)
             gbs = d["steps"] * GRID_BYTES_PER_SAMPLE / (d["ms"] / 1000.0) / 1e9
@@ -564,6 +582,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": desc, "name": args.workload, "image": f"{nx}x{ny}",
                            "precision": args.precision, "rays_per_step": rays, "tune": tune,
+                           "adaptive_ray_fraction": rays / (nx * ny),
                            "l2": "flushed (512 MB write) before every step, outside the timed "
                                  "region", "parallelism": f"replicas x{world}"},
                 "geodesic_steps_per_s": steps_per_render * args.steps * world / t_dev,

@@ -286,6 +286,13 @@ int art_graph_render_batch(art_ctx* ctx, const art_job* jobs, int32_t n, double*
 int art_profile(art_ctx* ctx, int enable);
 int art_profile_read(art_ctx* ctx, art_launch_record* recs_host, int cap, int* n);
 
+/* Measured peaks of the plain arithmetic pipes (not in the paper; the denominators of the tracer's
+ * roofline): fused multiply-add throughput in TFLOP/s (one FMA = 2 flops) of FP32 and FP64
+ * chains on every SM, the best of three CUDA-event timed launches each, written to *fp32_tflops
+ * and *fp64_tflops (host pointers).  Synchronises the context's stream first; allocates and
+ * frees a small device buffer.  Errors: ART_ERR_ARG (null pointer), ART_ERR_CUDA. */
+int art_measure_alu_peaks(art_ctx* ctx, double* fp32_tflops, double* fp64_tflops);
+
 /* art_trace_pixels for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant.  Some callers cannot let a library call cudaMalloc:
  * a process whose device memory is reserved up front by its own allocator (a render service with

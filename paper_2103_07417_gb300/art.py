@@ -111,7 +111,7 @@ EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_p
            "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid", "art_cnn_load",
            "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step",
            "art_cnn_sample", "art_set_tune", "art_get_tune", "art_autotune", "art_graph_render",
-           "art_graph_render_batch")
+           "art_graph_render_batch", "art_measure_alu_peaks")
 CNN_PARAMS = 28673
 NOALLOC_MAX_RAYS = 1 << 20
 
@@ -157,6 +157,7 @@ def load():
             lib.art_cnn_sample.argtypes = [vp, P(Job), vp, vp, i32, vp, vp]
             lib.art_set_tune.argtypes = [vp, P(Tune)]
             lib.art_get_tune.argtypes = [vp, P(Tune)]
+            lib.art_measure_alu_peaks.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double)]
             lib.art_autotune.argtypes = [vp, P(Job), vp, vp, i32, P(Tune), fp]
             lib.art_graph_render.argtypes = [vp, P(Job), vp, vp]
             lib.art_graph_render_batch.argtypes = [vp, P(Job), i32, P(vp), P(vp)]
@@ -428,6 +429,13 @@ class Context:
         _check(load().art_autotune(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask), int(reps),
                                    ctypes.byref(t), ctypes.byref(ms)), "art_autotune")
         return (t.quad_rays, t.pair_rays), ms.value
+
+    def art_measure_alu_peaks(self) -> dict:
+        """Measured FP32 and FP64 fused multiply-add throughput of this GPU, TFLOP/s."""
+        f32, f64 = ctypes.c_double(), ctypes.c_double()
+        _check(load().art_measure_alu_peaks(self._ctx, ctypes.byref(f32), ctypes.byref(f64)),
+               "art_measure_alu_peaks")
+        return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
 
     def art_profile(self, enable: bool):
         _check(load().art_profile(self._ctx, int(bool(enable))), "art_profile")

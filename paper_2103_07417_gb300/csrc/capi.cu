@@ -784,6 +784,15 @@ extern "C" int art_profile(art_ctx* c, int enable)
     return ART_OK;
 }
 
+extern "C" int art_measure_alu_peaks(art_ctx* c, double* fp32_tflops, double* fp64_tflops)
+{
+    if (!c || !fp32_tflops || !fp64_tflops) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(measure_alu_peaks(c->num_sms, c->stream, fp32_tflops, fp64_tflops));
+    return ART_OK;
+}
+
 extern "C" int art_profile_read(art_ctx* c, art_launch_record* recs, int cap, int* n)
 {
     if (!c || !n || (cap > 0 && !recs)) return ART_ERR_ARG;

@@ -134,6 +134,10 @@ cudaError_t launch_metrics(const double* truth, const double* img, const uint8_t
                            int ny, double* partials, int nblocks, double* out6, cudaStream_t st);
 constexpr int METRIC_BLOCKS = 304;
 
+// peaks.cu: measured FP32 / FP64 fused multiply-add throughput (TFLOP/s)
+cudaError_t measure_alu_peaks(int num_sms, cudaStream_t st, double* fp32_tflops,
+                              double* fp64_tflops);
+
 // cnn.cu
 struct CnnState;
 void cnn_destroy(CnnState* s);
