@@ -75,6 +75,9 @@ def parse():
                     help="skip training the block-proposal network and the learned path")
     ap.add_argument("--single", action="store_true",
                     help="one warm-up and one render, nothing else (for profiler captures)")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="one warm-up and one batched render of the 256-image config-3 batch, "
+                         "nothing else (for profiler captures)")
     ap.add_argument("--cnn", action="store_true",
                     help="one forward and one gradient pass of the block-proposal network on a "
                          "seeded 1025 x 1025 lattice, nothing else (for profiler captures)")
@@ -271,6 +274,17 @@ def main():
         ctx.art_cnn_load(W.cnn_init(0))
         cnn_measure(ctx, 1025, reps=1)
         print(json.dumps({"cnn": 1025}))
+        ctx.close()
+        return
+    if args.batch_only:
+        if snap is None:
+            snap = W.grmhd_snapshot(seed=0)
+            ctx.load_grid(snap)
+        bjobs = [art.make_job(**p) for p in W.cfg3(seed=0, n=256)]
+        bimgs, bmasks, _ = ctx.render_batch(bjobs)
+        bst = ctx.art_render_batch(bjobs, bimgs, bmasks)
+        print(json.dumps({"batch": len(bjobs), "rays": sum(b["rays_traced"] for b in bst),
+                          "steps": bst[0]["steps"]}))
         ctx.close()
         return
     if args.single:
@@ -475,7 +489,16 @@ def main():
                    "rays_per_s": brays / tb, "images_per_s": len(bjobs) / tb,
                    "ms_per_batch": 1000 * tb, "ms_per_batch_graph": 1000 * tg,
                    "rays": brays, "pixels": bpix,
-                   "geodesic_steps_per_s": bst[0]["steps"] / tb}
+                   "geodesic_steps_per_s": bst[0]["steps"] / tb,
+                   "rays_speculative": bst[0]["rays_speculative"],
+                   "rays_spec_used": bst[0]["rays_spec_used"]}
+        # per-launch split of one batched render (CUDA events on the library's stream)
+        ctx.art_profile(True)
+        ctx.art_render_batch(bjobs, bimgs, bmasks, stats=False)
+        brecs = ctx.art_profile_read()
+        ctx.art_profile(False)
+        batched["launches"] = [{"kind": r["kind"], "level": r["level"], "ms": round(r["ms"], 4),
+                                "steps": r["steps"]} for r in brecs]
         del bimgs, bmasks
 
     # the learned path: train the block-proposal network on seeded plain renders (the library's
