@@ -191,6 +191,45 @@ def cpu_baseline(params: dict, snap=None):
                             "seconds": dt1}}
 
 
+def accuracy(ctx, params: dict, img, mask):
+    """The render against the FP64 path on the same workload, per plane (Stokes parameter, or
+    subring n for unpolarized subring images): the BJ error sum (dI)^2 / (N mean(I)^2) of the
+    whole adaptive image against the FP64 adaptive render, the part of it on points whose mask
+    differs (the criterion decided them differently because its inputs differ by rounding; one
+    render traced the point, the other interpolated it), and the per-ray error over every traced
+    ray against the FP64 trace of the same ray."""
+    import torch
+    from paper_2103_07417_gb300 import art
+    if params.get("precision") == "fp64":
+        return None
+    job64 = art.make_job(**{**params, "precision": "fp64"})
+    ref, rmask, _ = ctx.render(job64)
+    planes = img.shape[0]
+    m0 = float(ref[0].double().mean())
+    n = img[0].numel()
+    d2 = (img - ref).double() ** 2
+    flip = mask != rmask
+    whole = [float(d2[c].sum()) / (n * m0 * m0) for c in range(planes)]
+    on_flips = [float(d2[c][flip].sum()) / (n * m0 * m0) for c in range(planes)]
+    pix = torch.nonzero(mask.reshape(-1) == art.MASK_TRACED).reshape(-1).to(torch.int32)
+    out = torch.empty((pix.numel(), planes), dtype=torch.float64, device=img.device)
+    ctx.art_trace_pixels(job64, pix, out)
+    got = img.reshape(planes, -1)[:, pix.long()].T
+    mr = float(out[:, 0].mean())
+    per_ray = [float(((got[:, c] - out[:, c]) ** 2).sum()) / (pix.numel() * mr * mr)
+               for c in range(planes)]
+    if params.get("stokes", 1) == 4:
+        names = [f"{'IQUV'[c % 4]}" + (f"_n{c // 4}" if params.get("subrings", 0) else "")
+                 for c in range(planes)]
+    else:
+        names = [f"I_n{c}" if params.get("subrings", 0) else "I" for c in range(planes)]
+    del ref, rmask, d2, out, got
+    return {"against": "the FP64 path on the same workload (equal to the FP64 oracle to 1e-6)",
+            "planes": names, "image_bj": whole, "image_bj_on_mask_flips": on_flips,
+            "mask_flips": int(flip.sum()), "traced_rays": int(pix.numel()),
+            "per_ray_bj": per_ray}
+
+
 def run_reference(args, params, desc):
     """The reference arm: the FP64 oracle on the host cores.  Each step is a bounded sample of the
     workload: one full adaptive render (unpolarized analytic) or 2048 evenly spaced base-level
@@ -415,6 +454,7 @@ def main():
                                             "ms_per_step": 1000 * tg / kp,
                                             "rays_high_precision": stats["rays_fp64"]}
     ctx.art_render(job, img, mask, stats=False)
+    acc = accuracy(ctx, params, img, mask)
     paths[args.precision] = {"rays_per_s": value / world,
                              "geodesic_steps_per_s": steps_per_render * args.steps / t_dev,
                              "ms_per_step": 1000 * t_dev / args.steps,
@@ -499,6 +539,23 @@ def main():
         ctx.art_profile(False)
         batched["launches"] = [{"kind": r["kind"], "level": r["level"], "ms": round(r["ms"], 4),
                                 "steps": r["steps"]} for r in brecs]
+        # per-image error against the FP64 batch, per subring plane
+        rjobs = [art.make_job(**{**p, "precision": "fp64"}) for p in bparams]
+        rimgs, rmasks, _ = ctx.render_batch(rjobs)
+        per = []
+        flips = 0
+        for a, b, ma, mb in zip(bimgs, rimgs, bmasks, rmasks):
+            m0 = float(b.sum(0).double().mean())
+            n = a[0].numel()
+            per.append([float(((a[c] - b[c]).double() ** 2).sum()) / (n * m0 * m0)
+                        for c in range(a.shape[0])])
+            flips += int((ma != mb).sum())
+        per = np.array(per)
+        batched["accuracy"] = {
+            "against": "the FP64 batch", "planes": [f"I_n{c}" for c in range(per.shape[1])],
+            "image_bj_median": np.median(per, 0).tolist(), "image_bj_max": per.max(0).tolist(),
+            "images_above_1e-5": int((per.sum(1) > 1e-5).sum()), "mask_flips": flips}
+        del rimgs, rmasks
         del bimgs, bmasks
 
     # the learned path: train the block-proposal network on seeded plain renders (the library's
@@ -610,7 +667,8 @@ def main():
                                  "region", "parallelism": f"replicas x{world}"},
                 "geodesic_steps_per_s": steps_per_render * args.steps * world / t_dev,
                 "paths": paths, "batched": batched, "learned": learned, "cnn": cnn,
-                "time_to_mse": time_to_mse, "roofline": roofline, "kernels": kernels,
+                "time_to_mse": time_to_mse, "accuracy": acc, "roofline": roofline,
+                "kernels": kernels,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(stats["kernel_launches"]) * args.steps}
         print(json.dumps(line), flush=True)

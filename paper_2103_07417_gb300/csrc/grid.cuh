@@ -116,7 +116,11 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     const Q iut = Q(1) / u[0];
 #pragma unroll
     for (int i = 1; i < 4; ++i) b[i] = fmad(b[0], u[i], B[i]) * iut;
-    const Q b2 = G.dot(b, b);
+    // b^mu b_mu = (g_ij B^i B^j + (b^t)^2) / (u^t)^2 (from b^mu = (B^mu + b^t u^mu)/u^t and
+    // u.u = -1): two positive terms, where the four-vector contraction -(b^t)^2 + ... cancels
+    // (by whole factors in FP32 for fast flows, which then moved points across the sigma cut)
+    const Q BB = fmad(B[3], B[3], fmad(B[2], B[2], B[1] * B[1]));
+    const Q b2 = fmad(b[0], b[0], fmad(G.F * LB, LB, BB)) * (iut * iut);
     if (!(b2 > Q(0))) return;
     if (b2 > Q(S.g_sigma_cut) * rho) return;
     const Q pg = Q(S.g_gm1) * ug, pm = Q(0.5) * b2;
