@@ -52,6 +52,12 @@ PEAK_TFLOPS = {"trace_fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "trace_fp64": 1.25,
 PEAK_SOURCE = {"trace_fp32": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                "trace_df": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (FP32 pipes)",
                "trace_fp64": "nominal GB300 dense FP64"}
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the
+# second of two renders (`bench.py --single [--workload cfg2]` under
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:trace_kernel`), averaged over
+# that render's FP32-pass launches (5 for config 1, 6 for config 2).  Reset to None whenever the
+# trace kernels change.
+TRAFFIC_PER_LAUNCH = {("cfg1", "trace_fp32"): 437558.0, ("cfg2", "trace_fp32"): 90996130.0}
 HBM_PEAK_GBPS = 6779.0  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
 DTYPE = {"mixed": "f32+f64", "mixed_df": "f32+df32x2", "fp64": "f64", "fp32": "f32"}
 METRIC = "rays/s"
@@ -392,7 +398,9 @@ def main():
         achieved = d["steps"] * fps[dom] / (d["ms"] / 1000.0) / 1e12
         peak = PEAK_TFLOPS[dom]
         roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, dom)),
+                    "traffic_unit": "bytes per launch (ncu, cold cache)",
                     "peak_source": PEAK_SOURCE[dom],
                     "launches": d["launches"], "steps": d["steps"],
                     "share_of_step": d["ms"] / total_ms}
