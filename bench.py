@@ -197,6 +197,23 @@ def cpu_baseline(params: dict, snap=None):
                             "seconds": dt1}}
 
 
+def max_over_ranks(t_local: float, dist=None, device=None) -> float:
+    """The slowest rank's time (an all-reduce MAX over the process group); t_local alone when
+    the run has one process."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return t_local
+    import torch
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(rays_per_step: int, steps: int, world: int, t_max: float) -> float:
+    """Replicas: every rank renders its own copy of the workload, so the job traces
+    rays_per_step x steps rays on each of `world` ranks within the slowest rank's time."""
+    return rays_per_step * steps * world / t_max
+
+
 def accuracy(ctx, params: dict, img, mask):
     """The render against the FP64 path on the same workload, per plane (Stokes parameter, or
     subring n for unpolarized subring images): the BJ error sum (dI)^2 / (N mean(I)^2) of the
@@ -370,10 +387,8 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
-    value = rays * args.steps * world / t_dev
+    t_dev = max_over_ranks(t_dev, dist, dev)
+    value = whole_job_value(rays, args.steps, world, t_dev)
     clocks = clk.summary()
 
     # per-kernel timing of one render with CUDA events on the library's stream
