@@ -149,7 +149,7 @@ struct PairRing {
     static constexpr int NPAIR = TRACE_BLOCK / 64;
     static constexpr int STG = NF > 13 ? 13 : 0;  // first stage field (0: none carried)
     Q v[NPAIR][SPLIT_SLOTS][NF][32];
-    int32_t code[NPAIR][SPLIT_SLOTS][32], pix[NPAIR][SPLIT_SLOTS][32];
+    int32_t code[NPAIR][SPLIT_SLOTS][32], pix[NPAIR][SPLIT_SLOTS][32], img[NPAIR][SPLIT_SLOTS][32];
     int64_t slot[NPAIR][SPLIT_SLOTS][32];
     int32_t last[NPAIR][SPLIT_SLOTS];
     uint64_t full[NPAIR][SPLIT_SLOTS], empty[NPAIR][SPLIT_SLOTS];
@@ -166,58 +166,149 @@ __device__ __forceinline__ void pair_ring_init(Ring& sm)
             }
 }
 
+// Outputs of a finished ray of the batched kernels: as finish_ray, into the ray's own image.
+template <class Q>
+__device__ __forceinline__ void finish_batch_ray(const BatchTraceArgs& A, int status, int steps,
+                                                 const XferState<Q>& x, int32_t pix, int64_t slot,
+                                                 int32_t img)
+{
+    atomicAdd(A.counters + C_STEPS, (unsigned long long)steps);
+    const bool rer = A.reroute != nullptr &&
+                     (status == RAY_REROUTE || status == ART_RAY_NAN || status == ART_RAY_CAP);
+    if (rer) {
+        unsigned long long w = atomicAdd(A.reroute_count, 1ull);
+        A.reroute[w] = (int32_t)slot;
+        return;
+    }
+    if (status == ART_RAY_CAP) atomicAdd(A.counters + C_CAPPED, 1ull);
+    if (status == ART_RAY_NAN) atomicAdd(A.counters + C_NAN, 1ull);
+    if (A.indirect) atomicAdd(A.counters + C_FP64, 1ull);
+    const DevJob& J = A.jobs[img];
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    double* out = A.imgs[img];
+#pragma unroll
+    for (int p = 0; p < MAXPL; ++p)
+        if (p < A.planes) out[(int64_t)p * npix + pix] = double(x.acc[p]);
+    uint8_t* mask = A.masks[img];
+    if (mask)
+        mask[pix] = (A.spec_from && (unsigned long long)slot >= *A.spec_from)
+                        ? MASK_SPEC_DONE
+                        : (uint8_t)ART_MASK_TRACED;
+}
+
+// Where the rays of a launch come from and where their results go, for the forms that hand a
+// ray's step between warps: one image (job, constants and camera shared by every ray) or a batch
+// (each queue entry names its image).  next() takes the next valid queue entry (warp-aggregated;
+// false once the queue is drained), finish() writes a finished ray.
+struct SingleSource {
+    const TraceArgs& A;
+    const Camera& cam;
+    unsigned long long n;
+    __device__ const DevJob& job(int32_t) const { return A.job; }
+    __device__ const SynchConst& synch(int32_t) const { return A.synch; }
+    __device__ const Camera& camera(int32_t) const { return cam; }
+    __device__ unsigned long long* counters() const { return A.counters; }
+    __device__ bool next(int64_t& slot, int32_t& pix, int32_t& img) const
+    {
+        while (true) {
+            const unsigned long long q = warp_fetch(A.fetch);
+            if (q >= n) return false;
+            const int64_t sq = A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
+            const int32_t px = A.queue[sq];
+            if (px < 0 || (int64_t)px >= A.npix) {
+                atomicAdd(A.counters + C_BADIDX, 1ull);
+                continue;
+            }
+            slot = sq;
+            pix = px;
+            img = 0;
+            return true;
+        }
+    }
+    template <class Q>
+    __device__ void finish(int status, int steps, const XferState<Q>& x, int32_t pix, int64_t slot,
+                           int32_t) const
+    {
+        finish_ray(A, status, steps, x, pix, slot);
+    }
+};
+
+struct BatchSource {
+    const BatchTraceArgs& A;
+    unsigned long long n;
+    __device__ const DevJob& job(int32_t img) const { return A.jobs[img]; }
+    __device__ const SynchConst& synch(int32_t img) const { return A.synchs[img]; }
+    __device__ const Camera& camera(int32_t img) const { return A.cams[img]; }
+    __device__ unsigned long long* counters() const { return A.counters; }
+    __device__ bool next(int64_t& slot, int32_t& pix, int32_t& img) const
+    {
+        while (true) {
+            const unsigned long long q = warp_fetch(A.fetch);
+            if (q >= n) return false;
+            const int64_t sq = A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
+            const int64_t e = A.queue[sq];
+            const int32_t im = (int32_t)(e >> 32), px = (int32_t)(e & 0xffffffff);
+            const DevJob& J = A.jobs[im];
+            if (px < 0 || (int64_t)px >= (int64_t)J.nx * J.ny) {
+                atomicAdd(A.counters + C_BADIDX, 1ull);
+                continue;
+            }
+            slot = sq;
+            pix = px;
+            img = im;
+            return true;
+        }
+    }
+    template <class Q>
+    __device__ void finish(int status, int steps, const XferState<Q>& x, int32_t pix, int64_t slot,
+                           int32_t img) const
+    {
+        finish_batch_ray(A, status, steps, x, pix, slot, img);
+    }
+};
+
 // Warp-pair form (the ring's mbarriers initialised and the block synchronised before the call).
 template <class R, bool POL>
 using PairRingOf = PairRing<typename Aux<R>::Q, XportOnGeo<R, POL>::value ? 13 : 13 + NSTG>;
 
-template <class R, bool SWEEP, bool POL, int EM>
-__device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& cam_s,
-                                            PairRingOf<R, POL>& sm)
+template <class R, bool SWEEP, bool POL, int EM, class Src>
+__device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL>& sm)
 {
     using Q = typename Aux<R>::Q;
     constexpr int NSL = SPLIT_SLOTS;
-    const DevJob& J = A.job;
-    const SynchConst& S = A.synch;
-    const unsigned long long n = *A.count;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, pr = warp >> 1;
     if ((warp & 1) == 0) {
         // geodesic warp
         GeoState<R> g;
         bool has = false, drained = false;
-        int32_t pix = 0;
+        int32_t pix = 0, img = 0;
         int64_t slot = 0;
         for (int it = 0;; ++it) {
             const int sl = it % NSL;
             const uint32_t ph = (uint32_t)(it / NSL) & 1u;
             if (it >= NSL &&
                 !__all_sync(0xffffffffu, pair_wait(&sm.empty[pr][sl], ph ^ 1u))) {
-                if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
+                if (lane == 0) atomicAdd(src.counters() + C_SYNCERR, 1ull);
                 return;
             }
             StepPoint<Q> pt;
             int code = REC_IDLE;
             if (has) {
-                code = geo_step<R, SWEEP, POL, EM>(g, J, pt, &sm.v[pr][sl][PairRingOf<R, POL>::STG][lane], 32);
+                code = geo_step<R, SWEEP, POL, EM>(g, src.job(img), pt,
+                                                   &sm.v[pr][sl][PairRingOf<R, POL>::STG][lane], 32);
                 if (code != RAY_GOING) has = false;
             } else if (!drained) {
-                while (true) {
-                    const unsigned long long q = warp_fetch(A.fetch);
-                    if (q >= n) {
-                        drained = true;
-                        break;
-                    }
-                    const int64_t sq = A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
-                    const int32_t px = A.queue[sq];
-                    if (px < 0 || (int64_t)px >= A.npix) {
-                        atomicAdd(A.counters + C_BADIDX, 1ull);
-                        continue;
-                    }
-                    geo_init<R, POL>(g, J, cam_s, px, pt);
+                int64_t sq;
+                int32_t px, im;
+                if (src.next(sq, px, im)) {
+                    geo_init<R, POL>(g, src.job(im), src.camera(im), px, pt);
                     pix = px;
+                    img = im;
                     slot = sq;
                     has = true;
                     code = REC_INIT;
-                    break;
+                } else {
+                    drained = true;
                 }
             }
             if (code != REC_IDLE) {
@@ -236,6 +327,7 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
             }
             sm.code[pr][sl][lane] = code;
             sm.pix[pr][sl][lane] = pix;
+            sm.img[pr][sl][lane] = img;
             sm.slot[pr][sl][lane] = slot;
             const bool last = __all_sync(0xffffffffu, code == REC_IDLE && drained);
             if (lane == 0) sm.last[pr][sl] = last ? 1 : 0;
@@ -246,14 +338,14 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
     } else {
         // transfer warp
         XferState<Q> x;
-        int32_t pix = 0;
+        int32_t pix = 0, img = 0;
         int64_t slot = 0;
         int steps = 0;
         for (int it = 0;; ++it) {
             const int sl = it % NSL;
             const uint32_t ph = (uint32_t)(it / NSL) & 1u;
             if (!__all_sync(0xffffffffu, pair_wait(&sm.full[pr][sl], ph))) {
-                if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
+                if (lane == 0) atomicAdd(src.counters() + C_SYNCERR, 1ull);
                 return;
             }
             const int code = sm.code[pr][sl][lane];
@@ -275,8 +367,10 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
             }
             if (code == REC_INIT) {
                 pix = sm.pix[pr][sl][lane];
+                img = sm.img[pr][sl][lane];
                 slot = sm.slot[pr][sl][lane];
             }
+            const DevJob& J = src.job(img);
             const bool moving = code != REC_IDLE && code != REC_INIT && code != ART_RAY_NAN &&
                                 code != RAY_REROUTE;
             if (!XportOnGeo<R, POL>::value && moving)
@@ -284,12 +378,12 @@ __device__ __forceinline__ void trace_pairs(const TraceArgs& A, const Camera& ca
             __syncwarp();
             pair_arrive(&sm.empty[pr][sl]);
             if (code == REC_INIT) {
-                xfer_init<Q, POL, EM>(x, pt, J, S);
+                xfer_init<Q, POL, EM>(x, pt, J, src.synch(img));
                 steps = 0;
             } else if (code != REC_IDLE) {
                 ++steps;
-                if (moving) xfer_step<Q, POL, EM>(x, pt, J, S);
-                if (code != RAY_GOING) finish_ray(A, code, steps, x, pix, slot);
+                if (moving) xfer_step<Q, POL, EM>(x, pt, J, src.synch(img));
+                if (code != RAY_GOING) src.finish(code, steps, x, pix, slot, img);
             }
             if (last) return;
         }
@@ -542,15 +636,16 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
             if (n <= blocks * (unsigned long long)A.quad_rays)
                 trace_quads<SWEEP, POL, EM>(A, cam_s, qring);
             else if (n <= blocks * (unsigned long long)A.pair_rays)
-                trace_pairs<R, SWEEP, POL, EM>(A, cam_s, ring);
+                trace_pairs<R, SWEEP, POL, EM>(SingleSource{A, cam_s, n}, ring);
             else
                 trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
         } else {
             __syncthreads();
             const unsigned long long pair_lanes =
                 (unsigned long long)gridDim.x * PairRingOf<R, POL>::NPAIR * 32ull;
-            if (*A.count <= pair_lanes)
-                trace_pairs<R, SWEEP, POL, EM>(A, cam_s, ring);
+            const unsigned long long n = *A.count;
+            if (n <= pair_lanes)
+                trace_pairs<R, SWEEP, POL, EM>(SingleSource{A, cam_s, n}, ring);
             else
                 trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
         }
@@ -561,7 +656,17 @@ template <class R, bool SWEEP, bool POL, int EM>
 __global__ void __launch_bounds__(TRACE_BLOCK) trace_batch_kernel(BatchTraceArgs A)
 {
     const unsigned long long n = *A.count;
-    const bool mixed32 = (A.reroute != nullptr);
+    if constexpr (std::is_same<R, df>::value) {
+        // the double-float re-trace holds few rays (the near-critical ones of the whole batch):
+        // the warp-pair form whenever the queue fits the grid's pairs, as for a single image
+        __shared__ __align__(16) PairRingOf<R, POL> ring;
+        pair_ring_init(ring);
+        __syncthreads();
+        if (n <= (unsigned long long)gridDim.x * PairRingOf<R, POL>::NPAIR * 32ull) {
+            trace_pairs<R, SWEEP, POL, EM>(BatchSource{A, n}, ring);
+            return;
+        }
+    }
     Tracer<R> t;
     bool active = false;
     auto fetch_next = [&]() {
@@ -587,27 +692,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_batch_kernel(BatchTraceArgs
         if (active) {
             const DevJob& J = A.jobs[t.img];
             if (ray_step<R, SWEEP, POL, EM>(t, J, A.synchs[t.img])) {
-                atomicAdd(A.counters + C_STEPS, (unsigned long long)t.g.steps);
-                bool rer = mixed32 && (t.status == RAY_REROUTE || t.status == ART_RAY_NAN ||
-                                       t.status == ART_RAY_CAP);
-                if (rer) {
-                    unsigned long long w = atomicAdd(A.reroute_count, 1ull);
-                    A.reroute[w] = (int32_t)t.slot;
-                } else {
-                    if (t.status == ART_RAY_CAP) atomicAdd(A.counters + C_CAPPED, 1ull);
-                    if (t.status == ART_RAY_NAN) atomicAdd(A.counters + C_NAN, 1ull);
-                    if (A.indirect) atomicAdd(A.counters + C_FP64, 1ull);
-                    const int64_t npix = (int64_t)J.nx * J.ny;
-                    double* img = A.imgs[t.img];
-#pragma unroll
-                    for (int p = 0; p < MAXPL; ++p)
-                        if (p < A.planes) img[(int64_t)p * npix + t.pix] = double(t.x.acc[p]);
-                    uint8_t* mask = A.masks[t.img];
-                    if (mask)
-                        mask[t.pix] = (A.spec_from && (unsigned long long)t.slot >= *A.spec_from)
-                                          ? MASK_SPEC_DONE
-                                          : (uint8_t)ART_MASK_TRACED;
-                }
+                finish_batch_ray(A, t.status, t.g.steps, t.x, t.pix, t.slot, t.img);
                 active = fetch_next();
             }
         }
