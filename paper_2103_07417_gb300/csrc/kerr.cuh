@@ -55,6 +55,21 @@ ART_HD double fmad<double>(double a, double b, double c)
     return fma(a, b, c);
 }
 
+// x c for a power of two c: exact in every arithmetic (a double-float scales both parts, which
+// keeps them normalised, instead of a full double-float product).
+template <class R>
+ART_HD R scale2(R x, float c)
+{
+    return x * R(c);
+}
+
+// 2 x + c: one fused multiply-add (for double-float: the exact scaling above and one addition).
+template <class R>
+ART_HD R twice_plus(R x, R c)
+{
+    return fmad(R(2), x, c);
+}
+
 // Job parameters as the kernels see them (POD, passed by value).
 struct DevJob {
     double a, a2, r_obs, pix, step_frac, h_min, r_in_stop, r_out_stop, inv_2w2;
@@ -80,7 +95,7 @@ ART_HD R ks_radius(R x, R y, R z, R a2)
 {
     R z2 = z * z;
     R b = (fmad(y, y, x * x) + z2) - a2;
-    R r2 = R(0.5) * (b + sqrt(fmad(b, b, R(4) * a2 * z2)));
+    R r2 = scale2(b + sqrt(fmad(b, b, scale2(a2, 4.f) * z2)), 0.5f);
     return sqrt(r2);
 }
 
@@ -92,13 +107,13 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
     R z2 = z * z;
     R a2z2 = a2 * z2;
     R b = (fmad(y, y, x * x) + z2) - a2;
-    R r2 = R(0.5) * (b + sqrt(fmad(b, b, R(4) * a2z2)));
+    R r2 = scale2(b + sqrt(fmad(b, b, scale2(a2z2, 4.f))), 0.5f);
     R ir = rsqrt(r2);
     R r = r2 * ir;
     R ir2 = ir * ir;
     R r4 = r2 * r2;
     R iQ = R(1) / (r4 + a2z2);
-    R f = R(2) * r2 * r * iQ;
+    R f = scale2(r2, 2.f) * r * iQ;
     R ira2 = R(1) / (r2 + a2);
     R Lx = fmad(r, x, -(a * y)) * ira2;
     R Ly = fmad(r, y, a * x) * ira2;
@@ -108,10 +123,10 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
     R iSig = r2 * iQ;  // Sigma = r^2 + a^2 z^2 / r^2 = Q / r^2
     R rs = r * iSig;
     R drx = x * rs, dry = y * rs, drz = z * (r2 + a2) * ir * iSig;
-    R B = f * ir * fmad(R(-4) * r4, iQ, R(3));
-    R A = fmad(fmad(R(-2) * r, Lkxy, fmad(y, ky, x * kx)), ira2, -(kz * z * ir2));
+    R B = f * ir * fmad(scale2(r4, -4.f), iQ, R(3));
+    R A = fmad(fmad(scale2(r, -2.f), Lkxy, fmad(y, ky, x * kx)), ira2, -(kz * z * ir2));
     R flk = f * lk;
-    R C = fmad(R(0.5) * B * lk, lk, -(flk * A));
+    R C = fmad(scale2(B, 0.5f) * lk, lk, -(flk * A));
     R Tx = fmad(r, kx, a * ky) * ira2;
     R Ty = fmad(r, ky, -(a * kx)) * ira2;
     R Tz = kz * ir;

@@ -316,7 +316,7 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
     Q hq = Q(J.step_frac) * t.r;
     if (hq < Q(J.h_min)) hq = Q(J.h_min);
     const R h = R(hq);
-    const R hh = R(0.5) * h;
+    const R hh = scale2(h, 0.5f);
     const Q hhq = Q(0.5) * hq;
     // ks = k1 + 2 k2 + 2 k3 + k4 (summed in that order) and likewise ds for the polarization.
     // The double-float and the polarized analytic-emission kernels run the four stages as one
@@ -337,9 +337,9 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
             if (st == 0) {
                 ks = k;
             } else if (st < 3) {
-                ks.x = fmad(R(2), k.x, ks.x); ks.y = fmad(R(2), k.y, ks.y);
-                ks.z = fmad(R(2), k.z, ks.z); ks.kx = fmad(R(2), k.kx, ks.kx);
-                ks.ky = fmad(R(2), k.ky, ks.ky); ks.kz = fmad(R(2), k.kz, ks.kz);
+                ks.x = twice_plus(k.x, ks.x); ks.y = twice_plus(k.y, ks.y);
+                ks.z = twice_plus(k.z, ks.z); ks.kx = twice_plus(k.kx, ks.kx);
+                ks.ky = twice_plus(k.ky, ks.ky); ks.kz = twice_plus(k.kz, ks.kz);
             } else {
                 ks.x = ks.x + k.x; ks.y = ks.y + k.y; ks.z = ks.z + k.z;
                 ks.kx = ks.kx + k.kx; ks.ky = ks.ky + k.ky; ks.kz = ks.kz + k.kz;
@@ -368,9 +368,9 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
                 if (POL)
                     for (int m = 0; m < 4; ++m) ds[m] = d[m];
             } else if (st < 3) {
-                ks.x = fmad(R(2), k.x, ks.x); ks.y = fmad(R(2), k.y, ks.y);
-                ks.z = fmad(R(2), k.z, ks.z); ks.kx = fmad(R(2), k.kx, ks.kx);
-                ks.ky = fmad(R(2), k.ky, ks.ky); ks.kz = fmad(R(2), k.kz, ks.kz);
+                ks.x = twice_plus(k.x, ks.x); ks.y = twice_plus(k.y, ks.y);
+                ks.z = twice_plus(k.z, ks.z); ks.kx = twice_plus(k.kx, ks.kx);
+                ks.ky = twice_plus(k.ky, ks.ky); ks.kz = twice_plus(k.kz, ks.kz);
                 if (POL)
                     for (int m = 0; m < 4; ++m) ds[m] = fmad(Q(2), d[m], ds[m]);
             } else {
@@ -409,12 +409,12 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
             for (int m = 0; m < 4; ++m) fy[m] = fmad(hq, d3[m], t.f[m]);
             transport_rhs<Q>(to_q<Q>(y), Q(t.kt), fy, aq, a2q, d4);
         }
-        ks.x = fmad(R(2), k3.x, fmad(R(2), k2.x, k1.x)) + k4.x;
-        ks.y = fmad(R(2), k3.y, fmad(R(2), k2.y, k1.y)) + k4.y;
-        ks.z = fmad(R(2), k3.z, fmad(R(2), k2.z, k1.z)) + k4.z;
-        ks.kx = fmad(R(2), k3.kx, fmad(R(2), k2.kx, k1.kx)) + k4.kx;
-        ks.ky = fmad(R(2), k3.ky, fmad(R(2), k2.ky, k1.ky)) + k4.ky;
-        ks.kz = fmad(R(2), k3.kz, fmad(R(2), k2.kz, k1.kz)) + k4.kz;
+        ks.x = twice_plus(k3.x, twice_plus(k2.x, k1.x)) + k4.x;
+        ks.y = twice_plus(k3.y, twice_plus(k2.y, k1.y)) + k4.y;
+        ks.z = twice_plus(k3.z, twice_plus(k2.z, k1.z)) + k4.z;
+        ks.kx = twice_plus(k3.kx, twice_plus(k2.kx, k1.kx)) + k4.kx;
+        ks.ky = twice_plus(k3.ky, twice_plus(k2.ky, k1.ky)) + k4.ky;
+        ks.kz = twice_plus(k3.kz, twice_plus(k2.kz, k1.kz)) + k4.kz;
         if (POL)
             for (int m = 0; m < 4; ++m)
                 ds[m] = fmad(Q(2), d3[m], fmad(Q(2), d2[m], d1[m])) + d4[m];
