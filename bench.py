@@ -53,12 +53,13 @@ PEAK_SOURCE = {"trace_fp32": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                "trace_df": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (FP32 pipes)",
                "trace_fp64": "nominal GB300 dense FP64"}
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the
-# second of two renders (`bench.py --single [--workload cfg2]` under
+# second of two renders (`bench.py --single [--workload grmhd_8193]` under
 # `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:trace_kernel`), averaged over
-# that render's FP32-pass launches (5 for config 1, 6 for config 2).  Reset to None whenever the
-# trace kernels change.
-TRAFFIC_PER_LAUNCH = {("cfg1", "trace_fp32"): 437558.0, ("cfg2", "trace_fp32"): 90996130.0}
-HBM_PEAK_GBPS = 6779.0  # measured copy bandwidth of the GB300s (MEASURED_PEAKS.json)
+# that render's FP32-pass launches (5 for the 2049^2 polarized render, 6 for the 8193^2 grid
+# render).  Reset to None whenever the trace kernels change.
+TRAFFIC_PER_LAUNCH = {("kerr_disk_2049", "trace_fp32"): 437558.0,
+                      ("grmhd_8193", "trace_fp32"): 90996130.0}
+HBM_PEAK_GBPS = 6779.0  # measured STREAM-style copy bandwidth of a GB300, GB/s
 DTYPE = {"mixed": "f32+f64", "mixed_df": "f32+df32x2", "fp64": "f64", "fp32": "f32"}
 METRIC = "rays/s"
 
@@ -69,7 +70,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cfg1", choices=sorted(W.BENCH_WORKLOADS))
+    ap.add_argument("--workload", default="kerr_disk_2049", choices=sorted(W.BENCH_WORKLOADS))
     ap.add_argument("--precision", default="mixed_df", choices=["mixed", "mixed_df", "fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-render measurement")
@@ -82,7 +83,7 @@ def parse():
     ap.add_argument("--single", action="store_true",
                     help="one warm-up and one render, nothing else (for profiler captures)")
     ap.add_argument("--batch-only", action="store_true",
-                    help="one warm-up and one batched render of the 256-image config-3 batch, "
+                    help="one warm-up and one batched render of the 256-image mixed-parameter batch, "
                          "nothing else (for profiler captures)")
     ap.add_argument("--cnn", action="store_true",
                     help="one forward and one gradient pass of the block-proposal network on a "
@@ -342,7 +343,7 @@ def main():
         if snap is None:
             snap = W.grmhd_snapshot(seed=0)
             ctx.load_grid(snap)
-        bjobs = [art.make_job(**p) for p in W.cfg3(seed=0, n=256)]
+        bjobs = [art.make_job(**p) for p in W.grmhd_batch(seed=0, n=256)]
         bimgs, bmasks, _ = ctx.render_batch(bjobs)
         bst = ctx.art_render_batch(bjobs, bimgs, bmasks)
         print(json.dumps({"batch": len(bjobs), "rays": sum(b["rays_traced"] for b in bst),
@@ -511,9 +512,9 @@ def main():
     # level for all of them) on the same GPU
     batched = None
     if not args.no_batch:
-        if snap is None:   # the batch renders config 2's emission model: load its snapshot
+        if snap is None:   # the batch renders the grid emission model: load its snapshot
             ctx.load_grid(W.grmhd_snapshot(seed=0))
-        bparams = W.cfg3(seed=0, n=256)
+        bparams = W.grmhd_batch(seed=0, n=256)
         bjobs = [art.make_job(**p) for p in bparams]
         bimgs, bmasks = [], []
         for bj in bjobs:
@@ -545,9 +546,9 @@ def main():
             evs.append((e0, e1))
         torch.cuda.synchronize()
         tg = sum(a.elapsed_time(b) for a, b in evs) / 1000.0 / len(evs)
-        batched = {"workload": "256 images (config-3 recipe): a~U[-0.94,0.94], i~U[10,170] deg, "
+        batched = {"workload": "256 images (mixed-parameter batch): a~U[-0.94,0.94], i~U[10,170] deg, "
                                "FOV log-U[40,400] M, 65^2..513^2 over 2-6 levels, emission from "
-                               "the config-2 snapshot (288x128x128 grid), subrings n=0,1,2, "
+                               "the GRMHD-like snapshot (288x128x128 grid), subrings n=0,1,2, "
                                "mixed_df",
                    "rays_per_s": brays / tb, "images_per_s": len(bjobs) / tb,
                    "ms_per_batch": 1000 * tb, "ms_per_batch_graph": 1000 * tg,
@@ -625,12 +626,12 @@ def main():
         nlat = 2049
         t_fw, t_fb = cnn_measure(lctx, nlat)
         fl = cnn_flops(nlat, nlat)
-        peak = 1941.4  # measured cuBLAS BF16 burst TFLOP/s of the GB300s
+        peak = 1941.4  # measured cuBLAS BF16 dense GEMM rate of a GB300 (burst), TFLOP/s
         cnn = {"lattice": f"{nlat}x{nlat}", "forward_ms": 1000 * t_fw,
                "forward_backward_ms": 1000 * t_fb,
                "roofline": {"bound": "tensor", "achieved": fl / t_fw / 1e12, "peak": peak,
                             "unit": "TFLOP/s", "frac": fl / t_fw / 1e12 / peak,
-                            "peak_source": "measured cuBLAS bf16 burst (MEASURED_PEAKS.json)",
+                            "peak_source": "measured cuBLAS bf16 dense GEMM, burst",
                             "flops_per_forward": fl}}
 
     # time to a 0.1 %-MSE image (paper MSE vs the full FP64 trace) for each path: the fastest

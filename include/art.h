@@ -45,7 +45,7 @@ extern "C" {
 #define ART_ERR_UNSUPPORTED (-4) /* option combination not built */
 #define ART_ERR_DEVICE (-5)      /* a kernel reported an internal inconsistency */
 
-enum { ART_EMIT_CFG0 = 0, ART_EMIT_SYNCH_DISK = 1, ART_EMIT_GRID = 2 };
+enum { ART_EMIT_ANALYTIC = 0, ART_EMIT_SYNCH_DISK = 1, ART_EMIT_GRID = 2 };
 enum { ART_FLOW_KEPLER = 0, ART_FLOW_STATIC = 1 };
 enum { ART_NORM_IBAR_INT = 0, ART_NORM_PEAK = 1 };
 enum { ART_INTERP_LINEAR = 0, ART_INTERP_NEAREST = 1 };

@@ -25,7 +25,7 @@ _SRC = [os.path.join(_HERE, "art_oracle.c")]
 _lock = threading.Lock()
 _lib = None
 
-EMIT_CFG0, EMIT_SYNCH_DISK, EMIT_GRID, EMIT_BLOB = 0, 1, 2, 8
+EMIT_ANALYTIC, EMIT_SYNCH_DISK, EMIT_GRID, EMIT_BLOB = 0, 1, 2, 8
 FLOW_KEPLER, FLOW_STATIC = 0, 1
 NORM_IBAR_INT, NORM_PEAK = 0, 1
 INTERP_LINEAR, INTERP_NEAREST = 0, 1
@@ -87,7 +87,7 @@ class Stats(ctypes.Structure):
 
 _DEFAULTS = dict(a=0.0, mass=1.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33, n0y=33,
                  levels=2, R_rel=0.01, R_abs=1e-4, abs_norm=NORM_IBAR_INT,
-                 interp=INTERP_LINEAR, edge_mode=EDGE_ONESIDED, emission=EMIT_CFG0,
+                 interp=INTERP_LINEAR, edge_mode=EDGE_ONESIDED, emission=EMIT_ANALYTIC,
                  flow=FLOW_KEPLER, stokes=1, subrings=0, max_steps=100000, step_frac=0.05,
                  h_min=1e-4, horizon_eps=0.01, escape_frac=1.01, disk_w=0.3, blob_sigma=1.0,
                  ne0=0.0, thetae0=0.0, b0=0.0, nu_hz=230e9, ne_slope=-1.1, te_slope=-0.84,
@@ -96,7 +96,7 @@ _DEFAULTS = dict(a=0.0, mass=1.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33,
 
 
 _NAMES = dict(
-    emission={"cfg0": EMIT_CFG0, "synch_disk": EMIT_SYNCH_DISK, "grid": EMIT_GRID,
+    emission={"analytic": EMIT_ANALYTIC, "synch_disk": EMIT_SYNCH_DISK, "grid": EMIT_GRID,
               "blob": EMIT_BLOB},
     flow={"kepler": FLOW_KEPLER, "static": FLOW_STATIC},
     abs_norm={"ibar_int": NORM_IBAR_INT, "peak": NORM_PEAK},
@@ -106,7 +106,7 @@ _NAMES = dict(
 
 
 def make_job(grid=None, **params) -> Job:
-    """Build the oracle's job from a parameter dict; option names ("cfg0", "peak", ...) are
+    """Build the oracle's job from a parameter dict; option names ("analytic", "peak", ...) are
     mapped to the oracle's enums and keys the oracle does not use are ignored.
 
     grid: the fluid snapshot for emission "grid", a dict with ``data`` (float32, shape

@@ -412,7 +412,7 @@ static void emission_unpol(const orc_job* job, const double* y, double* J, doubl
         double s2 = job->blob_sigma * job->blob_sigma;
         double d2 = y[1] * y[1] + y[2] * y[2] + y[3] * y[3];
         jnu = exp(-d2 / (2.0 * s2));
-    } else { /* ORC_EMIT_CFG0: j = r^-2 exp(-z^2 / (2 (w r)^2)), z = r cos(theta) */
+    } else { /* ORC_EMIT_ANALYTIC: j = r^-2 exp(-z^2 / (2 (w r)^2)), z = r cos(theta) */
         double ct = y[3] / r;
         double w = job->disk_w;
         jnu = exp(-ct * ct / (2.0 * w * w)) / (r * r);

@@ -15,7 +15,7 @@ extern "C" {
 #endif
 
 /* Emission models. */
-enum { ORC_EMIT_CFG0 = 0,      /* j = r^-2 exp(-z^2/(2 (w r)^2)), Keplerian flow, no absorption */
+enum { ORC_EMIT_ANALYTIC = 0,      /* j = r^-2 exp(-z^2/(2 (w r)^2)), Keplerian flow, no absorption */
        ORC_EMIT_SYNCH_DISK = 1,/* thermal synchrotron thin disk, polarized (Stokes IQUV)       */
        ORC_EMIT_GRID = 2,      /* thermal synchrotron from a fluid grid (rho, u, u^i, B^i)      */
        ORC_EMIT_BLOB = 8 };    /* flat-space test: static Gaussian blob, sigma = blob_sigma    */

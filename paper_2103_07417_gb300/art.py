@@ -21,7 +21,7 @@ MASK_UNSET, MASK_TRACED, MASK_INTERP = 0, 1, 2
 RAY_ESCAPED, RAY_CAPTURED, RAY_CAP, RAY_NAN = 0, 1, 2, 3
 
 _NAMES = dict(
-    emission={"cfg0": 0, "synch_disk": 1, "grid": 2},
+    emission={"analytic": 0, "synch_disk": 1, "grid": 2},
     flow={"kepler": 0, "static": 1},
     abs_norm={"ibar_int": 0, "peak": 1},
     interp={"linear": 0, "nearest": 1},

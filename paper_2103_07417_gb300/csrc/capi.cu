@@ -185,10 +185,10 @@ static int make_devjob(const art_job* job, DevJob* J)
         return ART_ERR_ARG;
     if (job->stokes != 1 && job->stokes != 4) return ART_ERR_UNSUPPORTED;
     if (job->subrings < 0 || job->subrings > 4) return ART_ERR_UNSUPPORTED;
-    if (job->emission != ART_EMIT_CFG0 && job->emission != ART_EMIT_SYNCH_DISK &&
+    if (job->emission != ART_EMIT_ANALYTIC && job->emission != ART_EMIT_SYNCH_DISK &&
         job->emission != ART_EMIT_GRID)
         return ART_ERR_UNSUPPORTED;
-    if (job->stokes == 4 && job->emission == ART_EMIT_CFG0) return ART_ERR_UNSUPPORTED;
+    if (job->stokes == 4 && job->emission == ART_EMIT_ANALYTIC) return ART_ERR_UNSUPPORTED;
     if (job->emission == ART_EMIT_SYNCH_DISK &&
         (!(job->ne0 >= 0.0) || !(job->thetae0 > 0.0) || !(job->b0 > 0.0) || !(job->nu_hz > 0.0) ||
          !(job->length_cm > 0.0) || !(job->r_in >= 0.0)))

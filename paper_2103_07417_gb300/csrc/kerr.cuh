@@ -143,7 +143,7 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
 // (z = r cos(theta)) for a fluid that is Keplerian (Omega = 1/(r^{3/2} + a) at Boyer-Lindquist
 // (r, theta), zero where no timelike such orbit exists) or static; nu = k_mu u^mu.
 template <class R>
-ART_HD R emission_cfg0(const RayState<R>& s, R r, R kt, const DevJob& J)
+ART_HD R emission_analytic(const RayState<R>& s, R r, R kt, const DevJob& J)
 {
     if (r < R(J.r_in_stop)) return R(0);
     R ct = s.z / r;

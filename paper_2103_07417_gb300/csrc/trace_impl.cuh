@@ -198,7 +198,7 @@ __device__ __forceinline__ void coefficients(const RayState<Q>& q, Q r, Q kt, co
     }
     for (int i = 1; i < 4; ++i) J4[i] = Q(0);
     for (int i = 0; i < 7; ++i) K7[i] = Q(0);
-    J4[0] = emission_cfg0<Q>(q, r, kt, J);
+    J4[0] = emission_analytic<Q>(q, r, kt, J);
 }
 
 // Geodesic part of a ray's start: camera ray of pixel pix; fills the start point for the transfer

@@ -17,8 +17,8 @@ from . import workloads as W
 def training_jobs(seed: int, n: int) -> list:
     """n seeded jobs mixing the three emission models at small sizes (final 129^2 .. 513^2 over
     3..5 levels), random spin, inclination and field of view: the configuration-3 recipe,
-    alternating the grid snapshot, the synchrotron disk of configuration 1 and the analytic
-    emissivity of configuration 0."""
+    alternating the grid snapshot, the polarized synchrotron disk and the analytic
+    Keplerian emissivity."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
@@ -31,11 +31,11 @@ def training_jobs(seed: int, n: int) -> list:
         common = dict(a=a, incl_deg=incl, fov=fov, n0x=n0, n0y=n0, levels=N, precision="mixed_df")
         kind = i % 3
         if kind == 0:
-            p = W.cfg2(**common)
+            p = W.grmhd_8193(**common)
         elif kind == 1:
-            p = W.cfg1(**common, stokes=1, r_in=W.r_isco(a))
+            p = W.kerr_disk_2049(**common, stokes=1, r_in=W.r_isco(a))
         else:
-            p = W.cfg1_analytic(**common)
+            p = W.kerr_analytic_2049(**common)
         out.append(p)
     return out
 

@@ -14,7 +14,7 @@ from __future__ import annotations
 import numpy as np
 
 # Options shared by both sides by NAME (each side owns its enum values).
-EMISSION = ("cfg0", "synch_disk", "grid", "blob")
+EMISSION = ("analytic", "synch_disk", "grid", "blob")
 FLOW = ("kepler", "static")
 ABS_NORM = ("ibar_int", "peak")
 INTERP = ("linear", "nearest")
@@ -23,7 +23,7 @@ PRECISION = ("fp64", "mixed", "fp32")
 
 BASE = dict(a=0.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33, n0y=33, levels=2,
             R_rel=0.01, R_abs=1e-4, abs_norm="ibar_int", interp="linear", edge_mode="onesided",
-            emission="cfg0", flow="kepler", stokes=1, subrings=0, precision="fp64",
+            emission="analytic", flow="kepler", stokes=1, subrings=0, precision="fp64",
             max_steps=100000, step_frac=0.05, h_min=1e-4, horizon_eps=0.01, escape_frac=1.01,
             disk_w=0.3, blob_sigma=1.0, ne0=0.0, thetae0=0.0, b0=0.0, nu_hz=230e9,
             ne_slope=-1.1, te_slope=-0.84, r_in=0.0, length_cm=9.6e14, bz_ratio=1.0,
@@ -42,18 +42,18 @@ def job(**over) -> dict:
 CRIT_BAND = 0.03
 
 
-def cfg0(**over) -> dict:
+def schwarzschild_129(**over) -> dict:
     """Schwarzschild, inclination 60 deg, r_obs 1000 M, FOV 40 M, j = r^-2 exp(-z^2/(2(0.3r)^2)),
     Keplerian, no absorption, FP64 RK4 with h = 0.05 r, 33^2 -> 129^2 over 2 levels,
     R_rel = 0.01, R_abs = 1e-4 of the peak."""
     return job(**{**dict(a=0.0, incl_deg=60.0, fov=40.0, n0x=33, n0y=33, levels=2, R_rel=0.01,
-                         R_abs=1e-4, abs_norm="peak", emission="cfg0", disk_w=0.3), **over})
+                         R_abs=1e-4, abs_norm="peak", emission="analytic", disk_w=0.3), **over})
 
 
-def cfg0_large(**over) -> dict:
-    """The cfg0 emission model on the 129^2 -> 2049^2 (4 levels) grid, paper tolerances
+def schwarzschild_large(**over) -> dict:
+    """The schwarzschild_129 emission model on the 129^2 -> 2049^2 (4 levels) grid, paper tolerances
     R_rel = R_abs = 1e-3 of I_bar_int (Sec. 4.1, semi-analytic models)."""
-    return cfg0(**{**dict(n0x=129, n0y=129, levels=4, R_rel=1e-3, R_abs=1e-3,
+    return schwarzschild_129(**{**dict(n0x=129, n0y=129, levels=4, R_rel=1e-3, R_abs=1e-3,
                           abs_norm="ibar_int"), **over})
 
 
@@ -105,7 +105,7 @@ def r_isco(a: float) -> float:
     return 3 + z2 - ((3 - z1) * (3 + z1 + 2 * z2)) ** 0.5 * (1 if a >= 0 else -1)
 
 
-def cfg1(**over) -> dict:
+def kerr_disk_2049(**over) -> dict:
     """Kerr a = 0.94, inclination 17 deg, FOV 40 M; thermal-synchrotron thin disk
     (n_e ~ r^-1.1, T_e ~ r^-0.84, toroidal : vertical field = 1 : 1, |B| ~ r^-0.97, Gaussian
     vertical profile of width 0.1 r, Keplerian, inner edge at the ISCO) at 230 GHz for an M87*-mass
@@ -120,16 +120,16 @@ def cfg1(**over) -> dict:
                          precision="mixed_df", crit_band=CRIT_BAND), **over})
 
 
-def cfg1_analytic(**over) -> dict:
+def kerr_analytic_2049(**over) -> dict:
     """The Kerr geometry of the 128^2 -> 2048^2 configuration (a = 0.94, inclination 17 deg,
     FOV 40 M, base 129^2, 4 levels to 2049^2, R_rel = R_abs = 1e-3 of I_bar_int) with the
     analytic emissivity j = r^-2 exp(-z^2/(2 (0.3 r)^2)) of a Keplerian flow, mixed precision."""
     return job(**{**dict(a=0.94, incl_deg=17.0, fov=40.0, n0x=129, n0y=129, levels=4,
-                         R_rel=1e-3, R_abs=1e-3, abs_norm="ibar_int", emission="cfg0",
+                         R_rel=1e-3, R_abs=1e-3, abs_norm="ibar_int", emission="analytic",
                          disk_w=0.3, precision="mixed", crit_band=CRIT_BAND), **over})
 
 
-def cfg2(**over) -> dict:
+def grmhd_8193(**over) -> dict:
     """The seeded GRMHD-like snapshot (grmhd_snapshot(0): Fishbone-Moncrief torus, a = 0.94,
     288 x 128 x 128 cells over ln r in [ln 1.2, ln 1000]) seen at inclination 163 deg with a
     160 M field of view, 257^2 -> 8193^2 over 5 levels, at 230 GHz with R_high = 20, R_low = 1,
@@ -144,38 +144,43 @@ def cfg2(**over) -> dict:
                          precision="mixed_df", crit_band=CRIT_BAND), **over})
 
 
-def cfg4(**over) -> dict:
-    """Evaluation workload of the learned block proposal: config 2's snapshot and emission seen
+def grmhd_16385(**over) -> dict:
+    """Evaluation workload of the learned block proposal: the GRMHD-like snapshot and its emission seen
     with a 1000 M field of view, 257^2 -> 16385^2 over 6 levels (the photon ring and the torus
     cover a small part of the image; most blocks of the finer levels are never refined)."""
-    return cfg2(**{**dict(fov=1000.0, levels=6), **over})
+    return grmhd_8193(**{**dict(fov=1000.0, levels=6), **over})
 
 
 BENCH_WORKLOADS = {
-    "cfg1": ("adaptive polarized render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, FOV 40 M, "
-             "r_obs 1000 M, RK4 h=0.05r; thermal-synchrotron thin disk (n_e~r^-1.1, T_e~r^-0.84, "
-             "toroidal:vertical B = 1:1) at 230 GHz, Stokes IQUV with Faraday rotation/conversion; "
-             "R_rel=R_abs=1e-3", cfg1),
-    "cfg1_analytic": ("adaptive render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, "
-                      "FOV 40 M, r_obs 1000 M, RK4 h=0.05r, analytic Keplerian emissivity "
-                      "r^-2 exp(-z^2/(2(0.3r)^2)), R_rel=R_abs=1e-3", cfg1_analytic),
-    "cfg2": ("adaptive render 257^2 -> 8193^2 (5 levels) of a seeded GRMHD-like snapshot "
-             "(Fishbone-Moncrief torus a=0.94 + lognormal k^-11/3 turbulence, 288x128x128 FP32 "
-             "cells over ln r in [ln 1.2, ln 1000]), i=163 deg, FOV 160 M, r_obs 1000 M, RK4 "
-             "h=0.05r, thermal synchrotron at 230 GHz with R_high=20, sigma cut 1; "
-             "R_rel=1e-3, R_abs=0.025", cfg2),
-    "cfg4": ("learned-proposal evaluation render 257^2 -> 16385^2 (6 levels) of the config-2 "
-             "snapshot and emission, i=163 deg, FOV 1000 M, r_obs 1000 M, RK4 h=0.05r; "
-             "R_rel=1e-3, R_abs=0.025", cfg4),
-    "cfg0": ("adaptive render 33^2 -> 129^2 (2 levels), Schwarzschild, i=60 deg, FOV 40 M, "
-             "R_rel=0.01, R_abs=1e-4 of peak", cfg0),
+    "kerr_disk_2049": (
+        "adaptive polarized render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, FOV 40 M, "
+        "r_obs 1000 M, RK4 h=0.05r; thermal-synchrotron thin disk (n_e~r^-1.1, T_e~r^-0.84, "
+        "toroidal:vertical B = 1:1) at 230 GHz, Stokes IQUV with Faraday rotation/conversion; "
+        "R_rel=R_abs=1e-3", kerr_disk_2049),
+    "kerr_analytic_2049": (
+        "adaptive render 129^2 -> 2049^2 (4 levels), Kerr a=0.94, i=17 deg, FOV 40 M, "
+        "r_obs 1000 M, RK4 h=0.05r, analytic Keplerian emissivity r^-2 exp(-z^2/(2(0.3r)^2)), "
+        "R_rel=R_abs=1e-3", kerr_analytic_2049),
+    "grmhd_8193": (
+        "adaptive render 257^2 -> 8193^2 (5 levels) of a seeded GRMHD-like snapshot "
+        "(Fishbone-Moncrief torus a=0.94 + lognormal k^-11/3 turbulence, 288x128x128 FP32 "
+        "cells over ln r in [ln 1.2, ln 1000]), i=163 deg, FOV 160 M, r_obs 1000 M, RK4 "
+        "h=0.05r, thermal synchrotron at 230 GHz with R_high=20, sigma cut 1; "
+        "R_rel=1e-3, R_abs=0.025", grmhd_8193),
+    "grmhd_16385": (
+        "learned-proposal evaluation render 257^2 -> 16385^2 (6 levels) of the GRMHD-like "
+        "snapshot and emission, i=163 deg, FOV 1000 M, r_obs 1000 M, RK4 h=0.05r; "
+        "R_rel=1e-3, R_abs=0.025", grmhd_16385),
+    "schwarzschild_129": (
+        "adaptive render 33^2 -> 129^2 (2 levels), Schwarzschild, i=60 deg, FOV 40 M, "
+        "R_rel=0.01, R_abs=1e-4 of peak", schwarzschild_129),
 }
 
 
-def cfg3(seed: int = 0, n: int = 256, **over) -> list:
+def grmhd_batch(seed: int = 0, n: int = 256, **over) -> list:
     """A batch of n images: spin a ~ U[-0.94, 0.94], inclination ~ U[10, 170] deg, FOV log-uniform
     in [40, 400] M, final grid 2^k + 1 with k ~ U{6..9} (65^2 .. 513^2) reached over N ~ U{2..6}
-    levels (base grid at least 5 points), the emission model of config 2 (the seeded snapshot
+    levels (base grid at least 5 points), the grid emission model (the seeded snapshot
     grmhd_snapshot(0), shared by every image whatever its spin) traced unpolarized with subrings
     n = 0, 1, 2; FP32 with the double-float re-trace."""
     rng = np.random.default_rng(seed)
@@ -186,7 +191,7 @@ def cfg3(seed: int = 0, n: int = 256, **over) -> list:
         N = int(rng.integers(2, 7))
         N = min(N, k - 2)
         n0 = (1 << (k - N)) + 1
-        p = cfg2(a=a, incl_deg=float(rng.uniform(10.0, 170.0)),
+        p = grmhd_8193(a=a, incl_deg=float(rng.uniform(10.0, 170.0)),
                  fov=float(np.exp(rng.uniform(np.log(40.0), np.log(400.0)))),
                  n0x=n0, n0y=n0, levels=N, stokes=1, subrings=3)
         p.update(over)
@@ -195,7 +200,7 @@ def cfg3(seed: int = 0, n: int = 256, **over) -> list:
 
 
 # ---------------------------------------------------------------------------------------------
-# Config 2: a seeded, GRMHD-like snapshot on a spherical Kerr-Schild grid
+# A seeded, GRMHD-like snapshot on a spherical Kerr-Schild grid
 # ---------------------------------------------------------------------------------------------
 
 GRID_FIELDS = ("rho", "uu", "U1", "U2", "U3", "B1", "B2", "B3")

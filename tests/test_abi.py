@@ -32,7 +32,7 @@ def test_header_declarations_are_exported():
 
 
 def test_image_size_and_planes_host_only():
-    job = art.make_job(**W.cfg0())
+    job = art.make_job(**W.schwarzschild_129())
     assert art.art_image_size(job) == (129, 129)
     assert art.art_planes(job) == 1
     job2 = art.make_job(**W.job(n0x=65, n0y=33, levels=4, subrings=3))
@@ -86,6 +86,6 @@ def test_job_struct_matches_header():
 def test_noalloc_rejects_grid_jobs_before_gpu_work():
     """A grid job has no context to hold its grid: the allocation-free call refuses it before
     touching any device state (checked on the host: an empty ray list, null pointers)."""
-    job = art.make_job(**W.cfg2(n0x=9, n0y=9, levels=0))
+    job = art.make_job(**W.grmhd_8193(n0x=9, n0y=9, levels=0))
     rc = art.load().art_trace_pixels_noalloc(ctypes.byref(job), None, 0, None, None, None)
     assert rc == art.ART_ERR_UNSUPPORTED

@@ -55,7 +55,7 @@ def test_reference_arm_runs_on_rank0_only(rank):
     env = {**os.environ, "RANK": str(rank), "WORLD_SIZE": "2", "LOCAL_RANK": str(rank),
            "MASTER_ADDR": "127.0.0.1"}
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                        "--workload", "cfg0", "--steps", "1", "--warmup", "0", "--gpus", "2"],
+                        "--workload", "schwarzschild_129", "--steps", "1", "--warmup", "0", "--gpus", "2"],
                        capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]

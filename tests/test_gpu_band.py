@@ -19,12 +19,12 @@ def ctx():
 
 
 CASES = [
-    ("cfg1_polarized", W.cfg1(n0x=33, n0y=33, levels=3)),
-    ("cfg1_retrograde_i75", W.cfg1(a=-0.6, incl_deg=75.0, r_in=W.r_isco(-0.6), n0x=17, n0y=17,
+    ("kerr_disk_polarized", W.kerr_disk_2049(n0x=33, n0y=33, levels=3)),
+    ("kerr_disk_retrograde_i75", W.kerr_disk_2049(a=-0.6, incl_deg=75.0, r_in=W.r_isco(-0.6), n0x=17, n0y=17,
                                    levels=3, stokes=1)),
-    ("cfg2_grid", W.cfg2(n0x=33, n0y=33, levels=4, fov=60.0)),
-    ("cfg0_schwarzschild_fp64", W.cfg0(precision="fp64", levels=3, n0x=17, n0y=17)),
-    ("cfg1_analytic_mixed", W.cfg1_analytic(n0x=33, n0y=33, levels=3)),
+    ("grmhd_grid", W.grmhd_8193(n0x=33, n0y=33, levels=4, fov=60.0)),
+    ("schwarzschild_fp64", W.schwarzschild_129(precision="fp64", levels=3, n0x=17, n0y=17)),
+    ("kerr_analytic_mixed", W.kerr_analytic_2049(n0x=33, n0y=33, levels=3)),
 ]
 
 
@@ -48,7 +48,7 @@ def test_band_moves_every_retrace_to_the_base_pass(ctx):
     """2049^2 polarized workload with the default band: the double-float passes of levels 1..4
     trace no ray (all near-critical rays of those levels were traced with level 0)."""
     from paper_2103_07417_gb300 import art
-    job = art.make_job(**W.cfg1())
+    job = art.make_job(**W.kerr_disk_2049())
     img, mask, st = ctx.render(job)
     ctx.art_profile(True)
     ctx.art_render(job, img, mask, stats=False)

@@ -23,9 +23,9 @@ def test_batch_equals_single_renders(snap, precision, stokes, model):
     from paper_2103_07417_gb300 import art
     ctx = art.Context(0)
     ctx.load_grid(snap)
-    params = W.cfg3(seed=3, n=7)
-    if model == "disk":   # the thermal-synchrotron disk of config 1 instead of the snapshot
-        params = [W.cfg1(a=p["a"], incl_deg=p["incl_deg"], fov=p["fov"], r_in=W.r_isco(p["a"]))
+    params = W.grmhd_batch(seed=3, n=7)
+    if model == "disk":   # the thermal-synchrotron disk instead of the snapshot
+        params = [W.kerr_disk_2049(a=p["a"], incl_deg=p["incl_deg"], fov=p["fov"], r_in=W.r_isco(p["a"]))
                   for p in params]
     elif stokes == 4:
         # at the workload's density the torus is Faraday thick (~1e3 rad), where the last-bit
@@ -78,17 +78,17 @@ def test_batch_equals_single_renders(snap, precision, stokes, model):
 def test_batch_rejects_mixed_kinds():
     from paper_2103_07417_gb300 import art
     ctx = art.Context(0)
-    a = art.make_job(**W.cfg0(n0x=9, n0y=9, levels=1))
-    b = art.make_job(**W.cfg0(n0x=9, n0y=9, levels=1, precision="mixed"))
+    a = art.make_job(**W.schwarzschild_129(n0x=9, n0y=9, levels=1))
+    b = art.make_job(**W.schwarzschild_129(n0x=9, n0y=9, levels=1, precision="mixed"))
     with pytest.raises(RuntimeError):
         ctx.render_batch([a, b])
     ctx.close()
 
 
 def _small_batch(seed, n, band):
-    """A config-3 style batch of small images (65^2 and 129^2, 2-4 levels) with the given
+    """A mixed-parameter batch of small images (65^2 and 129^2, 2-4 levels) with the given
     near-critical band width on every image (or a list of widths, one per image)."""
-    params = W.cfg3(seed=seed, n=n)
+    params = W.grmhd_batch(seed=seed, n=n)
     bands = band if isinstance(band, list) else [band] * n
     for i, p in enumerate(params):
         k = 6 + (i % 2)
@@ -140,13 +140,13 @@ def test_batch_band_without_masks(snap):
 
 
 def test_batch_band_moves_retraces_to_the_base_pass(snap):
-    """With the band, the double-float passes after the base level of a config-3 style batch
+    """With the band, the double-float passes after the base level of a mixed-parameter batch
     re-trace (almost) nothing: the photon-ring rays of every level of every image were traced
     with the base level."""
     from paper_2103_07417_gb300 import art
     ctx = art.Context(0)
     ctx.load_grid(snap)
-    jobs = [art.make_job(**p) for p in W.cfg3(seed=0, n=32)]
+    jobs = [art.make_job(**p) for p in W.grmhd_batch(seed=0, n=32)]
     imgs, masks, st = ctx.render_batch(jobs)
     ctx.art_profile(True)
     ctx.art_render_batch(jobs, imgs, masks, stats=False)

@@ -20,9 +20,9 @@ def ctx():
 
 
 CASES = [
-    ("cfg1_polarized", W.cfg1(n0x=65, n0y=65, levels=3)),
-    ("cfg2_grid", W.cfg2(n0x=65, n0y=57, levels=3)),
-    ("cfg0_fp64", W.cfg0(precision="fp64")),
+    ("kerr_disk_polarized", W.kerr_disk_2049(n0x=65, n0y=65, levels=3)),
+    ("grmhd_grid", W.grmhd_8193(n0x=65, n0y=57, levels=3)),
+    ("schwarzschild_fp64", W.schwarzschild_129(precision="fp64")),
 ]
 
 
@@ -43,8 +43,8 @@ def test_graph_replay_equals_render(ctx, name, params):
 
 def test_graph_recaptures_on_a_new_job(ctx):
     from paper_2103_07417_gb300 import art
-    a = art.make_job(**W.cfg1(n0x=33, n0y=33, levels=2))
-    b = art.make_job(**W.cfg1(n0x=33, n0y=33, levels=2, incl_deg=60.0))
+    a = art.make_job(**W.kerr_disk_2049(n0x=33, n0y=33, levels=2))
+    b = art.make_job(**W.kerr_disk_2049(n0x=33, n0y=33, levels=2, incl_deg=60.0))
     img, mask, _ = ctx.render(a)
     ref_b, ref_mask_b, _ = ctx.render(b)
     ref_a, ref_mask_a, _ = ctx.render(a)
@@ -58,7 +58,7 @@ def test_graph_recaptures_on_a_new_job(ctx):
 
 def test_graph_refuses_learned_jobs(ctx):
     from paper_2103_07417_gb300 import art
-    job = art.make_job(**W.cfg1(n0x=33, n0y=33, levels=2, proposal=1))
+    job = art.make_job(**W.kerr_disk_2049(n0x=33, n0y=33, levels=2, proposal=1))
     img = torch.empty((4, 129, 129), dtype=torch.float64, device="cuda")
     mask = torch.empty((129, 129), dtype=torch.uint8, device="cuda")
     with pytest.raises(RuntimeError, match="unsupported"):
@@ -66,11 +66,11 @@ def test_graph_refuses_learned_jobs(ctx):
 
 
 def test_graph_batch_replay_equals_batch_render(ctx):
-    """A config-3 style batch (mixed sizes and levels) replayed from its graph: images and masks
+    """A mixed-parameter batch (mixed sizes and levels) replayed from its graph: images and masks
     of art_render_batch, on two consecutive calls, and again after a larger single render made the
     context reallocate its ray queue (the graph is captured anew)."""
     from paper_2103_07417_gb300 import art
-    params = W.cfg3(seed=5, n=6)
+    params = W.grmhd_batch(seed=5, n=6)
     for i, p in enumerate(params):
         k = 5 + (i % 2)
         N = [1, 2, 3, 2, 3, 1][i]
@@ -81,7 +81,7 @@ def test_graph_batch_replay_equals_batch_render(ctx):
     masks = [torch.zeros_like(m) for m in ref_masks]
     for rnd in range(3):
         if rnd == 2:   # a larger render grows the single-image scratch (and not the batch's)
-            ctx.render(art.make_job(**W.cfg1(n0x=129, n0y=129, levels=3)))
+            ctx.render(art.make_job(**W.kerr_disk_2049(n0x=129, n0y=129, levels=3)))
         for t in imgs:
             t.fill_(np.nan)
         for m in masks:
@@ -97,11 +97,11 @@ def test_graph_batch_replay_equals_batch_render(ctx):
 def test_graph_single_recaptures_after_scratch_growth(ctx):
     """A replayed graph must not use buffers a later, larger render reallocated."""
     from paper_2103_07417_gb300 import art
-    small = art.make_job(**W.cfg1(n0x=33, n0y=33, levels=2))
+    small = art.make_job(**W.kerr_disk_2049(n0x=33, n0y=33, levels=2))
     img, mask, _ = ctx.render(small)
     ref = img.clone()
     ctx.art_graph_render(small, img, mask)
-    big = art.make_job(**W.cfg1(n0x=257, n0y=257, levels=3))
+    big = art.make_job(**W.kerr_disk_2049(n0x=257, n0y=257, levels=3))
     ctx.render(big)      # grows the ray queue
     img.fill_(np.nan)
     ctx.art_graph_render(small, img, mask)
@@ -113,7 +113,7 @@ def test_graph_batch_without_masks(ctx):
     """A batch replayed without caller masks: the near-critical band keeps its state in
     context-owned scratch masks, bound before the capture; images equal the batch render's."""
     from paper_2103_07417_gb300 import art
-    params = W.cfg3(seed=8, n=5)
+    params = W.grmhd_batch(seed=8, n=5)
     for i, p in enumerate(params):
         N = 2 + (i % 2)
         p.update(n0x=(1 << (6 - N)) + 1, n0y=(1 << (6 - N)) + 1, levels=N, crit_band=0.03)

@@ -54,9 +54,9 @@ def _trace_both(ctx, snap, params):
 
 
 CASES = [
-    ("cfg2_center", W.cfg2(n0x=33, n0y=33, levels=1, fov=60.0)),
-    ("cfg2_ragged_i100", W.cfg2(incl_deg=100.0, n0x=21, n0y=13, levels=1, fov=50.0)),
-    ("cfg2_edge_on_r_high80", W.cfg2(incl_deg=88.0, r_high=80.0, n0x=17, n0y=17, levels=1,
+    ("grmhd_center", W.grmhd_8193(n0x=33, n0y=33, levels=1, fov=60.0)),
+    ("grmhd_ragged_i100", W.grmhd_8193(incl_deg=100.0, n0x=21, n0y=13, levels=1, fov=50.0)),
+    ("grmhd_edge_on_r_high80", W.grmhd_8193(incl_deg=88.0, r_high=80.0, n0x=17, n0y=17, levels=1,
                                      fov=40.0)),
 ]
 
@@ -75,7 +75,7 @@ def test_grid_trace_fp64_matches_oracle(ctx, snap, name, params):
 def test_grid_polarized_fp64_matches_oracle(ctx, snap):
     """Polarized transfer through the snapshot with a mass unit that keeps the Faraday depth of
     order unity (rotation ~2 rad): every Stokes parameter within 2e-6."""
-    params = {**W.cfg2(n0x=15, n0y=15, levels=1, fov=50.0, stokes=4, incl_deg=60.0, m_unit=3e24),
+    params = {**W.grmhd_8193(n0x=15, n0y=15, levels=1, fov=50.0, stokes=4, incl_deg=60.0, m_unit=3e24),
               "precision": "fp64"}
     g, ref, _, _ = _trace_both(ctx, snap, params)
     ok = _close(g, ref, 2e-6)
@@ -87,7 +87,7 @@ def test_grid_polarized_faraday_thick_fp64(ctx, snap):
     """At the workload's mass unit the torus is Faraday thick (rotation up to ~1e3 rad), so the
     ~2e-7 relative accuracy of the device's Bessel-function ratios turns into ~1e-4 rad of EVPA:
     I within 2e-6, Q, U, V within 2e-3 I_peak."""
-    params = {**W.cfg2(n0x=15, n0y=15, levels=1, fov=50.0, stokes=4, incl_deg=60.0),
+    params = {**W.grmhd_8193(n0x=15, n0y=15, levels=1, fov=50.0, stokes=4, incl_deg=60.0),
               "precision": "fp64"}
     g, ref, _, _ = _trace_both(ctx, snap, params)
     assert _close(g[:, :1], ref[:, :1], 2e-6).all()
@@ -96,7 +96,7 @@ def test_grid_polarized_faraday_thick_fp64(ctx, snap):
 
 def test_grid_subrings_fp64_matches_oracle(ctx, snap):
     """Subring planes n = 0, 1, 2 of the snapshot image (face-on, the torus lensed into rings)."""
-    params = {**W.cfg2(n0x=17, n0y=17, levels=1, fov=30.0, subrings=3, incl_deg=163.0),
+    params = {**W.grmhd_8193(n0x=17, n0y=17, levels=1, fov=30.0, subrings=3, incl_deg=163.0),
               "precision": "fp64"}
     g, ref, aux, info = _trace_both(ctx, snap, params)
     I = ref.sum(axis=1)
@@ -109,7 +109,7 @@ def test_grid_subrings_fp64_matches_oracle(ctx, snap):
 def test_grid_render_fp64_matches_oracle(ctx, snap):
     """33^2 -> 129^2 adaptive render with the paper's GRMHD tolerances."""
     art = _art()
-    params = {**W.cfg2(n0x=33, n0y=33, levels=2, fov=60.0), "precision": "fp64"}
+    params = {**W.grmhd_8193(n0x=33, n0y=33, levels=2, fov=60.0), "precision": "fp64"}
     img, mask, st = ctx.render(art.make_job(**params))
     g, gm = img.cpu().numpy()[0], mask.cpu().numpy()
     ref, ref_mask, ref_st = O.render(O.make_job(grid=snap, **params), None)
@@ -124,7 +124,7 @@ def test_grid_render_fp64_matches_oracle(ctx, snap):
 @pytest.mark.parametrize("precision", ["mixed", "mixed_df", "fp32"])
 def test_grid_mixed_precision_error_bound(ctx, snap, precision):
     art = _art()
-    params = W.cfg2(n0x=33, n0y=33, levels=1, fov=60.0, R_rel=-1.0, R_abs=-1.0)
+    params = W.grmhd_8193(n0x=33, n0y=33, levels=1, fov=60.0, R_rel=-1.0, R_abs=-1.0)
     img, _, _ = ctx.render(art.make_job(**{**params, "precision": precision}))
     ref, _, _ = O.render(O.make_job(grid=snap, **{**params, "precision": "fp64"}), None)
     g = img.cpu().numpy()[0]
@@ -134,7 +134,7 @@ def test_grid_mixed_precision_error_bound(ctx, snap, precision):
 
 def test_grid_load_host_equals_device_and_errors(snap):
     art = _art()
-    params = {**W.cfg2(n0x=9, n0y=9, levels=1, fov=50.0), "precision": "fp64"}
+    params = {**W.grmhd_8193(n0x=9, n0y=9, levels=1, fov=50.0), "precision": "fp64"}
     job = art.make_job(**params)
     pix = torch.arange(17 * 17, dtype=torch.int32, device="cuda")
     c = art.Context(0)
@@ -164,7 +164,7 @@ def test_grid_workload_full_render_sampled(ctx, snap):
     MSE relative to mean(I)^2 <= 1e-5; sampled interpolated pixels equal the mean of their
     previous-level neighbours."""
     art = _art()
-    params = W.cfg2()
+    params = W.grmhd_8193()
     img, mask, st = ctx.render(art.make_job(**params))
     g = img[0].cpu().numpy()
     m = mask.cpu().numpy()
@@ -204,7 +204,7 @@ def test_grid_workload_every_traced_ray(ctx):
     sum (dI)^2 / (n mean(I)^2) <= 1e-5 over all of them (measured 4.3e-6; the largest single
     contributions are rays whose emission comes from a sample within rounding of the sigma cut)."""
     art = _art()
-    params = W.cfg2()
+    params = W.grmhd_8193()
     img, mask, st = ctx.render(art.make_job(**params))
     pix = torch.nonzero(mask.reshape(-1) == art.MASK_TRACED).reshape(-1).to(torch.int32)
     assert pix.numel() == st["rays_traced"]

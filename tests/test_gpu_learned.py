@@ -28,11 +28,11 @@ def ctx(snap):
 
 
 CASES = [
-    ("cfg2", W.cfg2(n0x=33, n0y=33, levels=4, fov=60.0, crit_band=0.0)),
-    ("cfg1_unpolarized", W.cfg1(n0x=17, n0y=17, levels=4, stokes=1, crit_band=0.0)),
-    ("cfg1_polarized_ragged", W.cfg1(n0x=17, n0y=13, levels=3, crit_band=0.0)),
-    ("cfg0_fp64", W.cfg0(precision="fp64", n0x=17, n0y=17, levels=3)),
-    ("cfg1_with_band", W.cfg1(n0x=17, n0y=17, levels=4, stokes=1)),
+    ("grmhd_8193", W.grmhd_8193(n0x=33, n0y=33, levels=4, fov=60.0, crit_band=0.0)),
+    ("kerr_disk_unpolarized", W.kerr_disk_2049(n0x=17, n0y=17, levels=4, stokes=1, crit_band=0.0)),
+    ("kerr_disk_polarized_ragged", W.kerr_disk_2049(n0x=17, n0y=13, levels=3, crit_band=0.0)),
+    ("schwarzschild_fp64", W.schwarzschild_129(precision="fp64", n0x=17, n0y=17, levels=3)),
+    ("kerr_disk_with_band", W.kerr_disk_2049(n0x=17, n0y=17, levels=4, stokes=1)),
 ]
 
 
@@ -61,7 +61,7 @@ def test_training_sample_matches_host_definition(ctx):
     normalisation, and at traced points 3 / max(r_min, 1) and the polar turns of the ray;
     targets: any point of level L + 2 or L + 3 traced in the 4 x 4-cell block."""
     from paper_2103_07417_gb300 import art
-    p = W.cfg1(n0x=17, n0y=17, levels=4, stokes=1)
+    p = W.kerr_disk_2049(n0x=17, n0y=17, levels=4, stokes=1)
     job = art.make_job(**p)
     img, mask, st = ctx.render(job)
     L = 1
@@ -118,7 +118,7 @@ def test_trained_proposal_gain(snap):
         p80 = max([sc["precision"] for sc in sweep if sc["recall"] >= 0.8], default=0.0)
         print("precision at 80 % recall:", p80, "sweep", sweep)
         assert p80 >= 2.0 * base, (sweep, base)
-        p = W.cfg1_analytic(crit_band=0.0)
+        p = W.kerr_analytic_2049(crit_band=0.0)
         plain = art.make_job(**p)
         lrn = art.make_job(**{**p, "proposal": 1, "proposal_p": 0.3, "proposal_depth": 3})
         img0, mask0, st0 = ctx.render(plain)

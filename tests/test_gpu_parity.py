@@ -47,10 +47,10 @@ def _close(gpu, ref, rtol=RTOL):
 # ------------------------------------------------------------------------------------------
 
 TRACE_CASES = [
-    ("cfg0", W.cfg0(n0x=17, n0y=17, levels=2)),                             # 65 x 65 grid
-    ("kerr17", W.cfg0(a=0.94, incl_deg=17.0, n0x=13, n0y=11, levels=2)),    # ragged 49 x 41
-    ("kerr_retro", W.cfg0(a=-0.7, incl_deg=75.0, n0x=9, n0y=9, levels=2, fov=24.0)),
-    ("static", W.cfg0(a=0.5, incl_deg=45.0, n0x=9, n0y=9, levels=2, flow="static")),
+    ("schwarzschild_129", W.schwarzschild_129(n0x=17, n0y=17, levels=2)),                             # 65 x 65 grid
+    ("kerr17", W.schwarzschild_129(a=0.94, incl_deg=17.0, n0x=13, n0y=11, levels=2)),    # ragged 49 x 41
+    ("kerr_retro", W.schwarzschild_129(a=-0.7, incl_deg=75.0, n0x=9, n0y=9, levels=2, fov=24.0)),
+    ("static", W.schwarzschild_129(a=0.5, incl_deg=45.0, n0x=9, n0y=9, levels=2, flow="static")),
 ]
 
 
@@ -76,7 +76,7 @@ def test_trace_pixels_fp64_matches_oracle(ctx, name, params):
 
 def test_trace_pixels_empty_and_bad_index(ctx):
     art = _art()
-    job = art.make_job(**W.cfg0(n0x=5, n0y=5, levels=1))
+    job = art.make_job(**W.schwarzschild_129(n0x=5, n0y=5, levels=1))
     empty = torch.empty(0, dtype=torch.int32, device="cuda")
     out = torch.empty((0, 1), dtype=torch.float64, device="cuda")
     ctx.art_trace_pixels(job, empty, out)
@@ -231,8 +231,8 @@ def test_render_on_truth_matches_oracle(ctx, levels, n0):
 # ------------------------------------------------------------------------------------------
 
 RENDER_CASES = [
-    ("cfg0", W.cfg0()),                                                      # 33^2 -> 129^2
-    ("kerr17_ragged", W.cfg0(a=0.94, incl_deg=17.0, n0x=21, n0y=17, levels=2, R_rel=1e-3,
+    ("schwarzschild_129", W.schwarzschild_129()),                                                      # 33^2 -> 129^2
+    ("kerr17_ragged", W.schwarzschild_129(a=0.94, incl_deg=17.0, n0x=21, n0y=17, levels=2, R_rel=1e-3,
                              R_abs=1e-3, abs_norm="ibar_int")),
 ]
 
@@ -278,7 +278,7 @@ def _estimates_at_final(oj, img, mask, norm):
 
 def test_render_host_equals_device(ctx):
     art = _art()
-    job = art.make_job(**W.cfg0(n0x=9, n0y=9, levels=2))
+    job = art.make_job(**W.schwarzschild_129(n0x=9, n0y=9, levels=2))
     img, mask, st = ctx.render(job)
     nx, ny = art.art_image_size(job)
     himg = np.zeros((1, ny, nx))
@@ -310,7 +310,7 @@ def test_mixed_precision_error_bound(ctx, precision):
     swept >= 3 pi, and plain FP32: the image MSE relative to the mean intensity squared stays
     below 1e-5 against the FP64 oracle (every pixel traced)."""
     art = _art()
-    params = W.cfg0(a=0.94, incl_deg=17.0, n0x=17, n0y=17, levels=2, R_rel=-1.0, R_abs=-1.0)
+    params = W.schwarzschild_129(a=0.94, incl_deg=17.0, n0x=17, n0y=17, levels=2, R_rel=-1.0, R_abs=-1.0)
     job = art.make_job(**{**params, "precision": precision})
     img, mask, st = ctx.render(job)
     ref, _, _ = O.render(O.make_job(**params), None)
@@ -327,7 +327,7 @@ def test_double_float_retrace_per_pixel(ctx, geom):
     """Every ray routed to the double-float re-trace (threshold 1e-9 rad): the geodesic carries
     ~48 bits, emission and transfer run in FP32, so each pixel matches the FP64 oracle to 2e-5."""
     art = _art()
-    params = W.cfg0(n0x=13, n0y=13, levels=2, **geom)
+    params = W.schwarzschild_129(n0x=13, n0y=13, levels=2, **geom)
     job = art.make_job(**{**params, "precision": "mixed_df", "fp64_sweep": 1e-9})
     nx, ny = art.art_image_size(job)
     pix = np.arange(nx * ny, dtype=np.int32)
@@ -357,7 +357,7 @@ def test_bench_workload_sampled(ctx, precision):
     re-traced by the oracle; sampled interpolated pixels must equal the mean of their 2 or 4
     previous-level neighbours; level counts add up."""
     art = _art()
-    params = W.cfg1_analytic(precision=precision)
+    params = W.kerr_analytic_2049(precision=precision)
     job = art.make_job(**params)
     img, mask, st = ctx.render(job)
     g = img.cpu().numpy()[0]

@@ -35,9 +35,9 @@ def _stokes_close(g, r, tol):
 
 
 CASES = [
-    ("cfg1", W.cfg1(n0x=17, n0y=17, levels=1, fov=30.0)),
-    ("cfg1_i60_ragged", W.cfg1(incl_deg=60.0, n0x=15, n0y=11, levels=1, fov=24.0)),
-    ("cfg1_retro_vertical", W.cfg1(a=-0.5, incl_deg=75.0, bz_ratio=3.0, n0x=11, n0y=11, levels=1,
+    ("kerr_disk_2049", W.kerr_disk_2049(n0x=17, n0y=17, levels=1, fov=30.0)),
+    ("kerr_disk_i60_ragged", W.kerr_disk_2049(incl_deg=60.0, n0x=15, n0y=11, levels=1, fov=24.0)),
+    ("kerr_disk_retro_vertical", W.kerr_disk_2049(a=-0.5, incl_deg=75.0, bz_ratio=3.0, n0x=11, n0y=11, levels=1,
                                    r_in=W.r_isco(-0.5), fov=30.0)),
 ]
 
@@ -59,7 +59,7 @@ def test_polarized_trace_fp64_matches_oracle(ctx, name, params):
 
 def test_unpolarized_synchrotron_with_absorption_matches_oracle(ctx):
     art = _art()
-    params = {**W.cfg1(n0x=13, n0y=13, levels=1, fov=30.0, stokes=1), "precision": "fp64"}
+    params = {**W.kerr_disk_2049(n0x=13, n0y=13, levels=1, fov=30.0, stokes=1), "precision": "fp64"}
     job = art.make_job(**params)
     nx, ny = art.art_image_size(job)
     pix = np.arange(nx * ny, dtype=np.int32)
@@ -71,7 +71,7 @@ def test_unpolarized_synchrotron_with_absorption_matches_oracle(ctx):
 def test_polarized_render_fp64_matches_oracle(ctx):
     """33^2 -> 65^2 adaptive render of all four Stokes planes (decisions on I)."""
     art = _art()
-    params = {**W.cfg1(n0x=33, n0y=33, levels=1), "precision": "fp64"}
+    params = {**W.kerr_disk_2049(n0x=33, n0y=33, levels=1), "precision": "fp64"}
     job = art.make_job(**params)
     img, mask, st = ctx.render(job)
     g, gm = img.cpu().numpy(), mask.cpu().numpy()
@@ -87,7 +87,7 @@ def test_polarized_render_fp64_matches_oracle(ctx):
 @pytest.mark.parametrize("precision", ["mixed", "mixed_df", "fp32"])
 def test_polarized_mixed_precision_error_bound(ctx, precision):
     art = _art()
-    params = W.cfg1(n0x=17, n0y=17, levels=1, fov=30.0, R_rel=-1.0, R_abs=-1.0)
+    params = W.kerr_disk_2049(n0x=17, n0y=17, levels=1, fov=30.0, R_rel=-1.0, R_abs=-1.0)
     job = art.make_job(**{**params, "precision": precision})
     img, mask, st = ctx.render(job)
     ref, _, _ = O.render(O.make_job(**{**params, "precision": "fp64"}), None)
@@ -103,7 +103,7 @@ def test_polarized_bench_workload_sampled(ctx):
     pixels re-traced by the oracle, Stokes MSE relative to mean(I)^2 <= 1e-5; sampled interpolated
     pixels equal the mean of their previous-level neighbours in every plane."""
     art = _art()
-    params = W.cfg1()
+    params = W.kerr_disk_2049()
     job = art.make_job(**params)
     img, mask, st = ctx.render(job)
     g = img.cpu().numpy()
@@ -144,7 +144,7 @@ def test_polarized_workload_every_traced_ray(ctx):
     sum (dS)^2 / (n mean(I)^2) <= 1e-5 over all of them (measured I 2.7e-6, Q 8e-7, U 5.6e-7,
     V 5.7e-8)."""
     art = _art()
-    params = W.cfg1()
+    params = W.kerr_disk_2049()
     img, mask, st = ctx.render(art.make_job(**params))
     pix = torch.nonzero(mask.reshape(-1) == art.MASK_TRACED).reshape(-1).to(torch.int32)
     assert pix.numel() == st["rays_traced"]

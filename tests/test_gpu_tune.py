@@ -32,14 +32,14 @@ def test_tune_roundtrip_and_validation(ctx):
 
 
 @pytest.mark.parametrize("name,over", [
-    ("cfg1_polarized", dict(n0x=65, n0y=65, levels=3)),
-    ("cfg1_analytic", dict(n0x=65, n0y=49, levels=3)),
+    ("kerr_disk_polarized", dict(n0x=65, n0y=65, levels=3)),
+    ("kerr_analytic_2049", dict(n0x=65, n0y=49, levels=3)),
 ])
 def test_every_setting_renders_the_same_image(ctx, name, over):
     """One-thread only, pair only, quad-heavy and pair-heavy settings: identical images, masks
     and ray counts (every level's FP32 launch changes form between them)."""
     from paper_2103_07417_gb300 import art
-    p = (W.cfg1 if name == "cfg1_polarized" else W.cfg1_analytic)(**over)
+    p = (W.kerr_disk_2049 if name == "kerr_disk_polarized" else W.kerr_analytic_2049)(**over)
     job = art.make_job(**p)
     ref = None
     for q, pr in ((0, 0), (0, 4096), (4096, 4096), (32, 64), (8, 16)):
@@ -55,7 +55,7 @@ def test_every_setting_renders_the_same_image(ctx, name, over):
 
 def test_autotune_keeps_a_candidate_and_the_image(ctx):
     from paper_2103_07417_gb300 import art
-    job = art.make_job(**W.cfg1(n0x=65, n0y=65, levels=3))
+    job = art.make_job(**W.kerr_disk_2049(n0x=65, n0y=65, levels=3))
     img0, mask0, _ = ctx.render(job)
     img = torch.empty_like(img0)
     mask = torch.empty_like(mask0)

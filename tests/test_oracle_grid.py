@@ -174,7 +174,7 @@ def test_ideal_mhd_field_invariant_flat_space():
 def test_snapshot_normalisation_and_orthogonality():
     """On the seeded torus snapshot: u.u = -1 and b.u = 0 at every sample (Kerr, a = 0.94)."""
     g = W.grmhd_snapshot(seed=0, n1=48, n2=32, n3=16)
-    job = O.make_job(grid=g, **W.cfg2())
+    job = O.make_job(grid=g, **W.grmhd_8193())
     rng = np.random.default_rng(4)
     r = np.exp(rng.uniform(np.log(1.5), np.log(60), 200))
     th = rng.uniform(0.05, np.pi - 0.05, 200)

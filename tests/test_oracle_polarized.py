@@ -218,7 +218,7 @@ def test_stokes_convention_toroidal_field_face_on():
     E-vector radial on the sky: Q < 0 on the horizontal axis, Q > 0 on the vertical axis, U > 0 in
     the north-east quadrant (up, left) and U < 0 in the north-west one (IAU: angle from north
     through east, east = left on the screen)."""
-    p = W.cfg1(a=0.0, incl_deg=1.0, bz_ratio=0.0, ne0=1e3, r_in=6.0)
+    p = W.kerr_disk_2049(a=0.0, incl_deg=1.0, bz_ratio=0.0, ne0=1e3, r_in=6.0)
     job = O.make_job(**p)
     al = np.array([8.0, 0.0, -6.0, 6.0])
     be = np.array([0.0, 8.0, 6.0, 6.0])
@@ -232,9 +232,9 @@ def test_stokes_convention_toroidal_field_face_on():
 
 
 def test_polarized_image_is_physical():
-    """|Q, U, V| <= I on every ray of a config-1 image (a Mueller-matrix invariant), V present
+    """|Q, U, V| <= I on every ray of a polarized disk image (a Mueller-matrix invariant), V present
     (Faraday conversion), and the I plane of the polarized trace close to the unpolarized one."""
-    p = W.cfg1(n0x=9, n0y=9, levels=1, fov=30.0)
+    p = W.kerr_disk_2049(n0x=9, n0y=9, levels=1, fov=30.0)
     job = O.make_job(**p)
     nx, ny = O.image_size(job)
     pix = np.arange(nx * ny)

@@ -214,7 +214,7 @@ def test_flat_space_inverse_square(rho):
     """M = 0, j = 1/r^2 along a straight line from the camera to where the ray leaves:
     I = (atan((s_end - s0)/b) + atan(s0/b)) / b."""
     r_obs = 1000.0
-    job = _job(a=0.0, r_obs=r_obs, incl_deg=45.0, step_frac=0.002, emission="cfg0",
+    job = _job(a=0.0, r_obs=r_obs, incl_deg=45.0, step_frac=0.002, emission="analytic",
                disk_w=1.0e6, flow="static")
     job.mass = 0.0
     rec, status = O.trace_record(job, rho, 0.0)
@@ -228,7 +228,7 @@ def test_keplerian_redshift_schwarzschild():
     """Emitter on a circular Keplerian orbit at r (equator, a = 0) and a photon moving
     tangentially there with E = 1, L = r/sqrt(1 - 2/r): nu_fluid = u^t (1 - Omega L),
     u^t = (1 - 3/r)^(-1/2), Omega = r^(-3/2) (Schwarzschild circular geodesics)."""
-    job = _job(a=0.0, emission="cfg0", disk_w=0.3)
+    job = _job(a=0.0, emission="analytic", disk_w=0.3)
     for r in (4.0, 6.0, 15.0):
         for sgn in (1.0, -1.0):
             L = sgn * r / np.sqrt(1 - 2 / r)

@@ -18,7 +18,7 @@ def test_lyapunov_narrowing_of_subrings_schwarzschild():
     (Sec. 5.1: delta rho_n ~ rho_c exp(-gamma n)); the peak brightness of the subrings stays
     roughly constant (Sec. 5.1)."""
     r_obs = 1.0e4
-    p = W.cfg0(a=0.0, incl_deg=0.1, disk_w=0.02, subrings=4, r_obs=r_obs, step_frac=0.02)
+    p = W.schwarzschild_129(a=0.0, incl_deg=0.1, disk_w=0.02, subrings=4, r_obs=r_obs, step_frac=0.02)
     job = O.make_job(**p)
     rho_c = r_obs * np.tan(np.arcsin(np.sqrt(27.0) * np.sqrt(1 - 2 / r_obs) / r_obs))  # Synge
     d = np.geomspace(1e-6, 1.5, 5000)
@@ -34,7 +34,7 @@ def test_lyapunov_narrowing_of_subrings_schwarzschild():
 
 
 def test_subring_planes_sum_to_total():
-    p = W.cfg0(a=0.94, incl_deg=17.0, disk_w=0.05, n0x=9, n0y=9, levels=1)
+    p = W.schwarzschild_129(a=0.94, incl_deg=17.0, disk_w=0.05, n0x=9, n0y=9, levels=1)
     job1 = O.make_job(**p)
     job3 = O.make_job(**{**p, "subrings": 3})
     pix = np.arange(17 * 17)
@@ -46,9 +46,9 @@ def test_subring_planes_sum_to_total():
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("params", [
-    W.cfg0(a=0.94, incl_deg=17.0, disk_w=0.05, n0x=13, n0y=13, levels=2, subrings=3),
-    W.cfg1(n0x=11, n0y=11, levels=1, fov=24.0, subrings=2),
-], ids=["cfg0_subrings3", "cfg1_pol_subrings2"])
+    W.schwarzschild_129(a=0.94, incl_deg=17.0, disk_w=0.05, n0x=13, n0y=13, levels=2, subrings=3),
+    W.kerr_disk_2049(n0x=11, n0y=11, levels=1, fov=24.0, subrings=2),
+], ids=["schwarzschild_subrings3", "kerr_disk_pol_subrings2"])
 def test_subring_planes_match_oracle_gpu(params):
     torch = pytest.importorskip("torch")
     from paper_2103_07417_gb300 import art

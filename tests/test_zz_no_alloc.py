@@ -24,8 +24,8 @@ def _close(got, ref):
 def test_noalloc_matches_context_tracer_on_consecutive_calls():
     from paper_2103_07417_gb300 import art
     ctx = art.Context(0)
-    cases = [W.cfg0(a=0.94, incl_deg=17.0, n0x=17, n0y=13, levels=2, precision="fp64"),
-             W.cfg0(a=0.94, incl_deg=17.0, n0x=17, n0y=13, levels=2, precision="mixed")]
+    cases = [W.schwarzschild_129(a=0.94, incl_deg=17.0, n0x=17, n0y=13, levels=2, precision="fp64"),
+             W.schwarzschild_129(a=0.94, incl_deg=17.0, n0x=17, n0y=13, levels=2, precision="mixed")]
     for params in cases:                      # two calls in a row on the same static scratch
         job = art.make_job(**params)
         nx, ny = art.art_image_size(job)
@@ -45,7 +45,7 @@ def test_noalloc_matches_context_tracer_on_consecutive_calls():
 
 def test_noalloc_rejects_more_rays_than_its_scratch():
     from paper_2103_07417_gb300 import art
-    job = art.make_job(**W.cfg0(n0x=1025, n0y=1025, levels=1))   # 2049^2 pixels
+    job = art.make_job(**W.schwarzschild_129(n0x=1025, n0y=1025, levels=1))   # 2049^2 pixels
     n = art.NOALLOC_MAX_RAYS + 1
     pix = torch.zeros(n, dtype=torch.int32, device="cuda")
     out = torch.zeros((n, 1), dtype=torch.float64, device="cuda")
