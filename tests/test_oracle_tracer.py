@@ -224,6 +224,34 @@ def test_flat_space_inverse_square(rho):
     assert rec[-1, 13] == pytest.approx(expect, rel=2e-5)
 
 
+@pytest.mark.parametrize("incl,rho", [(5.0, 1.5), (45.0, 3.0), (80.0, 6.0)])
+def test_flat_space_analytic_emissivity_by_quadrature(incl, rho):
+    """M = 0 and a static fluid (nu = 1): the analytic emissivity j = r^-2 exp(-z^2/(2 (w r)^2)),
+    w = 0.3, integrated along the straight ray from the camera to where it leaves.  The reference is
+    adaptive Gauss-Kronrod quadrature (scipy's quad), split at the closest approach; the tolerance
+    is the integrator's (2e-5 at step 0.002 r)."""
+    from scipy.integrate import quad
+    w = 0.3
+    job = _job(a=0.0, r_obs=1000.0, incl_deg=incl, step_frac=0.002, emission="analytic",
+               disk_w=w, flow="static")
+    job.mass = 0.0
+    rec, status = O.trace_record(job, rho, 0.0)
+    p0, p1 = rec[0, 2:5], rec[-1, 2:5]
+    length = np.linalg.norm(p1 - p0)
+    d = (p1 - p0) / length
+
+    def j(s):
+        x = p0 + s * d
+        r2 = x @ x
+        return np.exp(-x[2] ** 2 / (2.0 * w * w * r2)) / r2
+
+    s_c = -(p0 @ d)
+    expect = (quad(j, 0.0, s_c, epsabs=0.0, epsrel=1e-12, limit=500)[0]
+              + quad(j, s_c, length, epsabs=0.0, epsrel=1e-12, limit=500)[0])
+    assert status == O.RAY_ESCAPED
+    assert rec[-1, 13] == pytest.approx(expect, rel=2e-5)
+
+
 def test_keplerian_redshift_schwarzschild():
     """Emitter on a circular Keplerian orbit at r (equator, a = 0) and a photon moving
     tangentially there with E = 1, L = r/sqrt(1 - 2/r): nu_fluid = u^t (1 - Omega L),
