@@ -33,6 +33,57 @@ def test_lyapunov_narrowing_of_subrings_schwarzschild():
     assert max(peaks) / min(peaks) < 1.35
 
 
+def _agm_k(m):
+    """Complete elliptic integral K(m) = pi / (2 AGM(1, sqrt(1 - m))) (Gauss), m < 1."""
+    x, y = 1.0, np.sqrt(1.0 - m)
+    for _ in range(40):
+        x, y = 0.5 * (x + y), np.sqrt(x * y)
+    return np.pi / (2.0 * x)
+
+
+def _lyapunov_face_on(a):
+    """Lyapunov exponent of the photon orbit a face-on observer sees (lambda = 0), from the
+    photon-shell expressions (Sec. 5.1): gamma = 4 r sqrt(chi) / sqrt(-u_- a^2) K(u_+/u_-),
+    chi = 1 - Delta / (r (r - 1)^2), u_pm = D_th +- sqrt(D_th^2 + eta/a^2),
+    D_th = (1 - (eta + lambda^2)/a^2) / 2, with r from lambda_c(r) = 0 on Bardeen's curve."""
+    from scipy.optimize import brentq
+    lam = lambda r: (r * r * (3 - r) - a * a * (r + 1)) / (a * (r - 1))
+    r = brentq(lam, 2 * (1 + np.cos(2 / 3 * np.arccos(-a))), 2 * (1 + np.cos(2 / 3 * np.arccos(a))))
+    eta = r ** 3 * (4 * a * a - r * (r - 3) ** 2) / (a * a * (r - 1) ** 2)
+    chi = 1 - (r * r - 2 * r + a * a) / (r * (r - 1) ** 2)
+    dth = 0.5 * (1 - eta / (a * a))
+    up, um = dth + np.sqrt(dth ** 2 + eta / a ** 2), dth - np.sqrt(dth ** 2 + eta / a ** 2)
+    return 4 * r * np.sqrt(chi) / np.sqrt(-um * a * a) * _agm_k(up / um)
+
+
+def test_lyapunov_narrowing_of_subrings_kerr():
+    """Face-on Kerr disk (a = 0.94), camera at 1e4 M: from n = 2 to n = 3 the outer edge of the
+    subring band moves towards the critical curve by exp(-gamma) with the Kerr exponent of the
+    lambda = 0 photon orbit (gamma = 2.567, against pi for a = 0, to which the same expression
+    tends).  The critical radius on the screen is found by bisection on capture."""
+    assert _lyapunov_face_on(1e-3) == pytest.approx(np.pi, rel=1e-3)
+    a = 0.94
+    gamma = _lyapunov_face_on(a)
+    assert gamma == pytest.approx(2.567, abs=2e-3)
+    r_obs = 1.0e4
+    p = W.schwarzschild_129(a=a, incl_deg=0.1, disk_w=0.02, subrings=4, r_obs=r_obs, step_frac=0.02)
+    job = O.make_job(**p)
+    lo, hi = 4.0, 6.0
+    for _ in range(45):
+        mid = 0.5 * (lo + hi)
+        _, info = O.trace_screen(job, [mid], [0.0])
+        if info["status"][0] == O.RAY_CAPTURED:
+            lo = mid
+        else:
+            hi = mid
+    rho_c = hi
+    d = np.geomspace(1e-6, 1.5, 3000)
+    out, info = O.trace_screen(job, rho_c + d, np.zeros_like(d))
+    edge = {n: d[np.flatnonzero(out[:, n] > 1e-3 * out[:, n].max())[-1]] for n in (1, 2, 3)}
+    assert edge[3] / edge[2] == pytest.approx(np.exp(-gamma), rel=0.05)
+    assert 0.5 * np.exp(-gamma) < edge[2] / edge[1] < 1.5 * np.exp(-gamma)
+
+
 def test_subring_planes_sum_to_total():
     p = W.schwarzschild_129(a=0.94, incl_deg=17.0, disk_w=0.05, n0x=9, n0y=9, levels=1)
     job1 = O.make_job(**p)
@@ -48,7 +99,7 @@ def test_subring_planes_sum_to_total():
 @pytest.mark.parametrize("params", [
     W.schwarzschild_129(a=0.94, incl_deg=17.0, disk_w=0.05, n0x=13, n0y=13, levels=2, subrings=3),
     W.kerr_disk_2049(n0x=11, n0y=11, levels=1, fov=24.0, subrings=2),
-], ids=["schwarzschild_subrings3", "kerr_disk_pol_subrings2"])
+], ids=["analytic_kerr_subrings3", "kerr_disk_pol_subrings2"])
 def test_subring_planes_match_oracle_gpu(params):
     torch = pytest.importorskip("torch")
     from paper_2103_07417_gb300 import art
