@@ -136,6 +136,53 @@ def test_quadratic_estimate_is_twice_true_residual(edge_mode):
         assert (m2[~np.isnan(ea)] == O.MASK_TRACED).sum() > 4  # edge points forced to trace
 
 
+@pytest.mark.parametrize("coef", [(0.0, 0.0, 0.0, 0.75, -0.5), (0.125, -0.375, 0.25, 1.5, 0.25),
+                                  (-0.25, 0.5, 0.0, -2.0, 1.0)])
+def test_nearest_estimate_is_gradient_times_distance(coef):
+    """Nearest scheme, Appendix A.1: the residual of a nearest-neighbour copy is extremised by
+    |grad I| dx with dx the distance to the nearest sample, and the gradient comes from central
+    differences along the two diagonals through the corners (1-4 and 2-3).  On any quadratic
+    I = c2x x^2 + cxy x y + c2y y^2 + c1x x + c1y y the central differences are exact, so at
+    every cell centre (category 4) eps_abs * norm = |grad I(x)| * sqrt(2) s, and at every edge
+    midpoint (categories 2/3) it is |dI/dx| s (or |dI/dy| s) along the pair; eps_rel divides the
+    same numerator by |I_1| (the lower-left corner, resp. the lower/left neighbour), and the
+    interpolant is I_1.  A swapped diagonal pairing, a wrong divisor or another corner as the
+    nearest neighbour changes these values for a gradient that is not along an axis."""
+    c2x, cxy, c2y, c1x, c1y = coef
+    levels, level = 3, 2
+    norm = 1.75
+    job = _job(n0x=9, n0y=7, levels=levels, R_abs=np.inf, R_rel=np.inf, interp="nearest")
+    nx, ny = O.image_size(job)
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    truth = 3.0 + c2x * x * x + cxy * x * y + c2y * y * y + c1x * x + c1y * y
+    gx = 2 * c2x * x + cxy * y + c1x
+    gy = cxy * x + 2 * c2y * y + c1y
+    im, m = _level_setup(truth, levels, level)
+    out, m2, ea, er = O.refine_level(job, im, m, level, norm)
+    s = 1 << (levels - level)
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny))
+    new = ~np.isnan(ea)
+    oi, oj = (ii // s) % 2 == 1, (jj // s) % 2 == 1
+    cat4 = new & oi & oj
+    cat3 = new & oi & ~oj   # between a left/right pair
+    cat2 = new & ~oi & oj   # between a pair below/above
+    assert cat4.sum() > 0 and cat3.sum() > 0 and cat2.sum() > 0
+    num4 = np.hypot(gx, gy) * np.sqrt(2.0) * s
+    np.testing.assert_allclose(ea[cat4] * norm, num4[cat4], rtol=1e-13, atol=1e-12)
+    np.testing.assert_allclose(ea[cat3] * norm, np.abs(gx[cat3]) * s, rtol=1e-13, atol=1e-12)
+    np.testing.assert_allclose(ea[cat2] * norm, np.abs(gy[cat2]) * s, rtol=1e-13, atol=1e-12)
+    # I_1 of a centre is its lower-left corner (i - s, j - s); of a midpoint the lower/left one
+    i1 = np.full_like(truth, np.nan)
+    i1[s:, s:][cat4[s:, s:]] = truth[:-s, :-s][cat4[s:, s:]]
+    i1[:, s:][cat3[:, s:]] = truth[:, :-s][cat3[:, s:]]
+    i1[s:, :][cat2[s:, :]] = truth[:-s, :][cat2[s:, :]]
+    for sel, numv in ((cat4, num4), (cat3, np.abs(gx) * s), (cat2, np.abs(gy) * s)):
+        with np.errstate(divide="ignore"):
+            ref = numv[sel] / np.abs(i1[sel])
+        np.testing.assert_allclose(er[sel], ref, rtol=1e-13, atol=1e-12)
+        np.testing.assert_array_equal(out[sel], i1[sel])
+
+
 def test_tie_and_zero_denominator_rules():
     """Strict '>' (Sec. 3.2): an estimate equal to the tolerance interpolates.  S_in = 0 with a
     zero numerator gives eps_rel = 0; with a non-zero numerator eps_rel = inf."""
