@@ -50,7 +50,7 @@ enum { ART_FLOW_KEPLER = 0, ART_FLOW_STATIC = 1 };
 enum { ART_NORM_IBAR_INT = 0, ART_NORM_PEAK = 1 };
 enum { ART_INTERP_LINEAR = 0, ART_INTERP_NEAREST = 1 };
 enum { ART_EDGE_ONESIDED = 0, ART_EDGE_TRACE = 1 };
-enum { ART_FP64 = 0, ART_MIXED = 1, ART_FP32 = 2, ART_MIXED_DF = 3 };
+enum { ART_FP64 = 0, ART_MIXED = 1, ART_FP32 = 2, ART_MIXED_DF = 3, ART_MIXED_EXACT = 4 };
 enum { ART_MASK_UNSET = 0, ART_MASK_TRACED = 1, ART_MASK_INTERP = 2 };
 enum { ART_RAY_ESCAPED = 0, ART_RAY_CAPTURED = 1, ART_RAY_CAP = 2, ART_RAY_NAN = 3 };
 
@@ -73,7 +73,17 @@ typedef struct art_job {
     int32_t subrings;    /* 0, or the number of subring planes n = 0..subrings-1 */
     int32_t precision;   /* ART_FP64; ART_MIXED: FP32 with an FP64 re-trace of near-critical rays;
                           * ART_MIXED_DF: the same with the re-traced geodesic in double-float
-                          * (float pairs, ~48-bit significand) on the FP32 pipes; ART_FP32 */
+                          * (float pairs, ~48-bit significand) on the FP32 pipes; ART_FP32;
+                          * ART_MIXED_EXACT: ART_MIXED_DF with the refinement decisions of the
+                          * FP64 render (art_render only): the base level is traced in FP64, and
+                          * every point whose estimate lies within a relative band (0.25) of a
+                          * tolerance is decided in FP64 on exact values of its stencil (FP64
+                          * re-traces of the FP32-traced values it reads, recomputed interpolants
+                          * of the interpolated ones), so its mask equals the FP64 render's wherever
+                          * the FP32 values decide a point as the FP64 values would outside that
+                          * band.  In both mixed modes the FP32 pass also hands over rays with a
+                          * sample within rounding of a discontinuity of the emission model (the
+                          * magnetisation cut, the disk's inner edge). */
     int32_t max_steps;   /* RK4 step cap per ray */
     double fp64_sweep;   /* ART_MIXED: re-trace in FP64 the rays whose position vector swept at
                           * least this angle [rad] about the hole (3 pi: a full loop of
@@ -131,6 +141,11 @@ typedef struct art_stats {
     int64_t rays_speculative;   /* learned path: rays traced speculatively */
     int64_t rays_spec_used;     /* learned path: speculative rays the criterion asked for (these
                                  * are included in rays_traced; the rest were wasted) */
+    int64_t rays_exact;         /* ART_MIXED_EXACT: FP64 rays traced for exact decisions (base
+                                 * level, stencil re-traces, borderline points) */
+    int64_t border_points;      /* ART_MIXED_EXACT: points decided on exact stencil values */
+    int64_t border_overflow;    /* ART_MIXED_EXACT: borderline points decided without them
+                                 * because the library's list was full (0 in normal use) */
 } art_stats;
 
 /* One kernel launch timed by the profiler (art_profile). */
@@ -199,9 +214,10 @@ int art_refine_level(art_ctx* ctx, const art_job* job, double* img_dev, uint8_t*
  * for each level refine and trace the queue on the device (no host round trip inside).
  * img_dev: planes x ny x nx doubles; mask_dev (nullable): ny x nx bytes (ART_MASK_*).
  * truth_dev (nullable): if given (planes x ny x nx), "tracing" a pixel copies it from there, so
- * the refinement logic can be run on any precomputed image.  stats_host (nullable) is filled and
- * the stream synchronised if it is given.  Errors: ART_ERR_ARG, ART_ERR_CUDA, ART_ERR_OOM,
- * ART_ERR_DEVICE. */
+ * the refinement logic can be run on any precomputed image (not with ART_MIXED_EXACT:
+ * ART_ERR_ARG).  stats_host (nullable) is filled and the stream synchronised if it is given.
+ * Errors: ART_ERR_ARG, ART_ERR_CUDA, ART_ERR_OOM, ART_ERR_DEVICE (ART_MIXED_EXACT also reports
+ * a stencil value that was not exact when its decision was made, which would be a bug). */
 int art_render(art_ctx* ctx, const art_job* job, const double* truth_dev, double* img_dev,
                uint8_t* mask_dev, art_stats* stats_host);
 
@@ -216,7 +232,9 @@ int art_render(art_ctx* ctx, const art_job* job, const double* truth_dev, double
  * art_render (an image without a mask then uses a context-owned scratch mask).  stats_host
  * (nullable) receives n entries: rays per level and the normalisation per image; steps,
  * re-traced, capped, NaN and speculative rays and kernel launches are batch totals repeated in
- * every entry.  Synchronises when stats are requested.  Errors as art_render. */
+ * every entry.  Synchronises when stats are requested.  Jobs with precision ART_MIXED_EXACT
+ * (all of them, else ART_ERR_ARG) are rendered one after the other by art_render, with per-image
+ * stats.  Errors as art_render. */
 int art_render_batch(art_ctx* ctx, const art_job* jobs, int32_t n, double* const* imgs,
                      uint8_t* const* masks, art_stats* stats_host);
 

@@ -26,7 +26,7 @@ _NAMES = dict(
     abs_norm={"ibar_int": 0, "peak": 1},
     interp={"linear": 0, "nearest": 1},
     edge_mode={"onesided": 0, "trace": 1},
-    precision={"fp64": 0, "mixed": 1, "fp32": 2, "mixed_df": 3},
+    precision={"fp64": 0, "mixed": 1, "fp32": 2, "mixed_df": 3, "mixed_exact": 4},
 )
 
 
@@ -65,7 +65,9 @@ class Stats(ctypes.Structure):
                 ("steps", ctypes.c_int64), ("rays_capped", ctypes.c_int64),
                 ("rays_nan", ctypes.c_int64), ("rays_per_level", ctypes.c_int64 * 16),
                 ("norm", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("rays_speculative", ctypes.c_int64), ("rays_spec_used", ctypes.c_int64)]
+                ("rays_speculative", ctypes.c_int64), ("rays_spec_used", ctypes.c_int64),
+                ("rays_exact", ctypes.c_int64), ("border_points", ctypes.c_int64),
+                ("border_overflow", ctypes.c_int64)]
 
 
 class LaunchRecord(ctypes.Structure):
@@ -218,7 +220,8 @@ def _stats_dict(st: Stats, levels: int) -> dict:
     return dict(rays_traced=st.rays_traced, rays_fp64=st.rays_fp64, steps=st.steps,
                 rays_capped=st.rays_capped, rays_nan=st.rays_nan, norm=st.norm,
                 kernel_launches=st.kernel_launches, rays_speculative=st.rays_speculative,
-                rays_spec_used=st.rays_spec_used,
+                rays_spec_used=st.rays_spec_used, rays_exact=st.rays_exact,
+                border_points=st.border_points, border_overflow=st.border_overflow,
                 rays_per_level=[st.rays_per_level[k] for k in range(levels + 1)])
 
 

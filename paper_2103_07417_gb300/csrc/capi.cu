@@ -56,6 +56,16 @@ struct art_ctx {
     int64_t aux_cap = 0, aux_npix = 0;
     uint8_t* smask = nullptr;
     int64_t smask_cap = 0;
+    // exact decisions (ART_MIXED_EXACT): per-pixel exactness bytes, the borderline list, the FP64
+    // queue and the list of interpolants to recompute of the current level
+    uint8_t* xst = nullptr;
+    int64_t xst_cap = 0;
+    int32_t* cborder = nullptr;
+    int64_t cborder_cap = 0;
+    int32_t* cxq = nullptr;
+    int64_t cxq_cap = 0;
+    uint64_t* cfixq = nullptr;
+    int64_t cfixq_cap = 0;
     float* prob = nullptr;
     int64_t prob_cap = 0;
     // batched rendering tables and queue (grown, never shrunk)
@@ -202,7 +212,7 @@ static int make_devjob(const art_job* job, DevJob* J)
     if (job->interp != ART_INTERP_LINEAR && job->interp != ART_INTERP_NEAREST) return ART_ERR_ARG;
     if (job->edge_mode != ART_EDGE_ONESIDED && job->edge_mode != ART_EDGE_TRACE) return ART_ERR_ARG;
     if (job->abs_norm != ART_NORM_IBAR_INT && job->abs_norm != ART_NORM_PEAK) return ART_ERR_ARG;
-    if (job->precision < ART_FP64 || job->precision > ART_MIXED_DF) return ART_ERR_ARG;
+    if (job->precision < ART_FP64 || job->precision > ART_MIXED_EXACT) return ART_ERR_ARG;
     if (!(job->disk_w > 0.0)) return ART_ERR_ARG;
     if (!(job->fp64_sweep > 0.0)) return ART_ERR_ARG;
     J->a = job->a;
@@ -229,9 +239,19 @@ static int make_devjob(const art_job* job, DevJob* J)
     J->interp = job->interp;
     J->edge_mode = job->edge_mode;
     J->abs_norm = job->abs_norm;
-    J->precision = job->precision;
+    // exact decisions change the level loop only; the rays are traced as in ART_MIXED_DF
+    J->precision = job->precision == ART_MIXED_EXACT ? ART_MIXED_DF : job->precision;
     return ART_OK;
 }
+
+// Exact decisions (ART_MIXED_EXACT): relative band of a tolerance within which a decision on
+// FP32-traced values is re-made on exact values.  FP32-traced intensities differ from FP64 by
+// ~1e-5 relative (median; 1e-3 on lensed rays), and the estimates' cancellation (their numerators
+// are second differences) magnifies that ~10-500 times near the tolerances.
+constexpr double CERT_BAND = 2.5e-1;
+
+// Relative tolerances of the mixed modes' discontinuity flags (SynchConst::e_sig, e_rin).
+constexpr double EDGE_SIGMA_TOL = 1e-2, EDGE_RIN_TOL = 2e-3;
 
 // Constants of the synchrotron models in the scaled form the kernels use (cgs constants, CODATA).
 // g: the context's fluid grid (ART_EMIT_GRID), null where there is none.
@@ -271,6 +291,14 @@ static void make_synch(const art_job* job, const art_ctx* g, SynchConst* S)
         S->g_r_high = job->r_high;
         S->g_r_low = job->r_low;
         S->g_sigma_cut = job->sigma_cut;
+    }
+    if (job->precision == ART_MIXED || job->precision == ART_MIXED_DF ||
+        job->precision == ART_MIXED_EXACT) {
+        // the FP32 pass hands rays with a sample this close to a discontinuity of the emission
+        // model to the high-precision re-trace (FP32 positions of lensed rays differ from FP64
+        // by up to ~1e-3 in sigma, ~1e-5 in r)
+        S->e_sig = EDGE_SIGMA_TOL;
+        S->e_rin = EDGE_RIN_TOL;
     }
     S->LCj = L * sqrt(2.0) * pi * e * e / (3.0 * c);
     S->CB = e / (2.0 * pi * me * c);
@@ -370,6 +398,10 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFree(c->aux);
     cudaFree(c->smask);
     cudaFree(c->prob);
+    cudaFree(c->xst);
+    cudaFree(c->cborder);
+    cudaFree(c->cxq);
+    cudaFree(c->cfixq);
     for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -436,7 +468,8 @@ static int64_t max_level_rays(const DevJob& J)
 static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
                        const unsigned long long* count, double* img, uint8_t* mask, double* out,
                        const art_rayaux* aux, float* pix_minr = nullptr, float* pix_turn = nullptr,
-                       const unsigned long long* spec_from = nullptr)
+                       const unsigned long long* spec_from = nullptr,
+                       const int32_t* qbuf = nullptr)
 {
     TraceArgs a;
     memset(&a, 0, sizeof a);
@@ -448,7 +481,7 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
     a.spec_from = spec_from;
     make_synch(job, c, &a.synch);
     a.cam = c->cam;
-    a.queue = c->queue;
+    a.queue = qbuf ? qbuf : c->queue;
     a.count = count;
     a.counters = c->counters;
     a.img = img;
@@ -586,6 +619,8 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
     const bool band = job->crit_band > 0.0;
     if (band && (truth_dev || !(job->crit_band < 1.0))) return ART_ERR_ARG;
     const bool spec_any = learned || band;
+    const bool cert = job->precision == ART_MIXED_EXACT;
+    if (cert && truth_dev) return ART_ERR_ARG;
     CK(cudaSetDevice(c->device));
     const int64_t cap = max_level_rays(J);
     // the learned path appends speculative rays of later levels to a level's queue
@@ -604,13 +639,30 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
         c->aux_npix = 0;
     }
     uint8_t* mask = mask_dev;
-    if (spec_any) {
+    if (spec_any || cert) {
         if (!mask) {
             if ((rc = grow(c, c->smask, c->smask_cap, npix))) return rc;
             mask = c->smask;
         }
         CK(cudaMemsetAsync(mask, 0, npix, st));  // speculation claims points whose mask is unset
     }
+    // exact decisions: list capacities (a full borderline list leaves further points to the
+    // ordinary decision, counted in border_overflow; the closure lists hold every point at most
+    // once and are sized to the image)
+    unsigned long long bcap = 0, xcap = 0;
+    if (cert) {
+        const int64_t b = std::min<int64_t>(npix, std::max<int64_t>(65536, cap / 64));
+        const int64_t x = std::min<int64_t>(npix, 16 * b);
+        if ((rc = grow(c, c->xst, c->xst_cap, (npix + 3) / 4 * 4)) ||
+            (rc = grow(c, c->cborder, c->cborder_cap, b)) || (rc = grow(c, c->cxq, c->cxq_cap, x)) ||
+            (rc = grow(c, c->cfixq, c->cfixq_cap, x)))
+            return rc;
+        bcap = (unsigned long long)b;
+        xcap = (unsigned long long)x;
+        CK(cudaMemsetAsync(c->xst, 0, (npix + 3) / 4 * 4, st));
+    }
+    DevJob J64 = J;
+    J64.precision = ART_FP64;
     if (learned) {
         int64_t pc = 1;
         for (int lv = 0; lv + 2 <= J.levels; ++lv) pc = std::max(pc, cnn_head_cells(J, lv));
@@ -645,10 +697,40 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
             const int s = 1 << (J.levels - level);
             CK(cudaMemsetAsync(c->counters + C_QUEUE, 0, sizeof(unsigned long long), st));
             k = prof_begin(c);
-            CK(launch_refine(J, level, c->norm3, img_dev, mask, c->queue, c->counters + C_QUEUE, st,
-                             aminr, aturn, spec_any ? c->counters : nullptr));
+            if (cert) {
+                CK(cudaMemsetAsync(c->counters + C_BORDER, 0, 3 * sizeof(unsigned long long), st));
+                CK(launch_refine_cert(J, level, c->norm3, img_dev, mask, c->queue,
+                                      c->counters + C_QUEUE, st, aminr, aturn,
+                                      spec_any ? c->counters : nullptr, c->xst, CERT_BAND,
+                                      c->cborder, c->counters, bcap));
+            } else {
+                CK(launch_refine(J, level, c->norm3, img_dev, mask, c->queue,
+                                 c->counters + C_QUEUE, st, aminr, aturn,
+                                 spec_any ? c->counters : nullptr));
+            }
             prof_end(c, k, ART_K_REFINE, (int64_t)((J.nx - 1) / s + 1) * ((J.ny - 1) / s + 1));
             CK(launch_level_count(c->counters, level, st));
+            if (cert) {
+                // the borderline points: exact stencils (FP64 re-traces, recomputed
+                // interpolants, coarsest level first), then their FP64 decisions
+                CK(launch_counter_clamp(c->counters, C_BORDER, bcap, st));
+                k = prof_begin(c);
+                CK(launch_cert_closure(J, level, c->cborder, bcap, c->counters, c->xst, mask,
+                                       c->cxq, xcap, c->cfixq, xcap, st));
+                CK(launch_counter_clamp(c->counters, C_XQ, xcap, st));
+                CK(launch_counter_clamp(c->counters, C_FIXQ, xcap, st));
+                prof_end(c, k, ART_K_OTHER, -1);
+                if ((rc = trace_queue(c, job, J64, c->counters + C_XQ, img_dev, mask, nullptr,
+                                      nullptr, aminr, aturn, nullptr, c->cxq)))
+                    return rc;
+                k = prof_begin(c);
+                CK(launch_cert_mark_traced(c->cxq, c->counters, xcap, c->xst, st));
+                for (int lv = 1; lv < level; ++lv)
+                    CK(launch_cert_fixup(J, c->cfixq, c->counters, xcap, lv, img_dev, c->xst, st));
+                CK(launch_cert_redecide(J, level, c->norm3, c->cborder, c->counters, bcap, img_dev,
+                                        mask, c->xst, aminr, aturn, st));
+                prof_end(c, k, ART_K_OTHER, -1);
+            }
             if (learned && level + 1 <= J.levels && (level - 1) % job->proposal_depth == 0) {
                 // every D = proposal_depth levels the network reads the completed level-(k-1)
                 // lattice and proposes points of levels k+1 .. k+D, traced now together with
@@ -669,6 +751,24 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
             CK(launch_gather_truth(J, c->queue, c->counters + C_QUEUE, truth_dev, img_dev, mask_dev,
                                    cap, st));
             prof_end(c, k, ART_K_OTHER, -1);
+        } else if (cert && level == 0) {
+            // exact decisions: the base level in FP64 (exact I_bar_int and the exact ends of every
+            // closure), the band's speculative rays of later levels in the mixed precision
+            const int S0 = 1 << J.levels;
+            const int64_t n0 = (int64_t)((J.nx - 1) / S0 + 1) * ((J.ny - 1) / S0 + 1);
+            if ((rc = trace_queue(c, job, J64, c->counters + C_LEVEL0, img_dev, mask, nullptr,
+                                  nullptr, aminr, aturn)))
+                return rc;
+            k = prof_begin(c);
+            CK(launch_cert_mark_base(J, c->xst, st));
+            prof_end(c, k, ART_K_OTHER, -1);
+            if (spec) {
+                CK(launch_cert_spec_count(c->counters, st));
+                if ((rc = trace_queue(c, job, J, c->counters + C_SPECN, img_dev, mask, nullptr,
+                                      nullptr, aminr, aturn, c->counters + C_ZERO,
+                                      c->queue + n0)))
+                    return rc;
+            }
         } else {
             if ((rc = trace_queue(c, job, J, c->counters + C_QUEUE, img_dev, mask, nullptr, nullptr,
                                   aminr, aturn, spec ? c->counters + C_SPECFROM : nullptr)))
@@ -696,7 +796,13 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
         stats->kernel_launches = c->launches;
         stats->rays_speculative = (int64_t)c->pinned[C_SPEC];
         stats->rays_spec_used = (int64_t)c->pinned[C_SPECUSED];
-        if (c->pinned[C_BADIDX] || c->pinned[C_SYNCERR]) return ART_ERR_DEVICE;
+        if (cert) {
+            stats->rays_exact = (int64_t)c->pinned[C_XRAYS] + stats->rays_per_level[0];
+            stats->border_points = (int64_t)c->pinned[C_BTOT];
+            stats->border_overflow = (int64_t)c->pinned[C_CERTOVF];
+        }
+        if (c->pinned[C_BADIDX] || c->pinned[C_SYNCERR] || c->pinned[C_CERTERR])
+            return ART_ERR_DEVICE;
     }
     return ART_OK;
 }
@@ -958,6 +1064,7 @@ static int plan_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const*
     for (int i = 0; i < n; ++i) {
         int rc = make_devjob(&jobs[i], &P.J[i]);
         if (rc) return rc;
+        if (jobs[i].precision == ART_MIXED_EXACT) return ART_ERR_UNSUPPORTED;  // art_render only
         if (!imgs[i]) return ART_ERR_ARG;
         if (jobs[i].crit_band > 0.0) {
             if (!(jobs[i].crit_band < 1.0)) return ART_ERR_ARG;
@@ -1084,6 +1191,18 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
                                 uint8_t* const* masks, art_stats* stats)
 {
     if (!c || !jobs || !imgs || n < 1) return ART_ERR_ARG;
+    if (jobs[0].precision == ART_MIXED_EXACT) {
+        // exact decisions keep per-image closure lists: the images are rendered one after the
+        // other through the single-image level loop (every job of the batch must ask for them)
+        for (int i = 0; i < n; ++i)
+            if (jobs[i].precision != ART_MIXED_EXACT) return ART_ERR_ARG;
+        for (int i = 0; i < n; ++i) {
+            const int rc = art_render(c, &jobs[i], nullptr, imgs[i], masks ? masks[i] : nullptr,
+                                      stats ? &stats[i] : nullptr);
+            if (rc) return rc;
+        }
+        return ART_OK;
+    }
     BatchPlan P;
     int rc = plan_batch(c, jobs, n, imgs, masks, P);
     if (rc) return rc;

@@ -37,7 +37,8 @@ ART_HD void grid_axis_clamped(Q f, int n, int& i0, Q& w)
 // Emission of the grid model at one point (J4, K7 as emission_synch).  f nullable.
 template <class Q>
 __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, const Q* f,
-                                              const DevJob& J, const SynchConst& S, Q* J4, Q* K7)
+                                              const DevJob& J, const SynchConst& S, Q* J4, Q* K7,
+                                              int* edge = nullptr)
 {
     for (int i = 0; i < 4; ++i) J4[i] = Q(0);
     for (int i = 0; i < 7; ++i) K7[i] = Q(0);
@@ -122,6 +123,10 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     const Q BB = fmad(B[3], B[3], fmad(B[2], B[2], B[1] * B[1]));
     const Q b2 = fmad(b[0], b[0], fmad(G.F * LB, LB, BB)) * (iut * iut);
     if (!(b2 > Q(0))) return;
+    // a sample within rounding of the cut may keep or lose its emission in another precision
+    if (edge && S.e_sig > 0.0 &&
+        fabs(b2 - Q(S.g_sigma_cut) * rho) < Q(S.e_sig) * Q(S.g_sigma_cut) * rho)
+        *edge = 1;
     if (b2 > Q(S.g_sigma_cut) * rho) return;
     const Q pg = Q(S.g_gm1) * ug, pm = Q(0.5) * b2;
     const Q pg2 = pg * pg, pm2 = pm * pm;

@@ -25,9 +25,24 @@ enum Counter {
     C_SPEC = 10,     // learned path: rays queued speculatively (all levels)
     C_SPECUSED = 11, // learned path: speculative rays the exact criterion asked for
     C_SYNCERR = 12,  // warp-pair trace kernels: a hand-over wait that ran out of time
+    C_BORDER = 13,   // exact decisions: borderline points of the current level
+    C_XQ = 14,       // exact decisions: length of the FP64 queue of the current level
+    C_FIXQ = 15,     // exact decisions: interpolated points to recompute at the current level
     C_LEVEL0 = 16,   // C_LEVEL0 + k: rays of level k (16 slots)
-    C_COUNT = 32
+    C_CERTERR = 32,  // exact decisions: a stencil value was not exact when it was used
+    C_XRAYS = 33,    // exact decisions: FP64 rays traced for them (all levels)
+    C_BTOT = 34,     // exact decisions: borderline points (all levels)
+    C_CERTOVF = 35,  // exact decisions: points decided without them (lists full)
+    C_SPECN = 36,    // exact decisions: length of the speculative part of the base-level queue
+    C_ZERO = 37,     // always 0
+    C_COUNT = 64
 };
+
+// Exact-decision state of a pixel (one byte per pixel, ART_MIXED_EXACT): its value equals the
+// FP64 render's (FP64-traced, or interpolated from such values); claimed by the closure search.
+constexpr uint8_t XS_EXACT = 1, XS_CLAIM = 2;
+// Transient mask value of a borderline point whose decision waits for exact stencil values.
+constexpr uint8_t MASK_PENDING = 5;
 
 struct TraceArgs {
     DevJob job;
@@ -127,6 +142,31 @@ cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double
                           cudaStream_t st, float* aux_minr = nullptr, float* aux_turn = nullptr,
                           unsigned long long* spec_used = nullptr);
 cudaError_t launch_level_count(unsigned long long* counters, int level, cudaStream_t st);
+// refine.cu: exact decisions (ART_MIXED_EXACT)
+cudaError_t launch_refine_cert(const DevJob& J, int level, const double* norm, double* img,
+                               uint8_t* mask, int32_t* queue, unsigned long long* count,
+                               cudaStream_t st, float* aux_minr, float* aux_turn,
+                               unsigned long long* spec_counters, uint8_t* xst, double band,
+                               int32_t* border, unsigned long long* counters,
+                               unsigned long long border_cap);
+cudaError_t launch_cert_mark_base(const DevJob& J, uint8_t* xst, cudaStream_t st);
+cudaError_t launch_cert_spec_count(unsigned long long* counters, cudaStream_t st);
+cudaError_t launch_cert_closure(const DevJob& J, int level, const int32_t* border,
+                                unsigned long long border_cap, unsigned long long* counters,
+                                uint8_t* xst, const uint8_t* mask, int32_t* xq,
+                                unsigned long long xq_cap, uint64_t* fixq,
+                                unsigned long long fix_cap, cudaStream_t st);
+cudaError_t launch_cert_mark_traced(const int32_t* xq, unsigned long long* counters,
+                                    unsigned long long xq_cap, uint8_t* xst, cudaStream_t st);
+cudaError_t launch_cert_fixup(const DevJob& J, const uint64_t* fixq, unsigned long long* counters,
+                              unsigned long long fix_cap, int lvl, double* img, uint8_t* xst,
+                              cudaStream_t st);
+cudaError_t launch_cert_redecide(const DevJob& J, int level, const double* norm,
+                                 const int32_t* border, unsigned long long* counters,
+                                 unsigned long long border_cap, double* img, uint8_t* mask,
+                                 uint8_t* xst, float* aminr, float* aturn, cudaStream_t st);
+cudaError_t launch_counter_clamp(unsigned long long* counters, int idx, unsigned long long cap,
+                                 cudaStream_t st);
 cudaError_t launch_spec_mark(unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_queue_clamp(unsigned long long* counters, unsigned long long cap,
                                cudaStream_t st);

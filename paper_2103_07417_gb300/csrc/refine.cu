@@ -159,7 +159,7 @@ __device__ __forceinline__ double second_diff_sum(const double* img, int nx, int
 template <class IX>
 __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i, int j, int s,
                                       double norm, int cat, double& w1, double& w2, IX& p1, IX& p2,
-                                      IX& p3, IX& p4)
+                                      IX& p3, IX& p4, double& ea, double& er)
 {
     const int nx = J.nx, ny = J.ny;
     bool ok = true;
@@ -207,7 +207,6 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
             den = fabs(sin_) / 2.0;
         }
     }
-    double ea, er;
     if (!ok && J.interp == ART_INTERP_LINEAR) {
         ea = er = INFINITY;
     } else {
@@ -240,13 +239,16 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
 // X > 4 R_rel |S_in| in both cases.
 struct Screen {
     float tabs4, tabs2, rrel4;
+    float bup, bdn;         // 1 +/- the band of the exact-decision mode (1, 1 otherwise)
     bool abs_any, rel_any;  // negative tolerance: every estimate exceeds it
     bool on;
 };
 
-__device__ __forceinline__ Screen make_screen(const DevJob& J, double norm)
+__device__ __forceinline__ Screen make_screen(const DevJob& J, double norm, double band = 0.0)
 {
     Screen sc;
+    sc.bup = (float)(1.0 + band);
+    sc.bdn = (float)(1.0 - band);
     sc.on = J.interp == ART_INTERP_LINEAR && norm > 0.0 && norm < 1e300;
     sc.abs_any = J.R_abs < 0.0;
     sc.rel_any = J.R_rel < 0.0;
@@ -335,7 +337,7 @@ __device__ __forceinline__ int screen_decide(const Screen& sc, const double* img
     if (!ok) return -1;
     const float E = 0x1p-18f * C + 0x1p-118f;
     const float Es = 0x1p-18f * Cin + 0x1p-118f;
-    const float up = 1.f + 0x1p-18f, dn = 1.f - 0x1p-18f;
+    const float up = (1.f + 0x1p-18f) * sc.bup, dn = (1.f - 0x1p-18f) * sc.bdn;
     bool abs_t, abs_f, rel_t, rel_f;
     if (sc.abs_any) {
         abs_t = true;
@@ -399,68 +401,32 @@ __device__ __forceinline__ double scale_pow2(double v, int k)
     return v * (k == 1 ? 0.5 : 0.25);
 }
 
-// One new point of a level: decide (screen, else FP64), then mark it for tracing or write its
-// interpolant into every plane.  Returns true when the point is to be traced.
-// Learned path (spec = true): a point the criterion traces whose ray was already traced
-// speculatively (mask MASK_SPEC_DONE) is marked traced and not queued again (return 2).
-// Diagnostics planes (nullable) receive the mean of the interpolation parents.
+// Stencil of the interpolant of a new point (the points decide() names 1..4; nearest: point 1).
 template <class IX>
-__device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, double* img,
-                                            uint8_t* mask, int i, int j, int s, int cat,
-                                            double norm, int64_t npix, bool spec, float* aminr,
-                                            float* aturn)
+__device__ __forceinline__ void interp_parents(int nx, int i, int j, int s, int cat, IX& p1, IX& p2,
+                                               IX& p3, IX& p4)
 {
-    double w1, w2;
-    IX p1, p2, p3, p4;
-    const bool flat = sc.on && !sc.abs_any && J.interp == ART_INTERP_LINEAR &&
-                      uniform_stencil<IX>(img, J.nx, J.ny, i, j, s, cat);
-    const int scr = flat ? 0 : screen_decide<IX>(sc, img, J.nx, J.ny, i, j, s, cat);
-    bool trace;
-    if (scr < 0) {
-        trace = decide<IX>(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4);
+    if (cat == 4) {
+        p1 = (IX)(j - s) * nx + (i - s);
+        p4 = (IX)(j + s) * nx + (i + s);
+        p2 = (IX)(j + s) * nx + (i - s);
+        p3 = (IX)(j - s) * nx + (i + s);
     } else {
-        trace = scr == 1;
-        if (J.edge_mode == ART_EDGE_TRACE) {
-            const int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
-            if (i - 3 * di < 0 || i + 3 * di >= J.nx || j - 3 * dj < 0 || j + 3 * dj >= J.ny)
-                trace = true;
-        }
-        // stencil of the (linear) interpolant, as decide() sets it
-        const int nx = J.nx;
-        if (cat == 4) {
-            p1 = (IX)(j - s) * nx + (i - s);
-            p4 = (IX)(j + s) * nx + (i + s);
-            p2 = (IX)(j + s) * nx + (i - s);
-            p3 = (IX)(j - s) * nx + (i + s);
-        } else {
-            const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
-            p1 = (IX)(j - dj) * nx + (i - di);
-            p2 = (IX)(j + dj) * nx + (i + di);
-            p3 = p4 = -1;
-        }
-        w1 = w2 = 0.5;
+        const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
+        p1 = (IX)(j - dj) * nx + (i - di);
+        p2 = (IX)(j + dj) * nx + (i + di);
+        p3 = p4 = -1;
     }
-    const IX pix = (IX)j * J.nx + i;
-    if (trace) {
-        if (mask) {
-            const bool done = spec && mask[pix] == MASK_SPEC_DONE;
-            mask[pix] = ART_MASK_TRACED;
-            if (done) return 2;
-        }
-        return 1;
-    }
-    if (aminr) {
-        if (cat == 4) {
-            aminr[pix] = 0.25f * (((aminr[p1] + aminr[p2]) + aminr[p3]) + aminr[p4]);
-            aturn[pix] = 0.25f * (((aturn[p1] + aturn[p2]) + aturn[p3]) + aturn[p4]);
-        } else {
-            aminr[pix] = 0.5f * (aminr[p1] + aminr[p2]);
-            aturn[pix] = 0.5f * (aturn[p1] + aturn[p2]);
-        }
-    }
+}
+
+// The interpolant of a new point in every plane (linear: mean of the 2 or 4 parents; nearest:
+// point 1).  The one definition used by the criterion pass and by the exact-decision passes, so
+// that an interpolant recomputed from the same parents is the same bits.
+template <class IX>
+__device__ __forceinline__ void write_interp(const DevJob& J, double* img, IX pix, IX p1, IX p2,
+                                             IX p3, IX p4, int cat, int64_t npix)
+{
     const bool nearest = J.interp == ART_INTERP_NEAREST;
-    (void)w1;
-    (void)w2;
     for (int c = 0; c < J.planes; ++c) {
         const double* pl = img + c * npix;
         double v;
@@ -488,7 +454,123 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
         }
         img[c * npix + pix] = v;
     }
+}
+
+// Exact-decision mode (ART_MIXED_EXACT): per-pixel exactness bytes, the borderline list and the
+// band within which an FP64 decision on FP32-traced values is not trusted.
+struct CertArgs {
+    uint8_t* xst;
+    double band;
+};
+
+// Whether every value decide() reads for the point (parents, and for the linear scheme the outer
+// points inside the image) is exact.
+__device__ __forceinline__ bool stencil_exact(const DevJob& J, const uint8_t* xst, int i, int j,
+                                              int s, int cat)
+{
+    const int nx = J.nx, ny = J.ny;
+    auto ex = [&](int ii, int jj) {
+        if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) return true;  // outside: not read
+        return (xst[(int64_t)jj * nx + ii] & XS_EXACT) != 0;
+    };
+    const bool lin = J.interp == ART_INTERP_LINEAR;
+    if (cat == 4) {
+        if (!ex(i - s, j - s) || !ex(i + s, j + s) || !ex(i - s, j + s) || !ex(i + s, j - s))
+            return false;
+        if (lin && (!ex(i - 3 * s, j - 3 * s) || !ex(i + 3 * s, j + 3 * s) ||
+                    !ex(i - 3 * s, j + 3 * s) || !ex(i + 3 * s, j - 3 * s)))
+            return false;
+        return true;
+    }
+    const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
+    if (!ex(i - di, j - dj) || !ex(i + di, j + dj)) return false;
+    if (lin && (!ex(i - 3 * di, j - 3 * dj) || !ex(i + 3 * di, j + 3 * dj))) return false;
+    return true;
+}
+
+// Whether an FP64 decision on values with FP32 rounding in them can be trusted: every estimate
+// that decides it clears its tolerance by the relative band.  Negative tolerances are exceeded by
+// every estimate; infinite or NaN estimates trace whatever the values.
+__device__ __forceinline__ bool decision_robust(const DevJob& J, double ea, double er, double band)
+{
+    if (!(ea == ea) || !(er == er) || isinf(ea) || isinf(er)) return true;
+    const bool a_hi = J.R_abs < 0.0 || ea > J.R_abs * (1.0 + band);
+    const bool r_hi = J.R_rel < 0.0 || er > J.R_rel * (1.0 + band);
+    const bool a_lo = J.R_abs >= 0.0 && ea < J.R_abs * (1.0 - band);
+    const bool r_lo = J.R_rel >= 0.0 && er < J.R_rel * (1.0 - band);
+    return a_lo || r_lo || (a_hi && r_hi);
+}
+
+// One new point of a level: decide (screen, else FP64), then mark it for tracing or write its
+// interpolant into every plane.  Returns 1 when the point is to be traced, 0 when interpolated.
+// Learned path (spec = true): a point the criterion traces whose ray was already traced
+// speculatively (mask MASK_SPEC_DONE) is marked traced and not queued again (return 2).
+// Diagnostics planes (nullable) receive the mean of the interpolation parents.
+// CERT (exact decisions): a decision within the band of a tolerance whose stencil is not all
+// exact is left to the exact-decision passes (return 3, nothing written); an interpolated point
+// whose parents are exact is marked exact.
+template <class IX, bool CERT = false>
+__device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, double* img,
+                                            uint8_t* mask, int i, int j, int s, int cat,
+                                            double norm, int64_t npix, bool spec, float* aminr,
+                                            float* aturn, const CertArgs* ca = nullptr)
+{
+    double w1, w2;
+    IX p1, p2, p3, p4;
+    // a uniform stencil decides "interpolate" exactly; under CERT only where the tolerance
+    // leaves room for rounding of the values (R_abs > 0)
+    const bool flat = sc.on && !sc.abs_any && J.interp == ART_INTERP_LINEAR &&
+                      (!CERT || J.R_abs > 0.0) && uniform_stencil<IX>(img, J.nx, J.ny, i, j, s, cat);
+    const int scr = flat ? 0 : screen_decide<IX>(sc, img, J.nx, J.ny, i, j, s, cat);
+    bool trace;
+    if (scr < 0) {
+        double ea, er;
+        trace = decide<IX>(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4, ea, er);
+        if constexpr (CERT) {
+            if (!decision_robust(J, ea, er, ca->band) && !stencil_exact(J, ca->xst, i, j, s, cat))
+                return 3;
+        }
+    } else {
+        trace = scr == 1;
+        if (J.edge_mode == ART_EDGE_TRACE) {
+            const int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
+            if (i - 3 * di < 0 || i + 3 * di >= J.nx || j - 3 * dj < 0 || j + 3 * dj >= J.ny)
+                trace = true;
+        }
+        interp_parents<IX>(J.nx, i, j, s, cat, p1, p2, p3, p4);
+        w1 = w2 = 0.5;
+    }
+    const IX pix = (IX)j * J.nx + i;
+    if (trace) {
+        if (mask) {
+            const bool done = spec && mask[pix] == MASK_SPEC_DONE;
+            mask[pix] = ART_MASK_TRACED;
+            if (done) return 2;
+        }
+        return 1;
+    }
+    if (aminr) {
+        if (cat == 4) {
+            aminr[pix] = 0.25f * (((aminr[p1] + aminr[p2]) + aminr[p3]) + aminr[p4]);
+            aturn[pix] = 0.25f * (((aturn[p1] + aturn[p2]) + aturn[p3]) + aturn[p4]);
+        } else {
+            aminr[pix] = 0.5f * (aminr[p1] + aminr[p2]);
+            aturn[pix] = 0.5f * (aturn[p1] + aturn[p2]);
+        }
+    }
+    (void)w1;
+    (void)w2;
+    write_interp<IX>(J, img, pix, p1, p2, p3, p4, cat, npix);
     if (mask) mask[pix] = ART_MASK_INTERP;
+    if constexpr (CERT) {
+        const uint8_t* x = ca->xst;
+        bool ex = (x[p1] & XS_EXACT) != 0;
+        if (J.interp == ART_INTERP_LINEAR) {
+            ex = ex && (x[p2] & XS_EXACT);
+            if (cat == 4) ex = ex && (x[p3] & XS_EXACT) && (x[p4] & XS_EXACT);
+        }
+        if (ex) ca->xst[pix] = XS_EXACT;
+    }
     return 0;
 }
 
@@ -496,10 +578,12 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
 // division, and a warp covers 32 consecutive lattice points of one row.  Pixel offsets within a
 // plane are 32-bit (images are below 2^31 pixels: the ray queue holds 32-bit pixel indices), which
 // keeps the stencil's address arithmetic off the wide-multiply path.
+template <bool CERT>
 __global__ void __launch_bounds__(256)
     refine_kernel(DevJob J, int level, const double* __restrict__ norm_ptr, double* img,
                   uint8_t* mask, int32_t* queue, unsigned long long* qcount, float* aminr,
-                  float* aturn, unsigned long long* counters)
+                  float* aturn, unsigned long long* counters, CertArgs ca, int32_t* border,
+                  unsigned long long* cert_counters, unsigned long long border_cap)
 {
     const int s = 1 << (J.levels - level);
     const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
@@ -508,7 +592,7 @@ __global__ void __launch_bounds__(256)
     // the screen's thresholds once per block: made per thread, the compiler recomputed their
     // FP64 products inside the loop (to save registers), which kept GB300's FP64 pipe 75 % busy
     __shared__ Screen sc_s;
-    if (threadIdx.x == 0) sc_s = make_screen(J, norm);
+    if (threadIdx.x == 0) sc_s = make_screen(J, norm, CERT ? ca.band : 0.0);
     __syncthreads();
     const Screen sc = sc_s;
     const int lane = threadIdx.x & 31;
@@ -516,18 +600,46 @@ __global__ void __launch_bounds__(256)
         const int oj = jj & 1;
         for (int i0 = blockIdx.x * blockDim.x; i0 < nkx; i0 += gridDim.x * blockDim.x) {
             const int ii = i0 + (int)threadIdx.x;
-            bool trace = false, used = false;
+            bool trace = false, used = false, bord = false;
             int32_t pix = 0;
+            int i = 0, j = 0, cat = 0;
             if (ii < nkx) {
                 const int oi = ii & 1;
                 if (oi | oj) {
-                    const int i = ii * s, j = jj * s;
-                    const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                    const int r = refine_point<int>(J, sc, img, mask, i, j, s, cat, norm, npix,
-                                               counters != nullptr, aminr, aturn);
+                    i = ii * s;
+                    j = jj * s;
+                    cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+                    const int r = refine_point<int, CERT>(J, sc, img, mask, i, j, s, cat, norm,
+                                                          npix, counters != nullptr, aminr, aturn,
+                                                          &ca);
                     trace = r == 1;
                     used = r == 2;
+                    bord = r == 3;
                     pix = j * J.nx + i;
+                }
+            }
+            if constexpr (CERT) {
+                // borderline points join the exact-decision list; where it is full they are
+                // decided here after all (counted)
+                const unsigned bb = __ballot_sync(0xffffffffu, bord);
+                if (bb) {
+                    unsigned long long w = 0;
+                    if (lane == 0) w = atomicAdd(cert_counters + C_BORDER, (unsigned long long)__popc(bb));
+                    w = __shfl_sync(0xffffffffu, w, 0);
+                    if (bord) {
+                        const unsigned long long slot = w + __popc(bb & ((1u << lane) - 1u));
+                        if (slot < border_cap) {
+                            border[slot] = pix;
+                            if (mask) mask[pix] = MASK_PENDING;
+                        } else {
+                            atomicAdd(cert_counters + C_CERTOVF, 1ull);
+                            const int r = refine_point<int, false>(J, sc, img, mask, i, j, s, cat,
+                                                                   norm, npix, counters != nullptr,
+                                                                   aminr, aturn);
+                            trace = r == 1;
+                            used = r == 2;
+                        }
+                    }
                 }
             }
             // warp-aggregated append to the ray queue (ballot -> popc -> one atomic per warp)
@@ -569,8 +681,304 @@ cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double
 {
     const int s = 1 << (J.levels - level);
     const dim3 g = refine_grid((J.nx - 1) / s + 1, (J.ny - 1) / s + 1);
-    refine_kernel<<<g, 256, 0, st>>>(J, level, norm, img, mask, queue, count, aux_minr, aux_turn,
-                                     spec_counters);
+    refine_kernel<false><<<g, 256, 0, st>>>(J, level, norm, img, mask, queue, count, aux_minr,
+                                            aux_turn, spec_counters, CertArgs{nullptr, 0.0},
+                                            nullptr, nullptr, 0);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------------------------
+// Exact decisions (ART_MIXED_EXACT).  The FP32-traced values a decision reads differ from the FP64
+// render's by rounding, so a decision whose estimates lie within a band of a tolerance may differ
+// from the FP64 render's.  Those borderline points are decided here on exact values instead: the
+// values their stencil reads are made exact (FP64 re-traces of FP32-traced points, recomputed
+// interpolants of interpolated ones, down to exact values), then the point is decided in FP64.
+// The base level is traced in FP64, so I_bar_int and every closure end in exact values.
+// --------------------------------------------------------------------------------------------
+
+cudaError_t launch_refine_cert(const DevJob& J, int level, const double* norm, double* img,
+                               uint8_t* mask, int32_t* queue, unsigned long long* count,
+                               cudaStream_t st, float* aux_minr, float* aux_turn,
+                               unsigned long long* spec_counters, uint8_t* xst, double band,
+                               int32_t* border, unsigned long long* counters,
+                               unsigned long long border_cap)
+{
+    const int s = 1 << (J.levels - level);
+    const dim3 g = refine_grid((J.nx - 1) / s + 1, (J.ny - 1) / s + 1);
+    refine_kernel<true><<<g, 256, 0, st>>>(J, level, norm, img, mask, queue, count, aux_minr,
+                                           aux_turn, spec_counters, CertArgs{xst, band}, border,
+                                           counters, border_cap);
+    return cudaGetLastError();
+}
+
+// Level at which pixel (i, j) of the final grid is new (0: base lattice) and its stride there.
+__device__ __forceinline__ int pixel_level(int i, int j, int N, int& s)
+{
+    int k = N;
+    while (k > 0) {
+        const int st = 1 << (N - k + 1);  // stride of level k - 1
+        if ((i % st) != 0 || (j % st) != 0) break;
+        --k;
+    }
+    s = 1 << (N - k);
+    return k;
+}
+
+// Base lattice points are exact (traced in FP64).
+__global__ void cert_mark_base_kernel(DevJob J, uint8_t* xst)
+{
+    const int S0 = 1 << J.levels;
+    const int n0x = (J.nx - 1) / S0 + 1, n0y = (J.ny - 1) / S0 + 1;
+    const int64_t n = (int64_t)n0x * n0y;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int ii = (int)(q % n0x), jj = (int)(q / n0x);
+        xst[(int64_t)jj * S0 * J.nx + (int64_t)ii * S0] = XS_EXACT;
+    }
+}
+
+// counters[C_SPECN] = counters[C_QUEUE] - counters[C_LEVEL0]: the speculative part of the base
+// level's queue (band rays), traced in FP32 after the FP64 base rays.
+__global__ void cert_spec_count_kernel(unsigned long long* counters)
+{
+    const unsigned long long q = counters[C_QUEUE], b = counters[C_LEVEL0];
+    counters[C_SPECN] = q > b ? q - b : 0;
+}
+
+// Claim pixel p for the closure (true when this thread claimed it and it is not exact).
+__device__ __forceinline__ bool cert_claim(uint8_t* xst, int64_t p)
+{
+    if (xst[p] & (XS_EXACT | XS_CLAIM)) return false;
+    unsigned* w = reinterpret_cast<unsigned*>(xst + (p & ~(int64_t)3));
+    const unsigned bit = (unsigned)XS_CLAIM << (8 * (int)(p & 3));
+    const unsigned old = atomicOr(w, bit);
+    const unsigned prev = (old >> (8 * (int)(p & 3))) & 0xffu;
+    return (prev & (XS_EXACT | XS_CLAIM)) == 0;
+}
+
+constexpr int CERT_STACK = 96;
+
+// Closure of the borderline points: every non-exact value their decision reads is claimed once;
+// FP32-traced ones join the FP64 queue, interpolated ones the recompute list (with their level)
+// and their own parents are searched in turn.  The borderline points themselves join the FP64
+// queue too (traced speculatively: their decision may ask for them).
+__global__ void cert_closure_kernel(DevJob J, const int32_t* border, const unsigned long long* counters_ro,
+                                    unsigned long long* counters, uint8_t* xst, const uint8_t* mask,
+                                    int32_t* xq, unsigned long long xq_cap, uint64_t* fixq,
+                                    unsigned long long fix_cap, int level)
+{
+    const unsigned long long nb = counters_ro[C_BORDER];
+    const int nx = J.nx, ny = J.ny, N = J.levels;
+    const bool lin = J.interp == ART_INTERP_LINEAR;
+    for (unsigned long long b = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; b < nb;
+         b += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t p = border[b];
+        {
+            const unsigned long long w = atomicAdd(counters + C_XQ, 1ull);
+            if (w < xq_cap) xq[w] = p;
+            else atomicAdd(counters + C_CERTERR, 1ull);
+        }
+        int32_t stk[CERT_STACK];
+        int top = 0;
+        auto push = [&](int ii, int jj) {
+            if (ii < 0 || ii >= nx || jj < 0 || jj >= ny) return;
+            if (top < CERT_STACK) stk[top++] = jj * nx + ii;
+            else atomicAdd(counters + C_CERTERR, 1ull);
+        };
+        // the stencil decide() reads at the borderline point's level
+        const int i = p % nx, j = p / nx, s = 1 << (N - level);
+        const int oi = (i / s) & 1, oj = (j / s) & 1;
+        const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+        if (cat == 4) {
+            push(i - s, j - s); push(i + s, j + s); push(i - s, j + s); push(i + s, j - s);
+            if (lin) {
+                push(i - 3 * s, j - 3 * s); push(i + 3 * s, j + 3 * s);
+                push(i - 3 * s, j + 3 * s); push(i + 3 * s, j - 3 * s);
+            }
+        } else {
+            const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
+            push(i - di, j - dj); push(i + di, j + dj);
+            if (lin) { push(i - 3 * di, j - 3 * dj); push(i + 3 * di, j + 3 * dj); }
+        }
+        while (top > 0) {
+            const int32_t q = stk[--top];
+            if (!cert_claim(xst, q)) continue;
+            if (mask[q] == ART_MASK_INTERP) {
+                const int qi = q % nx, qj = q / nx;
+                int qs;
+                const int ql = pixel_level(qi, qj, N, qs);
+                const unsigned long long w = atomicAdd(counters + C_FIXQ, 1ull);
+                if (w < fix_cap) fixq[w] = ((uint64_t)ql << 32) | (uint32_t)q;
+                else atomicAdd(counters + C_CERTERR, 1ull);
+                const int qoi = (qi / qs) & 1, qoj = (qj / qs) & 1;
+                const int qc = (qoi && qoj) ? 4 : (qoi ? 3 : 2);
+                if (qc == 4) {
+                    push(qi - qs, qj - qs);
+                    if (lin) { push(qi + qs, qj + qs); push(qi - qs, qj + qs); push(qi + qs, qj - qs); }
+                } else {
+                    const int di = (qc == 3) ? qs : 0, dj = (qc == 2) ? qs : 0;
+                    push(qi - di, qj - dj);
+                    if (lin) push(qi + di, qj + dj);
+                }
+            } else {
+                // traced in FP32 (or at a level with speculation): re-trace in FP64
+                const unsigned long long w = atomicAdd(counters + C_XQ, 1ull);
+                if (w < xq_cap) xq[w] = q;
+                else atomicAdd(counters + C_CERTERR, 1ull);
+            }
+        }
+    }
+}
+
+// After the FP64 pass: its pixels are exact; C_XRAYS counts them.
+__global__ void cert_mark_traced_kernel(const int32_t* xq, unsigned long long* counters,
+                                        unsigned long long xq_cap, uint8_t* xst)
+{
+    unsigned long long n = counters[C_XQ];
+    if (n > xq_cap) n = xq_cap;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x)
+        xst[xq[q]] = XS_EXACT;
+    if (blockIdx.x == 0 && threadIdx.x == 0) counters[C_XRAYS] += n;
+}
+
+// Recompute the interpolants of the listed points of level `lvl` from their (now exact) parents.
+__global__ void cert_fixup_kernel(DevJob J, const uint64_t* fixq, unsigned long long* counters,
+                                  unsigned long long fix_cap, int lvl, double* img, uint8_t* xst)
+{
+    unsigned long long n = counters[C_FIXQ];
+    if (n > fix_cap) n = fix_cap;
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint64_t e = fixq[q];
+        if ((int)(e >> 32) != lvl) continue;
+        const int32_t p = (int32_t)(e & 0xffffffffu);
+        const int i = p % J.nx, j = p / J.nx, s = 1 << (J.levels - lvl);
+        const int oi = (i / s) & 1, oj = (j / s) & 1;
+        const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+        int p1, p2, p3, p4;
+        interp_parents<int>(J.nx, i, j, s, cat, p1, p2, p3, p4);
+        bool ok = (xst[p1] & XS_EXACT) != 0;
+        if (J.interp == ART_INTERP_LINEAR) {
+            ok = ok && (xst[p2] & XS_EXACT);
+            if (cat == 4) ok = ok && (xst[p3] & XS_EXACT) && (xst[p4] & XS_EXACT);
+        }
+        if (!ok) atomicAdd(counters + C_CERTERR, 1ull);
+        write_interp<int>(J, img, p, p1, p2, p3, p4, cat, npix);
+        xst[p] = XS_EXACT;
+    }
+}
+
+// Decide the borderline points of `level` in FP64 on their exact stencils.  Those to be traced
+// keep the FP64 ray traced for them (mask TRACED) and count as rays of the level; the others
+// receive their interpolant.  All become exact.
+__global__ void cert_redecide_kernel(DevJob J, int level, const double* __restrict__ norm_ptr,
+                                     const int32_t* border, unsigned long long* counters,
+                                     unsigned long long border_cap, double* img, uint8_t* mask,
+                                     uint8_t* xst, float* aminr, float* aturn)
+{
+    unsigned long long n = counters[C_BORDER];
+    if (n > border_cap) n = border_cap;
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    const double norm = *norm_ptr;
+    const int s = 1 << (J.levels - level);
+    unsigned long long traced = 0;
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t p = border[q];
+        const int i = p % J.nx, j = p / J.nx;
+        const int oi = (i / s) & 1, oj = (j / s) & 1;
+        const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+        if (!stencil_exact(J, xst, i, j, s, cat)) atomicAdd(counters + C_CERTERR, 1ull);
+        double w1, w2, ea, er;
+        int p1, p2, p3, p4;
+        bool tr = decide<int>(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4, ea, er);
+        if (J.edge_mode == ART_EDGE_TRACE) {
+            const int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
+            if (i - 3 * di < 0 || i + 3 * di >= J.nx || j - 3 * dj < 0 || j + 3 * dj >= J.ny)
+                tr = true;
+        }
+        if (tr) {
+            mask[p] = ART_MASK_TRACED;
+            ++traced;
+        } else {
+            interp_parents<int>(J.nx, i, j, s, cat, p1, p2, p3, p4);
+            if (aminr) {
+                if (cat == 4) {
+                    aminr[p] = 0.25f * (((aminr[p1] + aminr[p2]) + aminr[p3]) + aminr[p4]);
+                    aturn[p] = 0.25f * (((aturn[p1] + aturn[p2]) + aturn[p3]) + aturn[p4]);
+                } else {
+                    aminr[p] = 0.5f * (aminr[p1] + aminr[p2]);
+                    aturn[p] = 0.5f * (aturn[p1] + aturn[p2]);
+                }
+            }
+            write_interp<int>(J, img, p, p1, p2, p3, p4, cat, npix);
+            mask[p] = ART_MASK_INTERP;
+        }
+        xst[p] = XS_EXACT;
+    }
+    if (traced) atomicAdd(counters + C_LEVEL0 + level, traced);
+    if (blockIdx.x == 0 && threadIdx.x == 0) counters[C_BTOT] += n;
+}
+
+static int cert_grid(unsigned long long cap)
+{
+    unsigned long long g = (cap + 255) / 256;
+    if (g > 1216) g = 1216;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+cudaError_t launch_cert_mark_base(const DevJob& J, uint8_t* xst, cudaStream_t st)
+{
+    const int S0 = 1 << J.levels;
+    const int64_t n = (int64_t)((J.nx - 1) / S0 + 1) * ((J.ny - 1) / S0 + 1);
+    cert_mark_base_kernel<<<cert_grid((unsigned long long)n), 256, 0, st>>>(J, xst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cert_spec_count(unsigned long long* counters, cudaStream_t st)
+{
+    cert_spec_count_kernel<<<1, 1, 0, st>>>(counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cert_closure(const DevJob& J, int level, const int32_t* border,
+                                unsigned long long border_cap, unsigned long long* counters,
+                                uint8_t* xst, const uint8_t* mask, int32_t* xq,
+                                unsigned long long xq_cap, uint64_t* fixq,
+                                unsigned long long fix_cap, cudaStream_t st)
+{
+    cert_closure_kernel<<<cert_grid(border_cap), 256, 0, st>>>(J, border, counters, counters, xst,
+                                                               mask, xq, xq_cap, fixq, fix_cap,
+                                                               level);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cert_mark_traced(const int32_t* xq, unsigned long long* counters,
+                                    unsigned long long xq_cap, uint8_t* xst, cudaStream_t st)
+{
+    cert_mark_traced_kernel<<<cert_grid(xq_cap), 256, 0, st>>>(xq, counters, xq_cap, xst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cert_fixup(const DevJob& J, const uint64_t* fixq, unsigned long long* counters,
+                              unsigned long long fix_cap, int lvl, double* img, uint8_t* xst,
+                              cudaStream_t st)
+{
+    cert_fixup_kernel<<<cert_grid(fix_cap), 256, 0, st>>>(J, fixq, counters, fix_cap, lvl, img, xst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cert_redecide(const DevJob& J, int level, const double* norm,
+                                 const int32_t* border, unsigned long long* counters,
+                                 unsigned long long border_cap, double* img, uint8_t* mask,
+                                 uint8_t* xst, float* aminr, float* aturn, cudaStream_t st)
+{
+    cert_redecide_kernel<<<cert_grid(border_cap), 256, 0, st>>>(J, level, norm, border, counters,
+                                                                border_cap, img, mask, xst, aminr,
+                                                                aturn);
     return cudaGetLastError();
 }
 
@@ -602,6 +1010,18 @@ cudaError_t launch_spec_mark(unsigned long long* counters, cudaStream_t st)
 __global__ void queue_clamp_kernel(unsigned long long* counters, unsigned long long cap)
 {
     if (counters[C_QUEUE] > cap) counters[C_QUEUE] = cap;
+}
+
+__global__ void counter_clamp_kernel(unsigned long long* counters, int idx, unsigned long long cap)
+{
+    if (counters[idx] > cap) counters[idx] = cap;
+}
+
+cudaError_t launch_counter_clamp(unsigned long long* counters, int idx, unsigned long long cap,
+                                 cudaStream_t st)
+{
+    counter_clamp_kernel<<<1, 1, 0, st>>>(counters, idx, cap);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_queue_clamp(unsigned long long* counters, unsigned long long cap,

@@ -53,6 +53,10 @@ struct SynchConst {
     double g_b_unit;     // c sqrt(4 pi m_unit / L^3)       [gauss per code field]
     double g_th_unit;    // (m_p / m_e)(gamma_ad - 1)
     double g_r_high, g_r_low, g_sigma_cut;
+    // FP32 pass of the mixed modes (0 elsewhere): relative distances from the emission model's
+    // discontinuities (the magnetisation cut b^2/rho = sigma_cut, the disk's inner edge r_in) within
+    // which a sample flags its ray for the high-precision re-trace
+    double e_sig, e_rin;
 };
 
 // K_0, K_1, K_2 scaled by e^x (K_n(x) e^x), so that FP32 stays finite for cold plasma (large x).
@@ -206,10 +210,16 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
 // f (nullable) is the transported covector; without it only the I terms are returned.
 template <class Q>
 ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const DevJob& J,
-                           const SynchConst& S, Q* J4, Q* K7)
+                           const SynchConst& S, Q* J4, Q* K7, int* edge = nullptr)
 {
     for (int i = 0; i < 4; ++i) J4[i] = Q(0);
     for (int i = 0; i < 7; ++i) K7[i] = Q(0);
+    // a sample within rounding of the inner edge (in the emitting layer) may fall on either side
+    // of it in another precision: the ray's intensity then jumps by a whole segment's emission
+    if (edge && S.e_rin > 0.0 && fabs(r - Q(S.r_in)) < Q(S.e_rin) * Q(S.r_in)) {
+        const Q c0 = s.z / r;
+        if (c0 * c0 * Q(S.inv_2w2) < Q(20)) *edge = 1;
+    }
     if (r < Q(J.r_in_stop) || r < Q(S.r_in)) return;
     const Q a = Q(J.a), a2 = Q(J.a2);
     Q ct = s.z / r, ct2 = ct * ct, r2 = r * r;

@@ -153,6 +153,7 @@ struct XferState {
     Q T, oz;         // transmission (unpolarized); z of the current point
     float min_r;
     int nturn, tsign, crossed;
+    int edge;  // a sample lay near a discontinuity of the emission model (coefficients())
 };
 
 // The end point of a geodesic step as the transfer part needs it.
@@ -184,16 +185,19 @@ __device__ __forceinline__ R phi1(R x)
 enum EmitKernel { EM_ANALYTIC = 0, EM_GRID = 1 };
 
 // Emission/absorption/rotation coefficients at a point (J4, K7 as in synch.cuh).
+// edge: set to 1 when the point lies within the FP32 pass's tolerance of a discontinuity of the
+// emission model (left unchanged otherwise).
 template <class Q, bool POL, int EM>
 __device__ __forceinline__ void coefficients(const RayState<Q>& q, Q r, Q kt, const Q* f,
-                                             const DevJob& J, const SynchConst& S, Q* J4, Q* K7)
+                                             const DevJob& J, const SynchConst& S, Q* J4, Q* K7,
+                                             int& edge)
 {
     if (EM == EM_GRID) {
-        emission_grid<Q>(q, r, kt, POL ? f : nullptr, J, S, J4, K7);
+        emission_grid<Q>(q, r, kt, POL ? f : nullptr, J, S, J4, K7, &edge);
         return;
     }
     if (J.emission == ART_EMIT_SYNCH_DISK) {
-        emission_synch<Q>(q, r, kt, POL ? f : nullptr, J, S, J4, K7);
+        emission_synch<Q>(q, r, kt, POL ? f : nullptr, J, S, J4, K7, &edge);
         return;
     }
     for (int i = 1; i < 4; ++i) J4[i] = Q(0);
@@ -246,8 +250,9 @@ __device__ __forceinline__ void geo_init(GeoState<R>& g, const DevJob& J, const 
 // propagator, empty planes, turn counting from there.
 template <class Q, bool POL>
 __device__ __forceinline__ void xfer_init_with(XferState<Q>& x, const StepPoint<Q>& pt,
-                                               const Q* J1, const Q* K1)
+                                               const Q* J1, const Q* K1, int e1)
 {
+    x.edge = e1;
     for (int i = 0; i < 4; ++i) x.J0[i] = J1[i];
     for (int i = 0; i < 7; ++i) x.K0[i] = K1[i];
     if (POL)
@@ -270,8 +275,9 @@ __device__ __forceinline__ void xfer_init(XferState<Q>& x, const StepPoint<Q>& p
                                           const SynchConst& S)
 {
     Q J1[4], K1[7];
-    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1);
-    xfer_init_with<Q, POL>(x, pt, J1, K1);
+    int e1 = 0;
+    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1, e1);
+    xfer_init_with<Q, POL>(x, pt, J1, K1, e1);
 }
 
 template <class R, bool POL, int EM>
@@ -465,8 +471,9 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
 // in J and A, or the exact Stokes segment of the averaged coefficients).
 template <class Q, bool POL>
 __device__ __forceinline__ void xfer_apply(XferState<Q>& t, const StepPoint<Q>& pt, const Q* J1,
-                                           const Q* K1, const DevJob& J)
+                                           const Q* K1, const DevJob& J, int e1)
 {
+    t.edge |= e1;
     const RayState<Q>& q = pt.q;
     const Q rn = pt.r, hq = pt.h;
     int seg = t.nturn;
@@ -516,8 +523,9 @@ __device__ __forceinline__ void xfer_step(XferState<Q>& t, const StepPoint<Q>& p
                                           const SynchConst& S)
 {
     Q J1[4], K1[7];
-    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1);
-    xfer_apply<Q, POL>(t, pt, J1, K1, J);
+    int e1 = 0;
+    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1, e1);
+    xfer_apply<Q, POL>(t, pt, J1, K1, J, e1);
 }
 
 // The covector's RK4 step on the transfer half, along the stage states recorded by the geodesic

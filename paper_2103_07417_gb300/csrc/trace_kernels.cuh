@@ -23,8 +23,8 @@ __device__ __forceinline__ void finish_ray(const TraceArgs& A, int status, int s
                                            const XferState<Q>& x, int32_t pix, int64_t slot)
 {
     atomicAdd(A.counters + C_STEPS, (unsigned long long)steps);
-    const bool rer = A.reroute != nullptr &&
-                     (status == RAY_REROUTE || status == ART_RAY_NAN || status == ART_RAY_CAP);
+    const bool rer = A.reroute != nullptr && (status == RAY_REROUTE || status == ART_RAY_NAN ||
+                                              status == ART_RAY_CAP || x.edge);
     if (rer) {
         unsigned long long w = atomicAdd(A.reroute_count, 1ull);
         A.reroute[w] = (int32_t)slot;
@@ -173,8 +173,8 @@ __device__ __forceinline__ void finish_batch_ray(const BatchTraceArgs& A, int st
                                                  int32_t img)
 {
     atomicAdd(A.counters + C_STEPS, (unsigned long long)steps);
-    const bool rer = A.reroute != nullptr &&
-                     (status == RAY_REROUTE || status == ART_RAY_NAN || status == ART_RAY_CAP);
+    const bool rer = A.reroute != nullptr && (status == RAY_REROUTE || status == ART_RAY_NAN ||
+                                              status == ART_RAY_CAP || x.edge);
     if (rer) {
         unsigned long long w = atomicAdd(A.reroute_count, 1ull);
         A.reroute[w] = (int32_t)slot;
@@ -416,7 +416,7 @@ struct QuadRing {
     int32_t code[QUAD_SLOTS][32], pix[QUAD_SLOTS][32];
     int64_t slot[QUAD_SLOTS][32];
     int32_t last[QUAD_SLOTS];
-    Q c[QUAD_SLOTS][11][32];  // J1 (4) and K1 (7) at the record's point
+    Q c[QUAD_SLOTS][12][32];  // J1 (4), K1 (7) and the discontinuity flag at the record's point
     uint64_t a_full[QUAD_SLOTS], a_empty[QUAD_SLOTS], c_full[QUAD_SLOTS], c_empty[QUAD_SLOTS];
 };
 
@@ -540,7 +540,8 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
             __syncwarp();
             pair_arrive(&sm.a_empty[sl]);
             Q J1[4], K1[7];
-            if (need) coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1);
+            int e1 = 0;
+            if (need) coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1, e1);
             if (it >= NSL && !__all_sync(0xffffffffu, pair_wait(&sm.c_empty[sl], ph ^ 1u))) {
                 if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
                 return;
@@ -548,6 +549,7 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
             if (need) {
                 for (int i = 0; i < 4; ++i) sm.c[sl][i][lane] = J1[i];
                 for (int i = 0; i < 7; ++i) sm.c[sl][4 + i][lane] = K1[i];
+                sm.c[sl][11][lane] = Q(e1);
             }
             __syncwarp();
             pair_arrive(&sm.c_full[sl]);
@@ -584,18 +586,20 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
                 return;
             }
             Q J1[4], K1[7];
+            int e1 = 0;
             if (code == REC_INIT || moving) {
                 for (int i = 0; i < 4; ++i) J1[i] = sm.c[sl][i][lane];
                 for (int i = 0; i < 7; ++i) K1[i] = sm.c[sl][4 + i][lane];
+                e1 = sm.c[sl][11][lane] != Q(0);
             }
             __syncwarp();
             pair_arrive(&sm.c_empty[sl]);
             if (code == REC_INIT) {
-                xfer_init_with<Q, POL>(x, pt, J1, K1);
+                xfer_init_with<Q, POL>(x, pt, J1, K1, e1);
                 steps = 0;
             } else if (code != REC_IDLE) {
                 ++steps;
-                if (moving) xfer_apply<Q, POL>(x, pt, J1, K1, J);
+                if (moving) xfer_apply<Q, POL>(x, pt, J1, K1, J, e1);
                 if (code != RAY_GOING) finish_ray(A, code, steps, x, pix, slot);
             }
             if (last) {
@@ -609,8 +613,9 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
 // The single-image trace kernel.  The form follows the queue length (uniform over the grid): short
 // queues (the latency-bound regime of most levels) take the warp-quad (FP32) or warp-pair form, a
 // longer queue, where throughput counts, the one-thread form with the most rays in flight.  The
-// double-float kernel takes the pair form whenever its queue fits the grid's pairs; the FP64
-// kernel is always one-thread.
+// double-float and FP64 kernels take the pair form whenever their queue fits the grid's pairs
+// (GB300's FP64 pipe issues a warp instruction every 16 cycles, so an FP64 step is long even for
+// one warp per scheduler, and splitting it over two warps halves a launch's tail).
 template <class R, bool SWEEP, bool POL, int EM>
 __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
 {
@@ -622,10 +627,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
         for (int q = threadIdx.x; q < (int)(sizeof(Camera) / sizeof(double)); q += blockDim.x)
             dst[q] = src[q];
     }
-    if constexpr (std::is_same<R, double>::value) {
-        __syncthreads();
-        trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
-    } else {
+    {
         __shared__ __align__(16) PairRingOf<R, POL> ring;
         pair_ring_init(ring);
         if constexpr (std::is_same<R, float>::value) {

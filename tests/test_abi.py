@@ -83,6 +83,14 @@ def test_job_struct_matches_header():
         assert width[ctype] == pt, n
 
 
+def test_stats_struct_matches_header():
+    """art_stats in the binding has the header's fields, in order, with the same sizes."""
+    fields = _struct_fields("art_stats")
+    names = [n for n, _ in art.Stats._fields_]
+    assert names == [f[1].split("[")[0] for f in fields]
+    assert ctypes.sizeof(art.Stats) == 8 * (len(fields) + 15)  # rays_per_level holds 16
+
+
 def test_noalloc_rejects_grid_jobs_before_gpu_work():
     """A grid job has no context to hold its grid: the allocation-free call refuses it before
     touching any device state (checked on the host: an empty ray list, null pointers)."""
