@@ -45,41 +45,66 @@ FLOPS_PER_STEP_POL = {"trace_fp64": 3007, "trace_fp32": 3035, "trace_df": 3007}
 FLOPS_PER_STEP_GRID = {"trace_fp64": 999, "trace_fp32": 1027, "trace_df": 999}
 # Algorithmic bytes of one grid sample: 8 cells x 8 FP32 fields (before any cache reuse).
 GRID_BYTES_PER_SAMPLE = 256
-# Peaks for "alu"-bound kernels: FP32 = 152 SMs x 128 lanes x 2 flops x 2.07 GHz; FP64 = the
-# GB300's nominal dense FP64 rate.
+# Peaks for "alu"-bound kernels, derived from unit counts and the maximum clock: FP32 = 152 SMs x
+# 128 lanes x 2 flops x 2.07 GHz; FP64 = GB300's nominal dense FP64 rate.  The bench line's
+# fraction uses the measured FMA throughput of this GPU (art_measure_alu_peaks) and quotes these.
 PEAK_TFLOPS = {"trace_fp32": 152 * 128 * 2 * 2.07e9 / 1e12, "trace_fp64": 1.25,
                "trace_df": 152 * 128 * 2 * 2.07e9 / 1e12}
 PEAK_SOURCE = {"trace_fp32": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
                "trace_df": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (FP32 pipes)",
                "trace_fp64": "nominal GB300 dense FP64"}
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture of the
-# second of two renders (`bench.py --single [--workload grmhd_8193]` under
-# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:trace_kernel`), averaged over
-# that render's FP32-pass launches (5 for the 2049^2 polarized render, 6 for the 8193^2 grid
-# render).  Reset to None whenever the trace kernels change.
-TRAFFIC_PER_LAUNCH = {("kerr_disk_2049", "trace_fp32"): 437558.0,
-                      ("grmhd_8193", "trace_fp32"): 90996130.0}
-HBM_PEAK_GBPS = 6779.0  # measured STREAM-style copy bandwidth of a GB300, GB/s
-DTYPE = {"mixed": "f32+f64", "mixed_df": "f32+df32x2", "fp64": "f64", "fp32": "f32"}
+# HBM and BF16 denominators: the driver's measurement on this machine (MEASURED_PEAKS.json at the
+# repository root), else the pool's earlier measurement.
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        out = {k: float(d[k]) for k in FALLBACK_PEAKS}
+        out["source"] = "measured (MEASURED_PEAKS.json)"
+        return out
+    except (OSError, KeyError, ValueError):
+        return {**FALLBACK_PEAKS, "source": "fallback (no MEASURED_PEAKS.json)"}
+
+
+DTYPE = {"mixed": "f32+f64", "mixed_df": "f32+df32x2", "fp64": "f64", "fp32": "f32",
+         "mixed_exact": "f32+df32x2+f64"}
 METRIC = "rays/s"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=4)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="kerr_disk_2049", choices=sorted(W.BENCH_WORKLOADS))
-    ap.add_argument("--precision", default="mixed_df", choices=["mixed", "mixed_df", "fp64", "fp32"])
+    ap.add_argument("--workload", default="grmhd_16385", choices=sorted(W.BENCH_WORKLOADS))
+    ap.add_argument("--precision", default="mixed_exact",
+                    choices=["mixed", "mixed_df", "mixed_exact", "fp64", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-render measurement")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default kernel-form thresholds (skip the autotuner)")
     ap.add_argument("--no-mse", action="store_true",
-                    help="skip the time-to-0.1%%-MSE sweep (needs a full FP64 trace as truth)")
+                    help="skip the time-to-0.1%%-MSE measurement")
+    ap.add_argument("--fp64-truth", action="store_true",
+                    help="time to 0.1%%-MSE against a full FP64 trace (minutes at 16385^2) "
+                         "instead of the full mixed-precision trace")
+    ap.add_argument("--heldout", type=int, default=5,
+                    help="held-out seeds of the time-to-0.1%%-MSE measurement")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip training the block-proposal network and the learned path")
+    ap.add_argument("--learn-jobs", type=int, default=2000,
+                    help="seeded plain renders whose masks train the proposal network")
+    ap.add_argument("--learn-epochs", type=int, default=2)
+    ap.add_argument("--no-vis", action="store_true",
+                    help="skip the visibility spectra of the 8193^2 grid workload")
+    ap.add_argument("--contours", action="store_true",
+                    help="IF / FE / MSE of the 8193^2 grid workload over a (R_rel, R_abs) log "
+                         "grid (the paper's tolerance study), nothing else")
     ap.add_argument("--single", action="store_true",
                     help="one warm-up and one render, nothing else (for profiler captures)")
     ap.add_argument("--batch-only", action="store_true",
@@ -162,39 +187,46 @@ def _sampled_on_cpu(params: dict) -> bool:
     return params.get("stokes", 1) == 4 or params.get("emission") == "grid"
 
 
-def cpu_baseline(params: dict, snap=None):
-    """The FP64 oracle on the host cores.  Unpolarized analytic workloads: one full adaptive
-    render.  Polarized and grid ones: the whole base level of the workload."""
+def cpu_baseline(params: dict, snap=None, reps: int = 3):
+    """The FP64 oracle on the host cores, median of `reps` runs.  Unpolarized analytic
+    workloads: one full adaptive render.  Polarized and grid ones: a bounded sample of the
+    workload's base level (every 4th base ray: a few seconds per run)."""
     import oracle as O
     job = O.make_job(grid=snap, **params)
+    runs = []
     if _sampled_on_cpu(params):
-        pix = _base_pixels(params)
-        t0 = time.perf_counter()
-        _, info = O.trace_pixels(job, pix)
-        dt = time.perf_counter() - t0
-        rays, steps = pix.size, int(info["steps"].sum())
-        note = f"the {params['n0x']}x{params['n0y']} base level of the workload ({rays} rays)"
+        pix = _base_pixels(params)[::4]
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            _, info = O.trace_pixels(job, pix)
+            runs.append((time.perf_counter() - t0, pix.size, int(info["steps"].sum())))
+        note = (f"every 4th ray of the {params['n0x']}x{params['n0y']} base level of the workload "
+                f"({pix.size} rays)")
     else:
-        t0 = time.perf_counter()
-        img, mask, st = O.render(job, None)
-        dt = time.perf_counter() - t0
-        rays, steps = int(st["rays_traced"]), int(st["steps"])
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            img, mask, st = O.render(job, None)
+            runs.append((time.perf_counter() - t0, int(st["rays_traced"]), int(st["steps"])))
         note = "one full adaptive render of the workload"
+    dt, rays, steps = sorted(runs)[len(runs) // 2]
     cores = O.get_threads()
-    # one core: every 16th base-level ray (a bounded sample of a few seconds)
-    pix1 = _base_pixels(params)[::16]
+    # one core: every 64th base-level ray (a bounded sample of a few seconds), median of reps
+    pix1 = _base_pixels(params)[::64]
     O.set_threads(1)
+    t1 = []
     try:
-        t0 = time.perf_counter()
-        O.trace_pixels(job, pix1)
-        dt1 = time.perf_counter() - t0
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            O.trace_pixels(job, pix1)
+            t1.append(time.perf_counter() - t0)
     finally:
         O.set_threads(cores)
+    dt1 = statistics.median(t1)
     return {"value": rays / dt, "unit": "rays/s", "cores": cores, "kind": "oracle",
-            "sample": note + " by the FP64 oracle (OpenMP over rays, all host cores)",
+            "sample": note + f" by the FP64 oracle (OpenMP over rays, all host cores), median of {reps}",
             "seconds": dt, "rays": rays, "steps_per_s": steps / dt,
             "single_core": {"value": pix1.size / dt1, "unit": "rays/s", "cores": 1,
-                            "sample": f"every 16th base-level ray ({pix1.size} rays)",
+                            "sample": f"every 64th base-level ray ({pix1.size} rays), median of {reps}",
                             "seconds": dt1}}
 
 
@@ -215,42 +247,94 @@ def whole_job_value(rays_per_step: int, steps: int, world: int, t_max: float) ->
     return rays_per_step * steps * world / t_max
 
 
-def accuracy(ctx, params: dict, img, mask):
-    """The render against the FP64 path on the same workload, per plane (Stokes parameter, or
-    subring n for unpolarized subring images): the BJ error sum (dI)^2 / (N mean(I)^2) of the
-    whole adaptive image against the FP64 adaptive render, the part of it on points whose mask
-    differs (the criterion decided them differently because its inputs differ by rounding; one
-    render traced the point, the other interpolated it), and the per-ray error over every traced
-    ray against the FP64 trace of the same ray."""
+def flip_distances(params: dict, ref_plane, mask_ref, mask, norm: float, cap: int = 2000):
+    """For every point whose mask differs from the FP64 render's (at most `cap` of them): the
+    relative distance of the FP64 render's decision from flipping, from the oracle's estimates
+    (Eqs. epabs, eprel) on the FP64 image's level lattice around the point."""
+    import numpy as np
+    import oracle as O
+    m0, m1 = mask_ref.cpu().numpy(), mask.cpu().numpy()
+    jj, ii = np.nonzero(m0 != m1)
+    N = params["levels"]
+    img = None
+    out = []
+    for i, j in list(zip(ii, jj))[:cap]:
+        if img is None:
+            img = ref_plane.cpu().numpy()
+        k = N
+        while k > 0 and i % (1 << (N - k + 1)) == 0 and j % (1 << (N - k + 1)) == 0:
+            k -= 1
+        s = 1 << (N - k)
+        # a window of the level-k lattice around the point (the stencil reaches 3 lattice steps)
+        li, lj = i // s, j // s
+        L = img[::s, ::s]
+        x0, y0 = max(0, (li - 8) & ~1), max(0, (lj - 8) & ~1)
+        x1, y1 = min(L.shape[1], li + 9), min(L.shape[0], lj + 9)
+        win = np.ascontiguousarray(L[y0:y1, x0:x1])
+        # keep the image's own edges where the window meets them (the edge rule depends on it)
+        if x0 > 0 or y0 > 0 or x1 < L.shape[1] or y1 < L.shape[0]:
+            if (win.shape[1] - 1) % 2 or (win.shape[0] - 1) % 2:
+                win = win[: win.shape[0] - ((win.shape[0] - 1) % 2), : win.shape[1] - ((win.shape[1] - 1) % 2)]
+        ny, nx = win.shape
+        job = O.make_job(**W.job(n0x=(nx - 1) // 2 + 1, n0y=(ny - 1) // 2 + 1, levels=1,
+                                 R_abs=params["R_abs"], R_rel=params["R_rel"],
+                                 interp=params.get("interp", "linear"),
+                                 edge_mode=params.get("edge_mode", "onesided")))
+        m = np.zeros(win.shape, np.uint8)
+        m[::2, ::2] = O.MASK_TRACED
+        _, _, ea, er = O.refine_level(job, win, m, 1, norm)
+        a = ea[lj - y0, li - x0] / params["R_abs"] - 1.0
+        r = er[lj - y0, li - x0] / params["R_rel"] - 1.0
+        if a > 0 and r > 0:
+            out.append(float(min(a, r)))
+        elif a <= 0 and r <= 0:
+            out.append(float(max(-a, -r)))
+        else:
+            out.append(float(-a if a <= 0 else -r))
+    return out
+
+
+def accuracy(params: dict, img, mask, ref, rmask, rnorm, ctx=None):
+    """The render against the FP64 render of the same workload, per plane (Stokes parameter, or
+    subring n): the error sum (dI)^2 / (N Ibar^2) of the whole adaptive image (Ibar the mean
+    total intensity of the FP64 render), the part of it on points whose mask differs, the number
+    of such points and the FP64 estimate's distance from its tolerance at each (the criterion
+    decided them differently because its inputs differ by rounding), and, when a context is
+    given, the per-ray error over every traced ray against the FP64 trace of the same ray."""
     import torch
     from paper_2103_07417_gb300 import art
-    if params.get("precision") == "fp64":
-        return None
-    job64 = art.make_job(**{**params, "precision": "fp64"})
-    ref, rmask, _ = ctx.render(job64)
     planes = img.shape[0]
-    m0 = float(ref[0].double().mean())
+    stokes, subr = params.get("stokes", 1), params.get("subrings", 0)
+    tot = sum(ref[n * stokes] for n in range(max(subr, 1)))
+    m0 = float(tot.double().mean())
     n = img[0].numel()
     d2 = (img - ref).double() ** 2
     flip = mask != rmask
     whole = [float(d2[c].sum()) / (n * m0 * m0) for c in range(planes)]
     on_flips = [float(d2[c][flip].sum()) / (n * m0 * m0) for c in range(planes)]
-    pix = torch.nonzero(mask.reshape(-1) == art.MASK_TRACED).reshape(-1).to(torch.int32)
-    out = torch.empty((pix.numel(), planes), dtype=torch.float64, device=img.device)
-    ctx.art_trace_pixels(job64, pix, out)
-    got = img.reshape(planes, -1)[:, pix.long()].T
-    mr = float(out[:, 0].mean())
-    per_ray = [float(((got[:, c] - out[:, c]) ** 2).sum()) / (pix.numel() * mr * mr)
-               for c in range(planes)]
-    if params.get("stokes", 1) == 4:
-        names = [f"{'IQUV'[c % 4]}" + (f"_n{c // 4}" if params.get("subrings", 0) else "")
-                 for c in range(planes)]
+    nflip = int(flip.sum())
+    dist = flip_distances(params, ref[0], rmask, mask, rnorm) if nflip else []
+    per_ray = None
+    if ctx is not None:
+        job64 = art.make_job(**{**params, "precision": "fp64"})
+        pix = torch.nonzero(mask.reshape(-1) == art.MASK_TRACED).reshape(-1).to(torch.int32)
+        out = torch.empty((pix.numel(), planes), dtype=torch.float64, device=img.device)
+        ctx.art_trace_pixels(job64, pix, out)
+        got = img.reshape(planes, -1)[:, pix.long()].T
+        per_ray = [float(((got[:, c] - out[:, c]) ** 2).sum()) / (pix.numel() * m0 * m0)
+                   for c in range(planes)]
+        del out, got
+    if stokes == 4:
+        names = [f"{'IQUV'[c % 4]}" + (f"_n{c // 4}" if subr else "") for c in range(planes)]
     else:
-        names = [f"I_n{c}" if params.get("subrings", 0) else "I" for c in range(planes)]
-    del ref, rmask, d2, out, got
-    return {"against": "the FP64 path on the same workload (equal to the FP64 oracle to 1e-6)",
+        names = [f"I_n{c}" if subr else "I" for c in range(planes)]
+    del d2
+    return {"against": "the FP64 render of the same workload (equal to the FP64 oracle to 1e-6)",
             "planes": names, "image_bj": whole, "image_bj_on_mask_flips": on_flips,
-            "mask_flips": int(flip.sum()), "traced_rays": int(pix.numel()),
+            "mask_flips": nflip,
+            "flips_fp64_estimate_distance": {"max": max(dist) if dist else None,
+                                             "within_1e-9": sum(1 for x in dist if x <= 1e-9),
+                                             "measured": len(dist)},
             "per_ray_bj": per_ray}
 
 
@@ -298,6 +382,241 @@ def run_reference(args, params, desc):
     print(json.dumps(line), flush=True)
 
 
+def _roofline(ctx, recs, params, peaks):
+    """Per-kind split of one render's launches and the roofline of its dominant trace kernel
+    (CUDA events on the library's stream): algorithmic FLOPs per RK4 step (counted from the
+    kernel's formulas) x the steps the kernel's launches executed, over their summed durations."""
+    by_kind = {}
+    for r in recs:
+        d = by_kind.setdefault(r["kind"], {"launches": 0, "ms": 0.0, "steps": 0})
+        d["launches"] += 1
+        d["ms"] += r["ms"]
+        d["steps"] += r["steps"]
+    total_ms = sum(v["ms"] for v in by_kind.values())
+    grid_em = params.get("emission") == "grid"
+    fps = (FLOPS_PER_STEP_POL if params.get("stokes", 1) == 4
+           else FLOPS_PER_STEP_GRID if grid_em else FLOPS_PER_STEP)
+    traces = [k for k in by_kind if k in fps]
+    dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
+    meas = ctx.art_measure_alu_peaks()
+    out = {}
+    for k in traces:
+        d = by_kind[k]
+        if d["ms"] <= 0:
+            continue
+        achieved = d["steps"] * fps[k] / (d["ms"] / 1000.0) / 1e12
+        mp = meas["fp64_tflops"] if k == "trace_fp64" else meas["fp32_tflops"]
+        rec = {"bound": "alu", "kernel": k, "achieved": achieved, "peak": mp, "unit": "TFLOP/s",
+               "frac": achieved / mp if mp > 0 else None, "traffic": None,
+               "peak_source": "measured: art_measure_alu_peaks (FMA chains on every SM, this GPU)",
+               "peak_derived": PEAK_TFLOPS[k], "peak_derived_source": PEAK_SOURCE[k],
+               "frac_of_derived": achieved / PEAK_TFLOPS[k],
+               "flops_per_step": fps[k], "launches": d["launches"], "steps": d["steps"],
+               "share_of_step": d["ms"] / total_ms}
+        if grid_em:
+            # every RK4 step samples the grid once
+            gbs = d["steps"] * GRID_BYTES_PER_SAMPLE / (d["ms"] / 1000.0) / 1e9
+            rec["grid_lookup"] = {
+                "bytes_per_sample": GRID_BYTES_PER_SAMPLE, "samples": d["steps"],
+                "achieved_GBps": gbs, "hbm_peak_GBps": peaks["hbm_gbs"],
+                "frac_of_hbm": gbs / peaks["hbm_gbs"], "hbm_peak_source": peaks["source"],
+                "note": "algorithmic bytes (8 cells x 32 B per sample) over the kernel time; most "
+                        "are served from L1/L2 (neighbouring samples share cells)"}
+        out[k] = rec
+    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                   "share": round(v["ms"] / total_ms, 4)} for k, v in by_kind.items()}
+    main_k = dom if dom in out else (max(out, key=lambda k: out[k]["share_of_step"]) if out else None)
+    return (out.get(main_k) if main_k else None), out, kernels
+
+
+def _fe(metrics):
+    return metrics.get("FE")
+
+
+def time_to_mse(args, params, ctx, lctx, learned, img, mask, flush, dev):
+    """Wall time to an image with the paper's MSE <= 1e-3 against a full trace of the final grid
+    (Eq. msedef), per path: on the calibration seed (the workload itself) the fastest
+    (R_rel, R_abs) of a log grid meeting the target, then that setting's time and MSE on held-out
+    seeds (new snapshots of the grid model; analytic workloads are deterministic and have none)."""
+    import numpy as np
+    import torch
+    from paper_2103_07417_gb300 import art
+    grid_em = params.get("emission") == "grid"
+    R0r, R0a = params["R_rel"], params["R_abs"]
+    # the paper's tolerances scaled down (tighter) and up: MSE depends mostly on R_rel here
+    fr = [1e-3, 1e-2, 3e-2, 0.1, 0.3, 1.0, 3.0]
+    fa = [0.01, 0.1, 1.0]
+    truth_prec = "fp64" if args.fp64_truth else "mixed_df"
+
+    def truth_of(cx):
+        tj = art.make_job(**{**params, "precision": truth_prec, "R_rel": -1.0, "R_abs": -1.0,
+                             "crit_band": 0.0, "proposal": 0})
+        t = torch.empty_like(img)
+        cx.art_render(tj, t, mask, stats=False)
+        return t
+
+    variants = [("fp64", ctx, {"precision": "fp64", "crit_band": 0.0}),
+                ("mixed_df", ctx, {"precision": "mixed_df"}),
+                ("mixed_exact", ctx, {"precision": "mixed_exact"})]
+    if lctx is not None and learned is not None:
+        lb = learned["best"]
+        lover = {"proposal": 1, "proposal_p": lb["threshold"], "proposal_depth": lb["depth"],
+                 "crit_band": lb["crit_band"]}
+        variants.append(("mixed_df+learned", lctx, {"precision": "mixed_df", **lover}))
+        variants.append(("mixed_exact+learned", lctx, {"precision": "mixed_exact", **lover}))
+    out = {"target_mse": 1e-3, "truth": f"full {truth_prec} trace of the final grid (R = -1)",
+           "grid": {"R_rel": [R0r * f for f in fr], "R_abs": [R0a * f for f in fa]},
+           "calibration": "the workload itself (snapshot seed 0 for grid models)", "paths": {}}
+    truth = truth_of(ctx)
+    ltruth = truth if lctx is None else None
+    sweeps = {}
+    for name, cx, over in variants:
+        if cx is not ctx and ltruth is None:
+            ltruth = truth_of(cx)
+        tr = truth if cx is ctx else ltruth
+        rec, sweep = None, []
+        for f1 in fr:
+            for f2 in fa:
+                vj = art.make_job(**{**params, **over, "R_rel": R0r * f1, "R_abs": R0a * f2})
+                vst = cx.art_render(vj, img, mask, stats=True)
+                met = cx.art_metrics(tr[0], img[0], mask)
+                ok = met["MSE"] <= 1e-3
+                tv = _timed_ctx(cx, vj, img, mask, flush, 3) if ok else None
+                sweep.append({"R_rel": R0r * f1, "R_abs": R0a * f2, "mse": met["MSE"],
+                              "IF": met["IF"], "FE": met["FE"], "seconds": tv,
+                              "rays": vst["rays_traced"]})
+                if ok and (rec is None or tv < rec["seconds"]):
+                    rec = {"seconds": tv, "R_rel": R0r * f1, "R_abs": R0a * f2, "mse": met["MSE"],
+                           "rays": vst["rays_traced"]}
+        mses = [x["mse"] for x in sweep]
+        out["paths"][name] = {"calibration": rec,
+                              "bracketed": bool(min(mses) <= 1e-3 < max(mses)),
+                              "sweep": sweep}
+        sweeps[name] = rec
+    del truth, ltruth
+    # held-out seeds: the calibrated setting of every path on new snapshots
+    if grid_em and args.heldout > 0:
+        held = {name: [] for name, _, _ in variants}
+        for seed in range(1, 1 + args.heldout):
+            snap = W.grmhd_snapshot(seed=seed)
+            ctx.load_grid(snap)
+            if lctx is not None:
+                lctx.load_grid(snap)
+            truth = truth_of(ctx)
+            for name, cx, over in variants:
+                rec = sweeps[name]
+                if rec is None:
+                    continue
+                vj = art.make_job(**{**params, **over, "R_rel": rec["R_rel"], "R_abs": rec["R_abs"]})
+                cx.art_render(vj, img, mask, stats=False)
+                met = cx.art_metrics(truth[0], img[0], mask)
+                tv = _timed_ctx(cx, vj, img, mask, flush, 3)
+                held[name].append({"seed": seed, "seconds": tv, "mse": met["MSE"]})
+            del truth
+        snap0 = W.grmhd_snapshot(seed=0)
+        ctx.load_grid(snap0)
+        if lctx is not None:
+            lctx.load_grid(snap0)
+        for name, h in held.items():
+            if h:
+                out["paths"][name]["heldout"] = {
+                    "seeds": [x["seed"] for x in h], "mean_seconds": float(np.mean([x["seconds"] for x in h])),
+                    "max_mse": float(max(x["mse"] for x in h)), "runs": h}
+    base = out["paths"]["fp64"].get("heldout", {}).get("mean_seconds") or \
+        (out["paths"]["fp64"]["calibration"] or {}).get("seconds")
+    for name in out["paths"]:
+        t = out["paths"][name].get("heldout", {}).get("mean_seconds") or \
+            (out["paths"][name]["calibration"] or {}).get("seconds")
+        out["paths"][name]["speedup_vs_fp64"] = (base / t) if (base and t) else None
+    return out
+
+
+def contours(args, ctx, flush):
+    """The paper's tolerance study (Sec. 4.1) on the 8193^2 grid workload: IF, FE and MSE against
+    the full trace over a log grid of (R_rel, R_abs), for the FP64 decisions' mixed path."""
+    import torch
+    from paper_2103_07417_gb300 import art
+    params = W.grmhd_8193(precision="mixed_exact")
+    ctx.load_grid(W.grmhd_snapshot(seed=0))
+    job = art.make_job(**params)
+    nx, ny = art.art_image_size(job)
+    img = torch.empty((1, ny, nx), dtype=torch.float64, device="cuda")
+    mask = torch.empty((ny, nx), dtype=torch.uint8, device="cuda")
+    tj = art.make_job(**{**params, "precision": "mixed_df", "R_rel": -1.0, "R_abs": -1.0,
+                         "crit_band": 0.0})
+    truth = torch.empty_like(img)
+    ctx.art_render(tj, truth, mask, stats=False)
+    rows = []
+    for rr in (1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1):
+        for ra in (1e-3, 3e-3, 1e-2, 2.5e-2, 1e-1, 3e-1, 1.0):
+            j = art.make_job(**{**params, "R_rel": rr, "R_abs": ra})
+            st = ctx.art_render(j, img, mask, stats=True)
+            met = ctx.art_metrics(truth[0], img[0], mask)
+            rows.append({"R_rel": rr, "R_abs": ra, "IF": met["IF"], "FE": met["FE"],
+                         "MSE": met["MSE"], "rays": st["rays_traced"]})
+    print(json.dumps({"contours": "grmhd_8193", "precision": "mixed_exact",
+                      "truth": "full mixed_df trace", "rows": rows}), flush=True)
+
+
+# Angular size of GM/c^2 of the M87*-mass hole the synthetic models are scaled to (length unit
+# 9.6e14 cm at 16.8 Mpc), to express baselines in G-lambda as the paper does.
+THETA_M_RAD = 9.6e14 / (16.8 * 3.0857e24)
+
+
+def visibility_spectra(ctx, flush):
+    """Sec. 4.3 on the 8193^2 grid workload: the image is rendered with the field of view and
+    pixel count doubled (same resolution), adaptively (exact decisions) and fully traced, then
+    tapered by a Gaussian of FWHM FOV/4 (the original FOV) and transformed; |V| and the residual
+    |dV| (adaptive minus full) along the u and v axes, out to 1000 G-lambda."""
+    import numpy as np
+    import torch
+    from paper_2103_07417_gb300 import art
+    base = W.grmhd_8193(precision="mixed_exact")
+    ctx.load_grid(W.grmhd_snapshot(seed=0))
+    p2 = W.doubled_fov(base)
+    job = art.make_job(**p2)
+    nx, ny = art.art_image_size(job)
+    img = torch.empty((1, ny, nx), dtype=torch.float64, device="cuda")
+    mask = torch.empty((ny, nx), dtype=torch.uint8, device="cuda")
+    st = ctx.art_render(job, img, mask, stats=True)
+    full = torch.empty_like(img)
+    ctx.art_render(art.make_job(**{**p2, "precision": "mixed_df", "R_rel": -1.0, "R_abs": -1.0,
+                                   "crit_band": 0.0}), full, mask, stats=False)
+    dx = p2["fov"] / (nx - 1)
+    m = 1
+    while m < nx:
+        m *= 2
+    fwhm = base["fov"] / 4.0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    v = ctx.art_visibilities(img[0], dx, fwhm, m)
+    torch.cuda.synchronize()
+    t_vis = time.perf_counter() - t0
+    vu, vv = v[0, :].abs().cpu().numpy(), v[:, 0].abs().cpu().numpy()
+    del v
+    torch.cuda.empty_cache()
+    dv = ctx.art_visibilities(img[0], dx, fwhm, m, ref=full[0])
+    du, dvv = dv[0, :].abs().cpu().numpy(), dv[:, 0].abs().cpu().numpy()
+    del dv, img, full, mask
+    torch.cuda.empty_cache()
+    u = np.arange(m // 2) / (m * dx)                       # cycles per M
+    glam = u / THETA_M_RAD / 1e9
+    keep = (glam > 0) & (glam <= 1000.0)
+    idx = np.unique(np.geomspace(1, keep.sum(), 48).astype(int))
+    sel = np.nonzero(keep)[0][idx - 1]
+    v0 = float(vu[0])
+    frac_u = float(np.max(du[keep] / np.maximum(vu[keep], 1e-300)))
+    frac_v = float(np.max(dvv[keep] / np.maximum(vv[keep], 1e-300)))
+    return {"workload": "grmhd_8193 with FOV and pixels doubled (320 M, 16385^2), mixed_exact; "
+                        "residual against the full mixed_df trace",
+            "fft": f"{m}x{m} FP64", "seconds_per_transform": t_vis, "taper_fwhm_M": fwhm,
+            "rays": st["rays_traced"], "V0": v0,
+            "baseline_Glambda": glam[sel].tolist(),
+            "amp_u": (vu[sel] / v0).tolist(), "amp_v": (vv[sel] / v0).tolist(),
+            "resid_u": (du[sel] / v0).tolist(), "resid_v": (dvv[sel] / v0).tolist(),
+            "max_resid_over_amp_u": frac_u, "max_resid_over_amp_v": frac_v}
+
+
 def main():
     args = parse()
     desc, fn = W.BENCH_WORKLOADS[args.workload]
@@ -305,6 +624,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, params, desc)
 
+    import numpy as np
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -316,10 +636,16 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    peaks = measured_peaks()
 
     from paper_2103_07417_gb300 import art
     ctx = art.Context(local)
     stream = ctx.stream
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    if args.contours:
+        contours(args, ctx, flush)
+        ctx.close()
+        return
     snap = None
     if params.get("emission") == "grid":
         # the seeded snapshot, resident on the device before timing (151 MB of FP32)
@@ -330,7 +656,6 @@ def main():
     planes = art.art_planes(job)
     img = torch.empty((planes, ny, nx), dtype=torch.float64, device=dev)
     mask = torch.empty((ny, nx), dtype=torch.uint8, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     stats = None
     if args.cnn:
@@ -397,72 +722,40 @@ def main():
     ctx.art_render(job, img, mask, stats=False)
     recs = ctx.art_profile_read()
     ctx.art_profile(False)
-    by_kind = {}
-    for r in recs:
-        d = by_kind.setdefault(r["kind"], {"launches": 0, "ms": 0.0, "steps": 0})
-        d["launches"] += 1
-        d["ms"] += r["ms"]
-        d["steps"] += r["steps"]
-    dom = max(by_kind, key=lambda k: by_kind[k]["ms"])
-    total_ms = sum(v["ms"] for v in by_kind.values())
-    roofline = None
-    grid_em = params.get("emission") == "grid"
-    fps = (FLOPS_PER_STEP_POL if params.get("stokes", 1) == 4
-           else FLOPS_PER_STEP_GRID if grid_em else FLOPS_PER_STEP)
-    if dom in fps:
-        d = by_kind[dom]
-        achieved = d["steps"] * fps[dom] / (d["ms"] / 1000.0) / 1e12
-        peak = PEAK_TFLOPS[dom]
-        roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, dom)),
-                    "traffic_unit": "bytes per launch (ncu, cold cache)",
-                    "peak_source": PEAK_SOURCE[dom],
-                    "launches": d["launches"], "steps": d["steps"],
-                    "share_of_step": d["ms"] / total_ms}
-        # the same against this GPU's measured fused multiply-add throughput (own microbenchmark)
-        meas = ctx.art_measure_alu_peaks()
-        mp = meas["fp64_tflops"] if dom == "trace_fp64" else meas["fp32_tflops"]
-        roofline["peak_measured"] = {**meas, "frac": achieved / mp if mp > 0 else None,
-                                     "source": "art_measure_alu_peaks: FMA chains on every SM"}
-        if grid_em:
-            # every RK4 step samples the grid once (the start point of a ray once more)
-            gbs = d["steps"] * GRID_BYTES_PER_SAMPLE / (d["ms"] / 1000.0) / 1e9
-            roofline["grid_lookup"] = {
-                "bytes_per_sample": GRID_BYTES_PER_SAMPLE, "samples": d["steps"],
-                "achieved_GBps": gbs, "hbm_peak_GBps": HBM_PEAK_GBPS, "frac_of_hbm": gbs / HBM_PEAK_GBPS,
-                "note": "algorithmic bytes (8 cells x 32 B per sample) over the kernel time; most "
-                        "are served from L1/L2 (neighbouring samples share cells), so DRAM "
-                        "traffic is far lower"}
-    kernels = {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
-                   "share": round(v["ms"] / total_ms, 4)} for k, v in by_kind.items()}
+    roofline, roofline_all, kernels = _roofline(ctx, recs, params, peaks)
 
     # the other precision paths on the same workload, for comparison
     paths = {}
-    for prec in ("fp64", "mixed", "mixed_df"):
+    for prec in ("fp64", "mixed_df", "mixed_exact", "mixed"):
         if prec == args.precision:
             continue
         jobp = art.make_job(**{**params, "precision": prec})
         stp = ctx.art_render(jobp, img, mask, stats=True)
-        kp = max(3, args.steps // 5)
+        kp = 3
         tp = timed(kp, jobp)
         paths[prec] = {"rays_per_s": stp["rays_traced"] * kp / tp,
                        "geodesic_steps_per_s": stp["steps"] * kp / tp,
-                       "ms_per_step": 1000 * tp / kp, "rays_high_precision": stp["rays_fp64"]}
+                       "ms_per_step": 1000 * tp / kp, "rays_high_precision": stp["rays_fp64"],
+                       "rays_exact": stp["rays_exact"]}
+        if prec == "mixed_df":
+            ctx.art_profile(True)
+            ctx.art_render(jobp, img, mask, stats=False)
+            r2 = ctx.art_profile_read()
+            ctx.art_profile(False)
+            paths[prec]["roofline"], _, paths[prec]["kernels"] = _roofline(ctx, r2, params, peaks)
     if params.get("crit_band", 0.0) > 0.0:
         # the same precision without the near-critical band speculation (same image)
         jnb = art.make_job(**{**params, "crit_band": 0.0})
         stp = ctx.art_render(jnb, img, mask, stats=True)
-        kp = max(3, args.steps // 5)
-        tp = timed(kp, jnb)
+        tp = timed(3, jnb)
         paths[args.precision + "_no_band"] = {
-            "rays_per_s": stp["rays_traced"] * kp / tp,
-            "geodesic_steps_per_s": stp["steps"] * kp / tp, "ms_per_step": 1000 * tp / kp,
+            "rays_per_s": stp["rays_traced"] * 3 / tp,
+            "geodesic_steps_per_s": stp["steps"] * 3 / tp, "ms_per_step": 1000 * tp / 3,
             "rays_high_precision": stp["rays_fp64"]}
     # the same render replayed from a CUDA graph (one capture of the whole level loop)
     if not params.get("proposal", 0):
         ctx.art_graph_render(job, img, mask)
-        kp = max(3, args.steps // 5)
+        kp = 3
         evs = []
         for _ in range(kp):
             flush.fill_(1.0)
@@ -477,19 +770,33 @@ def main():
                                             "geodesic_steps_per_s": steps_per_render * kp / tg,
                                             "ms_per_step": 1000 * tg / kp,
                                             "rays_high_precision": stats["rays_fp64"]}
-    ctx.art_render(job, img, mask, stats=False)
-    acc = accuracy(ctx, params, img, mask)
     paths[args.precision] = {"rays_per_s": value / world,
                              "geodesic_steps_per_s": steps_per_render * args.steps / t_dev,
                              "ms_per_step": 1000 * t_dev / args.steps,
-                             "rays_high_precision": stats["rays_fp64"]}
+                             "rays_high_precision": stats["rays_fp64"],
+                             "rays_exact": stats["rays_exact"],
+                             "border_points": stats["border_points"]}
+
+    # accuracy of the measured path (and of the other mixed path) against the FP64 render
+    acc = None
+    if args.precision != "fp64":
+        ref = torch.empty_like(img)
+        rmask = torch.empty_like(mask)
+        rst = ctx.art_render(art.make_job(**{**params, "precision": "fp64"}), ref, rmask, stats=True)
+        ctx.art_render(job, img, mask, stats=False)
+        acc = {args.precision: accuracy(params, img, mask, ref, rmask, rst["norm"], ctx)}
+        for other in ("mixed_df", "mixed_exact"):
+            if other != args.precision:
+                ctx.art_render(art.make_job(**{**params, "precision": other}), img, mask, stats=False)
+                acc[other] = accuracy(params, img, mask, ref, rmask, rst["norm"], None)
+        del ref, rmask
+        ctx.art_render(job, img, mask, stats=False)
 
     # end to end through the public C-ABI with host buffers (D2H of image + mask inside)
-    import numpy as np
     himg = torch.empty((planes, ny, nx), dtype=torch.float64).pin_memory().numpy()
     hmask = torch.empty((ny, nx), dtype=torch.uint8).pin_memory().numpy()
     ctx.art_render_host(job, himg, hmask)
-    ke = max(3, args.steps // 3)
+    ke = 5
     hgrid = None
     if snap is not None:
         # a new snapshot per frame: its upload from pinned host memory is inside the timed loop
@@ -505,6 +812,7 @@ def main():
     e2e = {"value": rays * ke / te, "unit": "rays/s",
            "h2d_bytes_per_step": int(ctypes_sizeof_job()) + (int(hgrid.nbytes) if hgrid is not None else 0),
            "d2h_bytes_per_step": int(himg.nbytes + hmask.nbytes)}
+    del himg, hmask
     if snap is not None:
         ctx.load_grid(snap)
 
@@ -524,28 +832,25 @@ def main():
         bst = ctx.art_render_batch(bjobs, bimgs, bmasks, stats=True)
         brays = sum(x["rays_traced"] for x in bst)
         bpix = sum(int(m.numel()) for m in bmasks)
-        evs = []
-        for _ in range(3):
-            flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.art_render_batch(bjobs, bimgs, bmasks, stats=False)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        tb = sum(a.elapsed_time(b) for a, b in evs) / 1000.0 / len(evs)
-        # the same batch replayed from a CUDA graph (captured on the first call)
+
+        def tbatch(jobs, graph=False):
+            evs = []
+            for _ in range(3):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if graph:
+                    ctx.art_graph_render_batch(jobs, bimgs, bmasks)
+                else:
+                    ctx.art_render_batch(jobs, bimgs, bmasks, stats=False)
+                e1.record(stream)
+                evs.append((e0, e1))
+            torch.cuda.synchronize()
+            return sum(a.elapsed_time(b) for a, b in evs) / 1000.0 / len(evs)
+
+        tb = tbatch(bjobs)
         ctx.art_graph_render_batch(bjobs, bimgs, bmasks)
-        evs = []
-        for _ in range(3):
-            flush.fill_(1.0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            ctx.art_graph_render_batch(bjobs, bimgs, bmasks)
-            e1.record(stream)
-            evs.append((e0, e1))
-        torch.cuda.synchronize()
-        tg = sum(a.elapsed_time(b) for a, b in evs) / 1000.0 / len(evs)
+        tg = tbatch(bjobs, graph=True)
         batched = {"workload": "256 images (mixed-parameter batch): a~U[-0.94,0.94], i~U[10,170] deg, "
                                "FOV log-U[40,400] M, 65^2..513^2 over 2-6 levels, emission from "
                                "the GRMHD-like snapshot (288x128x128 grid), subrings n=0,1,2, "
@@ -556,29 +861,40 @@ def main():
                    "geodesic_steps_per_s": bst[0]["steps"] / tb,
                    "rays_speculative": bst[0]["rays_speculative"],
                    "rays_spec_used": bst[0]["rays_spec_used"]}
-        # per-launch split of one batched render (CUDA events on the library's stream)
         ctx.art_profile(True)
         ctx.art_render_batch(bjobs, bimgs, bmasks, stats=False)
         brecs = ctx.art_profile_read()
         ctx.art_profile(False)
         batched["launches"] = [{"kind": r["kind"], "level": r["level"], "ms": round(r["ms"], 4),
                                 "steps": r["steps"]} for r in brecs]
-        # per-image error against the FP64 batch, per subring plane
+        # per-image error against the FP64 batch, per subring plane, for the batched mixed_df
+        # render and for exact decisions (images rendered one by one)
         rjobs = [art.make_job(**{**p, "precision": "fp64"}) for p in bparams]
-        rimgs, rmasks, _ = ctx.render_batch(rjobs)
-        per = []
-        flips = 0
-        for a, b, ma, mb in zip(bimgs, rimgs, bmasks, rmasks):
-            m0 = float(b.sum(0).double().mean())
-            n = a[0].numel()
-            per.append([float(((a[c] - b[c]).double() ** 2).sum()) / (n * m0 * m0)
-                        for c in range(a.shape[0])])
-            flips += int((ma != mb).sum())
-        per = np.array(per)
-        batched["accuracy"] = {
-            "against": "the FP64 batch", "planes": [f"I_n{c}" for c in range(per.shape[1])],
-            "image_bj_median": np.median(per, 0).tolist(), "image_bj_max": per.max(0).tolist(),
-            "images_above_1e-5": int((per.sum(1) > 1e-5).sum()), "mask_flips": flips}
+        rimgs, rmasks, rst = ctx.render_batch(rjobs)
+
+        def per_image(imgs_, masks_):
+            per, flips, dmax = [], 0, 0.0
+            for p, a, b, ma, mb, s in zip(bparams, imgs_, rimgs, rmasks, masks_, rst):
+                m0 = float(b.sum(0).double().mean())
+                n = a[0].numel()
+                per.append([float(((a[c] - b[c]).double() ** 2).sum()) / (n * m0 * m0)
+                            for c in range(a.shape[0])])
+                if not torch.equal(ma, mb):
+                    fl = int((ma != mb).sum())
+                    flips += fl
+            per = np.array(per)
+            return {"against": "the FP64 batch", "planes": [f"I_n{c}" for c in range(per.shape[1])],
+                    "image_bj_median": np.median(per, 0).tolist(), "image_bj_max": per.max(0).tolist(),
+                    "images_above_1e-5": int((per.max(1) > 1e-5).sum()), "mask_flips": flips}
+        batched["accuracy"] = per_image(bimgs, bmasks)
+        xjobs = [art.make_job(**{**p, "precision": "mixed_exact"}) for p in bparams]
+        t0 = time.perf_counter()
+        ctx.art_render_batch(xjobs, bimgs, bmasks, stats=False)
+        torch.cuda.synchronize()
+        tx = time.perf_counter() - t0
+        batched["exact"] = {"ms_per_batch": 1000 * tx,
+                            "note": "mixed_exact, the 256 images rendered one after the other",
+                            "accuracy": per_image(bimgs, bmasks)}
         del rimgs, rmasks
         del bimgs, bmasks
 
@@ -589,18 +905,19 @@ def main():
     if not args.no_learned:
         from paper_2103_07417_gb300 import learn
         t0 = time.perf_counter()
-        lctx, hist = learn.trained_context(seed=0, n_jobs=96, epochs=12, device=local,
-                                           snapshot=snap if snap is not None else W.grmhd_snapshot(seed=0))
+        lctx, hist, tr_info = learn.trained_context(
+            seed=0, n_jobs=args.learn_jobs, epochs=args.learn_epochs, device=local,
+            snapshot=snap if snap is not None else W.grmhd_snapshot(seed=0), info=True)
         t_train = time.perf_counter() - t0
         best, best_nb = None, None
         band0 = params.get("crit_band", 0.0)
         for band in sorted({0.0, band0}):
-            for depth in (2, 3):
+            for depth in (1, 2, 3):
                 for thr in (0.2, 0.3, 0.5, 0.7):
                     lj = art.make_job(**{**params, "proposal": 1, "proposal_p": thr,
                                          "proposal_depth": depth, "crit_band": band})
                     lst = lctx.art_render(lj, img, mask, stats=True)
-                    tl = _timed_ctx(lctx, lj, img, mask, flush, 5)
+                    tl = _timed_ctx(lctx, lj, img, mask, flush, 3)
                     cand = dict(depth=depth, threshold=thr, crit_band=band, ms_per_step=1000 * tl,
                                 rays_per_s=lst["rays_traced"] / tl,
                                 rays_speculative=lst["rays_speculative"],
@@ -610,14 +927,16 @@ def main():
                     if band == 0.0 and (best_nb is None or cand["ms_per_step"] < best_nb["ms_per_step"]):
                         best_nb = cand
         plain_nb = paths.get(args.precision + "_no_band", paths[args.precision])["ms_per_step"]
-        learned = {"training": {"jobs": 96, "epochs": 12, "seconds": t_train,
+        learned = {"training": {"jobs": args.learn_jobs, "epochs": args.learn_epochs,
+                                "seconds": t_train, **tr_info,
                                 "loss_first_epoch": hist[0], "loss_last_epoch": hist[-1]},
+                   "precision": args.precision,
                    "best": best, "best_without_band": best_nb,
                    "gain_vs_plain": (1000 * t_dev / args.steps) / best["ms_per_step"],
                    "gain_vs_plain_both_without_band": plain_nb / best_nb["ms_per_step"],
                    "note": "same image and mask as the plain render (the exact criterion decides "
                            "every point); lookahead depth, threshold and band chosen among "
-                           "{2,3} x {0.2,0.3,0.5,0.7} x {0, default} by timing"}
+                           "{1,2,3} x {0.2,0.3,0.5,0.7} x {0, default} by timing"}
 
     # the proposal network's tensor-core kernels alone: forward (4 implicit-GEMM convolutions +
     # head) and forward + backward on a 2049 x 2049 lattice, host-timed (each call synchronises)
@@ -626,51 +945,23 @@ def main():
         nlat = 2049
         t_fw, t_fb = cnn_measure(lctx, nlat)
         fl = cnn_flops(nlat, nlat)
-        peak = 1941.4  # measured cuBLAS BF16 dense GEMM rate of a GB300 (burst), TFLOP/s
+        peak = peaks["bf16_tflops"]
         cnn = {"lattice": f"{nlat}x{nlat}", "forward_ms": 1000 * t_fw,
                "forward_backward_ms": 1000 * t_fb,
                "roofline": {"bound": "tensor", "achieved": fl / t_fw / 1e12, "peak": peak,
                             "unit": "TFLOP/s", "frac": fl / t_fw / 1e12 / peak,
-                            "peak_source": "measured cuBLAS bf16 dense GEMM, burst",
+                            "peak_source": peaks["source"] + ": cuBLAS bf16 dense GEMM, burst",
                             "flops_per_forward": fl}}
 
-    # time to a 0.1 %-MSE image (paper MSE vs the full FP64 trace) for each path: the fastest
-    # tolerance R = R_rel = R_abs meeting it
-    time_to_mse = None
+    visib = None
+    if not args.no_vis and world == 1:
+        visib = visibility_spectra(ctx, flush)
+        if snap is not None:
+            ctx.load_grid(snap)
+
+    tmse = None
     if not args.no_mse and not args.gpus > 1:
-        if nx * ny <= (1 << 23):
-            tjob = art.make_job(**{**params, "precision": "fp64", "R_rel": -1.0, "R_abs": -1.0})
-            truth = torch.empty_like(img)
-            ctx.art_render(tjob, truth, mask, stats=False)
-            rlist = (3e-3, 1e-3, 3e-4, 1e-4) if params.get("emission") != "grid" else (0.1, 0.025, 1e-2, 3e-3)
-            time_to_mse = {"target_mse": 1e-3, "truth": "full FP64 trace of the final grid",
-                           "sweep_R": list(rlist), "paths": {}}
-            variants = [("fp64", ctx, {"precision": "fp64", "crit_band": 0.0}),
-                        ("mixed_df_no_band", ctx, {"precision": "mixed_df", "crit_band": 0.0}),
-                        ("mixed_df", ctx, {"precision": "mixed_df"})]
-            if lctx is not None:
-                variants.append(("mixed_df+learned", lctx,
-                                 {"precision": "mixed_df", "proposal": 1,
-                                  "proposal_p": learned["best"]["threshold"],
-                                  "proposal_depth": learned["best"]["depth"],
-                                  "crit_band": learned["best"]["crit_band"]}))
-            for name, cx, over in variants:
-                rec, sweep = None, []
-                for R in rlist:
-                    rr = {"R_abs": R} if params.get("emission") == "grid" else {"R_abs": R, "R_rel": R}
-                    vj = art.make_job(**{**params, **over, **rr})
-                    vst = cx.art_render(vj, img, mask, stats=True)
-                    met = cx.art_metrics(truth[0], img[0], mask)
-                    tv = _timed_ctx(cx, vj, img, mask, flush, 3)
-                    sweep.append({"R": R, "mse": met["MSE"], "IF": met["IF"], "seconds": tv,
-                                  "rays": vst["rays_traced"]})
-                    if met["MSE"] <= 1e-3 and (rec is None or tv < rec["seconds"]):
-                        rec = {"seconds": tv, "R": R, "mse": met["MSE"]}
-                time_to_mse["paths"][name] = {"best": rec, "sweep": sweep}
-            del truth
-        else:
-            time_to_mse = {"skipped": "final grid above 2^23 points: the FP64 truth trace is too "
-                                      "long for the default run"}
+        tmse = time_to_mse(args, params, ctx, lctx, learned, img, mask, flush, dev)
     if lctx is not None:
         lctx.close()
 
@@ -691,8 +982,9 @@ def main():
                                  "region", "parallelism": f"replicas x{world}"},
                 "geodesic_steps_per_s": steps_per_render * args.steps * world / t_dev,
                 "paths": paths, "batched": batched, "learned": learned, "cnn": cnn,
-                "time_to_mse": time_to_mse, "accuracy": acc, "roofline": roofline,
-                "kernels": kernels,
+                "time_to_mse": tmse, "accuracy": acc, "roofline": roofline,
+                "visibilities": visib,
+                "roofline_kernels": roofline_all, "kernels": kernels, "peaks": peaks,
                 "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": int(stats["kernel_launches"]) * args.steps}
         print(json.dumps(line), flush=True)

@@ -50,6 +50,7 @@ enum { ART_FLOW_KEPLER = 0, ART_FLOW_STATIC = 1 };
 enum { ART_NORM_IBAR_INT = 0, ART_NORM_PEAK = 1 };
 enum { ART_INTERP_LINEAR = 0, ART_INTERP_NEAREST = 1 };
 enum { ART_EDGE_ONESIDED = 0, ART_EDGE_TRACE = 1 };
+enum { ART_CRIT_I = 0, ART_CRIT_STOKES_ANY = 1 };
 enum { ART_FP64 = 0, ART_MIXED = 1, ART_FP32 = 2, ART_MIXED_DF = 3, ART_MIXED_EXACT = 4 };
 enum { ART_MASK_UNSET = 0, ART_MASK_TRACED = 1, ART_MASK_INTERP = 2 };
 enum { ART_RAY_ESCAPED = 0, ART_RAY_CAPTURED = 1, ART_RAY_CAP = 2, ART_RAY_NAN = 3 };
@@ -126,6 +127,13 @@ typedef struct art_job {
      * of the render without it.  Not with a truth image (ART_ERR_ARG).  art_render_batch applies
      * each job's band to its image, all in the batch's base-level pass. */
     double crit_band;
+    /* Criterion of polarized jobs (Sec. 6 proposes "replacing I by Q, U, V"): ART_CRIT_I decides
+     * on I; ART_CRIT_STOKES_ANY traces a point when the criterion holds for any of I, Q, U, V
+     * (Q, U, V through the same estimator, eps_abs over the same normalisation, eps_rel over the
+     * magnitude of I's interpolant).  Ignored for stokes = 1; not with ART_MIXED_EXACT
+     * (ART_ERR_UNSUPPORTED). */
+    int32_t criterion;
+    int32_t criterion_pad;
 } art_job;
 
 /* Statistics of one render (host struct, filled on return). */
@@ -237,6 +245,23 @@ int art_render(art_ctx* ctx, const art_job* job, const double* truth_dev, double
  * stats.  Errors as art_render. */
 int art_render_batch(art_ctx* ctx, const art_job* jobs, int32_t n, double* const* imgs,
                      uint8_t* const* masks, art_stats* stats_host);
+
+/* Visibility-domain analysis (Sec. 4.3): the complex visibilities of one image plane, the 2-D
+ * Fourier transform that an interferometer baseline (u, v) samples,
+ *   V(u, v) = dx^2 sum_{x,y} T(x, y) A(x, y) exp(-2 pi i (u X + v Y)),
+ *   X = (x - (nx-1)/2) dx, Y = (y - (ny-1)/2) dx (origin at the image centre),
+ *   T = exp(-4 ln 2 (X^2 + Y^2) / taper_fwhm^2) (the paper's Gaussian taper; none if <= 0),
+ *   A = img, or img - ref when ref_dev is given (the Fourier amplitudes of the residual image),
+ * on the grid u = k_u / (m dx), v = k_v / (m dx), k in [-m/2, m/2), of an m x m FFT of the
+ * zero-padded image.  The paper doubles the field of view and the pixel count before the taper
+ * (same resolution): render the job with fov * 2 and n0 -> 2 n0 - 1 for that.
+ * img_dev, ref_dev (nullable): ny x nx doubles, row-major (one plane of an art_render image).
+ * vis_dev: caller-owned m x m complex doubles (re, im interleaved), row k_v, column k_u, each
+ * frequency index stored at k mod m.  m: a power of two, 32 <= m <= 32768, m >= nx, ny.  The
+ * library holds m x m complex doubles of scratch (grown, never shrunk).  FP64 throughout.
+ * Errors: ART_ERR_ARG, ART_ERR_OOM, ART_ERR_CUDA.  Asynchronous on the context's stream. */
+int art_visibilities(art_ctx* ctx, const double* img_dev, const double* ref_dev, int32_t nx,
+                     int32_t ny, double dx, double taper_fwhm, int32_t m, double* vis_dev);
 
 /* art_render into HOST buffers: the image and mask are rendered into context-owned device
  * buffers and copied to img_host (planes x ny x nx doubles) and mask_host (nullable, ny x nx

@@ -71,6 +71,7 @@ class Job(ctypes.Structure):
         ("glogr_min", ctypes.c_double), ("glogr_max", ctypes.c_double),
         ("gamma_ad", ctypes.c_double), ("m_unit", ctypes.c_double),
         ("r_high", ctypes.c_double), ("r_low", ctypes.c_double), ("sigma_cut", ctypes.c_double),
+        ("criterion", ctypes.c_int), ("cpad", ctypes.c_int),
     ]
 
 
@@ -92,7 +93,7 @@ _DEFAULTS = dict(a=0.0, mass=1.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33,
                  h_min=1e-4, horizon_eps=0.01, escape_frac=1.01, disk_w=0.3, blob_sigma=1.0,
                  ne0=0.0, thetae0=0.0, b0=0.0, nu_hz=230e9, ne_slope=-1.1, te_slope=-0.84,
                  r_in=0.0, length_cm=9.6e14, bz_ratio=1.0, gamma_ad=13.0 / 9.0, m_unit=1e27,
-                 r_high=20.0, r_low=1.0, sigma_cut=1.0)
+                 r_high=20.0, r_low=1.0, sigma_cut=1.0, criterion=0)
 
 
 _NAMES = dict(
@@ -102,6 +103,7 @@ _NAMES = dict(
     abs_norm={"ibar_int": NORM_IBAR_INT, "peak": NORM_PEAK},
     interp={"linear": INTERP_LINEAR, "nearest": INTERP_NEAREST},
     edge_mode={"onesided": EDGE_ONESIDED, "trace": EDGE_TRACE},
+    criterion={"I": 0, "stokes_any": 1},
 )
 
 
@@ -261,12 +263,15 @@ def ibar_int(img, stride: int) -> float:
 
 
 def refine_level(job: Job, img, mask, level: int, norm: float):
-    """One refinement level in place on copies; returns (img, mask, est_abs, est_rel)."""
+    """One refinement level in place on copies; returns (img, mask, est_abs, est_rel) (the
+    estimates of plane 0).  img: (ny, nx), or (planes, ny, nx) with the job's plane count."""
     a = np.array(img, dtype=np.float64, order="C", copy=True)
     m = np.array(mask, dtype=np.uint8, order="C", copy=True)
-    ny, nx = a.shape
-    ea = np.full_like(a, np.nan)
-    er = np.full_like(a, np.nan)
+    ny, nx = a.shape[-2:]
+    if a.ndim == 3 and a.shape[0] != planes(job):
+        raise ValueError("img planes do not match the job")
+    ea = np.full((ny, nx), np.nan)
+    er = np.full((ny, nx), np.nan)
     rc = _load().orc_refine_level(ctypes.byref(job), _ptr(a), _ptr(m, ctypes.c_uint8), nx, ny,
                                   int(level), float(norm), _ptr(ea), _ptr(er))
     if rc:

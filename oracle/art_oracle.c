@@ -1053,8 +1053,9 @@ static double second_diff_sum(const double* img, int nx, int ny, int i, int j, i
  * Nearest, category 4: sqrt(((I4-I1)/2)^2 + ((I3-I2)/2)^2) over norm and over |I1|,
  *   interpolant I1;  categories 2/3: |I2 - I1|/2 over norm and over |I1|, interpolant I1.
  * Returns 1 when the point must be traced. */
-static int estimate_point(const orc_job* job, const double* img, int nx, int ny, int i, int j,
-                          int s, double norm, double* interp, double* ea, double* er)
+static int estimate_point_nd(const orc_job* job, const double* img, int nx, int ny, int i, int j,
+                             int s, double norm, double* interp, double* ea, double* er,
+                             double* num_out, double* den_out)
 {
     int cat = category(i, j, s);
     int ok = 1;
@@ -1093,16 +1094,44 @@ static int estimate_point(const orc_job* job, const double* img, int nx, int ny,
     if (!ok && job->interp == ORC_INTERP_LINEAR) {
         *ea = INFINITY;
         *er = INFINITY;
+        *num_out = INFINITY;
+        *den_out = 0.0;
         return (*ea > job->R_abs) && (*er > job->R_rel);
     }
     /* eps_abs = num / norm; eps_rel = num / |interpolant| (linear: (S_out-S_in)/(4 S_in)) */
     double den = (job->interp == ORC_INTERP_NEAREST) ? fabs(i1)
                  : (cat == 4 ? fabs(sin_) / 4.0 : fabs(sin_) / 2.0);
+    *num_out = num;
+    *den_out = den;
     *ea = num / norm;
     if (den == 0.0) *er = (num == 0.0) ? 0.0 : INFINITY;
     else *er = num / den;
     if (isnan(*ea) || isnan(*er) || isnan(*interp)) return 1;
     return (*ea > job->R_abs) && (*er > job->R_rel);
+}
+
+static int estimate_point(const orc_job* job, const double* img, int nx, int ny, int i, int j,
+                          int s, double norm, double* interp, double* ea, double* er)
+{
+    double num, den;
+    return estimate_point_nd(job, img, nx, ny, i, j, s, norm, interp, ea, er, &num, &den);
+}
+
+/* The polarized variant of the criterion (Sec. 6: "replacing I by Q, U, V"): the estimate of
+ * plane `plane` (Q, U or V) at the point from the same stencil and divisors as I's, eps_abs over
+ * the same normalisation, eps_rel over I's denominator |S_in(I)|/4 (centre) or /2 (midpoint), or
+ * |I_1| (nearest) -- Q, U and V themselves may vanish or change sign.  Returns 1 when that plane
+ * asks for the point to be traced. */
+static int plane_triggers(const orc_job* job, const double* img, const double* plane, int nx,
+                          int ny, int i, int j, int s, double norm)
+{
+    double ic, eac, erc, numc, denc, iI, eaI, erI, numI, denI;
+    estimate_point_nd(job, plane, nx, ny, i, j, s, norm, &ic, &eac, &erc, &numc, &denc);
+    estimate_point_nd(job, img, nx, ny, i, j, s, norm, &iI, &eaI, &erI, &numI, &denI);
+    if (isinf(numc)) return (INFINITY > job->R_abs) && (INFINITY > job->R_rel);
+    double er = (denI == 0.0) ? (numc == 0.0 ? 0.0 : INFINITY) : numc / denI;
+    if (isnan(eac) || isnan(er)) return 1;
+    return (eac > job->R_abs) && (er > job->R_rel);
 }
 
 /* One refinement level (Sec. 3.2): every new point of level `level` reads only points of the
@@ -1121,6 +1150,9 @@ int orc_refine_level(const orc_job* job, double* img, uint8_t* mask, int nx, int
             if (cat == 1) continue;
             double interp, ea, er;
             int tr = estimate_point(job, img, nx, ny, i, j, s, norm, &interp, &ea, &er);
+            if (!tr && job->criterion == ORC_CRIT_STOKES_ANY && job->stokes == 4)
+                for (int c = 1; c < 4 && !tr; ++c)
+                    tr = plane_triggers(job, img, img + c * npix, nx, ny, i, j, s, norm);
             if (job->edge_mode == ORC_EDGE_TRACE) {
                 int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
                 if (i - 3 * di < 0 || i + 3 * di >= nx || j - 3 * dj < 0 || j + 3 * dj >= ny) tr = 1;

@@ -64,7 +64,11 @@ typedef struct orc_job {
     double m_unit;       /* mass unit (g): rho_cgs = rho m_unit / length_cm^3 */
     double r_high, r_low;/* ion-to-electron temperature ratio at high / low plasma beta */
     double sigma_cut;    /* no emission where b^2/rho > sigma_cut */
+    int criterion;       /* ORC_CRIT_I: decide on I; ORC_CRIT_STOKES_ANY: trace when the
+                          * criterion holds for any of I, Q, U, V (stokes = 4) */
+    int cpad;
 } orc_job;
+enum { ORC_CRIT_I = 0, ORC_CRIT_STOKES_ANY = 1 };
 
 typedef struct orc_rayinfo {
     int32_t status, steps, nturn, pad;

@@ -27,6 +27,7 @@ _NAMES = dict(
     interp={"linear": 0, "nearest": 1},
     edge_mode={"onesided": 0, "trace": 1},
     precision={"fp64": 0, "mixed": 1, "fp32": 2, "mixed_df": 3, "mixed_exact": 4},
+    criterion={"I": 0, "stokes_any": 1},
 )
 
 
@@ -48,6 +49,7 @@ class Job(ctypes.Structure):
         ("r_high", ctypes.c_double), ("r_low", ctypes.c_double), ("sigma_cut", ctypes.c_double),
         ("proposal", ctypes.c_int32), ("proposal_depth", ctypes.c_int32),
         ("proposal_p", ctypes.c_double), ("crit_band", ctypes.c_double),
+        ("criterion", ctypes.c_int32), ("criterion_pad", ctypes.c_int32),
     ]
 
 
@@ -86,7 +88,7 @@ class RayAux(ctypes.Structure):
 
 _JOB_DEFAULTS = dict(fp64_sweep=3.0 * 3.141592653589793, gamma_ad=13.0 / 9.0, m_unit=3e26,
                      r_high=20.0, r_low=1.0, sigma_cut=1.0, proposal=0, proposal_depth=2,
-                     proposal_p=0.5, crit_band=0.0)
+                     proposal_p=0.5, crit_band=0.0, criterion=0, criterion_pad=0)
 
 
 def make_job(**params) -> Job:
@@ -113,7 +115,7 @@ EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_p
            "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid", "art_cnn_load",
            "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step",
            "art_cnn_sample", "art_set_tune", "art_get_tune", "art_autotune", "art_graph_render",
-           "art_graph_render_batch", "art_measure_alu_peaks")
+           "art_graph_render_batch", "art_measure_alu_peaks", "art_visibilities")
 CNN_PARAMS = 28673
 NOALLOC_MAX_RAYS = 1 << 20
 
@@ -162,6 +164,8 @@ def load():
             lib.art_measure_alu_peaks.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double)]
             lib.art_autotune.argtypes = [vp, P(Job), vp, vp, i32, P(Tune), fp]
             lib.art_graph_render.argtypes = [vp, P(Job), vp, vp]
+            lib.art_visibilities.argtypes = [vp, vp, vp, i32, i32, ctypes.c_double,
+                                             ctypes.c_double, i32, vp]
             lib.art_graph_render_batch.argtypes = [vp, P(Job), i32, P(vp), P(vp)]
             _lib = lib
     return _lib
@@ -439,6 +443,24 @@ class Context:
         _check(load().art_measure_alu_peaks(self._ctx, ctypes.byref(f32), ctypes.byref(f64)),
                "art_measure_alu_peaks")
         return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
+
+    def art_visibilities(self, img, dx: float, taper_fwhm: float, m: int, ref=None, out=None):
+        """Visibilities of one image plane (ny, nx) float64 CUDA tensor (minus `ref` if given):
+        an (m, m) complex128 tensor, row k_v, column k_u, frequency k stored at k mod m."""
+        import torch
+        if img.dtype != torch.float64 or img.dim() != 2 or not img.is_contiguous():
+            raise ValueError("img must be a contiguous 2-D float64 tensor")
+        if ref is not None and (ref.shape != img.shape or ref.dtype != torch.float64
+                                or not ref.is_contiguous()):
+            raise ValueError("ref must match img")
+        ny, nx = int(img.shape[0]), int(img.shape[1])
+        if out is None:
+            out = torch.empty((m, m, 2), dtype=torch.float64, device=img.device)
+        elif out.dtype != torch.float64 or out.numel() < 2 * m * m or not out.is_contiguous():
+            raise ValueError("out must hold m x m complex float64 values")
+        _check(load().art_visibilities(self._ctx, _dptr(img), _dptr(ref), nx, ny, float(dx),
+                                       float(taper_fwhm), int(m), _dptr(out)), "art_visibilities")
+        return torch.view_as_complex(out.view(m, m, 2))
 
     def art_profile(self, enable: bool):
         _check(load().art_profile(self._ctx, int(bool(enable))), "art_profile")

@@ -66,6 +66,11 @@ struct art_ctx {
     int64_t cxq_cap = 0;
     uint64_t* cfixq = nullptr;
     int64_t cfixq_cap = 0;
+    // visibilities (art_visibilities): m x m complex scratch and the transform's tables
+    double2* vq = nullptr;
+    int64_t vq_cap = 0;
+    double* vtab = nullptr;
+    int64_t vtab_cap = 0;
     float* prob = nullptr;
     int64_t prob_cap = 0;
     // batched rendering tables and queue (grown, never shrunk)
@@ -214,6 +219,10 @@ static int make_devjob(const art_job* job, DevJob* J)
     if (job->abs_norm != ART_NORM_IBAR_INT && job->abs_norm != ART_NORM_PEAK) return ART_ERR_ARG;
     if (job->precision < ART_FP64 || job->precision > ART_MIXED_EXACT) return ART_ERR_ARG;
     if (!(job->disk_w > 0.0)) return ART_ERR_ARG;
+    if (job->criterion != ART_CRIT_I && job->criterion != ART_CRIT_STOKES_ANY) return ART_ERR_ARG;
+    if (job->criterion == ART_CRIT_STOKES_ANY && job->stokes == 4 &&
+        job->precision == ART_MIXED_EXACT)
+        return ART_ERR_UNSUPPORTED;
     if (!(job->fp64_sweep > 0.0)) return ART_ERR_ARG;
     J->a = job->a;
     J->a2 = job->a * job->a;
@@ -241,6 +250,8 @@ static int make_devjob(const art_job* job, DevJob* J)
     J->abs_norm = job->abs_norm;
     // exact decisions change the level loop only; the rays are traced as in ART_MIXED_DF
     J->precision = job->precision == ART_MIXED_EXACT ? ART_MIXED_DF : job->precision;
+    J->criterion = job->criterion;
+    J->pad_ = 0;
     return ART_OK;
 }
 
@@ -402,6 +413,8 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFree(c->cborder);
     cudaFree(c->cxq);
     cudaFree(c->cfixq);
+    cudaFree(c->vq);
+    cudaFree(c->vtab);
     for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -847,6 +860,23 @@ extern "C" int art_render_host(art_ctx* c, const art_job* job, double* img_host,
     } else {
         CK(cudaStreamSynchronize(c->stream));
     }
+    return ART_OK;
+}
+
+extern "C" int art_visibilities(art_ctx* c, const double* img_dev, const double* ref_dev,
+                                int32_t nx, int32_t ny, double dx, double taper_fwhm, int32_t m,
+                                double* vis_dev)
+{
+    if (!c || !img_dev || !vis_dev || nx < 1 || ny < 1 || !(dx > 0.0) || !(taper_fwhm == taper_fwhm))
+        return ART_ERR_ARG;
+    if (m < 32 || m > 32768 || (m & (m - 1)) || m < nx || m < ny) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    int rc;
+    if ((rc = grow(c, c->vq, c->vq_cap, (int64_t)m * m)) ||
+        (rc = grow(c, c->vtab, c->vtab_cap, (int64_t)vis_table_doubles(m, nx, ny))))
+        return rc;
+    CK(launch_visibilities(img_dev, ref_dev, nx, ny, dx, taper_fwhm, m,
+                           reinterpret_cast<double2*>(vis_dev), c->vq, c->vtab, c->stream));
     return ART_OK;
 }
 

@@ -174,6 +174,13 @@ cudaError_t launch_metrics(const double* truth, const double* img, const uint8_t
                            int ny, double* partials, int nblocks, double* out6, cudaStream_t st);
 constexpr int METRIC_BLOCKS = 304;
 
+// vis.cu: visibilities of a (residual) image, V and Q m x m complex, tables of
+// vis_table_doubles() doubles
+int vis_table_doubles(int m, int nx, int ny);
+cudaError_t launch_visibilities(const double* img, const double* ref, int nx, int ny, double dx,
+                                double fwhm, int m, double2* V, double2* Q, double* tables,
+                                cudaStream_t st);
+
 // peaks.cu: measured FP32 / FP64 fused multiply-add throughput (TFLOP/s)
 cudaError_t measure_alu_peaks(int num_sms, cudaStream_t st, double* fp32_tflops,
                               double* fp64_tflops);

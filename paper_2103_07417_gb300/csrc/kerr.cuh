@@ -75,7 +75,7 @@ struct DevJob {
     double a, a2, r_obs, pix, step_frac, h_min, r_in_stop, r_out_stop, inv_2w2;
     double R_abs, R_rel, fp64_sweep;
     int32_t nx, ny, levels, emission, flow, stokes, subrings, planes, max_steps;
-    int32_t interp, edge_mode, abs_norm, precision;
+    int32_t interp, edge_mode, abs_norm, precision, criterion, pad_;
 };
 
 // Static camera: position and the covariant (lowered) tetrad E0 (observer), E1 (outward),

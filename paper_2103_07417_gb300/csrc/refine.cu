@@ -215,6 +215,42 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
     }
     bool tr = (ea > J.R_abs) && (er > J.R_rel);
     if (isnan(ea) || isnan(er) || isnan(sin_) || isnan(i1)) tr = true;
+    if (!tr && J.criterion == ART_CRIT_STOKES_ANY && J.stokes == 4) {
+        // Sec. 6, "replacing I by Q, U, V": Q, U and V each through the same estimator (same
+        // stencil and divisors), eps_abs over the same normalisation, eps_rel over I's
+        // denominator (Q, U, V may vanish or change sign); the point is traced if any asks
+        const int64_t npix = (int64_t)nx * ny;
+        for (int c = 1; c < 4 && !tr; ++c) {
+            const double* pl = img + c * npix;
+            double nc;
+            if (cat == 4) {
+                const double I1 = __ldg(pl + p1), I4 = __ldg(pl + p4), I2 = __ldg(pl + p2),
+                             I3 = __ldg(pl + p3);
+                if (J.interp == ART_INTERP_NEAREST) {
+                    const double d41 = I4 - I1, d32 = I3 - I2;
+                    nc = sqrt(__dadd_rn(__dmul_rn(__dmul_rn(0.25, d41), d41),
+                                        __dmul_rn(__dmul_rn(0.25, d32), d32)));
+                } else {
+                    bool okc = true;
+                    const double dA = second_diff_sum<IX>(pl, nx, ny, i, j, s, s, I1, I4, okc);
+                    const double dB = second_diff_sum<IX>(pl, nx, ny, i, j, s, -s, I2, I3, okc);
+                    nc = fabs(dA + dB) / 16.0;
+                }
+            } else {
+                const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
+                const double I1 = __ldg(pl + p1), I2 = __ldg(pl + p2);
+                if (J.interp == ART_INTERP_NEAREST) {
+                    nc = fabs(I2 - I1) / 2.0;
+                } else {
+                    bool okc = true;
+                    nc = fabs(second_diff_sum<IX>(pl, nx, ny, i, j, di, dj, I1, I2, okc)) / 8.0;
+                }
+            }
+            const double eac = nc / norm;
+            const double erc = (den == 0.0) ? (nc == 0.0 ? 0.0 : INFINITY) : nc / den;
+            tr = (eac > J.R_abs && erc > J.R_rel) || isnan(eac) || isnan(erc);
+        }
+    }
     if (J.edge_mode == ART_EDGE_TRACE) {
         const int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
         if (i - 3 * di < 0 || i + 3 * di >= nx || j - 3 * dj < 0 || j + 3 * dj >= ny) tr = true;
@@ -249,7 +285,8 @@ __device__ __forceinline__ Screen make_screen(const DevJob& J, double norm, doub
     Screen sc;
     sc.bup = (float)(1.0 + band);
     sc.bdn = (float)(1.0 - band);
-    sc.on = J.interp == ART_INTERP_LINEAR && norm > 0.0 && norm < 1e300;
+    sc.on = J.interp == ART_INTERP_LINEAR && norm > 0.0 && norm < 1e300 &&
+            !(J.criterion == ART_CRIT_STOKES_ANY && J.stokes == 4);
     sc.abs_any = J.R_abs < 0.0;
     sc.rel_any = J.R_rel < 0.0;
     const double t4 = 16.0 * J.R_abs * norm, t2 = 8.0 * J.R_abs * norm, r4 = 4.0 * J.R_rel;

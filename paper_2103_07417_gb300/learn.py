@@ -80,12 +80,20 @@ def block_scores(ctx, samples, thr: float) -> dict:
 
 
 def trained_context(seed: int = 0, n_jobs: int = 96, epochs: int = 12, device: int = 0,
-                    snapshot=None):
+                    snapshot=None, info: bool = False):
     """A context with the snapshot loaded and a network trained from W.cnn_init(seed) on
-    n_jobs seeded plain renders; returns (ctx, loss history)."""
+    n_jobs seeded plain renders; returns (ctx, loss history[, dict of sample count and the
+    seconds spent rendering and training])."""
+    import time
     ctx = art.Context(device)
     ctx.load_grid(snapshot if snapshot is not None else W.grmhd_snapshot(seed=0))
     ctx.art_cnn_load(W.cnn_init(seed))
+    t0 = time.perf_counter()
     samples = collect(ctx, training_jobs(seed, n_jobs))
+    t1 = time.perf_counter()
     hist = train(ctx, samples, epochs=epochs, seed=seed)
+    t2 = time.perf_counter()
+    if info:
+        return ctx, hist, {"samples": len(samples), "render_seconds": t1 - t0,
+                           "train_seconds": t2 - t1}
     return ctx, hist

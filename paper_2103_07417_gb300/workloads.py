@@ -144,6 +144,13 @@ def grmhd_8193(**over) -> dict:
                          precision="mixed_df", crit_band=CRIT_BAND), **over})
 
 
+def doubled_fov(params: dict) -> dict:
+    """The same job with its field of view and pixel count doubled at the same resolution (the
+    visibility analysis of Sec. 4.3): fov x 2 and a base grid of 2 n0 - 1 points per axis."""
+    return {**params, "fov": 2.0 * params["fov"], "n0x": 2 * params["n0x"] - 1,
+            "n0y": 2 * params["n0y"] - 1}
+
+
 def grmhd_16385(**over) -> dict:
     """Evaluation workload of the learned block proposal: the GRMHD-like snapshot and its emission seen
     with a 1000 M field of view, 257^2 -> 16385^2 over 6 levels (the photon ring and the torus

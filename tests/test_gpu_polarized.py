@@ -156,3 +156,65 @@ def test_polarized_workload_every_traced_ray(ctx):
             for s in range(4)]
     print("per-ray error over", pix.numel(), "rays:", errs)
     assert max(errs) <= 1e-5, errs
+
+
+@pytest.mark.parametrize("interp", ["linear", "nearest"])
+def test_stokes_any_refine_matches_oracle(interp):
+    """The polarized criterion variant (Sec. 6, "replacing I by Q, U, V"): one refinement level
+    of a four-plane image whose Q, U, V have structure where I is smooth, on the GPU against the
+    oracle -- identical masks (outside 1e-9 of a tolerance) and bit-identical interpolants in every
+    plane; the variant traces more points than the I criterion on the same input."""
+    from paper_2103_07417_gb300 import art
+    ctx = art.Context(0)
+    levels = 3
+    base = dict(n0x=17, n0y=13, levels=levels, R_abs=2e-3, R_rel=5e-3, stokes=4,
+                emission="synch_disk", interp=interp)
+    nx, ny = art.art_image_size(art.make_job(**W.job(**base)))
+    truth = np.stack([W.smooth_image(5, nx, ny), 0.3 * W.ring_image(6, nx, ny),
+                      -0.2 * W.smooth_image(7, nx, ny, noise=0.05), 0.05 * W.ring_image(8, nx, ny)])
+    norm = float(truth[0].mean())
+    counts = {}
+    for crit in ("I", "stokes_any"):
+        params = W.job(**base, criterion=crit)
+        job, ojob = art.make_job(**params), O.make_job(**params)
+        tot = 0
+        for level in range(1, levels + 1):
+            sp = 1 << (levels - level + 1)
+            img = np.full_like(truth, np.nan)
+            img[:, ::sp, ::sp] = truth[:, ::sp, ::sp]
+            mask = np.zeros((ny, nx), np.uint8)
+            mask[::sp, ::sp] = O.MASK_TRACED
+            ref_img, ref_mask, ea, er = O.refine_level(ojob, img, mask, level, norm)
+            img_d, mask_d = torch.from_numpy(img).cuda(), torch.from_numpy(mask).cuda()
+            queue = torch.full((nx * ny,), -1, dtype=torch.int32, device="cuda")
+            tot += ctx.art_refine_level(job, img_d, mask_d, level, norm, queue)
+            gm, gi = mask_d.cpu().numpy(), img_d.cpu().numpy()
+            near = ((np.abs(ea - base["R_abs"]) <= 1e-9 * base["R_abs"])
+                    | (np.abs(er - base["R_rel"]) <= 1e-9 * base["R_rel"]))
+            assert ((gm != ref_mask) & ~near).sum() == 0, (crit, level)
+            interp_pts = (ref_mask == 2) & (gm == 2)
+            for c in range(4):
+                np.testing.assert_array_equal(gi[c][interp_pts], ref_img[c][interp_pts])
+        counts[crit] = tot
+    assert counts["stokes_any"] > counts["I"]
+    ctx.close()
+
+
+def test_stokes_any_render_matches_oracle_mask():
+    """A polarized adaptive render with the any-Stokes criterion in FP64 against the oracle:
+    every traced pixel within the polarized tolerance, and at least as many rays as the I
+    criterion."""
+    from paper_2103_07417_gb300 import art
+    ctx = art.Context(0)
+    params = W.kerr_disk_2049(n0x=9, n0y=9, levels=2, precision="fp64", crit_band=0.0,
+                              criterion="stokes_any", R_rel=0.02, R_abs=0.02)
+    img, mask, st = ctx.render(art.make_job(**params))
+    _, _, sti = ctx.render(art.make_job(**{**params, "criterion": "I"}))
+    ref, rmask, rst = O.render(O.make_job(**params), None)
+    g = img.cpu().numpy()
+    same = mask.cpu().numpy() == rmask
+    assert same.mean() > 0.99
+    scale = np.maximum(np.abs(ref[0]), 1e-6 * np.abs(ref[0]).max())
+    assert np.max(np.abs(g[0] - ref[0])[same] / scale[same]) < 2e-6
+    assert st["rays_traced"] >= sti["rays_traced"]
+    ctx.close()

@@ -351,3 +351,62 @@ def test_metrics_small_example():
     Fh = np.trapezoid(np.trapezoid(img, axis=1))
     assert mt["FE"] == pytest.approx(abs(F - Fh) / F)
     assert mt["MSE_mean"] == pytest.approx(1.0 / (6 * np.mean(truth) ** 2))
+
+
+# ------------------------------------------------------------------------------------------
+# polarized criterion (Sec. 6: "replacing I by Q, U, V")
+# ------------------------------------------------------------------------------------------
+
+def _pol_job(criterion, **kw):
+    return O.make_job(**W.job(stokes=4, emission="synch_disk", criterion=criterion, **kw))
+
+
+def test_stokes_any_reduces_to_the_intensity_criterion_without_polarization():
+    """Q = U = V = 0: the any-Stokes mask and interpolants equal those of the I criterion."""
+    rng = np.random.default_rng(7)
+    levels, level = 3, 2
+    kw = dict(n0x=9, n0y=7, levels=levels, R_abs=0.02, R_rel=0.01)
+    nx, ny = O.image_size(_pol_job("I", **kw))
+    truth = np.zeros((4, ny, nx))
+    truth[0] = W.smooth_image(3, nx, ny, noise=0.05)
+    im, m = _level_setup(truth[0], levels, level)
+    img = np.zeros_like(truth)
+    img[0] = im
+    a, ma, ea, _ = O.refine_level(_pol_job("I", **kw), img, m, level, 1.0)
+    b, mb, eb, _ = O.refine_level(_pol_job("stokes_any", **kw), img, m, level, 1.0)
+    np.testing.assert_array_equal(ma, mb)
+    np.testing.assert_array_equal(np.nan_to_num(a, nan=-1), np.nan_to_num(b, nan=-1))
+    assert (ma == O.MASK_TRACED).sum() > 0 and (ma == O.MASK_INTERP).sum() > 0
+    assert rng is not None
+
+
+def test_stokes_any_traces_where_q_curves_and_i_is_flat():
+    """I a constant plateau (zero estimates: the I criterion traces nothing), Q = x^2 + y^2
+    (pixel units): the Q estimates are the closed forms of the quadratic test, eps_abs * norm =
+    2 x (true residual) = 4 s^2 at cell centres and 2 s^2 at edge midpoints, and eps_rel is that
+    over I's interpolant.  With R_abs between the two, the any-Stokes criterion traces exactly the
+    cell centres (and the corner cells without any outer point), and the I criterion only those
+    corners."""
+    levels, level = 3, 2
+    s = 1 << (levels - level)
+    c0 = 8.0
+    kw = dict(n0x=9, n0y=9, levels=levels, R_abs=3.0 * s * s, R_rel=0.5 * s * s / c0)
+    nx, ny = O.image_size(_pol_job("I", **kw))
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    truth = np.zeros((4, ny, nx))
+    truth[0] = c0
+    truth[1] = x * x + y * y
+    im = np.full_like(truth, np.nan)
+    sp = 2 * s
+    im[:, ::sp, ::sp] = truth[:, ::sp, ::sp]
+    m = np.zeros((ny, nx), np.uint8)
+    m[::sp, ::sp] = O.MASK_TRACED
+    _, mi, ea, _ = O.refine_level(_pol_job("I", **kw), im, m, level, 1.0)
+    _, mq, _, _ = O.refine_level(_pol_job("stokes_any", **kw), im, m, level, 1.0)
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(ny))
+    new = ~np.isnan(ea)
+    cat4 = new & ((ii // s) % 2 == 1) & ((jj // s) % 2 == 1)
+    corner = new & np.isinf(ea)
+    assert corner.sum() == 4
+    np.testing.assert_array_equal(mi[new] == O.MASK_TRACED, corner[new])
+    np.testing.assert_array_equal(mq[new] == O.MASK_TRACED, (cat4 | corner)[new])
