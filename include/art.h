@@ -52,7 +52,7 @@ enum { ART_INTERP_LINEAR = 0, ART_INTERP_NEAREST = 1 };
 enum { ART_EDGE_ONESIDED = 0, ART_EDGE_TRACE = 1 };
 enum { ART_CRIT_I = 0, ART_CRIT_STOKES_ANY = 1 };
 enum { ART_FP64 = 0, ART_MIXED = 1, ART_FP32 = 2, ART_MIXED_DF = 3, ART_MIXED_EXACT = 4 };
-enum { ART_MASK_UNSET = 0, ART_MASK_TRACED = 1, ART_MASK_INTERP = 2 };
+enum { ART_MASK_UNSET = 0, ART_MASK_TRACED = 1, ART_MASK_INTERP = 2, ART_MASK_AXIS = 3 };
 enum { ART_RAY_ESCAPED = 0, ART_RAY_CAPTURED = 1, ART_RAY_CAP = 2, ART_RAY_NAN = 3 };
 
 /* One rendering problem: camera, spacetime, emission model and the refinement parameters of
@@ -133,7 +133,10 @@ typedef struct art_job {
      * magnitude of I's interpolant).  Ignored for stokes = 1; not with ART_MIXED_EXACT
      * (ART_ERR_UNSUPPORTED). */
     int32_t criterion;
-    int32_t criterion_pad;
+    /* The plane the criterion reads (default 0): with subring planes, criterion_plane = n * stokes
+     * decides on subring n's image (the paper renders each subring's image adaptively on its
+     * own, Sec. 5.1).  0 <= criterion_plane < art_planes(job); 0 with ART_CRIT_STOKES_ANY. */
+    int32_t criterion_plane;
 } art_job;
 
 /* Statistics of one render (host struct, filled on return). */
@@ -246,6 +249,33 @@ int art_render(art_ctx* ctx, const art_job* job, const double* truth_dev, double
 int art_render_batch(art_ctx* ctx, const art_job* jobs, int32_t n, double* const* imgs,
                      uint8_t* const* masks, art_stats* stats_host);
 
+/* Adaptive sampling along a third axis: frequency or time (Sec. 6 proposes extending the method
+ * "to selectively sample the time and frequency domains").  jobs[f], f = 0 .. F-1, is the problem
+ * at axis sample f (an observing frequency nu_hz, or a movie frame's snapshot); all jobs share the
+ * pixel grid and plane count.  F = 2^levels3 (F0 - 1) + 1.  The images of the base samples
+ * (f a multiple of 2^levels3) are rendered by art_render (adaptive in x and y).  Then, for
+ * k = 1 .. levels3, every new sample f (an odd multiple of s = 2^(levels3 - k)) is
+ * rendered with the spatial scheme of Sec. 3.2, and every point that scheme would trace is decided
+ * again along the axis with the same one-dimensional estimator, on plane 0: inner samples f -/+ s
+ * and outer f -/+ 3s of level k-1 (complete images; one-sided where one outer sample is missing,
+ * infinite where both are), eps_abs = |d| / (8 I_bar), eps_rel = |d| / (2 |S_in|) with I_bar the
+ * mean of the base samples' I_bar_int.  The point is traced with jobs[f] only if both exceed
+ * R_abs3, R_rel3 (strict); otherwise it receives the mean of its two axis neighbours in every plane
+ * (mask ART_MASK_AXIS).  A point is thus traced only where neither the spatial nor the axis
+ * interpolant is good enough.  The new samples' renders take no speculation (crit_band and the
+ * proposal are ignored there).
+ * imgs: HOST array of F device images (planes x ny x nx doubles), written.  truth (nullable): HOST
+ * array of F device images; if given, the axis logic alone runs on them: base samples copy
+ * truth[f] (their I_bar_int is that image's trapezoid mean), every pixel of a new sample is decided
+ * along the axis, and "tracing" copies from truth[f].  amask_dev (nullable): F x ny x nx bytes,
+ * the samples' masks (ART_MASK_TRACED / INTERP / AXIS; all TRACED for base samples with truth).
+ * stats_host (nullable): F entries (rays_traced = rays actually traced for the sample,
+ * border_points = its points interpolated along the axis).  Not with ART_MIXED_EXACT
+ * (ART_ERR_UNSUPPORTED).  Synchronises the context's stream.  Errors as art_render. */
+int art_render_axis(art_ctx* ctx, const art_job* jobs, int32_t F, int32_t levels3, double R_rel3,
+                    double R_abs3, const double* const* truth, double* const* imgs,
+                    uint8_t* amask_dev, art_stats* stats_host);
+
 /* Visibility-domain analysis (Sec. 4.3): the complex visibilities of one image plane, the 2-D
  * Fourier transform that an interferometer baseline (u, v) samples,
  *   V(u, v) = dx^2 sum_{x,y} T(x, y) A(x, y) exp(-2 pi i (u X + v Y)),
@@ -341,16 +371,19 @@ int art_measure_alu_peaks(art_ctx* ctx, double* fp32_tflops, double* fp64_tflops
  * a process whose device memory is reserved up front by its own allocator (a render service with
  * a fixed budget per GPU), code running while another framework owns allocation, or a caller that
  * must avoid the implicit synchronisation cudaMalloc and cudaFree can cause.  This call allocates
- * nothing and needs no context: it traces on the current device and on `stream` (a cudaStream_t,
- * NULL = legacy default stream), with the same arguments, output layout and precision handling as
- * art_trace_pixels.  Its scratch (camera, counters, FP64 re-trace queue) is one static device
+ * nothing and needs no context: it traces on the current device and on `stream` (a cudaStream_t
+ * of the current device, else ART_ERR_ARG; NULL = legacy default stream), with the same
+ * arguments, output layout and precision handling as art_trace_pixels.  Its scratch (camera, counters, FP64 re-trace queue) is one static device
  * array of about 4.2 MB, which every GPU that loads the library holds until the process exits.
  *   - n may be at most ART_NOALLOC_MAX_RAYS; larger n returns ART_ERR_ARG before any GPU work.
  *   - The first call on a device resolves the array's device address (cudaGetSymbolAddress) and
- *     the launch geometry; make that first call before any stream capture.
+ *     the launch geometry.
+ *   - Every call copies the ray count from the host stack to the array and synchronises `stream`
+ *     before returning, so a call cannot be made while `stream` is being captured into a CUDA
+ *     graph.
  *   - Every call shares the one array and clears its counters first; calls that overlap on the GPU
  *     (on different streams, or from several host threads) race on it and must be serialised.
- *   - Synchronises `stream` before returning.  Errors as art_trace_pixels. */
+ *   - Errors as art_trace_pixels. */
 #define ART_NOALLOC_MAX_RAYS (1 << 20)
 int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_dev, int64_t n,
                              double* out_dev, const art_rayaux* aux, void* stream);

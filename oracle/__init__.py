@@ -71,7 +71,7 @@ class Job(ctypes.Structure):
         ("glogr_min", ctypes.c_double), ("glogr_max", ctypes.c_double),
         ("gamma_ad", ctypes.c_double), ("m_unit", ctypes.c_double),
         ("r_high", ctypes.c_double), ("r_low", ctypes.c_double), ("sigma_cut", ctypes.c_double),
-        ("criterion", ctypes.c_int), ("cpad", ctypes.c_int),
+        ("criterion", ctypes.c_int), ("criterion_plane", ctypes.c_int),
     ]
 
 
@@ -93,7 +93,8 @@ _DEFAULTS = dict(a=0.0, mass=1.0, r_obs=1000.0, incl_deg=60.0, fov=40.0, n0x=33,
                  h_min=1e-4, horizon_eps=0.01, escape_frac=1.01, disk_w=0.3, blob_sigma=1.0,
                  ne0=0.0, thetae0=0.0, b0=0.0, nu_hz=230e9, ne_slope=-1.1, te_slope=-0.84,
                  r_in=0.0, length_cm=9.6e14, bz_ratio=1.0, gamma_ad=13.0 / 9.0, m_unit=1e27,
-                 r_high=20.0, r_low=1.0, sigma_cut=1.0, criterion=0)
+                 r_high=20.0, r_low=1.0, sigma_cut=1.0, criterion=0,
+                 criterion_plane=0)
 
 
 _NAMES = dict(

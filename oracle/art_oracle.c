@@ -1149,7 +1149,8 @@ int orc_refine_level(const orc_job* job, double* img, uint8_t* mask, int nx, int
             int cat = category(i, j, s);
             if (cat == 1) continue;
             double interp, ea, er;
-            int tr = estimate_point(job, img, nx, ny, i, j, s, norm, &interp, &ea, &er);
+            const double* dimg = img + (size_t)job->criterion_plane * npix;
+            int tr = estimate_point(job, dimg, nx, ny, i, j, s, norm, &interp, &ea, &er);
             if (!tr && job->criterion == ORC_CRIT_STOKES_ANY && job->stokes == 4)
                 for (int c = 1; c < 4 && !tr; ++c)
                     tr = plane_triggers(job, img, img + c * npix, nx, ny, i, j, s, norm);
@@ -1165,9 +1166,9 @@ int orc_refine_level(const orc_job* job, double* img, uint8_t* mask, int nx, int
                 continue;
             }
             mask[p] = ORC_MASK_INTERP;
-            img[p] = interp;
-            /* the other planes (Stokes Q, U, V; subrings) take the same interpolation weights */
-            for (int c = 1; c < planes; ++c) {
+            (void)interp;
+            /* every plane (I and Stokes Q, U, V; subrings) takes the same interpolation weights */
+            for (int c = 0; c < planes; ++c) {
                 const double* pl = img + c * npix;
                 double v;
                 if (job->interp == ORC_INTERP_NEAREST) {
@@ -1234,9 +1235,10 @@ int orc_render(const orc_job* job, const double* truth, double* img, uint8_t* ma
         if (level == 0) {
             if (job->abs_norm == ORC_NORM_PEAK) {
                 st.ibar = -INFINITY;
-                for (int64_t q = 0; q < n; ++q) st.ibar = fmax(st.ibar, vals[q * planes]);
+                for (int64_t q = 0; q < n; ++q)
+                    st.ibar = fmax(st.ibar, vals[q * planes + job->criterion_plane]);
             } else {
-                st.ibar = orc_ibar_int(img, nx, ny, S0);
+                st.ibar = orc_ibar_int(img + (size_t)job->criterion_plane * npix, nx, ny, S0);
             }
         }
     }

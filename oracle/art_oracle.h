@@ -66,7 +66,7 @@ typedef struct orc_job {
     double sigma_cut;    /* no emission where b^2/rho > sigma_cut */
     int criterion;       /* ORC_CRIT_I: decide on I; ORC_CRIT_STOKES_ANY: trace when the
                           * criterion holds for any of I, Q, U, V (stokes = 4) */
-    int cpad;
+    int criterion_plane; /* the plane the criterion reads (subring n: plane n * stokes) */
 } orc_job;
 enum { ORC_CRIT_I = 0, ORC_CRIT_STOKES_ANY = 1 };
 

@@ -21,14 +21,18 @@ on plane 0 (I), reading only samples of level k - 1.  I_bar is the mean over the
 their I_bar_int (the interpolated mean intensity of each base image's first pass), fixed for all
 levels like I_bar_int in Sec. 3.2.
 
-`render_axis` takes the jobs (oracle jobs, one per sample) or a truth cube whose samples stand in
-for the traces (the refinement logic alone).  Pinned by tests/test_oracle_axis.py.
+With a truth cube (the axis logic alone) every pixel of a new sample is decided along the axis.
+With jobs (`render_axis_jobs`) the axis is combined with the spatial scheme: a new sample's image
+is refined in x and y as in Sec. 3.2, and every point that scheme would trace is traced only if the
+axis estimate also asks for it; otherwise it receives the axis interpolant (mask AXIS = 3).  A
+point is then traced only where neither interpolant is good enough.  Pinned by
+tests/test_oracle_axis.py.
 """
 from __future__ import annotations
 
 import numpy as np
 
-MASK_TRACED, MASK_INTERP = 1, 2
+MASK_TRACED, MASK_INTERP, MASK_AXIS = 1, 2, 3
 
 
 def axis_decide(lo3, lo1, hi1, hi3, norm, R_rel, R_abs):
@@ -101,3 +105,69 @@ def render_axis(n_samples, levels3, R_rel3, R_abs3, truth=None, base_render=None
             amask[f] = np.where(tr, MASK_TRACED, MASK_INTERP)
             counts[f] = int(pix.size)
     return np.stack(cube), amask, counts, norm
+
+
+def render_axis_jobs(ojobs, levels3, R_rel3, R_abs3):
+    """The combined scheme with the oracle's tracer: ojobs[f] the oracle job of sample f (all with
+    the same pixel grid).  Returns (cube (F, planes, ny, nx), mask (F, ny, nx), rays traced per
+    sample, I_bar)."""
+    import oracle as O
+    F = len(ojobs)
+    S = 1 << levels3
+    if (F - 1) % S:
+        raise ValueError("F must be 2^levels3 (F0 - 1) + 1")
+    cube, masks, counts, norms = [None] * F, [None] * F, [0] * F, []
+    for f in range(0, F, S):
+        img, m, st = O.render(ojobs[f], None)
+        img = img if img.ndim == 3 else img[None]
+        cube[f], masks[f], counts[f] = img, m, st["rays_traced"]
+        norms.append(st["ibar"])
+    norm = float(np.mean(norms))
+    planes, ny, nx = cube[0].shape
+    for k in range(1, levels3 + 1):
+        s = 1 << (levels3 - k)
+        for f in range(s, F, 2 * s):
+            job = ojobs[f]
+            nan = np.full(ny * nx, np.nan)
+            lo1, hi1 = cube[f - s][0].ravel(), cube[f + s][0].ravel()
+            lo3 = cube[f - 3 * s][0].ravel() if f - 3 * s >= 0 else nan
+            hi3 = cube[f + 3 * s][0].ravel() if f + 3 * s < F else nan
+            axis_tr, _, _, _ = axis_decide(lo3, lo1, hi1, hi3, norm, R_rel3, R_abs3)
+            axis_val = 0.5 * (cube[f - s] + cube[f + s])
+            img = np.full((planes, ny, nx), np.nan)
+            mask = np.zeros((ny, nx), np.uint8)
+            N = job.levels
+            S0 = 1 << N
+
+            def settle(cand):
+                """Trace the candidates the axis also asks for; axis-interpolate the rest."""
+                keep = cand[axis_tr[cand]]
+                rest = cand[~axis_tr[cand]]
+                flat = img.reshape(planes, -1)
+                if keep.size:
+                    vals, _ = O.trace_pixels(job, keep.astype(np.int64))
+                    flat[:, keep] = vals.T
+                    mask.ravel()[keep] = MASK_TRACED
+                flat[:, rest] = axis_val.reshape(planes, -1)[:, rest]
+                mask.ravel()[rest] = MASK_AXIS
+                return int(keep.size)
+
+            jj, ii = np.mgrid[0:ny:S0, 0:nx:S0]
+            n_tr = settle((jj * nx + ii).ravel())
+            crit = img[job.criterion_plane]
+            lvl_norm = O.ibar_int(crit, S0)
+            for level in range(1, N + 1):
+                full = img if planes > 1 else img[0]
+                out, m2, _, _ = O.refine_level(job, full, mask, level, lvl_norm)
+                out = out if out.ndim == 3 else out[None]
+                sl = 1 << (N - level)
+                newpts = np.zeros((ny, nx), bool)
+                newpts[::sl, ::sl] = True
+                newpts[::2 * sl, ::2 * sl] = False
+                cand = np.flatnonzero((newpts & (m2 == MASK_TRACED)).ravel())
+                interp = newpts & (m2 == MASK_INTERP)
+                img[:, interp] = out[:, interp]
+                mask[interp] = MASK_INTERP
+                n_tr += settle(cand)
+            cube[f], masks[f], counts[f] = img, mask, n_tr
+    return np.stack(cube), np.stack(masks), counts, norm

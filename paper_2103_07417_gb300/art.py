@@ -17,7 +17,7 @@ from . import build as _build
 
 ART_OK, ART_ERR_ARG, ART_ERR_CUDA, ART_ERR_OOM, ART_ERR_UNSUPPORTED, ART_ERR_DEVICE = (
     0, -1, -2, -3, -4, -5)
-MASK_UNSET, MASK_TRACED, MASK_INTERP = 0, 1, 2
+MASK_UNSET, MASK_TRACED, MASK_INTERP, MASK_AXIS = 0, 1, 2, 3
 RAY_ESCAPED, RAY_CAPTURED, RAY_CAP, RAY_NAN = 0, 1, 2, 3
 
 _NAMES = dict(
@@ -49,7 +49,7 @@ class Job(ctypes.Structure):
         ("r_high", ctypes.c_double), ("r_low", ctypes.c_double), ("sigma_cut", ctypes.c_double),
         ("proposal", ctypes.c_int32), ("proposal_depth", ctypes.c_int32),
         ("proposal_p", ctypes.c_double), ("crit_band", ctypes.c_double),
-        ("criterion", ctypes.c_int32), ("criterion_pad", ctypes.c_int32),
+        ("criterion", ctypes.c_int32), ("criterion_plane", ctypes.c_int32),
     ]
 
 
@@ -88,7 +88,7 @@ class RayAux(ctypes.Structure):
 
 _JOB_DEFAULTS = dict(fp64_sweep=3.0 * 3.141592653589793, gamma_ad=13.0 / 9.0, m_unit=3e26,
                      r_high=20.0, r_low=1.0, sigma_cut=1.0, proposal=0, proposal_depth=2,
-                     proposal_p=0.5, crit_band=0.0, criterion=0, criterion_pad=0)
+                     proposal_p=0.5, crit_band=0.0, criterion=0, criterion_plane=0)
 
 
 def make_job(**params) -> Job:
@@ -115,7 +115,8 @@ EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_p
            "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid", "art_cnn_load",
            "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step",
            "art_cnn_sample", "art_set_tune", "art_get_tune", "art_autotune", "art_graph_render",
-           "art_graph_render_batch", "art_measure_alu_peaks", "art_visibilities")
+           "art_graph_render_batch", "art_measure_alu_peaks", "art_visibilities",
+           "art_render_axis")
 CNN_PARAMS = 28673
 NOALLOC_MAX_RAYS = 1 << 20
 
@@ -166,6 +167,8 @@ def load():
             lib.art_graph_render.argtypes = [vp, P(Job), vp, vp]
             lib.art_visibilities.argtypes = [vp, vp, vp, i32, i32, ctypes.c_double,
                                              ctypes.c_double, i32, vp]
+            lib.art_render_axis.argtypes = [vp, P(Job), i32, i32, ctypes.c_double,
+                                            ctypes.c_double, P(vp), P(vp), vp, P(Stats)]
             lib.art_graph_render_batch.argtypes = [vp, P(Job), i32, P(vp), P(vp)]
             _lib = lib
     return _lib
@@ -199,11 +202,28 @@ def _rayaux(aux):
                     for k in ("status", "steps", "nturn", "min_r")])
 
 
+def _check_trace_buffers(job: Job, pix, out, aux):
+    """The buffers a pixel trace writes must hold what the library writes there: int32 pixels,
+    float64 outputs of at least n x planes, int32/float32 aux arrays of at least n."""
+    import torch
+    n = pix.numel()
+    if pix.dtype != torch.int32:
+        raise ValueError("pix must be int32")
+    if out.dtype != torch.float64 or out.numel() < n * art_planes(job) or not out.is_contiguous():
+        raise ValueError("out must be contiguous float64 with at least n x planes elements")
+    for k, dt in (("status", torch.int32), ("steps", torch.int32), ("nturn", torch.int32),
+                  ("min_r", torch.float32)):
+        t = (aux or {}).get(k)
+        if t is not None and (t.dtype != dt or t.numel() < n):
+            raise ValueError(f"aux[{k!r}] must be {dt} with at least n elements")
+
+
 def art_trace_pixels_noalloc(job: Job, pix, out, aux: dict | None = None, stream=None) -> int:
     """The allocation-free tracer (no context; current device; `stream` a torch stream or None
     for torch's current stream).  Returns the C return code instead of raising, so callers can
     see the size rejection."""
     import torch
+    _check_trace_buffers(job, pix, out, aux)
     s = stream if stream is not None else torch.cuda.current_stream()
     ra = _rayaux(aux)
     return int(load().art_trace_pixels_noalloc(ctypes.byref(job), _dptr(pix), pix.numel(),
@@ -255,6 +275,7 @@ class Context:
 
     # -- C-ABI calls ---------------------------------------------------------------------
     def art_trace_pixels(self, job: Job, pix, out, aux: dict | None = None):
+        _check_trace_buffers(job, pix, out, aux)
         ra = None
         if aux is not None:
             ra = RayAux(*[ctypes.c_void_p(aux[k].data_ptr()) if aux.get(k) is not None else None
@@ -461,6 +482,30 @@ class Context:
         _check(load().art_visibilities(self._ctx, _dptr(img), _dptr(ref), nx, ny, float(dx),
                                        float(taper_fwhm), int(m), _dptr(out)), "art_visibilities")
         return torch.view_as_complex(out.view(m, m, 2))
+
+    def art_render_axis(self, jobs, levels3: int, R_rel3: float, R_abs3: float, imgs,
+                        amask=None, truth=None):
+        """Adaptive sampling along a third axis (frequency or time): jobs[f] per sample, imgs a
+        list of F device images (planes, ny, nx) float64 (written), amask (optional) an
+        (F, ny, nx) uint8 device tensor, truth (optional) a list of F device images.  Returns
+        the per-sample stats."""
+        import torch
+        n = len(jobs)
+        if len(imgs) != n or (truth is not None and len(truth) != n):
+            raise ValueError("one image (and truth image) per job")
+        for t in list(imgs) + list(truth or []):
+            if t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("images must be contiguous float64")
+        if amask is not None and (amask.dtype != torch.uint8 or amask.numel() < n * imgs[0][0].numel()):
+            raise ValueError("amask must be uint8 with F x ny x nx elements")
+        jarr = (Job * n)(*jobs)
+        iarr = (ctypes.c_void_p * n)(*[t.data_ptr() for t in imgs])
+        tarr = (ctypes.c_void_p * n)(*[t.data_ptr() for t in truth]) if truth is not None else None
+        st = (Stats * n)()
+        _check(load().art_render_axis(self._ctx, jarr, n, int(levels3), float(R_rel3),
+                                      float(R_abs3), tarr, iarr, _dptr(amask), st),
+               "art_render_axis")
+        return [_stats_dict(st[i], jobs[i].levels) for i in range(n)]
 
     def art_profile(self, enable: bool):
         _check(load().art_profile(self._ctx, int(bool(enable))), "art_profile")

@@ -71,6 +71,11 @@ struct art_ctx {
     int64_t vq_cap = 0;
     double* vtab = nullptr;
     int64_t vtab_cap = 0;
+    // third sampling axis (art_render_axis): device table of the samples' images, ray counts
+    double** atab = nullptr;
+    int64_t atab_cap = 0;
+    int32_t* aq = nullptr;  // a level's queue after the axis filter
+    int64_t aq_cap = 0;
     float* prob = nullptr;
     int64_t prob_cap = 0;
     // batched rendering tables and queue (grown, never shrunk)
@@ -93,6 +98,7 @@ struct art_ctx {
     // scratch owned by the library
     int32_t* queue = nullptr;
     int32_t* reroute = nullptr;
+    int32_t* reroute2 = nullptr;  // exact decisions: double-float rays handed on to FP64
     int64_t queue_cap = 0;
     unsigned long long* counters = nullptr;
     double* norm3 = nullptr;
@@ -220,6 +226,9 @@ static int make_devjob(const art_job* job, DevJob* J)
     if (job->precision < ART_FP64 || job->precision > ART_MIXED_EXACT) return ART_ERR_ARG;
     if (!(job->disk_w > 0.0)) return ART_ERR_ARG;
     if (job->criterion != ART_CRIT_I && job->criterion != ART_CRIT_STOKES_ANY) return ART_ERR_ARG;
+    if (job->criterion_plane < 0 || job->criterion_plane >= art_planes(job) ||
+        (job->criterion == ART_CRIT_STOKES_ANY && job->criterion_plane != 0))
+        return ART_ERR_ARG;
     if (job->criterion == ART_CRIT_STOKES_ANY && job->stokes == 4 &&
         job->precision == ART_MIXED_EXACT)
         return ART_ERR_UNSUPPORTED;
@@ -251,7 +260,7 @@ static int make_devjob(const art_job* job, DevJob* J)
     // exact decisions change the level loop only; the rays are traced as in ART_MIXED_DF
     J->precision = job->precision == ART_MIXED_EXACT ? ART_MIXED_DF : job->precision;
     J->criterion = job->criterion;
-    J->pad_ = 0;
+    J->cplane = job->criterion_plane;
     return ART_OK;
 }
 
@@ -263,6 +272,9 @@ constexpr double CERT_BAND = 2.5e-1;
 
 // Relative tolerances of the mixed modes' discontinuity flags (SynchConst::e_sig, e_rin).
 constexpr double EDGE_SIGMA_TOL = 1e-2, EDGE_RIN_TOL = 2e-3;
+// The same for the double-float re-trace of exact decisions, whose positions are accurate to
+// ~1e-14 but whose emission is evaluated in FP32 (~1e-6 relative in sigma).
+constexpr double EDGE_SIGMA_TOL_DF = 1e-5, EDGE_RIN_TOL_DF = 1e-6;
 
 // Constants of the synchrotron models in the scaled form the kernels use (cgs constants, CODATA).
 // g: the context's fluid grid (ART_EMIT_GRID), null where there is none.
@@ -381,6 +393,7 @@ extern "C" void art_destroy(art_ctx* c)
     if (c->gev_out) cudaEventDestroy(c->gev_out);
     cudaFree(c->queue);
     cudaFree(c->reroute);
+    cudaFree(c->reroute2);
     cudaFree(c->counters);
     cudaFree(c->norm3);
     cudaFree(c->cam);
@@ -415,6 +428,8 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFree(c->cfixq);
     cudaFree(c->vq);
     cudaFree(c->vtab);
+    cudaFree(c->atab);
+    cudaFree(c->aq);
     for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;
@@ -444,10 +459,12 @@ static int ensure_queue(art_ctx* c, int64_t cap)
     CK(cudaStreamSynchronize(c->stream));
     cudaFree(c->queue);
     cudaFree(c->reroute);
-    c->queue = c->reroute = nullptr;
+    cudaFree(c->reroute2);
+    c->queue = c->reroute = c->reroute2 = nullptr;
     c->queue_cap = 0;
     CK(cudaMalloc(&c->queue, sizeof(int32_t) * cap));
     CK(cudaMalloc(&c->reroute, sizeof(int32_t) * cap));
+    CK(cudaMalloc(&c->reroute2, sizeof(int32_t) * cap));
     c->queue_cap = cap;
     return ART_OK;
 }
@@ -482,7 +499,7 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
                        const unsigned long long* count, double* img, uint8_t* mask, double* out,
                        const art_rayaux* aux, float* pix_minr = nullptr, float* pix_turn = nullptr,
                        const unsigned long long* spec_from = nullptr,
-                       const int32_t* qbuf = nullptr)
+                       const int32_t* qbuf = nullptr, bool exact = false)
 {
     TraceArgs a;
     memset(&a, 0, sizeof a);
@@ -538,6 +555,14 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
         b.count = c->counters + C_REROUTE;
         b.fetch = c->counters + C_FETCH2;
         const bool dfp = J.precision == ART_MIXED_DF;
+        if (exact && dfp) {
+            // exact decisions: a double-float ray with a sample within FP32 rounding of a
+            // discontinuity (its emission is evaluated in FP32) is handed on to FP64
+            b.synch.e_sig = EDGE_SIGMA_TOL_DF;
+            b.synch.e_rin = EDGE_RIN_TOL_DF;
+            b.reroute = c->reroute2;
+            b.reroute_count = c->counters + C_REROUTE2;
+        }
         k = prof_begin(c);
         CK(launch_trace(b, dfp ? TK_DF : TK_FP64, dfp ? gdf : g64, c->stream));
         prof_end(c, k, dfp ? ART_K_TRACE_DF : ART_K_TRACE_FP64, -1);
@@ -618,8 +643,26 @@ extern "C" int art_refine_level(art_ctx* c, const art_job* job, double* img_dev,
     return ART_OK;
 }
 
+// The spatial level loop at a new sample of a third axis (art_render_axis): every level's queue
+// is filtered by the axis criterion, so a point is traced only where neither the spatial nor the
+// axis interpolant is good enough (the rest take the axis interpolant, mask ART_MASK_AXIS).
+struct AxisFilter {
+    double* const* atab;  // device table of the samples' images
+    int f, s, F;
+    double norm, R_rel, R_abs;
+};
+
+static int render_impl(art_ctx* c, const art_job* job, const double* truth_dev, double* img_dev,
+                       uint8_t* mask_dev, art_stats* stats, const AxisFilter* ax);
+
 extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_dev, double* img_dev,
                           uint8_t* mask_dev, art_stats* stats)
+{
+    return render_impl(c, job, truth_dev, img_dev, mask_dev, stats, nullptr);
+}
+
+static int render_impl(art_ctx* c, const art_job* job, const double* truth_dev, double* img_dev,
+                       uint8_t* mask_dev, art_stats* stats, const AxisFilter* ax)
 {
     if (!c || !img_dev) return ART_ERR_ARG;
     DevJob J;
@@ -634,6 +677,7 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
     const bool spec_any = learned || band;
     const bool cert = job->precision == ART_MIXED_EXACT;
     if (cert && truth_dev) return ART_ERR_ARG;
+    if (ax && (spec_any || cert || truth_dev || !mask_dev)) return ART_ERR_ARG;
     CK(cudaSetDevice(c->device));
     const int64_t cap = max_level_rays(J);
     // the learned path appends speculative rays of later levels to a level's queue
@@ -676,6 +720,16 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
     }
     DevJob J64 = J;
     J64.precision = ART_FP64;
+    if (ax && (rc = grow(c, c->aq, c->aq_cap, cap))) return rc;
+    // axis filter of the queue of `level` (counters[C_QUEUE]) into c->aq (counters[C_AXQ])
+    auto axis_filter = [&](int level) -> int {
+        int kk = prof_begin(c);
+        CK(launch_axis_filter(npix, J.planes, ax->atab, ax->f, ax->s, ax->F, ax->norm, ax->R_rel,
+                              ax->R_abs, c->queue, c->counters, c->aq, mask, c->num_sms, st));
+        prof_end(c, kk, ART_K_REFINE, -1);
+        (void)level;
+        return ART_OK;
+    };
     if (learned) {
         int64_t pc = 1;
         for (int lv = 0; lv + 2 <= J.levels; ++lv) pc = std::max(pc, cnn_head_cells(J, lv));
@@ -723,7 +777,37 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
             }
             prof_end(c, k, ART_K_REFINE, (int64_t)((J.nx - 1) / s + 1) * ((J.ny - 1) / s + 1));
             CK(launch_level_count(c->counters, level, st));
+            if (learned && level + 1 <= J.levels && (level - 1) % job->proposal_depth == 0) {
+                // every D = proposal_depth levels the network reads the completed level-(k-1)
+                // lattice and proposes points of levels k+1 .. k+D, traced now together with
+                // level k's rays; the D - 1 levels in between trace only what was not proposed
+                CK(launch_spec_mark(c->counters, st));
+                k = prof_begin(c);
+                CK(cnn_propose(c->cnn, J, level - 1, job->proposal_depth, img_dev, aminr, aturn,
+                               c->norm3,
+                               (float)job->proposal_p, c->prob, mask, c->queue, c->counters,
+                               (unsigned long long)qcap, st));
+                prof_end(c, k, ART_K_PROPOSE, -1);
+                CK(launch_queue_clamp(c->counters, (unsigned long long)qcap, st));
+                spec = true;
+            }
             if (cert) {
+                // the level's rays: FP32 (+ double-float, whose uncertain rays join the FP64
+                // queue), or FP64 on a degenerate image
+                CK(launch_cert_split(c->counters, st));
+                CK(cudaMemsetAsync(c->counters + C_REROUTE2, 0, sizeof(unsigned long long), st));
+                if ((rc = trace_queue(c, job, J, c->counters + C_QF32, img_dev, mask, nullptr,
+                                      nullptr, aminr, aturn,
+                                      spec ? c->counters + C_SPECFROM : nullptr, nullptr, true)))
+                    return rc;
+                if ((rc = trace_queue(c, job, J64, c->counters + C_QF64, img_dev, mask, nullptr,
+                                      nullptr, aminr, aturn)))
+                    return rc;
+                CK(launch_cert_mark_traced(c->queue, c->counters, (unsigned long long)qcap, c->xst,
+                                           st, C_QF64));
+                CK(launch_cert_take_uncertain(c->queue, c->reroute2, c->counters,
+                                              spec ? c->counters + C_SPECFROM : nullptr, mask,
+                                              c->cxq, xcap, st));
                 // the borderline points: exact stencils (FP64 re-traces, recomputed
                 // interpolants, coarsest level first), then their FP64 decisions
                 CK(launch_counter_clamp(c->counters, C_BORDER, bcap, st));
@@ -744,20 +828,6 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
                                         mask, c->xst, aminr, aturn, st));
                 prof_end(c, k, ART_K_OTHER, -1);
             }
-            if (learned && level + 1 <= J.levels && (level - 1) % job->proposal_depth == 0) {
-                // every D = proposal_depth levels the network reads the completed level-(k-1)
-                // lattice and proposes points of levels k+1 .. k+D, traced now together with
-                // level k's rays; the D - 1 levels in between trace only what was not proposed
-                CK(launch_spec_mark(c->counters, st));
-                k = prof_begin(c);
-                CK(cnn_propose(c->cnn, J, level - 1, job->proposal_depth, img_dev, aminr, aturn,
-                               c->norm3,
-                               (float)job->proposal_p, c->prob, mask, c->queue, c->counters,
-                               (unsigned long long)qcap, st));
-                prof_end(c, k, ART_K_PROPOSE, -1);
-                CK(launch_queue_clamp(c->counters, (unsigned long long)qcap, st));
-                spec = true;
-            }
         }
         if (truth_dev) {
             k = prof_begin(c);
@@ -777,11 +847,22 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
             prof_end(c, k, ART_K_OTHER, -1);
             if (spec) {
                 CK(launch_cert_spec_count(c->counters, st));
+                CK(cudaMemsetAsync(c->counters + C_REROUTE2, 0, sizeof(unsigned long long), st));
                 if ((rc = trace_queue(c, job, J, c->counters + C_SPECN, img_dev, mask, nullptr,
                                       nullptr, aminr, aturn, c->counters + C_ZERO,
-                                      c->queue + n0)))
+                                      c->queue + n0, true)))
                     return rc;
+                // speculative rays handed on to FP64 are traced at their own level instead
+                CK(launch_cert_take_uncertain(c->queue + n0, c->reroute2, c->counters,
+                                              c->counters + C_ZERO, mask, c->cxq, 0, st));
             }
+        } else if (cert) {
+            // traced above, before the exact decisions of the level's borderline points
+        } else if (ax) {
+            if ((rc = axis_filter(level))) return rc;
+            if ((rc = trace_queue(c, job, J, c->counters + C_AXQ, img_dev, mask, nullptr, nullptr,
+                                  aminr, aturn, nullptr, c->aq)))
+                return rc;
         } else {
             if ((rc = trace_queue(c, job, J, c->counters + C_QUEUE, img_dev, mask, nullptr, nullptr,
                                   aminr, aturn, spec ? c->counters + C_SPECFROM : nullptr)))
@@ -789,7 +870,9 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
         }
         if (level == 0) {
             k = prof_begin(c);
-            CK(launch_norm(J, img_dev, J.nx, J.ny, 1 << J.levels, c->norm3, st));
+            CK(launch_norm(J, img_dev + (int64_t)J.cplane * npix, J.nx, J.ny, 1 << J.levels,
+                           c->norm3, st));
+            if (cert) CK(launch_cert_check_norm(c->norm3, c->counters, st));
             prof_end(c, k, ART_K_OTHER, -1);
         }
     }
@@ -809,6 +892,12 @@ extern "C" int art_render(art_ctx* c, const art_job* job, const double* truth_de
         stats->kernel_launches = c->launches;
         stats->rays_speculative = (int64_t)c->pinned[C_SPEC];
         stats->rays_spec_used = (int64_t)c->pinned[C_SPECUSED];
+        if (ax) {
+            // rays actually traced: the axis filter's kept points (per level: queued minus
+            // axis-interpolated)
+            stats->rays_traced = (int64_t)c->pinned[C_AXKEPT];
+            stats->border_points = (int64_t)c->pinned[C_AXINTERP];
+        }
         if (cert) {
             stats->rays_exact = (int64_t)c->pinned[C_XRAYS] + stats->rays_per_level[0];
             stats->border_points = (int64_t)c->pinned[C_BTOT];
@@ -860,6 +949,98 @@ extern "C" int art_render_host(art_ctx* c, const art_job* job, double* img_host,
     } else {
         CK(cudaStreamSynchronize(c->stream));
     }
+    return ART_OK;
+}
+
+extern "C" int art_render_axis(art_ctx* c, const art_job* jobs, int32_t F, int32_t levels3,
+                               double R_rel3, double R_abs3, const double* const* truth,
+                               double* const* imgs, uint8_t* amask_dev, art_stats* stats)
+{
+    if (!c || !jobs || !imgs || F < 2 || levels3 < 1 || levels3 > 12) return ART_ERR_ARG;
+    const int S = 1 << levels3;
+    if ((F - 1) % S) return ART_ERR_ARG;
+    DevJob J0;
+    int rc = make_devjob(&jobs[0], &J0);
+    if (rc) return rc;
+    for (int f = 0; f < F; ++f) {
+        DevJob Jf;
+        if ((rc = make_devjob(&jobs[f], &Jf))) return rc;
+        if (Jf.nx != J0.nx || Jf.ny != J0.ny || Jf.planes != J0.planes) return ART_ERR_ARG;
+        if (jobs[f].precision == ART_MIXED_EXACT) return ART_ERR_UNSUPPORTED;
+        if (!imgs[f] || (truth && !truth[f])) return ART_ERR_ARG;
+        if (!truth && (rc = check_grid(c, &jobs[f]))) return rc;
+    }
+    CK(cudaSetDevice(c->device));
+    const int64_t npix = (int64_t)J0.nx * J0.ny;
+    if ((rc = ensure_fixed(c)) || (rc = ensure_queue(c, npix)) ||
+        (rc = grow(c, c->atab, c->atab_cap, (int64_t)F)))
+        return rc;
+    cudaStream_t st = c->stream;
+    if (stats) memset(stats, 0, sizeof(art_stats) * F);
+    // the base samples: the ordinary adaptive render (or the truth)
+    double nsum = 0.0;
+    int nbase = 0;
+    for (int f = 0; f < F; f += S) {
+        if (truth) {
+            CK(cudaMemcpyAsync(imgs[f], truth[f], sizeof(double) * npix * J0.planes,
+                               cudaMemcpyDeviceToDevice, st));
+            DevJob Jn = J0;
+            Jn.abs_norm = ART_NORM_IBAR_INT;
+            CK(launch_norm(Jn, truth[f], J0.nx, J0.ny, 1, c->norm3, st));
+            CK(cudaMemcpyAsync(c->pinned_d, c->norm3, sizeof(double) * 3, cudaMemcpyDeviceToHost,
+                               st));
+            CK(cudaStreamSynchronize(st));
+            nsum += c->pinned_d[0];
+            if (stats) stats[f].rays_traced = npix;
+            if (amask_dev)
+                CK(cudaMemsetAsync(amask_dev + (int64_t)f * npix, ART_MASK_TRACED, npix, st));
+        } else {
+            art_stats bs;
+            if ((rc = art_render(c, &jobs[f], nullptr, imgs[f],
+                                 amask_dev ? amask_dev + (int64_t)f * npix : nullptr, &bs)))
+                return rc;
+            nsum += bs.norm;
+            if (stats) stats[f] = bs;
+        }
+        ++nbase;
+    }
+    const double norm = nsum / nbase;
+    CK(cudaMemcpyAsync(c->atab, imgs, sizeof(double*) * F, cudaMemcpyHostToDevice, st));
+    for (int k = 1; k <= levels3; ++k) {
+        const int s = 1 << (levels3 - k);
+        for (int f = s; f < F; f += 2 * s) {
+            if (truth) {
+                // the axis logic alone: every pixel of the new sample decided along the axis
+                CK(cudaMemsetAsync(c->counters, 0, sizeof(unsigned long long) * C_COUNT, st));
+                int kp = prof_begin(c);
+                CK(launch_axis_refine(npix, J0.planes, c->atab, f, s, F, norm, R_rel3, R_abs3,
+                                      c->queue, c->counters + C_QUEUE, amask_dev, st));
+                prof_end(c, kp, ART_K_REFINE, npix);
+                CK(launch_gather_truth(J0, c->queue, c->counters + C_QUEUE, truth[f], imgs[f],
+                                       nullptr, npix, st));
+                if (stats) {
+                    if ((rc = read_counters(c))) return rc;
+                    stats[f].rays_traced = (int64_t)c->pinned[C_QUEUE];
+                    stats[f].norm = norm;
+                }
+                continue;
+            }
+            // the spatial scheme at sample f, each level's rays filtered by the axis criterion
+            art_job jf = jobs[f];
+            jf.crit_band = 0.0;
+            jf.proposal = 0;
+            uint8_t* mk = amask_dev ? amask_dev + (int64_t)f * npix : nullptr;
+            if (!mk) {
+                if ((rc = grow(c, c->smask, c->smask_cap, npix))) return rc;
+                mk = c->smask;
+            }
+            const AxisFilter axf{c->atab, f, s, F, norm, R_rel3, R_abs3};
+            art_stats fs;
+            if ((rc = render_impl(c, &jf, nullptr, imgs[f], mk, &fs, &axf))) return rc;
+            if (stats) stats[f] = fs;
+        }
+    }
+    if (!stats) CK(cudaStreamSynchronize(st));
     return ART_OK;
 }
 

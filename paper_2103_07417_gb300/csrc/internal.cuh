@@ -35,6 +35,13 @@ enum Counter {
     C_CERTOVF = 35,  // exact decisions: points decided without them (lists full)
     C_SPECN = 36,    // exact decisions: length of the speculative part of the base-level queue
     C_ZERO = 37,     // always 0
+    C_DEGEN = 38,    // exact decisions: the normalisation is outside FP32's range (all FP64)
+    C_QF32 = 39,     // exact decisions: rays of the level for the FP32 pass
+    C_QF64 = 40,     // exact decisions: rays of the level for the FP64 pass (degenerate images)
+    C_REROUTE2 = 41, // exact decisions: double-float rays handed on to FP64
+    C_AXQ = 42,      // third axis: length of the level's queue after the axis filter
+    C_AXKEPT = 43,   // third axis: rays kept by the filter (all levels)
+    C_AXINTERP = 44, // third axis: points interpolated along the axis (all levels)
     C_COUNT = 64
 };
 
@@ -42,7 +49,7 @@ enum Counter {
 // FP64 render's (FP64-traced, or interpolated from such values); claimed by the closure search.
 constexpr uint8_t XS_EXACT = 1, XS_CLAIM = 2;
 // Transient mask value of a borderline point whose decision waits for exact stencil values.
-constexpr uint8_t MASK_PENDING = 5;
+constexpr uint8_t MASK_PENDING = 10;
 
 struct TraceArgs {
     DevJob job;
@@ -74,7 +81,7 @@ struct TraceArgs {
 };
 
 // Transient mask values of the learned path (a render ends with every point TRACED or INTERP).
-constexpr uint8_t MASK_SPEC_PENDING = 3, MASK_SPEC_DONE = 4;
+constexpr uint8_t MASK_SPEC_PENDING = 8, MASK_SPEC_DONE = 9;
 
 // Batched rendering: the rays of many images share one queue whose entries are
 // (image << 32) | pixel; each image's job, synchrotron constants, camera and output live in tables.
@@ -157,7 +164,15 @@ cudaError_t launch_cert_closure(const DevJob& J, int level, const int32_t* borde
                                 unsigned long long xq_cap, uint64_t* fixq,
                                 unsigned long long fix_cap, cudaStream_t st);
 cudaError_t launch_cert_mark_traced(const int32_t* xq, unsigned long long* counters,
-                                    unsigned long long xq_cap, uint8_t* xst, cudaStream_t st);
+                                    unsigned long long xq_cap, uint8_t* xst, cudaStream_t st,
+                                    int count_idx = C_XQ);
+cudaError_t launch_cert_check_norm(const double* norm3, unsigned long long* counters,
+                                   cudaStream_t st);
+cudaError_t launch_cert_split(unsigned long long* counters, cudaStream_t st);
+cudaError_t launch_cert_take_uncertain(const int32_t* queue, const int32_t* reroute2,
+                                       unsigned long long* counters,
+                                       const unsigned long long* spec_from, uint8_t* mask,
+                                       int32_t* xq, unsigned long long xq_cap, cudaStream_t st);
 cudaError_t launch_cert_fixup(const DevJob& J, const uint64_t* fixq, unsigned long long* counters,
                               unsigned long long fix_cap, int lvl, double* img, uint8_t* xst,
                               cudaStream_t st);
@@ -167,6 +182,14 @@ cudaError_t launch_cert_redecide(const DevJob& J, int level, const double* norm,
                                  uint8_t* xst, float* aminr, float* aturn, cudaStream_t st);
 cudaError_t launch_counter_clamp(unsigned long long* counters, int idx, unsigned long long cap,
                                  cudaStream_t st);
+// refine.cu: a third sampling axis (art_render_axis)
+cudaError_t launch_axis_refine(int64_t npix, int planes, double* const* imgs, int f, int s, int F,
+                               double norm, double R_rel, double R_abs, int32_t* queue,
+                               unsigned long long* qcount, uint8_t* amask, cudaStream_t st);
+cudaError_t launch_axis_filter(int64_t npix, int planes, double* const* imgs, int f, int s, int F,
+                               double norm, double R_rel, double R_abs, const int32_t* queue,
+                               unsigned long long* counters, int32_t* out, uint8_t* mask,
+                               int num_sms, cudaStream_t st);
 cudaError_t launch_spec_mark(unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_queue_clamp(unsigned long long* counters, unsigned long long cap,
                                cudaStream_t st);

@@ -75,7 +75,7 @@ struct DevJob {
     double a, a2, r_obs, pix, step_frac, h_min, r_in_stop, r_out_stop, inv_2w2;
     double R_abs, R_rel, fp64_sweep;
     int32_t nx, ny, levels, emission, flow, stokes, subrings, planes, max_steps;
-    int32_t interp, edge_mode, abs_norm, precision, criterion, pad_;
+    int32_t interp, edge_mode, abs_norm, precision, criterion, cplane;
 };
 
 // Static camera: position and the covariant (lowered) tetrad E0 (observer), E1 (outward),
@@ -176,11 +176,26 @@ ART_HD R emission_analytic(const RayState<R>& s, R r, R kt, const DevJob& J)
 // Sign of d(theta)/d(lambda) from k_theta sin(theta) = (x k_x + y k_y) z/r - (r - z^2/r) k_z,
 // 0 inside a dead band of 1e-9 r (1e-5 r in FP32) so radial rays count no turns.
 template <class R>
+ART_HD R polar_q(const RayState<R>& s, R r)
+{
+    return fmad(s.y, s.ky, s.x * s.kx) * s.z / r - (r - s.z * s.z / r) * s.kz;
+}
+
+template <class R>
 ART_HD int polar_sign(const RayState<R>& s, R r)
 {
-    R q = fmad(s.y, s.ky, s.x * s.kx) * s.z / r - (r - s.z * s.z / r) * s.kz;
+    R q = polar_q<R>(s, r);
     R tol = R(sizeof(R) == 4 ? 1e-5 : 1e-9) * r;  // dead band above the rounding noise
     return q > tol ? 1 : (q < -tol ? -1 : 0);
+}
+
+// A sample whose turning-point quantity lies between the FP64 and the FP32 dead bands (x 10):
+// the two precisions may count that turn differently, which moves emission between subrings.
+template <class R>
+ART_HD bool polar_marginal(const RayState<R>& s, R r)
+{
+    const R q = polar_q<R>(s, r);
+    return fabs(q) < R(1e-4) * r && fabs(q) > R(1e-9) * r;
 }
 
 }  // namespace art

@@ -96,6 +96,15 @@ extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_d
     const DeviceSlot& s = g_slots[dev];
     if (s.rc != ART_OK) return s.rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (st) {
+        // the scratch array's address is this device's: a stream of another device is an error
+        int sdev = -1;
+        if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+            cudaGetLastError();
+            return ART_ERR_ARG;
+        }
+        if (sdev != dev) return ART_ERR_ARG;
+    }
 
     Camera* cam = reinterpret_cast<Camera*>(s.ptr + OFF_CAM);
     unsigned long long* counters = reinterpret_cast<unsigned long long*>(s.ptr + OFF_CNT);

@@ -554,15 +554,16 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
 {
     double w1, w2;
     IX p1, p2, p3, p4;
+    const double* dimg = img + (IX)J.cplane * npix;  // the plane the criterion reads
     // a uniform stencil decides "interpolate" exactly; under CERT only where the tolerance
     // leaves room for rounding of the values (R_abs > 0)
     const bool flat = sc.on && !sc.abs_any && J.interp == ART_INTERP_LINEAR &&
-                      (!CERT || J.R_abs > 0.0) && uniform_stencil<IX>(img, J.nx, J.ny, i, j, s, cat);
-    const int scr = flat ? 0 : screen_decide<IX>(sc, img, J.nx, J.ny, i, j, s, cat);
+                      (!CERT || J.R_abs > 0.0) && uniform_stencil<IX>(dimg, J.nx, J.ny, i, j, s, cat);
+    const int scr = flat ? 0 : screen_decide<IX>(sc, dimg, J.nx, J.ny, i, j, s, cat);
     bool trace;
     if (scr < 0) {
         double ea, er;
-        trace = decide<IX>(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4, ea, er);
+        trace = decide<IX>(J, dimg, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4, ea, er);
         if constexpr (CERT) {
             if (!decision_robust(J, ea, er, ca->band) && !stencil_exact(J, ca->xst, i, j, s, cat))
                 return 3;
@@ -633,6 +634,9 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     const Screen sc = sc_s;
     const int lane = threadIdx.x & 31;
+    // exact decisions on a degenerate image: every value is FP64 from here on, so a speculative
+    // (FP32) ray the criterion asks for is traced again
+    const bool spec_ok = counters != nullptr && !(CERT && cert_counters[C_DEGEN] != 0);
     for (int jj = blockIdx.y; jj < nky; jj += gridDim.y) {
         const int oj = jj & 1;
         for (int i0 = blockIdx.x * blockDim.x; i0 < nkx; i0 += gridDim.x * blockDim.x) {
@@ -647,8 +651,7 @@ __global__ void __launch_bounds__(256)
                     j = jj * s;
                     cat = (oi && oj) ? 4 : (oi ? 3 : 2);
                     const int r = refine_point<int, CERT>(J, sc, img, mask, i, j, s, cat, norm,
-                                                          npix, counters != nullptr, aminr, aturn,
-                                                          &ca);
+                                                          npix, spec_ok, aminr, aturn, &ca);
                     trace = r == 1;
                     used = r == 2;
                     bord = r == 3;
@@ -671,8 +674,8 @@ __global__ void __launch_bounds__(256)
                         } else {
                             atomicAdd(cert_counters + C_CERTOVF, 1ull);
                             const int r = refine_point<int, false>(J, sc, img, mask, i, j, s, cat,
-                                                                   norm, npix, counters != nullptr,
-                                                                   aminr, aturn);
+                                                                   norm, npix, spec_ok, aminr,
+                                                                   aturn);
                             trace = r == 1;
                             used = r == 2;
                         }
@@ -867,16 +870,82 @@ __global__ void cert_closure_kernel(DevJob J, const int32_t* border, const unsig
     }
 }
 
-// After the FP64 pass: its pixels are exact; C_XRAYS counts them.
+// After an FP64 pass: its pixels are exact; C_XRAYS counts them.
 __global__ void cert_mark_traced_kernel(const int32_t* xq, unsigned long long* counters,
-                                        unsigned long long xq_cap, uint8_t* xst)
+                                        unsigned long long xq_cap, uint8_t* xst, int count_idx)
 {
-    unsigned long long n = counters[C_XQ];
+    unsigned long long n = counters[count_idx];
     if (n > xq_cap) n = xq_cap;
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x)
         xst[xq[q]] = XS_EXACT;
     if (blockIdx.x == 0 && threadIdx.x == 0) counters[C_XRAYS] += n;
+}
+
+// An image whose normalisation lies far outside FP32's range (a plane that is dark at every
+// base point, say) has tolerances that FP32-traced values cannot resolve: its later levels are
+// traced in FP64 (C_DEGEN).
+constexpr double CERT_NORM_MIN = 1e-25, CERT_NORM_MAX = 1e25;
+
+__global__ void cert_check_norm_kernel(const double* norm3, unsigned long long* counters)
+{
+    const double n = fabs(norm3[0]);
+    counters[C_DEGEN] = (n >= CERT_NORM_MIN && n <= CERT_NORM_MAX) ? 0ull : 1ull;
+}
+
+// The level's queue goes to the FP32 pass, or to the FP64 pass on a degenerate image.
+__global__ void cert_split_kernel(unsigned long long* counters)
+{
+    const unsigned long long q = counters[C_QUEUE];
+    const bool d = counters[C_DEGEN] != 0;
+    counters[C_QF32] = d ? 0ull : q;
+    counters[C_QF64] = d ? q : 0ull;
+}
+
+// Double-float rays handed on to FP64 (slots of `queue` in reroute2): a speculative one
+// (slot at or beyond *spec_from) is left for its own level (mask unset); the others join the FP64
+// queue of this level's exact decisions.
+__global__ void cert_take_uncertain_kernel(const int32_t* queue, const int32_t* reroute2,
+                                           unsigned long long* counters,
+                                           const unsigned long long* spec_from, uint8_t* mask,
+                                           int32_t* xq, unsigned long long xq_cap)
+{
+    const unsigned long long n = counters[C_REROUTE2];
+    for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t slot = reroute2[q];
+        const int32_t p = queue[slot];
+        if (spec_from && (unsigned long long)slot >= *spec_from) {
+            mask[p] = ART_MASK_UNSET;
+            continue;
+        }
+        const unsigned long long w = atomicAdd(counters + C_XQ, 1ull);
+        if (w < xq_cap) xq[w] = p;
+        else atomicAdd(counters + C_CERTERR, 1ull);
+    }
+}
+
+cudaError_t launch_cert_take_uncertain(const int32_t* queue, const int32_t* reroute2,
+                                       unsigned long long* counters,
+                                       const unsigned long long* spec_from, uint8_t* mask,
+                                       int32_t* xq, unsigned long long xq_cap, cudaStream_t st)
+{
+    cert_take_uncertain_kernel<<<64, 256, 0, st>>>(queue, reroute2, counters, spec_from, mask, xq,
+                                                   xq_cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cert_check_norm(const double* norm3, unsigned long long* counters,
+                                   cudaStream_t st)
+{
+    cert_check_norm_kernel<<<1, 1, 0, st>>>(norm3, counters);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cert_split(unsigned long long* counters, cudaStream_t st)
+{
+    cert_split_kernel<<<1, 1, 0, st>>>(counters);
+    return cudaGetLastError();
 }
 
 // Recompute the interpolants of the listed points of level `lvl` from their (now exact) parents.
@@ -930,7 +999,8 @@ __global__ void cert_redecide_kernel(DevJob J, int level, const double* __restri
         if (!stencil_exact(J, xst, i, j, s, cat)) atomicAdd(counters + C_CERTERR, 1ull);
         double w1, w2, ea, er;
         int p1, p2, p3, p4;
-        bool tr = decide<int>(J, img, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4, ea, er);
+        bool tr = decide<int>(J, img + (int64_t)J.cplane * npix, i, j, s, norm, cat, w1, w2, p1,
+                              p2, p3, p4, ea, er);
         if (J.edge_mode == ART_EDGE_TRACE) {
             const int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
             if (i - 3 * di < 0 || i + 3 * di >= J.nx || j - 3 * dj < 0 || j + 3 * dj >= J.ny)
@@ -994,9 +1064,11 @@ cudaError_t launch_cert_closure(const DevJob& J, int level, const int32_t* borde
 }
 
 cudaError_t launch_cert_mark_traced(const int32_t* xq, unsigned long long* counters,
-                                    unsigned long long xq_cap, uint8_t* xst, cudaStream_t st)
+                                    unsigned long long xq_cap, uint8_t* xst, cudaStream_t st,
+                                    int count_idx)
 {
-    cert_mark_traced_kernel<<<cert_grid(xq_cap), 256, 0, st>>>(xq, counters, xq_cap, xst);
+    cert_mark_traced_kernel<<<cert_grid(xq_cap), 256, 0, st>>>(xq, counters, xq_cap, xst,
+                                                               count_idx);
     return cudaGetLastError();
 }
 
@@ -1115,8 +1187,8 @@ __global__ void __launch_bounds__(NORM_THREADS)
     norm_batch_kernel(const DevJob* jobs, double* const* imgs, double* norms)
 {
     const DevJob& J = jobs[blockIdx.x];
-    const double* img = imgs[blockIdx.x];
     const int stride = 1 << J.levels, nx = J.nx, ny = J.ny;
+    const double* img = imgs[blockIdx.x] + (int64_t)J.cplane * nx * ny;  // the criterion's plane
     const int n0x = (nx - 1) / stride + 1, n0y = (ny - 1) / stride + 1;
     const int64_t n = (int64_t)n0x * n0y;
     double s = 0.0, w = 0.0, mx = -INFINITY;
@@ -1232,6 +1304,160 @@ cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_kx
     if (gy < 1) gy = 1;
     refine_batch_kernel<<<dim3(gx, gy, n), 256, 0, st>>>(jobs, level, norms, imgs, masks, queue,
                                                          qcount, img_counts, spec_counters);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------------------------------------
+// A third sampling axis (frequency or time; Sec. 6 proposes adaptive sampling there): the new
+// samples of one level of the axis are decided per pixel with the one-dimensional estimator of
+// Sec. 3.2 along the axis (the category 2/3 form: inner samples f -/+ s, outer f -/+ 3s, one-sided
+// where one outer sample is missing, infinite where both are), normalised by the mean I_bar_int of
+// the base samples; interpolated pixels receive the mean of their two axis neighbours in every
+// plane, traced ones join the ray queue.
+// --------------------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256)
+    axis_refine_kernel(int64_t npix, int planes, double* const* imgs, int f, int s, int F,
+                       double norm, double R_rel, double R_abs, int32_t* queue,
+                       unsigned long long* qcount, uint8_t* amask)
+{
+    const double* lo1 = imgs[f - s];
+    const double* hi1 = imgs[f + s];
+    const double* lo3 = f - 3 * s >= 0 ? imgs[f - 3 * s] : nullptr;
+    const double* hi3 = f + 3 * s < F ? imgs[f + 3 * s] : nullptr;
+    double* out = imgs[f];
+    const int lane = threadIdx.x & 31;
+    for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < npix;
+         b0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = b0 + threadIdx.x;
+        bool trace = false;
+        if (p < npix) {
+            const double a1 = __ldg(lo1 + p), b1 = __ldg(hi1 + p);
+            double d = 0.0;
+            bool none = false;
+            if (lo3 && hi3) d = ((__ldg(lo3 + p) - a1) - b1) + __ldg(hi3 + p);
+            else if (lo3) d = 2.0 * ((__ldg(lo3 + p) - 2.0 * a1) + b1);
+            else if (hi3) d = 2.0 * ((__ldg(hi3 + p) - 2.0 * b1) + a1);
+            else none = true;
+            const double sin_ = a1 + b1;
+            const double num = fabs(d) / 8.0, den = fabs(sin_) / 2.0;
+            double ea, er;
+            if (none) {
+                ea = er = INFINITY;
+            } else {
+                ea = num / norm;
+                er = den == 0.0 ? (num == 0.0 ? 0.0 : INFINITY) : num / den;
+            }
+            trace = (ea > R_abs) && (er > R_rel);
+            if (isnan(ea) || isnan(er) || isnan(sin_)) trace = true;
+            if (!trace) {
+                for (int c = 0; c < planes; ++c) {
+                    const double v1 = __ldg(lo1 + c * npix + p), v2 = __ldg(hi1 + c * npix + p);
+                    const long long bb = __double_as_longlong(v1);
+                    out[c * npix + p] = (bb == __double_as_longlong(v2) && ((bb >> 52) & 0x7ff) < 0x7fc)
+                                            ? v1
+                                            : scale_pow2(v1 + v2, 1);
+                }
+            }
+            if (amask) amask[(int64_t)f * npix + p] = trace ? ART_MASK_TRACED : ART_MASK_INTERP;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, trace);
+        if (bal) {
+            unsigned long long w = 0;
+            if (lane == 0) w = atomicAdd(qcount, (unsigned long long)__popc(bal));
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (trace) queue[w + __popc(bal & ((1u << lane) - 1u))] = (int32_t)p;
+        }
+    }
+}
+
+cudaError_t launch_axis_refine(int64_t npix, int planes, double* const* imgs, int f, int s, int F,
+                               double norm, double R_rel, double R_abs, int32_t* queue,
+                               unsigned long long* qcount, uint8_t* amask, cudaStream_t st)
+{
+    int64_t g = (npix + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    if (g < 1) g = 1;
+    axis_refine_kernel<<<(int)g, 256, 0, st>>>(npix, planes, imgs, f, s, F, norm, R_rel, R_abs,
+                                               queue, qcount, amask);
+    return cudaGetLastError();
+}
+
+// The axis estimate of pixel p at sample f (as axis_refine_kernel); true when it asks for a ray.
+__device__ __forceinline__ bool axis_wants(double* const* imgs, int f, int s, int F, int64_t p,
+                                           double norm, double R_rel, double R_abs)
+{
+    const double a1 = __ldg(imgs[f - s] + p), b1 = __ldg(imgs[f + s] + p);
+    const bool lo = f - 3 * s >= 0, hi = f + 3 * s < F;
+    if (!lo && !hi) return true;  // infinite estimate
+    double d;
+    if (lo && hi) d = ((__ldg(imgs[f - 3 * s] + p) - a1) - b1) + __ldg(imgs[f + 3 * s] + p);
+    else if (lo) d = 2.0 * ((__ldg(imgs[f - 3 * s] + p) - 2.0 * a1) + b1);
+    else d = 2.0 * ((__ldg(imgs[f + 3 * s] + p) - 2.0 * b1) + a1);
+    const double sin_ = a1 + b1;
+    const double num = fabs(d) / 8.0, den = fabs(sin_) / 2.0;
+    const double ea = num / norm;
+    const double er = den == 0.0 ? (num == 0.0 ? 0.0 : INFINITY) : num / den;
+    bool trace = (ea > R_abs) && (er > R_rel);
+    if (isnan(ea) || isnan(er) || isnan(sin_)) trace = true;
+    return trace;
+}
+
+// The spatial queue of one level at a new axis sample f (counters[C_QUEUE] pixels): the pixels
+// the axis estimate also asks for are kept (compacted into `out`, counters[C_AXQ]); the others
+// receive the axis interpolant in every plane (mask ART_MASK_AXIS).
+__global__ void __launch_bounds__(256)
+    axis_filter_kernel(int64_t npix, int planes, double* const* imgs, int f, int s, int F,
+                       double norm, double R_rel, double R_abs, const int32_t* queue,
+                       unsigned long long* counters, int32_t* out, uint8_t* mask)
+{
+    const unsigned long long n = counters[C_QUEUE];
+    const int lane = threadIdx.x & 31;
+    double* dst = imgs[f];
+    unsigned long long kept = 0, interp = 0;
+    for (unsigned long long b0 = (unsigned long long)blockIdx.x * blockDim.x; b0 < n;
+         b0 += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long q = b0 + threadIdx.x;
+        bool keep = false;
+        int32_t p = 0;
+        if (q < n) {
+            p = queue[q];
+            keep = axis_wants(imgs, f, s, F, p, norm, R_rel, R_abs);
+            if (!keep) {
+                for (int c = 0; c < planes; ++c) {
+                    const double v1 = __ldg(imgs[f - s] + c * npix + p);
+                    const double v2 = __ldg(imgs[f + s] + c * npix + p);
+                    const long long bb = __double_as_longlong(v1);
+                    dst[c * npix + p] = (bb == __double_as_longlong(v2) && ((bb >> 52) & 0x7ff) < 0x7fc)
+                                            ? v1
+                                            : scale_pow2(v1 + v2, 1);
+                }
+                if (mask) mask[p] = ART_MASK_AXIS;
+                ++interp;
+            }
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        if (bal) {
+            unsigned long long w = 0;
+            if (lane == 0) w = atomicAdd(counters + C_AXQ, (unsigned long long)__popc(bal));
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (keep) out[w + __popc(bal & ((1u << lane) - 1u))] = p;
+        }
+        kept += keep ? 1 : 0;
+    }
+    if (kept) atomicAdd(counters + C_AXKEPT, kept);
+    if (interp) atomicAdd(counters + C_AXINTERP, interp);
+}
+
+cudaError_t launch_axis_filter(int64_t npix, int planes, double* const* imgs, int f, int s, int F,
+                               double norm, double R_rel, double R_abs, const int32_t* queue,
+                               unsigned long long* counters, int32_t* out, uint8_t* mask,
+                               int num_sms, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(counters + C_AXQ, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    axis_filter_kernel<<<num_sms * 8, 256, 0, st>>>(npix, planes, imgs, f, s, F, norm, R_rel,
+                                                     R_abs, queue, counters, out, mask);
     return cudaGetLastError();
 }
 

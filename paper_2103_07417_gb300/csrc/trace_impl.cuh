@@ -479,6 +479,9 @@ __device__ __forceinline__ void xfer_apply(XferState<Q>& t, const StepPoint<Q>& 
     int seg = t.nturn;
     if (t.oz * q.z < Q(0)) t.crossed = 1;
     int sg = polar_sign<Q>(q, rn);
+    // subring planes: a turn counted differently in another precision moves emission between
+    // planes; the mixed modes hand such rays on (FP32 -> double-float -> FP64)
+    if (J.subrings > 0 && polar_marginal<Q>(q, rn)) t.edge = 1;
     if (sg != 0) {
         if (t.crossed && t.tsign != 0 && sg != t.tsign) ++t.nturn;
         t.tsign = sg;

@@ -247,14 +247,15 @@ def test_render_fp64_matches_oracle(ctx, name, params):
     ref_img, ref_mask, ref_st = O.render(oj, None)
     assert abs(st["norm"] - ref_st["ibar"]) <= 1e-12 * abs(ref_st["ibar"])
     same = gm == ref_mask
+    print(name, "mask differences", int((~same).sum()))
     if not same.all():
-        # decisions may differ only where the oracle's estimate is within 1e-4 of a tolerance
+        # decisions may differ only where the oracle's estimate is within 1e-9 of a tolerance (observed: none)
         _, _, ea, er = _estimates_at_final(oj, ref_img, ref_mask, ref_st["ibar"])
         d = ~same
-        near = ((np.abs(ea[d] - oj.R_abs) <= 1e-4 * oj.R_abs)
-                | (np.abs(er[d] - oj.R_rel) <= 1e-4 * oj.R_rel))
-        assert near.all(), name
-    assert (~same).sum() <= max(2, 1e-3 * gm.size)
+        dist = np.minimum(np.abs(ea[d] / oj.R_abs - 1.0), np.abs(er[d] / oj.R_rel - 1.0))
+        print(name, "relative distance of the oracle's estimates from a tolerance", dist)
+        assert (dist <= 1e-9).all(), name
+    assert (~same).sum() <= 2
     bad = _close(gi[same], ref_img[same])
     assert bad.sum() == 0, name
     assert abs(st["rays_traced"] - ref_st["rays_traced"]) <= (~same).sum()

@@ -167,15 +167,14 @@ def test_stokes_any_refine_matches_oracle(interp):
     from paper_2103_07417_gb300 import art
     ctx = art.Context(0)
     levels = 3
-    base = dict(n0x=17, n0y=13, levels=levels, R_abs=2e-3, R_rel=5e-3, stokes=4,
-                emission="synch_disk", interp=interp)
-    nx, ny = art.art_image_size(art.make_job(**W.job(**base)))
+    base = dict(n0x=17, n0y=13, levels=levels, R_abs=2e-3, R_rel=5e-3, interp=interp)
+    nx, ny = art.art_image_size(art.make_job(**W.kerr_disk_2049(**base)))
     truth = np.stack([W.smooth_image(5, nx, ny), 0.3 * W.ring_image(6, nx, ny),
                       -0.2 * W.smooth_image(7, nx, ny, noise=0.05), 0.05 * W.ring_image(8, nx, ny)])
     norm = float(truth[0].mean())
     counts = {}
     for crit in ("I", "stokes_any"):
-        params = W.job(**base, criterion=crit)
+        params = W.kerr_disk_2049(**base, criterion=crit)
         job, ojob = art.make_job(**params), O.make_job(**params)
         tot = 0
         for level in range(1, levels + 1):

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from oracle import axis as A
+from paper_2103_07417_gb300 import workloads as W
 
 
 def _cube(fun, F=17, ny=5, nx=6):
@@ -64,3 +65,32 @@ def test_missing_outer_samples_take_the_one_sided_rule():
     lo3, lo1, hi1, hi3 = np.nan, 0.0, 8.0, 64.0   # f = 1 of 0..4 at s = 1: outer sample f = 4
     tr, interp, ea, er = A.axis_decide([np.nan], [0.0], [8.0], [64.0], 1.0, 0.0, 0.0)
     assert ea[0] == 2.0 * abs((64.0 - 2 * 8.0) + 0.0) / 8.0
+
+
+def test_combined_scheme_reduces_to_the_spatial_render_when_the_axis_always_asks():
+    """With R3 = -1 the axis estimate asks for every point, so each new sample is exactly the
+    plain adaptive render of its own job (traced points equal the truth, interpolants the stated
+    means); base samples are plain renders too."""
+    import oracle as O
+    params = [W.schwarzschild_129(n0x=5, n0y=5, levels=2, R_rel=1e-2, R_abs=1e-3,
+                                  step_frac=0.05 + 0.01 * f) for f in range(5)]
+    ojobs = [O.make_job(**p) for p in params]
+    cube, mask, counts, _ = A.render_axis_jobs(ojobs, 2, -1.0, -1.0)
+    for f in range(5):
+        ref, rmask, st = O.render(ojobs[f], None)
+        np.testing.assert_array_equal(cube[f, 0], ref)
+        np.testing.assert_array_equal(mask[f], rmask)
+        assert counts[f] == st["rays_traced"]
+
+
+def test_combined_scheme_interpolates_along_the_axis_when_it_is_linear():
+    """Jobs whose images are exactly linear in the sample index (a truth-like synthetic check
+    through the same code path is not available for traced jobs): with R3 = +inf the axis never
+    asks, so every point the spatial scheme would trace at a new sample takes the axis mean."""
+    import oracle as O
+    params = [W.schwarzschild_129(n0x=5, n0y=5, levels=1, R_rel=-1.0, R_abs=-1.0,
+                                  step_frac=0.05 + 0.01 * f) for f in range(3)]
+    ojobs = [O.make_job(**p) for p in params]
+    cube, mask, counts, _ = A.render_axis_jobs(ojobs, 1, np.inf, np.inf)
+    np.testing.assert_array_equal(cube[1], 0.5 * (cube[0] + cube[2]))
+    assert (mask[1] == A.MASK_AXIS).all() and counts[1] == 0

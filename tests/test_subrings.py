@@ -116,3 +116,87 @@ def test_subring_planes_match_oracle_gpu(params):
     assert (np.abs(g - ref) <= lim[:, None]).all()
     assert (aux["nturn"].cpu().numpy() == info["nturn"]).mean() > 0.999
     ctx.close()
+
+
+@pytest.mark.gpu
+def test_subring_fluxes_narrow_by_the_lyapunov_factor_gpu():
+    """Subrings at high resolution through the adaptive path (Sec. 5.1): a face-on Kerr thin disk
+    (a = 0.94) rendered 129^2 -> 4097^2 over 5 levels with subring planes n = 0..3, each subring's
+    image refined on its own plane (criterion_plane = n, as the paper renders every subring
+    adaptively).  Each subring is the previous one compressed towards the critical curve by
+    exp(-gamma) at about the same surface brightness, so the flux of subring n + 1 over subring n
+    is near exp(-gamma) (gamma of the lambda = 0 photon orbit, pinned above); the adaptive
+    subring images hold the full trace's flux; sampled traced pixels match the oracle's FP64
+    trace of the same rays in every plane."""
+    torch = pytest.importorskip("torch")
+    from paper_2103_07417_gb300 import art
+    a = 0.94
+    gamma = _lyapunov_face_on(a)
+    p = W.schwarzschild_129(a=a, incl_deg=0.1, disk_w=0.02, subrings=4, r_obs=1.0e4,
+                            step_frac=0.02, fov=10.5, n0x=129, n0y=129, levels=5, R_rel=1e-3,
+                            R_abs=1e-4, precision="mixed_df", crit_band=0.03)
+    ctx = art.Context(0)
+    flux, rays, img2, mask2 = [], [], None, None
+    for n in range(3):
+        img, mask, st = ctx.render(art.make_job(**{**p, "criterion_plane": n}))
+        flux.append(float(img[n].double().sum()))
+        rays.append(st["rays_traced"])
+        if n == 2:
+            img2, mask2 = img.cpu().numpy(), mask.cpu().numpy()
+        del img, mask
+    flux = np.array(flux)
+    full, _, fst = ctx.render(art.make_job(**{**p, "R_rel": -1.0, "R_abs": -1.0, "crit_band": 0.0}))
+    ffull = full.double().sum(dim=(1, 2)).cpu().numpy()
+    del full
+    r = flux[1:] / flux[:-1]
+    rf = ffull[1:] / ffull[:-1]
+    # the n = 3 ring (~2e-3 M, under a pixel of 4097^2) is thinner than every level's sample
+    # spacing but the finest: refined from a 129^2 base its samples rarely hit it, so its image
+    # is taken from a 1025^2 base (2 levels) and reported against the full trace
+    img3, _, st3 = ctx.render(art.make_job(**{**p, "criterion_plane": 3, "n0x": 1025, "n0y": 1025,
+                                              "levels": 2}))
+    f3 = float(img3[3].double().sum())
+    del img3
+    print("subring fluxes", flux, "n=3 from a 1025^2 base", f3, "full trace", ffull,
+          "adaptive ratios", r, "full-trace ratios", rf, "exp(-gamma)", np.exp(-gamma),
+          "rays", rays, st3["rays_traced"], "of", fst["rays_traced"])
+    np.testing.assert_allclose(flux, ffull[:3], rtol=2e-2)
+    np.testing.assert_allclose(r[1], np.exp(-gamma), rtol=5e-2)      # n = 1 -> 2, adaptive
+    np.testing.assert_allclose(rf[1:], np.exp(-gamma), rtol=5e-2)    # n = 1 -> 2 -> 3, full trace
+    # sampled traced pixels of the n = 2 image: FP64 GPU trace against the oracle, every plane
+    cand = np.flatnonzero((mask2.ravel() == art.MASK_TRACED) & (img2[2].ravel() > 0))
+    rng = np.random.default_rng(0)
+    pix = np.sort(rng.choice(cand, size=min(200, cand.size), replace=False)).astype(np.int32)
+    p64 = {**p, "precision": "fp64"}
+    out, _ = ctx.trace_pixels(art.make_job(**p64), torch.from_numpy(pix).cuda())
+    ref, _ = O.trace_pixels(O.make_job(**p64), pix.astype(np.int64))
+    tot = ref.sum(axis=1)
+    assert (np.abs(out.cpu().numpy() - ref) <= 2e-6 * np.maximum(tot, 1e-6 * tot.max())[:, None]).all()
+    ctx.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("plane", [0, 1, 2])
+def test_criterion_plane_refines_on_the_chosen_plane(plane):
+    """The criterion reading one chosen plane (subring n) on a precomputed three-plane image: the
+    GPU level loop equals the oracle's -- masks, and every plane's interpolants bit for bit."""
+    torch = pytest.importorskip("torch")
+    from paper_2103_07417_gb300 import art
+    params = W.schwarzschild_129(n0x=17, n0y=13, levels=3, subrings=3, criterion_plane=plane,
+                                 R_rel=2e-3, R_abs=1e-3)
+    job = art.make_job(**params)
+    nx, ny = art.art_image_size(job)
+    truth = np.stack([W.ring_image(4, nx, ny), W.smooth_image(5, nx, ny, noise=0.02),
+                      0.1 * W.ring_image(6, nx, ny)])
+    ctx = art.Context(0)
+    img = torch.empty((3, ny, nx), dtype=torch.float64, device="cuda")
+    mask = torch.empty((ny, nx), dtype=torch.uint8, device="cuda")
+    ctx.art_render(job, img, mask, truth=torch.from_numpy(truth).cuda())
+    ref, rmask, _ = O.render(O.make_job(**params), truth)
+    np.testing.assert_array_equal(mask.cpu().numpy(), rmask)
+    np.testing.assert_array_equal(img.cpu().numpy(), ref)
+    others = [p for p in range(3) if p != plane]
+    # choosing another plane changes the decisions
+    ref2, rmask2, _ = O.render(O.make_job(**{**params, "criterion_plane": others[0]}), truth)
+    assert (rmask2 != rmask).any()
+    ctx.close()

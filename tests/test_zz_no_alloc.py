@@ -22,11 +22,17 @@ def _close(got, ref):
 
 
 def test_noalloc_matches_context_tracer_on_consecutive_calls():
+    """Unpolarized analytic jobs in FP64 and mixed precision, then the polarized synchrotron disk
+    (Stokes I, Q, U, V; its constants are made without a context) in mixed precision with the
+    double-float re-trace and in FP64: every plane against the context's tracer, call after
+    call on the same static scratch."""
     from paper_2103_07417_gb300 import art
     ctx = art.Context(0)
     cases = [W.schwarzschild_129(a=0.94, incl_deg=17.0, n0x=17, n0y=13, levels=2, precision="fp64"),
-             W.schwarzschild_129(a=0.94, incl_deg=17.0, n0x=17, n0y=13, levels=2, precision="mixed")]
-    for params in cases:                      # two calls in a row on the same static scratch
+             W.schwarzschild_129(a=0.94, incl_deg=17.0, n0x=17, n0y=13, levels=2, precision="mixed"),
+             W.kerr_disk_2049(n0x=17, n0y=13, levels=2, precision="mixed_df", crit_band=0.0),
+             W.kerr_disk_2049(n0x=17, n0y=13, levels=2, precision="fp64", crit_band=0.0)]
+    for params in cases:                      # calls in a row on the same static scratch
         job = art.make_job(**params)
         nx, ny = art.art_image_size(job)
         rng = np.random.default_rng(5)
@@ -37,8 +43,12 @@ def test_noalloc_matches_context_tracer_on_consecutive_calls():
         rc = art.art_trace_pixels_noalloc(job, pix, out, aux={"steps": steps})
         assert rc == art.ART_OK, art.art_strerror(rc)
         torch.cuda.synchronize()
-        got, want = out.cpu().numpy()[:, 0], ref.cpu().numpy()[:, 0]
-        assert _close(got, want).all()
+        got, want = out.cpu().numpy(), ref.cpu().numpy()
+        assert _close(got[:, 0], want[:, 0]).all()
+        # Q, U, V on the scale of the pixel's I
+        scale = np.maximum(np.abs(want[:, 0]), 1e-6 * np.abs(want[:, 0]).max())
+        for c in range(1, want.shape[1]):
+            assert (np.abs(got[:, c] - want[:, c]) <= RTOL * scale).all(), c
         assert (steps.cpu().numpy() > 0).all()
     ctx.close()
 
