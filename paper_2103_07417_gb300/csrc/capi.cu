@@ -499,7 +499,8 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
                        const unsigned long long* count, double* img, uint8_t* mask, double* out,
                        const art_rayaux* aux, float* pix_minr = nullptr, float* pix_turn = nullptr,
                        const unsigned long long* spec_from = nullptr,
-                       const int32_t* qbuf = nullptr, bool exact = false)
+                       const int32_t* qbuf = nullptr, bool exact = false,
+                       bool skip_retrace = false)
 {
     TraceArgs a;
     memset(&a, 0, sizeof a);
@@ -546,7 +547,7 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
     k = prof_begin(c);
     CK(launch_trace(a, TK_FP32, g32, c->stream));
     prof_end(c, k, ART_K_TRACE_FP32, -1);
-    if (mixed) {
+    if (mixed && !skip_retrace) {
         // high-precision re-trace of the near-critical rays the FP32 pass routed
         TraceArgs b = a;
         b.reroute = nullptr;
@@ -795,17 +796,20 @@ static int render_impl(art_ctx* c, const art_job* job, const double* truth_dev, 
                 // the level's rays: FP32 (+ double-float, whose uncertain rays join the FP64
                 // queue), or FP64 on a degenerate image
                 CK(launch_cert_split(c->counters, st));
-                CK(cudaMemsetAsync(c->counters + C_REROUTE2, 0, sizeof(unsigned long long), st));
+                // the rays the FP32 pass hands over (near-critical ones, and samples near an
+                // emission discontinuity) join this level's FP64 pass instead of a double-float
+                // pass of their own
                 if ((rc = trace_queue(c, job, J, c->counters + C_QF32, img_dev, mask, nullptr,
                                       nullptr, aminr, aturn,
-                                      spec ? c->counters + C_SPECFROM : nullptr, nullptr, true)))
+                                      spec ? c->counters + C_SPECFROM : nullptr, nullptr, true,
+                                      true)))
                     return rc;
                 if ((rc = trace_queue(c, job, J64, c->counters + C_QF64, img_dev, mask, nullptr,
                                       nullptr, aminr, aturn)))
                     return rc;
                 CK(launch_cert_mark_traced(c->queue, c->counters, (unsigned long long)qcap, c->xst,
                                            st, C_QF64));
-                CK(launch_cert_take_uncertain(c->queue, c->reroute2, c->counters,
+                CK(launch_cert_take_uncertain(c->queue, c->reroute, c->counters, C_REROUTE,
                                               spec ? c->counters + C_SPECFROM : nullptr, mask,
                                               c->cxq, xcap, st));
                 // the borderline points: exact stencils (FP64 re-traces, recomputed
@@ -853,7 +857,7 @@ static int render_impl(art_ctx* c, const art_job* job, const double* truth_dev, 
                                       c->queue + n0, true)))
                     return rc;
                 // speculative rays handed on to FP64 are traced at their own level instead
-                CK(launch_cert_take_uncertain(c->queue + n0, c->reroute2, c->counters,
+                CK(launch_cert_take_uncertain(c->queue + n0, c->reroute2, c->counters, C_REROUTE2,
                                               c->counters + C_ZERO, mask, c->cxq, 0, st));
             }
         } else if (cert) {

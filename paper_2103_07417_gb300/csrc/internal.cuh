@@ -170,7 +170,7 @@ cudaError_t launch_cert_check_norm(const double* norm3, unsigned long long* coun
                                    cudaStream_t st);
 cudaError_t launch_cert_split(unsigned long long* counters, cudaStream_t st);
 cudaError_t launch_cert_take_uncertain(const int32_t* queue, const int32_t* reroute2,
-                                       unsigned long long* counters,
+                                       unsigned long long* counters, int count_idx,
                                        const unsigned long long* spec_from, uint8_t* mask,
                                        int32_t* xq, unsigned long long xq_cap, cudaStream_t st);
 cudaError_t launch_cert_fixup(const DevJob& J, const uint64_t* fixq, unsigned long long* counters,

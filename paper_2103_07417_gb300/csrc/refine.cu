@@ -902,15 +902,15 @@ __global__ void cert_split_kernel(unsigned long long* counters)
     counters[C_QF64] = d ? q : 0ull;
 }
 
-// Double-float rays handed on to FP64 (slots of `queue` in reroute2): a speculative one
-// (slot at or beyond *spec_from) is left for its own level (mask unset); the others join the FP64
-// queue of this level's exact decisions.
+// Rays handed on to FP64 (slots of `queue` in the list, counters[count_idx] of them): a
+// speculative one (slot at or beyond *spec_from) is left for its own level (mask unset); the
+// others join the FP64 queue of this level's exact decisions.
 __global__ void cert_take_uncertain_kernel(const int32_t* queue, const int32_t* reroute2,
-                                           unsigned long long* counters,
+                                           unsigned long long* counters, int count_idx,
                                            const unsigned long long* spec_from, uint8_t* mask,
                                            int32_t* xq, unsigned long long xq_cap)
 {
-    const unsigned long long n = counters[C_REROUTE2];
+    const unsigned long long n = counters[count_idx];
     for (unsigned long long q = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; q < n;
          q += (unsigned long long)gridDim.x * blockDim.x) {
         const int32_t slot = reroute2[q];
@@ -926,12 +926,12 @@ __global__ void cert_take_uncertain_kernel(const int32_t* queue, const int32_t* 
 }
 
 cudaError_t launch_cert_take_uncertain(const int32_t* queue, const int32_t* reroute2,
-                                       unsigned long long* counters,
+                                       unsigned long long* counters, int count_idx,
                                        const unsigned long long* spec_from, uint8_t* mask,
                                        int32_t* xq, unsigned long long xq_cap, cudaStream_t st)
 {
-    cert_take_uncertain_kernel<<<64, 256, 0, st>>>(queue, reroute2, counters, spec_from, mask, xq,
-                                                   xq_cap);
+    cert_take_uncertain_kernel<<<64, 256, 0, st>>>(queue, reroute2, counters, count_idx,
+                                                   spec_from, mask, xq, xq_cap);
     return cudaGetLastError();
 }
 
