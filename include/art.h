@@ -167,7 +167,8 @@ typedef struct art_launch_record {
     int32_t level;  /* refinement level of the launch (-1 outside a render) */
     float ms;       /* duration between CUDA events recorded around the launch on its stream */
     int64_t steps;  /* trace kernels: RK4 steps executed by this launch */
-    int64_t items;  /* trace: rays in its queue; refine: lattice points of the level */
+    int64_t items;  /* trace: rays it finished or handed on; refine: lattice points of the level */
+    int64_t max_steps; /* trace kernels: RK4 steps of its longest ray */
 } art_launch_record;
 
 /* Per-ray diagnostics (device arrays, one entry per traced ray; nullable members). */

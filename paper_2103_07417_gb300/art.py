@@ -74,7 +74,8 @@ class Stats(ctypes.Structure):
 
 class LaunchRecord(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32), ("ms", ctypes.c_float),
-                ("steps", ctypes.c_int64), ("items", ctypes.c_int64)]
+                ("steps", ctypes.c_int64), ("items", ctypes.c_int64),
+                ("max_steps", ctypes.c_int64)]
 
 
 KERNEL_KINDS = {0: "trace_fp64", 1: "trace_fp32", 2: "refine", 3: "other", 4: "trace_df",
@@ -515,7 +516,7 @@ class Context:
         n = ctypes.c_int()
         _check(load().art_profile_read(self._ctx, recs, cap, ctypes.byref(n)), "art_profile_read")
         return [dict(kind=KERNEL_KINDS.get(r.kind, "other"), level=r.level, ms=r.ms, steps=r.steps,
-                     items=r.items) for r in recs[: n.value]]
+                     items=r.items, max_steps=r.max_steps) for r in recs[: n.value]]
 
     # -- conveniences ----------------------------------------------------------------------
     def render(self, job: Job, truth=None):

@@ -117,7 +117,7 @@ struct art_ctx {
     int prof_n = 0;
     cudaEvent_t ev[2 * PROF_MAX] = {};
     art_launch_record rec[PROF_MAX];
-    unsigned long long* prof_steps = nullptr;  // device snapshots of C_STEPS after trace launches
+    unsigned long long* prof_steps = nullptr;  // device snapshots (steps, longest ray, rays) per launch
     int prof_level = -1;
 };
 
@@ -143,9 +143,15 @@ static void prof_end(art_ctx* c, int k, int kind, int64_t items)
     c->rec[k].ms = 0.f;
     c->rec[k].steps = 0;
     c->rec[k].items = items;
-    if (kind == ART_K_TRACE_FP64 || kind == ART_K_TRACE_FP32 || kind == ART_K_TRACE_DF)
-        cudaMemcpyAsync(c->prof_steps + k, c->counters + C_STEPS, sizeof(unsigned long long),
+    if (kind == ART_K_TRACE_FP64 || kind == ART_K_TRACE_FP32 || kind == ART_K_TRACE_DF) {
+        // snapshots of the summed steps and rays and of the launch's longest ray (reset after)
+        unsigned long long* snap = c->prof_steps + 3 * k;
+        cudaMemcpyAsync(snap, c->counters + C_STEPS, sizeof(unsigned long long),
                         cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(snap + 1, c->counters + C_MAXSTEP, 2 * sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemsetAsync(c->counters + C_MAXSTEP, 0, sizeof(unsigned long long), c->stream);
+    }
     c->prof_n = k + 1;
 }
 
@@ -1096,7 +1102,7 @@ extern "C" int art_profile(art_ctx* c, int enable)
         return ART_OK;
     }
     if (!c->prof_steps) {
-        CK(cudaMalloc(&c->prof_steps, sizeof(unsigned long long) * art_ctx::PROF_MAX));
+        CK(cudaMalloc(&c->prof_steps, 3 * sizeof(unsigned long long) * art_ctx::PROF_MAX));
         for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k) CK(cudaEventCreate(&c->ev[k]));
     }
     CK(cudaStreamSynchronize(c->stream));
@@ -1121,23 +1127,28 @@ extern "C" int art_profile_read(art_ctx* c, art_launch_record* recs, int cap, in
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
     if (!c->prof_steps) return ART_OK;
-    unsigned long long snap[art_ctx::PROF_MAX];
-    CK(cudaMemcpy(snap, c->prof_steps, sizeof(unsigned long long) * c->prof_n,
+    std::vector<unsigned long long> snap(3 * (size_t)art_ctx::PROF_MAX);
+    CK(cudaMemcpy(snap.data(), c->prof_steps, 3 * sizeof(unsigned long long) * c->prof_n,
                   cudaMemcpyDeviceToHost));
-    unsigned long long prev = 0;
+    unsigned long long prev = 0, prevr = 0;
     int out = 0;
     for (int k = 0; k < c->prof_n; ++k) {
         art_launch_record r = c->rec[k];
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]));
         r.ms = ms;
+        r.max_steps = 0;
         if (r.kind == ART_K_TRACE_FP64 || r.kind == ART_K_TRACE_FP32 || r.kind == ART_K_TRACE_DF) {
-            // the step counter restarts with every call: a snapshot below the previous one
-            // belongs to a new call
-            r.steps = (int64_t)(snap[k] >= prev ? snap[k] - prev : snap[k]);
-            prev = snap[k];
+            // the counters restart with every call: a snapshot below the previous one belongs to
+            // a new call
+            const unsigned long long st = snap[3 * k], mx = snap[3 * k + 1], nr = snap[3 * k + 2];
+            r.steps = (int64_t)(st >= prev ? st - prev : st);
+            r.items = (int64_t)(nr >= prevr ? nr - prevr : nr);
+            r.max_steps = (int64_t)mx;
+            prev = st;
+            prevr = nr;
         }
-        if (r.kind == ART_K_OTHER && r.items == 1) prev = 0;  // camera set-up opens a call
+        if (r.kind == ART_K_OTHER && r.items == 1) prev = prevr = 0;  // camera set-up opens a call
         if (out < cap) recs[out++] = r;
     }
     *n = out;

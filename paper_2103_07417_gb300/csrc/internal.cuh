@@ -42,6 +42,8 @@ enum Counter {
     C_AXQ = 42,      // third axis: length of the level's queue after the axis filter
     C_AXKEPT = 43,   // third axis: rays kept by the filter (all levels)
     C_AXINTERP = 44, // third axis: points interpolated along the axis (all levels)
+    C_MAXSTEP = 45,  // profiler: most RK4 steps of one ray since the last trace launch
+    C_RAYCNT = 46,   // profiler: rays finished (or handed on), summed
     C_COUNT = 64
 };
 

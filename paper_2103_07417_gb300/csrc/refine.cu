@@ -607,7 +607,9 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
             ex = ex && (x[p2] & XS_EXACT);
             if (cat == 4) ex = ex && (x[p3] & XS_EXACT) && (x[p4] & XS_EXACT);
         }
-        if (ex) ca->xst[pix] = XS_EXACT;
+        // (a point traced speculatively in FP64 and interpolated after all loses its exactness
+        // unless its parents are exact)
+        ca->xst[pix] = ex ? XS_EXACT : 0;
     }
     return 0;
 }
@@ -678,6 +680,7 @@ __global__ void __launch_bounds__(256)
                                                                    aturn);
                             trace = r == 1;
                             used = r == 2;
+                            if (r == 0) ca.xst[pix] = 0;  // an interpolant of unchecked parents
                         }
                     }
                 }
@@ -801,7 +804,8 @@ constexpr int CERT_STACK = 96;
 // Closure of the borderline points: every non-exact value their decision reads is claimed once;
 // FP32-traced ones join the FP64 queue, interpolated ones the recompute list (with their level)
 // and their own parents are searched in turn.  The borderline points themselves join the FP64
-// queue too (traced speculatively: their decision may ask for them).
+// queue too unless already traced in FP64 (traced speculatively: their decision may ask for
+// them).
 __global__ void cert_closure_kernel(DevJob J, const int32_t* border, const unsigned long long* counters_ro,
                                     unsigned long long* counters, uint8_t* xst, const uint8_t* mask,
                                     int32_t* xq, unsigned long long xq_cap, uint64_t* fixq,
@@ -813,7 +817,7 @@ __global__ void cert_closure_kernel(DevJob J, const int32_t* border, const unsig
     for (unsigned long long b = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; b < nb;
          b += (unsigned long long)gridDim.x * blockDim.x) {
         const int32_t p = border[b];
-        {
+        if (!(xst[p] & XS_EXACT)) {  // not already traced in FP64 (a band ray)
             const unsigned long long w = atomicAdd(counters + C_XQ, 1ull);
             if (w < xq_cap) xq[w] = p;
             else atomicAdd(counters + C_CERTERR, 1ull);

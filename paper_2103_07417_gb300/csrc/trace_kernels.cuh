@@ -23,6 +23,8 @@ __device__ __forceinline__ void finish_ray(const TraceArgs& A, int status, int s
                                            const XferState<Q>& x, int32_t pix, int64_t slot)
 {
     atomicAdd(A.counters + C_STEPS, (unsigned long long)steps);
+    atomicMax(A.counters + C_MAXSTEP, (unsigned long long)steps);
+    atomicAdd(A.counters + C_RAYCNT, 1ull);
     const bool rer = A.reroute != nullptr && (status == RAY_REROUTE || status == ART_RAY_NAN ||
                                               status == ART_RAY_CAP || x.edge);
     if (rer) {
@@ -55,6 +57,12 @@ __device__ __forceinline__ void finish_ray(const TraceArgs& A, int status, int s
     if (A.aux_minr) A.aux_minr[slot] = x.min_r;
 }
 
+// Queue position of the q-th ray a launch fetches.
+__device__ __forceinline__ int64_t fetch_slot(const TraceArgs& A, unsigned long long q)
+{
+    return A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
+}
+
 // One-thread form: each lane traces its ray's whole step and refills itself from the queue.
 template <class R, bool SWEEP, bool POL, int EM>
 __device__ __forceinline__ void trace_lanes(const TraceArgs& A, const Camera& cam_s)
@@ -68,7 +76,7 @@ __device__ __forceinline__ void trace_lanes(const TraceArgs& A, const Camera& ca
         while (true) {
             unsigned long long q = warp_fetch(A.fetch);
             if (q >= n) return false;
-            int64_t slot = A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
+            int64_t slot = fetch_slot(A, q);
             int32_t pix = A.queue[slot];
             if (pix < 0 || (int64_t)pix >= A.npix) {
                 atomicAdd(A.counters + C_BADIDX, 1ull);
@@ -173,6 +181,8 @@ __device__ __forceinline__ void finish_batch_ray(const BatchTraceArgs& A, int st
                                                  int32_t img)
 {
     atomicAdd(A.counters + C_STEPS, (unsigned long long)steps);
+    atomicMax(A.counters + C_MAXSTEP, (unsigned long long)steps);
+    atomicAdd(A.counters + C_RAYCNT, 1ull);
     const bool rer = A.reroute != nullptr && (status == RAY_REROUTE || status == ART_RAY_NAN ||
                                               status == ART_RAY_CAP || x.edge);
     if (rer) {
@@ -213,7 +223,7 @@ struct SingleSource {
         while (true) {
             const unsigned long long q = warp_fetch(A.fetch);
             if (q >= n) return false;
-            const int64_t sq = A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
+            const int64_t sq = fetch_slot(A, q);
             const int32_t px = A.queue[sq];
             if (px < 0 || (int64_t)px >= A.npix) {
                 atomicAdd(A.counters + C_BADIDX, 1ull);
@@ -486,7 +496,7 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
                         drained = true;
                         break;
                     }
-                    const int64_t sq = A.indirect ? (int64_t)A.indirect[q] : (int64_t)q;
+                    const int64_t sq = fetch_slot(A, q);
                     const int32_t px = A.queue[sq];
                     if (px < 0 || (int64_t)px >= A.npix) {
                         atomicAdd(A.counters + C_BADIDX, 1ull);
@@ -645,8 +655,13 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
             __syncthreads();
             const unsigned long long pair_lanes =
                 (unsigned long long)gridDim.x * PairRingOf<R, POL>::NPAIR * 32ull;
+            // FP64: always the warp-pair form.  GB300's FP64 pipe takes a warp instruction per
+            // 64 cycles on one scheduler whatever its ILP and active lanes (about 16 cycles per
+            // SM across the four), so a ray's latency is its warp's FP64 instruction count: the
+            // pair halves it, which shortens the launches whose longest rays finish last, and
+            // the SM-wide rate (the throughput bound) is the same in either form.
             const unsigned long long n = *A.count;
-            if (n <= pair_lanes)
+            if (n <= pair_lanes || std::is_same<R, double>::value)
                 trace_pairs<R, SWEEP, POL, EM>(SingleSource{A, cam_s, n}, ring);
             else
                 trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
