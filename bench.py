@@ -106,7 +106,8 @@ def parse():
                     help="IF / FE / MSE of the 8193^2 grid workload over a (R_rel, R_abs) log "
                          "grid (the paper's tolerance study), nothing else")
     ap.add_argument("--single", action="store_true",
-                    help="one warm-up and one render, nothing else (for profiler captures)")
+                    help="one warm-up and one profiled render, nothing else (for profiler "
+                         "captures): prints the stats and the per-launch records")
     ap.add_argument("--batch-only", action="store_true",
                     help="one warm-up and one batched render of the 256-image mixed-parameter batch, "
                          "nothing else (for profiler captures)")
@@ -737,9 +738,17 @@ def main():
         ctx.close()
         return
     if args.single:
+        # one warm-up render, then one render with the library's launch profiler on: per launch
+        # its kind, level, CUDA-event ms and, for trace launches, rays, steps and longest ray
         ctx.art_render(job, img, mask, stats=True)
+        ctx.art_profile(True)
         st = ctx.art_render(job, img, mask, stats=True)
-        print(json.dumps({"single": args.workload, "precision": args.precision, **st}))
+        recs = ctx.art_profile_read()
+        ctx.art_profile(False)
+        launches = [{k: (round(v, 4) if k == "ms" else v) for k, v in r.items()}
+                    for r in recs if r["kind"] != "other"]
+        print(json.dumps({"single": args.workload, "precision": args.precision, **st,
+                          "launches": launches}))
         ctx.close()
         return
     # the library's autotuner picks the FP32 kernel-form thresholds for this workload (outside

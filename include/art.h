@@ -367,6 +367,14 @@ int art_profile_read(art_ctx* ctx, art_launch_record* recs_host, int cap, int* n
  * frees a small device buffer.  Errors: ART_ERR_ARG (null pointer), ART_ERR_CUDA. */
 int art_measure_alu_peaks(art_ctx* ctx, double* fp32_tflops, double* fp64_tflops);
 
+/* Issue cost of FP64 fused multiply-adds on one SM (not in the paper; it sets how the tracer splits
+ * an FP64 ray's work between warps), in SM clock cycles per instruction, written to cycles3[0..2]
+ * (host array): [0] one warp, one dependent chain; [1] one warp, eight independent chains;
+ * [2] four warps (one per scheduler), eight chains each, per warp instruction of the SM.
+ * Synchronises the context's stream first; allocates and frees a small device buffer.
+ * Errors: ART_ERR_ARG (null pointer), ART_ERR_CUDA. */
+int art_measure_fp64_issue(art_ctx* ctx, double* cycles3);
+
 /* art_trace_pixels for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant.  Some callers cannot let a library call cudaMalloc:
  * a process whose device memory is reserved up front by its own allocator (a render service with

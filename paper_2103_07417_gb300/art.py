@@ -116,7 +116,8 @@ EXPORTS = ("art_create", "art_destroy", "art_strerror", "art_image_size", "art_p
            "art_trace_pixels_noalloc", "art_render_batch", "art_load_grid", "art_cnn_load",
            "art_cnn_read", "art_cnn_forward", "art_cnn_grad", "art_cnn_train_step",
            "art_cnn_sample", "art_set_tune", "art_get_tune", "art_autotune", "art_graph_render",
-           "art_graph_render_batch", "art_measure_alu_peaks", "art_visibilities",
+           "art_graph_render_batch", "art_measure_alu_peaks", "art_measure_fp64_issue",
+           "art_visibilities",
            "art_render_axis")
 CNN_PARAMS = 28673
 NOALLOC_MAX_RAYS = 1 << 20
@@ -164,6 +165,7 @@ def load():
             lib.art_set_tune.argtypes = [vp, P(Tune)]
             lib.art_get_tune.argtypes = [vp, P(Tune)]
             lib.art_measure_alu_peaks.argtypes = [vp, P(ctypes.c_double), P(ctypes.c_double)]
+            lib.art_measure_fp64_issue.argtypes = [vp, P(ctypes.c_double)]
             lib.art_autotune.argtypes = [vp, P(Job), vp, vp, i32, P(Tune), fp]
             lib.art_graph_render.argtypes = [vp, P(Job), vp, vp]
             lib.art_visibilities.argtypes = [vp, vp, vp, i32, i32, ctypes.c_double,
@@ -465,6 +467,13 @@ class Context:
         _check(load().art_measure_alu_peaks(self._ctx, ctypes.byref(f32), ctypes.byref(f64)),
                "art_measure_alu_peaks")
         return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
+
+    def art_measure_fp64_issue(self) -> dict:
+        """SM cycles per FP64 fused multiply-add: one warp with one dependent chain, one warp with
+        eight independent chains, and four warps (one per scheduler) per instruction of the SM."""
+        c = (ctypes.c_double * 3)()
+        _check(load().art_measure_fp64_issue(self._ctx, c), "art_measure_fp64_issue")
+        return {"one_warp_chain": c[0], "one_warp_8_chains": c[1], "four_warps_per_sm": c[2]}
 
     def art_visibilities(self, img, dx: float, taper_fwhm: float, m: int, ref=None, out=None):
         """Visibilities of one image plane (ny, nx) float64 CUDA tensor (minus `ref` if given):

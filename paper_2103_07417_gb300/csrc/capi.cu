@@ -1120,6 +1120,15 @@ extern "C" int art_measure_alu_peaks(art_ctx* c, double* fp32_tflops, double* fp
     return ART_OK;
 }
 
+extern "C" int art_measure_fp64_issue(art_ctx* c, double* cycles3)
+{
+    if (!c || !cycles3) return ART_ERR_ARG;
+    CK(cudaSetDevice(c->device));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(measure_fp64_issue(c->stream, cycles3));
+    return ART_OK;
+}
+
 extern "C" int art_profile_read(art_ctx* c, art_launch_record* recs, int cap, int* n)
 {
     if (!c || !n || (cap > 0 && !recs)) return ART_ERR_ARG;

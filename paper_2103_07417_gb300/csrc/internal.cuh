@@ -209,6 +209,7 @@ cudaError_t launch_visibilities(const double* img, const double* ref, int nx, in
 // peaks.cu: measured FP32 / FP64 fused multiply-add throughput (TFLOP/s)
 cudaError_t measure_alu_peaks(int num_sms, cudaStream_t st, double* fp32_tflops,
                               double* fp64_tflops);
+cudaError_t measure_fp64_issue(cudaStream_t st, double* cycles3);
 
 // cnn.cu
 struct CnnState;

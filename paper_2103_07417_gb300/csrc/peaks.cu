@@ -85,4 +85,57 @@ cudaError_t measure_alu_peaks(int num_sms, cudaStream_t st, double* fp32_tflops,
     return e;
 }
 
+// Issue cost of FP64 fused multiply-adds on one SM, read from the SM clock: one warp running one
+// dependent chain (the latency of a chain), one warp running ISSUE_NCH independent chains (the
+// rate one scheduler issues FP64 at), and one warp per scheduler (four) running ISSUE_NCH chains
+// each (the rate of the SM).  out[w] = elapsed cycles of warp w.
+constexpr int ISSUE_NCH = 8;
+constexpr int ISSUE_ITERS = 512;
+
+template <int NCH>
+__global__ void fp64_issue_kernel(double b, double c, long long* out, double* sink)
+{
+    double v[NCH];
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) v[k] = 1.0 + 1e-3 * (threadIdx.x + k);
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int it = 0; it < ISSUE_ITERS; ++it) {
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) v[k] = fma(v[k], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < NCH; ++k) s += v[k];
+    const long long t1 = clock64();
+    if ((threadIdx.x & 31) == 0) out[threadIdx.x >> 5] = t1 - t0;
+    if (s == -1.0) sink[threadIdx.x] = s;
+}
+
+cudaError_t measure_fp64_issue(cudaStream_t st, double* cycles3)
+{
+    void* buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, 64 * sizeof(long long) + 128 * sizeof(double));
+    if (e != cudaSuccess) return e;
+    long long* out = static_cast<long long*>(buf);
+    double* sink = reinterpret_cast<double*>(out + 64);
+    long long h[3][4] = {};
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {  // the first pass warms up
+        fp64_issue_kernel<1><<<1, 32, 0, st>>>(0.999999, 1e-7, out, sink);
+        fp64_issue_kernel<ISSUE_NCH><<<1, 32, 0, st>>>(0.999999, 1e-7, out + 4, sink);
+        fp64_issue_kernel<ISSUE_NCH><<<1, 128, 0, st>>>(0.999999, 1e-7, out + 8, sink);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    cudaFree(buf);
+    if (e != cudaSuccess) return e;
+    long long w4 = 0;
+    for (int w = 0; w < 4; ++w) w4 = h[2][w] > w4 ? h[2][w] : w4;
+    cycles3[0] = (double)h[0][0] / ISSUE_ITERS;
+    cycles3[1] = (double)h[1][0] / (ISSUE_ITERS * ISSUE_NCH);
+    cycles3[2] = (double)w4 / (4.0 * ISSUE_ITERS * ISSUE_NCH);
+    return cudaSuccess;
+}
+
 }  // namespace art

@@ -130,22 +130,51 @@ cudaError_t launch_norm(const DevJob& J, const double* img, int nx, int ny, int 
 // criterion + interpolation + compaction of one level
 // --------------------------------------------------------------------------------------------
 
+// High-word FP32 value of a double; ok = false for |x| >= 2^128, infinities and NaN.
+__device__ __forceinline__ float hiword_f32(double x, bool& ok)
+{
+    const int hi = __double2hiint(x);
+    const int e = (hi >> 20) & 0x7ff;
+    if (e > 1150) {
+        ok = false;
+        return 0.f;
+    }
+    if (e < 897) return 0.f;
+    return __int_as_float((hi & 0x80000000) | ((e - 896) << 23) | ((hi & 0xfffff) << 3));
+}
+
+// Where the stencil functions below read the criterion plane (fine-grid coordinates i, j of a
+// point of the coarser lattice): straight from the image (GlobalSrc), or from a block's shared-
+// memory tile of that lattice (TileSrc, the level kernel).  Both hold the image's own doubles, so
+// every decision and interpolant is the same bits either way.
+template <class IX>
+struct GlobalSrc {
+    const double* img;  // the criterion plane
+    int nx;
+    __device__ __forceinline__ double at(int i, int j) const { return __ldg(img + (IX)j * nx + i); }
+    __device__ __forceinline__ float at_f(int i, int j, bool& ok) const
+    {
+        return hiword_f32(at(i, j), ok);
+    }
+    __device__ __forceinline__ const double* plane() const { return img; }
+};
+
 // Sum of the two central second differences along one line through the point (inner
 // neighbours at -/+ d, outer at -/+ 3d): I(-3) - I(-1) - I(+1) + I(+3); where one outer point is
 // outside the image, twice the one second difference available; where none is, ok = false.
-template <class IX>
-__device__ __forceinline__ double second_diff_sum(const double* img, int nx, int ny, int i, int j,
+template <class Src>
+__device__ __forceinline__ double second_diff_sum(const Src& V, int nx, int ny, int i, int j,
                                                   int di, int dj, double Im, double Ip, bool& ok)
 {
     const int iom = i - 3 * di, jom = j - 3 * dj, iop = i + 3 * di, jop = j + 3 * dj;
     const bool has_m = iom >= 0 && iom < nx && jom >= 0 && jom < ny;
     const bool has_p = iop >= 0 && iop < nx && jop >= 0 && jop < ny;
     if (has_m && has_p) {
-        double Om = __ldg(img + (IX)jom * nx + iom), Op = __ldg(img + (IX)jop * nx + iop);
+        double Om = V.at(iom, jom), Op = V.at(iop, jop);
         return ((Om - Im) - Ip) + Op;
     }
-    if (has_m) return 2.0 * ((__ldg(img + (IX)jom * nx + iom) - 2.0 * Im) + Ip);
-    if (has_p) return 2.0 * ((__ldg(img + (IX)jop * nx + iop) - 2.0 * Ip) + Im);
+    if (has_m) return 2.0 * ((V.at(iom, jom) - 2.0 * Im) + Ip);
+    if (has_p) return 2.0 * ((V.at(iop, jop) - 2.0 * Ip) + Im);
     ok = false;
     return 0.0;
 }
@@ -156,11 +185,12 @@ __device__ __forceinline__ double second_diff_sum(const double* img, int nx, int
 // Nearest: sqrt(((I4-I1)/2)^2 + ((I3-I2)/2)^2) [centre] or |I2-I1|/2 [midpoints] over norm and
 // over |I1|, interpolant I1.  Decision: trace iff eps_abs > R_abs && eps_rel > R_rel (strict);
 // NaN traces; a line without any outer point gives +inf.
-template <class IX>
-__device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i, int j, int s,
+template <class IX, class Src>
+__device__ __forceinline__ bool decide(const DevJob& J, const Src& V, int i, int j, int s,
                                       double norm, int cat, double& w1, double& w2, IX& p1, IX& p2,
                                       IX& p3, IX& p4, double& ea, double& er)
 {
+    const double* img = V.plane();
     const int nx = J.nx, ny = J.ny;
     bool ok = true;
     double num, sin_, i1, den;
@@ -169,7 +199,8 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
         p4 = (IX)(j + s) * nx + (i + s);  // point 4 (opposite 1)
         p2 = (IX)(j + s) * nx + (i - s);  // point 2
         p3 = (IX)(j - s) * nx + (i + s);  // point 3 (opposite 2)
-        double I1 = __ldg(img + p1), I4 = __ldg(img + p4), I2 = __ldg(img + p2), I3 = __ldg(img + p3);
+        double I1 = V.at(i - s, j - s), I4 = V.at(i + s, j + s), I2 = V.at(i - s, j + s),
+               I3 = V.at(i + s, j - s);
         sin_ = ((I1 + I2) + I3) + I4;
         i1 = I1;
         if (J.interp == ART_INTERP_NEAREST) {
@@ -179,8 +210,8 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
             w2 = 0.0;
             den = fabs(i1);
         } else {
-            double dA = second_diff_sum<IX>(img, nx, ny, i, j, s, s, I1, I4, ok);
-            double dB = second_diff_sum<IX>(img, nx, ny, i, j, s, -s, I2, I3, ok);
+            double dA = second_diff_sum(V, nx, ny, i, j, s, s, I1, I4, ok);
+            double dB = second_diff_sum(V, nx, ny, i, j, s, -s, I2, I3, ok);
             num = fabs(dA + dB) / 16.0;
             w1 = 0.25;
             w2 = 0.25;
@@ -191,7 +222,7 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
         p1 = (IX)(j - dj) * nx + (i - di);
         p2 = (IX)(j + dj) * nx + (i + di);
         p3 = p4 = -1;
-        double I1 = __ldg(img + p1), I2 = __ldg(img + p2);
+        double I1 = V.at(i - di, j - dj), I2 = V.at(i + di, j + dj);
         sin_ = I1 + I2;
         i1 = I1;
         if (J.interp == ART_INTERP_NEAREST) {
@@ -200,7 +231,7 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
             w2 = 0.0;
             den = fabs(i1);
         } else {
-            double d = second_diff_sum<IX>(img, nx, ny, i, j, di, dj, I1, I2, ok);
+            double d = second_diff_sum(V, nx, ny, i, j, di, dj, I1, I2, ok);
             num = fabs(d) / 8.0;
             w1 = 0.5;
             w2 = 0.5;
@@ -222,6 +253,7 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
         const int64_t npix = (int64_t)nx * ny;
         for (int c = 1; c < 4 && !tr; ++c) {
             const double* pl = img + c * npix;
+            const GlobalSrc<IX> P{pl, nx};
             double nc;
             if (cat == 4) {
                 const double I1 = __ldg(pl + p1), I4 = __ldg(pl + p4), I2 = __ldg(pl + p2),
@@ -232,8 +264,8 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
                                         __dmul_rn(__dmul_rn(0.25, d32), d32)));
                 } else {
                     bool okc = true;
-                    const double dA = second_diff_sum<IX>(pl, nx, ny, i, j, s, s, I1, I4, okc);
-                    const double dB = second_diff_sum<IX>(pl, nx, ny, i, j, s, -s, I2, I3, okc);
+                    const double dA = second_diff_sum(P, nx, ny, i, j, s, s, I1, I4, okc);
+                    const double dB = second_diff_sum(P, nx, ny, i, j, s, -s, I2, I3, okc);
                     nc = fabs(dA + dB) / 16.0;
                 }
             } else {
@@ -243,7 +275,7 @@ __device__ __forceinline__ bool decide(const DevJob& J, const double* img, int i
                     nc = fabs(I2 - I1) / 2.0;
                 } else {
                     bool okc = true;
-                    nc = fabs(second_diff_sum<IX>(pl, nx, ny, i, j, di, dj, I1, I2, okc)) / 8.0;
+                    nc = fabs(second_diff_sum(P, nx, ny, i, j, di, dj, I1, I2, okc)) / 8.0;
                 }
             }
             const double eac = nc / norm;
@@ -300,22 +332,9 @@ __device__ __forceinline__ Screen make_screen(const DevJob& J, double norm, doub
     return sc;
 }
 
-// High-word FP32 value of a double; ok = false for |x| >= 2^128, infinities and NaN.
-__device__ __forceinline__ float hiword_f32(double x, bool& ok)
-{
-    const int hi = __double2hiint(x);
-    const int e = (hi >> 20) & 0x7ff;
-    if (e > 1150) {
-        ok = false;
-        return 0.f;
-    }
-    if (e < 897) return 0.f;
-    return __int_as_float((hi & 0x80000000) | ((e - 896) << 23) | ((hi & 0xfffff) << 3));
-}
-
 // FP32 second-difference sum along one line (as second_diff_sum) and its sum of |c_k v_k|.
-template <class IX>
-__device__ __forceinline__ float second_diff_f(const double* img, int nx, int ny, int i, int j,
+template <class Src>
+__device__ __forceinline__ float second_diff_f(const Src& V, int nx, int ny, int i, int j,
                                                int di, int dj, float Im, float Ip, float& C,
                                                bool& ok)
 {
@@ -323,18 +342,18 @@ __device__ __forceinline__ float second_diff_f(const double* img, int nx, int ny
     const bool has_m = iom >= 0 && iom < nx && jom >= 0 && jom < ny;
     const bool has_p = iop >= 0 && iop < nx && jop >= 0 && jop < ny;
     if (has_m && has_p) {
-        float Om = hiword_f32(__ldg(img + (IX)jom * nx + iom), ok);
-        float Op = hiword_f32(__ldg(img + (IX)jop * nx + iop), ok);
+        float Om = V.at_f(iom, jom, ok);
+        float Op = V.at_f(iop, jop, ok);
         C += ((fabsf(Om) + fabsf(Im)) + fabsf(Ip)) + fabsf(Op);
         return ((Om - Im) - Ip) + Op;
     }
     if (has_m) {
-        float Om = hiword_f32(__ldg(img + (IX)jom * nx + iom), ok);
+        float Om = V.at_f(iom, jom, ok);
         C += 2.f * fabsf(Om) + 4.f * fabsf(Im) + 2.f * fabsf(Ip);
         return 2.f * ((Om - 2.f * Im) + Ip);
     }
     if (has_p) {
-        float Op = hiword_f32(__ldg(img + (IX)jop * nx + iop), ok);
+        float Op = V.at_f(iop, jop, ok);
         C += 2.f * fabsf(Op) + 4.f * fabsf(Ip) + 2.f * fabsf(Im);
         return 2.f * ((Op - 2.f * Ip) + Im);
     }
@@ -343,8 +362,8 @@ __device__ __forceinline__ float second_diff_f(const double* img, int nx, int ny
 }
 
 // Screened decision: 1 = trace, 0 = interpolate, -1 = undecided (take the FP64 decision).
-template <class IX>
-__device__ __forceinline__ int screen_decide(const Screen& sc, const double* img, int nx, int ny,
+template <class Src>
+__device__ __forceinline__ int screen_decide(const Screen& sc, const Src& V, int nx, int ny,
                                              int i, int j, int s, int cat)
 {
     if (!sc.on) return -1;
@@ -352,23 +371,23 @@ __device__ __forceinline__ int screen_decide(const Screen& sc, const double* img
     float X, C = 0.f, Sin, Cin;
     float tabs;
     if (cat == 4) {
-        float I1 = hiword_f32(__ldg(img + (IX)(j - s) * nx + (i - s)), ok);
-        float I4 = hiword_f32(__ldg(img + (IX)(j + s) * nx + (i + s)), ok);
-        float I2 = hiword_f32(__ldg(img + (IX)(j + s) * nx + (i - s)), ok);
-        float I3 = hiword_f32(__ldg(img + (IX)(j - s) * nx + (i + s)), ok);
+        float I1 = V.at_f(i - s, j - s, ok);
+        float I4 = V.at_f(i + s, j + s, ok);
+        float I2 = V.at_f(i - s, j + s, ok);
+        float I3 = V.at_f(i + s, j - s, ok);
         Sin = ((I1 + I2) + I3) + I4;
         Cin = ((fabsf(I1) + fabsf(I2)) + fabsf(I3)) + fabsf(I4);
-        float dA = second_diff_f<IX>(img, nx, ny, i, j, s, s, I1, I4, C, ok);
-        float dB = second_diff_f<IX>(img, nx, ny, i, j, s, -s, I2, I3, C, ok);
+        float dA = second_diff_f(V, nx, ny, i, j, s, s, I1, I4, C, ok);
+        float dB = second_diff_f(V, nx, ny, i, j, s, -s, I2, I3, C, ok);
         X = fabsf(dA + dB);
         tabs = sc.tabs4;
     } else {
         const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
-        float I1 = hiword_f32(__ldg(img + (IX)(j - dj) * nx + (i - di)), ok);
-        float I2 = hiword_f32(__ldg(img + (IX)(j + dj) * nx + (i + di)), ok);
+        float I1 = V.at_f(i - di, j - dj, ok);
+        float I2 = V.at_f(i + di, j + dj, ok);
         Sin = I1 + I2;
         Cin = fabsf(I1) + fabsf(I2);
-        X = fabsf(second_diff_f<IX>(img, nx, ny, i, j, di, dj, I1, I2, C, ok));
+        X = fabsf(second_diff_f(V, nx, ny, i, j, di, dj, I1, I2, C, ok));
         tabs = sc.tabs2;
     }
     if (!ok) return -1;
@@ -401,8 +420,8 @@ __device__ __forceinline__ int screen_decide(const Screen& sc, const double* img
 // exactly 0, eps_abs = 0 / norm = 0 for a positive finite norm, and with R_abs >= 0 the FP64
 // decision is "interpolate" whatever R_rel is.  The dark background of a wide field takes this
 // exit on the integer pipes.
-template <class IX>
-__device__ __forceinline__ bool uniform_stencil(const double* img, int nx, int ny, int i, int j,
+template <class Src>
+__device__ __forceinline__ bool uniform_stencil(const Src& V, int nx, int ny, int i, int j,
                                                 int s, int cat)
 {
     int di1, dj1, di2 = 0, dj2 = 0;  // the one or two lines of the stencil
@@ -414,11 +433,9 @@ __device__ __forceinline__ bool uniform_stencil(const double* img, int nx, int n
     }
     const int ri = 3 * (di1 > di2 ? di1 : di2), rj = 3 * s * (cat != 3);
     if (i - ri < 0 || i + ri >= nx || j - rj < 0 || j + rj >= ny) return false;
-    const long long v = __double_as_longlong(__ldg(img + (IX)(j - dj1) * nx + (i - di1)));
+    const long long v = __double_as_longlong(V.at(i - di1, j - dj1));
     if (((v >> 52) & 0x7ff) == 0x7ff) return false;
-    auto same = [&](int ii, int jj) {
-        return __double_as_longlong(__ldg(img + (IX)jj * nx + ii)) == v;
-    };
+    auto same = [&](int ii, int jj) { return __double_as_longlong(V.at(ii, jj)) == v; };
     if (!same(i + di1, j + dj1) || !same(i - 3 * di1, j - 3 * dj1) || !same(i + 3 * di1, j + 3 * dj1))
         return false;
     if (cat == 4 && (!same(i - di2, j - dj2) || !same(i + di2, j + dj2) ||
@@ -493,6 +510,43 @@ __device__ __forceinline__ void write_interp(const DevJob& J, double* img, IX pi
     }
 }
 
+// write_interp for a one-plane image, the parents read through V: the same operations on the
+// same values, so the same bits.
+template <class Src>
+__device__ __forceinline__ void write_interp_v(const DevJob& J, const Src& V, double* out, int i,
+                                               int j, int s, int cat)
+{
+    double v;
+    if (cat == 4) {
+        const double v1 = V.at(i - s, j - s);
+        if (J.interp == ART_INTERP_NEAREST) {
+            *out = v1;
+            return;
+        }
+        const double v2 = V.at(i - s, j + s), v3 = V.at(i + s, j - s), v4 = V.at(i + s, j + s);
+        const long long b1 = __double_as_longlong(v1);
+        if (b1 == __double_as_longlong(v2) && b1 == __double_as_longlong(v3) &&
+            b1 == __double_as_longlong(v4) && ((b1 >> 52) & 0x7ff) < 0x7fc)
+            v = v1;
+        else
+            v = scale_pow2(((v1 + v2) + v3) + v4, 2);
+    } else {
+        const int di = (cat == 3) ? s : 0, dj = (cat == 2) ? s : 0;
+        const double v1 = V.at(i - di, j - dj);
+        if (J.interp == ART_INTERP_NEAREST) {
+            *out = v1;
+            return;
+        }
+        const double v2 = V.at(i + di, j + dj);
+        const long long b1 = __double_as_longlong(v1);
+        if (b1 == __double_as_longlong(v2) && ((b1 >> 52) & 0x7ff) < 0x7fc)
+            v = v1;
+        else
+            v = scale_pow2(v1 + v2, 1);
+    }
+    *out = v;
+}
+
 // Exact-decision mode (ART_MIXED_EXACT): per-pixel exactness bytes, the borderline list and the
 // band within which an FP64 decision on FP32-traced values is not trusted.
 struct CertArgs {
@@ -546,24 +600,24 @@ __device__ __forceinline__ bool decision_robust(const DevJob& J, double ea, doub
 // CERT (exact decisions): a decision within the band of a tolerance whose stencil is not all
 // exact is left to the exact-decision passes (return 3, nothing written); an interpolated point
 // whose parents are exact is marked exact.
-template <class IX, bool CERT = false>
-__device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, double* img,
-                                            uint8_t* mask, int i, int j, int s, int cat,
-                                            double norm, int64_t npix, bool spec, float* aminr,
-                                            float* aturn, const CertArgs* ca = nullptr)
+// V reads the criterion plane (plane J.cplane of img).
+template <class IX, bool CERT, class Src>
+__device__ __forceinline__ int refine_point_s(const DevJob& J, const Screen& sc, const Src& V,
+                                              double* img, uint8_t* mask, int i, int j, int s,
+                                              int cat, double norm, int64_t npix, bool spec,
+                                              float* aminr, float* aturn, const CertArgs* ca)
 {
     double w1, w2;
     IX p1, p2, p3, p4;
-    const double* dimg = img + (IX)J.cplane * npix;  // the plane the criterion reads
     // a uniform stencil decides "interpolate" exactly; under CERT only where the tolerance
     // leaves room for rounding of the values (R_abs > 0)
     const bool flat = sc.on && !sc.abs_any && J.interp == ART_INTERP_LINEAR &&
-                      (!CERT || J.R_abs > 0.0) && uniform_stencil<IX>(dimg, J.nx, J.ny, i, j, s, cat);
-    const int scr = flat ? 0 : screen_decide<IX>(sc, dimg, J.nx, J.ny, i, j, s, cat);
+                      (!CERT || J.R_abs > 0.0) && uniform_stencil(V, J.nx, J.ny, i, j, s, cat);
+    const int scr = flat ? 0 : screen_decide(sc, V, J.nx, J.ny, i, j, s, cat);
     bool trace;
     if (scr < 0) {
         double ea, er;
-        trace = decide<IX>(J, dimg, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4, ea, er);
+        trace = decide<IX>(J, V, i, j, s, norm, cat, w1, w2, p1, p2, p3, p4, ea, er);
         if constexpr (CERT) {
             if (!decision_robust(J, ea, er, ca->band) && !stencil_exact(J, ca->xst, i, j, s, cat))
                 return 3;
@@ -598,7 +652,10 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
     }
     (void)w1;
     (void)w2;
-    write_interp<IX>(J, img, pix, p1, p2, p3, p4, cat, npix);
+    if (J.planes == 1)
+        write_interp_v(J, V, img + pix, i, j, s, cat);
+    else
+        write_interp<IX>(J, img, pix, p1, p2, p3, p4, cat, npix);
     if (mask) mask[pix] = ART_MASK_INTERP;
     if constexpr (CERT) {
         const uint8_t* x = ca->xst;
@@ -614,51 +671,107 @@ __device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, d
     return 0;
 }
 
-// Rows of the level lattice over blockIdx.y, columns over blockIdx.x and the threads: no index
-// division, and a warp covers 32 consecutive lattice points of one row.  Pixel offsets within a
-// plane are 32-bit (images are below 2^31 pixels: the ray queue holds 32-bit pixel indices), which
-// keeps the stencil's address arithmetic off the wide-multiply path.
+template <class IX, bool CERT = false>
+__device__ __forceinline__ int refine_point(const DevJob& J, const Screen& sc, double* img,
+                                            uint8_t* mask, int i, int j, int s, int cat,
+                                            double norm, int64_t npix, bool spec, float* aminr,
+                                            float* aturn, const CertArgs* ca = nullptr)
+{
+    const GlobalSrc<IX> V{img + (IX)J.cplane * npix, J.nx};  // the plane the criterion reads
+    return refine_point_s<IX, CERT>(J, sc, V, img, mask, i, j, s, cat, norm, npix, spec, aminr,
+                                    aturn, ca);
+}
+
+// The level kernel works on tiles of the coarser (level k-1) lattice.  A block holds RT_X x RT_Y
+// coarse cells, one per thread; a cell owns the (up to) three new points at its right edge
+// midpoint (category 3), lower edge midpoint (2) and centre (4).  Their stencils reach one coarse
+// point before and two after the tile along each axis, so the block first copies that
+// (RT_X + 3) x (RT_Y + 3) window of the criterion plane into shared memory, once, with the FP32
+// high words the screen reads beside it; every stencil value is then a shared-memory read
+// instead of a global load per use (a coarse point is read by up to twelve stencils).
+constexpr int RT_X = 32, RT_Y = 8;
+constexpr int RT_HX = RT_X + 3, RT_HY = RT_Y + 3;
+
+struct TileSrc {
+    const double* v;    // [RT_HY][RT_HX] values of the criterion plane
+    const float* f;     // their FP32 high words, NaN where hiword_f32 reports not ok
+    const double* img;  // the criterion plane in global memory
+    int sh, ox, oy;     // coarse index = fine >> sh; coarse index of v[0][0]
+    __device__ __forceinline__ int idx(int i, int j) const
+    {
+        return ((j >> sh) - oy) * RT_HX + ((i >> sh) - ox);
+    }
+    __device__ __forceinline__ double at(int i, int j) const { return v[idx(i, j)]; }
+    __device__ __forceinline__ float at_f(int i, int j, bool& ok) const
+    {
+        const float x = f[idx(i, j)];
+        if (x != x) {
+            ok = false;
+            return 0.f;
+        }
+        return x;
+    }
+    __device__ __forceinline__ const double* plane() const { return img; }
+};
+
 template <bool CERT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(RT_X * RT_Y)
     refine_kernel(DevJob J, int level, const double* __restrict__ norm_ptr, double* img,
                   uint8_t* mask, int32_t* queue, unsigned long long* qcount, float* aminr,
                   float* aturn, unsigned long long* counters, CertArgs ca, int32_t* border,
                   unsigned long long* cert_counters, unsigned long long border_cap)
 {
     const int s = 1 << (J.levels - level);
-    const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
+    const int sh = J.levels - level + 1;  // coarse stride 2 s = 1 << sh
+    const int ncx = (J.nx - 1) / (2 * s) + 1, ncy = (J.ny - 1) / (2 * s) + 1;
     const int64_t npix = (int64_t)J.nx * J.ny;
+    const double* plane = img + (int64_t)J.cplane * npix;
     const double norm = *norm_ptr;
     // the screen's thresholds once per block: made per thread, the compiler recomputed their
     // FP64 products inside the loop (to save registers), which kept GB300's FP64 pipe 75 % busy
     __shared__ Screen sc_s;
+    __shared__ double tv[RT_HY * RT_HX];
+    __shared__ float tf[RT_HY * RT_HX];
     if (threadIdx.x == 0) sc_s = make_screen(J, norm, CERT ? ca.band : 0.0);
-    __syncthreads();
-    const Screen sc = sc_s;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, tx = threadIdx.x % RT_X, ty = threadIdx.x / RT_X;
     // exact decisions on a degenerate image: every value is FP64 from here on, so a speculative
     // (FP32) ray the criterion asks for is traced again
     const bool spec_ok = counters != nullptr && !(CERT && cert_counters[C_DEGEN] != 0);
-    for (int jj = blockIdx.y; jj < nky; jj += gridDim.y) {
-        const int oj = jj & 1;
-        for (int i0 = blockIdx.x * blockDim.x; i0 < nkx; i0 += gridDim.x * blockDim.x) {
-            const int ii = i0 + (int)threadIdx.x;
+    const int X0 = blockIdx.x * RT_X;
+    for (int Y0 = blockIdx.y * RT_Y; Y0 < ncy; Y0 += gridDim.y * RT_Y) {
+        __syncthreads();  // the previous tile is read; the screen is written
+        for (int q = threadIdx.x; q < RT_HY * RT_HX; q += blockDim.x) {
+            const int hy = q / RT_HX, hx = q - hy * RT_HX;
+            const int cx = X0 - 1 + hx, cy = Y0 - 1 + hy;
+            double v = 0.0;  // outside the lattice: never read (the stencils check the image edge)
+            if (cx >= 0 && cx < ncx && cy >= 0 && cy < ncy)
+                v = __ldg(plane + ((int64_t)cy << sh) * J.nx + ((int64_t)cx << sh));
+            bool ok = true;
+            const float f = hiword_f32(v, ok);
+            tv[q] = v;
+            tf[q] = ok ? f : __int_as_float(0x7fffffff);
+        }
+        __syncthreads();
+        const Screen sc = sc_s;
+        const TileSrc V{tv, tf, plane, sh, X0 - 1, Y0 - 1};
+        const int cx = X0 + tx, cy = Y0 + ty;
+#pragma unroll 1
+        for (int t = 0; t < 3; ++t) {
+            const int oi = t != 1, oj = t != 0;  // t = 0: category 3, 1: category 2, 2: category 4
+            const bool act = cx + oi < ncx && cy + oj < ncy;
             bool trace = false, used = false, bord = false;
             int32_t pix = 0;
             int i = 0, j = 0, cat = 0;
-            if (ii < nkx) {
-                const int oi = ii & 1;
-                if (oi | oj) {
-                    i = ii * s;
-                    j = jj * s;
-                    cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                    const int r = refine_point<int, CERT>(J, sc, img, mask, i, j, s, cat, norm,
-                                                          npix, spec_ok, aminr, aturn, &ca);
-                    trace = r == 1;
-                    used = r == 2;
-                    bord = r == 3;
-                    pix = j * J.nx + i;
-                }
+            if (act) {
+                i = (2 * cx + oi) * s;
+                j = (2 * cy + oj) * s;
+                cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+                const int r = refine_point_s<int, CERT>(J, sc, V, img, mask, i, j, s, cat, norm,
+                                                        npix, spec_ok, aminr, aturn, &ca);
+                trace = r == 1;
+                used = r == 2;
+                bord = r == 3;
+                pix = j * J.nx + i;
             }
             if constexpr (CERT) {
                 // borderline points join the exact-decision list; where it is full they are
@@ -666,7 +779,8 @@ __global__ void __launch_bounds__(256)
                 const unsigned bb = __ballot_sync(0xffffffffu, bord);
                 if (bb) {
                     unsigned long long w = 0;
-                    if (lane == 0) w = atomicAdd(cert_counters + C_BORDER, (unsigned long long)__popc(bb));
+                    if (lane == 0)
+                        w = atomicAdd(cert_counters + C_BORDER, (unsigned long long)__popc(bb));
                     w = __shfl_sync(0xffffffffu, w, 0);
                     if (bord) {
                         const unsigned long long slot = w + __popc(bb & ((1u << lane) - 1u));
@@ -675,9 +789,9 @@ __global__ void __launch_bounds__(256)
                             if (mask) mask[pix] = MASK_PENDING;
                         } else {
                             atomicAdd(cert_counters + C_CERTOVF, 1ull);
-                            const int r = refine_point<int, false>(J, sc, img, mask, i, j, s, cat,
-                                                                   norm, npix, spec_ok, aminr,
-                                                                   aturn);
+                            const int r = refine_point_s<int, false>(J, sc, V, img, mask, i, j, s,
+                                                                     cat, norm, npix, spec_ok,
+                                                                     aminr, aturn, nullptr);
                             trace = r == 1;
                             used = r == 2;
                             if (r == 0) ca.xst[pix] = 0;  // an interpolant of unchecked parents
@@ -704,17 +818,15 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Launch shape of the row-wise kernels: enough blocks along a row to cover it (at most 16), and
-// rows spread so that the grid holds about 152 x 16 blocks.
-static dim3 refine_grid(int nkx, int nky)
+// Launch shape of the level kernel: the tiles of a row of the coarse lattice over blockIdx.x, its
+// rows of tiles over blockIdx.y (a grid-stride loop past 65535).
+static dim3 refine_tile_grid(const DevJob& J, int level)
 {
-    int gx = (nkx + 255) / 256;
-    if (gx > 16) gx = 16;
-    if (gx < 1) gx = 1;
-    int gy = (152 * 16) / gx;
-    if (gy > nky) gy = nky;
-    if (gy < 1) gy = 1;
-    return dim3(gx, gy);
+    const int s = 1 << (J.levels - level);
+    const int ncx = (J.nx - 1) / (2 * s) + 1, ncy = (J.ny - 1) / (2 * s) + 1;
+    int gy = (ncy + RT_Y - 1) / RT_Y;
+    if (gy > 65535) gy = 65535;
+    return dim3((ncx + RT_X - 1) / RT_X, gy);
 }
 
 cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double* img,
@@ -722,11 +834,9 @@ cudaError_t launch_refine(const DevJob& J, int level, const double* norm, double
                           cudaStream_t st, float* aux_minr, float* aux_turn,
                           unsigned long long* spec_counters)
 {
-    const int s = 1 << (J.levels - level);
-    const dim3 g = refine_grid((J.nx - 1) / s + 1, (J.ny - 1) / s + 1);
-    refine_kernel<false><<<g, 256, 0, st>>>(J, level, norm, img, mask, queue, count, aux_minr,
-                                            aux_turn, spec_counters, CertArgs{nullptr, 0.0},
-                                            nullptr, nullptr, 0);
+    refine_kernel<false><<<refine_tile_grid(J, level), RT_X * RT_Y, 0, st>>>(
+        J, level, norm, img, mask, queue, count, aux_minr, aux_turn, spec_counters,
+        CertArgs{nullptr, 0.0}, nullptr, nullptr, 0);
     return cudaGetLastError();
 }
 
@@ -746,11 +856,9 @@ cudaError_t launch_refine_cert(const DevJob& J, int level, const double* norm, d
                                int32_t* border, unsigned long long* counters,
                                unsigned long long border_cap)
 {
-    const int s = 1 << (J.levels - level);
-    const dim3 g = refine_grid((J.nx - 1) / s + 1, (J.ny - 1) / s + 1);
-    refine_kernel<true><<<g, 256, 0, st>>>(J, level, norm, img, mask, queue, count, aux_minr,
-                                           aux_turn, spec_counters, CertArgs{xst, band}, border,
-                                           counters, border_cap);
+    refine_kernel<true><<<refine_tile_grid(J, level), RT_X * RT_Y, 0, st>>>(
+        J, level, norm, img, mask, queue, count, aux_minr, aux_turn, spec_counters,
+        CertArgs{xst, band}, border, counters, border_cap);
     return cudaGetLastError();
 }
 
@@ -1003,7 +1111,8 @@ __global__ void cert_redecide_kernel(DevJob J, int level, const double* __restri
         if (!stencil_exact(J, xst, i, j, s, cat)) atomicAdd(counters + C_CERTERR, 1ull);
         double w1, w2, ea, er;
         int p1, p2, p3, p4;
-        bool tr = decide<int>(J, img + (int64_t)J.cplane * npix, i, j, s, norm, cat, w1, w2, p1,
+        const GlobalSrc<int> V{img + (int64_t)J.cplane * npix, J.nx};
+        bool tr = decide<int>(J, V, i, j, s, norm, cat, w1, w2, p1,
                               p2, p3, p4, ea, er);
         if (J.edge_mode == ART_EDGE_TRACE) {
             const int di = (cat == 2) ? 0 : s, dj = (cat == 3) ? 0 : s;
