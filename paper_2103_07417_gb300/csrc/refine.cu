@@ -714,6 +714,24 @@ struct TileSrc {
     __device__ __forceinline__ const double* plane() const { return img; }
 };
 
+// Copy the window of coarse points [X0 - 1, X0 + RT_X + 1] x [Y0 - 1, Y0 + RT_Y + 1] of the
+// criterion plane and their FP32 high words into the block's tile (all threads take part).
+__device__ __forceinline__ void load_refine_tile(const double* plane, int nx, int ncx, int ncy,
+                                                 int sh, int X0, int Y0, double* tv, float* tf)
+{
+    for (int q = threadIdx.x; q < RT_HY * RT_HX; q += blockDim.x) {
+        const int hy = q / RT_HX, hx = q - hy * RT_HX;
+        const int cx = X0 - 1 + hx, cy = Y0 - 1 + hy;
+        double v = 0.0;  // outside the lattice: never read (the stencils check the image edge)
+        if (cx >= 0 && cx < ncx && cy >= 0 && cy < ncy)
+            v = __ldg(plane + ((int64_t)cy << sh) * nx + ((int64_t)cx << sh));
+        bool ok = true;
+        const float f = hiword_f32(v, ok);
+        tv[q] = v;
+        tf[q] = ok ? f : __int_as_float(0x7fffffff);
+    }
+}
+
 template <bool CERT>
 __global__ void __launch_bounds__(RT_X * RT_Y)
     refine_kernel(DevJob J, int level, const double* __restrict__ norm_ptr, double* img,
@@ -740,17 +758,7 @@ __global__ void __launch_bounds__(RT_X * RT_Y)
     const int X0 = blockIdx.x * RT_X;
     for (int Y0 = blockIdx.y * RT_Y; Y0 < ncy; Y0 += gridDim.y * RT_Y) {
         __syncthreads();  // the previous tile is read; the screen is written
-        for (int q = threadIdx.x; q < RT_HY * RT_HX; q += blockDim.x) {
-            const int hy = q / RT_HX, hx = q - hy * RT_HX;
-            const int cx = X0 - 1 + hx, cy = Y0 - 1 + hy;
-            double v = 0.0;  // outside the lattice: never read (the stencils check the image edge)
-            if (cx >= 0 && cx < ncx && cy >= 0 && cy < ncy)
-                v = __ldg(plane + ((int64_t)cy << sh) * J.nx + ((int64_t)cx << sh));
-            bool ok = true;
-            const float f = hiword_f32(v, ok);
-            tv[q] = v;
-            tf[q] = ok ? f : __int_as_float(0x7fffffff);
-        }
+        load_refine_tile(plane, J.nx, ncx, ncy, sh, X0, Y0, tv, tf);
         __syncthreads();
         const Screen sc = sc_s;
         const TileSrc V{tv, tf, plane, sh, X0 - 1, Y0 - 1};
@@ -1343,7 +1351,9 @@ cudaError_t launch_norm_batch(const DevJob* jobs, double* const* imgs, int n, do
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256)
+// The batched level kernel: the tiled level kernel over the images of a batch (blockIdx.z), the
+// rays appended as (image << 32) | pixel.
+__global__ void __launch_bounds__(RT_X * RT_Y)
     refine_batch_kernel(const DevJob* jobs, int level, const double* __restrict__ norms,
                         double* const* imgs, uint8_t* const* masks, int64_t* queue,
                         unsigned long long* qcount, unsigned long long* img_counts,
@@ -1355,31 +1365,40 @@ __global__ void __launch_bounds__(256)
     double* img = imgs[im];
     uint8_t* mask = masks[im];
     const int s = 1 << (J.levels - level);
-    const int nkx = (J.nx - 1) / s + 1, nky = (J.ny - 1) / s + 1;
+    const int sh = J.levels - level + 1;
+    const int ncx = (J.nx - 1) / (2 * s) + 1, ncy = (J.ny - 1) / (2 * s) + 1;
+    const int X0 = blockIdx.x * RT_X;
+    if (X0 >= ncx) return;  // the whole block: the image is narrower than the widest one
     const int64_t npix = (int64_t)J.nx * J.ny;
+    const double* plane = img + (int64_t)J.cplane * npix;  // the criterion's plane
     const double norm = norms[4 * im];
     __shared__ Screen sc_s;  // once per block, as in refine_kernel
+    __shared__ double tv[RT_HY * RT_HX];
+    __shared__ float tf[RT_HY * RT_HX];
     if (threadIdx.x == 0) sc_s = make_screen(J, norm);
-    __syncthreads();
-    const Screen sc = sc_s;
-    const int lane = threadIdx.x & 31;
-    for (int jj = blockIdx.y; jj < nky; jj += gridDim.y) {
-        const int oj = jj & 1;
-        for (int i0 = blockIdx.x * blockDim.x; i0 < nkx; i0 += gridDim.x * blockDim.x) {
-            const int ii = i0 + (int)threadIdx.x;
+    const int lane = threadIdx.x & 31, tx = threadIdx.x % RT_X, ty = threadIdx.x / RT_X;
+    for (int Y0 = blockIdx.y * RT_Y; Y0 < ncy; Y0 += gridDim.y * RT_Y) {
+        __syncthreads();
+        load_refine_tile(plane, J.nx, ncx, ncy, sh, X0, Y0, tv, tf);
+        __syncthreads();
+        const Screen sc = sc_s;
+        const TileSrc V{tv, tf, plane, sh, X0 - 1, Y0 - 1};
+        const int cx = X0 + tx, cy = Y0 + ty;
+#pragma unroll 1
+        for (int t = 0; t < 3; ++t) {
+            const int oi = t != 1, oj = t != 0;
+            const bool act = cx + oi < ncx && cy + oj < ncy;
             bool trace = false, used = false;
             int32_t pix = 0;
-            if (ii < nkx) {
-                const int oi = ii & 1;
-                if (oi | oj) {
-                    const int i = ii * s, j = jj * s;
-                    const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
-                    const int r = refine_point<int>(J, sc, img, mask, i, j, s, cat, norm, npix,
-                                                    counters != nullptr, nullptr, nullptr);
-                    trace = r == 1;
-                    used = r == 2;
-                    pix = j * J.nx + i;
-                }
+            if (act) {
+                const int i = (2 * cx + oi) * s, j = (2 * cy + oj) * s;
+                const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+                const int r = refine_point_s<int, false>(J, sc, V, img, mask, i, j, s, cat, norm,
+                                                         npix, counters != nullptr, nullptr,
+                                                         nullptr, nullptr);
+                trace = r == 1;
+                used = r == 2;
+                pix = j * J.nx + i;
             }
             const unsigned b = __ballot_sync(0xffffffffu, trace);
             if (b) {
@@ -1409,14 +1428,16 @@ cudaError_t launch_refine_batch(const DevJob* jobs, int n, int level, int max_kx
                                 unsigned long long* img_counts, cudaStream_t st,
                                 unsigned long long* spec_counters)
 {
-    int gx = (max_kx + 255) / 256;
-    if (gx > 16) gx = 16;
-    if (gx < 1) gx = 1;
-    int gy = (152 * 16) / (gx * (n > 0 ? n : 1));
-    if (gy > max_ky) gy = max_ky;
+    // tiles of the widest image's coarse lattice (max_kx, max_ky: the largest level lattice)
+    const int ncx = (max_kx - 1) / 2 + 1, ncy = (max_ky - 1) / 2 + 1;
+    int gy = (ncy + RT_Y - 1) / RT_Y;
+    if (gy > 65535) gy = 65535;
     if (gy < 1) gy = 1;
-    refine_batch_kernel<<<dim3(gx, gy, n), 256, 0, st>>>(jobs, level, norms, imgs, masks, queue,
-                                                         qcount, img_counts, spec_counters);
+    int gx = (ncx + RT_X - 1) / RT_X;
+    if (gx < 1) gx = 1;
+    refine_batch_kernel<<<dim3(gx, gy, n), RT_X * RT_Y, 0, st>>>(jobs, level, norms, imgs, masks,
+                                                                 queue, qcount, img_counts,
+                                                                 spec_counters);
     return cudaGetLastError();
 }
 
