@@ -16,6 +16,15 @@ using namespace art;
 
 struct art_ctx {
     art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT};
+    // exact decisions in a batch (art_render_batch): sub-contexts, each with a stream of its own
+    // and its own scratch, render the images concurrently; every image's counters and
+    // normalisation are copied into xsnap on its sub-context's stream
+    std::vector<art_ctx*> subs;
+    bool owns_stream = false;
+    cudaEvent_t sub_in = nullptr;
+    std::vector<cudaEvent_t> sub_out;
+    unsigned long long* xsnap = nullptr;
+    int64_t xsnap_cap = 0;
     // bumped whenever a scratch buffer is (re)allocated: a captured graph holds the pointers of
     // its capture and is replayed only while this is unchanged
     uint64_t scratch_gen = 0;
@@ -389,6 +398,11 @@ extern "C" void art_destroy(art_ctx* c)
 {
     if (!c) return;
     cudaSetDevice(c->device);
+    for (art_ctx* d : c->subs) art_destroy(d);
+    if (c->sub_in) cudaEventDestroy(c->sub_in);
+    for (cudaEvent_t e : c->sub_out)
+        if (e) cudaEventDestroy(e);
+    cudaFree(c->xsnap);
     cudaStreamSynchronize(c->stream);
     if (c->gstream) cudaStreamSynchronize(c->gstream);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -438,6 +452,7 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFree(c->aq);
     for (int k = 0; k < 2 * art_ctx::PROF_MAX; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->owns_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
@@ -647,6 +662,39 @@ extern "C" int art_refine_level(art_ctx* c, const art_job* job, double* img_dev,
                      c->stream));
     if ((rc = read_counters(c))) return rc;
     if (count_host) *count_host = (int64_t)c->pinned[C_QUEUE];
+    return ART_OK;
+}
+
+// A render's statistics from a copy of its counters and its normalisation; ART_ERR_DEVICE when a
+// kernel reported an inconsistency.
+static int stats_from(const DevJob& J, const unsigned long long* cnt, double norm, int launches,
+                      bool cert, bool ax, art_stats* stats)
+{
+    memset(stats, 0, sizeof *stats);
+    for (int k = 0; k <= J.levels && k < 16; ++k) {
+        stats->rays_per_level[k] = (int64_t)cnt[C_LEVEL0 + k];
+        stats->rays_traced += stats->rays_per_level[k];
+    }
+    stats->rays_fp64 = (int64_t)cnt[C_FP64];
+    stats->steps = (int64_t)cnt[C_STEPS];
+    stats->rays_capped = (int64_t)cnt[C_CAPPED];
+    stats->rays_nan = (int64_t)cnt[C_NAN];
+    stats->norm = norm;
+    stats->kernel_launches = launches;
+    stats->rays_speculative = (int64_t)cnt[C_SPEC];
+    stats->rays_spec_used = (int64_t)cnt[C_SPECUSED];
+    if (ax) {
+        // rays actually traced: the axis filter's kept points (per level: queued minus
+        // axis-interpolated)
+        stats->rays_traced = (int64_t)cnt[C_AXKEPT];
+        stats->border_points = (int64_t)cnt[C_AXINTERP];
+    }
+    if (cert) {
+        stats->rays_exact = (int64_t)cnt[C_XRAYS] + stats->rays_per_level[0];
+        stats->border_points = (int64_t)cnt[C_BTOT];
+        stats->border_overflow = (int64_t)cnt[C_CERTOVF];
+    }
+    if (cnt[C_BADIDX] || cnt[C_SYNCERR] || cnt[C_CERTERR]) return ART_ERR_DEVICE;
     return ART_OK;
 }
 
@@ -889,32 +937,7 @@ static int render_impl(art_ctx* c, const art_job* job, const double* truth_dev, 
     c->prof_level = -1;
     if (stats) {
         if ((rc = read_counters(c))) return rc;
-        memset(stats, 0, sizeof *stats);
-        for (int k = 0; k <= J.levels && k < 16; ++k) {
-            stats->rays_per_level[k] = (int64_t)c->pinned[C_LEVEL0 + k];
-            stats->rays_traced += stats->rays_per_level[k];
-        }
-        stats->rays_fp64 = (int64_t)c->pinned[C_FP64];
-        stats->steps = (int64_t)c->pinned[C_STEPS];
-        stats->rays_capped = (int64_t)c->pinned[C_CAPPED];
-        stats->rays_nan = (int64_t)c->pinned[C_NAN];
-        stats->norm = c->pinned_d[0];
-        stats->kernel_launches = c->launches;
-        stats->rays_speculative = (int64_t)c->pinned[C_SPEC];
-        stats->rays_spec_used = (int64_t)c->pinned[C_SPECUSED];
-        if (ax) {
-            // rays actually traced: the axis filter's kept points (per level: queued minus
-            // axis-interpolated)
-            stats->rays_traced = (int64_t)c->pinned[C_AXKEPT];
-            stats->border_points = (int64_t)c->pinned[C_AXINTERP];
-        }
-        if (cert) {
-            stats->rays_exact = (int64_t)c->pinned[C_XRAYS] + stats->rays_per_level[0];
-            stats->border_points = (int64_t)c->pinned[C_BTOT];
-            stats->border_overflow = (int64_t)c->pinned[C_CERTOVF];
-        }
-        if (c->pinned[C_BADIDX] || c->pinned[C_SYNCERR] || c->pinned[C_CERTERR])
-            return ART_ERR_DEVICE;
+        return stats_from(J, c->pinned, c->pinned_d[0], c->launches, cert, ax != nullptr, stats);
     }
     return ART_OK;
 }
@@ -1422,15 +1445,55 @@ static int run_batch(art_ctx* c, const BatchPlan& P)
 
 static void destroy_plan(BatchPlan* p) { delete p; }
 
-extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const* imgs,
-                                uint8_t* const* masks, art_stats* stats)
+// Exact decisions keep per-image closure lists, so a batch of them runs the single-image level
+// loop once per image.  Each level of an image ends in a short FP64 launch that lasts as long as
+// its longest ray while the rest of the GPU idles, so the images run concurrently: image i on
+// sub-context i mod EXACT_SUBS, each with its own stream and scratch, ordered after the caller's
+// stream by one event and joined back into it by one event per sub-context.  Jobs with the
+// learned proposal (whose network lives in this context) run one after the other here instead.
+constexpr int EXACT_SUBS = 32;
+
+static int ensure_subs(art_ctx* c)
 {
-    if (!c || !jobs || !imgs || n < 1) return ART_ERR_ARG;
-    if (jobs[0].precision == ART_MIXED_EXACT) {
-        // exact decisions keep per-image closure lists: the images are rendered one after the
-        // other through the single-image level loop (every job of the batch must ask for them)
-        for (int i = 0; i < n; ++i)
-            if (jobs[i].precision != ART_MIXED_EXACT) return ART_ERR_ARG;
+    if (c->subs.empty()) {
+        for (int k = 0; k < EXACT_SUBS; ++k) {
+            art_ctx* d = new art_ctx();
+            d->device = c->device;
+            d->num_sms = c->num_sms;
+            memcpy(d->occ, c->occ, sizeof c->occ);
+            memcpy(d->occb, c->occb, sizeof c->occb);
+            if (cudaStreamCreateWithFlags(&d->stream, cudaStreamNonBlocking) != cudaSuccess) {
+                delete d;
+                return ART_ERR_CUDA;
+            }
+            d->owns_stream = true;
+            c->subs.push_back(d);
+        }
+        CK(cudaEventCreateWithFlags(&c->sub_in, cudaEventDisableTiming));
+        c->sub_out.assign(EXACT_SUBS, nullptr);
+        for (cudaEvent_t& e : c->sub_out) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    for (art_ctx* d : c->subs) {  // the loaded snapshot (referenced) and the kernel-form tuning
+        d->grid = c->grid;
+        d->g_n1 = c->g_n1;
+        d->g_n2 = c->g_n2;
+        d->g_n3 = c->g_n3;
+        d->g_x1min = c->g_x1min;
+        d->g_x1max = c->g_x1max;
+        d->tune = c->tune;
+    }
+    return ART_OK;
+}
+
+static int render_batch_exact(art_ctx* c, const art_job* jobs, int n, double* const* imgs,
+                              uint8_t* const* masks, art_stats* stats)
+{
+    bool learned = false;
+    for (int i = 0; i < n; ++i) {
+        if (jobs[i].precision != ART_MIXED_EXACT) return ART_ERR_ARG;
+        learned = learned || jobs[i].proposal != 0;
+    }
+    if (learned) {
         for (int i = 0; i < n; ++i) {
             const int rc = art_render(c, &jobs[i], nullptr, imgs[i], masks ? masks[i] : nullptr,
                                       stats ? &stats[i] : nullptr);
@@ -1438,6 +1501,73 @@ extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, doub
         }
         return ART_OK;
     }
+    std::vector<DevJob> J(n);
+    for (int i = 0; i < n; ++i) {
+        int rc = make_devjob(&jobs[i], &J[i]);
+        if (rc || (rc = check_grid(c, &jobs[i]))) return rc;
+        if (!imgs[i]) return ART_ERR_ARG;
+    }
+    CK(cudaSetDevice(c->device));
+    int rc = ensure_subs(c);
+    if (rc) return rc;
+    constexpr int SNAP = C_COUNT + 1;  // counters, then the normalisation's bits
+    if (stats && (int64_t)n * SNAP > c->xsnap_cap) {
+        CK(cudaStreamSynchronize(c->stream));
+        cudaFree(c->xsnap);
+        c->xsnap = nullptr;
+        c->xsnap_cap = 0;
+        CK(cudaMalloc(&c->xsnap, sizeof(unsigned long long) * SNAP * n));
+        c->xsnap_cap = (int64_t)SNAP * n;
+    }
+    // the largest images first, so that a sub-context's scratch is sized by its first image
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return (int64_t)J[a].nx * J[a].ny > (int64_t)J[b].nx * J[b].ny;
+    });
+    std::vector<int> launches(n, 0);
+    CK(cudaEventRecord(c->sub_in, c->stream));
+    for (art_ctx* d : c->subs) CK(cudaStreamWaitEvent(d->stream, c->sub_in, 0));
+    for (int q = 0; q < n; ++q) {
+        const int i = order[q];
+        art_ctx* d = c->subs[q % EXACT_SUBS];
+        if ((rc = render_impl(d, &jobs[i], nullptr, imgs[i], masks ? masks[i] : nullptr, nullptr,
+                              nullptr)))
+            return rc;
+        launches[i] = d->launches;
+        if (stats) {
+            CK(cudaMemcpyAsync(c->xsnap + (int64_t)SNAP * i, d->counters,
+                               sizeof(unsigned long long) * C_COUNT, cudaMemcpyDeviceToDevice,
+                               d->stream));
+            CK(cudaMemcpyAsync(c->xsnap + (int64_t)SNAP * i + C_COUNT, d->norm3, sizeof(double),
+                               cudaMemcpyDeviceToDevice, d->stream));
+        }
+    }
+    for (int k = 0; k < EXACT_SUBS; ++k) {
+        CK(cudaEventRecord(c->sub_out[k], c->subs[k]->stream));
+        CK(cudaStreamWaitEvent(c->stream, c->sub_out[k], 0));
+    }
+    if (!stats) return ART_OK;
+    std::vector<unsigned long long> h((size_t)SNAP * n);
+    CK(cudaMemcpyAsync(h.data(), c->xsnap, sizeof(unsigned long long) * SNAP * n,
+                       cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int err = ART_OK;
+    for (int i = 0; i < n; ++i) {
+        double norm;
+        memcpy(&norm, &h[(size_t)SNAP * i + C_COUNT], sizeof norm);
+        const int r = stats_from(J[i], &h[(size_t)SNAP * i], norm, launches[i], true, false,
+                                 &stats[i]);
+        if (r && !err) err = r;
+    }
+    return err;
+}
+
+extern "C" int art_render_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const* imgs,
+                                uint8_t* const* masks, art_stats* stats)
+{
+    if (!c || !jobs || !imgs || n < 1) return ART_ERR_ARG;
+    if (jobs[0].precision == ART_MIXED_EXACT) return render_batch_exact(c, jobs, n, imgs, masks, stats);
     BatchPlan P;
     int rc = plan_batch(c, jobs, n, imgs, masks, P);
     if (rc) return rc;

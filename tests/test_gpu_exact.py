@@ -124,7 +124,7 @@ def test_exact_decisions_full_size(ctx, name):
 
 def test_exact_decisions_batch_images(ctx):
     """Every image of the 256-image mixed-parameter batch (subring planes n = 0, 1, 2) rendered
-    with exact decisions (art_render_batch renders them one by one) against the FP64 batch: each
+    with exact decisions (art_render_batch runs the images concurrently) against the FP64 batch: each
     plane of each image within the mixed bound, masks equal except within 1e-9 of a tolerance."""
     from paper_2103_07417_gb300 import art
     bp = W.grmhd_batch(seed=0, n=256)
@@ -142,6 +142,26 @@ def test_exact_decisions_batch_images(ctx):
             assert all(x <= 1e-9 for x in d), d
     print("batch worst bj", worst, "flips", nflip)
     assert worst <= 1e-5
+
+
+def test_exact_batch_equals_single_renders(ctx):
+    """art_render_batch with exact decisions runs the single-image level loop of each image on
+    sub-contexts with streams of their own, concurrently: images, masks and statistics equal the
+    images rendered one at a time by art_render, bit for bit, in any batch order and size (a
+    batch larger than the number of sub-contexts, images of different sizes and depths)."""
+    from paper_2103_07417_gb300 import art
+    bp = W.grmhd_batch(seed=4, n=40)
+    jx = [art.make_job(**{**p, "precision": "mixed_exact"}) for p in bp]
+    ix, mx, sx = ctx.render_batch(jx)
+    torch.cuda.synchronize()
+    for j, a, ma, sa in zip(jx, ix, mx, sx):
+        b, mb, sb = ctx.render(j)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        assert torch.equal(ma, mb)
+        for k in ("rays_per_level", "rays_exact", "border_points", "steps", "norm",
+                  "kernel_launches"):
+            assert sa[k] == sb[k], (k, sa[k], sb[k])
 
 
 def test_mixed_hands_over_rays_near_emission_edges(ctx):
