@@ -300,29 +300,36 @@ int art_visibilities(art_ctx* ctx, const double* img_dev, const double* ref_dev,
 int art_render_host(art_ctx* ctx, const art_job* job, double* img_host, uint8_t* mask_host,
                     art_stats* stats_host);
 
-/* Kernel forms of the FP32 pass (the paper has no counterpart: a scheduling choice of this
- * implementation).  A level's FP32 launch whose queue holds at most quad_rays rays per block of
- * the persistent grid splits each step over four warps per 32 rays (geodesic, two warps for the
- * emission coefficients of alternate steps, segment); at most pair_rays, over two warps (geodesic,
- * transfer); longer queues run one thread per ray.  The forms give bit-identical rays, so the
- * setting changes speed only.  Defaults ART_TUNE_QUAD_DEFAULT and ART_TUNE_PAIR_DEFAULT; valid
- * settings have 0 <= quad_rays <= pair_rays <= 4096. */
+/* Scheduling of the trace launches (the paper has no counterpart: choices of this
+ * implementation).  Kernel forms of the FP32 pass: a level's FP32 launch whose queue holds at most
+ * quad_rays rays per block of the persistent grid splits each step over four warps per 32 rays
+ * (geodesic, two warps for the emission coefficients of alternate steps, segment); at most
+ * pair_rays, over two warps (geodesic, transfer); longer queues run one thread per ray.  Grid size:
+ * the persistent grids of the FP64 launches hold blocks64 blocks of 128 threads per SM, those of
+ * the FP32 and double-float launches blocks32 (0: as many as fit; a larger value is capped there).
+ * The forms and grids give bit-identical rays, so the setting changes speed only.  Defaults
+ * ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, 0, 0; valid settings have
+ * 0 <= quad_rays <= pair_rays <= 4096 and 0 <= blocks64, blocks32 <= 64. */
 #define ART_TUNE_QUAD_DEFAULT 32
 #define ART_TUNE_PAIR_DEFAULT 64
 typedef struct art_tune {
     int32_t quad_rays;
     int32_t pair_rays;
+    int32_t blocks64;
+    int32_t blocks32;
 } art_tune;
 
-/* Set the context's kernel-form thresholds (t == NULL restores the defaults), or read them.
+/* Set the context's scheduling setting (t == NULL restores the defaults), or read it.
  * Errors: ART_ERR_ARG (null context, invalid setting). */
 int art_set_tune(art_ctx* ctx, const art_tune* t);
 int art_get_tune(art_ctx* ctx, art_tune* t_out);
 
-/* Autotuner: renders `job` (as art_render, into img_dev / mask_dev) with each of a fixed list of
- * kernel-form thresholds, once to warm up and `reps` times timed with CUDA events on the context's
- * stream, keeps the setting with the lowest median time in the context and returns it in *best
- * (nullable) with that median in *best_ms (nullable).  img_dev and mask_dev hold the job's image
+/* Autotuner: renders `job` (as art_render, into img_dev / mask_dev) with each candidate setting,
+ * once to warm up and `reps` times timed with CUDA events on the context's stream, one dimension at
+ * a time (eight FP32 kernel-form threshold pairs with both grids full; then, from the best, blocks64
+ * in {1, 2} if the job has FP64 launches; then blocks32 in {1, 2} if it has FP32 ones), keeps the
+ * setting with the lowest median time in the context and returns it in *best (nullable) with that
+ * median in *best_ms (nullable).  img_dev and mask_dev hold the job's image
  * afterwards (the same for every setting).  Synchronises the stream.  Errors: ART_ERR_ARG (reps
  * outside 1..32, or as art_render), and those of art_render, after which the previous setting is
  * kept. */

@@ -55,11 +55,13 @@ class Job(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     """art_tune: FP32 kernel-form thresholds in rays per block (quad form up to quad_rays, pair
-    form up to pair_rays)."""
-    _fields_ = [("quad_rays", ctypes.c_int32), ("pair_rays", ctypes.c_int32)]
+    form up to pair_rays) and the persistent grids' blocks per SM of the FP64 and of the FP32 /
+    double-float launches (0: as many as fit)."""
+    _fields_ = [("quad_rays", ctypes.c_int32), ("pair_rays", ctypes.c_int32),
+                ("blocks64", ctypes.c_int32), ("blocks32", ctypes.c_int32)]
 
 
-TUNE_DEFAULT = (32, 64)
+TUNE_DEFAULT = (32, 64, 0, 0)
 
 
 class Stats(ctypes.Structure):
@@ -439,27 +441,30 @@ class Context:
         _check(load().art_graph_render(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask)),
                "art_graph_render")
 
-    def art_set_tune(self, quad_rays: int | None = None, pair_rays: int | None = None):
-        """Set the FP32 kernel-form thresholds; no arguments restore the defaults."""
+    def art_set_tune(self, quad_rays: int | None = None, pair_rays: int | None = None,
+                     blocks64: int = 0, blocks32: int = 0):
+        """Set the scheduling (FP32 kernel-form thresholds, grid blocks per SM); no arguments
+        restore the defaults."""
         if quad_rays is None and pair_rays is None:
             _check(load().art_set_tune(self._ctx, None), "art_set_tune")
             return
-        t = Tune(int(quad_rays), int(pair_rays))
+        t = Tune(int(quad_rays), int(pair_rays), int(blocks64), int(blocks32))
         _check(load().art_set_tune(self._ctx, ctypes.byref(t)), "art_set_tune")
 
     def art_get_tune(self) -> tuple:
+        """(quad_rays, pair_rays, blocks64, blocks32)."""
         t = Tune()
         _check(load().art_get_tune(self._ctx, ctypes.byref(t)), "art_get_tune")
-        return t.quad_rays, t.pair_rays
+        return t.quad_rays, t.pair_rays, t.blocks64, t.blocks32
 
     def art_autotune(self, job: Job, img, mask, reps: int = 3):
         """Time `job` under each candidate setting, keep the fastest in the context; returns
-        ((quad_rays, pair_rays), median ms)."""
+        ((quad_rays, pair_rays, blocks64, blocks32), median ms)."""
         t = Tune()
         ms = ctypes.c_float()
         _check(load().art_autotune(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask), int(reps),
                                    ctypes.byref(t), ctypes.byref(ms)), "art_autotune")
-        return (t.quad_rays, t.pair_rays), ms.value
+        return (t.quad_rays, t.pair_rays, t.blocks64, t.blocks32), ms.value
 
     def art_measure_alu_peaks(self) -> dict:
         """Measured FP32 and FP64 fused multiply-add throughput of this GPU, TFLOP/s."""

@@ -15,7 +15,7 @@
 using namespace art;
 
 struct art_ctx {
-    art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT};
+    art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, 0, 0};
     // exact decisions in a batch (art_render_batch): sub-contexts, each with a stream of its own
     // and its own scratch, render the images concurrently; every image's counters and
     // normalisation are copied into xsnap on its sub-context's stream
@@ -353,6 +353,13 @@ static int check_grid(const art_ctx* c, const art_job* job)
     return (job->emission == ART_EMIT_GRID && !c->grid) ? ART_ERR_ARG : ART_OK;
 }
 
+// Persistent grid of a trace launch: SMs x resident blocks per SM, capped by the tuned blocks
+// per SM (0: as many as fit).
+static int trace_grid(const art_ctx* c, int occ, int tuned)
+{
+    return c->num_sms * (tuned > 0 && tuned < occ ? tuned : occ);
+}
+
 // Trace-kernel variant of a job (occupancy table index).
 static int variant_of(const DevJob& J)
 {
@@ -547,8 +554,9 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
         a.aux_minr = aux->min_r;
     }
     const int pl = variant_of(J);
-    const int g64 = c->num_sms * c->occ[TK_FP64][pl], g32 = c->num_sms * c->occ[TK_FP32][pl];
-    const int gdf = c->num_sms * c->occ[TK_DF][pl];
+    const int g64 = trace_grid(c, c->occ[TK_FP64][pl], c->tune.blocks64);
+    const int g32 = trace_grid(c, c->occ[TK_FP32][pl], c->tune.blocks32);
+    const int gdf = trace_grid(c, c->occ[TK_DF][pl], c->tune.blocks32);
     int k;
     if (J.precision == ART_FP64) {
         a.fetch = c->counters + C_FETCH;
@@ -1255,7 +1263,8 @@ static int trace_queue_batch(art_ctx* c, const DevJob& J0, const unsigned long l
     int k;
     if (J0.precision == ART_FP64) {
         k = prof_begin(c);
-        CK(launch_trace_batch(a, TK_FP64, c->num_sms * c->occb[TK_FP64][pl], c->stream));
+        CK(launch_trace_batch(a, TK_FP64, trace_grid(c, c->occb[TK_FP64][pl], c->tune.blocks64),
+                              c->stream));
         prof_end(c, k, ART_K_TRACE_FP64, -1);
         return ART_OK;
     }
@@ -1265,7 +1274,8 @@ static int trace_queue_batch(art_ctx* c, const DevJob& J0, const unsigned long l
         a.reroute_count = c->counters + C_REROUTE;
     }
     k = prof_begin(c);
-    CK(launch_trace_batch(a, TK_FP32, c->num_sms * c->occb[TK_FP32][pl], c->stream));
+    CK(launch_trace_batch(a, TK_FP32, trace_grid(c, c->occb[TK_FP32][pl], c->tune.blocks32),
+                          c->stream));
     prof_end(c, k, ART_K_TRACE_FP32, -1);
     if (mixed) {
         BatchTraceArgs b = a;
@@ -1276,7 +1286,9 @@ static int trace_queue_batch(art_ctx* c, const DevJob& J0, const unsigned long l
         b.fetch = c->counters + C_FETCH2;
         const int kd = J0.precision == ART_MIXED_DF ? TK_DF : TK_FP64;
         k = prof_begin(c);
-        CK(launch_trace_batch(b, kd, c->num_sms * c->occb[kd][pl], c->stream));
+        CK(launch_trace_batch(
+            b, kd, trace_grid(c, c->occb[kd][pl], kd == TK_FP64 ? c->tune.blocks64 : c->tune.blocks32),
+            c->stream));
         prof_end(c, k, kd == TK_DF ? ART_K_TRACE_DF : ART_K_TRACE_FP64, -1);
     }
     return ART_OK;
@@ -1726,14 +1738,15 @@ extern "C" int art_cnn_sample(art_ctx* c, const art_job* job, const double* img_
 
 static bool tune_valid(const art_tune* t)
 {
-    return t->quad_rays >= 0 && t->pair_rays >= t->quad_rays && t->pair_rays <= 4096;
+    return t->quad_rays >= 0 && t->pair_rays >= t->quad_rays && t->pair_rays <= 4096 &&
+           t->blocks64 >= 0 && t->blocks64 <= 64 && t->blocks32 >= 0 && t->blocks32 <= 64;
 }
 
 extern "C" int art_set_tune(art_ctx* c, const art_tune* t)
 {
     if (!c) return ART_ERR_ARG;
     if (!t) {
-        c->tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT};
+        c->tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, 0, 0};
         return ART_OK;
     }
     if (!tune_valid(t)) return ART_ERR_ARG;
@@ -1752,10 +1765,13 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
                             int32_t reps, art_tune* best, float* best_ms)
 {
     if (!c || !job || !img_dev || reps < 1 || reps > 32) return ART_ERR_ARG;
-    // candidates: one-thread only, pair only, and quad/pair splits around the defaults
-    static const art_tune cand[] = {{0, 0},    {0, 64},  {32, 64},  {32, 96},
-                                    {64, 96},  {32, 128}, {64, 128}, {16, 64}};
-    const int ncand = (int)(sizeof cand / sizeof cand[0]);
+    // candidates, one dimension at a time: the FP32 kernel-form thresholds (one-thread only, pair
+    // only, quad/pair splits around the defaults), then with the best of them the persistent
+    // grids' blocks per SM, of the FP64 launches (where the job has any) and of the FP32 and
+    // double-float ones (0 = as many as fit, else 1 or 2)
+    static const int forms[][2] = {{0, 0},   {0, 64},   {32, 64},  {32, 96},
+                                   {64, 96}, {32, 128}, {64, 128}, {16, 64}};
+    const bool has64 = job->precision != ART_FP32, has32 = job->precision != ART_FP64;
     CK(cudaSetDevice(c->device));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -1764,13 +1780,13 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
         return ART_ERR_CUDA;
     }
     const art_tune saved = c->tune;
-    art_tune win = saved;
+    art_tune win = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, 0, 0};
     float win_ms = INFINITY;
     int rc = ART_OK;
     std::vector<float> t(reps);
-    for (int k = 0; k < ncand && rc == ART_OK; ++k) {
-        c->tune = cand[k];
-        if ((rc = art_render(c, job, nullptr, img_dev, mask_dev, nullptr))) break;  // warm-up
+    auto trial = [&](const art_tune& cand) {
+        c->tune = cand;
+        if ((rc = art_render(c, job, nullptr, img_dev, mask_dev, nullptr))) return;  // warm-up
         for (int r = 0; r < reps && rc == ART_OK; ++r) {
             if (cudaEventRecord(e0, c->stream) != cudaSuccess) rc = ART_ERR_CUDA;
             if (!rc) rc = art_render(c, job, nullptr, img_dev, mask_dev, nullptr);
@@ -1778,14 +1794,31 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
             if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = ART_ERR_CUDA;
             if (!rc && cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess) rc = ART_ERR_CUDA;
         }
-        if (rc) break;
-        std::vector<float> s(t);
-        std::sort(s.begin(), s.end());
-        const float med = s[reps / 2];
+        if (rc) return;
+        std::vector<float> srt(t);
+        std::sort(srt.begin(), srt.end());
+        const float med = srt[reps / 2];
         if (med < win_ms) {
             win_ms = med;
-            win = cand[k];
+            win = cand;
         }
+    };
+    for (const auto& f : forms) {
+        if (rc) break;
+        if (has32 || (f[0] == ART_TUNE_QUAD_DEFAULT && f[1] == ART_TUNE_PAIR_DEFAULT))
+            trial(art_tune{f[0], f[1], 0, 0});
+    }
+    for (int b = 1; b <= 2 && has64 && !rc; ++b) {
+        art_tune cand = win;
+        cand.blocks64 = b;
+        trial(cand);
+    }
+    const int best64 = win.blocks64;
+    for (int b = 1; b <= 2 && has32 && !rc; ++b) {
+        art_tune cand = win;
+        cand.blocks64 = best64;
+        cand.blocks32 = b;
+        trial(cand);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -1,6 +1,7 @@
-"""Kernel-form thresholds (art_set_tune / art_get_tune) and the autotuner (art_autotune): the
-forms give bit-identical rays, so every setting renders the same image and mask, and the
-autotuner leaves one of its candidates in the context."""
+"""Trace scheduling (art_set_tune / art_get_tune: FP32 kernel-form thresholds and the persistent
+grids' blocks per SM) and the autotuner (art_autotune): the forms and grids give bit-identical rays,
+so every setting renders the same image and mask, and the autotuner leaves one of its candidates in
+the context."""
 import numpy as np
 import pytest
 import torch
@@ -21,12 +22,12 @@ def ctx():
 def test_tune_roundtrip_and_validation(ctx):
     from paper_2103_07417_gb300 import art
     assert ctx.art_get_tune() == art.TUNE_DEFAULT
-    ctx.art_set_tune(16, 128)
-    assert ctx.art_get_tune() == (16, 128)
-    for bad in ((-1, 64), (64, 32), (0, 5000)):
+    ctx.art_set_tune(16, 128, 1, 2)
+    assert ctx.art_get_tune() == (16, 128, 1, 2)
+    for bad in ((-1, 64), (64, 32), (0, 5000), (16, 128, -1, 0), (16, 128, 0, 65)):
         with pytest.raises(RuntimeError):
             ctx.art_set_tune(*bad)
-    assert ctx.art_get_tune() == (16, 128)
+    assert ctx.art_get_tune() == (16, 128, 1, 2)
     ctx.art_set_tune()
     assert ctx.art_get_tune() == art.TUNE_DEFAULT
 
@@ -42,13 +43,14 @@ def test_every_setting_renders_the_same_image(ctx, name, over):
     p = (W.kerr_disk_2049 if name == "kerr_disk_polarized" else W.kerr_analytic_2049)(**over)
     job = art.make_job(**p)
     ref = None
-    for q, pr in ((0, 0), (0, 4096), (4096, 4096), (32, 64), (8, 16)):
-        ctx.art_set_tune(q, pr)
+    for q, pr, b64, b32 in ((0, 0, 0, 0), (0, 4096, 0, 0), (4096, 4096, 0, 0), (32, 64, 0, 0),
+                            (8, 16, 0, 0), (32, 64, 1, 1), (0, 0, 2, 1), (4096, 4096, 1, 2)):
+        ctx.art_set_tune(q, pr, b64, b32)
         img, mask, st = ctx.render(job)
         if ref is None:
             ref = (img.clone(), mask.clone(), st["rays_per_level"])
         else:
-            assert torch.equal(img, ref[0]) and torch.equal(mask, ref[1]), (q, pr)
+            assert torch.equal(img, ref[0]) and torch.equal(mask, ref[1]), (q, pr, b64, b32)
             assert st["rays_per_level"] == ref[2]
     ctx.art_set_tune()
 
@@ -59,11 +61,33 @@ def test_autotune_keeps_a_candidate_and_the_image(ctx):
     img0, mask0, _ = ctx.render(job)
     img = torch.empty_like(img0)
     mask = torch.empty_like(mask0)
-    (q, pr), ms = ctx.art_autotune(job, img, mask, reps=2)
-    assert 0 <= q <= pr <= 4096 and ms > 0
-    assert ctx.art_get_tune() == (q, pr)
+    best, ms = ctx.art_autotune(job, img, mask, reps=2)
+    q, pr, b64, b32 = best
+    assert 0 <= q <= pr <= 4096 and ms > 0 and b64 in (0, 1, 2) and b32 in (0, 1, 2)
+    assert ctx.art_get_tune() == best
     assert torch.equal(img, img0) and torch.equal(mask, mask0)
     with pytest.raises(RuntimeError):
         ctx.art_autotune(job, img, mask, reps=0)
-    assert ctx.art_get_tune() == (q, pr)
+    assert ctx.art_get_tune() == best
     ctx.art_set_tune()
+
+
+def test_fp64_grids_render_the_same_image():
+    """Exact decisions (FP64 base level and closure passes) under every FP64 grid size: the same
+    image, mask and rays."""
+    from paper_2103_07417_gb300 import art
+    c = art.Context(0)
+    try:
+        c.load_grid(W.grmhd_snapshot(seed=0))
+        job = art.make_job(**W.grmhd_8193(n0x=33, n0y=33, levels=4, precision="mixed_exact"))
+        ref = None
+        for b64 in (0, 1, 2, 3):
+            c.art_set_tune(32, 64, b64, 0)
+            img, mask, st = c.render(job)
+            if ref is None:
+                ref = (img.clone(), mask.clone(), st["rays_per_level"], st["rays_exact"])
+            else:
+                assert torch.equal(img, ref[0]) and torch.equal(mask, ref[1]), b64
+                assert (st["rays_per_level"], st["rays_exact"]) == ref[2:]
+    finally:
+        c.close()
