@@ -46,11 +46,28 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     const Q lr = log(r);
     if (!(lr >= Q(S.g_x1min) && lr <= Q(S.g_x1max))) return;
     const Q a = Q(J.a), a2 = Q(J.a2);
-    Q ct = s.z / r;
+    const Q ir = Q(1) / r;
+    Q ct = s.z * ir;
     ct = ct > Q(1) ? Q(1) : (ct < Q(-1) ? Q(-1) : ct);
     const Q th = acos(ct);
     const Q twopi = Q(6.283185307179586476925);
-    Q ph = atan2(s.y, s.x) + atan2(a, r);
+    // phi = arg(x + i y) + arg(r + i a) = arg((x + i y)(r + i a)): one arctangent, and its cosine
+    // and sine from the product's parts instead of evaluating them (on the axis, x = y = 0, the
+    // first argument is taken as 0)
+    const Q px = fmad(s.x, r, -(s.y * a)), py = fmad(s.y, r, s.x * a);
+    const Q pp = fmad(px, px, py * py);
+    Q ph, sp, cp;
+    if (pp > Q(0)) {
+        ph = atan2(py, px);
+        const Q ip = rsqrt(pp);
+        cp = px * ip;
+        sp = py * ip;
+    } else {
+        const Q ira = rsqrt(fmad(r, r, a2));
+        ph = atan2(a, r);
+        cp = r * ira;
+        sp = a * ira;
+    }
     if (ph < Q(0)) ph += twopi;
     if (ph >= twopi) ph -= twopi;
     const int n1 = S.g_n1, n2 = S.g_n2, n3 = S.g_n3;
@@ -87,8 +104,6 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     const Q rho = P[0], ug = P[1];
     if (!(rho > Q(0)) || !(ug > Q(0))) return;
     // d(x, y, z)/d(r, theta, phi) of x + i y = (r - i a) sin(theta) e^{i phi}, z = r cos(theta)
-    Q sp, cp;
-    sincos(ph, &sp, &cp);
     const Q st = sqrt(Q(1) - ct * ct);
     const Q Jm[3][3] = {{st * cp, ct * fmad(r, cp, a * sp), -s.y},
                         {st * sp, ct * fmad(r, sp, -(a * cp)), s.x},
@@ -100,7 +115,7 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
         u[1 + i] = fmad(Jm[i][2], P[4], fmad(Jm[i][1], P[3], Jm[i][0] * P[2]));
         B[1 + i] = fmad(Jm[i][2], P[7], fmad(Jm[i][1], P[6], Jm[i][0] * P[5]));
     }
-    const KSPoint<Q> G = ks_point<Q>(s.x, s.y, s.z, r, a, a2);
+    const KSPoint<Q> G = ks_point<Q>(s.x, s.y, s.z, r, ir, a, a2);
     const Q Lu = fmad(G.Lz, u[3], fmad(G.Ly, u[2], G.Lx * u[1]));
     const Q LB = fmad(G.Lz, B[3], fmad(G.Ly, B[2], G.Lx * B[1]));
     const Q uu = fmad(u[3], u[3], fmad(u[2], u[2], u[1] * u[1]));
@@ -110,11 +125,13 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     if (!(D >= Q(0))) return;
     const Q den = sqrt(D) - pn;
     if (!(den > Q(0))) return;
-    u[0] = qn / den;
+    // u^t = qn / den and 1/u^t = den / qn from one reciprocal
+    const Q iqd = Q(1) / (qn * den);
+    u[0] = qn * qn * iqd;
     const Q Bu = fmad(B[3], u[3], fmad(B[2], u[2], B[1] * u[1]));
     Q b[4];
     b[0] = fmad(G.F * LB, Lu - u[0], Bu);
-    const Q iut = Q(1) / u[0];
+    const Q iut = den * den * iqd;
 #pragma unroll
     for (int i = 1; i < 4; ++i) b[i] = fmad(b[0], u[i], B[i]) * iut;
     // b^mu b_mu = (g_ij B^i B^j + (b^t)^2) / (u^t)^2 (from b^mu = (B^mu + b^t u^mu)/u^t and
@@ -133,9 +150,9 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     const Q trat = fmad(Q(S.g_r_high), pg2, Q(S.g_r_low) * pm2) / (pg2 + pm2);
     const Q Th = Q(S.g_th_unit) * ug / (rho * (Q(1) + trat));
     const Q ne = Q(S.g_ne_unit) * rho;
-    const Q bm = sqrt(b2);
+    const Q ib = rsqrt(b2);
+    const Q bm = b2 * ib;
     const Q Bm = Q(S.g_b_unit) * bm;
-    const Q ib = Q(1) / bm;
 #pragma unroll
     for (int m = 0; m < 4; ++m) b[m] *= ib;
     const Q nu = fmad(s.kz, u[3], fmad(s.ky, u[2], fmad(s.kx, u[1], kt * u[0])));

@@ -112,9 +112,12 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
     R r = r2 * ir;
     R ir2 = ir * ir;
     R r4 = r2 * r2;
-    R iQ = R(1) / (r4 + a2z2);
+    // 1/Q and 1/(r^2 + a^2) from one reciprocal of their product
+    const R Qd = r4 + a2z2, ra2 = r2 + a2;
+    const R iP = R(1) / (Qd * ra2);
+    R iQ = ra2 * iP;
     R f = scale2(r2, 2.f) * r * iQ;
-    R ira2 = R(1) / (r2 + a2);
+    R ira2 = Qd * iP;
     R Lx = fmad(r, x, -(a * y)) * ira2;
     R Ly = fmad(r, y, a * x) * ira2;
     R Lz = z * ir;
