@@ -308,10 +308,12 @@ int art_render_host(art_ctx* ctx, const art_job* job, double* img_host, uint8_t*
  * the persistent grids of the FP64 launches hold blocks64 blocks of 128 threads per SM, those of
  * the FP32 and double-float launches blocks32 (0: as many as fit; a larger value is capped there).
  * The forms and grids give bit-identical rays, so the setting changes speed only.  Defaults
- * ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, 0, 0; valid settings have
+ * ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT (one block of two warp
+ * pairs per SM: one warp per scheduler, which is all the FP64 pipe takes), 0; valid settings have
  * 0 <= quad_rays <= pair_rays <= 4096 and 0 <= blocks64, blocks32 <= 64. */
 #define ART_TUNE_QUAD_DEFAULT 32
 #define ART_TUNE_PAIR_DEFAULT 64
+#define ART_TUNE_BLOCKS64_DEFAULT 1
 typedef struct art_tune {
     int32_t quad_rays;
     int32_t pair_rays;
@@ -326,8 +328,8 @@ int art_get_tune(art_ctx* ctx, art_tune* t_out);
 
 /* Autotuner: renders `job` (as art_render, into img_dev / mask_dev) with each candidate setting,
  * once to warm up and `reps` times timed with CUDA events on the context's stream, one dimension at
- * a time (eight FP32 kernel-form threshold pairs with both grids full; then, from the best, blocks64
- * in {1, 2} if the job has FP64 launches; then blocks32 in {1, 2} if it has FP32 ones), keeps the
+ * a time (eight FP32 kernel-form threshold pairs with the default grids; then, from the best,
+ * blocks64 in {0, 1, 2} if the job has FP64 launches; then blocks32 in {1, 2} if it has FP32 ones), keeps the
  * setting with the lowest median time in the context and returns it in *best (nullable) with that
  * median in *best_ms (nullable).  img_dev and mask_dev hold the job's image
  * afterwards (the same for every setting).  Synchronises the stream.  Errors: ART_ERR_ARG (reps

@@ -61,7 +61,7 @@ class Tune(ctypes.Structure):
                 ("blocks64", ctypes.c_int32), ("blocks32", ctypes.c_int32)]
 
 
-TUNE_DEFAULT = (32, 64, 0, 0)
+TUNE_DEFAULT = (32, 64, 1, 0)
 
 
 class Stats(ctypes.Structure):
@@ -442,7 +442,7 @@ class Context:
                "art_graph_render")
 
     def art_set_tune(self, quad_rays: int | None = None, pair_rays: int | None = None,
-                     blocks64: int = 0, blocks32: int = 0):
+                     blocks64: int = 1, blocks32: int = 0):
         """Set the scheduling (FP32 kernel-form thresholds, grid blocks per SM); no arguments
         restore the defaults."""
         if quad_rays is None and pair_rays is None:

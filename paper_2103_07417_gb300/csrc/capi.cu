@@ -15,7 +15,7 @@
 using namespace art;
 
 struct art_ctx {
-    art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, 0, 0};
+    art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT, 0};
     // exact decisions in a batch (art_render_batch): sub-contexts, each with a stream of its own
     // and its own scratch, render the images concurrently; every image's counters and
     // normalisation are copied into xsnap on its sub-context's stream
@@ -25,6 +25,14 @@ struct art_ctx {
     std::vector<cudaEvent_t> sub_out;
     unsigned long long* xsnap = nullptr;
     int64_t xsnap_cap = 0;
+    // exact decisions: each traced pixel's RK4 steps, the longest-first copy of an FP64 queue and
+    // its sort's counters; cur_steps is what trace launches record into (null outside them)
+    uint16_t* steps_map = nullptr;
+    int64_t steps_cap = 0;
+    int32_t* lptq = nullptr;
+    int64_t lptq_cap = 0;
+    unsigned int* lpt_hist = nullptr;
+    uint16_t* cur_steps = nullptr;
     // bumped whenever a scratch buffer is (re)allocated: a captured graph holds the pointers of
     // its capture and is replayed only while this is unchanged
     uint64_t scratch_gen = 0;
@@ -354,7 +362,9 @@ static int check_grid(const art_ctx* c, const art_job* job)
 }
 
 // Persistent grid of a trace launch: SMs x resident blocks per SM, capped by the tuned blocks
-// per SM (0: as many as fit).
+// per SM (0: as many as fit).  FP64 queues known to hold more than FP64_FULL_GRID_RAYS_PER_SM rays
+// per SM take every resident block whatever the setting.
+constexpr int FP64_FULL_GRID_RAYS_PER_SM = 4096;
 static int trace_grid(const art_ctx* c, int occ, int tuned)
 {
     return c->num_sms * (tuned > 0 && tuned < occ ? tuned : occ);
@@ -411,6 +421,9 @@ extern "C" void art_destroy(art_ctx* c)
         if (e) cudaEventDestroy(e);
     cudaFree(c->xsnap);
     cudaStreamSynchronize(c->stream);
+    cudaFree(c->steps_map);
+    cudaFree(c->lptq);
+    cudaFree(c->lpt_hist);
     if (c->gstream) cudaStreamSynchronize(c->gstream);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->gbexec) cudaGraphExecDestroy(c->gbexec);
@@ -528,11 +541,12 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
                        const art_rayaux* aux, float* pix_minr = nullptr, float* pix_turn = nullptr,
                        const unsigned long long* spec_from = nullptr,
                        const int32_t* qbuf = nullptr, bool exact = false,
-                       bool skip_retrace = false)
+                       bool skip_retrace = false, int64_t n_host = -1)
 {
     TraceArgs a;
     memset(&a, 0, sizeof a);
     a.job = J;
+    a.pix_steps = c->cur_steps;
     a.quad_rays = c->tune.quad_rays;
     a.pair_rays = c->tune.pair_rays;
     a.pix_minr = pix_minr;
@@ -554,7 +568,10 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
         a.aux_minr = aux->min_r;
     }
     const int pl = variant_of(J);
-    const int g64 = trace_grid(c, c->occ[TK_FP64][pl], c->tune.blocks64);
+    // a queue the host knows to be very long (a large base level) keeps every resident block:
+    // there the pipe needs the latency hiding more than the launch's last rays need their SMs
+    const bool long_queue = n_host > (int64_t)FP64_FULL_GRID_RAYS_PER_SM * c->num_sms;
+    const int g64 = trace_grid(c, c->occ[TK_FP64][pl], long_queue ? 0 : c->tune.blocks64);
     const int g32 = trace_grid(c, c->occ[TK_FP32][pl], c->tune.blocks32);
     const int gdf = trace_grid(c, c->occ[TK_DF][pl], c->tune.blocks32);
     int k;
@@ -780,7 +797,15 @@ static int render_impl(art_ctx* c, const art_job* job, const double* truth_dev, 
         bcap = (unsigned long long)b;
         xcap = (unsigned long long)x;
         CK(cudaMemsetAsync(c->xst, 0, (npix + 3) / 4 * 4, st));
+        const int64_t n0 = (int64_t)((J.nx - 1) / (1 << J.levels) + 1) * ((J.ny - 1) / (1 << J.levels) + 1);
+        if (npix > c->steps_cap) {
+            if ((rc = grow(c, c->steps_map, c->steps_cap, npix))) return rc;
+            CK(cudaMemsetAsync(c->steps_map, 0, sizeof(uint16_t) * npix, st));
+        }
+        if ((rc = grow(c, c->lptq, c->lptq_cap, std::max<int64_t>(x, n0)))) return rc;
+        if (!c->lpt_hist) CK(cudaMalloc(&c->lpt_hist, sizeof(unsigned int) * LPT_BUCKETS));
     }
+    c->cur_steps = cert ? c->steps_map : nullptr;
     DevJob J64 = J;
     J64.precision = ART_FP64;
     if (ax && (rc = grow(c, c->aq, c->aq_cap, cap))) return rc;
@@ -883,8 +908,11 @@ static int render_impl(art_ctx* c, const art_job* job, const double* truth_dev, 
                 CK(launch_counter_clamp(c->counters, C_XQ, xcap, st));
                 CK(launch_counter_clamp(c->counters, C_FIXQ, xcap, st));
                 prof_end(c, k, ART_K_OTHER, -1);
+                // longest rays first (an FP64 launch ends with its last ray)
+                CK(launch_lpt_order(J, c->cxq, c->counters + C_XQ, xcap, c->steps_map, mask,
+                                    c->lptq, c->lpt_hist, c->num_sms, st));
                 if ((rc = trace_queue(c, job, J64, c->counters + C_XQ, img_dev, mask, nullptr,
-                                      nullptr, aminr, aturn, nullptr, c->cxq)))
+                                      nullptr, aminr, aturn, nullptr, c->lptq)))
                     return rc;
                 k = prof_begin(c);
                 CK(launch_cert_mark_traced(c->cxq, c->counters, xcap, c->xst, st));
@@ -905,8 +933,17 @@ static int render_impl(art_ctx* c, const art_job* job, const double* truth_dev, 
             // closure), the band's speculative rays of later levels in the mixed precision
             const int S0 = 1 << J.levels;
             const int64_t n0 = (int64_t)((J.nx - 1) / S0 + 1) * ((J.ny - 1) / S0 + 1);
-            if ((rc = trace_queue(c, job, J64, c->counters + C_LEVEL0, img_dev, mask, nullptr,
+            // the lengths of the base rays from an FP32 pass (its values are overwritten), then
+            // the FP64 pass longest first
+            DevJob J32 = J;
+            J32.precision = ART_FP32;
+            if ((rc = trace_queue(c, job, J32, c->counters + C_LEVEL0, img_dev, mask, nullptr,
                                   nullptr, aminr, aturn)))
+                return rc;
+            CK(launch_lpt_order(J, c->queue, c->counters + C_LEVEL0, (unsigned long long)n0,
+                                c->steps_map, mask, c->lptq, c->lpt_hist, c->num_sms, st));
+            if ((rc = trace_queue(c, job, J64, c->counters + C_LEVEL0, img_dev, mask, nullptr,
+                                  nullptr, aminr, aturn, nullptr, c->lptq, false, false, n0)))
                 return rc;
             k = prof_begin(c);
             CK(launch_cert_mark_base(J, c->xst, st));
@@ -930,8 +967,13 @@ static int render_impl(art_ctx* c, const art_job* job, const double* truth_dev, 
                                   aminr, aturn, nullptr, c->aq)))
                 return rc;
         } else {
+            // at level 0 the host knows the base grid's size (a lower bound with speculation)
+            const int64_t nb = level == 0 ? (int64_t)((J.nx - 1) / (1 << J.levels) + 1) *
+                                                ((J.ny - 1) / (1 << J.levels) + 1)
+                                          : -1;
             if ((rc = trace_queue(c, job, J, c->counters + C_QUEUE, img_dev, mask, nullptr, nullptr,
-                                  aminr, aturn, spec ? c->counters + C_SPECFROM : nullptr)))
+                                  aminr, aturn, spec ? c->counters + C_SPECFROM : nullptr, nullptr,
+                                  false, false, nb)))
                 return rc;
         }
         if (level == 0) {
@@ -1746,7 +1788,7 @@ extern "C" int art_set_tune(art_ctx* c, const art_tune* t)
 {
     if (!c) return ART_ERR_ARG;
     if (!t) {
-        c->tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, 0, 0};
+        c->tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT, 0};
         return ART_OK;
     }
     if (!tune_valid(t)) return ART_ERR_ARG;
@@ -1767,8 +1809,8 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
     if (!c || !job || !img_dev || reps < 1 || reps > 32) return ART_ERR_ARG;
     // candidates, one dimension at a time: the FP32 kernel-form thresholds (one-thread only, pair
     // only, quad/pair splits around the defaults), then with the best of them the persistent
-    // grids' blocks per SM, of the FP64 launches (where the job has any) and of the FP32 and
-    // double-float ones (0 = as many as fit, else 1 or 2)
+    // grids' blocks per SM, of the FP64 launches (where the job has any: 0 = as many as fit, 1,
+    // 2) and of the FP32 and double-float ones (0, then 1 or 2)
     static const int forms[][2] = {{0, 0},   {0, 64},   {32, 64},  {32, 96},
                                    {64, 96}, {32, 128}, {64, 128}, {16, 64}};
     const bool has64 = job->precision != ART_FP32, has32 = job->precision != ART_FP64;
@@ -1780,7 +1822,7 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
         return ART_ERR_CUDA;
     }
     const art_tune saved = c->tune;
-    art_tune win = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, 0, 0};
+    art_tune win = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT, 0};
     float win_ms = INFINITY;
     int rc = ART_OK;
     std::vector<float> t(reps);
@@ -1806,9 +1848,10 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
     for (const auto& f : forms) {
         if (rc) break;
         if (has32 || (f[0] == ART_TUNE_QUAD_DEFAULT && f[1] == ART_TUNE_PAIR_DEFAULT))
-            trial(art_tune{f[0], f[1], 0, 0});
+            trial(art_tune{f[0], f[1], ART_TUNE_BLOCKS64_DEFAULT, 0});
     }
-    for (int b = 1; b <= 2 && has64 && !rc; ++b) {
+    for (int b = 0; b <= 2 && has64 && !rc; ++b) {
+        if (b == ART_TUNE_BLOCKS64_DEFAULT) continue;
         art_tune cand = win;
         cand.blocks64 = b;
         trial(cand);

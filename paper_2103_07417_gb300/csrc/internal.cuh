@@ -76,6 +76,7 @@ struct TraceArgs {
     // of speculative rays (nullable; slots at or beyond it are marked MASK_SPEC_DONE)
     float* pix_minr;
     float* pix_turn;
+    uint16_t* pix_steps;  // nullable: RK4 steps of each traced pixel's ray (saturated at 65535)
     const unsigned long long* spec_from;
     // kernel forms of the FP32 pass (trace_kernels.cuh): queues of at most quad_rays rays per
     // block take the four-warp form, of at most pair_rays the two-warp form (art_tune)
@@ -210,6 +211,13 @@ cudaError_t launch_visibilities(const double* img, const double* ref, int nx, in
 cudaError_t measure_alu_peaks(int num_sms, cudaStream_t st, double* fp32_tflops,
                               double* fp64_tflops);
 cudaError_t measure_fp64_issue(cudaStream_t st, double* cycles3);
+// Longest first: the pixels of q_in (count entries, at most cap) into q_out in descending order
+// of their rays' expected RK4 steps (refine.cu); hist: LPT_BUCKETS + 1 scratch counters.
+constexpr int LPT_BUCKETS = 256;
+cudaError_t launch_lpt_order(const DevJob& J, const int32_t* q_in,
+                             const unsigned long long* count, unsigned long long cap,
+                             const uint16_t* pix_steps, const uint8_t* mask, int32_t* q_out,
+                             unsigned int* hist, int num_sms, cudaStream_t st);
 
 // cnn.cu
 struct CnnState;

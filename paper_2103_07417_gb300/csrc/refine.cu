@@ -1184,6 +1184,103 @@ cudaError_t launch_cert_closure(const DevJob& J, int level, const int32_t* borde
     return cudaGetLastError();
 }
 
+// Longest first (exact decisions).  An FP64 launch ends when its last ray does, and the rays of one
+// launch differ several-fold in length (~300 RK4 steps near the photon ring, ~70 for a ray that
+// escapes), so its queue is reordered longest first: a counting sort over LPT_BUCKETS buckets of
+// 4 steps.  A ray's expected length is the steps its pixel's ray took in an earlier pass (mask
+// traced or speculatively traced), else the longest of its interpolation parents' (0 where none
+// of them has been traced).
+__device__ __forceinline__ int lpt_key(const DevJob& J, int32_t p, const uint16_t* steps,
+                                       const uint8_t* mask)
+{
+    const int64_t npix = (int64_t)J.nx * J.ny;
+    if (p < 0 || p >= npix) return 0;
+    auto traced = [&](int q) {
+        const uint8_t m = mask[q];
+        return (m == ART_MASK_TRACED || m == MASK_SPEC_DONE) ? (int)steps[q] : 0;
+    };
+    const uint8_t m = mask[p];
+    if (m == ART_MASK_TRACED || m == MASK_SPEC_DONE) return steps[p];
+    const int i = p % J.nx, j = p / J.nx;
+    int s;
+    if (pixel_level(i, j, J.levels, s) == 0) return 0;
+    const int oi = (i / s) & 1, oj = (j / s) & 1;
+    const int cat = (oi && oj) ? 4 : (oi ? 3 : 2);
+    int p1, p2, p3, p4;
+    interp_parents<int>(J.nx, i, j, s, cat, p1, p2, p3, p4);
+    int k = max(traced(p1), traced(p2));
+    if (cat == 4) k = max(k, max(traced(p3), traced(p4)));
+    return k;
+}
+
+__device__ __forceinline__ int lpt_bucket(int key)
+{
+    const int b = key >> 2;
+    return LPT_BUCKETS - 1 - (b < LPT_BUCKETS - 1 ? b : LPT_BUCKETS - 1);
+}
+
+__global__ void lpt_hist_kernel(DevJob J, const int32_t* q, const unsigned long long* count,
+                                unsigned long long cap, const uint16_t* steps,
+                                const uint8_t* mask, unsigned int* hist)
+{
+    __shared__ unsigned int h[LPT_BUCKETS];
+    for (int b = threadIdx.x; b < LPT_BUCKETS; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    unsigned long long n = *count;
+    if (n > cap) n = cap;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x)
+        atomicAdd(&h[lpt_bucket(lpt_key(J, q[k], steps, mask))], 1u);
+    __syncthreads();
+    for (int b = threadIdx.x; b < LPT_BUCKETS; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// Exclusive prefix sum of the LPT_BUCKETS counts in place (one block of LPT_BUCKETS threads).
+__global__ void __launch_bounds__(LPT_BUCKETS) lpt_scan_kernel(unsigned int* hist)
+{
+    __shared__ unsigned int t[LPT_BUCKETS];
+    const int b = threadIdx.x;
+    const unsigned int own = hist[b];
+    t[b] = own;
+    __syncthreads();
+    for (int off = 1; off < LPT_BUCKETS; off <<= 1) {
+        const unsigned int v = b >= off ? t[b - off] : 0u;
+        __syncthreads();
+        t[b] += v;
+        __syncthreads();
+    }
+    hist[b] = t[b] - own;
+}
+
+__global__ void lpt_scatter_kernel(DevJob J, const int32_t* q_in, const unsigned long long* count,
+                                   unsigned long long cap, const uint16_t* steps,
+                                   const uint8_t* mask, int32_t* q_out, unsigned int* cursor)
+{
+    unsigned long long n = *count;
+    if (n > cap) n = cap;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t p = q_in[k];
+        const unsigned int pos = atomicAdd(&cursor[lpt_bucket(lpt_key(J, p, steps, mask))], 1u);
+        q_out[pos] = p;
+    }
+}
+
+cudaError_t launch_lpt_order(const DevJob& J, const int32_t* q_in,
+                             const unsigned long long* count, unsigned long long cap,
+                             const uint16_t* pix_steps, const uint8_t* mask, int32_t* q_out,
+                             unsigned int* hist, int num_sms, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(unsigned int) * LPT_BUCKETS, st);
+    if (e != cudaSuccess) return e;
+    const int grid = 2 * num_sms;
+    lpt_hist_kernel<<<grid, 256, 0, st>>>(J, q_in, count, cap, pix_steps, mask, hist);
+    lpt_scan_kernel<<<1, LPT_BUCKETS, 0, st>>>(hist);
+    lpt_scatter_kernel<<<grid, 256, 0, st>>>(J, q_in, count, cap, pix_steps, mask, q_out, hist);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_cert_mark_traced(const int32_t* xq, unsigned long long* counters,
                                     unsigned long long xq_cap, uint8_t* xst, cudaStream_t st,
                                     int count_idx)

@@ -47,6 +47,7 @@ __device__ __forceinline__ void finish_ray(const TraceArgs& A, int status, int s
         A.mask[pix] = (A.spec_from && (unsigned long long)slot >= *A.spec_from)
                           ? MASK_SPEC_DONE
                           : (uint8_t)ART_MASK_TRACED;
+    if (A.img && A.pix_steps) A.pix_steps[pix] = (uint16_t)(steps < 65535 ? steps : 65535);
     if (A.img && A.pix_minr) {
         A.pix_minr[pix] = x.min_r;
         A.pix_turn[pix] = (float)x.nturn;
