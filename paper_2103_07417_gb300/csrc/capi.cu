@@ -98,6 +98,7 @@ struct art_ctx {
     // batched rendering tables and queue (grown, never shrunk)
     DevJob* bjobs = nullptr;
     SynchConst* bsynch = nullptr;
+    SynchConstF* bsynchf = nullptr;
     Camera* bcams = nullptr;
     double* bparams = nullptr;
     double** bimgs = nullptr;
@@ -284,6 +285,16 @@ static int make_devjob(const art_job* job, DevJob* J)
     J->precision = job->precision == ART_MIXED_EXACT ? ART_MIXED_DF : job->precision;
     J->criterion = job->criterion;
     J->cplane = job->criterion_plane;
+    J->f_a = (float)J->a;
+    J->f_a_lo = (float)(J->a - (double)J->f_a);
+    J->f_a2 = (float)J->a2;
+    J->f_a2_lo = (float)(J->a2 - (double)J->f_a2);
+    J->f_step_frac = (float)J->step_frac;
+    J->f_h_min = (float)J->h_min;
+    J->f_r_in_stop = (float)J->r_in_stop;
+    J->f_r_out_stop = (float)J->r_out_stop;
+    J->f_fp64_sweep = (float)J->fp64_sweep;
+    J->f_inv_2w2 = (float)J->inv_2w2;
     return ART_OK;
 }
 
@@ -446,6 +457,7 @@ extern "C" void art_destroy(art_ctx* c)
     cudaFree(c->prof_steps);
     cudaFree(c->bjobs);
     cudaFree(c->bsynch);
+    cudaFree(c->bsynchf);
     cudaFree(c->bcams);
     cudaFree(c->bparams);
     cudaFree(c->bimgs);
@@ -553,6 +565,7 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
     a.pix_turn = pix_turn;
     a.spec_from = spec_from;
     make_synch(job, c, &a.synch);
+    a.synchf = synch_to_float(a.synch);
     a.cam = c->cam;
     a.queue = qbuf ? qbuf : c->queue;
     a.count = count;
@@ -1248,6 +1261,7 @@ static int ensure_batch(art_ctx* c, int n, int64_t qcap)
         CK(cudaStreamSynchronize(c->stream));
         cudaFree(c->bjobs);
         cudaFree(c->bsynch);
+        cudaFree(c->bsynchf);
         cudaFree(c->bcams);
         cudaFree(c->bparams);
         cudaFree(c->bimgs);
@@ -1259,6 +1273,7 @@ static int ensure_batch(art_ctx* c, int n, int64_t qcap)
         c->bcap = 0;
         CK(cudaMalloc(&c->bjobs, sizeof(DevJob) * n));
         CK(cudaMalloc(&c->bsynch, sizeof(SynchConst) * n));
+        CK(cudaMalloc(&c->bsynchf, sizeof(SynchConstF) * n));
         CK(cudaMalloc(&c->bcams, sizeof(Camera) * n));
         CK(cudaMalloc(&c->bparams, sizeof(double) * 3 * n));
         CK(cudaMalloc(&c->bimgs, sizeof(double*) * n));
@@ -1289,6 +1304,7 @@ static int trace_queue_batch(art_ctx* c, const DevJob& J0, const unsigned long l
     a.spec_from = spec_from;
     a.jobs = c->bjobs;
     a.synchs = c->bsynch;
+    a.synchfs = c->bsynchf;
     a.cams = c->bcams;
     a.imgs = c->bimgs;
     a.masks = c->bmasks;
@@ -1342,6 +1358,7 @@ struct BatchPlan {
     int n = 0;
     std::vector<DevJob> J;
     std::vector<SynchConst> S;
+    std::vector<SynchConstF> SF;
     std::vector<double> p3;
     std::vector<double*> im;
     std::vector<uint8_t*> mk;
@@ -1362,6 +1379,7 @@ static int plan_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const*
     P.n = n;
     P.J.assign(n, DevJob{});
     P.S.assign(n, SynchConst{});
+    P.SF.assign(n, SynchConstF{});
     P.p3.assign(3 * (size_t)n, 0.0);
     P.im.assign(imgs, imgs + n);
     P.mk.assign(n, nullptr);
@@ -1391,6 +1409,7 @@ static int plan_batch(art_ctx* c, const art_job* jobs, int32_t n, double* const*
             return ART_ERR_ARG;  // one kernel kind and one plane count per batch
         if ((rc = check_grid(c, &jobs[i]))) return rc;
         make_synch(&jobs[i], c, &P.S[i]);
+        P.SF[i] = synch_to_float(P.S[i]);
         P.p3[3 * i] = jobs[i].a;
         P.p3[3 * i + 1] = jobs[i].r_obs;
         P.p3[3 * i + 2] = jobs[i].incl_deg;
@@ -1441,6 +1460,8 @@ static int upload_batch(art_ctx* c, const BatchPlan& P)
     const int n = P.n;
     CK(cudaMemcpyAsync(c->bjobs, P.J.data(), sizeof(DevJob) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->bsynch, P.S.data(), sizeof(SynchConst) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->bsynchf, P.SF.data(), sizeof(SynchConstF) * n, cudaMemcpyHostToDevice,
+                       st));
     CK(cudaMemcpyAsync(c->bparams, P.p3.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->bimgs, P.im.data(), sizeof(double*) * n, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->bmasks, P.mk.data(), sizeof(uint8_t*) * n, cudaMemcpyHostToDevice, st));

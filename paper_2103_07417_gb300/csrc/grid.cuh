@@ -37,15 +37,16 @@ ART_HD void grid_axis_clamped(Q f, int n, int& i0, Q& w)
 // Emission of the grid model at one point (J4, K7 as emission_synch).  f nullable.
 template <class Q>
 __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, const Q* f,
-                                              const DevJob& J, const SynchConst& S, Q* J4, Q* K7,
+                                              const DevJob& J, const SynchConstT<Q>& S, Q* J4,
+                                              Q* K7,
                                               int* edge = nullptr)
 {
     for (int i = 0; i < 4; ++i) J4[i] = Q(0);
     for (int i = 0; i < 7; ++i) K7[i] = Q(0);
-    if (r < Q(J.r_in_stop)) return;
+    if (r < jq<Q>(J.r_in_stop, J.f_r_in_stop)) return;
     const Q lr = log(r);
     if (!(lr >= Q(S.g_x1min) && lr <= Q(S.g_x1max))) return;
-    const Q a = Q(J.a), a2 = Q(J.a2);
+    const Q a = jq<Q>(J.a, J.f_a), a2 = jq<Q>(J.a2, J.f_a2);
     const Q ir = Q(1) / r;
     Q ct = s.z * ir;
     ct = ct > Q(1) ? Q(1) : (ct < Q(-1) ? Q(-1) : ct);
@@ -141,7 +142,7 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     const Q b2 = fmad(b[0], b[0], fmad(G.F * LB, LB, BB)) * (iut * iut);
     if (!(b2 > Q(0))) return;
     // a sample within rounding of the cut may keep or lose its emission in another precision
-    if (edge && S.e_sig > 0.0 &&
+    if (edge && S.e_sig > Q(0) &&
         fabs(b2 - Q(S.g_sigma_cut) * rho) < Q(S.e_sig) * Q(S.g_sigma_cut) * rho)
         *edge = 1;
     if (b2 > Q(S.g_sigma_cut) * rho) return;

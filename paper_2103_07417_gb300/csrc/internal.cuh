@@ -56,6 +56,7 @@ constexpr uint8_t MASK_PENDING = 10;
 struct TraceArgs {
     DevJob job;
     SynchConst synch;
+    SynchConstF synchf;  // its float copy (the FP32 and double-float kernels' transfer)
     const Camera* cam;
     const int32_t* queue;           // pixel indices
     const int32_t* indirect;        // nullable: slot -> queue position (re-trace pass)
@@ -91,6 +92,7 @@ constexpr uint8_t MASK_SPEC_PENDING = 8, MASK_SPEC_DONE = 9;
 struct BatchTraceArgs {
     const DevJob* jobs;
     const SynchConst* synchs;
+    const SynchConstF* synchfs;  // their float copies
     const Camera* cams;
     double* const* imgs;
     uint8_t* const* masks;           // table entries may be null

@@ -76,7 +76,18 @@ struct DevJob {
     double R_abs, R_rel, fp64_sweep;
     int32_t nx, ny, levels, emission, flow, stokes, subrings, planes, max_steps;
     int32_t interp, edge_mode, abs_norm, precision, criterion, cplane;
+    // float copies of the constants the per-step code reads, for the FP32 and double-float kernels
+    // (a conversion from double runs on GB300's FP64 pipe, one warp instruction per 64 cycles on a
+    // scheduler), with the low parts of a and a^2 for double-float geodesics
+    float f_a, f_a2, f_a_lo, f_a2_lo, f_step_frac, f_h_min, f_r_in_stop, f_r_out_stop;
+    float f_fp64_sweep, f_inv_2w2;
 };
+
+// A job constant in arithmetic T: the double itself, or its float copy.
+template <class T>
+ART_HD T jq(double d, float) { return T(d); }
+template <>
+ART_HD float jq<float>(double, float f) { return f; }
 
 // Static camera: position and the covariant (lowered) tetrad E0 (observer), E1 (outward),
 // E2 (screen up), E3 (screen right), so that k_mu = -E0 + s (-E1 + (al/r_obs) E3 + (be/r_obs) E2).
@@ -148,12 +159,12 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
 template <class R>
 ART_HD R emission_analytic(const RayState<R>& s, R r, R kt, const DevJob& J)
 {
-    if (r < R(J.r_in_stop)) return R(0);
+    if (r < jq<R>(J.r_in_stop, J.f_r_in_stop)) return R(0);
     R ct = s.z / r;
     R ct2 = ct * ct;
     R r2 = r * r;
-    R jnu = exp(-ct2 * R(J.inv_2w2)) / r2;
-    R a = R(J.a), a2 = R(J.a2);
+    R jnu = exp(-ct2 * jq<R>(J.inv_2w2, J.f_inv_2w2)) / r2;
+    R a = jq<R>(J.a, J.f_a), a2 = jq<R>(J.a2, J.f_a2);
     R nu;
     if (J.flow == 0) {
         R st2 = R(1) - ct2;

@@ -31,33 +31,59 @@
 
 namespace art {
 
-// Constants of the synchrotron models, precomputed on the host in double (keeps FP32 in range).
-struct SynchConst {
-    double ne0, th0, b0, ne_s, te_s, b_s, inv_2w2, r_in, bz, bnorm;
-    double LCj;    // L sqrt2 pi e^2 / (3 c)
-    double CB;     // e / (2 pi m c)   [nu_B per gauss]
-    double nu_obs; // observed frequency [Hz]
-    double xB;     // h nu_obs / (m c^2)
-    double invKB;  // c^2 / (2 h nu_obs^3)
-    double LCV;    // L e^3 / (pi m^2 c^2 nu_obs^2)
-    double LCQ;    // L e^4 / (4 pi^2 m^3 c^3 nu_obs^3)
+// Constants of the synchrotron models, precomputed on the host in double (keeps FP32 in range);
+// the FP32 and double-float kernels read a float copy (SynchConstF) made on the host, so that no
+// per-step conversion from double runs on the FP64 pipe.
+template <class T>
+struct SynchConstT {
+    T ne0, th0, b0, ne_s, te_s, b_s, inv_2w2, r_in, bz, bnorm;
+    T LCj;    // L sqrt2 pi e^2 / (3 c)
+    T CB;     // e / (2 pi m c)   [nu_B per gauss]
+    T nu_obs; // observed frequency [Hz]
+    T xB;     // h nu_obs / (m c^2)
+    T invKB;  // c^2 / (2 h nu_obs^3)
+    T LCV;    // L e^3 / (pi m^2 c^2 nu_obs^2)
+    T LCQ;    // L e^4 / (4 pi^2 m^3 c^3 nu_obs^3)
     // fluid grid (ART_EMIT_GRID): cells of 8 FP32 primitives as two float4
     // {rho, u, u^r, u^theta}, {u^phi, B^r, B^theta, B^phi}, cell (k, j, i) at float4 index
     // 2 ((k n2 + j) n1 + i); cell centres at ln r = x1_min + (i + 1/2)/inv_dx1, theta = (j + 1/2)
     // pi/n2, phi = (k + 1/2) 2 pi/n3
     const float4* grid;
     int32_t g_n1, g_n2, g_n3, g_pad;
-    double g_x1min, g_x1max, g_inv_dx1, g_inv_dth, g_inv_dph;
-    double g_gm1;        // gamma_ad - 1
-    double g_ne_unit;    // m_unit / (L^3 (m_p + m_e))      [cm^-3 per code density]
-    double g_b_unit;     // c sqrt(4 pi m_unit / L^3)       [gauss per code field]
-    double g_th_unit;    // (m_p / m_e)(gamma_ad - 1)
-    double g_r_high, g_r_low, g_sigma_cut;
+    T g_x1min, g_x1max, g_inv_dx1, g_inv_dth, g_inv_dph;
+    T g_gm1;        // gamma_ad - 1
+    T g_ne_unit;    // m_unit / (L^3 (m_p + m_e))      [cm^-3 per code density]
+    T g_b_unit;     // c sqrt(4 pi m_unit / L^3)       [gauss per code field]
+    T g_th_unit;    // (m_p / m_e)(gamma_ad - 1)
+    T g_r_high, g_r_low, g_sigma_cut;
     // FP32 pass of the mixed modes (0 elsewhere): relative distances from the emission model's
     // discontinuities (the magnetisation cut b^2/rho = sigma_cut, the disk's inner edge r_in) within
     // which a sample flags its ray for the high-precision re-trace
-    double e_sig, e_rin;
+    T e_sig, e_rin;
 };
+using SynchConst = SynchConstT<double>;
+using SynchConstF = SynchConstT<float>;
+
+// The float copy (every value rounded to nearest).
+inline SynchConstF synch_to_float(const SynchConst& d)
+{
+    SynchConstF f;
+    f.ne0 = (float)d.ne0; f.th0 = (float)d.th0; f.b0 = (float)d.b0; f.ne_s = (float)d.ne_s;
+    f.te_s = (float)d.te_s; f.b_s = (float)d.b_s; f.inv_2w2 = (float)d.inv_2w2;
+    f.r_in = (float)d.r_in; f.bz = (float)d.bz; f.bnorm = (float)d.bnorm;
+    f.LCj = (float)d.LCj; f.CB = (float)d.CB; f.nu_obs = (float)d.nu_obs; f.xB = (float)d.xB;
+    f.invKB = (float)d.invKB; f.LCV = (float)d.LCV; f.LCQ = (float)d.LCQ;
+    f.grid = d.grid;
+    f.g_n1 = d.g_n1; f.g_n2 = d.g_n2; f.g_n3 = d.g_n3; f.g_pad = d.g_pad;
+    f.g_x1min = (float)d.g_x1min; f.g_x1max = (float)d.g_x1max;
+    f.g_inv_dx1 = (float)d.g_inv_dx1; f.g_inv_dth = (float)d.g_inv_dth;
+    f.g_inv_dph = (float)d.g_inv_dph; f.g_gm1 = (float)d.g_gm1;
+    f.g_ne_unit = (float)d.g_ne_unit; f.g_b_unit = (float)d.g_b_unit;
+    f.g_th_unit = (float)d.g_th_unit; f.g_r_high = (float)d.g_r_high;
+    f.g_r_low = (float)d.g_r_low; f.g_sigma_cut = (float)d.g_sigma_cut;
+    f.e_sig = (float)d.e_sig; f.e_rin = (float)d.e_rin;
+    return f;
+}
 
 // K_0, K_1, K_2 scaled by e^x (K_n(x) e^x), so that FP32 stays finite for cold plasma (large x).
 template <class Q>
@@ -149,7 +175,8 @@ ART_HD Q det4(const Q* A, const Q* B, const Q* C, const Q* D)
 // covector.  J4, K7 in code units, in the (e_N, e_E) basis of f.
 template <class Q>
 ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const Q* u, const Q* b,
-                         Q nu, Q ne, Q Th, Q Bm, const Q* f, const SynchConst& S, Q* J4, Q* K7)
+                         Q nu, Q ne, Q Th, Q Bm, const Q* f, const SynchConstT<Q>& S, Q* J4,
+                         Q* K7)
 {
     Q kc[4] = {kt, s.kx, s.ky, s.kz}, ku[4];
     G.raise(kc, ku);
@@ -216,18 +243,18 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
 // f (nullable) is the transported covector; without it only the I terms are returned.
 template <class Q>
 ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const DevJob& J,
-                           const SynchConst& S, Q* J4, Q* K7, int* edge = nullptr)
+                           const SynchConstT<Q>& S, Q* J4, Q* K7, int* edge = nullptr)
 {
     for (int i = 0; i < 4; ++i) J4[i] = Q(0);
     for (int i = 0; i < 7; ++i) K7[i] = Q(0);
     // a sample within rounding of the inner edge (in the emitting layer) may fall on either side
     // of it in another precision: the ray's intensity then jumps by a whole segment's emission
-    if (edge && S.e_rin > 0.0 && fabs(r - Q(S.r_in)) < Q(S.e_rin) * Q(S.r_in)) {
+    if (edge && S.e_rin > Q(0) && fabs(r - Q(S.r_in)) < Q(S.e_rin) * Q(S.r_in)) {
         const Q c0 = s.z / r;
         if (c0 * c0 * Q(S.inv_2w2) < Q(20)) *edge = 1;
     }
-    if (r < Q(J.r_in_stop) || r < Q(S.r_in)) return;
-    const Q a = Q(J.a), a2 = Q(J.a2);
+    if (r < jq<Q>(J.r_in_stop, J.f_r_in_stop) || r < Q(S.r_in)) return;
+    const Q a = jq<Q>(J.a, J.f_a), a2 = jq<Q>(J.a2, J.f_a2);
     const Q ir = Q(1) / r;
     Q ct = s.z * ir, ct2 = ct * ct, r2 = r * r;
     // Keplerian flow (Omega at Boyer-Lindquist r, theta)

@@ -37,6 +37,26 @@ struct Aux<df> {
     using Q = float;
 };
 
+// A job constant in the geodesic's arithmetic R (double-float: the float copy and its low part).
+template <class R>
+__device__ __forceinline__ R jr(double d, float f, float) { return jq<R>(d, f); }
+template <>
+__device__ __forceinline__ df jr<df>(double, float f, float lo) { return df(f, lo); }
+
+// The synchrotron constants of the arithmetic Q: the double originals or their float copy.
+template <class Q>
+__device__ __forceinline__ const SynchConstT<Q>& synch_of(const SynchConst& d, const SynchConstF& f);
+template <>
+__device__ __forceinline__ const SynchConst& synch_of<double>(const SynchConst& d, const SynchConstF&)
+{
+    return d;
+}
+template <>
+__device__ __forceinline__ const SynchConstF& synch_of<float>(const SynchConst&, const SynchConstF& f)
+{
+    return f;
+}
+
 template <class Q, class R>
 __device__ __forceinline__ RayState<Q> to_q(const RayState<R>& s)
 {
@@ -189,7 +209,7 @@ enum EmitKernel { EM_ANALYTIC = 0, EM_GRID = 1 };
 // emission model (left unchanged otherwise).
 template <class Q, bool POL, int EM>
 __device__ __forceinline__ void coefficients(const RayState<Q>& q, Q r, Q kt, const Q* f,
-                                             const DevJob& J, const SynchConst& S, Q* J4, Q* K7,
+                                             const DevJob& J, const SynchConstT<Q>& S, Q* J4, Q* K7,
                                              int& edge)
 {
     if (EM == EM_GRID) {
@@ -236,7 +256,7 @@ __device__ __forceinline__ void geo_init(GeoState<R>& g, const DevJob& J, const 
         }
     }
     pt.q = to_q<Q>(g.s);
-    g.r = ks_radius<Q>(pt.q.x, pt.q.y, pt.q.z, Q(J.a2));
+    g.r = ks_radius<Q>(pt.q.x, pt.q.y, pt.q.z, jq<Q>(J.a2, J.f_a2));
     g.sweep = Q(0);
     g.steps = 0;
     pt.kt = Q(g.kt);
@@ -272,7 +292,7 @@ __device__ __forceinline__ void xfer_init_with(XferState<Q>& x, const StepPoint<
 // Transfer part of a ray's start: coefficients at the camera point, identity propagator.
 template <class Q, bool POL, int EM>
 __device__ __forceinline__ void xfer_init(XferState<Q>& x, const StepPoint<Q>& pt, const DevJob& J,
-                                          const SynchConst& S)
+                                          const SynchConstT<Q>& S)
 {
     Q J1[4], K1[7];
     int e1 = 0;
@@ -281,7 +301,8 @@ __device__ __forceinline__ void xfer_init(XferState<Q>& x, const StepPoint<Q>& p
 }
 
 template <class R, bool POL, int EM>
-__device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J, const SynchConst& S,
+__device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J,
+                                         const SynchConstT<typename Aux<R>::Q>& S,
                                          const Camera& cam, int32_t pix)
 {
     StepPoint<typename Aux<R>::Q> pt;
@@ -317,10 +338,11 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
                                         typename Aux<R>::Q* stg, int sstride)
 {
     using Q = typename Aux<R>::Q;
-    const R a = R(J.a), a2 = R(J.a2);
-    const Q aq = Q(J.a), a2q = Q(J.a2);
-    Q hq = Q(J.step_frac) * t.r;
-    if (hq < Q(J.h_min)) hq = Q(J.h_min);
+    const R a = jr<R>(J.a, J.f_a, J.f_a_lo), a2 = jr<R>(J.a2, J.f_a2, J.f_a2_lo);
+    const Q aq = jq<Q>(J.a, J.f_a), a2q = jq<Q>(J.a2, J.f_a2);
+    const Q hmin = jq<Q>(J.h_min, J.f_h_min);
+    Q hq = jq<Q>(J.step_frac, J.f_step_frac) * t.r;
+    if (hq < hmin) hq = hmin;
     const R h = R(hq);
     const R hh = scale2(h, 0.5f);
     const Q hhq = Q(0.5) * hq;
@@ -450,7 +472,7 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
         t.sweep += sqrt(fmad(cz, cz, fmad(cy, cy, cx * cx)) / n2);
         // a near-critical ray is re-traced at high precision anyway: stop it as soon as it is
         // known to be one (these orbiting rays are also the longest of the FP32 pass)
-        if (t.sweep >= Q(J.fp64_sweep)) return RAY_REROUTE;
+        if (t.sweep >= jq<Q>(J.fp64_sweep, J.f_fp64_sweep)) return RAY_REROUTE;
     }
     Q rn = ks_radius<Q>(q.x, q.y, q.z, a2q);
     t.r = rn;
@@ -460,8 +482,8 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
     pt.h = hq;
     if (POL && XP)
         for (int m = 0; m < 4; ++m) pt.f[m] = t.f[m];
-    if (rn < Q(J.r_in_stop)) return ART_RAY_CAPTURED;
-    if (rn > Q(J.r_out_stop)) return ART_RAY_ESCAPED;
+    if (rn < jq<Q>(J.r_in_stop, J.f_r_in_stop)) return ART_RAY_CAPTURED;
+    if (rn > jq<Q>(J.r_out_stop, J.f_r_out_stop)) return ART_RAY_ESCAPED;
     if (t.steps >= J.max_steps) return ART_RAY_CAP;
     return RAY_GOING;
 }
@@ -523,7 +545,7 @@ __device__ __forceinline__ void xfer_apply(XferState<Q>& t, const StepPoint<Q>& 
 // Transfer part of one step ending at pt: the coefficients there, then xfer_apply.
 template <class Q, bool POL, int EM>
 __device__ __forceinline__ void xfer_step(XferState<Q>& t, const StepPoint<Q>& pt, const DevJob& J,
-                                          const SynchConst& S)
+                                          const SynchConstT<Q>& S)
 {
     Q J1[4], K1[7];
     int e1 = 0;
@@ -538,7 +560,7 @@ template <class Q>
 __device__ __forceinline__ void xfer_transport(XferState<Q>& x, StepPoint<Q>& pt, const Q* stg,
                                                int sstride, const DevJob& J)
 {
-    const Q aq = Q(J.a), a2q = Q(J.a2), hq = pt.h, hhq = Q(0.5) * hq;
+    const Q aq = jq<Q>(J.a, J.f_a), a2q = jq<Q>(J.a2, J.f_a2), hq = pt.h, hhq = Q(0.5) * hq;
     Q d[4], ds[4], fy[4];
     RayState<Q> y = x.y0;
 #pragma unroll 1
@@ -572,7 +594,8 @@ __device__ __forceinline__ void xfer_transport(XferState<Q>& x, StepPoint<Q>& pt
 
 // One RK4 step plus the transfer segment in one thread; returns true when the ray has terminated.
 template <class R, bool SWEEP, bool POL, int EM>
-__device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J, const SynchConst& S)
+__device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J,
+                                         const SynchConstT<typename Aux<R>::Q>& S)
 {
     using Q = typename Aux<R>::Q;
     StepPoint<Q> pt;

@@ -69,7 +69,7 @@ template <class R, bool SWEEP, bool POL, int EM>
 __device__ __forceinline__ void trace_lanes(const TraceArgs& A, const Camera& cam_s)
 {
     const DevJob& J = A.job;
-    const SynchConst& S = A.synch;
+    const auto& S = synch_of<typename Aux<R>::Q>(A.synch, A.synchf);
     const unsigned long long n = *A.count;
     Tracer<R> t;
     bool active = false;
@@ -216,7 +216,11 @@ struct SingleSource {
     const Camera& cam;
     unsigned long long n;
     __device__ const DevJob& job(int32_t) const { return A.job; }
-    __device__ const SynchConst& synch(int32_t) const { return A.synch; }
+    template <class Q>
+    __device__ const SynchConstT<Q>& synch(int32_t) const
+    {
+        return synch_of<Q>(A.synch, A.synchf);
+    }
     __device__ const Camera& camera(int32_t) const { return cam; }
     __device__ unsigned long long* counters() const { return A.counters; }
     __device__ bool next(int64_t& slot, int32_t& pix, int32_t& img) const
@@ -248,7 +252,11 @@ struct BatchSource {
     const BatchTraceArgs& A;
     unsigned long long n;
     __device__ const DevJob& job(int32_t img) const { return A.jobs[img]; }
-    __device__ const SynchConst& synch(int32_t img) const { return A.synchs[img]; }
+    template <class Q>
+    __device__ const SynchConstT<Q>& synch(int32_t img) const
+    {
+        return synch_of<Q>(A.synchs[img], A.synchfs[img]);
+    }
     __device__ const Camera& camera(int32_t img) const { return A.cams[img]; }
     __device__ unsigned long long* counters() const { return A.counters; }
     __device__ bool next(int64_t& slot, int32_t& pix, int32_t& img) const
@@ -389,11 +397,11 @@ __device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL>& 
             __syncwarp();
             pair_arrive(&sm.empty[pr][sl]);
             if (code == REC_INIT) {
-                xfer_init<Q, POL, EM>(x, pt, J, src.synch(img));
+                xfer_init<Q, POL, EM>(x, pt, J, src.template synch<Q>(img));
                 steps = 0;
             } else if (code != REC_IDLE) {
                 ++steps;
-                if (moving) xfer_step<Q, POL, EM>(x, pt, J, src.synch(img));
+                if (moving) xfer_step<Q, POL, EM>(x, pt, J, src.template synch<Q>(img));
                 if (code != RAY_GOING) src.finish(code, steps, x, pix, slot, img);
             }
             if (last) return;
@@ -468,7 +476,7 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
     using Q = float;
     constexpr int NSL = QUAD_SLOTS;
     const DevJob& J = A.job;
-    const SynchConst& S = A.synch;
+    const SynchConstF& S = A.synchf;
     const unsigned long long n = *A.count;
     const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
     if (role == 0) {
@@ -699,7 +707,8 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_batch_kernel(BatchTraceArgs
                 atomicAdd(A.counters + C_BADIDX, 1ull);
                 continue;
             }
-            ray_init<R, POL, EM>(t, J, A.synchs[img], A.cams[img], pix);
+            ray_init<R, POL, EM>(t, J, synch_of<typename Aux<R>::Q>(A.synchs[img], A.synchfs[img]),
+                                 A.cams[img], pix);
             t.img = img;
             t.slot = slot;
             return true;
@@ -709,7 +718,8 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_batch_kernel(BatchTraceArgs
     while (__any_sync(0xffffffffu, active)) {
         if (active) {
             const DevJob& J = A.jobs[t.img];
-            if (ray_step<R, SWEEP, POL, EM>(t, J, A.synchs[t.img])) {
+            if (ray_step<R, SWEEP, POL, EM>(
+                    t, J, synch_of<typename Aux<R>::Q>(A.synchs[t.img], A.synchfs[t.img]))) {
                 finish_batch_ray(A, t.status, t.g.steps, t.x, t.pix, t.slot, t.img);
                 active = fetch_next();
             }
