@@ -192,10 +192,15 @@ struct Halo {
 // CIN = 8 (the 3 input features, S = 1): one channel group per pixel, so a K = 16 slice holds two
 // taps; its second core matrix is the next tap's view of the same plane (LBO = the taps' address
 // difference, 16 B along a row), matching the weights' [tap][channel] columns.
-template <int S, int CIN>
+// MODE 0: forward (bias, ReLU).  MODE 1 (stride 1, CIN = CH): the input gradient of a stride-1
+// layer, which is the same convolution of dY with the taps flipped (B rows ci, columns
+// t' 32 + co holding W[co][8 - t'][ci]) and, instead of bias and ReLU, the forward input's ReLU
+// mask (a.mask > 0) at the output pixel.
+template <int S, int CIN, int MODE = 0>
 __global__ void __launch_bounds__(GEMM_THREADS) conv_halo_kernel(ConvArgs a)
 {
     static_assert(CIN == CH || (CIN == CIN0 && S == 1), "halo convolution variants");
+    static_assert(MODE == 0 || (S == 1 && CIN == CH), "input gradient of stride-1 layers only");
     using HT = Halo<S, CIN>;
     constexpr int CGR = HT::CG;
     constexpr int NQ = HT::HR * HT::HC * CGR;                    // 16-byte chunks of one halo
@@ -305,10 +310,27 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_halo_kernel(ConvArgs a)
             const int oy = y0 + (m >> 3), ox = x0 + (m & 7);
             if (oy < a.Ho && ox < a.Wo) {
                 uint32_t w[16];
+                if (MODE == 0) {
 #pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    w[c] = pack_bf16x2(fmaxf(v[2 * c] + __ldg(a.bias + 2 * c), 0.f),
-                                       fmaxf(v[2 * c + 1] + __ldg(a.bias + 2 * c + 1), 0.f));
+                    for (int c = 0; c < 16; ++c)
+                        w[c] = pack_bf16x2(fmaxf(v[2 * c] + __ldg(a.bias + 2 * c), 0.f),
+                                           fmaxf(v[2 * c + 1] + __ldg(a.bias + 2 * c + 1), 0.f));
+                } else {
+                    const uint4* mk =
+                        reinterpret_cast<const uint4*>(a.mask + ((int64_t)oy * a.Wo + ox) * CH);
+#pragma unroll
+                    for (int c4 = 0; c4 < 4; ++c4) {
+                        const uint4 mv = __ldg(mk + c4);
+                        const __nv_bfloat162* mh = reinterpret_cast<const __nv_bfloat162*>(&mv);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 m2 = __bfloat1622float2(mh[e]);
+                            const int c = 8 * c4 + 2 * e;
+                            w[c / 2] = pack_bf16x2(m2.x > 0.f ? v[c] : 0.f,
+                                                   m2.y > 0.f ? v[c + 1] : 0.f);
+                        }
+                    }
+                }
                 uint4* o = reinterpret_cast<uint4*>(a.out + ((int64_t)oy * a.Wo + ox) * CH);
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4)
@@ -333,25 +355,40 @@ struct WgradArgs {
     int w_off, b_off;  // offsets of this layer's W and b in the vector
     int cin_real;      // channels of the layer's real input (3 or 32)
     int H, W, Ho, Wo, stride;
-    int pix_per_cta;   // output pixels reduced by one CTA (a multiple of WG_PIX)
+    int pix_per_cta;   // output-row segments (of at most WG_PIX pixels) reduced by one CTA
     int* err;
 };
 
-// Weight and bias gradient: rows (t, ci) of one 128-row tile (blockIdx.y), K = output pixels of
-// this CTA's range, in stages of WG_PIX; row 9 CIN is all ones and yields the bias gradient.
-template <int CIN>
+// Weight and bias gradient: rows (t, ci) of one 128-row tile (blockIdx.y), N = the 32 output
+// channels, K = output pixels, one segment of at most WG_PIX pixels of one output row per stage
+// (this CTA's segments: a.pix_per_cta of them from blockIdx.x on).  Per stage the CTA copies the
+// three input rows under the segment (the columns its taps reach, zeros outside the image) and the
+// segment's dY into shared memory with 16-byte loads, then builds the canonical K-major operands
+// from there; row 9 CIN is all ones and yields the bias gradient.  Partial sums per CTA.
+template <int CIN, int S>
+struct WgradSmem {
+    static constexpr int XC = S * WG_PIX + 2;  // staged input columns per row: S x0 - 1 + [0, XC)
+    static constexpr int A_BYTES = 128 * WG_PIX * 2, B_BYTES = CH * WG_PIX * 2;
+    static constexpr int X_BYTES = 3 * XC * CIN * 2;
+    static constexpr int BYTES = A_BYTES + B_BYTES + X_BYTES;
+};
+
+template <int CIN, int S>
 __global__ void __launch_bounds__(GEMM_THREADS) conv_wgrad_kernel(WgradArgs a)
 {
-    __shared__ __align__(1024) uint8_t sA[128 * WG_PIX * 2];
-    __shared__ __align__(1024) uint8_t sB[CH * WG_PIX * 2];
+    using L = WgradSmem<CIN, S>;
+    constexpr int KC = WG_PIX / 8, XC = L::XC, CG = CIN / 8;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + L::A_BYTES;
+    bf16* xt = reinterpret_cast<bf16*>(smem + L::A_BYTES + L::B_BYTES);  // [ky][column][ci]
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tslot;
-    constexpr int KC = WG_PIX / 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int npo = a.Ho * a.Wo;
-    const int o_begin = blockIdx.x * a.pix_per_cta;
-    if (o_begin >= npo) return;  // uniform over the CTA
-    const int o_end = min(npo, o_begin + a.pix_per_cta);
+    const int nsx = (a.Wo + WG_PIX - 1) / WG_PIX, nseg = a.Ho * nsx;
+    const int s_begin = blockIdx.x * a.pix_per_cta;
+    if (s_begin >= nseg) return;  // uniform over the CTA
+    const int s_end = min(nseg, s_begin + a.pix_per_cta);
     const int m0 = blockIdx.y * 128;
     if (tid == 0) umma::mbar_init(&bar);
     if (warp == 0) umma::tmem_alloc(&tslot, 32);
@@ -361,49 +398,55 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_wgrad_kernel(WgradArgs a)
     const uint32_t tmem = tslot;
     bool ok = true;
     int stage = 0;
-    for (int ob = o_begin; ob < o_end; ob += WG_PIX, ++stage) {
-        // A chunk (row m, pixel octet c8): 8 values of row m at 8 consecutive output pixels
+    for (int sg = s_begin; sg < s_end; ++sg, ++stage) {
+        const int oy = sg / nsx, x0 = (sg - oy * nsx) * WG_PIX;
+        const int npx = min(WG_PIX, a.Wo - x0);
+        const int cx0 = S * x0 - 1;  // input column of staged column 0
+        // the three input rows under the segment, 16 bytes (8 channels) per load
+        for (int q = tid; q < 3 * XC * CG; q += GEMM_THREADS) {
+            const int g = q % CG, rest = q / CG, c = rest % XC, ky = rest / XC;
+            const int iy = S * oy + ky - 1, ix = cx0 + c;
+            uint4 v = bf16x8_zero();
+            if (iy >= 0 && iy < a.H && ix >= 0 && ix < a.W)
+                v = __ldg(reinterpret_cast<const uint4*>(a.X + ((int64_t)iy * a.W + ix) * CIN) + g);
+            *reinterpret_cast<uint4*>(xt + (ky * XC + c) * CIN + 8 * g) = v;
+        }
+        // dY of the segment into the canonical B layout (rows co, K = pixels)
+        for (int q = tid; q < WG_PIX * (CH / 8); q += GEMM_THREADS) {
+            const int g = q & 3, px = q >> 2;
+            uint4 v = bf16x8_zero();
+            if (px < npx)
+                v = __ldg(reinterpret_cast<const uint4*>(a.dY + ((int64_t)oy * a.Wo + x0 + px) * CH) + g);
+            const uint16_t* h = reinterpret_cast<const uint16_t*>(&v);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                *reinterpret_cast<uint16_t*>(sB + umma::chunk_off(8 * g + e, px >> 3, WG_PIX) +
+                                             (px & 7) * 2) = h[e];
+        }
+        __syncthreads();
+        // A chunk (row m, pixel octet c8) from the staged rows
         for (int q = tid; q < 128 * KC; q += GEMM_THREADS) {
             const int r = q & 7, rest = q >> 3;
             const int c8 = rest % KC, g = rest / KC;
             const int m = m0 + g * 8 + r;
             uint32_t w[4] = {0, 0, 0, 0};
-            if (m <= 9 * CIN) {
+            if (m < 9 * CIN) {
                 const int tap = m / CIN, ci = m - tap * CIN;
                 const int ky = tap / 3, kx = tap - ky * 3;
+                const uint16_t* row = reinterpret_cast<const uint16_t*>(xt) + ky * XC * CIN + ci;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const int o = ob + c8 * 8 + j;
-                    float v = 0.f;
-                    if (o < o_end) {
-                        if (m == 9 * CIN) {
-                            v = 1.f;
-                        } else {
-                            const int oy = o / a.Wo, ox = o - oy * a.Wo;
-                            const int iy = a.stride * oy + ky - 1, ix = a.stride * ox + kx - 1;
-                            if (iy >= 0 && iy < a.H && ix >= 0 && ix < a.W)
-                                v = __bfloat162float(a.X[((int64_t)iy * a.W + ix) * CIN + ci]);
-                        }
-                    }
-                    const uint32_t h = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+                    const int px = c8 * 8 + j;
+                    const uint32_t h = px < npx ? row[(S * px + kx) * CIN] : 0u;
                     w[j >> 1] |= h << (16 * (j & 1));
                 }
+            } else if (m == 9 * CIN) {
+                const uint32_t one = __bfloat16_as_ushort(__float2bfloat16_rn(1.f));
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (c8 * 8 + j < npx) w[j >> 1] |= one << (16 * (j & 1));
             }
             *reinterpret_cast<uint4*>(sA + umma::chunk_off(g * 8 + r, c8, WG_PIX)) =
-                make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        for (int q = tid; q < CH * KC; q += GEMM_THREADS) {
-            const int r = q & 7, rest = q >> 3;
-            const int c8 = rest % KC, g = rest / KC;
-            const int n = g * 8 + r;
-            uint32_t w[4] = {0, 0, 0, 0};
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int o = ob + c8 * 8 + j;
-                const uint32_t h = o < o_end ? __bfloat16_as_ushort(a.dY[(int64_t)o * CH + n]) : 0u;
-                w[j >> 1] |= h << (16 * (j & 1));
-            }
-            *reinterpret_cast<uint4*>(sB + umma::chunk_off(n, c8, WG_PIX)) =
                 make_uint4(w[0], w[1], w[2], w[3]);
         }
         umma::fence_smem_async();
@@ -423,7 +466,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_wgrad_kernel(WgradArgs a)
         if (!ok) break;
     }
     if (ok) {
-        // this CTA's sums over its pixel range, reduced across CTAs in a fixed order afterwards
+        // this CTA's sums over its segments, reduced across CTAs in a fixed order afterwards
         // (wgrad_reduce_kernel), so that training is reproducible
         float v[32];
         umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
@@ -460,7 +503,7 @@ __global__ void wgrad_reduce_kernel(const float* part, int nblk, int cin_real, f
 // BF16 GEMM operands from the FP32 parameters: forward B[co][t CIN + ci] per layer and the input
 // gradient's B[ci][t 32 + co] for layers 2-4.
 __global__ void cnn_prep_weights_kernel(const float* prm, bf16* f1, bf16* f2, bf16* f3, bf16* f4,
-                                        bf16* d2, bf16* d3, bf16* d4)
+                                        bf16* d2, bf16* d3, bf16* d4, bf16* d2f)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < CH * K1) {
@@ -481,6 +524,11 @@ __global__ void cnn_prep_weights_kernel(const float* prm, bf16* f1, bf16* f2, bf
             d2[i] = __float2bfloat16_rn(prm[P_W2 + idx]);
             d3[i] = __float2bfloat16_rn(prm[P_W3 + idx]);
             d4[i] = __float2bfloat16_rn(prm[P_W4 + idx]);
+        }
+        {   // the stride-1 layer's input gradient as a forward convolution of dY: r = ci,
+            // k = t' 32 + co with the tap flipped (t = 8 - t')
+            const int tf = k / CH, co = k - tf * CH, idx = (co * 9 + (8 - tf)) * CH + r;
+            d2f[i] = __float2bfloat16_rn(prm[P_W2 + idx]);
         }
     }
 }
@@ -608,7 +656,7 @@ __global__ void cnn_adam_kernel(float* prm, float* grad, float* m, float* v, int
 struct CnnState {
     float *prm = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr, *loss = nullptr;
     bf16 *f1 = nullptr, *f2 = nullptr, *f3 = nullptr, *f4 = nullptr, *d2 = nullptr, *d3 = nullptr,
-         *d4 = nullptr;
+         *d4 = nullptr, *d2f = nullptr;
     int* err = nullptr;
     int step = 0;
     bool weights_ready = false;
@@ -640,13 +688,14 @@ static cudaError_t run_conv(const ConvArgs& a, cudaStream_t st)
 }
 
 // Forward convolution of stride S through the halo-tile kernel.
-template <int S, int CIN>
+template <int S, int CIN, int MODE_ = 0>
 static cudaError_t run_conv_halo(const ConvArgs& a, cudaStream_t st)
 {
     using HT = Halo<S, CIN>;
+    constexpr int MODE = MODE_;
     static bool attr = false;  // one device per process is the supported configuration
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv_halo_kernel<S, CIN>,
+        cudaError_t e = cudaFuncSetAttribute(conv_halo_kernel<S, CIN, MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              HT::SMEM);
         if (e != cudaSuccess) return e;
@@ -662,7 +711,7 @@ static cudaError_t run_conv_halo(const ConvArgs& a, cudaStream_t st)
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
             e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv_halo_kernel<S, CIN>);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv_halo_kernel<S, CIN, MODE>);
         if (e != cudaSuccess) return e;
         const int by_smem = smem_sm / (HT::SMEM + (int)fa.sharedSizeBytes + 1024);
         const int by_regs = 65536 / ((fa.numRegs > 0 ? fa.numRegs : 255) * GEMM_THREADS);
@@ -671,37 +720,49 @@ static cudaError_t run_conv_halo(const ConvArgs& a, cudaStream_t st)
         grid_cap = sms * (per > 0 ? per : 1);
     }
     const int tiles = ((a.Wo + HT::TW - 1) / HT::TW) * ((a.Ho + HT::TH - 1) / HT::TH);
-    conv_halo_kernel<S, CIN><<<tiles < grid_cap ? tiles : grid_cap, GEMM_THREADS, HT::SMEM, st>>>(a);
+    conv_halo_kernel<S, CIN, MODE><<<tiles < grid_cap ? tiles : grid_cap, GEMM_THREADS, HT::SMEM,
+                                     st>>>(a);
     return cudaGetLastError();
 }
 
-// CTAs along the pixels of a weight-gradient launch: about 2048 output pixels each, at most
-// WG_CTAS (their partial sums are reduced afterwards), every one with a non-empty range.
+// CTAs along the output-row segments of a weight-gradient launch: about 32 segments (2048 output
+// pixels) each, at most WG_CTAS (their partial sums are reduced afterwards), every one with a
+// non-empty range.
 constexpr int WG_CTAS = 608;
-static int wgrad_ctas(int npo, int* ppc)
+static int wgrad_ctas(int Ho, int Wo, int* spc)
 {
-    int ctas = (npo + 2047) / 2048;
+    const int nseg = Ho * ((Wo + WG_PIX - 1) / WG_PIX);
+    int ctas = (nseg + 31) / 32;
     if (ctas < 1) ctas = 1;
     if (ctas > WG_CTAS) ctas = WG_CTAS;
-    *ppc = ((npo + ctas - 1) / ctas + WG_PIX - 1) / WG_PIX * WG_PIX;
-    return (npo + *ppc - 1) / *ppc;
+    *spc = (nseg + ctas - 1) / ctas;
+    return (nseg + *spc - 1) / *spc;
 }
 
 // Weight and bias gradients of one layer: the tensor-core partial sums, then their reduction into
 // grad (a.part must hold wgrad_ctas() x (9 CH cin_real + CH) floats).
-template <int CIN>
-static cudaError_t run_wgrad(WgradArgs a, float* grad, cudaStream_t st)
+template <int CIN, int S>
+static cudaError_t run_wgrad_s(WgradArgs a, float* grad, cudaStream_t st)
 {
-    const int npo = a.Ho * a.Wo;
-    const int ctas = wgrad_ctas(npo, &a.pix_per_cta);
+    using L = WgradSmem<CIN, S>;
+    const int ctas = wgrad_ctas(a.Ho, a.Wo, &a.pix_per_cta);
     const int mtiles = (9 * CIN + 1 + 127) / 128;
-    conv_wgrad_kernel<CIN><<<dim3(ctas, mtiles), GEMM_THREADS, 0, st>>>(a);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaFuncSetAttribute(conv_wgrad_kernel<CIN, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+    if (e != cudaSuccess) return e;
+    conv_wgrad_kernel<CIN, S><<<dim3(ctas, mtiles), GEMM_THREADS, L::BYTES, st>>>(a);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int np = CH * 9 * a.cin_real + CH;
     wgrad_reduce_kernel<<<(np + 255) / 256, 256, 0, st>>>(a.part, ctas, a.cin_real, grad, a.w_off,
                                                           a.b_off);
     return cudaGetLastError();
+}
+
+template <int CIN>
+static cudaError_t run_wgrad(WgradArgs a, float* grad, cudaStream_t st)
+{
+    return a.stride == 1 ? run_wgrad_s<CIN, 1>(a, grad, st) : run_wgrad_s<CIN, 2>(a, grad, st);
 }
 
 #define CKE(x)                                 \
@@ -722,7 +783,7 @@ static cudaError_t ensure_state(CnnState*& s)
     CKE(cudaMalloc(&s->err, sizeof(int)));
     CKE(cudaMemset(s->err, 0, sizeof(int)));
     CKE(cudaMalloc(&s->f1, sizeof(bf16) * CH * K1));
-    for (bf16** p : {&s->f2, &s->f3, &s->f4, &s->d2, &s->d3, &s->d4})
+    for (bf16** p : {&s->f2, &s->f3, &s->f4, &s->d2, &s->d3, &s->d4, &s->d2f})
         CKE(cudaMalloc(p, sizeof(bf16) * CH * KH));
     return cudaSuccess;
 }
@@ -747,8 +808,8 @@ void cnn_destroy(CnnState* s)
 {
     if (!s) return;
     for (float* p : {s->prm, s->grad, s->m, s->v, s->loss}) cudaFree(p);
-    for (bf16* p : {s->f1, s->f2, s->f3, s->f4, s->d2, s->d3, s->d4, s->x0, s->a1, s->a2, s->a3,
-                    s->a4, s->g1, s->g2, s->g3, s->g4})
+    for (bf16* p : {s->f1, s->f2, s->f3, s->f4, s->d2, s->d3, s->d4, s->d2f, s->x0, s->a1, s->a2,
+                    s->a3, s->a4, s->g1, s->g2, s->g3, s->g4})
         cudaFree(p);
     cudaFree(s->err);
     cudaFree(s->part);
@@ -776,8 +837,8 @@ cudaError_t cnn_read(CnnState* s, float* host_params, cudaStream_t st)
 static cudaError_t prep_weights(CnnState* s, cudaStream_t st)
 {
     if (s->weights_ready) return cudaSuccess;
-    cnn_prep_weights_kernel<<<(CH * KH + 255) / 256, 256, 0, st>>>(s->prm, s->f1, s->f2, s->f3,
-                                                                   s->f4, s->d2, s->d3, s->d4);
+    cnn_prep_weights_kernel<<<(CH * KH + 255) / 256, 256, 0, st>>>(
+        s->prm, s->f1, s->f2, s->f3, s->f4, s->d2, s->d3, s->d4, s->d2f);
     CKE(cudaGetLastError());
     s->weights_ready = true;
     return cudaSuccess;
@@ -812,7 +873,7 @@ static cudaError_t forward_backward(CnnState* s, int H, int W, const float* targ
         // partial-sum scratch: the head's blocks, and the largest weight-gradient launch
         int ppc;
         int64_t need = (int64_t)hblk * (CH + 2);
-        need = std::max<int64_t>(need, (int64_t)wgrad_ctas(H * W, &ppc) * (CH * 9 * CH + CH));
+        need = std::max<int64_t>(need, (int64_t)wgrad_ctas(H, W, &ppc) * (CH * 9 * CH + CH));
         if (need > s->part_cap) {
             CKE(cudaStreamSynchronize(st));
             cudaFree(s->part);
@@ -851,9 +912,10 @@ static cudaError_t forward_backward(CnnState* s, int H, int W, const float* targ
     w.X = s->a1; w.dY = s->g2; w.w_off = P_W2; w.b_off = P_B2;
     w.Ho = H; w.Wo = W; w.stride = 1;
     CKE(run_wgrad<CH>(w, s->grad, st));
-    d.src = s->g2; d.B = s->d2; d.mask = s->a1; d.out = s->g1;
-    d.Ho = H; d.Wo = W; d.stride = 1;
-    CKE((run_conv<CH, KH, 1>(d, st)));
+    // its input gradient: the forward halo kernel on dY with the flipped taps, ReLU mask of a1
+    d.src = s->g2; d.B = s->d2f; d.mask = s->a1; d.out = s->g1;
+    d.H = H; d.W = W; d.Ho = H; d.Wo = W; d.stride = 1;
+    CKE((run_conv_halo<1, CH, 1>(d, st)));
     // layer 1: X = x0 (8 channels, 3 real), dY = g1
     w.X = s->x0; w.dY = s->g1; w.w_off = P_W1; w.b_off = P_B1; w.cin_real = NFEAT;
     CKE(run_wgrad<CIN0>(w, s->grad, st));
