@@ -62,10 +62,13 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b)
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-// Implicit-GEMM convolution (forward, MODE 0) or its input gradient (MODE 1), one 128-row tile
-// of pixels per CTA, N = 32 channels, K = KPAD.
-template <int CIN, int KPAD, int MODE>
-__global__ void __launch_bounds__(GEMM_THREADS) conv_gemm_kernel(ConvArgs a)
+// Input gradient of a stride-2 layer as an implicit GEMM: 128-row tiles of input pixels, N = 32
+// channels, K = KPAD (9 taps x 32 output channels of dY, gathered; the taps that do not land on an
+// output pixel of the strided forward are zero).  The CTAs are persistent: the weights are loaded
+// once per CTA, then tiles blockIdx.x, + gridDim.x, ...  Output: dX times the forward input's ReLU
+// mask.
+template <int CIN, int KPAD>
+__global__ void __launch_bounds__(GEMM_THREADS) conv_dgrad_kernel(ConvArgs a)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ __align__(8) uint64_t bar;
@@ -74,37 +77,10 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_gemm_kernel(ConvArgs a)
     uint8_t* sB = smem + 128 * KPAD * 2;
     constexpr int KC = KPAD / 8, TAPC = CIN / 8;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int rows = MODE == 0 ? a.Ho * a.Wo : a.H * a.W;
-    const int p0 = blockIdx.x * 128;
-    const int sW = MODE == 0 ? a.W : a.Wo, sH = MODE == 0 ? a.H : a.Ho;  // source grid
-    const int rW = MODE == 0 ? a.Wo : a.W;                             // row grid width
-    // A: chunk (row m, column group kc); rows fastest within an 8-row group
-    for (int q = tid; q < 128 * KC; q += GEMM_THREADS) {
-        const int r = q & 7, rest = q >> 3;
-        const int kc = rest % KC, g = rest / KC;
-        const int m = g * 8 + r, p = p0 + m;
-        uint4 v = bf16x8_zero();
-        const int tap = kc / TAPC, cg = kc - tap * TAPC;
-        if (p < rows && tap < 9) {
-            const int py = p / rW, px = p - py * rW;
-            const int ky = tap / 3, kx = tap - ky * 3;
-            int sy, sx;
-            bool ok;
-            if (MODE == 0) {
-                sy = a.stride * py + ky - 1;
-                sx = a.stride * px + kx - 1;
-                ok = true;
-            } else {
-                const int ny = py + 1 - ky, nx = px + 1 - kx;
-                sy = ny / a.stride;
-                sx = nx / a.stride;
-                ok = ny >= 0 && nx >= 0 && sy * a.stride == ny && sx * a.stride == nx;
-            }
-            if (ok && sy >= 0 && sy < sH && sx >= 0 && sx < sW)
-                v = __ldg(reinterpret_cast<const uint4*>(a.src + ((int64_t)sy * sW + sx) * CIN) + cg);
-        }
-        *reinterpret_cast<uint4*>(sA + umma::chunk_off(m, kc, KPAD)) = v;
-    }
+    const int rows = a.H * a.W;
+    const int ntiles = (rows + 127) / 128;
+    const int sW = a.Wo, sH = a.Ho;  // source grid (dY)
+    const int rW = a.W;              // row grid width
     for (int q = tid; q < CH * KC; q += GEMM_THREADS) {
         const int r = q & 7, rest = q >> 3;
         const int kc = rest % KC, g = rest / KC;
@@ -114,32 +90,51 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_gemm_kernel(ConvArgs a)
     }
     if (tid == 0) umma::mbar_init(&bar);
     if (warp == 0) umma::tmem_alloc(&tslot, 32);
-    umma::fence_smem_async();
     umma::fence_before();
     __syncthreads();
     umma::fence_after();
     const uint32_t tmem = tslot;
-    if (tid == 0) {
-        const uint32_t ab = umma::smem_u32(sA), bb = umma::smem_u32(sB), sbo = KC * 128;
-        for (int kb = 0; kb < KPAD / 16; ++kb)
-            umma::mma(tmem, umma::desc(ab + kb * 256, 128, sbo), umma::desc(bb + kb * 256, 128, sbo),
-                      umma::idesc_bf16(128, CH), kb > 0);
-        umma::commit(&bar);
-    }
-    const bool ok = __syncthreads_and(umma::wait(&bar, 0));
-    umma::fence_after();
-    if (ok) {
-        float v[32];
-        umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
-        const int p = p0 + warp * 32 + lane;
-        if (p < rows) {
-            uint32_t w[16];
-            if (MODE == 0) {
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    w[c] = pack_bf16x2(fmaxf(v[2 * c] + __ldg(a.bias + 2 * c), 0.f),
-                                       fmaxf(v[2 * c + 1] + __ldg(a.bias + 2 * c + 1), 0.f));
-            } else {
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, phase ^= 1u) {
+        const int p0 = tile * 128;
+        // A: chunk (row m, column group kc); rows fastest within an 8-row group
+        for (int q = tid; q < 128 * KC; q += GEMM_THREADS) {
+            const int r = q & 7, rest = q >> 3;
+            const int kc = rest % KC, g = rest / KC;
+            const int m = g * 8 + r, p = p0 + m;
+            uint4 v = bf16x8_zero();
+            const int tap = kc / TAPC, cg = kc - tap * TAPC;
+            if (p < rows && tap < 9) {
+                const int py = p / rW, px = p - py * rW;
+                const int ky = tap / 3, kx = tap - ky * 3;
+                const int ny = py + 1 - ky, nx = px + 1 - kx;
+                const int sy = ny / a.stride, sx = nx / a.stride;
+                if (ny >= 0 && nx >= 0 && sy * a.stride == ny && sx * a.stride == nx && sy < sH &&
+                    sx < sW)
+                    v = __ldg(reinterpret_cast<const uint4*>(a.src + ((int64_t)sy * sW + sx) * CIN) + cg);
+            }
+            *reinterpret_cast<uint4*>(sA + umma::chunk_off(m, kc, KPAD)) = v;
+        }
+        umma::fence_smem_async();
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
+        if (tid == 0) {
+            const uint32_t ab = umma::smem_u32(sA), bb = umma::smem_u32(sB), sbo = KC * 128;
+            for (int kb = 0; kb < KPAD / 16; ++kb)
+                umma::mma(tmem, umma::desc(ab + kb * 256, 128, sbo),
+                          umma::desc(bb + kb * 256, 128, sbo), umma::idesc_bf16(128, CH), kb > 0);
+            umma::commit(&bar);
+        }
+        ok = __syncthreads_and(umma::wait(&bar, phase));
+        umma::fence_after();
+        if (ok) {
+            float v[32];
+            umma::ld32(tmem + ((uint32_t)(warp * 32) << 16), v);
+            const int p = p0 + warp * 32 + lane;
+            if (p < rows) {
+                uint32_t w[16];
                 const uint4* mk = reinterpret_cast<const uint4*>(a.mask + (int64_t)p * CH);
 #pragma unroll
                 for (int c4 = 0; c4 < 4; ++c4) {
@@ -152,16 +147,19 @@ __global__ void __launch_bounds__(GEMM_THREADS) conv_gemm_kernel(ConvArgs a)
                         w[c / 2] = pack_bf16x2(f.x > 0.f ? v[c] : 0.f, f.y > 0.f ? v[c + 1] : 0.f);
                     }
                 }
-            }
-            uint4* o = reinterpret_cast<uint4*>(a.out + (int64_t)p * CH);
+                uint4* o = reinterpret_cast<uint4*>(a.out + (int64_t)p * CH);
 #pragma unroll
-            for (int c4 = 0; c4 < 4; ++c4)
-                o[c4] = make_uint4(w[4 * c4], w[4 * c4 + 1], w[4 * c4 + 2], w[4 * c4 + 3]);
+                for (int c4 = 0; c4 < 4; ++c4)
+                    o[c4] = make_uint4(w[4 * c4], w[4 * c4 + 1], w[4 * c4 + 2], w[4 * c4 + 3]);
+            }
+        } else if (tid == 0) {
+            atomicExch(a.err, 1);
         }
-    } else if (tid == 0) {
-        atomicExch(a.err, 1);
+        // the tensor-memory reads and the shared-memory tile are done before the next tile
+        umma::fence_before();
+        __syncthreads();
+        umma::fence_after();
     }
-    umma::fence_before();
     __syncthreads();
     if (warp == 0) umma::tmem_free(tmem, 32);
 }
@@ -671,19 +669,29 @@ struct CnnState {
 
 static int conv_smem(int kpad) { return (128 + CH) * kpad * 2; }
 
-template <int CIN, int KPAD, int MODE>
-static cudaError_t run_conv(const ConvArgs& a, cudaStream_t st)
+template <int CIN, int KPAD>
+static cudaError_t run_dgrad(const ConvArgs& a, cudaStream_t st)
 {
-    static bool attr = false;  // one device per process is the supported configuration
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(conv_gemm_kernel<CIN, KPAD, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             conv_smem(KPAD));
+    cudaError_t e = cudaFuncSetAttribute(conv_dgrad_kernel<CIN, KPAD>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem(KPAD));
+    if (e != cudaSuccess) return e;
+    static int grid_cap = 0;  // resident CTAs of the device (persistent grid)
+    if (!grid_cap) {
+        int dev = 0, sms = 0, smem_sm = 0;
+        cudaFuncAttributes fa;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv_dgrad_kernel<CIN, KPAD>);
         if (e != cudaSuccess) return e;
-        attr = true;
+        int per = smem_sm / (conv_smem(KPAD) + (int)fa.sharedSizeBytes + 1024);
+        if (per > 8) per = 8;  // 8 x 32 tensor-memory columns of 512
+        grid_cap = sms * (per > 0 ? per : 1);
     }
-    const int rows = MODE == 0 ? a.Ho * a.Wo : a.H * a.W;
-    conv_gemm_kernel<CIN, KPAD, MODE><<<(rows + 127) / 128, GEMM_THREADS, conv_smem(KPAD), st>>>(a);
+    const int tiles = (a.H * a.W + 127) / 128;
+    conv_dgrad_kernel<CIN, KPAD><<<tiles < grid_cap ? tiles : grid_cap, GEMM_THREADS,
+                                  conv_smem(KPAD), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -900,14 +908,14 @@ static cudaError_t forward_backward(CnnState* s, int H, int W, const float* targ
     CKE(run_wgrad<CH>(w, s->grad, st));
     d.src = s->g4; d.B = s->d4; d.mask = s->a3; d.out = s->g3;
     d.H = H2; d.W = W2; d.Ho = H4; d.Wo = W4; d.stride = 2;
-    CKE((run_conv<CH, KH, 1>(d, st)));
+    CKE((run_dgrad<CH, KH>(d, st)));
     // layer 3: X = a2 (H x W), dY = g3 (H2 x W2)
     w.X = s->a2; w.dY = s->g3; w.w_off = P_W3; w.b_off = P_B3;
     w.H = H; w.W = W; w.Ho = H2; w.Wo = W2; w.stride = 2;
     CKE(run_wgrad<CH>(w, s->grad, st));
     d.src = s->g3; d.B = s->d3; d.mask = s->a2; d.out = s->g2;
     d.H = H; d.W = W; d.Ho = H2; d.Wo = W2; d.stride = 2;
-    CKE((run_conv<CH, KH, 1>(d, st)));
+    CKE((run_dgrad<CH, KH>(d, st)));
     // layer 2: X = a1, dY = g2 (stride 1)
     w.X = s->a1; w.dY = s->g2; w.w_off = P_W2; w.b_off = P_B2;
     w.Ho = H; w.Wo = W; w.stride = 1;
