@@ -11,9 +11,11 @@
 //   forward  D[o][co]        = sum_{t, ci} X[s o + t - 1][ci] W[co][t][ci]        (M = output pixels)
 //   dgrad    D[i][ci]        = sum_{t, co} dY[(i + 1 - t)/s][co] W[co][t][ci]     (M = input pixels)
 //   wgrad    D[(t, ci)][co]  = sum_o X[s o + t - 1][ci] dY[o][co]                 (K = output pixels)
-// with 128-row tiles gathered into shared memory in the canonical K-major layout (umma.cuh), one
-// thread issuing the MMAs, completion through an mbarrier, and the epilogue reading D from tensor
-// memory.  The weight gradient carries one extra row of ones so the same GEMM yields the bias
+// with 128-row operand tiles in shared memory in the canonical K-major layout (umma.cuh): views
+// of a staged input halo (the forward, and the stride-1 layer's dgrad as a forward convolution of
+// dY with flipped taps), a gathered tile (the stride-2 dgrad), or one built from staged input rows
+// (the wgrad); one thread issues the MMAs, completion through an mbarrier, and the epilogue reads D
+// from tensor memory.  The weight gradient carries one extra row of ones so the same GEMM yields the bias
 // gradient.  Activations are NHWC BF16 (32 channels, 64 B per pixel; the 3 input features padded
 // to 8 channels); the head, the loss and the optimizer (Adam) run in FP32 on the CUDA cores.
 #include <cuda_bf16.h>
