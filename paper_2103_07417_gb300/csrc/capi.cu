@@ -620,6 +620,8 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
             // discontinuity (its emission is evaluated in FP32) is handed on to FP64
             b.synch.e_sig = EDGE_SIGMA_TOL_DF;
             b.synch.e_rin = EDGE_RIN_TOL_DF;
+            b.synchf.e_sig = (float)EDGE_SIGMA_TOL_DF;  // the copy the double-float transfer reads
+            b.synchf.e_rin = (float)EDGE_RIN_TOL_DF;
             b.reroute = c->reroute2;
             b.reroute_count = c->counters + C_REROUTE2;
         }
