@@ -755,8 +755,9 @@ def main():
     # the timed region; every setting renders the same image)
     tune = None
     if not args.no_tune:
-        (tq, tp, tb64, tb32), tms = ctx.art_autotune(job, img, mask, reps=3)
+        (tq, tp, tb64, tb32, tq64), tms = ctx.art_autotune(job, img, mask, reps=3)
         tune = {"quad_rays": tq, "pair_rays": tp, "blocks64": tb64, "blocks32": tb32,
+                "quad64_rays": tq64,
                 "median_ms": tms,
                 "default": list(art.TUNE_DEFAULT)}
     for _ in range(max(args.warmup, 1)):

@@ -304,21 +304,27 @@ int art_render_host(art_ctx* ctx, const art_job* job, double* img_host, uint8_t*
  * implementation).  Kernel forms of the FP32 pass: a level's FP32 launch whose queue holds at most
  * quad_rays rays per block of the persistent grid splits each step over four warps per 32 rays
  * (geodesic, two warps for the emission coefficients of alternate steps, segment); at most
- * pair_rays, over two warps (geodesic, transfer); longer queues run one thread per ray.  Grid size:
+ * pair_rays, over two warps (geodesic, transfer); longer queues run one thread per ray.  FP64
+ * launches take the four-warp form when their queue holds at most quad64_rays rays per block, the
+ * two-warp form otherwise (an FP64 warp instruction costs a scheduler 64 cycles whatever its
+ * active lanes, so a lone ray's step lasts as long as its slowest warp's FP64 chain).  Grid size:
  * the persistent grids of the FP64 launches hold blocks64 blocks of 128 threads per SM, those of
  * the FP32 and double-float launches blocks32 (0: as many as fit; a larger value is capped there).
  * The forms and grids give bit-identical rays, so the setting changes speed only.  Defaults
- * ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT (one block of two warp
- * pairs per SM: one warp per scheduler, which is all the FP64 pipe takes), 0; valid settings have
- * 0 <= quad_rays <= pair_rays <= 4096 and 0 <= blocks64, blocks32 <= 64. */
+ * ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT (one block of four
+ * warps per SM: one warp per scheduler, which is all the FP64 pipe takes), 0,
+ * ART_TUNE_QUAD64_DEFAULT; valid settings have 0 <= quad_rays <= pair_rays <= 4096,
+ * 0 <= quad64_rays <= 4096 and 0 <= blocks64, blocks32 <= 64. */
 #define ART_TUNE_QUAD_DEFAULT 32
 #define ART_TUNE_PAIR_DEFAULT 64
 #define ART_TUNE_BLOCKS64_DEFAULT 1
+#define ART_TUNE_QUAD64_DEFAULT 32
 typedef struct art_tune {
     int32_t quad_rays;
     int32_t pair_rays;
     int32_t blocks64;
     int32_t blocks32;
+    int32_t quad64_rays;
 } art_tune;
 
 /* Set the context's scheduling setting (t == NULL restores the defaults), or read it.
@@ -329,9 +335,10 @@ int art_get_tune(art_ctx* ctx, art_tune* t_out);
 /* Autotuner: renders `job` (as art_render, into img_dev / mask_dev) with each candidate setting,
  * once to warm up and `reps` times timed with CUDA events on the context's stream, one dimension at
  * a time (eight FP32 kernel-form threshold pairs with the default grids; then, from the best,
- * blocks64 in {0, 1, 2} if the job has FP64 launches; then blocks32 in {1, 2} if it has FP32 ones), keeps the
- * setting with the lowest median time in the context and returns it in *best (nullable) with that
- * median in *best_ms (nullable).  img_dev and mask_dev hold the job's image
+ * blocks64 in {0, 1, 2} if the job has FP64 launches; then blocks32 in {1, 2} if it has FP32
+ * ones; then quad64_rays in {0, 64} if it has FP64 launches), keeps the setting with the lowest
+ * median time in the context and returns it in *best (nullable) with that median in *best_ms
+ * (nullable).  img_dev and mask_dev hold the job's image
  * afterwards (the same for every setting).  Synchronises the stream.  Errors: ART_ERR_ARG (reps
  * outside 1..32, or as art_render), and those of art_render, after which the previous setting is
  * kept. */

@@ -55,13 +55,14 @@ class Job(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     """art_tune: FP32 kernel-form thresholds in rays per block (quad form up to quad_rays, pair
-    form up to pair_rays) and the persistent grids' blocks per SM of the FP64 and of the FP32 /
-    double-float launches (0: as many as fit)."""
+    form up to pair_rays), the persistent grids' blocks per SM of the FP64 and of the FP32 /
+    double-float launches (0: as many as fit), and the FP64 launches' quad-form threshold."""
     _fields_ = [("quad_rays", ctypes.c_int32), ("pair_rays", ctypes.c_int32),
-                ("blocks64", ctypes.c_int32), ("blocks32", ctypes.c_int32)]
+                ("blocks64", ctypes.c_int32), ("blocks32", ctypes.c_int32),
+                ("quad64_rays", ctypes.c_int32)]
 
 
-TUNE_DEFAULT = (32, 64, 1, 0)
+TUNE_DEFAULT = (32, 64, 1, 0, 32)
 
 
 class Stats(ctypes.Structure):
@@ -442,29 +443,29 @@ class Context:
                "art_graph_render")
 
     def art_set_tune(self, quad_rays: int | None = None, pair_rays: int | None = None,
-                     blocks64: int = 1, blocks32: int = 0):
-        """Set the scheduling (FP32 kernel-form thresholds, grid blocks per SM); no arguments
-        restore the defaults."""
+                     blocks64: int = 1, blocks32: int = 0, quad64_rays: int = 32):
+        """Set the scheduling (FP32 kernel-form thresholds, grid blocks per SM, FP64 quad-form
+        threshold); no arguments restore the defaults."""
         if quad_rays is None and pair_rays is None:
             _check(load().art_set_tune(self._ctx, None), "art_set_tune")
             return
-        t = Tune(int(quad_rays), int(pair_rays), int(blocks64), int(blocks32))
+        t = Tune(int(quad_rays), int(pair_rays), int(blocks64), int(blocks32), int(quad64_rays))
         _check(load().art_set_tune(self._ctx, ctypes.byref(t)), "art_set_tune")
 
     def art_get_tune(self) -> tuple:
-        """(quad_rays, pair_rays, blocks64, blocks32)."""
+        """(quad_rays, pair_rays, blocks64, blocks32, quad64_rays)."""
         t = Tune()
         _check(load().art_get_tune(self._ctx, ctypes.byref(t)), "art_get_tune")
-        return t.quad_rays, t.pair_rays, t.blocks64, t.blocks32
+        return t.quad_rays, t.pair_rays, t.blocks64, t.blocks32, t.quad64_rays
 
     def art_autotune(self, job: Job, img, mask, reps: int = 3):
         """Time `job` under each candidate setting, keep the fastest in the context; returns
-        ((quad_rays, pair_rays, blocks64, blocks32), median ms)."""
+        ((quad_rays, pair_rays, blocks64, blocks32, quad64_rays), median ms)."""
         t = Tune()
         ms = ctypes.c_float()
         _check(load().art_autotune(self._ctx, ctypes.byref(job), _dptr(img), _dptr(mask), int(reps),
                                    ctypes.byref(t), ctypes.byref(ms)), "art_autotune")
-        return (t.quad_rays, t.pair_rays, t.blocks64, t.blocks32), ms.value
+        return (t.quad_rays, t.pair_rays, t.blocks64, t.blocks32, t.quad64_rays), ms.value
 
     def art_measure_alu_peaks(self) -> dict:
         """Measured FP32 and FP64 fused multiply-add throughput of this GPU, TFLOP/s."""

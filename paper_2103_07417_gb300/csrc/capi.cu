@@ -15,7 +15,8 @@
 using namespace art;
 
 struct art_ctx {
-    art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT, 0};
+    art_tune tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT, 0,
+                ART_TUNE_QUAD64_DEFAULT};
     // exact decisions in a batch (art_render_batch): sub-contexts, each with a stream of its own
     // and its own scratch, render the images concurrently; every image's counters and
     // normalisation are copied into xsnap on its sub-context's stream
@@ -561,6 +562,7 @@ static int trace_queue(art_ctx* c, const art_job* job, const DevJob& J,
     a.pix_steps = c->cur_steps;
     a.quad_rays = c->tune.quad_rays;
     a.pair_rays = c->tune.pair_rays;
+    a.quad64_rays = c->tune.quad64_rays;
     a.pix_minr = pix_minr;
     a.pix_turn = pix_turn;
     a.spec_from = spec_from;
@@ -1804,14 +1806,16 @@ extern "C" int art_cnn_sample(art_ctx* c, const art_job* job, const double* img_
 static bool tune_valid(const art_tune* t)
 {
     return t->quad_rays >= 0 && t->pair_rays >= t->quad_rays && t->pair_rays <= 4096 &&
-           t->blocks64 >= 0 && t->blocks64 <= 64 && t->blocks32 >= 0 && t->blocks32 <= 64;
+           t->blocks64 >= 0 && t->blocks64 <= 64 && t->blocks32 >= 0 && t->blocks32 <= 64 &&
+           t->quad64_rays >= 0 && t->quad64_rays <= 4096;
 }
 
 extern "C" int art_set_tune(art_ctx* c, const art_tune* t)
 {
     if (!c) return ART_ERR_ARG;
     if (!t) {
-        c->tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT, 0};
+        c->tune = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT, 0,
+                ART_TUNE_QUAD64_DEFAULT};
         return ART_OK;
     }
     if (!tune_valid(t)) return ART_ERR_ARG;
@@ -1833,7 +1837,8 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
     // candidates, one dimension at a time: the FP32 kernel-form thresholds (one-thread only, pair
     // only, quad/pair splits around the defaults), then with the best of them the persistent
     // grids' blocks per SM, of the FP64 launches (where the job has any: 0 = as many as fit, 1,
-    // 2) and of the FP32 and double-float ones (0, then 1 or 2)
+    // 2) and of the FP32 and double-float ones (0, then 1 or 2), then the FP64 launches' quad
+    // threshold (0: never, 64)
     static const int forms[][2] = {{0, 0},   {0, 64},   {32, 64},  {32, 96},
                                    {64, 96}, {32, 128}, {64, 128}, {16, 64}};
     const bool has64 = job->precision != ART_FP32, has32 = job->precision != ART_FP64;
@@ -1845,7 +1850,8 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
         return ART_ERR_CUDA;
     }
     const art_tune saved = c->tune;
-    art_tune win = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT, 0};
+    art_tune win = {ART_TUNE_QUAD_DEFAULT, ART_TUNE_PAIR_DEFAULT, ART_TUNE_BLOCKS64_DEFAULT, 0,
+                ART_TUNE_QUAD64_DEFAULT};
     float win_ms = INFINITY;
     int rc = ART_OK;
     std::vector<float> t(reps);
@@ -1871,7 +1877,7 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
     for (const auto& f : forms) {
         if (rc) break;
         if (has32 || (f[0] == ART_TUNE_QUAD_DEFAULT && f[1] == ART_TUNE_PAIR_DEFAULT))
-            trial(art_tune{f[0], f[1], ART_TUNE_BLOCKS64_DEFAULT, 0});
+            trial(art_tune{f[0], f[1], ART_TUNE_BLOCKS64_DEFAULT, 0, ART_TUNE_QUAD64_DEFAULT});
     }
     for (int b = 0; b <= 2 && has64 && !rc; ++b) {
         if (b == ART_TUNE_BLOCKS64_DEFAULT) continue;
@@ -1884,6 +1890,12 @@ extern "C" int art_autotune(art_ctx* c, const art_job* job, double* img_dev, uin
         art_tune cand = win;
         cand.blocks64 = best64;
         cand.blocks32 = b;
+        trial(cand);
+    }
+    static const int quad64[] = {0, 64};
+    for (int k = 0; k < 2 && has64 && !rc; ++k) {
+        art_tune cand = win;
+        cand.quad64_rays = quad64[k];
         trial(cand);
     }
     cudaEventDestroy(e0);
@@ -1913,8 +1925,7 @@ extern "C" int art_graph_render(art_ctx* c, const art_job* job, double* img_dev,
                              c->g_x1max};
     const bool same = c->gexec && memcmp(&c->gjob, job, sizeof(art_job)) == 0 &&
                       c->gimg == img_dev && c->gmask == mask_dev &&
-                      c->gtune.quad_rays == c->tune.quad_rays &&
-                      c->gtune.pair_rays == c->tune.pair_rays && c->ggrid == c->grid &&
+                      memcmp(&c->gtune, &c->tune, sizeof(art_tune)) == 0 && c->ggrid == c->grid &&
                       memcmp(c->ggmeta, gmeta, sizeof gmeta) == 0 && c->ggen == c->scratch_gen;
     if (!same) {
         // one ordinary render sizes every scratch buffer (no allocation or synchronisation may

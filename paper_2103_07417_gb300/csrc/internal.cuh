@@ -82,6 +82,8 @@ struct TraceArgs {
     // kernel forms of the FP32 pass (trace_kernels.cuh): queues of at most quad_rays rays per
     // block take the four-warp form, of at most pair_rays the two-warp form (art_tune)
     int32_t quad_rays, pair_rays;
+    // FP64 launches: queues of at most quad64_rays rays per block take the four-warp form
+    int32_t quad64_rays;
 };
 
 // Transient mask values of the learned path (a render ends with every point TRACED or INTERP).

@@ -124,6 +124,7 @@ extern "C" int art_trace_pixels_noalloc(const art_job* job, const int32_t* pix_d
     a.job = J;
     a.quad_rays = ART_TUNE_QUAD_DEFAULT;
     a.pair_rays = ART_TUNE_PAIR_DEFAULT;
+    a.quad64_rays = ART_TUNE_QUAD64_DEFAULT;
     art_make_synch(job, &a.synch);
     a.synchf = synch_to_float(a.synch);
     a.cam = cam;

@@ -410,8 +410,8 @@ __device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL>& 
 }
 
 // --------------------------------------------------------------------------------------------
-// Warp-quad form (FP32 kernels).  In the warp-pair form the transfer warp is the slower half: the
-// emission coefficients at a point are a long dependent chain, but a pure function of the point,
+// Warp-quad form (FP32 and FP64 kernels).  In the warp-pair form the transfer warp is the slower
+// half: the emission coefficients at a point are a long dependent chain, but a pure function of the point,
 // so consecutive steps' coefficients can be computed at the same time.  Here a block's four warps
 // share 32 rays: warp 0 integrates the geodesics (and transports the covector), warps 1 and 2
 // compute the coefficients at the end points of the even and the odd steps, and warp 3 applies
@@ -427,7 +427,8 @@ constexpr int QUAD_SLOTS = 4;
 // FP32 kernels: queues of up to A.quad_rays rays per block take the quad form (one group of 32
 // rays per block at once; longer queues are drained by the same warps in turn), up to
 // A.pair_rays the pair form, longer ones the one-thread form (defaults 32 and 64, set per context
-// by art_set_tune or art_autotune).
+// by art_set_tune or art_autotune).  FP64 kernels: up to A.quad64_rays rays per block the quad
+// form, longer queues the pair form (default 32).
 
 template <class Q>
 struct QuadRing {
@@ -469,19 +470,21 @@ __device__ __forceinline__ void quad_read_point(const QuadRing<Q>& sm, int sl, i
 }
 
 // Warp-quad form (ring mbarriers initialised and the block synchronised before the call).
-template <bool SWEEP, bool POL, int EM>
+template <class R, bool SWEEP, bool POL, int EM>
 __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& cam_s,
-                                            QuadRing<float>& sm)
+                                            QuadRing<R>& sm)
 {
-    using Q = float;
+    static_assert(std::is_same<R, float>::value || std::is_same<R, double>::value,
+                  "the quad form carries FP32 or FP64 rays");
+    using Q = R;
     constexpr int NSL = QUAD_SLOTS;
     const DevJob& J = A.job;
-    const SynchConstF& S = A.synchf;
+    const SynchConstT<Q>& S = synch_of<Q>(A.synch, A.synchf);
     const unsigned long long n = *A.count;
     const int lane = threadIdx.x & 31, role = threadIdx.x >> 5;
     if (role == 0) {
         // geodesic warp
-        GeoState<float> g;
+        GeoState<R> g;
         bool has = false, drained = false;
         int32_t pix = 0;
         int64_t slot = 0;
@@ -496,7 +499,7 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
             StepPoint<Q> pt;
             int code = REC_IDLE;
             if (has) {
-                code = geo_step<float, SWEEP, POL, EM>(g, J, pt, nullptr, 0);
+                code = geo_step<R, SWEEP, POL, EM>(g, J, pt, nullptr, 0);
                 if (code != RAY_GOING) has = false;
             } else if (!drained) {
                 while (true) {
@@ -511,7 +514,7 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
                         atomicAdd(A.counters + C_BADIDX, 1ull);
                         continue;
                     }
-                    geo_init<float, POL>(g, J, cam_s, px, pt);
+                    geo_init<R, POL>(g, J, cam_s, px, pt);
                     pix = px;
                     slot = sq;
                     has = true;
@@ -647,34 +650,47 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
             dst[q] = src[q];
     }
     {
-        __shared__ __align__(16) PairRingOf<R, POL> ring;
-        pair_ring_init(ring);
-        if constexpr (std::is_same<R, float>::value) {
-            __shared__ __align__(16) QuadRing<float> qring;
-            quad_ring_init(qring);
-            __syncthreads();
-            const unsigned long long n = *A.count, blocks = gridDim.x;
-            if (n <= blocks * (unsigned long long)A.quad_rays)
-                trace_quads<SWEEP, POL, EM>(A, cam_s, qring);
-            else if (n <= blocks * (unsigned long long)A.pair_rays)
-                trace_pairs<R, SWEEP, POL, EM>(SingleSource{A, cam_s, n}, ring);
-            else
-                trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
-        } else {
-            __syncthreads();
-            const unsigned long long pair_lanes =
-                (unsigned long long)gridDim.x * PairRingOf<R, POL>::NPAIR * 32ull;
-            // FP64: always the warp-pair form.  GB300's FP64 pipe takes a warp instruction per
-            // 64 cycles on one scheduler whatever its ILP and active lanes (about 16 cycles per
-            // SM across the four), so a ray's latency is its warp's FP64 instruction count: the
-            // pair halves it, which shortens the launches whose longest rays finish last, and
-            // the SM-wide rate (the throughput bound) is the same in either form.
-            const unsigned long long n = *A.count;
-            if (n <= pair_lanes || std::is_same<R, double>::value)
-                trace_pairs<R, SWEEP, POL, EM>(SingleSource{A, cam_s, n}, ring);
-            else
-                trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
-        }
+        // The rings of the two split forms share one buffer: the queue length, and so the form,
+        // is uniform over the grid, and only the chosen form's mbarriers are initialised.
+        using PRing = PairRingOf<R, POL>;
+        using QRing = QuadRing<Q>;
+        constexpr bool HAS_QUAD = !std::is_same<R, df>::value;
+        constexpr size_t RING_BYTES =
+            HAS_QUAD && sizeof(QRing) > sizeof(PRing) ? sizeof(QRing) : sizeof(PRing);
+        __shared__ __align__(16) unsigned char rings[RING_BYTES];
+        const unsigned long long n = *A.count, blocks = gridDim.x;
+        const unsigned long long pair_lanes = blocks * PRing::NPAIR * 32ull;
+        // 2: quad form, 1: pair form, 0: one thread per ray.  FP32: by the tuned thresholds.
+        // FP64: the pair form at least.  GB300's FP64 pipe takes a warp instruction per 64 cycles
+        // on one scheduler whatever its ILP and active lanes (about 16 cycles per SM across the
+        // four), so a ray's latency is its slowest warp's FP64 instruction count: the pair halves
+        // it, the quad (emission coefficients of alternate steps on two warps) cuts the transfer
+        // half again, which shortens the launches whose longest rays finish last; the SM-wide
+        // rate (the throughput bound) is the same in every form.  Double-float: the pair form
+        // while the queue fits the grid's pairs.
+        int form;
+        if constexpr (std::is_same<R, float>::value)
+            form = n <= blocks * (unsigned long long)A.quad_rays   ? 2
+                   : n <= blocks * (unsigned long long)A.pair_rays ? 1
+                                                                   : 0;
+        else if constexpr (std::is_same<R, double>::value)
+            form = n <= blocks * (unsigned long long)A.quad64_rays ? 2 : 1;
+        else
+            form = n <= pair_lanes ? 1 : 0;
+        if constexpr (HAS_QUAD)
+            if (form == 2) quad_ring_init(*reinterpret_cast<QRing*>(rings));
+        if (form == 1) pair_ring_init(*reinterpret_cast<PRing*>(rings));
+        __syncthreads();
+        if constexpr (HAS_QUAD)
+            if (form == 2) {
+                trace_quads<R, SWEEP, POL, EM>(A, cam_s, *reinterpret_cast<QRing*>(rings));
+                return;
+            }
+        if (form == 1)
+            trace_pairs<R, SWEEP, POL, EM>(SingleSource{A, cam_s, n},
+                                           *reinterpret_cast<PRing*>(rings));
+        else
+            trace_lanes<R, SWEEP, POL, EM>(A, cam_s);
     }
 }
 
