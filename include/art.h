@@ -93,7 +93,7 @@ typedef struct art_job {
     double step_frac;    /* RK4 step h = step_frac * r */
     double h_min;        /* floor of h */
     double horizon_eps;  /* stop rays at r < (1 + horizon_eps) r_+ */
-    double escape_frac;  /* stop rays at r > escape_frac * r_obs */
+    double escape_frac;  /* stop rays at r > escape_frac * r_obs (at most 1e8 [M]) */
     double disk_w;       /* vertical Gaussian width of the emitter as a fraction of r */
     /* ART_EMIT_SYNCH_DISK: thermal-synchrotron thin disk, n_e = ne0 r^ne_slope
      * exp(-cos^2(theta)/(2 disk_w^2)) [cm^-3], Theta_e = thetae0 r^te_slope, |B| = b0

@@ -229,6 +229,7 @@ static int make_devjob(const art_job* job, DevJob* J)
     if (!(job->step_frac > 0.0 && job->step_frac <= 0.5) || !(job->h_min > 0.0)) return ART_ERR_ARG;
     if (job->max_steps < 1 || !(job->escape_frac > 1.0) || !(job->horizon_eps >= 0.0))
         return ART_ERR_ARG;
+    if (!(job->escape_frac * job->r_obs <= 1e8)) return ART_ERR_ARG;  // the tracers form r^4 in FP32
     if (job->stokes != 1 && job->stokes != 4) return ART_ERR_UNSUPPORTED;
     if (job->subrings < 0 || job->subrings > 4) return ART_ERR_UNSUPPORTED;
     if (job->emission != ART_EMIT_ANALYTIC && job->emission != ART_EMIT_SYNCH_DISK &&

@@ -21,6 +21,7 @@
 #pragma once
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #if defined(__CUDACC__)
 #define ART_HD __host__ __device__ __forceinline__
@@ -119,13 +120,25 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
     R a2z2 = a2 * z2;
     R b = (fmad(y, y, x * x) + z2) - a2;
     R r2 = scale2(b + sqrt(fmad(b, b, scale2(a2z2, 4.f))), 0.5f);
-    R ir = rsqrt(r2);
-    R r = r2 * ir;
-    R ir2 = ir * ir;
     R r4 = r2 * r2;
-    // 1/Q and 1/(r^2 + a^2) from one reciprocal of their product
     const R Qd = r4 + a2z2, ra2 = r2 + a2;
-    const R iP = R(1) / (Qd * ra2);
+    R ir, r, iP;  // 1/r, r and 1/P with P = Q (r^2 + a^2)
+    if constexpr (std::is_same<R, double>::value) {
+        // all three from one reciprocal square root X = 1/(r P) (no division): 1/r = X P,
+        // r = r^2 / r, 1/P = X r.  r^2 P^2 ~ r^14 stays finite for r <= 1e8 (the job's bound).
+        const R P = Qd * ra2;
+        const R X = rsqrt(r2 * P * P);
+        ir = X * P;
+        r = r2 * ir;
+        iP = X * r;
+    } else {
+        // r^14 would leave the single-precision range: a reciprocal square root and a reciprocal
+        ir = rsqrt(r2);
+        r = r2 * ir;
+        iP = R(1) / (Qd * ra2);
+    }
+    R ir2 = ir * ir;
+    // 1/Q and 1/(r^2 + a^2) from the one reciprocal of their product
     R iQ = ra2 * iP;
     R f = scale2(r2, 2.f) * r * iQ;
     R ira2 = Qd * iP;

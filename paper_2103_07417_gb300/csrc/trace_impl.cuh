@@ -148,6 +148,7 @@ template <class R>
 struct GeoState {
     using Q = typename Aux<R>::Q;
     RayState<R> s;
+    RayState<R> k1;  // the geodesic right-hand side at s (CarryRhs kernels)
     R kt;
     Q r, sweep;
     Q f[4];  // polarized rays: parallel-transported reference covector
@@ -204,6 +205,16 @@ __device__ __forceinline__ R phi1(R x)
 // run time by the job) or the fluid grid, whose lookup is kept out of the other kernels' code.
 enum EmitKernel { EM_ANALYTIC = 0, EM_GRID = 1 };
 
+// Kernels whose step runs its four RK4 stages as one rolled loop (the double-float and the
+// polarized analytic-emission kernels: see geo_step) hold the geodesic right-hand side once in
+// their code.  The others evaluate the right-hand side at the end point of each step, where it is
+// both the next step's first stage and the source of the end point's radius (no separate solve of
+// the radius quadratic).
+template <class R, bool POL, int EM>
+struct CarryRhs {
+    static constexpr bool value = !((POL && EM == EM_ANALYTIC) || std::is_same<R, df>::value);
+};
+
 // Emission/absorption/rotation coefficients at a point (J4, K7 as in synch.cuh).
 // edge: set to 1 when the point lies within the FP32 pass's tolerance of a discontinuity of the
 // emission model (left unchanged otherwise).
@@ -227,7 +238,7 @@ __device__ __forceinline__ void coefficients(const RayState<Q>& q, Q r, Q kt, co
 
 // Geodesic part of a ray's start: camera ray of pixel pix; fills the start point for the transfer
 // part's initialisation.
-template <class R, bool POL>
+template <class R, bool POL, int EM>
 __device__ __forceinline__ void geo_init(GeoState<R>& g, const DevJob& J, const Camera& cam,
                                          int32_t pix, StepPoint<typename Aux<R>::Q>& pt)
 {
@@ -256,7 +267,11 @@ __device__ __forceinline__ void geo_init(GeoState<R>& g, const DevJob& J, const 
         }
     }
     pt.q = to_q<Q>(g.s);
-    g.r = ks_radius<Q>(pt.q.x, pt.q.y, pt.q.z, jq<Q>(J.a2, J.f_a2));
+    if constexpr (CarryRhs<R, POL, EM>::value)
+        g.r = Q(geodesic_rhs<R>(g.s, g.kt, jr<R>(J.a, J.f_a, J.f_a_lo),
+                                jr<R>(J.a2, J.f_a2, J.f_a2_lo), g.k1));
+    else
+        g.r = ks_radius<Q>(pt.q.x, pt.q.y, pt.q.z, jq<Q>(J.a2, J.f_a2));
     g.sweep = Q(0);
     g.steps = 0;
     pt.kt = Q(g.kt);
@@ -306,7 +321,7 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J,
                                          const Camera& cam, int32_t pix)
 {
     StepPoint<typename Aux<R>::Q> pt;
-    geo_init<R, POL>(t.g, J, cam, pix, pt);
+    geo_init<R, POL, EM>(t.g, J, cam, pix, pt);
     xfer_init<typename Aux<R>::Q, POL, EM>(t.x, pt, J, S);
     t.status = ART_RAY_CAP;
     t.pix = pix;
@@ -417,7 +432,10 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
     } else {
         RayState<R> k1, k2, k3, k4, y;
         Q d1[4], d2[4], d3[4], d4[4], fy[4];
-        geodesic_rhs<R>(t.s, t.kt, a, a2, k1);
+        if constexpr (CarryRhs<R, POL, EM>::value)
+            k1 = t.k1;  // evaluated at the end of the previous step (or by geo_init)
+        else
+            geodesic_rhs<R>(t.s, t.kt, a, a2, k1);
         if (POL) transport_rhs<Q>(to_q<Q>(t.s), Q(t.kt), t.f, aq, a2q, d1);
         rk4_offset(t.s, hh, k1, y);
         geodesic_rhs<R>(y, t.kt, a, a2, k2);
@@ -447,7 +465,11 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
             for (int m = 0; m < 4; ++m)
                 ds[m] = fmad(Q(2), d3[m], fmad(Q(2), d2[m], d1[m])) + d4[m];
     }
-    const R h6 = h / R(6);
+    R h6;
+    if constexpr (std::is_same<R, double>::value)
+        h6 = h * R(1.0 / 6.0);  // a multiply in place of the FP64 division
+    else
+        h6 = h / R(6);
     const Q ox = Q(t.s.x), oy = Q(t.s.y), oz = Q(t.s.z);
     t.s.x = fmad(h6, ks.x, t.s.x);
     t.s.y = fmad(h6, ks.y, t.s.y);
@@ -474,7 +496,11 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
         // known to be one (these orbiting rays are also the longest of the FP32 pass)
         if (t.sweep >= jq<Q>(J.fp64_sweep, J.f_fp64_sweep)) return RAY_REROUTE;
     }
-    Q rn = ks_radius<Q>(q.x, q.y, q.z, a2q);
+    Q rn;
+    if constexpr (CarryRhs<R, POL, EM>::value)
+        rn = Q(geodesic_rhs<R>(t.s, t.kt, a, a2, t.k1));
+    else
+        rn = ks_radius<Q>(q.x, q.y, q.z, a2q);
     t.r = rn;
     pt.q = q;
     pt.kt = Q(t.kt);

@@ -320,7 +320,7 @@ __device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL>& 
                 int64_t sq;
                 int32_t px, im;
                 if (src.next(sq, px, im)) {
-                    geo_init<R, POL>(g, src.job(im), src.camera(im), px, pt);
+                    geo_init<R, POL, EM>(g, src.job(im), src.camera(im), px, pt);
                     pix = px;
                     img = im;
                     slot = sq;
@@ -514,7 +514,7 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
                         atomicAdd(A.counters + C_BADIDX, 1ull);
                         continue;
                     }
-                    geo_init<R, POL>(g, J, cam_s, px, pt);
+                    geo_init<R, POL, EM>(g, J, cam_s, px, pt);
                     pix = px;
                     slot = sq;
                     has = true;
