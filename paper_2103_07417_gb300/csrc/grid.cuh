@@ -23,6 +23,25 @@
 
 namespace art {
 
+// float -> double on the integer units.  GB300 converts between the two precisions at the FP64
+// rate (a warp instruction per 64 cycles on a scheduler), its integer units issue every cycle,
+// and a sample widens 64 cell values.  For zeros and normal numbers the exponent is rebiased
+// (127 -> 1023) and the significand moved into place: the conversion's exact result.  The other
+// values (subnormal, infinite, NaN) are flagged by widen_special; a sample holding one takes the
+// conversion instruction for all its cells.
+__device__ __forceinline__ double widen(float f)
+{
+    const unsigned u = __float_as_uint(f), au = u & 0x7fffffffu;
+    const unsigned hi = au != 0u ? (au >> 3) + (896u << 20) : 0u;
+    return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(au << 29));
+}
+
+__device__ __forceinline__ unsigned widen_special(float f)
+{
+    const unsigned au = __float_as_uint(f) & 0x7fffffffu;
+    return (unsigned)(au != 0u) & (unsigned)(au - 0x00800000u >= 0x7f000000u);
+}
+
 template <class Q>
 ART_HD void grid_axis_clamped(Q f, int n, int& i0, Q& w)
 {
@@ -84,23 +103,40 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     k0 = ((k0 % n3) + n3) % n3;
     const int k1 = k0 + 1 == n3 ? 0 : k0 + 1;
     Q P[8];
+    // P = sum over the eight cells of weight x value; conv takes a cell value into Q and returns
+    // whether it was one that widen does not cover
+    auto trilinear = [&](auto conv) {
+        unsigned special = 0u;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) P[q] = Q(0);
+        for (int q = 0; q < 8; ++q) P[q] = Q(0);
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const int ii = (c & 1) ? i1 : i0, jj = (c & 2) ? j1 : j0, kk = (c & 4) ? k1 : k0;
-        const Q wt = ((c & 1) ? w1 : Q(1) - w1) * ((c & 2) ? w2 : Q(1) - w2) *
-                     ((c & 4) ? w3 : Q(1) - w3);
-        const float4* cell = S.grid + 2 * (((int64_t)kk * n2 + jj) * n1 + ii);
-        const float4 v0 = __ldg(cell), v1 = __ldg(cell + 1);
-        P[0] = fmad(wt, Q(v0.x), P[0]);
-        P[1] = fmad(wt, Q(v0.y), P[1]);
-        P[2] = fmad(wt, Q(v0.z), P[2]);
-        P[3] = fmad(wt, Q(v0.w), P[3]);
-        P[4] = fmad(wt, Q(v1.x), P[4]);
-        P[5] = fmad(wt, Q(v1.y), P[5]);
-        P[6] = fmad(wt, Q(v1.z), P[6]);
-        P[7] = fmad(wt, Q(v1.w), P[7]);
+        for (int c = 0; c < 8; ++c) {
+            const int ii = (c & 1) ? i1 : i0, jj = (c & 2) ? j1 : j0, kk = (c & 4) ? k1 : k0;
+            const Q wt = ((c & 1) ? w1 : Q(1) - w1) * ((c & 2) ? w2 : Q(1) - w2) *
+                         ((c & 4) ? w3 : Q(1) - w3);
+            const float4* cell = S.grid + 2 * (((int64_t)kk * n2 + jj) * n1 + ii);
+            const float4 v0 = __ldg(cell), v1 = __ldg(cell + 1);
+            P[0] = fmad(wt, conv(v0.x, special), P[0]);
+            P[1] = fmad(wt, conv(v0.y, special), P[1]);
+            P[2] = fmad(wt, conv(v0.z, special), P[2]);
+            P[3] = fmad(wt, conv(v0.w, special), P[3]);
+            P[4] = fmad(wt, conv(v1.x, special), P[4]);
+            P[5] = fmad(wt, conv(v1.y, special), P[5]);
+            P[6] = fmad(wt, conv(v1.z, special), P[6]);
+            P[7] = fmad(wt, conv(v1.w, special), P[7]);
+        }
+        return special;
+    };
+    if constexpr (std::is_same<Q, double>::value) {
+        // integer widening; a sample with a value it does not cover is summed again with the
+        // conversion instruction (the same cells, still in L1)
+        if (trilinear([](float v, unsigned& sp) {
+                sp |= widen_special(v);
+                return widen(v);
+            }))
+            trilinear([](float v, unsigned&) { return (double)v; });
+    } else {
+        trilinear([](float v, unsigned&) { return v; });
     }
     const Q rho = P[0], ug = P[1];
     if (!(rho > Q(0)) || !(ug > Q(0))) return;

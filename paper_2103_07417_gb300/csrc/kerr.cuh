@@ -64,6 +64,24 @@ ART_HD R scale2(R x, float c)
     return x * R(c);
 }
 
+#ifdef __CUDA_ARCH__
+// FP64 on the device: the product with 2^k as integer arithmetic on the exponent field (GB300 issues
+// an FP64 instruction per scheduler every 64 cycles, an integer one every cycle).  Equal to the
+// product for every finite normal x whose product is normal; zeros, infinities and NaNs keep their
+// exponent (only the sign follows c).  Subnormal inputs (not met by the tracer's values) would
+// stay unscaled.
+template <>
+ART_HD double scale2<double>(double x, float c)
+{
+    const int cb = __float_as_int(c);
+    const int k = ((cb >> 23) & 0xff) - 127;  // c = +-2^k, a compile-time constant at every use
+    const int hi = __double2hiint(x);
+    const int e = hi & 0x7ff00000;
+    const int hs = (e != 0 && e != 0x7ff00000) ? hi + k * (1 << 20) : hi;
+    return __hiloint2double(hs ^ (cb & (int)0x80000000), __double2loint(x));
+}
+#endif
+
 // 2 x + c: one fused multiply-add (for double-float: the exact scaling above and one addition).
 template <class R>
 ART_HD R twice_plus(R x, R c)
