@@ -53,11 +53,13 @@ ART_HD void grid_axis_clamped(Q f, int n, int& i0, Q& w)
     w = n > 1 ? f - Q(i) : Q(0);
 }
 
-// Emission of the grid model at one point (J4, K7 as emission_synch).  f nullable.
+// Emission of the grid model at one point (J4, K7 as emission_synch).  f nullable.  ks
+// (nullable): 1/r, F, Lx, Ly, Lz at the point, as the geodesic's right-hand side computed them
+// (spares a division and the Kerr-Schild pieces of ks_point).
 template <class Q>
 __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, const Q* f,
-                                              const DevJob& J, const SynchConstT<Q>& S, Q* J4,
-                                              Q* K7,
+                                              const Q* ks, const DevJob& J,
+                                              const SynchConstT<Q>& S, Q* J4, Q* K7,
                                               int* edge = nullptr)
 {
     for (int i = 0; i < 4; ++i) J4[i] = Q(0);
@@ -66,7 +68,7 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     const Q lr = log(r);
     if (!(lr >= Q(S.g_x1min) && lr <= Q(S.g_x1max))) return;
     const Q a = jq<Q>(J.a, J.f_a), a2 = jq<Q>(J.a2, J.f_a2);
-    const Q ir = Q(1) / r;
+    const Q ir = ks ? ks[0] : Q(1) / r;
     Q ct = s.z * ir;
     ct = ct > Q(1) ? Q(1) : (ct < Q(-1) ? Q(-1) : ct);
     const Q th = acos(ct);
@@ -152,7 +154,15 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
         u[1 + i] = fmad(Jm[i][2], P[4], fmad(Jm[i][1], P[3], Jm[i][0] * P[2]));
         B[1 + i] = fmad(Jm[i][2], P[7], fmad(Jm[i][1], P[6], Jm[i][0] * P[5]));
     }
-    const KSPoint<Q> G = ks_point<Q>(s.x, s.y, s.z, r, ir, a, a2);
+    KSPoint<Q> G;
+    if (ks) {
+        G.F = ks[1];
+        G.Lx = ks[2];
+        G.Ly = ks[3];
+        G.Lz = ks[4];
+    } else {
+        G = ks_point<Q>(s.x, s.y, s.z, r, ir, a, a2);
+    }
     const Q Lu = fmad(G.Lz, u[3], fmad(G.Ly, u[2], G.Lx * u[1]));
     const Q LB = fmad(G.Lz, B[3], fmad(G.Ly, B[2], G.Lx * B[1]));
     const Q uu = fmad(u[3], u[3], fmad(u[2], u[2], u[1] * u[1]));

@@ -129,9 +129,11 @@ ART_HD R ks_radius(R x, R y, R z, R a2)
     return sqrt(r2);
 }
 
-// Hamilton's equations (see the header comment); returns r of the evaluation point.
+// Hamilton's equations (see the header comment); returns r of the evaluation point.  ks
+// (nullable) receives the Kerr-Schild pieces of the point the emission models use: 1/r,
+// F = 2 r^3 / (r^4 + a^2 z^2) and L = (Lx, Ly, Lz).
 template <class R>
-ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
+ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d, R* ks = nullptr)
 {
     const R x = s.x, y = s.y, z = s.z, kx = s.kx, ky = s.ky, kz = s.kz;
     R z2 = z * z;
@@ -181,6 +183,13 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d)
     d.x = fmad(flk, Lx, kx);
     d.y = fmad(flk, Ly, ky);
     d.z = fmad(flk, Lz, kz);
+    if (ks) {
+        ks[0] = ir;
+        ks[1] = f;
+        ks[2] = Lx;
+        ks[3] = Ly;
+        ks[4] = Lz;
+    }
     return r;
 }
 

@@ -183,6 +183,7 @@ struct StepPoint {
     RayState<Q> q;
     Q kt, r, h;
     Q f[4];
+    Q ks[5];  // CarryRhs kernels: 1/r, F, Lx, Ly, Lz at the point (geodesic_rhs)
 };
 
 template <class R>
@@ -217,14 +218,17 @@ struct CarryRhs {
 
 // Emission/absorption/rotation coefficients at a point (J4, K7 as in synch.cuh).
 // edge: set to 1 when the point lies within the FP32 pass's tolerance of a discontinuity of the
-// emission model (left unchanged otherwise).
-template <class Q, bool POL, int EM>
-__device__ __forceinline__ void coefficients(const RayState<Q>& q, Q r, Q kt, const Q* f,
-                                             const DevJob& J, const SynchConstT<Q>& S, Q* J4, Q* K7,
-                                             int& edge)
+// emission model (left unchanged otherwise).  KS: the point carries its Kerr-Schild pieces
+// (StepPoint::ks, from the geodesic's right-hand side there), which the grid model then reuses.
+template <class Q, bool POL, int EM, bool KS>
+__device__ __forceinline__ void coefficients(const StepPoint<Q>& pt, const DevJob& J,
+                                             const SynchConstT<Q>& S, Q* J4, Q* K7, int& edge)
 {
+    const RayState<Q>& q = pt.q;
+    const Q r = pt.r, kt = pt.kt;
+    const Q* f = pt.f;
     if (EM == EM_GRID) {
-        emission_grid<Q>(q, r, kt, POL ? f : nullptr, J, S, J4, K7, &edge);
+        emission_grid<Q>(q, r, kt, POL ? f : nullptr, KS ? pt.ks : nullptr, J, S, J4, K7, &edge);
         return;
     }
     if (J.emission == ART_EMIT_SYNCH_DISK) {
@@ -267,10 +271,12 @@ __device__ __forceinline__ void geo_init(GeoState<R>& g, const DevJob& J, const 
         }
     }
     pt.q = to_q<Q>(g.s);
-    if constexpr (CarryRhs<R, POL, EM>::value)
+    if constexpr (CarryRhs<R, POL, EM>::value) {
+        R kr[5];
         g.r = Q(geodesic_rhs<R>(g.s, g.kt, jr<R>(J.a, J.f_a, J.f_a_lo),
-                                jr<R>(J.a2, J.f_a2, J.f_a2_lo), g.k1));
-    else
+                                jr<R>(J.a2, J.f_a2, J.f_a2_lo), g.k1, kr));
+        for (int m = 0; m < 5; ++m) pt.ks[m] = Q(kr[m]);
+    } else
         g.r = ks_radius<Q>(pt.q.x, pt.q.y, pt.q.z, jq<Q>(J.a2, J.f_a2));
     g.sweep = Q(0);
     g.steps = 0;
@@ -305,13 +311,13 @@ __device__ __forceinline__ void xfer_init_with(XferState<Q>& x, const StepPoint<
 }
 
 // Transfer part of a ray's start: coefficients at the camera point, identity propagator.
-template <class Q, bool POL, int EM>
+template <class Q, bool POL, int EM, bool KS>
 __device__ __forceinline__ void xfer_init(XferState<Q>& x, const StepPoint<Q>& pt, const DevJob& J,
                                           const SynchConstT<Q>& S)
 {
     Q J1[4], K1[7];
     int e1 = 0;
-    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1, e1);
+    coefficients<Q, POL, EM, KS>(pt, J, S, J1, K1, e1);
     xfer_init_with<Q, POL>(x, pt, J1, K1, e1);
 }
 
@@ -322,7 +328,7 @@ __device__ __forceinline__ void ray_init(Tracer<R>& t, const DevJob& J,
 {
     StepPoint<typename Aux<R>::Q> pt;
     geo_init<R, POL, EM>(t.g, J, cam, pix, pt);
-    xfer_init<typename Aux<R>::Q, POL, EM>(t.x, pt, J, S);
+    xfer_init<typename Aux<R>::Q, POL, EM, CarryRhs<R, POL, EM>::value>(t.x, pt, J, S);
     t.status = ART_RAY_CAP;
     t.pix = pix;
 }
@@ -497,9 +503,11 @@ __device__ __forceinline__ int geo_step(GeoState<R>& t, const DevJob& J,
         if (t.sweep >= jq<Q>(J.fp64_sweep, J.f_fp64_sweep)) return RAY_REROUTE;
     }
     Q rn;
-    if constexpr (CarryRhs<R, POL, EM>::value)
-        rn = Q(geodesic_rhs<R>(t.s, t.kt, a, a2, t.k1));
-    else
+    if constexpr (CarryRhs<R, POL, EM>::value) {
+        R kr[5];
+        rn = Q(geodesic_rhs<R>(t.s, t.kt, a, a2, t.k1, kr));
+        for (int m = 0; m < 5; ++m) pt.ks[m] = Q(kr[m]);
+    } else
         rn = ks_radius<Q>(q.x, q.y, q.z, a2q);
     t.r = rn;
     pt.q = q;
@@ -569,13 +577,13 @@ __device__ __forceinline__ void xfer_apply(XferState<Q>& t, const StepPoint<Q>& 
 }
 
 // Transfer part of one step ending at pt: the coefficients there, then xfer_apply.
-template <class Q, bool POL, int EM>
+template <class Q, bool POL, int EM, bool KS>
 __device__ __forceinline__ void xfer_step(XferState<Q>& t, const StepPoint<Q>& pt, const DevJob& J,
                                           const SynchConstT<Q>& S)
 {
     Q J1[4], K1[7];
     int e1 = 0;
-    coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1, e1);
+    coefficients<Q, POL, EM, KS>(pt, J, S, J1, K1, e1);
     xfer_apply<Q, POL>(t, pt, J1, K1, J, e1);
 }
 
@@ -632,7 +640,7 @@ __device__ __forceinline__ bool ray_step(Tracer<R>& t, const DevJob& J,
         return true;
     }
     if (!XportOnGeo<R, POL>::value) xfer_transport<Q>(t.x, pt, stg, 1, J);
-    xfer_step<Q, POL, EM>(t.x, pt, J, S);
+    xfer_step<Q, POL, EM, CarryRhs<R, POL, EM>::value>(t.x, pt, J, S);
     if (st == RAY_GOING) return false;
     t.status = st;
     return true;

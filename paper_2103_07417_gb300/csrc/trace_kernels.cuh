@@ -151,12 +151,16 @@ __device__ __forceinline__ bool pair_wait(uint64_t* bar, uint32_t parity)
     }
 }
 
-// Shared memory of the warp-pair form: the hand-over rings and their mbarriers.  Fields per lane:
-// x y z kx ky kz kt r h f0..f3, then (transport on the transfer half) the NSTG stage values.
+// Fields of an end-point record: x y z kx ky kz kt r h f0..f3, then either the point's Kerr-Schild
+// pieces (StepPoint::ks: CarryRhs kernels) or, when the transfer half transports the covector, the
+// NSTG stage values.
+constexpr int REC_EXTRA = 13, REC_KS = 5;
+
+// Shared memory of the warp-pair form: the hand-over rings and their mbarriers.
 template <class Q, int NF>
 struct PairRing {
     static constexpr int NPAIR = TRACE_BLOCK / 64;
-    static constexpr int STG = NF > 13 ? 13 : 0;  // first stage field (0: none carried)
+    static constexpr int STG = REC_EXTRA;  // first stage field (read only with NF > REC_EXTRA + REC_KS)
     Q v[NPAIR][SPLIT_SLOTS][NF][32];
     int32_t code[NPAIR][SPLIT_SLOTS][32], pix[NPAIR][SPLIT_SLOTS][32], img[NPAIR][SPLIT_SLOTS][32];
     int64_t slot[NPAIR][SPLIT_SLOTS][32];
@@ -287,13 +291,17 @@ struct BatchSource {
 };
 
 // Warp-pair form (the ring's mbarriers initialised and the block synchronised before the call).
-template <class R, bool POL>
-using PairRingOf = PairRing<typename Aux<R>::Q, XportOnGeo<R, POL>::value ? 13 : 13 + NSTG>;
+template <class R, bool POL, int EM>
+using PairRingOf =
+    PairRing<typename Aux<R>::Q, !XportOnGeo<R, POL>::value ? REC_EXTRA + NSTG
+                                 : CarryRhs<R, POL, EM>::value ? REC_EXTRA + REC_KS
+                                                               : REC_EXTRA>;
 
 template <class R, bool SWEEP, bool POL, int EM, class Src>
-__device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL>& sm)
+__device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL, EM>& sm)
 {
     using Q = typename Aux<R>::Q;
+    constexpr bool KS = CarryRhs<R, POL, EM>::value;
     constexpr int NSL = SPLIT_SLOTS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, pr = warp >> 1;
     if ((warp & 1) == 0) {
@@ -314,7 +322,7 @@ __device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL>& 
             int code = REC_IDLE;
             if (has) {
                 code = geo_step<R, SWEEP, POL, EM>(g, src.job(img), pt,
-                                                   &sm.v[pr][sl][PairRingOf<R, POL>::STG][lane], 32);
+                                                   &sm.v[pr][sl][PairRingOf<R, POL, EM>::STG][lane], 32);
                 if (code != RAY_GOING) has = false;
             } else if (!drained) {
                 int64_t sq;
@@ -343,6 +351,8 @@ __device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL>& 
                 v[8 * 32] = pt.h;
                 if (POL)
                     for (int m = 0; m < 4; ++m) v[(9 + m) * 32] = pt.f[m];
+                if constexpr (KS)
+                    for (int m = 0; m < REC_KS; ++m) v[(REC_EXTRA + m) * 32] = pt.ks[m];
             }
             sm.code[pr][sl][lane] = code;
             sm.pix[pr][sl][lane] = pix;
@@ -383,6 +393,8 @@ __device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL>& 
                 pt.h = v[8 * 32];
                 if (POL)
                     for (int m = 0; m < 4; ++m) pt.f[m] = v[(9 + m) * 32];
+                if constexpr (KS)
+                    for (int m = 0; m < REC_KS; ++m) pt.ks[m] = v[(REC_EXTRA + m) * 32];
             }
             if (code == REC_INIT) {
                 pix = sm.pix[pr][sl][lane];
@@ -393,15 +405,15 @@ __device__ __forceinline__ void trace_pairs(const Src& src, PairRingOf<R, POL>& 
             const bool moving = code != REC_IDLE && code != REC_INIT && code != ART_RAY_NAN &&
                                 code != RAY_REROUTE;
             if (!XportOnGeo<R, POL>::value && moving)
-                xfer_transport<Q>(x, pt, &sm.v[pr][sl][PairRingOf<R, POL>::STG][lane], 32, J);
+                xfer_transport<Q>(x, pt, &sm.v[pr][sl][PairRingOf<R, POL, EM>::STG][lane], 32, J);
             __syncwarp();
             pair_arrive(&sm.empty[pr][sl]);
             if (code == REC_INIT) {
-                xfer_init<Q, POL, EM>(x, pt, J, src.template synch<Q>(img));
+                xfer_init<Q, POL, EM, KS>(x, pt, J, src.template synch<Q>(img));
                 steps = 0;
             } else if (code != REC_IDLE) {
                 ++steps;
-                if (moving) xfer_step<Q, POL, EM>(x, pt, J, src.template synch<Q>(img));
+                if (moving) xfer_step<Q, POL, EM, KS>(x, pt, J, src.template synch<Q>(img));
                 if (code != RAY_GOING) src.finish(code, steps, x, pix, slot, img);
             }
             if (last) return;
@@ -432,7 +444,7 @@ constexpr int QUAD_SLOTS = 4;
 
 template <class Q>
 struct QuadRing {
-    Q a[QUAD_SLOTS][13][32];  // end point records: x y z kx ky kz kt r h f0..f3
+    Q a[QUAD_SLOTS][REC_EXTRA + REC_KS][32];  // end point records (fields as in the pair form)
     int32_t code[QUAD_SLOTS][32], pix[QUAD_SLOTS][32];
     int64_t slot[QUAD_SLOTS][32];
     int32_t last[QUAD_SLOTS];
@@ -452,7 +464,7 @@ __device__ __forceinline__ void quad_ring_init(QuadRing<Q>& sm)
         }
 }
 
-template <class Q, bool POL>
+template <class Q, bool POL, bool KS>
 __device__ __forceinline__ void quad_read_point(const QuadRing<Q>& sm, int sl, int lane,
                                                 StepPoint<Q>& pt)
 {
@@ -467,6 +479,8 @@ __device__ __forceinline__ void quad_read_point(const QuadRing<Q>& sm, int sl, i
     pt.h = sm.a[sl][8][lane];
     if (POL)
         for (int m = 0; m < 4; ++m) pt.f[m] = sm.a[sl][9 + m][lane];
+    if (KS)
+        for (int m = 0; m < REC_KS; ++m) pt.ks[m] = sm.a[sl][REC_EXTRA + m][lane];
 }
 
 // Warp-quad form (ring mbarriers initialised and the block synchronised before the call).
@@ -478,6 +492,7 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
                   "the quad form carries FP32 or FP64 rays");
     using Q = R;
     constexpr int NSL = QUAD_SLOTS;
+    constexpr bool KS = CarryRhs<R, POL, EM>::value;
     const DevJob& J = A.job;
     const SynchConstT<Q>& S = synch_of<Q>(A.synch, A.synchf);
     const unsigned long long n = *A.count;
@@ -534,6 +549,8 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
                 sm.a[sl][8][lane] = pt.h;
                 if (POL)
                     for (int m = 0; m < 4; ++m) sm.a[sl][9 + m][lane] = pt.f[m];
+                if (KS)
+                    for (int m = 0; m < REC_KS; ++m) sm.a[sl][REC_EXTRA + m][lane] = pt.ks[m];
             }
             sm.code[sl][lane] = code;
             sm.pix[sl][lane] = pix;
@@ -558,12 +575,12 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
             StepPoint<Q> pt;
             const bool need = code == REC_INIT ||
                               (code != REC_IDLE && code != ART_RAY_NAN && code != RAY_REROUTE);
-            if (need) quad_read_point<Q, POL>(sm, sl, lane, pt);
+            if (need) quad_read_point<Q, POL, KS>(sm, sl, lane, pt);
             __syncwarp();
             pair_arrive(&sm.a_empty[sl]);
             Q J1[4], K1[7];
             int e1 = 0;
-            if (need) coefficients<Q, POL, EM>(pt.q, pt.r, pt.kt, pt.f, J, S, J1, K1, e1);
+            if (need) coefficients<Q, POL, EM, KS>(pt, J, S, J1, K1, e1);
             if (it >= NSL && !__all_sync(0xffffffffu, pair_wait(&sm.c_empty[sl], ph ^ 1u))) {
                 if (lane == 0) atomicAdd(A.counters + C_SYNCERR, 1ull);
                 return;
@@ -596,7 +613,7 @@ __device__ __forceinline__ void trace_quads(const TraceArgs& A, const Camera& ca
             const bool moving = code != REC_IDLE && code != REC_INIT && code != ART_RAY_NAN &&
                                 code != RAY_REROUTE;
             StepPoint<Q> pt;
-            if (code == REC_INIT || moving) quad_read_point<Q, POL>(sm, sl, lane, pt);
+            if (code == REC_INIT || moving) quad_read_point<Q, POL, false>(sm, sl, lane, pt);
             if (code == REC_INIT) {
                 pix = sm.pix[sl][lane];
                 slot = sm.slot[sl][lane];
@@ -652,7 +669,7 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_kernel(TraceArgs A)
     {
         // The rings of the two split forms share one buffer: the queue length, and so the form,
         // is uniform over the grid, and only the chosen form's mbarriers are initialised.
-        using PRing = PairRingOf<R, POL>;
+        using PRing = PairRingOf<R, POL, EM>;
         using QRing = QuadRing<Q>;
         constexpr bool HAS_QUAD = !std::is_same<R, df>::value;
         constexpr size_t RING_BYTES =
@@ -701,10 +718,10 @@ __global__ void __launch_bounds__(TRACE_BLOCK) trace_batch_kernel(BatchTraceArgs
     if constexpr (std::is_same<R, df>::value) {
         // the double-float re-trace holds few rays (the near-critical ones of the whole batch):
         // the warp-pair form whenever the queue fits the grid's pairs, as for a single image
-        __shared__ __align__(16) PairRingOf<R, POL> ring;
+        __shared__ __align__(16) PairRingOf<R, POL, EM> ring;
         pair_ring_init(ring);
         __syncthreads();
-        if (n <= (unsigned long long)gridDim.x * PairRingOf<R, POL>::NPAIR * 32ull) {
+        if (n <= (unsigned long long)gridDim.x * PairRingOf<R, POL, EM>::NPAIR * 32ull) {
             trace_pairs<R, SWEEP, POL, EM>(BatchSource{A, n}, ring);
             return;
         }
