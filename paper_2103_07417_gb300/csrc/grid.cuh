@@ -194,8 +194,22 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     if (b2 > Q(S.g_sigma_cut) * rho) return;
     const Q pg = Q(S.g_gm1) * ug, pm = Q(0.5) * b2;
     const Q pg2 = pg * pg, pm2 = pm * pm;
-    const Q trat = fmad(Q(S.g_r_high), pg2, Q(S.g_r_low) * pm2) / (pg2 + pm2);
-    const Q Th = Q(S.g_th_unit) * ug / (rho * (Q(1) + trat));
+    Q Th, iTh;
+    if constexpr (std::is_same<Q, double>::value) {
+        // Theta_e = nm / dn and its reciprocal from one division: with s2 = pg^2 + pm^2,
+        // nm = th_unit u s2, dn = rho (s2 + r_high pg^2 + r_low pm^2) (T_i/T_e = (dn/rho - s2)/s2)
+        const Q s2 = pg2 + pm2;
+        const Q nm = Q(S.g_th_unit) * ug * s2;
+        const Q dn = rho * (s2 + fmad(Q(S.g_r_high), pg2, Q(S.g_r_low) * pm2));
+        const Q inv = Q(1) / (nm * dn);
+        Th = nm * nm * inv;
+        iTh = dn * dn * inv;
+    } else {
+        // (single precision: nm dn can leave the range; its divisions are cheap)
+        const Q trat = fmad(Q(S.g_r_high), pg2, Q(S.g_r_low) * pm2) / (pg2 + pm2);
+        Th = Q(S.g_th_unit) * ug / (rho * (Q(1) + trat));
+        iTh = Q(1) / Th;
+    }
     const Q ne = Q(S.g_ne_unit) * rho;
     const Q ib = rsqrt(b2);
     const Q bm = b2 * ib;
@@ -204,7 +218,7 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     for (int m = 0; m < 4; ++m) b[m] *= ib;
     const Q nu = fmad(s.kz, u[3], fmad(s.ky, u[2], fmad(s.kx, u[1], kt * u[0])));
     if (!(nu > Q(0))) return;
-    synch_coeffs<Q>(G, s, kt, u, b, nu, ne, Th, Bm, f, S, J4, K7);
+    synch_coeffs<Q>(G, s, kt, u, b, nu, ne, Th, iTh, Bm, f, S, J4, K7);
 }
 
 }  // namespace art

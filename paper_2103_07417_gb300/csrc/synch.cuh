@@ -170,21 +170,21 @@ ART_HD Q det4(const Q* A, const Q* B, const Q* C, const Q* D)
 }
 
 // Thermal-synchrotron coefficients of a fluid element (velocity u, unit field direction b in its
-// frame, density ne [cm^-3], temperature Th, field Bm [G]) seen by the ray with covariant k
-// (kt, s.k) and fluid-frame frequency ratio nu = k.u > 0; f (nullable) is the transported
-// covector.  J4, K7 in code units, in the (e_N, e_E) basis of f.
+// frame, density ne [cm^-3], temperature Th and its reciprocal iTh, field Bm [G]) seen by the ray
+// with covariant k (kt, s.k) and fluid-frame frequency ratio nu = k.u > 0; f (nullable) is the
+// transported covector.  J4, K7 in code units, in the (e_N, e_E) basis of f.
 template <class Q>
 ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const Q* u, const Q* b,
-                         Q nu, Q ne, Q Th, Q Bm, const Q* f, const SynchConstT<Q>& S, Q* J4,
-                         Q* K7)
+                         Q nu, Q ne, Q Th, Q iTh, Q Bm, const Q* f, const SynchConstT<Q>& S,
+                         Q* J4, Q* K7)
 {
     Q kc[4] = {kt, s.kx, s.ky, s.kz}, ku[4];
     G.raise(kc, ku);
-    const Q inu = Q(1) / nu;
+    // unit propagation direction in the fluid frame: -(k + nu u)/|k + nu u| (nu > 0; the
+    // integrated k is null only to the truncation error)
     Q d[4];
-    for (int m = 0; m < 4; ++m) d[m] = fmad(-ku[m], inu, -u[m]);
-    // unit propagation direction (the integrated k is null only to the truncation error)
-    Q dn = rsqrt(G.dot(d, d));
+    for (int m = 0; m < 4; ++m) d[m] = fmad(nu, u[m], ku[m]);
+    Q dn = -rsqrt(G.dot(d, d));
     for (int m = 0; m < 4; ++m) d[m] *= dn;
     Q cth = G.dot(d, b);
     cth = cth > Q(1) ? Q(1) : (cth < Q(-1) ? Q(-1) : cth);
@@ -192,14 +192,19 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
     Q sth = sqrt(sth2);
     // coefficients in the E-vector frame; K_n e^x keeps 1/K_2 finite, e^(x - X^1/3) recombines
     const Q lTh = log(Th);
-    Q x = Q(1) / Th, K0, K1, K2;
+    Q x = iTh, K0, K1, K2;
     bessel_k012_scaled<Q>(x, Th, -lTh, K0, K1, K2);
+    // 1/nu, 1/nu_s and 1/K2 from one division
+    const bool emits = sth > Q(1e-12);
+    const Q nus = emits ? Q(2.0 / 9.0) * Q(S.CB) * Bm * Th * Th * sth : Q(1);
+    const Q nuK2 = nu * K2;
+    const Q idv = Q(1) / (nuK2 * nus);
+    const Q inu = (nus * K2) * idv, inus = nuK2 * idv, iK2 = (nu * nus) * idv;
     Q jI = Q(0), jQ = Q(0);
-    if (sth > Q(1e-12)) {
-        Q nus = Q(2.0 / 9.0) * Q(S.CB) * Bm * Th * Th * sth;
-        Q X = Q(S.nu_obs) * nu / nus;
+    if (emits) {
+        Q X = Q(S.nu_obs) * nu * inus;
         Q x3 = cbrt(X), x6 = sqrt(x3), x2 = x3 * x6;  // X^1/3, X^1/6, X^1/2
-        Q pre = Q(S.LCj) * ne * nus * exp(x - x3) * (inu * inu) / K2;
+        Q pre = Q(S.LCj) * ne * nus * exp(x - x3) * (inu * inu) * iK2;
         Q t96 = exp(Q(0.96) * lTh);
         Q q = fmad(Q(7), t96, Q(35)) / fmad(Q(10), t96, Q(75));
         const Q k1112 = Q(1.8877486253633868);  // 2^(11/12)
@@ -211,7 +216,6 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
     J4[0] = jI;
     K7[0] = jI * kir;
     if (!f) return;
-    const Q iK2 = Q(1) / K2;
     Q rV = Q(S.LCV) * ne * Bm * cth * inu * (K0 * iK2);
     Q rQ = Q(S.LCQ) * ne * Bm * Bm * sth2 * (inu * inu) * fmad(Q(6), Th, K1 * iK2);
     // polarization basis from the transported covector
@@ -227,8 +231,9 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
     Q c2 = Q(1), s2 = Q(0);
     if (bp2 > Q(0)) {
         // E-vector at angle chi from north: cos chi = -bE/|b_perp|, sin chi = bN/|b_perp|
-        c2 = fmad(bE, bE, -(bN * bN)) / bp2;
-        s2 = Q(-2) * bE * bN / bp2;
+        const Q ibp2 = Q(1) / bp2;
+        c2 = fmad(bE, bE, -(bN * bN)) * ibp2;
+        s2 = Q(-2) * bE * bN * ibp2;
     }
     J4[1] = jQ * c2;
     J4[2] = jQ * s2;
@@ -288,7 +293,7 @@ ART_HD void emission_synch(const RayState<Q>& s, Q r, Q kt, const Q* f, const De
     Q nz = Q(1) / sqrt(G.dot(ez, ez));
     Q b[4];
     for (int m = 0; m < 4; ++m) b[m] = fmad(Q(S.bz) * nz, ez[m], ephi[m]) * Q(S.bnorm);
-    synch_coeffs<Q>(G, s, kt, u, b, nu, ne, Th, Bm, f, S, J4, K7);
+    synch_coeffs<Q>(G, s, kt, u, b, nu, ne, Th, Q(1) / Th, Bm, f, S, J4, K7);
 }
 
 // Parallel transport of the covector f along the geodesic (outgoing Kerr-Schild form):
