@@ -683,6 +683,12 @@ def main():
     args = parse()
     desc, fn = W.BENCH_WORKLOADS[args.workload]
     params = fn(precision=args.precision)
+    band_default = params.get("crit_band", 0.0)
+    if args.precision == "mixed_exact":
+        # exact decisions trace the band's photon-ring rays in FP32 and double-float with the base
+        # level and still need their stencils' FP64 values at their own level: the render is
+        # faster without the band (the variant with it is reported in paths)
+        params["crit_band"] = 0.0
     if args.impl == "reference":
         return run_reference(args, params, desc)
 
@@ -824,6 +830,15 @@ def main():
             "rays_per_s": stp["rays_traced"] * 3 / tp,
             "geodesic_steps_per_s": stp["steps"] * 3 / tp, "ms_per_step": 1000 * tp / 3,
             "rays_high_precision": stp["rays_fp64"]}
+    elif band_default > 0.0:
+        # the same precision with the workload's near-critical band (same image)
+        jb = art.make_job(**{**params, "crit_band": band_default})
+        stp = ctx.art_render(jb, img, mask, stats=True)
+        tp = timed(3, jb)
+        paths[args.precision + "_with_band"] = {
+            "rays_per_s": stp["rays_traced"] * 3 / tp,
+            "geodesic_steps_per_s": stp["steps"] * 3 / tp, "ms_per_step": 1000 * tp / 3,
+            "rays_high_precision": stp["rays_fp64"], "crit_band": band_default}
     # the same render replayed from a CUDA graph (one capture of the whole level loop)
     if not params.get("proposal", 0):
         ctx.art_graph_render(job, img, mask)
@@ -1058,6 +1073,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": desc, "name": args.workload, "image": f"{nx}x{ny}",
                            "precision": args.precision, "rays_per_step": rays, "tune": tune,
+                           "crit_band": params.get("crit_band", 0.0),
                            "adaptive_ray_fraction": rays / (nx * ny),
                            "l2": "flushed (512 MB write) before every step, outside the timed "
                                  "region", "parallelism": f"replicas x{world}"},
