@@ -85,31 +85,35 @@ inline SynchConstF synch_to_float(const SynchConst& d)
     return f;
 }
 
-// K_0, K_1, K_2 scaled by e^x (K_n(x) e^x), so that FP32 stays finite for cold plasma (large x).
 template <class Q>
 ART_HD Q horner7(Q t, Q c0, Q c1, Q c2, Q c3, Q c4, Q c5, Q c6)
 {
     return fmad(t, fmad(t, fmad(t, fmad(t, fmad(t, fmad(t, c6, c5), c4), c3), c2), c1), c0);
 }
 
+// K_0, K_1, K_2 (the polynomials of Abramowitz & Stegun 9.8.1-9.8.8).  For x > 2 they are returned
+// scaled by e^x (K_n(x) e^x, so that FP32 stays finite for cold plasma, large x) and the function
+// returns true; for x <= 2 unscaled (false), which spares the exponential there: the caller's
+// e^-X^1/3 / K_2 takes the factor e^x exactly when the K_n carry it.
 // ix = 1/x and lx = log(x) are passed in (the caller has them), which spares divisions and a
 // logarithm on GB300's FP64 pipe.
 template <class Q>
-ART_HD void bessel_k012_scaled(Q x, Q ix, Q lx, Q& K0, Q& K1, Q& K2)
+ART_HD bool bessel_k012(Q x, Q ix, Q lx, Q& K0, Q& K1, Q& K2)
 {
-    if (x <= Q(2)) {
+    const bool scaled = x > Q(2);
+    if (!scaled) {
         Q t = x * Q(1.0 / 3.75), t2 = t * t;
         Q i0 = horner7<Q>(t2, Q(1), Q(3.5156229), Q(3.0899424), Q(1.2067492), Q(0.2659732),
                           Q(0.0360768), Q(0.0045813));
         Q i1 = x * horner7<Q>(t2, Q(0.5), Q(0.87890594), Q(0.51498869), Q(0.15084934),
                               Q(0.02658733), Q(0.00301532), Q(0.00032411));
-        Q y = Q(0.25) * x * x, lg = lx - Q(0.69314718055994530942), ex = exp(x);
-        K0 = ex * fmad(-lg, i0, horner7<Q>(y, Q(-0.57721566), Q(0.42278420), Q(0.23069756),
-                                           Q(0.03488590), Q(0.00262698), Q(0.00010750),
-                                           Q(0.0000074)));
-        K1 = ex * fmad(lg, i1, ix * horner7<Q>(y, Q(1), Q(0.15443144), Q(-0.67278579),
-                                                       Q(-0.18156897), Q(-0.01919402),
-                                                       Q(-0.00110404), Q(-0.00004686)));
+        Q y = Q(0.25) * x * x, lg = lx - Q(0.69314718055994530942);
+        K0 = fmad(-lg, i0, horner7<Q>(y, Q(-0.57721566), Q(0.42278420), Q(0.23069756),
+                                      Q(0.03488590), Q(0.00262698), Q(0.00010750),
+                                      Q(0.0000074)));
+        K1 = fmad(lg, i1, ix * horner7<Q>(y, Q(1), Q(0.15443144), Q(-0.67278579),
+                                                  Q(-0.18156897), Q(-0.01919402),
+                                                  Q(-0.00110404), Q(-0.00004686)));
     } else {
         Q y = Q(2) * ix, pre = sqrt(ix);
         K0 = pre * horner7<Q>(y, Q(1.25331414), Q(-0.07832358), Q(0.02189568), Q(-0.01062446),
@@ -118,6 +122,7 @@ ART_HD void bessel_k012_scaled(Q x, Q ix, Q lx, Q& K0, Q& K1, Q& K2)
                               Q(-0.00780353), Q(0.00325614), Q(-0.00068245));
     }
     K2 = fmad(Q(2), K1 * ix, K0);
+    return scaled;
 }
 
 // Minkowski + Kerr-Schild pieces at a point: F = 2 r^3 / (r^4 + a^2 z^2), L (outgoing l = (1,-L)).
@@ -190,10 +195,11 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
     cth = cth > Q(1) ? Q(1) : (cth < Q(-1) ? Q(-1) : cth);
     Q sth2 = fmad(-cth, cth, Q(1));
     Q sth = sqrt(sth2);
-    // coefficients in the E-vector frame; K_n e^x keeps 1/K_2 finite, e^(x - X^1/3) recombines
+    // coefficients in the E-vector frame; K_n e^x keeps 1/K_2 finite for large x, where
+    // e^(x - X^1/3) recombines (bessel_k012)
     const Q lTh = log(Th);
     Q x = iTh, K0, K1, K2;
-    bessel_k012_scaled<Q>(x, Th, -lTh, K0, K1, K2);
+    const bool kscaled = bessel_k012<Q>(x, Th, -lTh, K0, K1, K2);
     // 1/nu, 1/nu_s and 1/K2 from one division
     const bool emits = sth > Q(1e-12);
     const Q nus = emits ? Q(2.0 / 9.0) * Q(S.CB) * Bm * Th * Th * sth : Q(1);
@@ -204,7 +210,7 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
     if (emits) {
         Q X = Q(S.nu_obs) * nu * inus;
         Q x3 = cbrt(X), x6 = sqrt(x3), x2 = x3 * x6;  // X^1/3, X^1/6, X^1/2
-        Q pre = Q(S.LCj) * ne * nus * exp(x - x3) * (inu * inu) * iK2;
+        Q pre = Q(S.LCj) * ne * nus * exp(kscaled ? x - x3 : -x3) * (inu * inu) * iK2;
         Q t96 = exp(Q(0.96) * lTh);
         Q q = fmad(Q(7), t96, Q(35)) / fmad(Q(10), t96, Q(75));
         const Q k1112 = Q(1.8877486253633868);  // 2^(11/12)
