@@ -94,7 +94,7 @@ def test_grid_polarized_faraday_thick_fp64(ctx, snap):
     assert np.abs(g[:, 1:] - ref[:, 1:]).max() <= 2e-3 * ref[:, 0].max()
 
 
-def test_grid_subrings_fp64_matches_oracle(ctx, snap):
+def test_grid_subrings_fp64_matches_oracle(ctx, snap, near_critical):
     """Subring planes n = 0, 1, 2 of the snapshot image (face-on, the torus lensed into rings)."""
     params = {**W.grmhd_8193(n0x=17, n0y=17, levels=1, fov=30.0, subrings=3, incl_deg=163.0),
               "precision": "fp64"}
@@ -103,7 +103,8 @@ def test_grid_subrings_fp64_matches_oracle(ctx, snap):
     lim = 1e-6 * np.maximum(I, 1e-6 * I.max())
     assert (np.abs(g - ref) <= lim[:, None]).all()
     assert ref[:, 1].max() > 1e-3 * ref[:, 0].max()      # the n = 1 ring is present
-    assert (aux["nturn"].cpu().numpy() == info["nturn"]).mean() > 0.999
+    ok = ~near_critical(params["a"], info)
+    assert (aux["nturn"].cpu().numpy()[ok] == info["nturn"][ok]).all()
 
 
 def test_grid_render_fp64_matches_oracle(ctx, snap):

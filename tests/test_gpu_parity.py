@@ -5,8 +5,9 @@ Tolerances (the FP64 path computes the same discretisation in a different operat
   - traced intensities: |dI| <= 1e-6 max(|I|, 1e-6 I_peak) per pixel;
   - refinement on identical inputs: masks identical and interpolants bit-identical, except points
     whose estimate lies within 1e-9 of the tolerance;
-  - full renders: masks may differ only where the oracle's estimate is within 1e-4 (relative) of
-    the tolerance; all other pixels within the intensity tolerance.
+  - full renders: masks may differ only where the oracle's estimate is within 1e-9 (relative) of
+    the tolerance, on at most 2 points; all other pixels within the intensity tolerance;
+  - ray status and RK4 step counts equal on every ray off the near-critical band.
 """
 import numpy as np
 import pytest
@@ -55,7 +56,7 @@ TRACE_CASES = [
 
 
 @pytest.mark.parametrize("name,params", TRACE_CASES, ids=[c[0] for c in TRACE_CASES])
-def test_trace_pixels_fp64_matches_oracle(ctx, name, params):
+def test_trace_pixels_fp64_matches_oracle(ctx, name, params, near_critical):
     art = _art()
     job = art.make_job(**params)
     nx, ny = art.art_image_size(job)
@@ -68,9 +69,13 @@ def test_trace_pixels_fp64_matches_oracle(ctx, name, params):
     assert bad.sum() == 0, (name, np.flatnonzero(bad)[:10])
     st = aux["status"].cpu().numpy()
     steps = aux["steps"].cpu().numpy()
-    assert (st == info["status"]).mean() > 0.999
-    same = st == info["status"]
-    assert (steps[same] == info["steps"][same]).mean() > 0.999
+    # status and RK4 steps equal on every ray off the near-critical band (there the photon
+    # shell's instability amplifies the two programs' rounding differences)
+    nc = near_critical(params["a"], info)
+    ok = ~nc
+    print(name, "near-critical rays", int(nc.sum()), "of", len(nc))
+    assert (st[ok] == info["status"][ok]).all(), np.flatnonzero(ok & (st != info["status"]))[:10]
+    assert (steps[ok] == info["steps"][ok]).all(), np.flatnonzero(ok & (steps != info["steps"]))[:10]
     assert np.all(np.isin(st, [art.RAY_ESCAPED, art.RAY_CAPTURED]))
 
 

@@ -266,3 +266,21 @@ def test_keplerian_redshift_schwarzschild():
             expect = (1 - r ** -1.5 * L) / np.sqrt(1 - 3 / r)
             assert nu == pytest.approx(expect, rel=1e-13)
             assert J == pytest.approx(r ** -2 / nu ** 2, rel=1e-13)
+
+
+@pytest.mark.parametrize("a", [0.0, 0.5, 0.94, -0.7])
+def test_near_critical_distance_vanishes_on_bardeens_curve(a):
+    """The tests' near-critical flag (conftest.crit_distance): zero at the constants of every
+    spherical photon orbit (Bardeen 1973), clearly positive for a photon far from the shell."""
+    from conftest import crit_distance
+    aa = abs(a) if a != 0.0 else 0.0
+    r_pro = 2 * (1 + np.cos(2 / 3 * np.arccos(-aa)))
+    r_ret = 2 * (1 + np.cos(2 / 3 * np.arccos(aa)))
+    if a == 0.0:
+        lam = np.array([np.sqrt(27.0), 0.0, -np.sqrt(27.0)])
+        eta = 27.0 - lam ** 2
+    else:
+        rt = np.linspace(r_pro + 1e-3, r_ret - 1e-3, 7)
+        lam, eta = _bardeen(a, rt)
+    assert (crit_distance(a, lam, eta, samples=200001) < 1e-6).all()
+    assert (crit_distance(a, np.array([0.0, 1.0]), np.array([0.0, 1.0])) > 0.03).all()

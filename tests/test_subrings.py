@@ -100,7 +100,7 @@ def test_subring_planes_sum_to_total():
     W.schwarzschild_129(a=0.94, incl_deg=17.0, disk_w=0.05, n0x=13, n0y=13, levels=2, subrings=3),
     W.kerr_disk_2049(n0x=11, n0y=11, levels=1, fov=24.0, subrings=2),
 ], ids=["analytic_kerr_subrings3", "kerr_disk_pol_subrings2"])
-def test_subring_planes_match_oracle_gpu(params):
+def test_subring_planes_match_oracle_gpu(params, near_critical):
     torch = pytest.importorskip("torch")
     from paper_2103_07417_gb300 import art
     ctx = art.Context(0)
@@ -114,7 +114,8 @@ def test_subring_planes_match_oracle_gpu(params):
     I = ref.reshape(len(pix), -1, params["stokes"])[:, :, 0].sum(axis=1)
     lim = 2e-6 * np.maximum(I, 1e-6 * I.max())
     assert (np.abs(g - ref) <= lim[:, None]).all()
-    assert (aux["nturn"].cpu().numpy() == info["nturn"]).mean() > 0.999
+    ok = ~near_critical(params["a"], info)
+    assert (aux["nturn"].cpu().numpy()[ok] == info["nturn"][ok]).all()
     ctx.close()
 
 
