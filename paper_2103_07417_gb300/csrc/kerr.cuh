@@ -157,29 +157,29 @@ ART_HD R geodesic_rhs(const RayState<R>& s, R kt, R a, R a2, RayState<R>& d, R* 
         r = r2 * ir;
         iP = R(1) / (Qd * ra2);
     }
-    R ir2 = ir * ir;
     // 1/Q and 1/(r^2 + a^2) from the one reciprocal of their product
     R iQ = ra2 * iP;
-    R f = scale2(r2, 2.f) * r * iQ;
+    R u = r * iQ;
+    R rs = r2 * u;            // r^3 / Q = r / Sigma, Sigma = r^2 + a^2 z^2 / r^2 = Q / r^2
+    R f = scale2(rs, 2.f);    // 2 r^3 / Q
     R ira2 = Qd * iP;
     R Lx = fmad(r, x, -(a * y)) * ira2;
     R Ly = fmad(r, y, a * x) * ira2;
     R Lz = z * ir;
     R Lkxy = fmad(Ly, ky, Lx * kx);
     R lk = -kt - fmad(Lz, kz, Lkxy);
-    R iSig = r2 * iQ;  // Sigma = r^2 + a^2 z^2 / r^2 = Q / r^2
-    R rs = r * iSig;
-    R drx = x * rs, dry = y * rs, drz = z * (r2 + a2) * ir * iSig;
+    // grad r = (x r / Sigma, y r / Sigma, z (r^2 + a^2) / (r Sigma))
+    R drx = x * rs, dry = y * rs, drz = (z * ra2) * u;
     R B = f * ir * fmad(scale2(r4, -4.f), iQ, R(3));
-    R A = fmad(fmad(scale2(r, -2.f), Lkxy, fmad(y, ky, x * kx)), ira2, -(kz * z * ir2));
+    R Tz = kz * ir;
+    R A = fmad(fmad(scale2(r, -2.f), Lkxy, fmad(y, ky, x * kx)), ira2, -(Lz * Tz));
     R flk = f * lk;
     R C = fmad(scale2(B, 0.5f) * lk, lk, -(flk * A));
     R Tx = fmad(r, kx, a * ky) * ira2;
     R Ty = fmad(r, ky, -(a * kx)) * ira2;
-    R Tz = kz * ir;
     d.kx = fmad(C, drx, -(flk * Tx));
     d.ky = fmad(C, dry, -(flk * Ty));
-    d.kz = fmad(C, drz, -(flk * Tz)) - flk * lk * a2 * z * iQ;
+    d.kz = fmad(-(flk * lk), (a2 * z) * iQ, fmad(C, drz, -(flk * Tz)));
     d.x = fmad(flk, Lx, kx);
     d.y = fmad(flk, Ly, ky);
     d.z = fmad(flk, Lz, kz);
