@@ -196,10 +196,15 @@ struct Tracer {
     int64_t slot;  // queue position
 };
 
-template <class R>
-__device__ __forceinline__ R phi1(R x)
+// A float that is zero or normal (a radius) in the arithmetic Q (FP64: widened on the integer
+// units, grid.cuh).
+template <class Q>
+__device__ __forceinline__ Q from_float(float v)
 {
-    return x > R(1e-8) ? -expm1(-x) / x : R(1) - R(0.5) * x;
+    if constexpr (std::is_same<Q, double>::value)
+        return widen(v);
+    else
+        return Q(v);
 }
 
 // Emission models as a compile-time choice of the trace kernels: the analytic models (selected at
@@ -565,15 +570,26 @@ __device__ __forceinline__ void xfer_apply(XferState<Q>& t, const StepPoint<Q>& 
     } else {
         Q Jb = Q(0.5) * (t.J0[0] + J1[0]), Ab = Q(0.5) * (t.K0[0] + K1[0]);
         Q dtau = Ab * hq;
-        Q dI = t.T * Jb * hq * phi1<Q>(dtau);
+        // slab of constant coefficients: dI = T J h (1 - e^-dtau)/dtau, T <- T e^-dtau, both from
+        // one expm1 (e^-dtau = 1 + expm1(-dtau), accurate where 1 - e^-dtau would cancel)
+        Q ph = Q(1) - Q(0.5) * dtau, em1 = Q(0);
+        if (dtau > Q(1e-8)) {
+            em1 = expm1(-dtau);
+            ph = -em1 / dtau;
+        } else if (Ab != Q(0)) {
+            em1 = -dtau * ph;
+        }
+        Q dI = t.T * Jb * hq * ph;
 #pragma unroll
         for (int c = 0; c < 4; ++c)
             if (c == sub) t.acc[c] += dI;
-        if (Ab != Q(0)) t.T *= exp(-dtau);
+        if (Ab != Q(0)) t.T = fmad(t.T, em1, t.T);
     }
     for (int i = 0; i < 4; ++i) t.J0[i] = J1[i];
     for (int i = 0; i < 7; ++i) t.K0[i] = K1[i];
-    if (float(rn) < t.min_r) t.min_r = float(rn);
+    // the smallest radius as a float: compared in Q, converted only when it changes (a float
+    // rounds monotonically, so the result is the smallest float(r))
+    if (rn < from_float<Q>(t.min_r)) t.min_r = float(rn);
 }
 
 // Transfer part of one step ending at pt: the coefficients there, then xfer_apply.
