@@ -65,7 +65,7 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
     for (int i = 0; i < 4; ++i) J4[i] = Q(0);
     for (int i = 0; i < 7; ++i) K7[i] = Q(0);
     if (r < jq<Q>(J.r_in_stop, J.f_r_in_stop)) return;
-    const Q lr = log(r);
+    const Q lr = log_q<Q>(r);
     if (!(lr >= Q(S.g_x1min) && lr <= Q(S.g_x1max))) return;
     const Q a = jq<Q>(J.a, J.f_a), a2 = jq<Q>(J.a2, J.f_a2);
     const Q ir = ks ? ks[0] : Q(1) / r;

@@ -28,6 +28,7 @@
 #include <cstdint>
 
 #include "kerr.cuh"
+#include "fmath64.cuh"
 
 namespace art {
 
@@ -197,7 +198,7 @@ ART_HD void synch_coeffs(const KSPoint<Q>& G, const RayState<Q>& s, Q kt, const 
     Q sth = sqrt(sth2);
     // coefficients in the E-vector frame; K_n e^x keeps 1/K_2 finite for large x, where
     // e^(x - X^1/3) recombines (bessel_k012)
-    const Q lTh = log(Th);
+    const Q lTh = log_q<Q>(Th);
     Q x = iTh, K0, K1, K2;
     const bool kscaled = bessel_k012<Q>(x, Th, -lTh, K0, K1, K2);
     // 1/nu, 1/nu_s and 1/K2 from one division
