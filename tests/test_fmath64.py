@@ -69,3 +69,12 @@ def test_log_fp64_within_one_ulp(tmp_path):
     worst, special = float(out[0]), int(out[1])
     assert worst <= 1.1, worst
     assert special == 1
+
+
+def test_log_table_is_the_generators_output():
+    """log_table.cuh is exactly what gen_log_table.py writes (60-digit decimal logarithms)."""
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(CSRC, "gen_log_table.py")], check=True,
+                         capture_output=True, text=True).stdout
+    with open(os.path.join(CSRC, "log_table.cuh")) as f:
+        assert f.read() == out
