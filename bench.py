@@ -27,22 +27,24 @@ from paper_2103_07417_gb300 import workloads as W  # noqa: E402
 
 # Algorithmic FLOPs per RK4 step of the trace kernel, counting +, -, *, /, sqrt, rsqrt and exp
 # as one each (an FMA counts 2): 4 Hamiltonian right-hand sides of 97 (388), the RK4 stage and
-# update arithmetic for 6 variables (81), the new point's radius (15), the Keplerian emissivity
-# (44), the polar-turn test (11) and the transfer segment (11); the FP32 pass of the mixed path
-# adds the swept-angle accumulation (28).
-# The double-float re-trace counts the same 550 algorithmic flops per step (each carried out as
-# a double-float operation of several FP32 instructions).
-FLOPS_PER_STEP = {"trace_fp64": 550, "trace_fp32": 578, "trace_df": 550}
+# update arithmetic for 6 variables (81), the Keplerian emissivity (44), the polar-turn test (11)
+# and the transfer segment (11).  The FP32 and FP64 kernels take the end point's radius from the
+# right-hand side there, which is the next step's first stage; the double-float kernel (one rolled
+# loop of stages) solves the radius quadratic separately (15 more).  The FP32 pass of the mixed
+# path adds the swept-angle accumulation (28).
+FLOPS_PER_STEP = {"trace_fp64": 535, "trace_fp32": 563, "trace_df": 550}
 # Polarized synchrotron steps, counted from the kernel's formulas (+-10 %): the geodesic (495),
 # parallel transport of the polarization covector at the 4 RK4 stages plus its update (1332), the
 # synchrotron coefficients in the fluid frame (590) and the exact Stokes segment (590).
 FLOPS_PER_STEP_POL = {"trace_fp64": 3007, "trace_fp32": 3035, "trace_df": 3007}
-# Fluid-grid (GRMHD-like snapshot) steps, unpolarized: the geodesic and transfer as above (506)
+# Fluid-grid (GRMHD-like snapshot) steps, unpolarized: the geodesic and transfer as above (491)
 # plus the grid emission instead of the analytic one: angles and cell coordinates (22), the
 # trilinear interpolation of 8 fields from 8 cells (147), the Jacobian to Cartesian components and
-# u, B (46), Kerr-Schild metric pieces (18), u^t from the normalisation (28), b^mu and b^2 (41),
-# the two-temperature plasma state (29) and the thermal-synchrotron j_I, alpha_I (164).
-FLOPS_PER_STEP_GRID = {"trace_fp64": 999, "trace_fp32": 1027, "trace_df": 999}
+# u, B (46), u^t from the normalisation (28), b^mu and b^2 (41), the two-temperature plasma state
+# (29) and the thermal-synchrotron j_I, alpha_I (164).  The FP32 and FP64 kernels take 1/r and the
+# Kerr-Schild F and L of the sample from the geodesic's right-hand side there; the double-float
+# kernel evaluates them (18) and the radius (15) itself.
+FLOPS_PER_STEP_GRID = {"trace_fp64": 968, "trace_fp32": 996, "trace_df": 1001}
 # Algorithmic bytes of one grid sample: 8 cells x 8 FP32 fields (before any cache reuse).
 GRID_BYTES_PER_SAMPLE = 256
 # Peaks for "alu"-bound kernels, derived from unit counts and the maximum clock: FP32 = 152 SMs x
