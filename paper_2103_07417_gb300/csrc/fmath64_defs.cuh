@@ -37,4 +37,15 @@ ART_FM_DEV double fm_double(int64_t b)
 #endif
 }
 
+ART_FM_DEV uint32_t fm_f32bits(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(x);
+#else
+    uint32_t b;
+    std::memcpy(&b, &x, sizeof b);
+    return b;
+#endif
+}
+
 }  // namespace art

@@ -29,17 +29,29 @@ namespace art {
 // (127 -> 1023) and the significand moved into place: the conversion's exact result.  The other
 // values (subnormal, infinite, NaN) are flagged by widen_special; a sample holding one takes the
 // conversion instruction for all its cells.
-__device__ __forceinline__ double widen(float f)
+ART_FM_DEV double widen(float f)
 {
-    const unsigned u = __float_as_uint(f), au = u & 0x7fffffffu;
-    const unsigned hi = au != 0u ? (au >> 3) + (896u << 20) : 0u;
-    return __hiloint2double((int)(hi | (u & 0x80000000u)), (int)(au << 29));
+    const uint32_t u = fm_f32bits(f), au = u & 0x7fffffffu;
+    const uint32_t hi = au != 0u ? (au >> 3) + (896u << 20) : 0u;
+    const uint32_t lo = au << 29;
+    return fm_double((int64_t)(((uint64_t)(hi | (u & 0x80000000u)) << 32) | (uint64_t)lo));
 }
 
-__device__ __forceinline__ unsigned widen_special(float f)
+ART_FM_DEV unsigned widen_special(float f)
 {
-    const unsigned au = __float_as_uint(f) & 0x7fffffffu;
+    const uint32_t au = fm_f32bits(f) & 0x7fffffffu;
     return (unsigned)(au != 0u) & (unsigned)(au - 0x00800000u >= 0x7f000000u);
+}
+
+// Two float4 of a snapshot cell through the read-only data path (a plain load on the host, where
+// the same code is built for the accuracy checks).
+ART_FM_DEV float4 grid_load(const float4* p)
+{
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
 }
 
 template <class Q>
@@ -57,7 +69,7 @@ ART_HD void grid_axis_clamped(Q f, int n, int& i0, Q& w)
 // (nullable): 1/r, F, Lx, Ly, Lz at the point, as the geodesic's right-hand side computed them
 // (spares a division and the Kerr-Schild pieces of ks_point).
 template <class Q>
-__device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, const Q* f,
+ART_FM_DEV void emission_grid(const RayState<Q>& s, Q r, Q kt, const Q* f,
                                               const Q* ks, const DevJob& J,
                                               const SynchConstT<Q>& S, Q* J4, Q* K7,
                                               int* edge = nullptr)
@@ -117,7 +129,7 @@ __device__ __forceinline__ void emission_grid(const RayState<Q>& s, Q r, Q kt, c
             const Q wt = ((c & 1) ? w1 : Q(1) - w1) * ((c & 2) ? w2 : Q(1) - w2) *
                          ((c & 4) ? w3 : Q(1) - w3);
             const float4* cell = S.grid + 2 * (((int64_t)kk * n2 + jj) * n1 + ii);
-            const float4 v0 = __ldg(cell), v1 = __ldg(cell + 1);
+            const float4 v0 = grid_load(cell), v1 = grid_load(cell + 1);
             P[0] = fmad(wt, conv(v0.x, special), P[0]);
             P[1] = fmad(wt, conv(v0.y, special), P[1]);
             P[2] = fmad(wt, conv(v0.z, special), P[2]);
